@@ -1,0 +1,1073 @@
+/*
+ * dispatch_oracle.c -- plain, slow FP64 CPU oracle of the per-patch update.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load this library.  It shares no code with
+ * the CUDA path and must never be called by the product path.
+ *
+ * What it computes (DISPATCH I, Nordlund et al. 2018):
+ *   - patches with guard zones on a periodic Cartesian level (Sec. 2.3,
+ *     "cartesian" component; task/patch data types, Sec. 2.1);
+ *   - a circular buffer of time slices per patch; a new state overwrites the
+ *     oldest slice (Sec. 3 A, single-task view);
+ *   - guard zones filled by linear interpolation in time from the neighbours'
+ *     slices (Sec. 3 A and the closing paragraph of Sec. 3 B);
+ *   - readiness by Eq. (1), t_self <= t_nbor + g dt_nbor, with grace g = 0;
+ *   - a dispatcher in two forms: a time-sorted ready queue (Sec. 3 B, mode i)
+ *     and a sweep over the ready set (same schedule, see below);
+ *   - local Courant time steps per patch (Sec. 5.1), quantised to powers of
+ *     two so that patch times are exact dyadic numbers;
+ *   - one step of ideal MHD per update.  The paper names its solvers (HLL-type
+ *     Riemann solvers, Sec. 4.1; constrained transport with edge-centred
+ *     electric fields, Sec. 4.3) but prints no scheme, so the scheme is the
+ *     textbook one: primitive variables, MC-limited slopes, a MUSCL-Hancock
+ *     half-step predictor, HLL face fluxes with Davis speed estimates, an
+ *     upwind HLL edge EMF for constrained transport, and a conservative update.
+ *
+ * Every floating-point expression is written in a fixed evaluation order and
+ * compiled with -ffp-contract=off, so that the result is a pure function of
+ * the inputs.  No blocking or reordering: each stage loops over the whole
+ * padded patch.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_ENOMEM (-2)
+#define ORC_EUNPHYS (-4)
+#define ORC_EDEADLOCK (-6)
+#define ORC_EBRACKET (-9)
+
+enum { RHO = 0, VX = 1, VY = 2, VZ = 3, PR = 4, BX = 5, BY = 6, BZ = 7 };
+
+typedef struct {
+  int n[3];
+  int64_t lo[3];
+  int nslot;
+  double **U, **bx, **by, **bz; /* [slot] -> interior arrays */
+  double *ts;                   /* time of each slot (NAN = empty) */
+  double *smax;                 /* signal speed sum of each slot */
+  int latest;
+  double dt_last;
+  int nnb;
+  int *nb;
+} opatch;
+
+typedef struct {
+  int np;
+  opatch *p;
+  double gamma, cfl, t0, dt_max, dx;
+  int64_t L[3];
+  int g, nslot, time_mode, disp_mode;
+  int64_t nsched, capsched;
+  int64_t *s_patch;
+  double *s_t, *s_dt;
+  int64_t n_updates, n_cells, n_sweeps, n_fallback;
+  int status;
+  char err[256];
+} orc_ctx;
+
+/* ------------------------------------------------------------------ */
+/* Cell-level physics                                                  */
+/* ------------------------------------------------------------------ */
+
+/* Primitive state from conserved U = (rho, m, E) and the six faces of the
+ * cell.  Heaviside-Lorentz units (E = -v x B, J = curl B, Sec. 4.3): total
+ * energy E = p/(gamma-1) + rho v^2/2 + B^2/2; cell-centred B is the mean of
+ * the two faces. */
+static void prim(const double u[5], double bxl, double bxr, double byl, double byr,
+                 double bzl, double bzr, double gamma, double W[8]) {
+  double rho = u[0];
+  double Bx = 0.5 * (bxl + bxr);
+  double By = 0.5 * (byl + byr);
+  double Bz = 0.5 * (bzl + bzr);
+  double vx = u[1] / rho;
+  double vy = u[2] / rho;
+  double vz = u[3] / rho;
+  double ke = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+  double me = 0.5 * (Bx * Bx + By * By + Bz * Bz);
+  double p = (gamma - 1.0) * (u[4] - ke - me);
+  W[RHO] = rho; W[VX] = vx; W[VY] = vy; W[VZ] = vz; W[PR] = p;
+  W[BX] = Bx; W[BY] = By; W[BZ] = Bz;
+}
+
+/* Fast magnetosonic speed along the axis whose field component is bn:
+ * c_f^2 = [a^2 + B^2/rho + sqrt((a^2 + B^2/rho)^2 - 4 a^2 bn^2/rho)] / 2. */
+static double cfast(double gamma, double rho, double p, double bn, double bt1, double bt2) {
+  double a2 = gamma * p / rho;
+  double bb = (bn * bn + bt1 * bt1 + bt2 * bt2) / rho;
+  double ca2 = bn * bn / rho;
+  double s = a2 + bb;
+  double disc = s * s - 4.0 * a2 * ca2;
+  if (disc < 0.0) disc = 0.0;
+  return sqrt(0.5 * (s + sqrt(disc)));
+}
+
+/* Monotonised-central limited slope. */
+static double mc(double dl, double dr) {
+  if (dl * dr <= 0.0) return 0.0;
+  double s = fmin(fmin(2.0 * fabs(dl), 2.0 * fabs(dr)), 0.5 * fabs(dl + dr));
+  return dl > 0.0 ? s : -s;
+}
+
+/* Hancock half-step predictor in primitive form, with d/dx_d replaced by the
+ * limited slope dW_d (h = dt/(2 dx)):
+ *   rho_t = -v.grad rho - rho div v
+ *   v_t   = -(v.grad) v - (grad p + grad B^2/2 - (B.grad) B)/rho
+ *   p_t   = -v.grad p - gamma p div v
+ *   B_t   = (B.grad) v - (v.grad) B - B div v                              */
+static void predict(const double W[8], const double *dX, const double *dY, const double *dZ,
+                    double gamma, double h, double Ws[8]) {
+  double rho = W[RHO], vx = W[VX], vy = W[VY], vz = W[VZ], p = W[PR];
+  double Bx = W[BX], By = W[BY], Bz = W[BZ];
+  double divv = dX[VX] + dY[VY] + dZ[VZ];
+  double r_rho = -(vx * dX[RHO] + vy * dY[RHO] + vz * dZ[RHO]) - rho * divv;
+  double gpx = dX[PR] + (Bx * dX[BX] + By * dX[BY] + Bz * dX[BZ]);
+  double gpy = dY[PR] + (Bx * dY[BX] + By * dY[BY] + Bz * dY[BZ]);
+  double gpz = dZ[PR] + (Bx * dZ[BX] + By * dZ[BY] + Bz * dZ[BZ]);
+  double tx = Bx * dX[BX] + By * dY[BX] + Bz * dZ[BX];
+  double ty = Bx * dX[BY] + By * dY[BY] + Bz * dZ[BY];
+  double tz = Bx * dX[BZ] + By * dY[BZ] + Bz * dZ[BZ];
+  double r_vx = -(vx * dX[VX] + vy * dY[VX] + vz * dZ[VX]) - (gpx - tx) / rho;
+  double r_vy = -(vx * dX[VY] + vy * dY[VY] + vz * dZ[VY]) - (gpy - ty) / rho;
+  double r_vz = -(vx * dX[VZ] + vy * dY[VZ] + vz * dZ[VZ]) - (gpz - tz) / rho;
+  double r_p = -(vx * dX[PR] + vy * dY[PR] + vz * dZ[PR]) - gamma * p * divv;
+  double r_bx = (Bx * dX[VX] + By * dY[VX] + Bz * dZ[VX]) - (vx * dX[BX] + vy * dY[BX] + vz * dZ[BX]) - Bx * divv;
+  double r_by = (Bx * dX[VY] + By * dY[VY] + Bz * dZ[VY]) - (vx * dX[BY] + vy * dY[BY] + vz * dZ[BY]) - By * divv;
+  double r_bz = (Bx * dX[VZ] + By * dY[VZ] + Bz * dZ[VZ]) - (vx * dX[BZ] + vy * dY[BZ] + vz * dZ[BZ]) - Bz * divv;
+  Ws[RHO] = rho + h * r_rho;
+  Ws[VX] = vx + h * r_vx;
+  Ws[VY] = vy + h * r_vy;
+  Ws[VZ] = vz + h * r_vz;
+  Ws[PR] = p + h * r_p;
+  Ws[BX] = Bx + h * r_bx;
+  Ws[BY] = By + h * r_by;
+  Ws[BZ] = Bz + h * r_bz;
+}
+
+/* HLL flux through a face with normal axis d (Harten, Lax & van Leer 1983,
+ * Davis speed estimates).  WL, WR are lab-frame primitive states; the normal
+ * field of both is replaced by their mean.  Output F[0..4] in the lab frame
+ * (mass, momentum x,y,z, energy), F[5], F[6] the induction fluxes of the two
+ * tangential field components (cyclic order after d), S[0] = S_L, S[1] = S_R. */
+static void hll(const double WL[8], const double WR[8], int d, double gamma, double F[7], double S[2]) {
+  int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  double gm1 = gamma - 1.0;
+  double bn = 0.5 * (WL[BX + d] + WR[BX + d]);
+  double FL[7], FR[7], UL[7], UR[7], cL, cR, vnL, vnR;
+  for (int side = 0; side < 2; side++) {
+    const double *W = side ? WR : WL;
+    double *Fs = side ? FR : FL;
+    double *Us = side ? UR : UL;
+    double rho = W[RHO], p = W[PR];
+    double vn = W[VX + d], vt1 = W[VX + t1], vt2 = W[VX + t2];
+    double bt1 = W[BX + t1], bt2 = W[BX + t2];
+    double v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
+    double B2 = bn * bn + bt1 * bt1 + bt2 * bt2;
+    double E = p / gm1 + 0.5 * rho * v2 + 0.5 * B2;
+    double PT = p + 0.5 * B2;
+    double vB = vn * bn + vt1 * bt1 + vt2 * bt2;
+    double cf = cfast(gamma, rho, p, bn, bt1, bt2);
+    Us[0] = rho; Us[1] = rho * vn; Us[2] = rho * vt1; Us[3] = rho * vt2; Us[4] = E;
+    Us[5] = bt1; Us[6] = bt2;
+    Fs[0] = rho * vn;
+    Fs[1] = rho * vn * vn + PT - bn * bn;
+    Fs[2] = rho * vn * vt1 - bn * bt1;
+    Fs[3] = rho * vn * vt2 - bn * bt2;
+    Fs[4] = (E + PT) * vn - bn * vB;
+    Fs[5] = vn * bt1 - vt1 * bn;
+    Fs[6] = vn * bt2 - vt2 * bn;
+    if (side) { cR = cf; vnR = vn; } else { cL = cf; vnL = vn; }
+  }
+  double SL = fmin(vnL - cL, vnR - cR);
+  double SR = fmax(vnL + cL, vnR + cR);
+  double Fr[7];
+  for (int c = 0; c < 7; c++) {
+    if (SL >= 0.0) Fr[c] = FL[c];
+    else if (SR <= 0.0) Fr[c] = FR[c];
+    else Fr[c] = (SR * FL[c] - SL * FR[c] + SL * SR * (UR[c] - UL[c])) / (SR - SL);
+  }
+  F[0] = Fr[0];
+  F[1 + d] = Fr[1];
+  F[1 + t1] = Fr[2];
+  F[1 + t2] = Fr[3];
+  F[4] = Fr[4];
+  F[5] = Fr[5];
+  F[6] = Fr[6];
+  S[0] = SL;
+  S[1] = SR;
+}
+
+/* Upwind HLL edge EMF (two-dimensional HLL average of the four corner
+ * states around an edge along axis e; a and b are the next two axes in cyclic
+ * order).  Corner LL is the corner of the cell on the low side of both a and
+ * b, RL the cell on the high-a/low-b side, LR low-a/high-b, RR high/high.
+ * E_e at a corner is v_b B_a - v_a B_b (E = -v x B).  apa/ama are
+ * max(0, +-S) over the two a-faces that touch the edge, apb/amb over the two
+ * b-faces. */
+static double emf(const double Wll[8], const double Wrl[8], const double Wlr[8], const double Wrr[8],
+                  int e, double apa, double ama, double apb, double amb) {
+  int a = (e + 1) % 3, b = (e + 2) % 3;
+  double Ell = Wll[VX + b] * Wll[BX + a] - Wll[VX + a] * Wll[BX + b];
+  double Erl = Wrl[VX + b] * Wrl[BX + a] - Wrl[VX + a] * Wrl[BX + b];
+  double Elr = Wlr[VX + b] * Wlr[BX + a] - Wlr[VX + a] * Wlr[BX + b];
+  double Err = Wrr[VX + b] * Wrr[BX + a] - Wrr[VX + a] * Wrr[BX + b];
+  double BbL = 0.5 * (Wll[BX + b] + Wlr[BX + b]);
+  double BbR = 0.5 * (Wrl[BX + b] + Wrr[BX + b]);
+  double BaL = 0.5 * (Wll[BX + a] + Wrl[BX + a]);
+  double BaR = 0.5 * (Wlr[BX + a] + Wrr[BX + a]);
+  double num = apa * apb * Ell + ama * apb * Erl + apa * amb * Elr + ama * amb * Err;
+  double den = (apa + ama) * (apb + amb);
+  return num / den + apa * ama / (apa + ama) * (BbR - BbL) - apb * amb / (apb + amb) * (BaR - BaL);
+}
+
+/* Power of two not above x (x > 0), exact via frexp. */
+static double pow2_floor(double x) {
+  int e;
+  frexp(x, &e);
+  return ldexp(1.0, e - 1);
+}
+
+/* ------------------------------------------------------------------ */
+/* Exported cell-level entry points (unit pins)                        */
+/* ------------------------------------------------------------------ */
+void orc_prim(const double *u, const double *faces, double gamma, double *W) {
+  prim(u, faces[0], faces[1], faces[2], faces[3], faces[4], faces[5], gamma, W);
+}
+double orc_cfast(double gamma, double rho, double p, double bn, double bt1, double bt2) {
+  return cfast(gamma, rho, p, bn, bt1, bt2);
+}
+double orc_mc(double dl, double dr) { return mc(dl, dr); }
+void orc_predict(const double *W, const double *dX, const double *dY, const double *dZ, double gamma,
+                 double h, double *Ws) {
+  predict(W, dX, dY, dZ, gamma, h, Ws);
+}
+void orc_hll(const double *WL, const double *WR, int d, double gamma, double *F, double *S) {
+  hll(WL, WR, d, gamma, F, S);
+}
+double orc_emf(const double *Wll, const double *Wrl, const double *Wlr, const double *Wrr, int e,
+               double apa, double ama, double apb, double amb) {
+  return emf(Wll, Wrl, Wlr, Wrr, e, apa, ama, apb, amb);
+}
+double orc_pow2_floor(double x) { return pow2_floor(x); }
+
+/* ------------------------------------------------------------------ */
+/* Context, layout and neighbours                                      */
+/* ------------------------------------------------------------------ */
+static int64_t imod(int64_t a, int64_t m) {
+  int64_t r = a % m;
+  return r < 0 ? r + m : r;
+}
+static int64_t ncell(const opatch *P) { return (int64_t)P->n[0] * P->n[1] * P->n[2]; }
+static int64_t nfx(const opatch *P) { return (int64_t)(P->n[0] + 1) * P->n[1] * P->n[2]; }
+static int64_t nfy(const opatch *P) { return (int64_t)P->n[0] * (P->n[1] + 1) * P->n[2]; }
+static int64_t nfz(const opatch *P) { return (int64_t)P->n[0] * P->n[1] * (P->n[2] + 1); }
+
+/* Does some periodic image of [qlo, qlo+qn) intersect [plo-g, plo+pn+g)?
+ * Writes the set of intersecting image shifts as a bit mask (-L, 0, +L). */
+static int axis_hit(int64_t plo, int pn, int64_t qlo, int qn, int g, int64_t L) {
+  int mask = 0;
+  for (int s = -1; s <= 1; s++) {
+    int64_t a = qlo + s * L, b = a + qn;
+    if (a < plo + pn + g && b > plo - g) mask |= 1 << (s + 1);
+  }
+  return mask;
+}
+
+void orc_destroy(orc_ctx *c);
+
+orc_ctx *orc_create(int np, const int32_t *n, const int64_t *lo, double gamma, double cfl, double t0,
+                    double dt_max, const double *box_len, const int32_t *base, int nguard, int nslot,
+                    int time_mode, int disp_mode) {
+  if (np <= 0 || nguard < 2 || nslot < 3) return NULL;
+  /* a patch must be wider than its guard depth so that every guard cell and
+   * guard face lies in one of the adjacent patches */
+  for (int i = 0; i < 3 * np; i++)
+    if (n[i] <= nguard) return NULL;
+  orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+  c->np = np;
+  c->gamma = gamma; c->cfl = cfl; c->t0 = t0; c->dt_max = dt_max;
+  c->g = nguard; c->nslot = nslot; c->time_mode = time_mode; c->disp_mode = disp_mode;
+  c->dx = box_len[0] / base[0];
+  for (int d = 0; d < 3; d++) c->L[d] = base[d];
+  c->p = (opatch *)calloc(np, sizeof(opatch));
+  for (int i = 0; i < np; i++) {
+    opatch *P = &c->p[i];
+    for (int d = 0; d < 3; d++) { P->n[d] = n[3 * i + d]; P->lo[d] = lo[3 * i + d]; }
+    P->nslot = nslot;
+    P->U = (double **)calloc(nslot, sizeof(double *));
+    P->bx = (double **)calloc(nslot, sizeof(double *));
+    P->by = (double **)calloc(nslot, sizeof(double *));
+    P->bz = (double **)calloc(nslot, sizeof(double *));
+    P->ts = (double *)malloc(nslot * sizeof(double));
+    P->smax = (double *)calloc(nslot, sizeof(double));
+    for (int s = 0; s < nslot; s++) {
+      P->U[s] = (double *)calloc(5 * ncell(P), sizeof(double));
+      P->bx[s] = (double *)calloc(nfx(P), sizeof(double));
+      P->by[s] = (double *)calloc(nfy(P), sizeof(double));
+      P->bz[s] = (double *)calloc(nfz(P), sizeof(double));
+      P->ts[s] = NAN;
+      if (!P->U[s] || !P->bx[s] || !P->by[s] || !P->bz[s]) { orc_destroy(c); return NULL; }
+    }
+    P->latest = 0;
+    P->dt_last = 0.0;
+  }
+  /* neighbours: every patch with an interior that some periodic image puts
+   * inside this patch's padded box (the patch itself counts only through a
+   * non-trivial image) */
+  int *tmp = (int *)malloc(sizeof(int) * np);
+  for (int i = 0; i < np; i++) {
+    opatch *P = &c->p[i];
+    int cnt = 0;
+    for (int j = 0; j < np; j++) {
+      opatch *Q = &c->p[j];
+      int m[3], ok = 1;
+      for (int d = 0; d < 3; d++) {
+        m[d] = axis_hit(P->lo[d], P->n[d], Q->lo[d], Q->n[d], nguard, c->L[d]);
+        if (!m[d]) ok = 0;
+      }
+      if (!ok) continue;
+      if (j == i && m[0] == 2 && m[1] == 2 && m[2] == 2) continue;
+      tmp[cnt++] = j;
+    }
+    P->nnb = cnt;
+    P->nb = (int *)malloc(sizeof(int) * (cnt > 0 ? cnt : 1));
+    memcpy(P->nb, tmp, sizeof(int) * cnt);
+  }
+  free(tmp);
+  return c;
+}
+
+void orc_destroy(orc_ctx *c) {
+  if (!c) return;
+  for (int i = 0; i < c->np; i++) {
+    opatch *P = &c->p[i];
+    for (int s = 0; s < c->nslot; s++) {
+      if (P->U) free(P->U[s]);
+      if (P->bx) free(P->bx[s]);
+      if (P->by) free(P->by[s]);
+      if (P->bz) free(P->bz[s]);
+    }
+    free(P->U); free(P->bx); free(P->by); free(P->bz);
+    free(P->ts); free(P->smax); free(P->nb);
+  }
+  free(c->p);
+  free(c->s_patch); free(c->s_t); free(c->s_dt);
+  free(c);
+}
+
+int orc_num_nbors(orc_ctx *c, int P, int *out) {
+  if (out) memcpy(out, c->p[P].nb, sizeof(int) * c->p[P].nnb);
+  return c->p[P].nnb;
+}
+
+const char *orc_last_error(orc_ctx *c) { return c->err; }
+
+/* Signal speed sum of a stored slice: max over interior cells of
+ * sum_d (|v_d| + c_f,d). */
+static double slice_smax(orc_ctx *c, opatch *P, int s, int *bad) {
+  int nx = P->n[0], ny = P->n[1], nz = P->n[2];
+  int64_t nc = ncell(P);
+  double m = 0.0;
+  *bad = 0;
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        int64_t id = ((int64_t)k * ny + j) * nx + i;
+        double u[5], W[8];
+        for (int q = 0; q < 5; q++) u[q] = P->U[s][q * nc + id];
+        double bxl = P->bx[s][((int64_t)k * ny + j) * (nx + 1) + i];
+        double bxr = P->bx[s][((int64_t)k * ny + j) * (nx + 1) + i + 1];
+        double byl = P->by[s][((int64_t)k * (ny + 1) + j) * nx + i];
+        double byr = P->by[s][((int64_t)k * (ny + 1) + j + 1) * nx + i];
+        double bzl = P->bz[s][((int64_t)k * ny + j) * nx + i];
+        double bzr = P->bz[s][((int64_t)(k + 1) * ny + j) * nx + i];
+        prim(u, bxl, bxr, byl, byr, bzl, bzr, c->gamma, W);
+        if (!(W[RHO] > 0.0) || !(W[PR] > 0.0)) *bad = 1;
+        double cx = cfast(c->gamma, W[RHO], W[PR], W[BX], W[BY], W[BZ]);
+        double cy = cfast(c->gamma, W[RHO], W[PR], W[BY], W[BZ], W[BX]);
+        double cz = cfast(c->gamma, W[RHO], W[PR], W[BZ], W[BX], W[BY]);
+        double sum = (fabs(W[VX]) + cx) + (fabs(W[VY]) + cy) + (fabs(W[VZ]) + cz);
+        if (sum > m) m = sum;
+      }
+  return m;
+}
+
+/* Load the initial state of every patch (concatenated in patch order, each
+ * interior-only: U[5][nz][ny][nx], bx[nz][ny][nx+1], by[nz][ny+1][nx],
+ * bz[nz+1][ny][nx]) into slot 0 at time t0. */
+int orc_set_state(orc_ctx *c, const double *U, const double *bx, const double *by, const double *bz) {
+  int64_t oU = 0, ox = 0, oy = 0, oz = 0;
+  for (int i = 0; i < c->np; i++) {
+    opatch *P = &c->p[i];
+    for (int s = 0; s < c->nslot; s++) P->ts[s] = NAN;
+    P->latest = 0;
+    P->ts[0] = c->t0;
+    P->dt_last = 0.0;
+    memcpy(P->U[0], U + oU, sizeof(double) * 5 * ncell(P));
+    memcpy(P->bx[0], bx + ox, sizeof(double) * nfx(P));
+    memcpy(P->by[0], by + oy, sizeof(double) * nfy(P));
+    memcpy(P->bz[0], bz + oz, sizeof(double) * nfz(P));
+    oU += 5 * ncell(P); ox += nfx(P); oy += nfy(P); oz += nfz(P);
+    int bad;
+    P->smax[0] = slice_smax(c, P, 0, &bad);
+    if (bad) { snprintf(c->err, sizeof c->err, "non-positive rho or p in patch %d", i); return ORC_EUNPHYS; }
+  }
+  c->nsched = 0;
+  c->n_updates = c->n_cells = c->n_sweeps = c->n_fallback = 0;
+  c->status = 0;
+  return ORC_OK;
+}
+
+/* Load one stored slot of one patch (used to reproduce a single update from
+ * a saved dispatcher state).  The signal speed of the slot is recomputed. */
+int orc_set_slot(orc_ctx *c, int ip, int s, double t, const double *U, const double *bx, const double *by,
+                 const double *bz) {
+  opatch *P = &c->p[ip];
+  if (s < 0 || s >= c->nslot) return ORC_EINVAL;
+  P->ts[s] = t;
+  if (isnan(t)) return ORC_OK;
+  memcpy(P->U[s], U, sizeof(double) * 5 * ncell(P));
+  memcpy(P->bx[s], bx, sizeof(double) * nfx(P));
+  memcpy(P->by[s], by, sizeof(double) * nfy(P));
+  memcpy(P->bz[s], bz, sizeof(double) * nfz(P));
+  int bad;
+  P->smax[s] = slice_smax(c, P, s, &bad);
+  return bad ? ORC_EUNPHYS : ORC_OK;
+}
+
+int orc_set_latest(orc_ctx *c, int ip, int s, double dt_last) {
+  if (s < 0 || s >= c->nslot) return ORC_EINVAL;
+  c->p[ip].latest = s;
+  c->p[ip].dt_last = dt_last;
+  return ORC_OK;
+}
+
+int orc_get_state(orc_ctx *c, double *U, double *bx, double *by, double *bz) {
+  int64_t oU = 0, ox = 0, oy = 0, oz = 0;
+  for (int i = 0; i < c->np; i++) {
+    opatch *P = &c->p[i];
+    int s = P->latest;
+    memcpy(U + oU, P->U[s], sizeof(double) * 5 * ncell(P));
+    memcpy(bx + ox, P->bx[s], sizeof(double) * nfx(P));
+    memcpy(by + oy, P->by[s], sizeof(double) * nfy(P));
+    memcpy(bz + oz, P->bz[s], sizeof(double) * nfz(P));
+    oU += 5 * ncell(P); ox += nfx(P); oy += nfy(P); oz += nfz(P);
+  }
+  return ORC_OK;
+}
+
+int orc_get_times(orc_ctx *c, double *t, double *dt_last, double *smax) {
+  for (int i = 0; i < c->np; i++) {
+    opatch *P = &c->p[i];
+    if (t) t[i] = P->ts[P->latest];
+    if (dt_last) dt_last[i] = P->dt_last;
+    if (smax) smax[i] = P->smax[P->latest];
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Guard fill (time interpolation)                                     */
+/* ------------------------------------------------------------------ */
+
+/* Which stored slices of patch Q supply values at time t: a slice at exactly
+ * t is copied; otherwise the two newest slices must bracket t and are
+ * interpolated linearly with weight w = (t - t_a)/(t_b - t_a). */
+static int pick(orc_ctx *c, opatch *Q, double t, int *sa, int *sb, double *w) {
+  int L = Q->latest, Pv = (Q->latest + c->nslot - 1) % c->nslot;
+  if (Q->ts[L] == t) { *sa = L; *sb = -1; *w = 0.0; return ORC_OK; }
+  if (Q->ts[Pv] == t) { *sa = Pv; *sb = -1; *w = 0.0; return ORC_OK; }
+  double ta = Q->ts[Pv], tb = Q->ts[L];
+  if (ta < t && t < tb) {
+    *sa = Pv; *sb = L; *w = (t - ta) / (tb - ta);
+    return ORC_OK;
+  }
+  return ORC_EBRACKET;
+}
+
+static double tval(const double *A, const double *B, int64_t idx, double w) {
+  if (!B) return A[idx];
+  return A[idx] + w * (B[idx] - A[idx]);
+}
+
+/* Locate the patch among P's neighbours (or P itself) whose interior holds
+ * the level cell (gx, gy, gz) (periodic), and the local cell index there. */
+static int owner(orc_ctx *c, opatch *P, int ip, int64_t gx, int64_t gy, int64_t gz, int loc[3]) {
+  int64_t g[3] = {gx, gy, gz};
+  for (int q = -1; q < P->nnb; q++) {
+    int iq = q < 0 ? ip : P->nb[q];
+    opatch *Q = &c->p[iq];
+    int in = 1;
+    for (int d = 0; d < 3; d++) {
+      int64_t r = imod(g[d] - Q->lo[d], c->L[d]);
+      if (r >= Q->n[d]) { in = 0; break; }
+      loc[d] = (int)r;
+    }
+    if (in) return iq;
+  }
+  return -1;
+}
+
+typedef struct {
+  int N[3];          /* padded cell counts per axis */
+  double *U;         /* [5][Nz][Ny][Nx] */
+  double *bx, *by, *bz;
+} padded;
+
+#define PC(pd, i, j, k) ((((int64_t)(k) + g) * (pd)->N[1] + ((j) + g)) * (pd)->N[0] + ((i) + g))
+#define PFX(pd, i, j, k) ((((int64_t)(k) + g) * (pd)->N[1] + ((j) + g)) * ((pd)->N[0] + 1) + ((i) + g))
+#define PFY(pd, i, j, k) ((((int64_t)(k) + g) * ((pd)->N[1] + 1) + ((j) + g)) * (pd)->N[0] + ((i) + g))
+#define PFZ(pd, i, j, k) ((((int64_t)(k) + g) * (pd)->N[1] + ((j) + g)) * (pd)->N[0] + ((i) + g))
+
+/* Fill the padded box of patch ip at its current time.  Cell-centred values
+ * of guard cells come from the neighbour owning the cell.  A face on one of
+ * P's interior cells is P's own; any other face is taken from the patch that
+ * owns the cell on the face's upper side. */
+static int fill_padded(orc_ctx *c, int ip, padded *pd) {
+  opatch *P = &c->p[ip];
+  int g = c->g;
+  int nx = P->n[0], ny = P->n[1], nz = P->n[2];
+  int Nx = nx + 2 * g, Ny = ny + 2 * g, Nz = nz + 2 * g;
+  int64_t Nc = (int64_t)Nx * Ny * Nz;
+  double t = P->ts[P->latest];
+  int s0 = P->latest;
+  int64_t nc = ncell(P);
+  pd->N[0] = Nx; pd->N[1] = Ny; pd->N[2] = Nz;
+  for (int k = -g; k < nz + g; k++)
+    for (int j = -g; j < ny + g; j++)
+      for (int i = -g; i < nx + g; i++) {
+        int64_t pi = PC(pd, i, j, k);
+        if (i >= 0 && i < nx && j >= 0 && j < ny && k >= 0 && k < nz) {
+          int64_t id = ((int64_t)k * ny + j) * nx + i;
+          for (int q = 0; q < 5; q++) pd->U[q * Nc + pi] = P->U[s0][q * nc + id];
+          continue;
+        }
+        int loc[3], sa, sb;
+        double w;
+        int iq = owner(c, P, ip, P->lo[0] + i, P->lo[1] + j, P->lo[2] + k, loc);
+        if (iq < 0) return ORC_EINVAL;
+        opatch *Q = &c->p[iq];
+        if (pick(c, Q, t, &sa, &sb, &w) != ORC_OK) return ORC_EBRACKET;
+        int64_t qc = ncell(Q);
+        int64_t id = ((int64_t)loc[2] * Q->n[1] + loc[1]) * Q->n[0] + loc[0];
+        for (int q = 0; q < 5; q++)
+          pd->U[q * Nc + pi] = tval(Q->U[sa] + q * qc, sb >= 0 ? Q->U[sb] + q * qc : NULL, id, w);
+      }
+  /* faces, one axis at a time */
+  for (int ax = 0; ax < 3; ax++) {
+    int ex = ax == 0, ey = ax == 1, ez = ax == 2;
+    for (int k = -g; k < nz + g + ez; k++)
+      for (int j = -g; j < ny + g + ey; j++)
+        for (int i = -g; i < nx + g + ex; i++) {
+          int64_t pi = ax == 0 ? PFX(pd, i, j, k) : ax == 1 ? PFY(pd, i, j, k) : PFZ(pd, i, j, k);
+          double *dst = ax == 0 ? pd->bx : ax == 1 ? pd->by : pd->bz;
+          int own = (i >= 0 && i < nx + ex && j >= 0 && j < ny + ey && k >= 0 && k < nz + ez);
+          if (own) {
+            int64_t id = ax == 0 ? ((int64_t)k * ny + j) * (nx + 1) + i
+                       : ax == 1 ? ((int64_t)k * (ny + 1) + j) * nx + i
+                                 : ((int64_t)k * ny + j) * nx + i;
+            dst[pi] = (ax == 0 ? P->bx[s0] : ax == 1 ? P->by[s0] : P->bz[s0])[id];
+            continue;
+          }
+          int loc[3], sa, sb;
+          double w;
+          int iq = owner(c, P, ip, P->lo[0] + i, P->lo[1] + j, P->lo[2] + k, loc);
+          if (iq < 0) return ORC_EINVAL;
+          opatch *Q = &c->p[iq];
+          if (pick(c, Q, t, &sa, &sb, &w) != ORC_OK) return ORC_EBRACKET;
+          int qx = Q->n[0], qy = Q->n[1];
+          int64_t id = ax == 0 ? ((int64_t)loc[2] * qy + loc[1]) * (qx + 1) + loc[0]
+                     : ax == 1 ? ((int64_t)loc[2] * (qy + 1) + loc[1]) * qx + loc[0]
+                               : ((int64_t)loc[2] * qy + loc[1]) * qx + loc[0];
+          double **arr = ax == 0 ? Q->bx : ax == 1 ? Q->by : Q->bz;
+          dst[pi] = tval(arr[sa], sb >= 0 ? arr[sb] : NULL, id, w);
+        }
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* One update of one patch                                             */
+/* ------------------------------------------------------------------ */
+
+/* Advance patch ip by dt from its current time, writing the new interior
+ * state into the given arrays and its signal-speed sum into *smax_out. */
+static int update_patch(orc_ctx *c, int ip, double dt, double *oU, double *obx, double *oby, double *obz,
+                        double *smax_out, int64_t *nfallback) {
+  opatch *P = &c->p[ip];
+  int g = c->g;
+  int nx = P->n[0], ny = P->n[1], nz = P->n[2];
+  int Nx = nx + 2 * g, Ny = ny + 2 * g, Nz = nz + 2 * g;
+  int64_t Nc = (int64_t)Nx * Ny * Nz;
+  int64_t Nfx = (int64_t)(Nx + 1) * Ny * Nz, Nfy = (int64_t)Nx * (Ny + 1) * Nz, Nfz = (int64_t)Nx * Ny * (Nz + 1);
+  int64_t Ne = (int64_t)(Nx + 1) * (Ny + 1) * (Nz + 1);
+  padded pdv, *pd = &pdv;
+  pd->U = (double *)malloc(sizeof(double) * 5 * Nc);
+  pd->bx = (double *)malloc(sizeof(double) * Nfx);
+  pd->by = (double *)malloc(sizeof(double) * Nfy);
+  pd->bz = (double *)malloc(sizeof(double) * Nfz);
+  double *W = (double *)malloc(sizeof(double) * 8 * Nc);
+  double *Ws = (double *)malloc(sizeof(double) * 8 * Nc);
+  double *dW = (double *)malloc(sizeof(double) * 24 * Nc);
+  double *F[3], *S[3];
+  for (int d = 0; d < 3; d++) {
+    F[d] = (double *)malloc(sizeof(double) * 5 * Ne);
+    S[d] = (double *)malloc(sizeof(double) * 2 * Ne);
+  }
+  double *E[3];
+  for (int d = 0; d < 3; d++) E[d] = (double *)malloc(sizeof(double) * Ne);
+  int rc = fill_padded(c, ip, pd);
+  if (rc != ORC_OK) goto done;
+
+  double gamma = c->gamma;
+  double h = 0.5 * dt / c->dx;
+  double dtdx = dt / c->dx;
+
+  /* A4: primitives on every padded cell */
+  for (int k = -g; k < nz + g; k++)
+    for (int j = -g; j < ny + g; j++)
+      for (int i = -g; i < nx + g; i++) {
+        int64_t pi = PC(pd, i, j, k);
+        double u[5], w8[8];
+        for (int q = 0; q < 5; q++) u[q] = pd->U[q * Nc + pi];
+        prim(u, pd->bx[PFX(pd, i, j, k)], pd->bx[PFX(pd, i + 1, j, k)], pd->by[PFY(pd, i, j, k)],
+             pd->by[PFY(pd, i, j + 1, k)], pd->bz[PFZ(pd, i, j, k)], pd->bz[PFZ(pd, i, j, k + 1)], gamma, w8);
+        for (int q = 0; q < 8; q++) W[q * Nc + pi] = w8[q];
+      }
+
+  /* A5/A6: limited slopes and the half-step predictor on cells [-1, n] */
+  for (int k = -1; k <= nz; k++)
+    for (int j = -1; j <= ny; j++)
+      for (int i = -1; i <= nx; i++) {
+        int64_t pi = PC(pd, i, j, k);
+        double w8[8], d3[3][8], ws[8];
+        for (int q = 0; q < 8; q++) w8[q] = W[q * Nc + pi];
+        for (int d = 0; d < 3; d++) {
+          int64_t pm = d == 0 ? PC(pd, i - 1, j, k) : d == 1 ? PC(pd, i, j - 1, k) : PC(pd, i, j, k - 1);
+          int64_t pp = d == 0 ? PC(pd, i + 1, j, k) : d == 1 ? PC(pd, i, j + 1, k) : PC(pd, i, j, k + 1);
+          for (int q = 0; q < 8; q++) {
+            if (q == BX + d) {
+              double fl = d == 0 ? pd->bx[PFX(pd, i, j, k)] : d == 1 ? pd->by[PFY(pd, i, j, k)] : pd->bz[PFZ(pd, i, j, k)];
+              double fr = d == 0 ? pd->bx[PFX(pd, i + 1, j, k)] : d == 1 ? pd->by[PFY(pd, i, j + 1, k)] : pd->bz[PFZ(pd, i, j, k + 1)];
+              d3[d][q] = fr - fl;
+            } else {
+              double dl = w8[q] - W[q * Nc + pm];
+              double dr = W[q * Nc + pp] - w8[q];
+              d3[d][q] = mc(dl, dr);
+            }
+          }
+        }
+        predict(w8, d3[0], d3[1], d3[2], gamma, h, ws);
+        /* positivity fallback: any face state with rho <= 0 or p <= 0 */
+        int bad = 0;
+        for (int d = 0; d < 3; d++) {
+          double rp = ws[RHO] + 0.5 * d3[d][RHO], rm = ws[RHO] - 0.5 * d3[d][RHO];
+          double pp_ = ws[PR] + 0.5 * d3[d][PR], pm_ = ws[PR] - 0.5 * d3[d][PR];
+          if (!(rp > 0.0) || !(rm > 0.0) || !(pp_ > 0.0) || !(pm_ > 0.0)) bad = 1;
+        }
+        if (bad) {
+          (*nfallback)++;
+          for (int d = 0; d < 3; d++)
+            for (int q = 0; q < 8; q++) d3[d][q] = 0.0;
+          for (int q = 0; q < 8; q++) ws[q] = w8[q];
+        }
+        for (int q = 0; q < 8; q++) Ws[q * Nc + pi] = ws[q];
+        for (int d = 0; d < 3; d++)
+          for (int q = 0; q < 8; q++) dW[(d * 8 + q) * Nc + pi] = d3[d][q];
+      }
+
+#define EI(i, j, k) ((((int64_t)(k) + g) * (Ny + 1) + ((j) + g)) * (Nx + 1) + ((i) + g))
+  /* A7: HLL fluxes.  Face index i on axis d is the face at i-1/2 between
+   * cells i-1 and i; computed for all faces whose two cells lie in [-1, n]. */
+  for (int d = 0; d < 3; d++) {
+    int ex = d == 0, ey = d == 1, ez = d == 2;
+    for (int k = ez ? 0 : -1; k <= nz; k++)
+      for (int j = ey ? 0 : -1; j <= ny; j++)
+        for (int i = ex ? 0 : -1; i <= nx; i++) {
+          int64_t pr = PC(pd, i, j, k);
+          int64_t pl = PC(pd, i - ex, j - ey, k - ez);
+          double WL[8], WR[8], f7[7], s2[2];
+          for (int q = 0; q < 8; q++) {
+            WL[q] = Ws[q * Nc + pl] + 0.5 * dW[(d * 8 + q) * Nc + pl];
+            WR[q] = Ws[q * Nc + pr] - 0.5 * dW[(d * 8 + q) * Nc + pr];
+          }
+          hll(WL, WR, d, gamma, f7, s2);
+          int64_t e = EI(i, j, k);
+          for (int q = 0; q < 5; q++) F[d][q * Ne + e] = f7[q];
+          S[d][e] = s2[0];
+          S[d][Ne + e] = s2[1];
+        }
+  }
+
+  /* A8: edge EMFs.  E[e] at index (i,j,k) is the edge along axis e located at
+   * the low corner of cell (i,j,k) in the two other axes. */
+  for (int e = 0; e < 3; e++) {
+    int a = (e + 1) % 3, b = (e + 2) % 3;
+    int lo3[3] = {0, 0, 0}, hi3[3] = {nx, ny, nz};
+    hi3[a] += 1; hi3[b] += 1;
+    for (int k = lo3[2]; k < hi3[2]; k++)
+      for (int j = lo3[1]; j < hi3[1]; j++)
+        for (int i = lo3[0]; i < hi3[0]; i++) {
+          int o[3] = {i, j, k};
+          int cll[3], crl[3], clr[3], crr[3];
+          for (int q = 0; q < 3; q++) { cll[q] = crl[q] = clr[q] = crr[q] = o[q]; }
+          cll[a] -= 1; cll[b] -= 1;
+          crl[b] -= 1;
+          clr[a] -= 1;
+          int *cs[4] = {cll, crl, clr, crr};
+          double sa_[4] = {+0.5, -0.5, +0.5, -0.5};
+          double sb_[4] = {+0.5, +0.5, -0.5, -0.5};
+          double Wc[4][8];
+          for (int r = 0; r < 4; r++) {
+            int64_t pi = PC(pd, cs[r][0], cs[r][1], cs[r][2]);
+            for (int q = 0; q < 8; q++) {
+              double ws = Ws[q * Nc + pi];
+              double da = dW[(a * 8 + q) * Nc + pi];
+              double db = dW[(b * 8 + q) * Nc + pi];
+              double v = sa_[r] > 0 ? ws + 0.5 * da : ws - 0.5 * da;
+              Wc[r][q] = sb_[r] > 0 ? v + 0.5 * db : v - 0.5 * db;
+            }
+          }
+          /* a-faces touching the edge: face index o on axis a, cells b-1 and b */
+          int fa1[3] = {i, j, k}, fb1[3] = {i, j, k};
+          fa1[b] -= 1;
+          fb1[a] -= 1;
+          int64_t ea0 = EI(fa1[0], fa1[1], fa1[2]), ea1 = EI(i, j, k);
+          int64_t eb0 = EI(fb1[0], fb1[1], fb1[2]), eb1 = EI(i, j, k);
+          double apa = fmax(0.0, fmax(S[a][Ne + ea0], S[a][Ne + ea1]));
+          double ama = fmax(0.0, fmax(-S[a][ea0], -S[a][ea1]));
+          double apb = fmax(0.0, fmax(S[b][Ne + eb0], S[b][Ne + eb1]));
+          double amb = fmax(0.0, fmax(-S[b][eb0], -S[b][eb1]));
+          E[e][EI(i, j, k)] = emf(Wc[0], Wc[1], Wc[2], Wc[3], e, apa, ama, apb, amb);
+        }
+  }
+
+  /* A9: conservative update of U and constrained-transport update of b */
+  int64_t nc = ncell(P);
+  const double *U0 = P->U[P->latest];
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        int64_t id = ((int64_t)k * ny + j) * nx + i;
+        for (int q = 0; q < 5; q++) {
+          double fxp = F[0][q * Ne + EI(i + 1, j, k)], fxm = F[0][q * Ne + EI(i, j, k)];
+          double fyp = F[1][q * Ne + EI(i, j + 1, k)], fym = F[1][q * Ne + EI(i, j, k)];
+          double fzp = F[2][q * Ne + EI(i, j, k + 1)], fzm = F[2][q * Ne + EI(i, j, k)];
+          oU[q * nc + id] = U0[q * nc + id] - dtdx * ((fxp - fxm) + (fyp - fym) + (fzp - fzm));
+        }
+      }
+  const double *bx0 = P->bx[P->latest], *by0 = P->by[P->latest], *bz0 = P->bz[P->latest];
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i <= nx; i++) {
+        int64_t id = ((int64_t)k * ny + j) * (nx + 1) + i;
+        obx[id] = bx0[id] - dtdx * ((E[2][EI(i, j + 1, k)] - E[2][EI(i, j, k)]) - (E[1][EI(i, j, k + 1)] - E[1][EI(i, j, k)]));
+      }
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j <= ny; j++)
+      for (int i = 0; i < nx; i++) {
+        int64_t id = ((int64_t)k * (ny + 1) + j) * nx + i;
+        oby[id] = by0[id] - dtdx * ((E[0][EI(i, j, k + 1)] - E[0][EI(i, j, k)]) - (E[2][EI(i + 1, j, k)] - E[2][EI(i, j, k)]));
+      }
+  for (int k = 0; k <= nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        int64_t id = ((int64_t)k * ny + j) * nx + i;
+        obz[id] = bz0[id] - dtdx * ((E[1][EI(i + 1, j, k)] - E[1][EI(i, j, k)]) - (E[0][EI(i, j + 1, k)] - E[0][EI(i, j, k)]));
+      }
+#undef EI
+
+  /* A10: signal speed of the new state, and the positivity check */
+  {
+    double m = 0.0;
+    int bad = 0;
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+          int64_t id = ((int64_t)k * ny + j) * nx + i;
+          double u[5], w8[8];
+          for (int q = 0; q < 5; q++) u[q] = oU[q * nc + id];
+          prim(u, obx[((int64_t)k * ny + j) * (nx + 1) + i], obx[((int64_t)k * ny + j) * (nx + 1) + i + 1],
+               oby[((int64_t)k * (ny + 1) + j) * nx + i], oby[((int64_t)k * (ny + 1) + j + 1) * nx + i],
+               obz[((int64_t)k * ny + j) * nx + i], obz[((int64_t)(k + 1) * ny + j) * nx + i], gamma, w8);
+          if (!(w8[RHO] > 0.0) || !(w8[PR] > 0.0)) bad = 1;
+          double cx = cfast(gamma, w8[RHO], w8[PR], w8[BX], w8[BY], w8[BZ]);
+          double cy = cfast(gamma, w8[RHO], w8[PR], w8[BY], w8[BZ], w8[BX]);
+          double cz = cfast(gamma, w8[RHO], w8[PR], w8[BZ], w8[BX], w8[BY]);
+          double sum = (fabs(w8[VX]) + cx) + (fabs(w8[VY]) + cy) + (fabs(w8[VZ]) + cz);
+          if (sum > m) m = sum;
+        }
+    *smax_out = m;
+    if (bad) rc = ORC_EUNPHYS;
+  }
+
+done:
+  free(pd->U); free(pd->bx); free(pd->by); free(pd->bz);
+  free(W); free(Ws); free(dW);
+  for (int d = 0; d < 3; d++) { free(F[d]); free(S[d]); free(E[d]); }
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Time steps, readiness and the dispatcher                            */
+/* ------------------------------------------------------------------ */
+
+/* Eq. (1) with g = 0: ready iff t_self < t_end and t_self <= t_nbor for all
+ * neighbours. */
+static int ready(orc_ctx *c, int ip, double t_end) {
+  opatch *P = &c->p[ip];
+  double t = P->ts[P->latest];
+  if (!(t < t_end)) return 0;
+  for (int q = 0; q < P->nnb; q++) {
+    opatch *Q = &c->p[P->nb[q]];
+    if (!(t <= Q->ts[Q->latest])) return 0;
+  }
+  return 1;
+}
+
+/* Local Courant step of patch ip at its time, quantised to a power of two,
+ * capped by dt_max, halved until it divides the time, clipped to t_end.
+ * The signal speed is the largest over the patch's newest slice and every
+ * neighbour slice that its guard fill reads. */
+static int patch_dt(orc_ctx *c, int ip, double t_end, double *dt_out) {
+  opatch *P = &c->p[ip];
+  double t = P->ts[P->latest];
+  double M = P->smax[P->latest];
+  for (int q = 0; q < P->nnb; q++) {
+    opatch *Q = &c->p[P->nb[q]];
+    int sa, sb;
+    double w;
+    if (pick(c, Q, t, &sa, &sb, &w) != ORC_OK) return ORC_EBRACKET;
+    M = fmax(M, Q->smax[sa]);
+    if (sb >= 0) M = fmax(M, Q->smax[sb]);
+  }
+  double dtc = c->cfl * c->dx / M;
+  double dt = pow2_floor(dtc);
+  if (c->dt_max > 0.0 && dt > c->dt_max) dt = c->dt_max;
+  while (fmod(t, dt) != 0.0) dt = dt * 0.5;
+  if (dt > t_end - t) dt = t_end - t;
+  *dt_out = dt;
+  return ORC_OK;
+}
+
+int orc_patch_dt(orc_ctx *c, int ip, double t_end, double *dt) { return patch_dt(c, ip, t_end, dt); }
+
+static void sched_push(orc_ctx *c, int ip, double t, double dt) {
+  if (c->nsched == c->capsched) {
+    c->capsched = c->capsched ? 2 * c->capsched : 1024;
+    c->s_patch = (int64_t *)realloc(c->s_patch, sizeof(int64_t) * c->capsched);
+    c->s_t = (double *)realloc(c->s_t, sizeof(double) * c->capsched);
+    c->s_dt = (double *)realloc(c->s_dt, sizeof(double) * c->capsched);
+  }
+  c->s_patch[c->nsched] = ip;
+  c->s_t[c->nsched] = t;
+  c->s_dt[c->nsched] = dt;
+  c->nsched++;
+}
+
+static void publish(orc_ctx *c, int ip, double dt, double smax) {
+  opatch *P = &c->p[ip];
+  double t = P->ts[P->latest];
+  int ns = (P->latest + 1) % c->nslot;
+  P->ts[ns] = t + dt;
+  P->smax[ns] = smax;
+  P->latest = ns;
+  P->dt_last = dt;
+  sched_push(c, ip, t, dt);
+  c->n_updates++;
+  c->n_cells += ncell(P);
+}
+
+/* Compute one update of patch ip by dt into caller arrays, without
+ * publishing it (reproduces a single update for sampled comparisons). */
+int orc_update_patch(orc_ctx *c, int ip, double dt, double *U, double *bx, double *by, double *bz, double *smax) {
+  int64_t nf = 0;
+  return update_patch(c, ip, dt, U, bx, by, bz, smax, &nf);
+}
+
+/* One sweep: snapshot every time, collect the ready set R, update every
+ * patch of R from the pre-sweep slices, then publish them all. */
+static int sweep(orc_ctx *c, double t_end, int *nready) {
+  int np = c->np;
+  int *R = (int *)malloc(sizeof(int) * np);
+  double *dt = (double *)malloc(sizeof(double) * np);
+  double *sm = (double *)malloc(sizeof(double) * np);
+  int nr = 0, rc = ORC_OK;
+  for (int i = 0; i < np; i++)
+    if (ready(c, i, t_end)) R[nr++] = i;
+  *nready = nr;
+  if (nr == 0) goto out;
+  for (int r = 0; r < nr; r++) {
+    rc = patch_dt(c, R[r], t_end, &dt[r]);
+    if (rc) goto out;
+  }
+  if (c->time_mode == 0) {
+    double m = dt[0];
+    for (int r = 1; r < nr; r++) m = fmin(m, dt[r]);
+    for (int r = 0; r < nr; r++) dt[r] = m;
+  }
+  int64_t nfb = 0;
+  int err = ORC_OK;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nfb)
+  for (int r = 0; r < nr; r++) {
+    opatch *P = &c->p[R[r]];
+    int ns = (P->latest + 1) % c->nslot;
+    int64_t f = 0;
+    int e = update_patch(c, R[r], dt[r], P->U[ns], P->bx[ns], P->by[ns], P->bz[ns], &sm[r], &f);
+    nfb += f;
+    if (e) {
+#pragma omp critical
+      err = e;
+    }
+  }
+  c->n_fallback += nfb;
+  if (err) { rc = err; goto out; }
+  for (int r = 0; r < nr; r++) publish(c, R[r], dt[r], sm[r]);
+  c->n_sweeps++;
+out:
+  free(R); free(dt); free(sm);
+  return rc;
+}
+
+/* Time-sorted ready queue (the paper's first dispatcher mode, run on one
+ * thread): pop the oldest ready patch (ties by index), update and publish
+ * it, then re-check it and its neighbours and queue any that became ready. */
+static int queue_run(orc_ctx *c, double t_end) {
+  int np = c->np;
+  char *queued = (char *)calloc(np, 1);
+  int rc = ORC_OK;
+  for (int i = 0; i < np; i++) queued[i] = (char)ready(c, i, t_end);
+  for (;;) {
+    int best = -1;
+    for (int i = 0; i < np; i++) {
+      if (!queued[i]) continue;
+      if (best < 0) { best = i; continue; }
+      double ti = c->p[i].ts[c->p[i].latest], tb = c->p[best].ts[c->p[best].latest];
+      if (ti < tb) best = i;
+    }
+    if (best < 0) break;
+    queued[best] = 0;
+    opatch *P = &c->p[best];
+    double dt, sm;
+    rc = patch_dt(c, best, t_end, &dt);
+    if (rc) break;
+    int ns = (P->latest + 1) % c->nslot;
+    int64_t f = 0;
+    rc = update_patch(c, best, dt, P->U[ns], P->bx[ns], P->by[ns], P->bz[ns], &sm, &f);
+    c->n_fallback += f;
+    if (rc) break;
+    publish(c, best, dt, sm);
+    if (!queued[best] && ready(c, best, t_end)) queued[best] = 1;
+    for (int q = 0; q < P->nnb; q++) {
+      int iq = P->nb[q];
+      if (!queued[iq] && ready(c, iq, t_end)) queued[iq] = 1;
+    }
+  }
+  free(queued);
+  if (rc == ORC_OK) {
+    for (int i = 0; i < np; i++)
+      if (c->p[i].ts[c->p[i].latest] < t_end) { rc = ORC_EDEADLOCK; break; }
+  }
+  return rc;
+}
+
+/* Advance until every patch has reached t_end, or until max_sweeps sweeps
+ * have run (sweep dispatcher; <= 0 means no limit).  In global time-step
+ * mode every sweep is one step of the whole domain with the smallest patch
+ * step. */
+int orc_advance(orc_ctx *c, double t_end, int64_t max_sweeps) {
+  int rc = ORC_OK;
+  if (!(t_end < INFINITY) && (max_sweeps <= 0 || (c->time_mode == 1 && c->disp_mode == 0))) {
+    snprintf(c->err, sizeof c->err, "an unbounded advance needs a finite t_end or a sweep limit");
+    return ORC_EINVAL;
+  }
+  if (c->time_mode == 1 && c->disp_mode == 0) {
+    rc = queue_run(c, t_end);
+  } else {
+    for (int64_t s = 0; max_sweeps <= 0 || s < max_sweeps; s++) {
+      int nr;
+      rc = sweep(c, t_end, &nr);
+      if (rc) break;
+      if (nr == 0) {
+        for (int i = 0; i < c->np; i++)
+          if (c->p[i].ts[c->p[i].latest] < t_end) { rc = ORC_EDEADLOCK; break; }
+        break;
+      }
+    }
+  }
+  if (rc) {
+    c->status = rc;
+    if (!c->err[0]) snprintf(c->err, sizeof c->err, "advance failed with code %d", rc);
+  }
+  return rc;
+}
+
+int64_t orc_get_schedule(orc_ctx *c, int64_t *patch, double *t, double *dt, int64_t cap) {
+  int64_t n = c->nsched < cap ? c->nsched : cap;
+  if (patch) memcpy(patch, c->s_patch, sizeof(int64_t) * n);
+  if (t) memcpy(t, c->s_t, sizeof(double) * n);
+  if (dt) memcpy(dt, c->s_dt, sizeof(double) * n);
+  return c->nsched;
+}
+
+void orc_stats(orc_ctx *c, int64_t *out) {
+  out[0] = c->n_updates;
+  out[1] = c->n_cells;
+  out[2] = c->n_sweeps;
+  out[3] = c->n_fallback;
+}
+
+/* ------------------------------------------------------------------ */
+/* Diagnostics: compensated sums and div B                              */
+/* ------------------------------------------------------------------ */
+typedef struct { double s, c; } nsum;
+static void nadd(nsum *a, double x) {
+  double t = a->s + x;
+  if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+  else a->c += (x - t) + a->s;
+  a->s = t;
+}
+
+/* out[0..4]: volume integrals of rho, m_x, m_y, m_z, E (Neumaier sums);
+ * out[5..7]: volume integrals of the face fields, each face counted once
+ * (the low face of every cell); out[8]: max over cells of |sum_d Delta_d b|;
+ * out[9]: max |b| over faces. */
+void orc_diagnostics(orc_ctx *c, double *out) {
+  nsum acc[8];
+  memset(acc, 0, sizeof acc);
+  double dV = c->dx * c->dx * c->dx;
+  double mdiv = 0.0, mb = 0.0;
+  for (int ip = 0; ip < c->np; ip++) {
+    opatch *P = &c->p[ip];
+    int s = P->latest, nx = P->n[0], ny = P->n[1], nz = P->n[2];
+    int64_t nc = ncell(P);
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+          int64_t id = ((int64_t)k * ny + j) * nx + i;
+          for (int q = 0; q < 5; q++) nadd(&acc[q], P->U[s][q * nc + id] * dV);
+          double bxl = P->bx[s][((int64_t)k * ny + j) * (nx + 1) + i];
+          double bxr = P->bx[s][((int64_t)k * ny + j) * (nx + 1) + i + 1];
+          double byl = P->by[s][((int64_t)k * (ny + 1) + j) * nx + i];
+          double byr = P->by[s][((int64_t)k * (ny + 1) + j + 1) * nx + i];
+          double bzl = P->bz[s][((int64_t)k * ny + j) * nx + i];
+          double bzr = P->bz[s][((int64_t)(k + 1) * ny + j) * nx + i];
+          nadd(&acc[5], bxl * dV);
+          nadd(&acc[6], byl * dV);
+          nadd(&acc[7], bzl * dV);
+          double dv = (bxr - bxl) + (byr - byl) + (bzr - bzl);
+          if (fabs(dv) > mdiv) mdiv = fabs(dv);
+          if (fabs(bxl) > mb) mb = fabs(bxl);
+          if (fabs(byl) > mb) mb = fabs(byl);
+          if (fabs(bzl) > mb) mb = fabs(bzl);
+        }
+  }
+  for (int q = 0; q < 8; q++) out[q] = acc[q].s + acc[q].c;
+  out[8] = mdiv;
+  out[9] = mb;
+}

@@ -1,0 +1,384 @@
+"""Seeded synthetic inputs: patch layouts and initial states.
+
+This module only *defines inputs*.  It holds none of the update scheme's
+arithmetic and is shared by the CUDA path's tests and by the oracle's tests.
+Every generator is seeded and returns interior-only patch arrays in the layout
+the library uses (x fastest):
+
+    U  : concatenation over patches of [5][nz][ny][nx]  (rho, m_x, m_y, m_z, E)
+    bx : concatenation of [nz][ny][nx+1]   (x-faces, both boundary faces)
+    by : concatenation of [nz][ny+1][nx]
+    bz : concatenation of [nz+1][ny][nx]
+
+Face fields come from a vector potential on cell edges, so their discrete
+divergence is zero to round-off.  Units are Heaviside-Lorentz (E = -v x B,
+J = curl B), as in DISPATCH I, Sec. 4.3, so E = p/(gamma-1) + rho v^2/2 + B^2/2.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Layout:
+    """Uniform Cartesian decomposition of a periodic box (DISPATCH I,
+    Sec. 2.3, the 'cartesian' component)."""
+    n: np.ndarray          # (npatch, 3) int32 cells per axis
+    lo: np.ndarray         # (npatch, 3) int64 first interior cell
+    base_cells: tuple      # level-0 cells per axis (x, y, z)
+    box_len: tuple         # box length per axis
+
+    @property
+    def npatch(self):
+        return self.n.shape[0]
+
+    @property
+    def dx(self):
+        return self.box_len[0] / self.base_cells[0]
+
+
+def cartesian(patches_per_axis, cells_per_patch, dx=None):
+    """Patches ordered x fastest; cells_per_patch may be an int or a 3-tuple."""
+    pp = np.broadcast_to(np.asarray(patches_per_axis, dtype=np.int64), (3,))
+    cp = np.broadcast_to(np.asarray(cells_per_patch, dtype=np.int64), (3,))
+    base = tuple(int(a * b) for a, b in zip(pp, cp))
+    if dx is None:
+        dx = 1.0 / base[0]
+    box = tuple(float(b * dx) for b in base)
+    los = []
+    for kz in range(pp[2]):
+        for ky in range(pp[1]):
+            for kx in range(pp[0]):
+                los.append((kx * cp[0], ky * cp[1], kz * cp[2]))
+    lo = np.array(los, dtype=np.int64)
+    n = np.tile(cp.astype(np.int32), (lo.shape[0], 1))
+    return Layout(n=n, lo=lo, base_cells=base, box_len=box)
+
+
+@dataclass
+class Fields:
+    """A global periodic state on the level grid (index order z, y, x)."""
+    rho: np.ndarray
+    v: np.ndarray          # (3, Z, Y, X)
+    p: np.ndarray
+    bx: np.ndarray         # x-face at i-1/2, periodic: (Z, Y, X)
+    by: np.ndarray
+    bz: np.ndarray
+    gamma: float
+    meta: dict = field(default_factory=dict)
+
+
+def _grid(layout):
+    X, Y, Z = layout.base_cells
+    dx = layout.dx
+    x = (np.arange(X) + 0.5) * dx
+    y = (np.arange(Y) + 0.5) * dx
+    z = (np.arange(Z) + 0.5) * dx
+    return x, y, z, dx
+
+
+def curl_faces(Ax, Ay, Az, dx):
+    """Face fields b = curl A from edge potentials (periodic).
+
+    Ax[k,j,i] sits at (x_i, y_{j-1/2}, z_{k-1/2}), Ay at (x_{i-1/2}, y_j, z_{k-1/2}),
+    Az at (x_{i-1/2}, y_{j-1/2}, z_k).  bx[k,j,i] is the face at x_{i-1/2}."""
+    bx = (np.roll(Az, -1, axis=1) - Az) / dx - (np.roll(Ay, -1, axis=0) - Ay) / dx
+    by = (np.roll(Ax, -1, axis=0) - Ax) / dx - (np.roll(Az, -1, axis=2) - Az) / dx
+    bz = (np.roll(Ay, -1, axis=2) - Ay) / dx - (np.roll(Ax, -1, axis=1) - Ax) / dx
+    return bx, by, bz
+
+
+def to_patches(layout: Layout, f: Fields, dtype=np.float64):
+    """Cut the global state into interior-only patch arrays (conserved U)."""
+    Bxc = 0.5 * (f.bx + np.roll(f.bx, -1, axis=2))
+    Byc = 0.5 * (f.by + np.roll(f.by, -1, axis=1))
+    Bzc = 0.5 * (f.bz + np.roll(f.bz, -1, axis=0))
+    v2 = f.v[0] ** 2 + f.v[1] ** 2 + f.v[2] ** 2
+    E = f.p / (f.gamma - 1.0) + 0.5 * f.rho * v2 + 0.5 * (Bxc ** 2 + Byc ** 2 + Bzc ** 2)
+    Ug = np.stack([f.rho, f.rho * f.v[0], f.rho * f.v[1], f.rho * f.v[2], E])
+    Z, Y, X = f.rho.shape
+    Us, bxs, bys, bzs = [], [], [], []
+    for (nx, ny, nz), (x0, y0, z0) in zip(layout.n, layout.lo):
+        zi = np.arange(z0, z0 + nz) % Z
+        yi = np.arange(y0, y0 + ny) % Y
+        xi = np.arange(x0, x0 + nx) % X
+        Us.append(Ug[:, zi][:, :, yi][:, :, :, xi].ravel())
+        bxs.append(f.bx[zi][:, yi][:, :, np.arange(x0, x0 + nx + 1) % X].ravel())
+        bys.append(f.by[zi][:, np.arange(y0, y0 + ny + 1) % Y][:, :, xi].ravel())
+        bzs.append(f.bz[np.arange(z0, z0 + nz + 1) % Z][:, yi][:, :, xi].ravel())
+    cat = lambda a: np.concatenate(a).astype(dtype)
+    return cat(Us), cat(bxs), cat(bys), cat(bzs)
+
+
+def from_patches(layout: Layout, U, bx, by, bz):
+    """Reassemble global cell arrays (U on cells, faces at i-1/2) from patch
+    arrays; the inverse of to_patches for a full tiling."""
+    X, Y, Z = layout.base_cells
+    Ug = np.zeros((5, Z, Y, X))
+    bxg = np.zeros((Z, Y, X)); byg = np.zeros((Z, Y, X)); bzg = np.zeros((Z, Y, X))
+    oU = ox = oy = oz = 0
+    for (nx, ny, nz), (x0, y0, z0) in zip(layout.n, layout.lo):
+        nc = nx * ny * nz
+        u = np.asarray(U[oU:oU + 5 * nc]).reshape(5, nz, ny, nx)
+        fx = np.asarray(bx[ox:ox + (nx + 1) * ny * nz]).reshape(nz, ny, nx + 1)
+        fy = np.asarray(by[oy:oy + nx * (ny + 1) * nz]).reshape(nz, ny + 1, nx)
+        fz = np.asarray(bz[oz:oz + nx * ny * (nz + 1)]).reshape(nz + 1, ny, nx)
+        sl = (slice(z0, z0 + nz), slice(y0, y0 + ny), slice(x0, x0 + nx))
+        Ug[(slice(None),) + sl] = u
+        bxg[sl] = fx[:, :, :nx]
+        byg[sl] = fy[:, :ny, :]
+        bzg[sl] = fz[:nz]
+        oU += 5 * nc; ox += (nx + 1) * ny * nz; oy += nx * (ny + 1) * nz; oz += nx * ny * (nz + 1)
+    return Ug, bxg, byg, bzg
+
+
+# ---------------------------------------------------------------- linear MHD
+
+def primitive_jacobian(W0, khat, gamma):
+    """A(k) = sum_d khat_d A_d of ideal MHD in primitive variables
+    (rho, v, p, B) about a uniform state, with div B = 0 assumed.  Its
+    eigenvectors define the linear wave families used as inputs."""
+    rho, v, p, B = W0[0], W0[1:4], W0[4], W0[5:8]
+    A = np.zeros((8, 8))
+    for d in range(3):
+        Ad = np.zeros((8, 8))
+        Ad[0, 0] = v[d]; Ad[0, 1 + d] = rho
+        for c in range(3):
+            Ad[1 + c, 1 + c] += v[d]
+            Ad[1 + c, 5 + c] -= B[d] / rho
+        Ad[1 + d, 4] += 1.0 / rho
+        for e in range(3):
+            Ad[1 + d, 5 + e] += B[e] / rho
+        Ad[4, 4] = v[d]; Ad[4, 1 + d] = gamma * p
+        for c in range(3):
+            Ad[5 + c, 1 + c] -= B[d]
+            Ad[5 + c, 5 + c] += v[d]
+            Ad[5 + c, 1 + d] += B[c]
+        A += khat[d] * Ad
+    return A
+
+
+def eigenmode(W0, khat, gamma, kind):
+    """Right eigenvector (unit norm, real) and speed of a wave family moving
+    along +khat: kind in {'fast', 'alfven', 'slow'}."""
+    A = primitive_jacobian(W0, khat, gamma)
+    lam, R = np.linalg.eig(A)
+    lam = lam.real
+    R = R.real
+    vn = float(np.dot(W0[1:4], khat))
+    pos = [i for i in range(8) if lam[i] - vn > 1e-9]
+    pos.sort(key=lambda i: lam[i])
+    if len(pos) != 3:
+        raise ValueError("degenerate wave families for this direction")
+    i = {"slow": pos[0], "alfven": pos[1], "fast": pos[2]}[kind]
+    r = R[:, i] / np.linalg.norm(R[:, i])
+    if r[np.argmax(np.abs(r))] < 0:
+        r = -r
+    return r, lam[i]
+
+
+def linear_modes(layout, modes, W0, gamma, amplitude):
+    """Superposition of linear eigenmodes.  modes: list of (kind, n_vec,
+    phase) with wavevector k = 2 pi n / box.  The field perturbation is set
+    through an edge vector potential so that div b = 0 discretely."""
+    x, y, z, dx = _grid(layout)
+    X, Y, Z = layout.base_cells
+    L = np.array(layout.box_len)
+    zz, yy, xx = np.meshgrid(z, y, x, indexing="ij")
+    xe = np.arange(X) * dx
+    ye = np.arange(Y) * dx
+    ze = np.arange(Z) * dx
+    rho = np.full((Z, Y, X), W0[0]); p = np.full((Z, Y, X), W0[4])
+    v = np.zeros((3, Z, Y, X)); v += np.asarray(W0[1:4])[:, None, None, None]
+    Ax = np.zeros((Z, Y, X)); Ay = np.zeros((Z, Y, X)); Az = np.zeros((Z, Y, X))
+    for kind, nvec, phase in modes:
+        k = 2 * np.pi * np.asarray(nvec, float) / L
+        kh = k / np.linalg.norm(k)
+        r, _ = eigenmode(np.asarray(W0, float), kh, gamma, kind)
+        th = k[0] * xx + k[1] * yy + k[2] * zz + phase
+        cs = amplitude * np.cos(th)
+        rho += r[0] * cs
+        for c in range(3):
+            v[c] += r[1 + c] * cs
+        p += r[4] * cs
+        dB = amplitude * r[5:8]
+        # curl(a sin(k.x + phase)) = (k x a) cos(...) = dB cos(...) for a = -(k x dB)/k^2
+        Avec = -np.cross(k, dB) / np.dot(k, k)
+        zg, yg, xg = np.meshgrid(ze, ye, x, indexing="ij")
+        Ax += Avec[0] * np.sin(k[0] * xg + k[1] * yg + k[2] * zg + phase)
+        zg, yg, xg = np.meshgrid(ze, y, xe, indexing="ij")
+        Ay += Avec[1] * np.sin(k[0] * xg + k[1] * yg + k[2] * zg + phase)
+        zg, yg, xg = np.meshgrid(z, ye, xe, indexing="ij")
+        Az += Avec[2] * np.sin(k[0] * xg + k[1] * yg + k[2] * zg + phase)
+    bx, by, bz = curl_faces(Ax, Ay, Az, dx)
+    bx = bx + W0[5]; by = by + W0[6]; bz = bz + W0[7]
+    return Fields(rho=rho, v=v, p=p, bx=bx, by=by, bz=bz, gamma=gamma)
+
+
+def config_linear_waves(seed=1705, patches=2, n=16, amplitude=1e-6):
+    """Eight patches of 16^3 on the unit periodic cube, rho=1, p=0.6, B=(1,0,0),
+    v=0, plus four seeded linear fast/Alfven/slow modes with integer
+    wavenumbers 1 <= |n| <= 2 (never parallel to x) and random phases."""
+    rng = np.random.default_rng(seed)
+    lay = cartesian(patches, n)
+    W0 = np.array([1.0, 0, 0, 0, 0.6, 1.0, 0, 0])
+    modes = []
+    while len(modes) < 4:
+        nv = rng.integers(-2, 3, size=3)
+        nn = np.linalg.norm(nv)
+        if nn < 1 or nn > 2 or (nv[1] == 0 and nv[2] == 0):
+            continue
+        kind = ["fast", "alfven", "slow"][rng.integers(0, 3)]
+        phase = rng.uniform(0, 2 * np.pi)
+        try:   # skip directions (e.g. k normal to B) where the families coincide
+            eigenmode(W0, nv / nn, 5.0 / 3.0, kind)
+        except ValueError:
+            continue
+        modes.append((kind, nv, phase))
+    f = linear_modes(lay, modes, W0, 5.0 / 3.0, amplitude)
+    f.meta = dict(modes=modes)
+    return lay, f
+
+
+# ------------------------------------------------------- turbulence inputs
+
+def solenoidal_velocity(shape, box, kmin, kmax, rms, rng):
+    """Gaussian random solenoidal velocity with shell spectrum E(k) ~ k^-2 on
+    kmin <= |k|/2pi <= kmax (so |v_hat| ~ k^-2), zero mean, scaled to the
+    given volume rms of |v|."""
+    Z, Y, X = shape
+    kz = np.fft.fftfreq(Z, d=box[2] / Z)
+    ky = np.fft.fftfreq(Y, d=box[1] / Y)
+    kx = np.fft.rfftfreq(X, d=box[0] / X)
+    KZ, KY, KX = np.meshgrid(kz, ky, kx, indexing="ij")
+    K = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)
+    band = (K >= kmin) & (K <= kmax)
+    amp = np.zeros_like(K)
+    amp[band] = K[band] ** -2.0
+    vh = [(rng.standard_normal(K.shape) + 1j * rng.standard_normal(K.shape)) * amp for _ in range(3)]
+    Ks = np.where(K > 0, K, 1.0)
+    kd = (KX * vh[0] + KY * vh[1] + KZ * vh[2]) / Ks ** 2
+    vh = [vh[0] - KX * kd, vh[1] - KY * kd, vh[2] - KZ * kd]
+    v = np.stack([np.fft.irfftn(c, s=shape, axes=(0, 1, 2)) for c in vh])
+    v -= v.mean(axis=(1, 2, 3), keepdims=True)
+    r = np.sqrt(np.mean(v[0] ** 2 + v[1] ** 2 + v[2] ** 2))
+    return v * (rms / r)
+
+
+def config_turbulence(seed=10774, patches=8, n=32, mach=2.0):
+    """Decaying-turbulence input: 8^3 patches of 32^3 (256^3 cells), rho=1,
+    p=0.6 (sound speed 1), solenoidal Gaussian velocity with E(k) ~ k^-2 on
+    1 <= |k|/2pi <= 4 at rms Mach 2, uniform B along x with beta = 1."""
+    rng = np.random.default_rng(seed)
+    lay = cartesian(patches, n)
+    X, Y, Z = lay.base_cells
+    shape = (Z, Y, X)
+    v = solenoidal_velocity(shape, lay.box_len, 1.0, 4.0, mach, rng)
+    rho = np.ones(shape)
+    p = np.full(shape, 0.6)
+    B0 = np.sqrt(2 * 0.6 / 1.0)       # beta = 2p/B^2 = 1
+    f = Fields(rho=rho, v=v, p=p, bx=np.full(shape, B0), by=np.zeros(shape), bz=np.zeros(shape),
+               gamma=5.0 / 3.0)
+    return lay, f
+
+
+def gaussian_filtered_noise(shape, box, sigma_f, rng):
+    Z, Y, X = shape
+    w = rng.standard_normal(shape)
+    kz = np.fft.fftfreq(Z, d=box[2] / Z) * 2 * np.pi
+    ky = np.fft.fftfreq(Y, d=box[1] / Y) * 2 * np.pi
+    kx = np.fft.rfftfreq(X, d=box[0] / X) * 2 * np.pi
+    KZ, KY, KX = np.meshgrid(kz, ky, kx, indexing="ij")
+    g = np.fft.irfftn(np.fft.rfftn(w) * np.exp(-0.5 * (KX ** 2 + KY ** 2 + KZ ** 2) * sigma_f ** 2), s=shape, axes=(0, 1, 2))
+    g -= g.mean()
+    return g / g.std()
+
+
+def config_lts(seed=17051, patches=16, n=16, sigma_ln=1.5, hot_radius=0.1, hot_factor=1000.0,
+               mach=1.0, beta=10.0):
+    """Local-time-step stress input: log-normal density (sigma_ln = 1.5,
+    Gaussian-filtered noise, filter width 1/16 of the box) in pressure
+    equilibrium p = 0.6, a central sphere of radius 0.1 at 1000x temperature
+    (density / 1000), random solenoidal velocity at rms Mach 1, uniform B
+    along x at beta = 10."""
+    rng = np.random.default_rng(seed)
+    lay = cartesian(patches, n)
+    X, Y, Z = lay.base_cells
+    shape = (Z, Y, X)
+    x, y, zc, _ = _grid(lay)
+    g = gaussian_filtered_noise(shape, lay.box_len, lay.box_len[0] / 16.0, rng)
+    rho = np.exp(sigma_ln * g - 0.5 * sigma_ln ** 2)
+    zz, yy, xx = np.meshgrid(zc, y, x, indexing="ij")
+    c = np.array(lay.box_len) / 2
+    r2 = (xx - c[0]) ** 2 + (yy - c[1]) ** 2 + (zz - c[2]) ** 2
+    rho = np.where(r2 < hot_radius ** 2, rho / hot_factor, rho)
+    v = solenoidal_velocity(shape, lay.box_len, 1.0, 4.0, mach, rng)
+    p = np.full(shape, 0.6)
+    B0 = np.sqrt(2 * 0.6 / beta)
+    f = Fields(rho=rho, v=v, p=p, bx=np.full(shape, B0), by=np.zeros(shape), bz=np.zeros(shape),
+               gamma=5.0 / 3.0)
+    return lay, f
+
+
+def config_orszag_tang(seed=10775, patches=16, n=32, pert=1e-3):
+    """3-D Orszag-Tang-type vortex: rho = 25/(36 pi), p = 5/(12 pi),
+    v = (-sin 2 pi y, sin 2 pi x, 0), b = curl(A_z z) with
+    A_z = B0 (cos 4 pi x / 4 pi + cos 2 pi y / 2 pi), B0 = 1/sqrt(4 pi),
+    and a seeded 1e-3 Gaussian v_z per cell."""
+    rng = np.random.default_rng(seed)
+    lay = cartesian(patches, n)
+    X, Y, Z = lay.base_cells
+    shape = (Z, Y, X)
+    x, y, z, dx = _grid(lay)
+    zz, yy, xx = np.meshgrid(z, y, x, indexing="ij")
+    rho = np.full(shape, 25.0 / (36.0 * np.pi))
+    p = np.full(shape, 5.0 / (12.0 * np.pi))
+    v = np.zeros((3,) + shape)
+    v[0] = -np.sin(2 * np.pi * yy)
+    v[1] = np.sin(2 * np.pi * xx)
+    v[2] = pert * rng.standard_normal(shape)
+    B0 = 1.0 / np.sqrt(4 * np.pi)
+    xe = np.arange(X) * dx
+    ye = np.arange(Y) * dx
+    _, YE, XE = np.meshgrid(z, ye, xe, indexing="ij")
+    Az = B0 * (np.cos(4 * np.pi * XE) / (4 * np.pi) + np.cos(2 * np.pi * YE) / (2 * np.pi))
+    zero = np.zeros(shape)
+    bx, by, bz = curl_faces(zero, zero, Az, dx)
+    return lay, Fields(rho=rho, v=v, p=p, bx=bx, by=by, bz=bz, gamma=5.0 / 3.0)
+
+
+def config_uniform(layout, W0, gamma, seed=0, eps=0.0):
+    """Uniform state plus an optional seeded cell-wise density perturbation."""
+    rng = np.random.default_rng(seed)
+    X, Y, Z = layout.base_cells
+    shape = (Z, Y, X)
+    rho = np.full(shape, W0[0]) * (1.0 + eps * rng.standard_normal(shape))
+    v = np.zeros((3,) + shape) + np.asarray(W0[1:4])[:, None, None, None]
+    return Fields(rho=rho, v=v, p=np.full(shape, W0[4]), bx=np.full(shape, W0[5]), by=np.full(shape, W0[6]),
+                  bz=np.full(shape, W0[7]), gamma=gamma)
+
+
+def config_sod(axis, n_per_unit, cells_per_patch=64, thin=4):
+    """Sod tube along `axis` on a periodic box of length 2 (left state
+    (rho, p) = (1, 1) on [0.5, 1.5), right state (0.125, 0.1) elsewhere,
+    gamma = 1.4, B = 0): the standard Sod interface sits at 1.5, and the waves
+    of the mirrored interface at 0.5 stay clear of [1, 2) until t = 0.2."""
+    N = 2 * n_per_unit
+    cpp = [thin, thin, thin]
+    cpp[axis] = cells_per_patch
+    ppa = [1, 1, 1]
+    ppa[axis] = N // cells_per_patch
+    lay = cartesian(ppa, cpp, dx=1.0 / n_per_unit)
+    X, Y, Z = lay.base_cells
+    shape = (Z, Y, X)
+    coords = _grid(lay)[axis]
+    s = [1, 1, 1]
+    s[2 - axis] = -1
+    c = coords.reshape(s)
+    left = (c >= 0.5) & (c < 1.5)
+    rho = np.broadcast_to(np.where(left, 1.0, 0.125), shape).copy()
+    p = np.broadcast_to(np.where(left, 1.0, 0.1), shape).copy()
+    z = np.zeros(shape)
+    return lay, Fields(rho=rho, v=np.zeros((3,) + shape), p=p, bx=z.copy(), by=z.copy(), bz=z.copy(), gamma=1.4)
