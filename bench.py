@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the per-patch update: MHD cell-updates/s on one GB300.
+
+Workload (one line per run): decaying MHD turbulence on a periodic 256^3 box
+cut into 8^3 = 512 patches of 32^3 cells, FP64, one global power-of-two
+Courant step per sweep (C = 0.4), seeded solenoidal Mach-2 velocity with
+E(k) ~ k^-2 on 1 <= |k|/2pi <= 4, uniform B along x at beta = 1.  A bench
+"step" is one sweep: every patch fills its guard zones, advances one step and
+publishes it.  The state (1.07 GB per slice in FP64) is larger than L2, so no
+flush is needed between steps.  The FP32-state form of the same run is
+measured too and reported under "forms".
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (32 patch updates per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MHD cell-updates/s (FP64 vs FP32 form) and % of GB300 HBM roofline"
+UNIT = "cell-updates/s"
+PATCHES, NCELL = 8, 32
+WORKLOAD = "decaying MHD turbulence, 256^3 periodic, 512 patches of 32^3, global dt, CFL 0.4"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def radius2_guard_fraction(n):
+    return ((n + 4) ** 3 - n ** 3) / n ** 3
+
+
+def alg_bytes_per_cell(n, esize, sbar=1.0):
+    """Algorithmic HBM bytes per cell-update: read and write the 8 stored
+    fields once, plus the guard shell the stencil reads (radius 2), taken
+    from sbar neighbour slices."""
+    V = 8
+    return esize * (2 * V + sbar * radius2_guard_fraction(n) * V)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as fh:
+                d = json.load(fh)
+            v = d.get("hbm_gbs") or d.get("hbm_GBs") or d.get("hbm")
+            if isinstance(v, dict):
+                v = v.get("value")
+            if v:
+                return float(v), "measured"
+        except Exception:
+            pass
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("gloo")
+        return tdist, rank, ws
+    return None, rank, ws
+
+
+def max_over_ranks(td, x):
+    if td is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(td, x):
+    if td is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    td.all_reduce(t, op=td.ReduceOp.SUM)
+    return float(t.item())
+
+
+def make_input():
+    from paper_1705_10774_gb300 import ics
+    lay, f = ics.config_turbulence(seed=10774, patches=PATCHES, n=NCELL, mach=2.0)
+    return lay, f, ics.to_patches(lay, f)
+
+
+def run_form(lay, state_dev, precision, steps, warmup, td):
+    """Time `steps` global steps of one precision form from the initial state."""
+    import torch
+    from paper_1705_10774_gb300.dispatch import Dispatch
+    stream = torch.cuda.current_stream()
+    g = Dispatch(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
+                 precision=precision, time_mode=0, timing=1, stream=stream.cuda_stream)
+    g.set_state(*state_dev)
+    if warmup:
+        g.advance(max_sweeps=warmup)
+    g.set_state(*state_dev)
+    torch.cuda.synchronize()
+    if td is not None:
+        td.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = g.advance(max_sweeps=steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if td is not None:
+        td.barrier()
+    ms = e0.elapsed_time(e1)
+    return g, st, ms
+
+
+def gpu_arm(args):
+    import torch
+    td, rank, ws = dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_1705_10774_gb300 import dispatch as D
+    D.load()
+    lay, f, state = make_input()
+    state_dev = [torch.from_numpy(a).cuda() for a in state]
+    ncells = int(np.prod(lay.base_cells))
+    peak, peak_kind = measured_peaks()
+
+    with Clocks(local) as clk:
+        g, st, ms = run_form(lay, state_dev, 0, args.steps, args.warmup, td)
+    ms_max = max_over_ranks(td, ms)
+    cells_all = sum_over_ranks(td, float(st["cell_updates"]))
+    value = cells_all / (ms_max * 1e-3)
+    kavg = st["kernel_ms"] / max(st["kernel_launches"], 1)
+    bpl = alg_bytes_per_cell(NCELL, 8) * ncells
+    achieved = bpl / (kavg * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "update_kernel<double,16,8,256>", "kernel_ms_avg": kavg,
+            "alg_bytes_per_launch": bpl, "peak_kind": peak_kind}
+    g.close()
+
+    forms = {}
+    if not args.no_f32:
+        state32 = [a.float() for a in state_dev]
+        g32, st32, ms32 = run_form(lay, state32, 1, args.steps, args.warmup, td)
+        ms32_max = max_over_ranks(td, ms32)
+        v32 = sum_over_ranks(td, float(st32["cell_updates"])) / (ms32_max * 1e-3)
+        k32 = st32["kernel_ms"] / max(st32["kernel_launches"], 1)
+        b32 = alg_bytes_per_cell(NCELL, 4) * ncells
+        a32 = b32 / (k32 * 1e-3) / 1e9
+        forms["f32"] = {"value": v32, "ms_per_step": ms32_max / args.steps, "dtype": "f32",
+                        "roofline": {"bound": "hbm", "achieved": a32, "peak": peak, "unit": "GB/s",
+                                     "frac": a32 / peak, "kernel_ms_avg": k32, "alg_bytes_per_launch": b32}}
+        g32.close()
+        del state32
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_measure(lay, state, min(args.steps, args.e2e_steps), td)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(lay, state)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "patches": lay.npatch, "cells_per_patch": [NCELL] * 3,
+                       "cells": ncells, "time_mode": "global", "precision": "f64",
+                       "l2": "inputs larger than L2 (1.07 GB per slice)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+            "roofline": roof,
+            "forms": {"f64": {"value": value, "ms_per_step": ms_max / args.steps}, **forms},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(st["kernel_launches"] + st["plan_launches"]),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(out))
+    if td is not None:
+        td.barrier()
+        td.destroy_process_group()
+
+
+def e2e_measure(lay, state, steps, td):
+    """Through the public API with host buffers: every step copies the input
+    state from pinned host memory, advances one global step and reads the
+    new state back into pinned host memory."""
+    import torch
+    from paper_1705_10774_gb300.dispatch import Dispatch
+    pinned = [torch.from_numpy(a).pin_memory() for a in state]
+    outs = [torch.empty_like(a).pin_memory() for a in pinned]
+    stream = torch.cuda.current_stream()
+    g = Dispatch(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
+                 precision=0, time_mode=0, stream=stream.cuda_stream)
+    h_in = sum(a.numel() * a.element_size() for a in pinned)
+    h_out = sum(a.numel() * a.element_size() for a in outs)
+    g.set_state(*[a.numpy() for a in pinned])   # allocate the staging buffer before timing
+    g.advance(max_sweeps=1)
+    g.get_state(out=[a.numpy() for a in outs])
+    torch.cuda.synchronize()
+    if td is not None:
+        td.barrier()
+    cells = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        g.set_state(*[a.numpy() for a in pinned])
+        st = g.advance(max_sweeps=1)
+        g.get_state(out=[a.numpy() for a in outs])
+        cells += st["cell_updates"]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    dt = max_over_ranks(td, dt)
+    cells = sum_over_ranks(td, cells)
+    g.close()
+    return {"value": cells / dt, "unit": UNIT, "h2d_bytes_per_step": h_in, "d2h_bytes_per_step": h_out,
+            "steps": steps}
+
+
+def cpu_baseline(lay, state, target_s=12.0):
+    """The FP64 oracle as it stands (OpenMP over the ready patches of a
+    sweep), on the host cores: whole global steps of the same workload."""
+    from oracle import Oracle
+    o = Oracle(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
+    o.set_state(*state)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.advance(max_sweeps=1)
+        n += 1
+        if time.perf_counter() - t0 > target_s or n >= 8:
+            break
+    dt = time.perf_counter() - t0
+    cells = o.stats()["cell_updates"]
+    return {"value": cells / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d global step(s) of the 256^3 / 512-patch workload (%d cell-updates, %.1f s)" % (n, cells, dt)}
+
+
+def reference_arm(args):
+    """The FP64 CPU oracle, timed on the host cores; each step is a bounded
+    sample of the workload: 32 patch updates (1.05M cell-updates) from the
+    initial state, spread over the cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import Oracle
+    lay, f, state = make_input()
+    o = Oracle(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
+    o.set_state(*state)
+    dt = min(o.patch_dt(i) for i in range(lay.npatch))
+    cores = os.cpu_count() or 1
+    per_step = 32
+    order = np.random.default_rng(1).permutation(lay.npatch)
+    pool = ThreadPoolExecutor(max_workers=cores)
+
+    def step(k):
+        ids = [int(order[(k * per_step + j) % lay.npatch]) for j in range(per_step)]
+        list(pool.map(lambda i: o.update_patch(i, dt), ids))
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    el = time.perf_counter() - t0
+    cells = args.steps * per_step * NCELL ** 3
+    value = cells / el
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "patches": lay.npatch, "cells_per_patch": [NCELL] * 3,
+                   "sample_per_step": "%d patch updates" % per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d patch updates of 32^3 per step, %d steps" % (per_step, args.steps)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-f32", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

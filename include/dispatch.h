@@ -1,0 +1,176 @@
+/*
+ * dispatch.h -- C ABI of the GB300 per-patch update library (libdispatch_gpu.so).
+ *
+ * The library advances a set of Cartesian patches of ideal MHD with local,
+ * power-of-two time steps, as in DISPATCH (Nordlund et al. 2018, "DISPATCH: a
+ * numerical simulation framework for the exa-scale era. I. Fundamentals"):
+ *
+ *   - each patch is a task with a position, a size, guard zones and a circular
+ *     buffer of time slices (Sec. 2.1; Sec. 3 A);
+ *   - before an update its guard zones are filled by linear interpolation in
+ *     time from its neighbours' slices (Sec. 3 A; closing paragraph of
+ *     Sec. 3 B);
+ *   - a patch is ready when Eq. (1) holds for every neighbour with grace
+ *     g = 0: t_self <= t_nbor;
+ *   - the update is one local Courant step (Sec. 5.1) of a MUSCL-Hancock
+ *     scheme with HLL fluxes and constrained transport of face-centred B
+ *     (Secs. 4.1 and 4.3 name the solver family; the paper prints no scheme);
+ *   - the new state overwrites the oldest slice (Sec. 3 A).
+ *
+ * Every call returns 0 on success or one of the negative DSP_ERR_* codes.
+ * After DSP_ERR_UNPHYSICAL, DSP_ERR_TIMEOUT, DSP_ERR_DEADLOCK, DSP_ERR_BRACKET
+ * or DSP_ERR_CUDA the context is poisoned: only dsp_get_state, dsp_get_times,
+ * dsp_get_schedule, dsp_diagnostics, dsp_last_error and dsp_destroy remain
+ * valid.  Calls on one context are not thread-safe; distinct contexts are
+ * independent.  All device work is issued on the stream given to dsp_create
+ * and is ordered after the caller's earlier work on that stream.
+ */
+#ifndef DISPATCH_GPU_H
+#define DISPATCH_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DSP_API __attribute__((visibility("default")))
+#else
+#define DSP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DSP_OK 0
+#define DSP_ERR_INVALID_ARG (-1)      /* bad pointer, size, layout or parameter */
+#define DSP_ERR_OOM (-2)              /* device or host allocation failed */
+#define DSP_ERR_CUDA (-3)             /* a CUDA runtime call failed */
+#define DSP_ERR_UNPHYSICAL (-4)       /* rho <= 0 or p <= 0 in a new state */
+#define DSP_ERR_TIMEOUT (-5)          /* a bounded device wait ran out */
+#define DSP_ERR_DEADLOCK (-6)         /* no patch ready while some are behind t_end */
+#define DSP_ERR_SCHEDULE_OVERFLOW (-7) /* the schedule log was larger than its capacity */
+#define DSP_ERR_UNSUPPORTED (-8)      /* a valid request this build does not implement */
+#define DSP_ERR_BRACKET (-9)          /* a neighbour's slices do not bracket a guard time */
+
+typedef struct dsp_ctx dsp_ctx;
+
+/* One patch (Sec. 2.1, the patch data type): its refinement level, its
+ * interior cells per axis (x, y, z) and the index of its first interior cell
+ * in the level's cell index space.  All patches of one context must have the
+ * same n, with n > nguard on every axis, and must tile the periodic box. */
+typedef struct {
+  int32_t level;
+  int32_t n[3];
+  int64_t lo[3];
+} dsp_patch_desc;
+
+/* Physics and execution parameters.
+ *   gamma        adiabatic index of the gamma-law equation of state
+ *   cfl          Courant number C of the local step dt = C dx / s_max
+ *   t0           time of the initial state
+ *   dt_max       upper bound on any step (0 = none); use a power of two
+ *   grace        g of Eq. (1); only 0 is supported (DSP_ERR_UNSUPPORTED otherwise)
+ *   box_lo, box_len   the periodic box; cells must be cubic
+ *   base_cells   level-0 cells per axis
+ *   nguard       guard zones per side (>= 2; the stencil reads two)
+ *   nslices      time slices per patch (>= 3)
+ *   precision    0: all state and arithmetic in FP64;
+ *                1: FP32 state and stencil arithmetic, FP64 times and steps
+ *   time_mode    0: one global step per sweep (the smallest patch step);
+ *                1: local steps, each patch its own
+ *   dt_pow2      must be 1: steps are powers of two, so times are exact
+ *   dispatcher   1: sweeps over the ready set (one kernel pair per sweep);
+ *                0: reserved for a persistent device ready queue
+ *   tile_x, tile_y, tile_z   update tile in cells (0 = defaults)
+ *   sched_capacity  entries kept in the schedule log (0 = no log)
+ *   timing       1: time every update-kernel launch with CUDA events on the
+ *                context's stream and report the total in dsp_stats */
+typedef struct {
+  double gamma, cfl, t0, dt_max, grace;
+  double box_lo[3], box_len[3];
+  int32_t base_cells[3];
+  int32_t nguard, nslices, precision, time_mode, dt_pow2, dispatcher;
+  int32_t tile_x, tile_y, tile_z;
+  int64_t sched_capacity;
+  int32_t timing;
+} dsp_params;
+
+/* Counters of one dsp_advance call.  kernel_ms and kernel_launches are the
+ * summed device time and the number of launches of the update kernel (only
+ * when timing was requested); plan_launches counts the dispatcher kernels. */
+typedef struct {
+  int64_t patch_updates, cell_updates, sweeps, fallbacks;
+  double t_min, t_max;
+  int32_t status;
+  double kernel_ms;
+  int64_t kernel_launches, plan_launches;
+} dsp_stats;
+
+/* One schedule entry: patch index, start time, step. */
+typedef struct {
+  int64_t patch;
+  double t_start, dt;
+} dsp_sched_entry;
+
+/* Diagnostics of the newest slices: volume integrals of rho, m, E and of the
+ * face fields (each face once), with FP64 compensated sums; the largest
+ * |sum_d Delta_d b| over cells and the largest |b| over faces. */
+typedef struct {
+  double mass, mom[3], energy, bmean[3], max_divb, max_b;
+} dsp_diag;
+
+/* Create a context: validates the layout, builds the neighbour tables,
+ * allocates every slice on the current CUDA device.  stream is a
+ * cudaStream_t (NULL = legacy default stream).  On success *out owns all
+ * device memory until dsp_destroy. */
+DSP_API int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const dsp_params *params, void *stream,
+               dsp_ctx **out);
+
+/* Load the state of patches [first, first+count) into their first slice at
+ * time t0 (and reset every patch's time to t0 when first == 0 and count ==
+ * npatch).  Arrays are the concatenation, in patch order, of each patch's
+ * interior: U[5][nz][ny][nx] (rho, m_x, m_y, m_z, E), bx[nz][ny][nx+1],
+ * by[nz][ny+1][nx], bz[nz+1][ny][nx], x fastest.  dtype: 0 = float64,
+ * 1 = float32 (converted to the context's precision).  on_device: 1 if the
+ * pointers are device memory.  The arrays are copied; the caller keeps them. */
+DSP_API int dsp_set_state(dsp_ctx *ctx, int32_t first, int32_t count, const void *U, const void *bx, const void *by,
+                  const void *bz, int32_t dtype, int32_t on_device);
+
+/* Advance until every patch has reached t_end, or until max_sweeps sweeps
+ * have run (<= 0: no limit; then t_end must be finite).  Synchronous: returns
+ * after the device work finished, with the status of the run.  out may be NULL. */
+DSP_API int dsp_advance(dsp_ctx *ctx, double t_end, int64_t max_sweeps, dsp_stats *out);
+
+/* Copy the newest slice of patches [first, first+count) out, same layout and
+ * dtype/on_device conventions as dsp_set_state. */
+DSP_API int dsp_get_state(dsp_ctx *ctx, int32_t first, int32_t count, void *U, void *bx, void *by, void *bz,
+                  int32_t dtype, int32_t on_device);
+
+/* Per-patch time of the newest slice and last step (host arrays of npatch). */
+DSP_API int dsp_get_times(dsp_ctx *ctx, double *t, double *dt_last);
+
+/* Copy up to cap schedule entries, in execution order; *n receives the
+ * total recorded so far.  Returns DSP_ERR_SCHEDULE_OVERFLOW if more updates
+ * ran than the log's capacity (the first capacity entries are still valid). */
+DSP_API int dsp_get_schedule(dsp_ctx *ctx, dsp_sched_entry *buf, int64_t cap, int64_t *n);
+
+DSP_API int dsp_diagnostics(dsp_ctx *ctx, dsp_diag *out);
+
+/* Save the whole dispatcher state (every slice, its time and signal speed,
+ * the newest-slice index and last step of every patch) into host memory.
+ * With buf == NULL only *used (the required size) is written.  dsp_load
+ * restores a state saved from a context with the same layout and parameters;
+ * a run resumed from it is bit-identical to the uninterrupted run. */
+DSP_API int dsp_save(dsp_ctx *ctx, void *buf, size_t cap, size_t *used);
+DSP_API int dsp_load(dsp_ctx *ctx, const void *buf, size_t size);
+
+/* Message of the last error on this context ("" if none).  Valid until the
+ * next call on the context. */
+DSP_API const char *dsp_last_error(dsp_ctx *ctx);
+
+DSP_API void dsp_destroy(dsp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,832 @@
+// dsp_host.cu -- the C ABI (include/dispatch.h): context set-up, the sweep
+// dispatcher, state transfer, diagnostics and save/load.
+//
+// Dispatcher (DISPATCH I, Sec. 3 B): each sweep runs one plan kernel and one
+// update kernel on the context's stream.  The plan kernel first publishes the
+// previous sweep (new slice becomes the newest, patch time += dt, schedule log
+// entry), then finds every patch that is ready by Eq. (1) with grace 0
+// (t_P < t_end and t_P <= t_N for every neighbour N), gives it its local
+// Courant step, and compacts the ready patches in index order.  The update
+// kernel then advances every ready patch from the pre-sweep slices.  Because
+// ready neighbours share their time and every read touches only a
+// neighbour's two newest slices, any order of execution inside a sweep gives
+// the same result, and sweeping gives the same per-patch schedule as a
+// time-sorted ready queue.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dsp_internal.h"
+#include "dsp_physics.cuh"
+
+using namespace dsp;
+
+struct dsp_ctx {
+  DevCtx d;
+  dsp_params prm;
+  cudaStream_t stream;
+  int precision;
+  size_t esize;
+  std::string err;
+  int poisoned;
+  // host copies of the tables
+  std::vector<int> nb27, nbl_off, nbl;
+  // device allocations
+  void *slab;
+  double *t_slot, *smax_slot, *dt_last, *dtR;
+  int *latest, *nb27_d, *nbl_off_d, *nbl_d, *R, *ctl;
+  unsigned long long *smax_new;
+  long long *cnt;
+  dsp_sched_entry *sched;
+  void *staging;
+  size_t staging_bytes;
+  int *h_ctl;  // pinned
+  int grid_update;
+  cudaEvent_t ev[2 * 32];
+  int nev;
+};
+
+namespace {
+
+int fail(dsp_ctx *c, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(dsp_ctx *c, int code, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+    if (code == DSP_ERR_CUDA || code == DSP_ERR_UNPHYSICAL || code == DSP_ERR_TIMEOUT || code == DSP_ERR_DEADLOCK ||
+        code == DSP_ERR_BRACKET)
+      c->poisoned = 1;
+  }
+  return code;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return fail(c, DSP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ------------------------------------------------------------------ kernels
+
+// Local Courant step of patch P at time t (all FP64): the signal speed is the
+// largest over P's newest slice and every neighbour slice its guard fill
+// reads; the step is the power of two not above C dx / s, capped by dt_max,
+// halved until it divides t, and clipped to t_end.
+__device__ int patch_dt(const DevCtx &c, int P, double t, double t_end, double *out) {
+  const int ns = c.ns;
+  double M = c.smax_slot[(long long)P * ns + c.latest[P]];
+  for (int k = c.nbl_off[P]; k < c.nbl_off[P + 1]; k++) {
+    const int N = c.nbl[k];
+    const int L = c.latest[N];
+    const double tq = c.t_slot[(long long)N * ns + L];
+    if (tq == t) {
+      M = fmax(M, c.smax_slot[(long long)N * ns + L]);
+    } else {
+      const int Pv = (L + ns - 1) % ns;
+      const double ta = c.t_slot[(long long)N * ns + Pv];
+      if (ta == t) {
+        M = fmax(M, c.smax_slot[(long long)N * ns + Pv]);
+      } else if (ta < t && t < tq) {
+        M = fmax(M, c.smax_slot[(long long)N * ns + Pv]);
+        M = fmax(M, c.smax_slot[(long long)N * ns + L]);
+      } else {
+        return DSP_ERR_BRACKET;
+      }
+    }
+  }
+  const double dtc = c.cfl * c.dx / M;
+  int e;
+  frexp(dtc, &e);
+  double dt = ldexp(1.0, e - 1);
+  if (c.dt_max > 0.0 && dt > c.dt_max) dt = c.dt_max;
+  int guard = 0;
+  while (fmod(t, dt) != 0.0) {
+    dt = dt * 0.5;
+    if (++guard > 1200 || !(dt > 0.0)) return DSP_ERR_INVALID_ARG;
+  }
+  if (dt > t_end - t) dt = t_end - t;
+  *out = dt;
+  return DSP_OK;
+}
+
+__device__ void set_status(const DevCtx &c, int code, int P) {
+  if (atomicCAS(&c.ctl[CTL_STATUS], 0, code) == 0) c.ctl[CTL_ERRP] = P;
+}
+
+constexpr int PLAN_NT = 1024;
+
+__global__ void __launch_bounds__(PLAN_NT) plan_kernel(DevCtx c, double t_end, int global_mode, int publish_only) {
+  __shared__ int s_wsum[PLAN_NT / 32];
+  __shared__ int s_base, s_notdone, s_total;
+  __shared__ unsigned long long s_dtmin;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int ns = c.ns;
+  // 1. publish the previous sweep
+  const int nprev = c.ctl[CTL_NREADY];
+  const long long s0 = c.cnt[CNT_NSCHED];
+  for (int r = tid; r < nprev; r += PLAN_NT) {
+    const int P = c.R[r];
+    const double dt = c.dtR[r];
+    const int L = c.latest[P], Ln = (L + 1) % ns;
+    const double t = c.t_slot[(long long)P * ns + L];
+    c.t_slot[(long long)P * ns + Ln] = t + dt;
+    c.smax_slot[(long long)P * ns + Ln] = __longlong_as_double((long long)c.smax_new[P]);
+    c.latest[P] = Ln;
+    c.dt_last[P] = dt;
+    const long long e = s0 + r;
+    if (e < c.sched_cap) {
+      c.sched[e].patch = P;
+      c.sched[e].t_start = t;
+      c.sched[e].dt = dt;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (nprev > 0) {
+      c.cnt[CNT_NSCHED] += nprev;
+      c.cnt[CNT_PATCH_UPDATES] += nprev;
+      c.cnt[CNT_CELL_UPDATES] += (long long)nprev * c.nc;
+      c.cnt[CNT_SWEEPS] += 1;
+    }
+    c.ctl[CTL_NREADY] = 0;
+    s_base = 0;
+    s_notdone = 0;
+    s_dtmin = 0x7ff0000000000000ull;  // +inf
+  }
+  __syncthreads();
+  if (publish_only || c.ctl[CTL_STATUS] != 0) return;
+  // 2. ready set, steps, compaction in patch order
+  for (int chunk = 0; chunk < c.np; chunk += PLAN_NT) {
+    const int P = chunk + tid;
+    int flag = 0;
+    double dtP = 0.0;
+    if (P < c.np) {
+      const double t = c.t_slot[(long long)P * ns + c.latest[P]];
+      if (t < t_end) {
+        s_notdone = 1;
+        bool ready = true;
+        for (int k = c.nbl_off[P]; k < c.nbl_off[P + 1]; k++) {
+          const int N = c.nbl[k];
+          if (!(t <= c.t_slot[(long long)N * ns + c.latest[N]])) { ready = false; break; }
+        }
+        if (ready) {
+          const int rc = patch_dt(c, P, t, t_end, &dtP);
+          if (rc != DSP_OK) set_status(c, rc, P);
+          else flag = 1;
+        }
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) s_wsum[wid] = __popc(bal);
+    __syncthreads();
+    if (wid == 0) {
+      int v = s_wsum[lane];
+      int incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+      }
+      s_wsum[lane] = incl - v;
+      if (lane == 31) s_total = incl;
+    }
+    __syncthreads();
+    if (flag) {
+      const int idx = s_base + s_wsum[wid] + __popc(bal & ((1u << lane) - 1u));
+      c.R[idx] = P;
+      c.dtR[idx] = dtP;
+      c.smax_new[P] = 0ull;
+      if (global_mode) atomicMin(&s_dtmin, (unsigned long long)__double_as_longlong(dtP));
+    }
+    __syncthreads();
+    if (tid == 0) s_base += s_total;
+    __syncthreads();
+  }
+  const int nr = s_base;
+  if (global_mode) {
+    const double dtg = __longlong_as_double((long long)s_dtmin);
+    for (int r = tid; r < nr; r += PLAN_NT) c.dtR[r] = dtg;
+  }
+  if (tid == 0) {
+    if (c.ctl[CTL_STATUS] != 0) {
+      c.ctl[CTL_NREADY] = 0;
+    } else {
+      c.ctl[CTL_NREADY] = nr;
+      if (nr == 0) {
+        if (!s_notdone) c.ctl[CTL_DONE] = 1;
+        else set_status(c, DSP_ERR_DEADLOCK, -1);
+      }
+    }
+  }
+}
+
+// Signal speed and positivity of slice s of every patch (one block per patch).
+template <typename T>
+__global__ void smax_kernel(DevCtx c, int slot, int first, int count) {
+  const int P = first + blockIdx.x;
+  if (P >= first + count) return;
+  const T *base = (const T *)c.slab + (long long)slot * c.slot_stride + (long long)P * c.patch_len;
+  const int nx = c.nx, ny = c.ny, nz = c.nz;
+  const long long nc = c.nc;
+  const T *bxa = base + 5 * nc, *bya = bxa + c.nfx, *bza = bya + c.nfy;
+  const T gamma = (T)c.gamma;
+  double m = 0.0;
+  for (long long id = threadIdx.x; id < nc; id += blockDim.x) {
+    const int i = (int)(id % nx), j = (int)((id / nx) % ny), k = (int)(id / ((long long)nx * ny));
+    T W[8];
+    prim(base[id], base[nc + id], base[2 * nc + id], base[3 * nc + id], base[4 * nc + id],
+         bxa[((long long)k * ny + j) * (nx + 1) + i], bxa[((long long)k * ny + j) * (nx + 1) + i + 1],
+         bya[((long long)k * (ny + 1) + j) * nx + i], bya[((long long)k * (ny + 1) + j + 1) * nx + i],
+         bza[((long long)k * ny + j) * nx + i], bza[((long long)(k + 1) * ny + j) * nx + i], gamma, W);
+    if (!(W[RHO] > T(0)) || !(W[PR] > T(0))) set_status(c, DSP_ERR_UNPHYSICAL, P);
+    m = fmax(m, (double)signal_sum(W, gamma));
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double u = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) u = fmax(u, __shfl_xor_sync(0xffffffffu, u, o));
+    if (threadIdx.x == 0) c.smax_slot[(long long)P * c.ns + slot] = u;
+  }
+}
+
+// Copy between the caller's four arrays (patches [first, first+count)) and
+// the slices: dir 0 loads slot 0, dir 1 stores each patch's newest slot.
+template <typename TS, typename TU>
+__global__ void xfer_kernel(DevCtx c, int first, int count, TU *U, TU *bx, TU *by, TU *bz, int dir) {
+  const long long per[4] = {5 * c.nc, c.nfx, c.nfy, c.nfz};
+  const long long off[4] = {0, 5 * c.nc, 5 * c.nc + c.nfx, 5 * c.nc + c.nfx + c.nfy};
+  TU *arr[4] = {U, bx, by, bz};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int f = 0; f < 4; f++) {
+    const long long n = per[f] * count;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+      const int P = first + (int)(e / per[f]);
+      const long long l = e % per[f];
+      const int s = dir == 0 ? 0 : c.latest[P];
+      TS *slot = (TS *)c.slab + (long long)s * c.slot_stride + (long long)P * c.patch_len + off[f];
+      if (dir == 0) slot[l] = (TS)arr[f][e];
+      else arr[f][e] = (TU)slot[l];
+    }
+  }
+}
+
+__global__ void reset_times_kernel(DevCtx c, int first, int count, double t0) {
+  for (int P = first + blockIdx.x * blockDim.x + threadIdx.x; P < first + count; P += gridDim.x * blockDim.x) {
+    for (int s = 0; s < c.ns; s++) c.t_slot[(long long)P * c.ns + s] = s == 0 ? t0 : __longlong_as_double(0x7ff8000000000000ll);
+    c.latest[P] = 0;
+    c.dt_last[P] = 0.0;
+  }
+}
+
+struct NSum {
+  double s, c;
+};
+__device__ __forceinline__ void nadd(NSum &a, double x) {
+  const double t = a.s + x;
+  if (fabs(a.s) >= fabs(x)) a.c += (a.s - t) + x;
+  else a.c += (x - t) + a.s;
+  a.s = t;
+}
+
+// Per-patch compensated sums of the newest slice (deterministic order:
+// fixed strided assignment, then a fixed tree), plus max |div b| and max |b|.
+template <typename T>
+__global__ void diag_kernel(DevCtx c, double *out) {
+  const int P = blockIdx.x;
+  const int s = c.latest[P];
+  const T *base = (const T *)c.slab + (long long)s * c.slot_stride + (long long)P * c.patch_len;
+  const int nx = c.nx, ny = c.ny;
+  const long long nc = c.nc;
+  const T *bxa = base + 5 * nc, *bya = bxa + c.nfx, *bza = bya + c.nfy;
+  const double dV = c.dx * c.dx * c.dx;
+  NSum acc[8];
+  for (int q = 0; q < 8; q++) acc[q].s = acc[q].c = 0.0;
+  double mdiv = 0.0, mb = 0.0;
+  for (long long id = threadIdx.x; id < nc; id += blockDim.x) {
+    const int i = (int)(id % nx), j = (int)((id / nx) % ny), k = (int)(id / ((long long)nx * ny));
+    for (int q = 0; q < 5; q++) nadd(acc[q], (double)base[q * nc + id] * dV);
+    const double bxl = bxa[((long long)k * ny + j) * (nx + 1) + i], bxr = bxa[((long long)k * ny + j) * (nx + 1) + i + 1];
+    const double byl = bya[((long long)k * (ny + 1) + j) * nx + i], byr = bya[((long long)k * (ny + 1) + j + 1) * nx + i];
+    const double bzl = bza[((long long)k * ny + j) * nx + i], bzr = bza[((long long)(k + 1) * ny + j) * nx + i];
+    nadd(acc[5], bxl * dV);
+    nadd(acc[6], byl * dV);
+    nadd(acc[7], bzl * dV);
+    mdiv = fmax(mdiv, fabs((bxr - bxl) + (byr - byl) + (bzr - bzl)));
+    mb = fmax(mb, fmax(fabs(bxl), fmax(fabs(byl), fabs(bzl))));
+  }
+  __shared__ double sh[256][18];
+  for (int q = 0; q < 8; q++) {
+    sh[threadIdx.x][2 * q] = acc[q].s;
+    sh[threadIdx.x][2 * q + 1] = acc[q].c;
+  }
+  sh[threadIdx.x][16] = mdiv;
+  sh[threadIdx.x][17] = mb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    NSum tot[8];
+    for (int q = 0; q < 8; q++) tot[q].s = tot[q].c = 0.0;
+    double md = 0.0, mm = 0.0;
+    for (int t = 0; t < (int)blockDim.x; t++) {
+      for (int q = 0; q < 8; q++) {
+        nadd(tot[q], sh[t][2 * q]);
+        nadd(tot[q], sh[t][2 * q + 1]);
+      }
+      md = fmax(md, sh[t][16]);
+      mm = fmax(mm, sh[t][17]);
+    }
+    for (int q = 0; q < 8; q++) out[(long long)P * 10 + q] = tot[q].s + tot[q].c;
+    out[(long long)P * 10 + 8] = md;
+    out[(long long)P * 10 + 9] = mm;
+  }
+}
+
+int launch_update(dsp_ctx *c) {
+  if (c->precision == 0) return launch_update_f64(c->d, c->grid_update, c->stream);
+  return launch_update_f32(c->d, c->grid_update, c->stream);
+}
+
+int read_status(dsp_ctx *c) {
+  CK(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(int) * CTL_COUNT, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return DSP_OK;
+}
+
+int ensure_staging(dsp_ctx *c, size_t bytes) {
+  if (c->staging_bytes >= bytes) return DSP_OK;
+  if (c->staging) cudaFree(c->staging);
+  c->staging = nullptr;
+  c->staging_bytes = 0;
+  if (cudaMalloc(&c->staging, bytes) != cudaSuccess) return fail(c, DSP_ERR_OOM, "staging buffer of %zu bytes", bytes);
+  c->staging_bytes = bytes;
+  return DSP_OK;
+}
+
+template <typename TS>
+int run_xfer(dsp_ctx *c, int first, int count, void *U, void *bx, void *by, void *bz, int dtype, int dir) {
+  const int grid = 1184;
+  if (dtype == 0)
+    xfer_kernel<TS, double><<<grid, 256, 0, c->stream>>>(c->d, first, count, (double *)U, (double *)bx, (double *)by,
+                                                       (double *)bz, dir);
+  else
+    xfer_kernel<TS, float><<<grid, 256, 0, c->stream>>>(c->d, first, count, (float *)U, (float *)bx, (float *)by,
+                                                      (float *)bz, dir);
+  CK(cudaGetLastError());
+  return DSP_OK;
+}
+
+int transfer(dsp_ctx *c, int first, int count, const void *U, const void *bx, const void *by, const void *bz, int dtype,
+             int on_device, int dir) {
+  const size_t es = dtype == 0 ? 8 : 4;
+  const size_t nU = (size_t)5 * c->d.nc * count, nX = (size_t)c->d.nfx * count, nY = (size_t)c->d.nfy * count,
+               nZ = (size_t)c->d.nfz * count;
+  void *dU = (void *)U, *dX = (void *)bx, *dY = (void *)by, *dZ = (void *)bz;
+  if (!on_device) {
+    int rc = ensure_staging(c, es * (nU + nX + nY + nZ));
+    if (rc) return rc;
+    char *s = (char *)c->staging;
+    dU = s;
+    dX = s + es * nU;
+    dY = s + es * (nU + nX);
+    dZ = s + es * (nU + nX + nY);
+    if (dir == 0) {
+      CK(cudaMemcpyAsync(dU, U, es * nU, cudaMemcpyHostToDevice, c->stream));
+      CK(cudaMemcpyAsync(dX, bx, es * nX, cudaMemcpyHostToDevice, c->stream));
+      CK(cudaMemcpyAsync(dY, by, es * nY, cudaMemcpyHostToDevice, c->stream));
+      CK(cudaMemcpyAsync(dZ, bz, es * nZ, cudaMemcpyHostToDevice, c->stream));
+    }
+  }
+  int rc = c->precision == 0 ? run_xfer<double>(c, first, count, dU, dX, dY, dZ, dtype, dir)
+                             : run_xfer<float>(c, first, count, dU, dX, dY, dZ, dtype, dir);
+  if (rc) return rc;
+  if (!on_device && dir == 1) {
+    CK(cudaMemcpyAsync((void *)U, dU, es * nU, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync((void *)bx, dX, es * nX, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync((void *)by, dY, es * nY, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync((void *)bz, dZ, es * nZ, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return DSP_OK;
+}
+
+void free_all(dsp_ctx *c) {
+  void *ptrs[] = {c->slab,  c->t_slot, c->smax_slot, c->dt_last, c->dtR,      c->latest, c->nb27_d, c->nbl_off_d,
+                  c->nbl_d, c->R,      c->ctl,       c->smax_new, c->cnt,     c->sched,  c->staging};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_ctl) cudaFreeHost(c->h_ctl);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const dsp_params *prm, void *stream,
+                          dsp_ctx **out) {
+  if (!out) return DSP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!patches || !prm || npatch <= 0) return DSP_ERR_INVALID_ARG;
+  if (prm->grace != 0.0 || prm->dt_pow2 != 1 || prm->dispatcher != 1) return DSP_ERR_UNSUPPORTED;
+  if (prm->nguard < 2 || prm->nslices < 3 || (prm->precision != 0 && prm->precision != 1) ||
+      (prm->time_mode != 0 && prm->time_mode != 1) || !(prm->cfl > 0.0) || !(prm->gamma > 1.0))
+    return DSP_ERR_INVALID_ARG;
+  const int nx = patches[0].n[0], ny = patches[0].n[1], nz = patches[0].n[2];
+  for (int d = 0; d < 3; d++)
+    if (prm->base_cells[d] <= 0 || !(prm->box_len[d] > 0.0)) return DSP_ERR_INVALID_ARG;
+  const double dx = prm->box_len[0] / prm->base_cells[0];
+  for (int d = 1; d < 3; d++)
+    if (std::fabs(prm->box_len[d] / prm->base_cells[d] - dx) > 1e-12 * dx) return DSP_ERR_INVALID_ARG;
+  if (nx <= prm->nguard || ny <= prm->nguard || nz <= prm->nguard) return DSP_ERR_INVALID_ARG;
+  if (prm->base_cells[0] % nx || prm->base_cells[1] % ny || prm->base_cells[2] % nz) return DSP_ERR_INVALID_ARG;
+  const int px = prm->base_cells[0] / nx, py = prm->base_cells[1] / ny, pz = prm->base_cells[2] / nz;
+  if ((long long)px * py * pz != npatch) return DSP_ERR_INVALID_ARG;
+  std::vector<int> grid((size_t)npatch, -1);
+  for (int i = 0; i < npatch; i++) {
+    const dsp_patch_desc &p = patches[i];
+    if (p.level != 0) return DSP_ERR_UNSUPPORTED;
+    if (p.n[0] != nx || p.n[1] != ny || p.n[2] != nz) return DSP_ERR_UNSUPPORTED;
+    if (p.lo[0] % nx || p.lo[1] % ny || p.lo[2] % nz) return DSP_ERR_INVALID_ARG;
+    const long long gx = p.lo[0] / nx, gy = p.lo[1] / ny, gz = p.lo[2] / nz;
+    if (gx < 0 || gy < 0 || gz < 0 || gx >= px || gy >= py || gz >= pz) return DSP_ERR_INVALID_ARG;
+    int &slot = grid[(size_t)((gz * py + gy) * px + gx)];
+    if (slot >= 0) return DSP_ERR_INVALID_ARG;
+    slot = i;
+  }
+  dsp_ctx *c = new dsp_ctx();
+  memset(&c->d, 0, sizeof c->d);
+  c->prm = *prm;
+  c->stream = (cudaStream_t)stream;
+  c->precision = prm->precision;
+  c->esize = prm->precision == 0 ? 8 : 4;
+  c->poisoned = 0;
+  c->nev = 0;
+  DevCtx &d = c->d;
+  d.np = npatch;
+  d.ns = prm->nslices;
+  d.nx = nx; d.ny = ny; d.nz = nz;
+  d.nc = (long long)nx * ny * nz;
+  d.nfx = (long long)(nx + 1) * ny * nz;
+  d.nfy = (long long)nx * (ny + 1) * nz;
+  d.nfz = (long long)nx * ny * (nz + 1);
+  d.patch_len = 5 * d.nc + d.nfx + d.nfy + d.nfz;
+  d.slot_stride = d.patch_len * npatch;
+  d.gamma = prm->gamma;
+  d.cfl = prm->cfl;
+  d.dx = dx;
+  d.dt_max = prm->dt_max;
+  int TX, TY;
+  if (c->precision == 0) update_tile_f64(&TX, &TY);
+  else update_tile_f32(&TX, &TY);
+  d.tx = TX;
+  d.ty = TY;
+  d.tz = prm->tile_z > 0 ? std::min(prm->tile_z, nz) : nz;
+  d.ntx = (nx + TX - 1) / TX;
+  d.nty = (ny + TY - 1) / TY;
+  d.ntz = (nz + d.tz - 1) / d.tz;
+  d.tiles = d.ntx * d.nty * d.ntz;
+  // neighbour tables
+  c->nb27.resize((size_t)npatch * 27);
+  c->nbl_off.assign((size_t)npatch + 1, 0);
+  for (int i = 0; i < npatch; i++) {
+    const int gx = (int)(patches[i].lo[0] / nx), gy = (int)(patches[i].lo[1] / ny), gz = (int)(patches[i].lo[2] / nz);
+    std::vector<int> uniq;
+    for (int oz = -1; oz <= 1; oz++)
+      for (int oy = -1; oy <= 1; oy++)
+        for (int ox = -1; ox <= 1; ox++) {
+          const int qx = (gx + ox + px) % px, qy = (gy + oy + py) % py, qz = (gz + oz + pz) % pz;
+          const int q = grid[(size_t)((qz * py + qy) * px + qx)];
+          c->nb27[(size_t)i * 27 + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] = q;
+          if (q != i && std::find(uniq.begin(), uniq.end(), q) == uniq.end()) uniq.push_back(q);
+        }
+    std::sort(uniq.begin(), uniq.end());
+    c->nbl_off[i + 1] = c->nbl_off[i] + (int)uniq.size();
+    c->nbl.insert(c->nbl.end(), uniq.begin(), uniq.end());
+  }
+  auto alloc = [&](void **p, size_t bytes) {
+    if (cudaMalloc(p, bytes ? bytes : 1) != cudaSuccess) return false;
+    return true;
+  };
+  const size_t slab_bytes = c->esize * (size_t)d.slot_stride * d.ns;
+  const long long cap = prm->sched_capacity > 0 ? prm->sched_capacity : 0;
+  bool ok = alloc(&c->slab, slab_bytes) && alloc((void **)&c->t_slot, sizeof(double) * npatch * d.ns) &&
+            alloc((void **)&c->smax_slot, sizeof(double) * npatch * d.ns) &&
+            alloc((void **)&c->dt_last, sizeof(double) * npatch) && alloc((void **)&c->dtR, sizeof(double) * npatch) &&
+            alloc((void **)&c->latest, sizeof(int) * npatch) && alloc((void **)&c->nb27_d, sizeof(int) * npatch * 27) &&
+            alloc((void **)&c->nbl_off_d, sizeof(int) * (npatch + 1)) &&
+            alloc((void **)&c->nbl_d, sizeof(int) * std::max<size_t>(1, c->nbl.size())) &&
+            alloc((void **)&c->R, sizeof(int) * npatch) && alloc((void **)&c->ctl, sizeof(int) * CTL_COUNT) &&
+            alloc((void **)&c->smax_new, sizeof(unsigned long long) * npatch) &&
+            alloc((void **)&c->cnt, sizeof(long long) * CNT_COUNT) &&
+            alloc((void **)&c->sched, sizeof(dsp_sched_entry) * std::max<long long>(1, cap));
+  if (ok && cudaMallocHost((void **)&c->h_ctl, sizeof(int) * CTL_COUNT) != cudaSuccess) ok = false;
+  if (!ok) {
+    free_all(c);
+    delete c;
+    return DSP_ERR_OOM;
+  }
+  d.slab = c->slab;
+  d.t_slot = c->t_slot;
+  d.smax_slot = c->smax_slot;
+  d.latest = c->latest;
+  d.dt_last = c->dt_last;
+  d.nb27 = c->nb27_d;
+  d.nbl_off = c->nbl_off_d;
+  d.nbl = c->nbl_d;
+  d.R = c->R;
+  d.dtR = c->dtR;
+  d.smax_new = c->smax_new;
+  d.ctl = c->ctl;
+  d.cnt = c->cnt;
+  d.sched = c->sched;
+  d.sched_cap = cap;
+  cudaError_t e = cudaMemcpyAsync(c->nb27_d, c->nb27.data(), sizeof(int) * c->nb27.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->nbl_off_d, c->nbl_off.data(), sizeof(int) * c->nbl_off.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && !c->nbl.empty())
+    e = cudaMemcpyAsync(c->nbl_d, c->nbl.data(), sizeof(int) * c->nbl.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl, 0, sizeof(int) * CTL_COUNT, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_COUNT, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->slab, 0, slab_bytes, c->stream);
+  if (e == cudaSuccess) {
+    reset_times_kernel<<<(npatch + 255) / 256, 256, 0, c->stream>>>(d, 0, npatch, prm->t0);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete c;
+    return DSP_ERR_CUDA;
+  }
+  c->grid_update = c->precision == 0 ? update_grid_f64(d) : update_grid_f32(d);
+  *out = c;
+  return DSP_OK;
+}
+
+extern "C" int dsp_set_state(dsp_ctx *c, int32_t first, int32_t count, const void *U, const void *bx, const void *by,
+                             const void *bz, int32_t dtype, int32_t on_device) {
+  if (!c) return DSP_ERR_INVALID_ARG;
+  if (c->poisoned) return fail(c, DSP_ERR_INVALID_ARG, "context is poisoned by an earlier error");
+  if (first < 0 || count <= 0 || first + count > c->d.np || !U || !bx || !by || !bz || (dtype != 0 && dtype != 1))
+    return fail(c, DSP_ERR_INVALID_ARG, "bad arguments to dsp_set_state");
+  int rc = transfer(c, first, count, U, bx, by, bz, dtype, on_device, 0);
+  if (rc) return rc;
+  reset_times_kernel<<<(count + 255) / 256, 256, 0, c->stream>>>(c->d, first, count, c->prm.t0);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(c->ctl, 0, sizeof(int) * CTL_COUNT, c->stream));
+  CK(cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_COUNT, c->stream));
+  if (c->precision == 0) smax_kernel<double><<<count, 256, 0, c->stream>>>(c->d, 0, first, count);
+  else smax_kernel<float><<<count, 256, 0, c->stream>>>(c->d, 0, first, count);
+  CK(cudaGetLastError());
+  rc = read_status(c);
+  if (rc) return rc;
+  if (c->h_ctl[CTL_STATUS] != 0)
+    return fail(c, c->h_ctl[CTL_STATUS], "initial state has rho <= 0 or p <= 0 in patch %d", c->h_ctl[CTL_ERRP]);
+  return DSP_OK;
+}
+
+extern "C" int dsp_advance(dsp_ctx *c, double t_end, int64_t max_sweeps, dsp_stats *out) {
+  if (!c) return DSP_ERR_INVALID_ARG;
+  if (c->poisoned) return fail(c, DSP_ERR_INVALID_ARG, "context is poisoned by an earlier error");
+  if (std::isnan(t_end) || (!(t_end < INFINITY) && max_sweeps <= 0))
+    return fail(c, DSP_ERR_INVALID_ARG, "an unbounded advance needs a finite t_end or a sweep limit");
+  long long c0[CNT_COUNT];
+  CK(cudaMemcpyAsync(c0, c->cnt, sizeof c0, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemsetAsync(c->ctl + CTL_DONE, 0, sizeof(int), c->stream));
+  const int global_mode = c->prm.time_mode == 0;
+  const int batch = 32;
+  long long done_sweeps = 0, plans = 0, kl = 0;
+  double kms = 0.0;
+  int rc = DSP_OK;
+  const bool timing = c->prm.timing != 0;
+  if (timing && c->nev == 0) {
+    for (int i = 0; i < 2 * batch; i++) CK(cudaEventCreate(&c->ev[i]));
+    c->nev = 2 * batch;
+  }
+  for (;;) {
+    long long nb = batch;
+    if (max_sweeps > 0) nb = std::min<long long>(nb, max_sweeps - done_sweeps);
+    for (long long s = 0; s < nb; s++) {
+      plan_kernel<<<1, PLAN_NT, 0, c->stream>>>(c->d, t_end, global_mode, 0);
+      CK(cudaGetLastError());
+      plans++;
+      if (timing) CK(cudaEventRecord(c->ev[2 * s], c->stream));
+      rc = launch_update(c);
+      if (rc) return fail(c, rc, "update kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+      if (timing) CK(cudaEventRecord(c->ev[2 * s + 1], c->stream));
+    }
+    done_sweeps += nb;
+    rc = read_status(c);
+    if (rc) return rc;
+    if (timing) {
+      for (long long s = 0; s < nb; s++) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[2 * s], c->ev[2 * s + 1]));
+        kms += ms;
+      }
+    }
+    kl += nb;
+    if (c->h_ctl[CTL_STATUS] != 0 || c->h_ctl[CTL_DONE]) break;
+    if (max_sweeps > 0 && done_sweeps >= max_sweeps) break;
+  }
+  plan_kernel<<<1, PLAN_NT, 0, c->stream>>>(c->d, t_end, global_mode, 1);
+  CK(cudaGetLastError());
+  plans++;
+  rc = read_status(c);
+  if (rc) return rc;
+  long long c1[CNT_COUNT];
+  CK(cudaMemcpyAsync(c1, c->cnt, sizeof c1, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const int st = c->h_ctl[CTL_STATUS];
+  if (out) {
+    out->patch_updates = c1[CNT_PATCH_UPDATES] - c0[CNT_PATCH_UPDATES];
+    out->cell_updates = c1[CNT_CELL_UPDATES] - c0[CNT_CELL_UPDATES];
+    out->sweeps = c1[CNT_SWEEPS] - c0[CNT_SWEEPS];
+    out->fallbacks = c1[CNT_FALLBACKS] - c0[CNT_FALLBACKS];
+    out->status = st;
+    out->kernel_ms = timing ? kms : 0.0;
+    out->kernel_launches = kl;
+    out->plan_launches = plans;
+    std::vector<double> t((size_t)c->d.np);
+    if (dsp_get_times(c, t.data(), nullptr) == DSP_OK) {
+      out->t_min = *std::min_element(t.begin(), t.end());
+      out->t_max = *std::max_element(t.begin(), t.end());
+    } else {
+      out->t_min = out->t_max = NAN;
+    }
+  }
+  if (st != 0) {
+    const char *what = st == DSP_ERR_UNPHYSICAL ? "rho <= 0 or p <= 0 in a new state"
+                       : st == DSP_ERR_DEADLOCK  ? "no patch is ready but some are behind t_end"
+                       : st == DSP_ERR_BRACKET   ? "neighbour slices do not bracket a guard-zone time"
+                                                 : "device error";
+    return fail(c, st, "%s (patch %d, cell %d)", what, c->h_ctl[CTL_ERRP], c->h_ctl[CTL_ERRC]);
+  }
+  return DSP_OK;
+}
+
+extern "C" int dsp_get_state(dsp_ctx *c, int32_t first, int32_t count, void *U, void *bx, void *by, void *bz,
+                             int32_t dtype, int32_t on_device) {
+  if (!c) return DSP_ERR_INVALID_ARG;
+  if (first < 0 || count <= 0 || first + count > c->d.np || !U || !bx || !by || !bz || (dtype != 0 && dtype != 1))
+    return fail(c, DSP_ERR_INVALID_ARG, "bad arguments to dsp_get_state");
+  return transfer(c, first, count, U, bx, by, bz, dtype, on_device, 1);
+}
+
+extern "C" int dsp_get_times(dsp_ctx *c, double *t, double *dt_last) {
+  if (!c || !t) return DSP_ERR_INVALID_ARG;
+  const int np = c->d.np, ns = c->d.ns;
+  std::vector<double> ts((size_t)np * ns);
+  std::vector<int> lat((size_t)np);
+  CK(cudaMemcpyAsync(ts.data(), c->t_slot, sizeof(double) * ts.size(), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(lat.data(), c->latest, sizeof(int) * np, cudaMemcpyDeviceToHost, c->stream));
+  if (dt_last) CK(cudaMemcpyAsync(dt_last, c->dt_last, sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < np; i++) t[i] = ts[(size_t)i * ns + lat[i]];
+  return DSP_OK;
+}
+
+extern "C" int dsp_get_schedule(dsp_ctx *c, dsp_sched_entry *buf, int64_t cap, int64_t *n) {
+  if (!c || !n) return DSP_ERR_INVALID_ARG;
+  long long cnt[CNT_COUNT];
+  CK(cudaMemcpyAsync(cnt, c->cnt, sizeof cnt, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const long long total = cnt[CNT_NSCHED];
+  *n = total;
+  const long long have = std::min<long long>(total, c->d.sched_cap);
+  const long long k = std::min<long long>(have, cap);
+  if (buf && k > 0) {
+    CK(cudaMemcpyAsync(buf, c->sched, sizeof(dsp_sched_entry) * k, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  if (total > c->d.sched_cap) return fail(c, DSP_ERR_SCHEDULE_OVERFLOW, "schedule log holds %lld of %lld entries", (long long)c->d.sched_cap, total);
+  return DSP_OK;
+}
+
+extern "C" int dsp_diagnostics(dsp_ctx *c, dsp_diag *out) {
+  if (!c || !out) return DSP_ERR_INVALID_ARG;
+  const int np = c->d.np;
+  double *dd = nullptr;
+  CK(cudaMalloc(&dd, sizeof(double) * 10 * np));
+  if (c->precision == 0) diag_kernel<double><<<np, 256, 0, c->stream>>>(c->d, dd);
+  else diag_kernel<float><<<np, 256, 0, c->stream>>>(c->d, dd);
+  cudaError_t e = cudaGetLastError();
+  std::vector<double> h((size_t)10 * np);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), dd, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(dd);
+  if (e != cudaSuccess) return fail(c, DSP_ERR_CUDA, "diagnostics: %s", cudaGetErrorString(e));
+  double s[8], cc[8];
+  for (int q = 0; q < 8; q++) s[q] = cc[q] = 0.0;
+  double md = 0.0, mb = 0.0;
+  for (int P = 0; P < np; P++) {
+    for (int q = 0; q < 8; q++) {
+      const double x = h[(size_t)P * 10 + q];
+      const double t = s[q] + x;
+      if (std::fabs(s[q]) >= std::fabs(x)) cc[q] += (s[q] - t) + x;
+      else cc[q] += (x - t) + s[q];
+      s[q] = t;
+    }
+    md = std::max(md, h[(size_t)P * 10 + 8]);
+    mb = std::max(mb, h[(size_t)P * 10 + 9]);
+  }
+  out->mass = s[0] + cc[0];
+  for (int d = 0; d < 3; d++) out->mom[d] = s[1 + d] + cc[1 + d];
+  out->energy = s[4] + cc[4];
+  for (int d = 0; d < 3; d++) out->bmean[d] = s[5 + d] + cc[5 + d];
+  out->max_divb = md;
+  out->max_b = mb;
+  return DSP_OK;
+}
+
+namespace {
+struct SaveHeader {
+  char magic[8];
+  int32_t version, np, ns, precision;
+  int64_t patch_len, slot_stride;
+};
+}  // namespace
+
+extern "C" int dsp_save(dsp_ctx *c, void *buf, size_t cap, size_t *used) {
+  if (!c || !used) return DSP_ERR_INVALID_ARG;
+  const int np = c->d.np, ns = c->d.ns;
+  const size_t slab = c->esize * (size_t)c->d.slot_stride * ns;
+  const size_t need = sizeof(SaveHeader) + sizeof(double) * 2 * np * ns + sizeof(int) * np + sizeof(double) * np + slab;
+  *used = need;
+  if (!buf) return DSP_OK;
+  if (cap < need) return fail(c, DSP_ERR_INVALID_ARG, "save buffer too small (%zu < %zu)", cap, need);
+  char *p = (char *)buf;
+  SaveHeader h;
+  memset(&h, 0, sizeof h);
+  memcpy(h.magic, "DSPSAVE", 8);
+  h.version = 1;
+  h.np = np;
+  h.ns = ns;
+  h.precision = c->precision;
+  h.patch_len = c->d.patch_len;
+  h.slot_stride = c->d.slot_stride;
+  memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  CK(cudaMemcpyAsync(p, c->t_slot, sizeof(double) * np * ns, cudaMemcpyDeviceToHost, c->stream));
+  p += sizeof(double) * np * ns;
+  CK(cudaMemcpyAsync(p, c->smax_slot, sizeof(double) * np * ns, cudaMemcpyDeviceToHost, c->stream));
+  p += sizeof(double) * np * ns;
+  CK(cudaMemcpyAsync(p, c->latest, sizeof(int) * np, cudaMemcpyDeviceToHost, c->stream));
+  p += sizeof(int) * np;
+  CK(cudaMemcpyAsync(p, c->dt_last, sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
+  p += sizeof(double) * np;
+  CK(cudaMemcpyAsync(p, c->slab, slab, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return DSP_OK;
+}
+
+extern "C" int dsp_load(dsp_ctx *c, const void *buf, size_t size) {
+  if (!c || !buf) return DSP_ERR_INVALID_ARG;
+  const int np = c->d.np, ns = c->d.ns;
+  const size_t slab = c->esize * (size_t)c->d.slot_stride * ns;
+  const size_t need = sizeof(SaveHeader) + sizeof(double) * 2 * np * ns + sizeof(int) * np + sizeof(double) * np + slab;
+  if (size < need) return fail(c, DSP_ERR_INVALID_ARG, "saved state too small");
+  SaveHeader h;
+  memcpy(&h, buf, sizeof h);
+  if (memcmp(h.magic, "DSPSAVE", 8) || h.version != 1 || h.np != np || h.ns != ns || h.precision != c->precision ||
+      h.patch_len != c->d.patch_len)
+    return fail(c, DSP_ERR_INVALID_ARG, "saved state does not match this context");
+  const char *p = (const char *)buf + sizeof h;
+  CK(cudaMemcpyAsync(c->t_slot, p, sizeof(double) * np * ns, cudaMemcpyHostToDevice, c->stream));
+  p += sizeof(double) * np * ns;
+  CK(cudaMemcpyAsync(c->smax_slot, p, sizeof(double) * np * ns, cudaMemcpyHostToDevice, c->stream));
+  p += sizeof(double) * np * ns;
+  CK(cudaMemcpyAsync(c->latest, p, sizeof(int) * np, cudaMemcpyHostToDevice, c->stream));
+  p += sizeof(int) * np;
+  CK(cudaMemcpyAsync(c->dt_last, p, sizeof(double) * np, cudaMemcpyHostToDevice, c->stream));
+  p += sizeof(double) * np;
+  CK(cudaMemcpyAsync(c->slab, p, slab, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->ctl, 0, sizeof(int) * CTL_COUNT, c->stream));
+  CK(cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_COUNT, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->poisoned = 0;
+  c->err.clear();
+  return DSP_OK;
+}
+
+extern "C" const char *dsp_last_error(dsp_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" void dsp_destroy(dsp_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (int i = 0; i < c->nev; i++) cudaEventDestroy(c->ev[i]);
+  free_all(c);
+  delete c;
+}

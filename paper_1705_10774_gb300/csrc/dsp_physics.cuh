@@ -1,0 +1,166 @@
+// dsp_physics.cuh -- cell- and face-level arithmetic of the MHD step.
+//
+// Every expression has a fixed evaluation order; the FP64 translation units
+// are compiled with -fmad=false so that each result is a pure function of its
+// inputs (IEEE division and square root, no contraction).  Heaviside-Lorentz
+// units: E = -v x B, total energy E = p/(gamma-1) + rho v^2/2 + B^2/2.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace dsp {
+
+enum { RHO = 0, VX = 1, VY = 2, VZ = 3, PR = 4, BX = 5, BY = 6, BZ = 7 };
+
+template <typename T> __device__ __forceinline__ T tmin(T a, T b);
+template <typename T> __device__ __forceinline__ T tmax(T a, T b);
+template <> __device__ __forceinline__ double tmin<double>(double a, double b) { return fmin(a, b); }
+template <> __device__ __forceinline__ double tmax<double>(double a, double b) { return fmax(a, b); }
+template <> __device__ __forceinline__ float tmin<float>(float a, float b) { return fminf(a, b); }
+template <> __device__ __forceinline__ float tmax<float>(float a, float b) { return fmaxf(a, b); }
+template <typename T> __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
+__device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float tsqrt(float a) { return sqrtf(a); }
+
+// Primitive state (rho, v, p, B) from conserved (rho, m, E) and the six faces.
+template <typename T>
+__device__ __forceinline__ void prim(T rho, T mx, T my, T mz, T E, T bxl, T bxr, T byl, T byr, T bzl, T bzr,
+                                     T gamma, T W[8]) {
+  const T h = T(0.5);
+  T Bx = h * (bxl + bxr);
+  T By = h * (byl + byr);
+  T Bz = h * (bzl + bzr);
+  T vx = mx / rho;
+  T vy = my / rho;
+  T vz = mz / rho;
+  T ke = h * rho * (vx * vx + vy * vy + vz * vz);
+  T me = h * (Bx * Bx + By * By + Bz * Bz);
+  T p = (gamma - T(1)) * (E - ke - me);
+  W[RHO] = rho; W[VX] = vx; W[VY] = vy; W[VZ] = vz; W[PR] = p;
+  W[BX] = Bx; W[BY] = By; W[BZ] = Bz;
+}
+
+// Fast magnetosonic speed along the axis whose field component is bn.
+template <typename T>
+__device__ __forceinline__ T cfast(T gamma, T rho, T p, T bn, T bt1, T bt2) {
+  T a2 = gamma * p / rho;
+  T bb = (bn * bn + bt1 * bt1 + bt2 * bt2) / rho;
+  T ca2 = bn * bn / rho;
+  T s = a2 + bb;
+  T disc = s * s - T(4) * a2 * ca2;
+  if (disc < T(0)) disc = T(0);
+  return tsqrt(T(0.5) * (s + tsqrt(disc)));
+}
+
+// Sum over axes of |v_d| + c_f,d: the signal speed that sets the Courant step.
+template <typename T>
+__device__ __forceinline__ T signal_sum(const T W[8], T gamma) {
+  T cx = cfast(gamma, W[RHO], W[PR], W[BX], W[BY], W[BZ]);
+  T cy = cfast(gamma, W[RHO], W[PR], W[BY], W[BZ], W[BX]);
+  T cz = cfast(gamma, W[RHO], W[PR], W[BZ], W[BX], W[BY]);
+  return (tabs(W[VX]) + cx) + (tabs(W[VY]) + cy) + (tabs(W[VZ]) + cz);
+}
+
+// Monotonised-central limited slope.
+template <typename T>
+__device__ __forceinline__ T mc(T dl, T dr) {
+  if (dl * dr <= T(0)) return T(0);
+  T s = tmin(tmin(T(2) * tabs(dl), T(2) * tabs(dr)), T(0.5) * tabs(dl + dr));
+  return dl > T(0) ? s : -s;
+}
+
+// Hancock half-step predictor in primitive form with d/dx_d -> dW_d, h = dt/(2dx).
+template <typename T>
+__device__ __forceinline__ void predict(const T W[8], const T dX[8], const T dY[8], const T dZ[8], T gamma, T h,
+                                        T Ws[8]) {
+  T rho = W[RHO], vx = W[VX], vy = W[VY], vz = W[VZ], p = W[PR];
+  T Bx = W[BX], By = W[BY], Bz = W[BZ];
+  T divv = dX[VX] + dY[VY] + dZ[VZ];
+  T r_rho = -(vx * dX[RHO] + vy * dY[RHO] + vz * dZ[RHO]) - rho * divv;
+  T gpx = dX[PR] + (Bx * dX[BX] + By * dX[BY] + Bz * dX[BZ]);
+  T gpy = dY[PR] + (Bx * dY[BX] + By * dY[BY] + Bz * dY[BZ]);
+  T gpz = dZ[PR] + (Bx * dZ[BX] + By * dZ[BY] + Bz * dZ[BZ]);
+  T tx = Bx * dX[BX] + By * dY[BX] + Bz * dZ[BX];
+  T ty = Bx * dX[BY] + By * dY[BY] + Bz * dZ[BY];
+  T tz = Bx * dX[BZ] + By * dY[BZ] + Bz * dZ[BZ];
+  T r_vx = -(vx * dX[VX] + vy * dY[VX] + vz * dZ[VX]) - (gpx - tx) / rho;
+  T r_vy = -(vx * dX[VY] + vy * dY[VY] + vz * dZ[VY]) - (gpy - ty) / rho;
+  T r_vz = -(vx * dX[VZ] + vy * dY[VZ] + vz * dZ[VZ]) - (gpz - tz) / rho;
+  T r_p = -(vx * dX[PR] + vy * dY[PR] + vz * dZ[PR]) - gamma * p * divv;
+  T r_bx = (Bx * dX[VX] + By * dY[VX] + Bz * dZ[VX]) - (vx * dX[BX] + vy * dY[BX] + vz * dZ[BX]) - Bx * divv;
+  T r_by = (Bx * dX[VY] + By * dY[VY] + Bz * dZ[VY]) - (vx * dX[BY] + vy * dY[BY] + vz * dZ[BY]) - By * divv;
+  T r_bz = (Bx * dX[VZ] + By * dY[VZ] + Bz * dZ[VZ]) - (vx * dX[BZ] + vy * dY[BZ] + vz * dZ[BZ]) - Bz * divv;
+  Ws[RHO] = rho + h * r_rho;
+  Ws[VX] = vx + h * r_vx;
+  Ws[VY] = vy + h * r_vy;
+  Ws[VZ] = vz + h * r_vz;
+  Ws[PR] = p + h * r_p;
+  Ws[BX] = Bx + h * r_bx;
+  Ws[BY] = By + h * r_by;
+  Ws[BZ] = Bz + h * r_bz;
+}
+
+// HLL flux through a face with normal axis D (compile-time), Davis speeds.
+// WL/WR: lab-frame primitive states.  F[0..4]: lab-frame mass, momentum
+// x,y,z, energy fluxes.  SL, SR: the two signal speeds.
+template <typename T, int D>
+__device__ __forceinline__ void hll(const T WL[8], const T WR[8], T gamma, T F[5], T &SL, T &SR) {
+  constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
+  const T gm1 = gamma - T(1);
+  const T h = T(0.5);
+  T bn = h * (WL[BX + D] + WR[BX + D]);
+  T FL[5], FR[5], UL[5], UR[5], cL, cR, vnL, vnR;
+#pragma unroll
+  for (int side = 0; side < 2; side++) {
+    const T *W = side ? WR : WL;
+    T rho = W[RHO], p = W[PR];
+    T vn = W[VX + D], vt1 = W[VX + t1], vt2 = W[VX + t2];
+    T bt1 = W[BX + t1], bt2 = W[BX + t2];
+    T v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
+    T B2 = bn * bn + bt1 * bt1 + bt2 * bt2;
+    T E = p / gm1 + h * rho * v2 + h * B2;
+    T PT = p + h * B2;
+    T vB = vn * bn + vt1 * bt1 + vt2 * bt2;
+    T cf = cfast(gamma, rho, p, bn, bt1, bt2);
+    T *Us = side ? UR : UL;
+    T *Fs = side ? FR : FL;
+    Us[0] = rho; Us[1] = rho * vn; Us[2] = rho * vt1; Us[3] = rho * vt2; Us[4] = E;
+    Fs[0] = rho * vn;
+    Fs[1] = rho * vn * vn + PT - bn * bn;
+    Fs[2] = rho * vn * vt1 - bn * bt1;
+    Fs[3] = rho * vn * vt2 - bn * bt2;
+    Fs[4] = (E + PT) * vn - bn * vB;
+    if (side) { cR = cf; vnR = vn; } else { cL = cf; vnL = vn; }
+  }
+  SL = tmin(vnL - cL, vnR - cR);
+  SR = tmax(vnL + cL, vnR + cR);
+  T Fr[5];
+#pragma unroll
+  for (int q = 0; q < 5; q++) {
+    if (SL >= T(0)) Fr[q] = FL[q];
+    else if (SR <= T(0)) Fr[q] = FR[q];
+    else Fr[q] = (SR * FL[q] - SL * FR[q] + SL * SR * (UR[q] - UL[q])) / (SR - SL);
+  }
+  F[0] = Fr[0];
+  F[1 + D] = Fr[1];
+  F[1 + t1] = Fr[2];
+  F[1 + t2] = Fr[3];
+  F[4] = Fr[4];
+}
+
+// Upwind HLL edge EMF from the four corner values around an edge (LL: low
+// a and low b side, RL: high a / low b, LR: low a / high b, RR: high/high),
+// with ap/am = max(0, +-S) over the faces touching the edge.
+template <typename T>
+__device__ __forceinline__ T emf(T Ell, T Erl, T Elr, T Err, T Ba_ll, T Ba_rl, T Ba_lr, T Ba_rr, T Bb_ll, T Bb_rl,
+                                 T Bb_lr, T Bb_rr, T apa, T ama, T apb, T amb) {
+  const T h = T(0.5);
+  T BbL = h * (Bb_ll + Bb_lr);
+  T BbR = h * (Bb_rl + Bb_rr);
+  T BaL = h * (Ba_ll + Ba_rl);
+  T BaR = h * (Ba_lr + Ba_rr);
+  T num = apa * apb * Ell + ama * apb * Erl + apa * amb * Elr + ama * amb * Err;
+  T den = (apa + ama) * (apb + amb);
+  return num / den + apa * ama / (apa + ama) * (BbR - BbL) - apb * amb / (apb + amb) * (BaR - BaL);
+}
+
+}  // namespace dsp

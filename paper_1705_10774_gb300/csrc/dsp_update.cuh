@@ -1,0 +1,600 @@
+// dsp_update.cuh -- the fused per-patch update kernel.
+//
+// One work item is a tile of one ready patch: TX x TY columns of cells and a
+// run of tz planes along z.  The block marches through the planes; for each
+// plane it
+//   A  gathers the next plane of the padded tile (radius 2) from the patch's
+//      own newest slice and its neighbours' slices, interpolating linearly in
+//      time where a neighbour is ahead (DISPATCH I, Sec. 3 A), and converts to
+//      primitive variables;
+//   B  computes MC-limited slopes and the Hancock half-step predictor;
+//   C  computes HLL fluxes through the x- and y-faces of the plane and the
+//      z-faces below it;
+//   D  computes the upwind edge EMFs on the x- and y-edges below the plane and
+//      the in-plane part of the flux divergence;
+//   E  writes the conservative update of the plane below and the
+//      constrained-transport update of its faces into the patch's next slice
+//      (the oldest slice is overwritten, Sec. 3 A);
+//   F  computes the z-edge EMFs of the plane, the signal speed of the freshly
+//      written cells, and the values carried to the next plane.
+// Every intermediate lives in shared memory; HBM sees the gathered input and
+// the written output only.  The arithmetic per cell, face and edge is the
+// same sequence of operations as the oracle's, so the FP64 build (no FMA
+// contraction) reproduces it bit for bit.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dsp_internal.h"
+#include "dsp_physics.cuh"
+
+namespace dsp {
+
+template <int TX, int TY>
+struct Lay {
+  static constexpr int H2N = (TX + 4) * (TY + 4);
+  static constexpr int H1N = (TX + 2) * (TY + 2);
+  static constexpr int oW = 0;                 // [3 planes][8][H2N] primitive ring
+  static constexpr int oFB = oW + 24 * H2N;    // [3 planes][3][H2N] low faces ring
+  static constexpr int oWS = oFB + 9 * H2N;    // [8][H1N] predicted state W*
+  static constexpr int oDX = oWS + 8 * H1N;    // [8][H1N] slopes along x
+  static constexpr int oDY = oDX + 8 * H1N;
+  static constexpr int oDZ = oDY + 8 * H1N;
+  static constexpr int oZP = oDZ + 8 * H1N;    // [8][H1N] upper z-face state of the previous plane
+  static constexpr int oCX = oZP + 8 * H1N;    // [6][H1N] previous plane's +z corners for x-edges
+  static constexpr int oCY = oCX + 6 * H1N;    // [6][H1N] previous plane's +z corners for y-edges
+  static constexpr int oSX = oCY + 6 * H1N;    // [2 parity][2][H1N] x-face speeds
+  static constexpr int oSY = oSX + 4 * H1N;    // [2 parity][2][H1N] y-face speeds
+  static constexpr int oSZ = oSY + 4 * H1N;    // [2][H1N] z-face speeds
+  static constexpr int oFX = oSZ + 2 * H1N;    // [5][H1N] x-face fluxes of the plane
+  static constexpr int oFY = oFX + 5 * H1N;    // [5][H1N]
+  static constexpr int oDU = oFY + 5 * H1N;    // [2 parity][5][H1N] in-plane flux divergence
+  static constexpr int oFZ = oDU + 10 * H1N;   // [2 parity][5][H1N] z-face fluxes
+  static constexpr int oEX = oFZ + 10 * H1N;   // [2 parity][H1N] x-edge EMFs
+  static constexpr int oEY = oEX + 2 * H1N;    // [2 parity][H1N] y-edge EMFs
+  static constexpr int oEZ = oEY + 2 * H1N;    // [H1N] z-edge EMFs of the previous plane
+  static constexpr int oNBX = oEZ + H1N;       // [H1N] new x-faces of the updated plane
+  static constexpr int oNBY = oNBX + H1N;      // [H1N] new y-faces
+  static constexpr int oNBZ = oNBY + H1N;      // [2 parity][H1N] new z-faces
+  static constexpr int total = oNBZ + 2 * H1N;
+};
+
+__device__ __forceinline__ int off1(int x, int n) { return x < 0 ? 0 : (x >= n ? 2 : 1); }
+
+__device__ __forceinline__ void set_error(const DevCtx &c, int code, int P, long long cell) {
+  if (atomicCAS(&c.ctl[CTL_STATUS], 0, code) == 0) {
+    c.ctl[CTL_ERRP] = P;
+    c.ctl[CTL_ERRC] = (int)cell;
+  }
+}
+
+template <typename T, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT, 1) update_kernel(DevCtx c) {
+  static_assert(TX * TY <= NT, "one updated cell per thread");
+  using L = Lay<TX, TY>;
+  constexpr int H2N = L::H2N, H1N = L::H1N;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *sm = reinterpret_cast<T *>(smraw);
+  T *const Wr = sm + L::oW;
+  T *const FB = sm + L::oFB;
+  T *const Sws = sm + L::oWS;
+  T *const SdX = sm + L::oDX;
+  T *const SdY = sm + L::oDY;
+  T *const SdZ = sm + L::oDZ;
+  T *const ZP = sm + L::oZP;
+  T *const CX = sm + L::oCX;
+  T *const CY = sm + L::oCY;
+  T *const SX = sm + L::oSX;
+  T *const SY = sm + L::oSY;
+  T *const SZ = sm + L::oSZ;
+  T *const FX = sm + L::oFX;
+  T *const FY = sm + L::oFY;
+  T *const DU = sm + L::oDU;
+  T *const FZ = sm + L::oFZ;
+  T *const EX = sm + L::oEX;
+  T *const EY = sm + L::oEY;
+  T *const EZ = sm + L::oEZ;
+  T *const NBX = sm + L::oNBX;
+  T *const NBY = sm + L::oNBY;
+  T *const NBZ = sm + L::oNBZ;
+
+  __shared__ const T *srcA[27];
+  __shared__ const T *srcB[27];
+  __shared__ T wgt[27];
+  __shared__ double red[NT / 32];
+  __shared__ int s_fallback;
+
+  const int tid = threadIdx.x;
+  const int nx = c.nx, ny = c.ny, nz = c.nz;
+  const long long nc = c.nc, ofy = 5 * c.nc + c.nfx, ofz = 5 * c.nc + c.nfx + c.nfy, ofx = 5 * c.nc;
+  const T gamma = (T)c.gamma;
+  const T half = T(0.5);
+  const long long nwork = (long long)c.ctl[CTL_NREADY] * c.tiles;
+
+#define H2(i, j) (((j) + 2) * (TX + 4) + ((i) + 2))
+#define H1(i, j) (((j) + 1) * (TX + 2) + ((i) + 1))
+
+  for (long long w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int r = (int)(w / c.tiles), tile = (int)(w % c.tiles);
+    const int P = c.R[r];
+    const double dt = c.dtR[r];
+    const T hdt = (T)(0.5 * dt / c.dx);
+    const T dtdx = (T)(dt / c.dx);
+    const int tix = tile % c.ntx, tiy = (tile / c.ntx) % c.nty, tiz = tile / (c.ntx * c.nty);
+    const int x0 = tix * TX, y0 = tiy * TY, z0 = tiz * c.tz;
+    const int tx = min(TX, nx - x0), ty = min(TY, ny - y0), tz = min(c.tz, nz - z0);
+    const int Lp = c.latest[P];
+    const double tP = c.t_slot[(long long)P * c.ns + Lp];
+    T *const dst = (T *)c.slab + (long long)((Lp + 1) % c.ns) * c.slot_stride + (long long)P * c.patch_len;
+
+    // Which slices of each of the 27 neighbours (self at 13) supply time tP:
+    // an exact-time slice is copied, else the two newest are interpolated.
+    if (tid < 27) {
+      const int Q = c.nb27[(long long)P * 27 + tid];
+      const int Lq = c.latest[Q];
+      const double tq = c.t_slot[(long long)Q * c.ns + Lq];
+      const T *base = (const T *)c.slab + (long long)Q * c.patch_len;
+      const T *A;
+      const T *B = nullptr;
+      T wv = T(0);
+      if (tq == tP) {
+        A = base + (long long)Lq * c.slot_stride;
+      } else {
+        const int Pv = (Lq + c.ns - 1) % c.ns;
+        const double ta = c.t_slot[(long long)Q * c.ns + Pv];
+        if (ta == tP) {
+          A = base + (long long)Pv * c.slot_stride;
+        } else if (ta < tP && tP < tq) {
+          A = base + (long long)Pv * c.slot_stride;
+          B = base + (long long)Lq * c.slot_stride;
+          wv = (T)((tP - ta) / (tq - ta));
+        } else {
+          A = base + (long long)Lq * c.slot_stride;
+          set_error(c, DSP_ERR_BRACKET, P, -1);
+        }
+      }
+      srcA[tid] = A;
+      srcB[tid] = B;
+      wgt[tid] = wv;
+    }
+    if (tid == 0) s_fallback = 0;
+    __syncthreads();
+    const T *const own = srcA[13];
+
+    auto val = [&](int o, long long idx) -> T {
+      T a = srcA[o][idx];
+      const T *B = srcB[o];
+      if (B) {
+        T b = B[idx];
+        a = a + wgt[o] * (b - a);
+      }
+      return a;
+    };
+    // Cell-centred component q of patch-local cell (x,y,z), |offset| <= 2.
+    auto cellv = [&](int x, int y, int z, long long q) -> T {
+      const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
+      const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
+      return val((oz * 3 + oy) * 3 + ox, q * nc + ((long long)lz * ny + ly) * nx + lx);
+    };
+    // Face below cell (x,y,z) along each axis: the patch's own face when it
+    // lies on one of its interior cells, else the face of the patch that owns
+    // cell (x,y,z).
+    auto facex = [&](int x, int y, int z) -> T {
+      const bool ownf = x >= 0 && x <= nx && y >= 0 && y < ny && z >= 0 && z < nz;
+      const int ox = ownf ? 1 : off1(x, nx), oy = ownf ? 1 : off1(y, ny), oz = ownf ? 1 : off1(z, nz);
+      const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
+      return val((oz * 3 + oy) * 3 + ox, ofx + ((long long)lz * ny + ly) * (nx + 1) + lx);
+    };
+    auto facey = [&](int x, int y, int z) -> T {
+      const bool ownf = x >= 0 && x < nx && y >= 0 && y <= ny && z >= 0 && z < nz;
+      const int ox = ownf ? 1 : off1(x, nx), oy = ownf ? 1 : off1(y, ny), oz = ownf ? 1 : off1(z, nz);
+      const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
+      return val((oz * 3 + oy) * 3 + ox, ofy + ((long long)lz * (ny + 1) + ly) * nx + lx);
+    };
+    auto facez = [&](int x, int y, int z) -> T {
+      const bool ownf = x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z <= nz;
+      const int ox = ownf ? 1 : off1(x, nx), oy = ownf ? 1 : off1(y, ny), oz = ownf ? 1 : off1(z, nz);
+      const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
+      return val((oz * 3 + oy) * 3 + ox, ofz + ((long long)lz * ny + ly) * nx + lx);
+    };
+
+    // ---- A: gather plane q of the radius-2 padded tile, to primitives
+    auto load_plane = [&](int q) {
+      const int rs = (q - z0 + 3) % 3;
+      T *Wq = Wr + rs * 8 * H2N;
+      T *Fq = FB + rs * 3 * H2N;
+      const int nxx = tx + 4, ncell = (tx + 4) * (ty + 4);
+      for (int ci = tid; ci < ncell; ci += NT) {
+        const int i = ci % nxx - 2, j = ci / nxx - 2;
+        const int x = x0 + i, y = y0 + j;
+        const T u0 = cellv(x, y, q, 0), u1 = cellv(x, y, q, 1), u2 = cellv(x, y, q, 2);
+        const T u3 = cellv(x, y, q, 3), u4 = cellv(x, y, q, 4);
+        const T bxl = facex(x, y, q), bxr = facex(x + 1, y, q);
+        const T byl = facey(x, y, q), byr = facey(x, y + 1, q);
+        const T bzl = facez(x, y, q), bzr = facez(x, y, q + 1);
+        T Wt[8];
+        prim(u0, u1, u2, u3, u4, bxl, bxr, byl, byr, bzl, bzr, gamma, Wt);
+        const int h = H2(i, j);
+#pragma unroll
+        for (int k = 0; k < 8; k++) Wq[k * H2N + h] = Wt[k];
+        Fq[h] = bxl;
+        Fq[H2N + h] = byl;
+        Fq[2 * H2N + h] = bzl;
+      }
+    };
+
+    load_plane(z0 - 2);
+    load_plane(z0 - 1);
+    __syncthreads();
+
+    T smax_t = T(0);
+    T unew[5];
+    for (int it = 0; it <= tz + 1; it++) {
+      const int p = z0 - 1 + it;
+      const int par = it & 1;
+      T *const SXc = SX + par * 2 * H1N, *const SXp = SX + (par ^ 1) * 2 * H1N;
+      T *const SYc = SY + par * 2 * H1N, *const SYp = SY + (par ^ 1) * 2 * H1N;
+      T *const FZc = FZ + par * 5 * H1N, *const FZp = FZ + (par ^ 1) * 5 * H1N;
+      T *const DUc = DU + par * 5 * H1N, *const DUp = DU + (par ^ 1) * 5 * H1N;
+      T *const EXc = EX + par * H1N, *const EXp = EX + (par ^ 1) * H1N;
+      T *const EYc = EY + par * H1N, *const EYp = EY + (par ^ 1) * H1N;
+      T *const NBZc = NBZ + par * H1N, *const NBZp = NBZ + (par ^ 1) * H1N;
+
+      // ---- A
+      load_plane(p + 1);
+      __syncthreads();
+
+      // ---- B: slopes and predictor on the H1 region of plane p
+      {
+        const int rm = (p - 1 - z0 + 3) % 3, r0 = (p - z0 + 3) % 3, rp = (p + 1 - z0 + 3) % 3;
+        const T *Wm = Wr + rm * 8 * H2N, *W0 = Wr + r0 * 8 * H2N, *Wp = Wr + rp * 8 * H2N;
+        const T *F0 = FB + r0 * 3 * H2N, *Fp = FB + rp * 3 * H2N;
+        const int nxx = tx + 2, ncell = (tx + 2) * (ty + 2);
+        for (int ci = tid; ci < ncell; ci += NT) {
+          const int i = ci % nxx - 1, j = ci / nxx - 1;
+          const int h = H2(i, j);
+          T w8[8], dX[8], dY[8], dZ[8], ws[8];
+#pragma unroll
+          for (int k = 0; k < 8; k++) w8[k] = W0[k * H2N + h];
+#pragma unroll
+          for (int k = 0; k < 8; k++) {
+            if (k == BX) dX[k] = F0[H2(i + 1, j)] - F0[h];
+            else dX[k] = mc(w8[k] - W0[k * H2N + H2(i - 1, j)], W0[k * H2N + H2(i + 1, j)] - w8[k]);
+            if (k == BY) dY[k] = F0[H2N + H2(i, j + 1)] - F0[H2N + h];
+            else dY[k] = mc(w8[k] - W0[k * H2N + H2(i, j - 1)], W0[k * H2N + H2(i, j + 1)] - w8[k]);
+            if (k == BZ) dZ[k] = Fp[2 * H2N + h] - F0[2 * H2N + h];
+            else dZ[k] = mc(w8[k] - Wm[k * H2N + h], Wp[k * H2N + h] - w8[k]);
+          }
+          predict(w8, dX, dY, dZ, gamma, hdt, ws);
+          bool bad = false;
+#pragma unroll
+          for (int d = 0; d < 3; d++) {
+            const T *d3 = d == 0 ? dX : d == 1 ? dY : dZ;
+            const T rp_ = ws[RHO] + half * d3[RHO], rm_ = ws[RHO] - half * d3[RHO];
+            const T pp_ = ws[PR] + half * d3[PR], pm_ = ws[PR] - half * d3[PR];
+            if (!(rp_ > T(0)) || !(rm_ > T(0)) || !(pp_ > T(0)) || !(pm_ > T(0))) bad = true;
+          }
+          if (bad) {
+            atomicAdd(&s_fallback, 1);
+#pragma unroll
+            for (int k = 0; k < 8; k++) { dX[k] = T(0); dY[k] = T(0); dZ[k] = T(0); ws[k] = w8[k]; }
+          }
+          const int g = H1(i, j);
+#pragma unroll
+          for (int k = 0; k < 8; k++) {
+            Sws[k * H1N + g] = ws[k];
+            SdX[k * H1N + g] = dX[k];
+            SdY[k * H1N + g] = dY[k];
+            SdZ[k * H1N + g] = dZ[k];
+          }
+        }
+      }
+      __syncthreads();
+
+      // ---- C: face fluxes
+      {
+        // x-faces (i-1/2, j) of plane p, i in [0,tx], j in [-1,ty]
+        const int nxx = tx + 1, n1 = (tx + 1) * (ty + 2);
+        for (int ci = tid; ci < n1; ci += NT) {
+          const int i = ci % nxx, j = ci / nxx - 1;
+          const int hl = H1(i - 1, j), hr = H1(i, j);
+          T WL[8], WR[8], F[5], SL, SR;
+#pragma unroll
+          for (int k = 0; k < 8; k++) {
+            WL[k] = Sws[k * H1N + hl] + half * SdX[k * H1N + hl];
+            WR[k] = Sws[k * H1N + hr] - half * SdX[k * H1N + hr];
+          }
+          hll<T, 0>(WL, WR, gamma, F, SL, SR);
+          SXc[hr] = SL;
+          SXc[H1N + hr] = SR;
+          if (j >= 0 && j < ty) {
+#pragma unroll
+            for (int k = 0; k < 5; k++) FX[k * H1N + hr] = F[k];
+          }
+        }
+        // y-faces (i, j-1/2) of plane p, i in [-1,tx], j in [0,ty]
+        const int nxy = tx + 2, n2 = (tx + 2) * (ty + 1);
+        for (int ci = tid; ci < n2; ci += NT) {
+          const int i = ci % nxy - 1, j = ci / nxy;
+          const int hl = H1(i, j - 1), hr = H1(i, j);
+          T WL[8], WR[8], F[5], SL, SR;
+#pragma unroll
+          for (int k = 0; k < 8; k++) {
+            WL[k] = Sws[k * H1N + hl] + half * SdY[k * H1N + hl];
+            WR[k] = Sws[k * H1N + hr] - half * SdY[k * H1N + hr];
+          }
+          hll<T, 1>(WL, WR, gamma, F, SL, SR);
+          SYc[hr] = SL;
+          SYc[H1N + hr] = SR;
+          if (i >= 0 && i < tx) {
+#pragma unroll
+            for (int k = 0; k < 5; k++) FY[k * H1N + hr] = F[k];
+          }
+        }
+        // z-faces (i, j, p-1/2) on the H1 region
+        if (it > 0) {
+          const int nxz = tx + 2, n3 = (tx + 2) * (ty + 2);
+          for (int ci = tid; ci < n3; ci += NT) {
+            const int i = ci % nxz - 1, j = ci / nxz - 1;
+            const int h = H1(i, j);
+            T WL[8], WR[8], F[5], SL, SR;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+              WL[k] = ZP[k * H1N + h];
+              WR[k] = Sws[k * H1N + h] - half * SdZ[k * H1N + h];
+            }
+            hll<T, 2>(WL, WR, gamma, F, SL, SR);
+            SZ[h] = SL;
+            SZ[H1N + h] = SR;
+            if (i >= 0 && i < tx && j >= 0 && j < ty) {
+#pragma unroll
+              for (int k = 0; k < 5; k++) FZc[k * H1N + h] = F[k];
+            }
+          }
+        }
+      }
+      __syncthreads();
+
+      // ---- D: x- and y-edge EMFs at p-1/2, in-plane divergence of plane p
+      if (it > 0) {
+        // x-edges (i, j-1/2, p-1/2): i in [0,tx), j in [0,ty]; a = y, b = z
+        const int n1 = tx * (ty + 1);
+        for (int ci = tid; ci < n1; ci += NT) {
+          const int i = ci % tx, j = ci / tx;
+          const int hm = H1(i, j - 1), h0 = H1(i, j);
+          const T Ell = CX[0 * H1N + hm], Ba_ll = CX[1 * H1N + hm], Bb_ll = CX[2 * H1N + hm];
+          const T Erl = CX[3 * H1N + h0], Ba_rl = CX[4 * H1N + h0], Bb_rl = CX[5 * H1N + h0];
+          const T lr_vy = (Sws[VY * H1N + hm] + half * SdY[VY * H1N + hm]) - half * SdZ[VY * H1N + hm];
+          const T lr_vz = (Sws[VZ * H1N + hm] + half * SdY[VZ * H1N + hm]) - half * SdZ[VZ * H1N + hm];
+          const T lr_by = (Sws[BY * H1N + hm] + half * SdY[BY * H1N + hm]) - half * SdZ[BY * H1N + hm];
+          const T lr_bz = (Sws[BZ * H1N + hm] + half * SdY[BZ * H1N + hm]) - half * SdZ[BZ * H1N + hm];
+          const T rr_vy = (Sws[VY * H1N + h0] - half * SdY[VY * H1N + h0]) - half * SdZ[VY * H1N + h0];
+          const T rr_vz = (Sws[VZ * H1N + h0] - half * SdY[VZ * H1N + h0]) - half * SdZ[VZ * H1N + h0];
+          const T rr_by = (Sws[BY * H1N + h0] - half * SdY[BY * H1N + h0]) - half * SdZ[BY * H1N + h0];
+          const T rr_bz = (Sws[BZ * H1N + h0] - half * SdY[BZ * H1N + h0]) - half * SdZ[BZ * H1N + h0];
+          const T Elr = lr_vz * lr_by - lr_vy * lr_bz;
+          const T Err = rr_vz * rr_by - rr_vy * rr_bz;
+          const T apa = tmax(T(0), tmax(SYp[H1N + h0], SYc[H1N + h0]));
+          const T ama = tmax(T(0), tmax(-SYp[h0], -SYc[h0]));
+          const T apb = tmax(T(0), tmax(SZ[H1N + hm], SZ[H1N + h0]));
+          const T amb = tmax(T(0), tmax(-SZ[hm], -SZ[h0]));
+          EXc[h0] = emf(Ell, Erl, Elr, Err, Ba_ll, Ba_rl, lr_by, rr_by, Bb_ll, Bb_rl, lr_bz, rr_bz, apa, ama, apb, amb);
+        }
+        // y-edges (i-1/2, j, p-1/2): i in [0,tx], j in [0,ty); a = z, b = x
+        const int nxx = tx + 1, n2 = (tx + 1) * ty;
+        for (int ci = tid; ci < n2; ci += NT) {
+          const int i = ci % nxx, j = ci / nxx;
+          const int hm = H1(i - 1, j), h0 = H1(i, j);
+          const T Ell = CY[0 * H1N + hm], Ba_ll = CY[1 * H1N + hm], Bb_ll = CY[2 * H1N + hm];
+          const T Elr = CY[3 * H1N + h0], Ba_lr = CY[4 * H1N + h0], Bb_lr = CY[5 * H1N + h0];
+          const T rl_vz = (Sws[VZ * H1N + hm] - half * SdZ[VZ * H1N + hm]) + half * SdX[VZ * H1N + hm];
+          const T rl_vx = (Sws[VX * H1N + hm] - half * SdZ[VX * H1N + hm]) + half * SdX[VX * H1N + hm];
+          const T rl_bz = (Sws[BZ * H1N + hm] - half * SdZ[BZ * H1N + hm]) + half * SdX[BZ * H1N + hm];
+          const T rl_bx = (Sws[BX * H1N + hm] - half * SdZ[BX * H1N + hm]) + half * SdX[BX * H1N + hm];
+          const T rr_vz = (Sws[VZ * H1N + h0] - half * SdZ[VZ * H1N + h0]) - half * SdX[VZ * H1N + h0];
+          const T rr_vx = (Sws[VX * H1N + h0] - half * SdZ[VX * H1N + h0]) - half * SdX[VX * H1N + h0];
+          const T rr_bz = (Sws[BZ * H1N + h0] - half * SdZ[BZ * H1N + h0]) - half * SdX[BZ * H1N + h0];
+          const T rr_bx = (Sws[BX * H1N + h0] - half * SdZ[BX * H1N + h0]) - half * SdX[BX * H1N + h0];
+          const T Erl = rl_vx * rl_bz - rl_vz * rl_bx;
+          const T Err = rr_vx * rr_bz - rr_vz * rr_bx;
+          const T apa = tmax(T(0), tmax(SZ[H1N + hm], SZ[H1N + h0]));
+          const T ama = tmax(T(0), tmax(-SZ[hm], -SZ[h0]));
+          const T apb = tmax(T(0), tmax(SXp[H1N + h0], SXc[H1N + h0]));
+          const T amb = tmax(T(0), tmax(-SXp[h0], -SXc[h0]));
+          EYc[h0] = emf(Ell, Erl, Elr, Err, Ba_ll, rl_bz, Ba_lr, rr_bz, Bb_ll, rl_bx, Bb_lr, rr_bx, apa, ama, apb, amb);
+        }
+        if (p < z0 + tz) {
+          const int n3 = tx * ty;
+          for (int ci = tid; ci < n3; ci += NT) {
+            const int i = ci % tx, j = ci / tx;
+            const int h = H1(i, j), hx = H1(i + 1, j), hy = H1(i, j + 1);
+#pragma unroll
+            for (int k = 0; k < 5; k++)
+              DUc[k * H1N + h] = (FX[k * H1N + hx] - FX[k * H1N + h]) + (FY[k * H1N + hy] - FY[k * H1N + h]);
+          }
+        }
+      }
+      __syncthreads();
+
+      // ---- E: update plane p-1 and the z-faces at p-1/2
+      const bool upd = it >= 2;
+      if (upd && tid < tx * ty) {
+        const int i = tid % tx, j = tid / tx, h = H1(i, j);
+        const long long ci = ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i);
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+          const T fz = FZc[k * H1N + h] - FZp[k * H1N + h];
+          unew[k] = own[k * nc + ci] - dtdx * (DUp[k * H1N + h] + fz);
+          dst[k * nc + ci] = unew[k];
+        }
+      }
+      if (upd) {
+        const int k = p - 1;
+        const int nxx = tx + 1, n1 = (tx + 1) * ty;
+        for (int ci = tid; ci < n1; ci += NT) {
+          const int i = ci % nxx, j = ci / nxx, h = H1(i, j);
+          const long long id = ((long long)k * ny + (y0 + j)) * (nx + 1) + (x0 + i);
+          const T b = own[ofx + id] - dtdx * ((EZ[H1(i, j + 1)] - EZ[h]) - (EYc[h] - EYp[h]));
+          NBX[h] = b;
+          dst[ofx + id] = b;
+        }
+        const int n2 = tx * (ty + 1);
+        for (int ci = tid; ci < n2; ci += NT) {
+          const int i = ci % tx, j = ci / tx, h = H1(i, j);
+          const long long id = ((long long)k * (ny + 1) + (y0 + j)) * nx + (x0 + i);
+          const T b = own[ofy + id] - dtdx * ((EXc[h] - EXp[h]) - (EZ[H1(i + 1, j)] - EZ[h]));
+          NBY[h] = b;
+          dst[ofy + id] = b;
+        }
+      }
+      if (it >= 1) {
+        const int n3 = tx * ty;
+        for (int ci = tid; ci < n3; ci += NT) {
+          const int i = ci % tx, j = ci / tx, h = H1(i, j);
+          const long long id = ((long long)p * ny + (y0 + j)) * nx + (x0 + i);
+          const T b = own[ofz + id] - dtdx * ((EYc[H1(i + 1, j)] - EYc[h]) - (EXc[H1(i, j + 1)] - EXc[h]));
+          NBZc[h] = b;
+          dst[ofz + id] = b;
+        }
+      }
+      __syncthreads();
+
+      // ---- F: signal speed of plane p-1, z-edge EMFs of plane p, carried values
+      if (upd && tid < tx * ty) {
+        const int i = tid % tx, j = tid / tx, h = H1(i, j);
+        T Wn[8];
+        prim(unew[0], unew[1], unew[2], unew[3], unew[4], NBX[h], NBX[H1(i + 1, j)], NBY[h], NBY[H1(i, j + 1)],
+             NBZp[h], NBZc[h], gamma, Wn);
+        if (!(Wn[RHO] > T(0)) || !(Wn[PR] > T(0)))
+          set_error(c, DSP_ERR_UNPHYSICAL, P, ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i));
+        smax_t = tmax(smax_t, signal_sum(Wn, gamma));
+      }
+      if (p >= z0 && p < z0 + tz) {
+        // z-edges (i-1/2, j-1/2, p): i in [0,tx], j in [0,ty]; a = x, b = y
+        const int nxx = tx + 1, n1 = (tx + 1) * (ty + 1);
+        for (int ci = tid; ci < n1; ci += NT) {
+          const int i = ci % nxx, j = ci / nxx;
+          const int hll_ = H1(i - 1, j - 1), hrl = H1(i, j - 1), hlr = H1(i - 1, j), hrr = H1(i, j);
+          const T ll_vx = (Sws[VX * H1N + hll_] + half * SdX[VX * H1N + hll_]) + half * SdY[VX * H1N + hll_];
+          const T ll_vy = (Sws[VY * H1N + hll_] + half * SdX[VY * H1N + hll_]) + half * SdY[VY * H1N + hll_];
+          const T ll_bx = (Sws[BX * H1N + hll_] + half * SdX[BX * H1N + hll_]) + half * SdY[BX * H1N + hll_];
+          const T ll_by = (Sws[BY * H1N + hll_] + half * SdX[BY * H1N + hll_]) + half * SdY[BY * H1N + hll_];
+          const T rl_vx = (Sws[VX * H1N + hrl] - half * SdX[VX * H1N + hrl]) + half * SdY[VX * H1N + hrl];
+          const T rl_vy = (Sws[VY * H1N + hrl] - half * SdX[VY * H1N + hrl]) + half * SdY[VY * H1N + hrl];
+          const T rl_bx = (Sws[BX * H1N + hrl] - half * SdX[BX * H1N + hrl]) + half * SdY[BX * H1N + hrl];
+          const T rl_by = (Sws[BY * H1N + hrl] - half * SdX[BY * H1N + hrl]) + half * SdY[BY * H1N + hrl];
+          const T lr_vx = (Sws[VX * H1N + hlr] + half * SdX[VX * H1N + hlr]) - half * SdY[VX * H1N + hlr];
+          const T lr_vy = (Sws[VY * H1N + hlr] + half * SdX[VY * H1N + hlr]) - half * SdY[VY * H1N + hlr];
+          const T lr_bx = (Sws[BX * H1N + hlr] + half * SdX[BX * H1N + hlr]) - half * SdY[BX * H1N + hlr];
+          const T lr_by = (Sws[BY * H1N + hlr] + half * SdX[BY * H1N + hlr]) - half * SdY[BY * H1N + hlr];
+          const T rr_vx = (Sws[VX * H1N + hrr] - half * SdX[VX * H1N + hrr]) - half * SdY[VX * H1N + hrr];
+          const T rr_vy = (Sws[VY * H1N + hrr] - half * SdX[VY * H1N + hrr]) - half * SdY[VY * H1N + hrr];
+          const T rr_bx = (Sws[BX * H1N + hrr] - half * SdX[BX * H1N + hrr]) - half * SdY[BX * H1N + hrr];
+          const T rr_by = (Sws[BY * H1N + hrr] - half * SdX[BY * H1N + hrr]) - half * SdY[BY * H1N + hrr];
+          const T Ell = ll_vy * ll_bx - ll_vx * ll_by;
+          const T Erl = rl_vy * rl_bx - rl_vx * rl_by;
+          const T Elr = lr_vy * lr_bx - lr_vx * lr_by;
+          const T Err = rr_vy * rr_bx - rr_vx * rr_by;
+          const T apa = tmax(T(0), tmax(SXc[H1N + hrl], SXc[H1N + hrr]));
+          const T ama = tmax(T(0), tmax(-SXc[hrl], -SXc[hrr]));
+          const T apb = tmax(T(0), tmax(SYc[H1N + hlr], SYc[H1N + hrr]));
+          const T amb = tmax(T(0), tmax(-SYc[hlr], -SYc[hrr]));
+          EZ[hrr] = emf(Ell, Erl, Elr, Err, ll_bx, rl_bx, lr_bx, rr_bx, ll_by, rl_by, lr_by, rr_by, apa, ama, apb, amb);
+        }
+      }
+      {
+        // values of plane p carried to the next plane: its upper z-face
+        // state and its +z corner values for the x- and y-edges above it
+        const int nxx = tx + 2, n2 = (tx + 2) * (ty + 2);
+        for (int ci = tid; ci < n2; ci += NT) {
+          const int i = ci % nxx - 1, j = ci / nxx - 1, h = H1(i, j);
+#pragma unroll
+          for (int k = 0; k < 8; k++) ZP[k * H1N + h] = Sws[k * H1N + h] + half * SdZ[k * H1N + h];
+          {  // x-edges: a = y, b = z; corners (+y,+z) and (-y,+z)
+            const T py_vy = (Sws[VY * H1N + h] + half * SdY[VY * H1N + h]) + half * SdZ[VY * H1N + h];
+            const T py_vz = (Sws[VZ * H1N + h] + half * SdY[VZ * H1N + h]) + half * SdZ[VZ * H1N + h];
+            const T py_by = (Sws[BY * H1N + h] + half * SdY[BY * H1N + h]) + half * SdZ[BY * H1N + h];
+            const T py_bz = (Sws[BZ * H1N + h] + half * SdY[BZ * H1N + h]) + half * SdZ[BZ * H1N + h];
+            const T my_vy = (Sws[VY * H1N + h] - half * SdY[VY * H1N + h]) + half * SdZ[VY * H1N + h];
+            const T my_vz = (Sws[VZ * H1N + h] - half * SdY[VZ * H1N + h]) + half * SdZ[VZ * H1N + h];
+            const T my_by = (Sws[BY * H1N + h] - half * SdY[BY * H1N + h]) + half * SdZ[BY * H1N + h];
+            const T my_bz = (Sws[BZ * H1N + h] - half * SdY[BZ * H1N + h]) + half * SdZ[BZ * H1N + h];
+            CX[0 * H1N + h] = py_vz * py_by - py_vy * py_bz;
+            CX[1 * H1N + h] = py_by;
+            CX[2 * H1N + h] = py_bz;
+            CX[3 * H1N + h] = my_vz * my_by - my_vy * my_bz;
+            CX[4 * H1N + h] = my_by;
+            CX[5 * H1N + h] = my_bz;
+          }
+          {  // y-edges: a = z, b = x; corners (+z,+x) and (+z,-x)
+            const T px_vz = (Sws[VZ * H1N + h] + half * SdZ[VZ * H1N + h]) + half * SdX[VZ * H1N + h];
+            const T px_vx = (Sws[VX * H1N + h] + half * SdZ[VX * H1N + h]) + half * SdX[VX * H1N + h];
+            const T px_bz = (Sws[BZ * H1N + h] + half * SdZ[BZ * H1N + h]) + half * SdX[BZ * H1N + h];
+            const T px_bx = (Sws[BX * H1N + h] + half * SdZ[BX * H1N + h]) + half * SdX[BX * H1N + h];
+            const T mx_vz = (Sws[VZ * H1N + h] + half * SdZ[VZ * H1N + h]) - half * SdX[VZ * H1N + h];
+            const T mx_vx = (Sws[VX * H1N + h] + half * SdZ[VX * H1N + h]) - half * SdX[VX * H1N + h];
+            const T mx_bz = (Sws[BZ * H1N + h] + half * SdZ[BZ * H1N + h]) - half * SdX[BZ * H1N + h];
+            const T mx_bx = (Sws[BX * H1N + h] + half * SdZ[BX * H1N + h]) - half * SdX[BX * H1N + h];
+            CY[0 * H1N + h] = px_vx * px_bz - px_vz * px_bx;
+            CY[1 * H1N + h] = px_bz;
+            CY[2 * H1N + h] = px_bx;
+            CY[3 * H1N + h] = mx_vx * mx_bz - mx_vz * mx_bx;
+            CY[4 * H1N + h] = mx_bz;
+            CY[5 * H1N + h] = mx_bx;
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    // signal speed of the new slice: block max, then the patch max
+    {
+      double v = (double)smax_t;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if ((tid & 31) == 0) red[tid >> 5] = v;
+      __syncthreads();
+      if (tid < 32) {
+        double u = tid < NT / 32 ? red[tid] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u = fmax(u, __shfl_xor_sync(0xffffffffu, u, o));
+        if (tid == 0) {
+          atomicMax(&c.smax_new[P], (unsigned long long)__double_as_longlong(u));
+          if (s_fallback) atomicAdd((unsigned long long *)&c.cnt[CNT_FALLBACKS], (unsigned long long)s_fallback);
+        }
+      }
+      __syncthreads();
+    }
+  }
+#undef H2
+#undef H1
+}
+
+template <typename T, int TX, int TY, int NT>
+int launch_update(const DevCtx &c, int grid, void *stream) {
+  const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
+  static bool configured = false;
+  if (!configured) {
+    if (cudaFuncSetAttribute(update_kernel<T, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return DSP_ERR_CUDA;
+    configured = true;
+  }
+  update_kernel<T, TX, TY, NT><<<grid, NT, smem, (cudaStream_t)stream>>>(c);
+  return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
+}
+
+template <typename T, int TX, int TY, int NT>
+int update_grid(const DevCtx &c) {
+  const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
+  cudaFuncSetAttribute(update_kernel<T, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, update_kernel<T, TX, TY, NT>, NT, smem);
+  if (per < 1) per = 1;
+  long long maxwork = (long long)c.np * c.tiles;
+  long long g = (long long)nsm * per;
+  return (int)(g < maxwork ? g : maxwork);
+}
+
+}  // namespace dsp

@@ -1,0 +1,234 @@
+"""Thin ctypes binding of libdispatch_gpu.so (include/dispatch.h).
+
+Argument marshalling only: every step of the update runs in the library's
+CUDA kernels.  The functions keep the C names; ``Dispatch`` bundles a context
+handle with numpy (host) or torch (device) array marshalling.  If the library
+cannot be loaded, every call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+DSP_OK = 0
+DSP_ERR_INVALID_ARG = -1
+DSP_ERR_OOM = -2
+DSP_ERR_CUDA = -3
+DSP_ERR_UNPHYSICAL = -4
+DSP_ERR_TIMEOUT = -5
+DSP_ERR_DEADLOCK = -6
+DSP_ERR_SCHEDULE_OVERFLOW = -7
+DSP_ERR_UNSUPPORTED = -8
+DSP_ERR_BRACKET = -9
+
+ERRORS = {v: k for k, v in globals().items() if k.startswith("DSP_ERR_")}
+
+EXPORTS = ["dsp_create", "dsp_set_state", "dsp_advance", "dsp_get_state", "dsp_get_times",
+           "dsp_get_schedule", "dsp_diagnostics", "dsp_save", "dsp_load", "dsp_last_error",
+           "dsp_destroy"]
+
+
+class dsp_patch_desc(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("lo", ctypes.c_int64 * 3)]
+
+
+class dsp_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("t0", ctypes.c_double),
+                ("dt_max", ctypes.c_double), ("grace", ctypes.c_double),
+                ("box_lo", ctypes.c_double * 3), ("box_len", ctypes.c_double * 3),
+                ("base_cells", ctypes.c_int32 * 3),
+                ("nguard", ctypes.c_int32), ("nslices", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("time_mode", ctypes.c_int32), ("dt_pow2", ctypes.c_int32), ("dispatcher", ctypes.c_int32),
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
+                ("sched_capacity", ctypes.c_int64), ("timing", ctypes.c_int32)]
+
+
+class dsp_stats(ctypes.Structure):
+    _fields_ = [("patch_updates", ctypes.c_int64), ("cell_updates", ctypes.c_int64),
+                ("sweeps", ctypes.c_int64), ("fallbacks", ctypes.c_int64),
+                ("t_min", ctypes.c_double), ("t_max", ctypes.c_double), ("status", ctypes.c_int32),
+                ("kernel_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("plan_launches", ctypes.c_int64)]
+
+
+class dsp_sched_entry(ctypes.Structure):
+    _fields_ = [("patch", ctypes.c_int64), ("t_start", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
+class dsp_diag(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("mom", ctypes.c_double * 3), ("energy", ctypes.c_double),
+                ("bmean", ctypes.c_double * 3), ("max_divb", ctypes.c_double), ("max_b", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+VP = ctypes.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it in-tree with nvcc if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libdispatch_gpu.so is not built (%s); run paper_1705_10774_gb300.build" % path)
+        L = ctypes.CDLL(path)
+        L.dsp_create.argtypes = [ctypes.POINTER(dsp_patch_desc), ctypes.c_int32, ctypes.POINTER(dsp_params), VP,
+                                 ctypes.POINTER(VP)]
+        L.dsp_set_state.argtypes = [VP, ctypes.c_int32, ctypes.c_int32, VP, VP, VP, VP, ctypes.c_int32, ctypes.c_int32]
+        L.dsp_advance.argtypes = [VP, ctypes.c_double, ctypes.c_int64, ctypes.POINTER(dsp_stats)]
+        L.dsp_get_state.argtypes = [VP, ctypes.c_int32, ctypes.c_int32, VP, VP, VP, VP, ctypes.c_int32, ctypes.c_int32]
+        L.dsp_get_times.argtypes = [VP, VP, VP]
+        L.dsp_get_schedule.argtypes = [VP, VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+        L.dsp_diagnostics.argtypes = [VP, ctypes.POINTER(dsp_diag)]
+        L.dsp_save.argtypes = [VP, VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+        L.dsp_load.argtypes = [VP, VP, ctypes.c_size_t]
+        L.dsp_last_error.argtypes = [VP]
+        L.dsp_last_error.restype = ctypes.c_char_p
+        L.dsp_destroy.argtypes = [VP]
+        L.dsp_destroy.restype = None
+        for name in EXPORTS:
+            if name not in ("dsp_last_error", "dsp_destroy"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+class DispatchError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "DSP_ERR"), code, msg))
+        self.code = code
+
+
+def _addr(a):
+    """Device or host address of a torch tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr()), bool(a.is_cuda), (0 if str(a.dtype).endswith("float64") else 1)
+    a = np.asarray(a)
+    return a.ctypes.data_as(ctypes.c_void_p), False, (0 if a.dtype == np.float64 else 1)
+
+
+class Dispatch:
+    """A context of patches on one periodic level (one GPU)."""
+
+    def __init__(self, n, lo, *, gamma, cfl, base_cells, box_len=(1.0, 1.0, 1.0), t0=0.0, dt_max=0.0,
+                 nguard=3, nslices=3, precision=0, time_mode=0, dispatcher=1, tile_z=0,
+                 sched_capacity=0, timing=0, stream=None):
+        L = load()
+        n = np.asarray(n, dtype=np.int64).reshape(-1, 3)
+        lo = np.asarray(lo, dtype=np.int64).reshape(-1, 3)
+        self.np = n.shape[0]
+        descs = (dsp_patch_desc * self.np)()
+        for i in range(self.np):
+            descs[i].level = 0
+            for d in range(3):
+                descs[i].n[d] = int(n[i, d])
+                descs[i].lo[d] = int(lo[i, d])
+        p = dsp_params()
+        p.gamma, p.cfl, p.t0, p.dt_max, p.grace = gamma, cfl, t0, dt_max, 0.0
+        for d in range(3):
+            p.box_lo[d] = 0.0
+            p.box_len[d] = box_len[d]
+            p.base_cells[d] = int(base_cells[d])
+        p.nguard, p.nslices, p.precision = nguard, nslices, precision
+        p.time_mode, p.dt_pow2, p.dispatcher = time_mode, 1, dispatcher
+        p.tile_x = p.tile_y = 0
+        p.tile_z = tile_z
+        p.sched_capacity = sched_capacity
+        p.timing = timing
+        self.params = p
+        h = VP()
+        rc = L.dsp_create(descs, self.np, ctypes.byref(p), VP(stream or 0), ctypes.byref(h))
+        if rc != 0:
+            raise DispatchError(rc, "dsp_create rejected the layout or parameters")
+        self._h = h
+        self.n = n
+        self.precision = precision
+        nc = int(n[0, 0] * n[0, 1] * n[0, 2])
+        self.sizes = (5 * nc * self.np, int((n[0, 0] + 1) * n[0, 1] * n[0, 2]) * self.np,
+                      int(n[0, 0] * (n[0, 1] + 1) * n[0, 2]) * self.np, int(n[0, 0] * n[0, 1] * (n[0, 2] + 1)) * self.np)
+
+    def _check(self, rc):
+        if rc != 0 and rc != DSP_ERR_SCHEDULE_OVERFLOW:
+            raise DispatchError(rc, load().dsp_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dsp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, U, bx, by, bz, first=0, count=None):
+        count = self.np - first if count is None else count
+        ptrs = [_addr(a) for a in (U, bx, by, bz)]
+        dev, dt = ptrs[0][1], ptrs[0][2]
+        assert all(p[1] == dev and p[2] == dt for p in ptrs)
+        self._check(load().dsp_set_state(self._h, first, count, *[p[0] for p in ptrs], dt, int(dev)))
+
+    def get_state(self, out=None, dtype=np.float64, first=0, count=None):
+        count = self.np - first if count is None else count
+        if out is None:
+            f = count / self.np
+            out = [np.empty(int(s * f), dtype=dtype) for s in self.sizes]
+        ptrs = [_addr(a) for a in out]
+        self._check(load().dsp_get_state(self._h, first, count, *[p[0] for p in ptrs], ptrs[0][2], int(ptrs[0][1])))
+        return out
+
+    def advance(self, t_end=float("inf"), max_sweeps=0):
+        st = dsp_stats()
+        self._check(load().dsp_advance(self._h, t_end, max_sweeps, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in dsp_stats._fields_}
+
+    def times(self):
+        t = np.empty(self.np)
+        dt = np.empty(self.np)
+        self._check(load().dsp_get_times(self._h, t.ctypes.data_as(VP), dt.ctypes.data_as(VP)))
+        return t, dt
+
+    def schedule(self):
+        n = ctypes.c_int64()
+        load().dsp_get_schedule(self._h, None, 0, ctypes.byref(n))
+        cap = n.value
+        buf = (dsp_sched_entry * max(cap, 1))()
+        rc = self._check(load().dsp_get_schedule(self._h, buf, cap, ctypes.byref(n)))
+        k = min(cap, n.value)
+        a = np.frombuffer(buf, dtype=np.dtype([("patch", np.int64), ("t", np.float64), ("dt", np.float64)]),
+                          count=k).copy() if k else np.zeros(0, dtype=[("patch", np.int64), ("t", np.float64), ("dt", np.float64)])
+        if rc == DSP_ERR_SCHEDULE_OVERFLOW:
+            raise DispatchError(rc, "schedule log overflowed")
+        return a["patch"], a["t"], a["dt"]
+
+    def diagnostics(self):
+        d = dsp_diag()
+        self._check(load().dsp_diagnostics(self._h, ctypes.byref(d)))
+        return dict(mass=d.mass, mom=np.array(d.mom[:]), energy=d.energy, bmean=np.array(d.bmean[:]),
+                    max_divb=d.max_divb, max_b=d.max_b)
+
+    def save(self) -> bytes:
+        used = ctypes.c_size_t()
+        self._check(load().dsp_save(self._h, None, 0, ctypes.byref(used)))
+        buf = ctypes.create_string_buffer(used.value)
+        self._check(load().dsp_save(self._h, buf, used.value, ctypes.byref(used)))
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        self._check(load().dsp_load(self._h, blob, len(blob)))

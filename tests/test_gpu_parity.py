@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+FP64: relative L-infinity per field <= 1e-11 (max|a-b| / max|b|); the FP64
+kernels and the oracle evaluate the same operation sequence without FMA
+contraction, so the expected difference is 0.  Schedules must be identical.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1705_10774_gb300 import ics
+from paper_1705_10774_gb300.dispatch import Dispatch, DispatchError, DSP_ERR_UNSUPPORTED, DSP_ERR_INVALID_ARG, \
+    DSP_ERR_UNPHYSICAL
+from oracle import Oracle
+
+TOL64 = 1e-11
+
+
+def rel_linf(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+def kw_of(lay, f, **extra):
+    d = dict(gamma=f.gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
+    d.update(extra)
+    return d
+
+
+def pair(lay, f, gpu_extra=None, **common):
+    state = ics.to_patches(lay, f)
+    ge = dict(sched_capacity=1 << 20)
+    ge.update(gpu_extra or {})
+    g = Dispatch(lay.n, lay.lo, **kw_of(lay, f, **common), **ge)
+    g.set_state(*state)
+    o = Oracle(lay.n, lay.lo, **kw_of(lay, f, **common))
+    o.set_state(*state)
+    return g, o
+
+
+def assert_same(g, o, tol=TOL64):
+    out = g.get_state()
+    ref = o.get_state()
+    for name, a, b in zip(("U", "bx", "by", "bz"), out, ref):
+        assert rel_linf(a, b) <= tol, (name, rel_linf(a, b))
+    assert np.array_equal(g.times()[0], o.get_times()[0])
+
+
+def test_linear_waves_global_step_bit_parity():
+    """Eight 16^3 patches, four seeded linear modes, 20 global steps."""
+    lay, f = ics.config_linear_waves()
+    g, o = pair(lay, f, time_mode=0)
+    st = g.advance(max_sweeps=20)
+    o.advance(max_sweeps=20)
+    assert st["patch_updates"] == 160 and st["cell_updates"] == 160 * 16 ** 3
+    assert_same(g, o)
+    gp, gt, gd = g.schedule()
+    op, ot, od = o.schedule()
+    assert np.array_equal(gp, op) and np.array_equal(gt, ot) and np.array_equal(gd, od)
+    out = g.get_state()
+    ref = o.get_state()
+    assert all(np.array_equal(a, b) for a, b in zip(out, ref)), "expected bit-identical FP64 results"
+
+
+@pytest.mark.parametrize("tile_z", [0, 3])
+def test_ragged_tiles_and_non_cubic_patches(tile_z):
+    """Patches of 20 x 12 x 10 cells: x spans a full and a partial tile, y a
+    full and a partial one, and with tile_z = 3 the z runs end ragged too."""
+    lay = ics.cartesian((2, 2, 2), (20, 12, 10), dx=1.0 / 40)
+    rng = np.random.default_rng(9)
+    X, Y, Z = lay.base_cells
+    shape = (Z, Y, X)
+    v = ics.solenoidal_velocity(shape, lay.box_len, 1.0, 3.0, 1.2, rng)
+    A = [ics.gaussian_filtered_noise(shape, lay.box_len, 0.08, rng) * 0.01 for _ in range(3)]
+    bx, by, bz = ics.curl_faces(*A, lay.dx)
+    f = ics.Fields(rho=1.0 + 0.3 * ics.gaussian_filtered_noise(shape, lay.box_len, 0.1, rng) ** 2, v=v,
+                   p=np.full(shape, 0.6), bx=bx + 0.5, by=by + 0.2, bz=bz, gamma=5.0 / 3.0)
+    g, o = pair(lay, f, gpu_extra=dict(tile_z=tile_z), time_mode=0)
+    g.advance(max_sweeps=6)
+    o.advance(max_sweeps=6)
+    assert_same(g, o)
+
+
+def test_single_patch_is_its_own_neighbour():
+    lay = ics.cartesian(1, 8)
+    f = ics.config_uniform(lay, [1.0, 0.2, -0.1, 0.3, 0.6, 0.8, 0.1, -0.2], 5.0 / 3.0, seed=4, eps=1e-3)
+    g, o = pair(lay, f, time_mode=0)
+    g.advance(max_sweeps=5)
+    o.advance(max_sweeps=5)
+    assert_same(g, o)
+
+
+def _lts_case():
+    return ics.config_lts(patches=6, n=4, sigma_ln=1.0, hot_radius=0.15, hot_factor=100.0)
+
+
+def test_local_time_steps_schedule_and_state():
+    """Local steps spanning a factor > 8: the GPU sweep dispatcher must
+    reproduce the oracle's schedule entry by entry, and the states."""
+    lay, f = _lts_case()
+    g, o = pair(lay, f, time_mode=1, dispatcher=1)
+    t_end = 0.003
+    g.advance(t_end=t_end)
+    o.advance(t_end=t_end)
+    gp, gt, gd = g.schedule()
+    op, ot, od = o.schedule()
+    assert len(np.unique(od)) >= 3
+    assert np.array_equal(gp, op) and np.array_equal(gt, ot) and np.array_equal(gd, od)
+    assert_same(g, o)
+    assert np.all(g.times()[0] == t_end)
+
+
+def test_sweep_schedule_equals_time_sorted_queue():
+    """The GPU sweep schedule equals the oracle's time-sorted queue schedule
+    as a set of (patch, t_start, dt)."""
+    lay, f = _lts_case()
+    state = ics.to_patches(lay, f)
+    g = Dispatch(lay.n, lay.lo, **kw_of(lay, f, time_mode=1), sched_capacity=1 << 20)
+    g.set_state(*state)
+    g.advance(t_end=0.002)
+    q = Oracle(lay.n, lay.lo, **kw_of(lay, f, time_mode=1, dispatcher=0))
+    q.set_state(*state)
+    q.advance(t_end=0.002)
+    key = lambda s: sorted(zip(*(x.tolist() for x in s)))
+    assert key(g.schedule()) == key(q.schedule())
+    for a, b in zip(g.get_state(), q.get_state()):
+        assert np.array_equal(a, b)
+
+
+def test_conservation_and_divb_on_gpu():
+    lay, f = ics.config_turbulence(seed=5, patches=2, n=16, mach=1.0)
+    g = Dispatch(lay.n, lay.lo, **kw_of(lay, f, time_mode=0))
+    g.set_state(*ics.to_patches(lay, f))
+    d0 = g.diagnostics()
+    g.advance(max_sweeps=10)
+    d1 = g.diagnostics()
+    U = g.get_state()[0]
+    tol = 1e-13 * 10 * np.abs(U).sum() * lay.dx ** 3
+    assert abs(d1["mass"] - d0["mass"]) <= tol and abs(d1["energy"] - d0["energy"]) <= tol
+    assert np.all(np.abs(d1["mom"] - d0["mom"]) <= tol)
+    assert d1["max_divb"] <= 1e-13 * d1["max_b"]
+
+
+def test_fp32_form_against_fp64():
+    """FP32 state and stencil with FP64 times: relative L1 <= 1e-5 per field
+    against the FP64 path after 20 steps of the linear-wave input."""
+    lay, f = ics.config_linear_waves(amplitude=1e-3)
+    state = ics.to_patches(lay, f)
+    g64 = Dispatch(lay.n, lay.lo, **kw_of(lay, f, time_mode=0))
+    g32 = Dispatch(lay.n, lay.lo, precision=1, **kw_of(lay, f, time_mode=0))
+    g64.set_state(*state)
+    g32.set_state(*state)
+    g64.advance(max_sweeps=20)
+    g32.advance(max_sweeps=20)
+    a = g64.get_state()
+    b = g32.get_state()
+    for x, y in zip(a, b):
+        assert np.sum(np.abs(x - y)) / np.sum(np.abs(x)) <= 1e-5
+    assert np.array_equal(g64.times()[0], g32.times()[0])
+
+
+def test_save_load_resume_is_bit_identical():
+    lay, f = _lts_case()
+    state = ics.to_patches(lay, f)
+    a = Dispatch(lay.n, lay.lo, **kw_of(lay, f, time_mode=1))
+    a.set_state(*state)
+    a.advance(t_end=0.001)
+    blob = a.save()
+    a.advance(t_end=0.002)
+    b = Dispatch(lay.n, lay.lo, **kw_of(lay, f, time_mode=1))
+    b.load_state(blob)
+    b.advance(t_end=0.002)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.times()[0], b.times()[0])
+
+
+def test_device_pointers_and_fp32_input():
+    lay, f = ics.config_linear_waves(n=8, amplitude=1e-3)
+    state = ics.to_patches(lay, f)
+    g = Dispatch(lay.n, lay.lo, **kw_of(lay, f, time_mode=0))
+    g.set_state(*[torch.from_numpy(x).cuda() for x in state])
+    out = [torch.empty(x.size, dtype=torch.float64, device="cuda") for x in state]
+    g.get_state(out=out)
+    for x, y in zip(out, state):
+        assert np.array_equal(x.cpu().numpy(), y)
+    g.set_state(*[x.astype(np.float32) for x in state])
+    back = g.get_state(dtype=np.float32)
+    for x, y in zip(back, state):
+        assert np.array_equal(x, y.astype(np.float32))
+
+
+def test_rejected_inputs():
+    lay = ics.cartesian(2, 8)
+    base = dict(gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
+    with pytest.raises(DispatchError) as e:
+        Dispatch(lay.n, lay.lo, **base, nguard=8)          # patch not wider than its guard depth
+    assert e.value.code == DSP_ERR_INVALID_ARG
+    with pytest.raises(DispatchError) as e:
+        Dispatch(lay.n, lay.lo, **base, dispatcher=7)
+    assert e.value.code in (DSP_ERR_UNSUPPORTED, DSP_ERR_INVALID_ARG)
+    with pytest.raises(DispatchError) as e:
+        Dispatch(lay.n[:-1], lay.lo[:-1], **base)           # does not tile the box
+    assert e.value.code == DSP_ERR_INVALID_ARG
+    f = ics.config_uniform(lay, [1.0, 0, 0, 0, 0.6, 0, 0, 0], 5.0 / 3.0)
+    U, bx, by, bz = ics.to_patches(lay, f)
+    U[0] = -1.0
+    g = Dispatch(lay.n, lay.lo, **base)
+    with pytest.raises(DispatchError) as e:
+        g.set_state(U, bx, by, bz)
+    assert e.value.code == DSP_ERR_UNPHYSICAL
