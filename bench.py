@@ -194,6 +194,13 @@ def gpu_arm(args):
     ncells = int(np.prod(lay.base_cells))
     peak, peak_kind = measured_peaks()
 
+    if args.form == "f32":
+        state32 = [a.float() for a in state_dev]
+        g, st, ms = run_form(lay, state32, 1, args.steps, args.warmup, td)
+        if rank == 0:
+            print(json.dumps({"form": "f32", "ms_per_step": ms / args.steps,
+                              "kernel_ms_avg": st["kernel_ms"] / max(st["kernel_launches"], 1)}))
+        return
     with Clocks(local) as clk:
         g, st, ms = run_form(lay, state_dev, 0, args.steps, args.warmup, td)
     ms_max = max_over_ranks(td, ms)
@@ -208,7 +215,7 @@ def gpu_arm(args):
     g.close()
 
     forms = {}
-    if not args.no_f32:
+    if not args.no_f32 and args.form == "both":
         state32 = [a.float() for a in state_dev]
         g32, st32, ms32 = run_form(lay, state32, 1, args.steps, args.warmup, td)
         ms32_max = max_over_ranks(td, ms32)
@@ -354,6 +361,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-f32", action="store_true")
+    ap.add_argument("--form", default="both", choices=["both", "f64", "f32"],
+                    help="f32: time only the FP32-state form (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -1,0 +1,114 @@
+"""Parity at full benchmark sizes, on outputs the oracle can compute one by
+one: the GPU runs the whole workload in the benchmark's launch configuration,
+the oracle loads the GPU's state at some point and reproduces the next update
+of sampled patches (and the step and ready set of that sweep)."""
+import struct
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1705_10774_gb300 import ics
+from paper_1705_10774_gb300.dispatch import Dispatch
+from oracle import Oracle
+
+TOL64 = 1e-11
+
+
+def rel_linf(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def patch_slices(lay, arrays, P):
+    n = lay.n[0]
+    nc = int(n[0] * n[1] * n[2])
+    sizes = [5 * nc, (n[0] + 1) * n[1] * n[2], n[0] * (n[1] + 1) * n[2], n[0] * n[1] * (n[2] + 1)]
+    return [a[P * s:(P + 1) * s] for a, s in zip(arrays, sizes)]
+
+
+def test_turbulence_256cubed_sampled_patches_fp64():
+    """512 patches of 32^3, global steps: after 3 steps the oracle takes the
+    GPU state, recomputes the global step and the 4th update of 8 patches."""
+    lay, f = ics.config_turbulence(seed=10774, patches=8, n=32, mach=2.0)
+    state = ics.to_patches(lay, f)
+    kw = dict(gamma=f.gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
+    g = Dispatch(lay.n, lay.lo, time_mode=0, **kw)
+    g.set_state(*[torch.from_numpy(a).cuda() for a in state])
+    g.advance(max_sweeps=3)
+    snap = g.get_state()
+    t3 = g.times()[0]
+    assert np.all(t3 == t3[0])
+    g.advance(max_sweeps=1)
+    after = g.get_state()
+    t4, dt4 = g.times()
+    o = Oracle(lay.n, lay.lo, t0=float(t3[0]), **kw)
+    o.set_state(*snap)
+    dt = min(o.patch_dt(i) for i in range(lay.npatch))
+    assert np.all(dt4 == dt) and np.all(t4 == t3[0] + dt)
+    for P in (0, 7, 63, 64, 200, 365, 448, 511):
+        ref = o.update_patch(P, dt)[:4]
+        got = patch_slices(lay, after, P)
+        for a, b in zip(got, ref):
+            assert rel_linf(a, b) <= TOL64
+
+
+def parse_save(blob, lay, nslot):
+    magic = blob[:8]
+    assert magic.startswith(b"DSPSAVE")
+    version, npch, ns, prec = struct.unpack_from("<4i", blob, 8)
+    patch_len, slot_stride = struct.unpack_from("<2q", blob, 24)
+    off = 40
+    ts = np.frombuffer(blob, np.float64, npch * ns, off).reshape(npch, ns); off += 8 * npch * ns
+    sm = np.frombuffer(blob, np.float64, npch * ns, off).reshape(npch, ns); off += 8 * npch * ns
+    latest = np.frombuffer(blob, np.int32, npch, off); off += 4 * npch
+    dtl = np.frombuffer(blob, np.float64, npch, off); off += 8 * npch
+    slab = np.frombuffer(blob, np.float64, ns * slot_stride, off).reshape(ns, npch, patch_len)
+    return ts, sm, latest, dtl, slab
+
+
+def test_local_steps_4096_patches_sampled_sweep_fp64():
+    """4096 patches of 16^3 with local steps (log-normal density, hot
+    sphere): after 24 sweeps the oracle loads the GPU's full dispatcher state
+    (every slice), finds the ready set and steps of the next sweep, and
+    reproduces sampled updates of it."""
+    lay, f = ics.config_lts(patches=16, n=16)
+    state = ics.to_patches(lay, f)
+    kw = dict(gamma=f.gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
+    t_end = 0.05
+    g = Dispatch(lay.n, lay.lo, time_mode=1, sched_capacity=1 << 22, **kw)
+    g.set_state(*[torch.from_numpy(a).cuda() for a in state])
+    g.advance(t_end=t_end, max_sweeps=24)
+    blob = g.save()
+    n_before = len(g.schedule()[0])
+    g.advance(t_end=t_end, max_sweeps=1)
+    sp, st, sdt = g.schedule()
+    sp, st, sdt = sp[n_before:], st[n_before:], sdt[n_before:]
+    after = g.get_state()
+    ts, sm, latest, dtl, slab = parse_save(blob, lay, 3)
+    o = Oracle(lay.n, lay.lo, time_mode=1, **kw)
+    n = lay.n[0]
+    nc = int(n[0] * n[1] * n[2])
+    cuts = np.cumsum([5 * nc, (n[0] + 1) * n[1] * n[2], n[0] * (n[1] + 1) * n[2]])
+    for P in range(lay.npatch):
+        for s in range(3):
+            U, bx, by, bz = np.split(slab[s, P], cuts)
+            o.set_slot(P, s, float(ts[P, s]), U, bx, by, bz)
+        o.set_latest(P, int(latest[P]), float(dtl[P]))
+    t = ts[np.arange(lay.npatch), latest]
+    ready = []
+    for P in range(lay.npatch):
+        if t[P] < t_end and all(t[P] <= t[q] for q in o.nbors(P)):
+            ready.append(P)
+    assert sorted(sp.tolist()) == ready
+    assert len(np.unique(dtl[dtl > 0])) >= 2 or len(np.unique(sdt)) >= 2
+    want = {P: o.patch_dt(P, t_end) for P in ready}
+    for P, t0, d in zip(sp, st, sdt):
+        assert t0 == t[P] and d == want[int(P)]
+    rng = np.random.default_rng(0)
+    for P in rng.choice(ready, size=min(6, len(ready)), replace=False):
+        ref = o.update_patch(int(P), want[int(P)])[:4]
+        got = patch_slices(lay, after, int(P))
+        for a, b in zip(got, ref):
+            assert rel_linf(a, b) <= TOL64
