@@ -82,12 +82,13 @@ typedef struct {
 static void prim(const double u[5], double bxl, double bxr, double byl, double byr,
                  double bzl, double bzr, double gamma, double W[8]) {
   double rho = u[0];
+  double irho = 1.0 / rho;
   double Bx = 0.5 * (bxl + bxr);
   double By = 0.5 * (byl + byr);
   double Bz = 0.5 * (bzl + bzr);
-  double vx = u[1] / rho;
-  double vy = u[2] / rho;
-  double vz = u[3] / rho;
+  double vx = u[1] * irho;
+  double vy = u[2] * irho;
+  double vz = u[3] * irho;
   double ke = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
   double me = 0.5 * (Bx * Bx + By * By + Bz * Bz);
   double p = (gamma - 1.0) * (u[4] - ke - me);
@@ -96,11 +97,12 @@ static void prim(const double u[5], double bxl, double bxr, double byl, double b
 }
 
 /* Fast magnetosonic speed along the axis whose field component is bn:
- * c_f^2 = [a^2 + B^2/rho + sqrt((a^2 + B^2/rho)^2 - 4 a^2 bn^2/rho)] / 2. */
-static double cfast(double gamma, double rho, double p, double bn, double bt1, double bt2) {
-  double a2 = gamma * p / rho;
-  double bb = (bn * bn + bt1 * bt1 + bt2 * bt2) / rho;
-  double ca2 = bn * bn / rho;
+ * c_f^2 = [a^2 + B^2/rho + sqrt((a^2 + B^2/rho)^2 - 4 a^2 bn^2/rho)] / 2,
+ * with irho = 1/rho. */
+static double cfast(double gamma, double irho, double p, double bn, double bt1, double bt2) {
+  double a2 = gamma * p * irho;
+  double bb = (bn * bn + bt1 * bt1 + bt2 * bt2) * irho;
+  double ca2 = bn * bn * irho;
   double s = a2 + bb;
   double disc = s * s - 4.0 * a2 * ca2;
   if (disc < 0.0) disc = 0.0;
@@ -124,6 +126,7 @@ static void predict(const double W[8], const double *dX, const double *dY, const
                     double gamma, double h, double Ws[8]) {
   double rho = W[RHO], vx = W[VX], vy = W[VY], vz = W[VZ], p = W[PR];
   double Bx = W[BX], By = W[BY], Bz = W[BZ];
+  double irho = 1.0 / rho;
   double divv = dX[VX] + dY[VY] + dZ[VZ];
   double r_rho = -(vx * dX[RHO] + vy * dY[RHO] + vz * dZ[RHO]) - rho * divv;
   double gpx = dX[PR] + (Bx * dX[BX] + By * dX[BY] + Bz * dX[BZ]);
@@ -132,9 +135,9 @@ static void predict(const double W[8], const double *dX, const double *dY, const
   double tx = Bx * dX[BX] + By * dY[BX] + Bz * dZ[BX];
   double ty = Bx * dX[BY] + By * dY[BY] + Bz * dZ[BY];
   double tz = Bx * dX[BZ] + By * dY[BZ] + Bz * dZ[BZ];
-  double r_vx = -(vx * dX[VX] + vy * dY[VX] + vz * dZ[VX]) - (gpx - tx) / rho;
-  double r_vy = -(vx * dX[VY] + vy * dY[VY] + vz * dZ[VY]) - (gpy - ty) / rho;
-  double r_vz = -(vx * dX[VZ] + vy * dY[VZ] + vz * dZ[VZ]) - (gpz - tz) / rho;
+  double r_vx = -(vx * dX[VX] + vy * dY[VX] + vz * dZ[VX]) - (gpx - tx) * irho;
+  double r_vy = -(vx * dX[VY] + vy * dY[VY] + vz * dZ[VY]) - (gpy - ty) * irho;
+  double r_vz = -(vx * dX[VZ] + vy * dY[VZ] + vz * dZ[VZ]) - (gpz - tz) * irho;
   double r_p = -(vx * dX[PR] + vy * dY[PR] + vz * dZ[PR]) - gamma * p * divv;
   double r_bx = (Bx * dX[VX] + By * dY[VX] + Bz * dZ[VX]) - (vx * dX[BX] + vy * dY[BX] + vz * dZ[BX]) - Bx * divv;
   double r_by = (Bx * dX[VY] + By * dY[VY] + Bz * dZ[VY]) - (vx * dX[BY] + vy * dY[BY] + vz * dZ[BY]) - By * divv;
@@ -156,7 +159,7 @@ static void predict(const double W[8], const double *dX, const double *dY, const
  * tangential field components (cyclic order after d), S[0] = S_L, S[1] = S_R. */
 static void hll(const double WL[8], const double WR[8], int d, double gamma, double F[7], double S[2]) {
   int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-  double gm1 = gamma - 1.0;
+  double igm1 = 1.0 / (gamma - 1.0);
   double bn = 0.5 * (WL[BX + d] + WR[BX + d]);
   double FL[7], FR[7], UL[7], UR[7], cL, cR, vnL, vnR;
   for (int side = 0; side < 2; side++) {
@@ -168,10 +171,10 @@ static void hll(const double WL[8], const double WR[8], int d, double gamma, dou
     double bt1 = W[BX + t1], bt2 = W[BX + t2];
     double v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
     double B2 = bn * bn + bt1 * bt1 + bt2 * bt2;
-    double E = p / gm1 + 0.5 * rho * v2 + 0.5 * B2;
+    double E = p * igm1 + 0.5 * rho * v2 + 0.5 * B2;
     double PT = p + 0.5 * B2;
     double vB = vn * bn + vt1 * bt1 + vt2 * bt2;
-    double cf = cfast(gamma, rho, p, bn, bt1, bt2);
+    double cf = cfast(gamma, 1.0 / rho, p, bn, bt1, bt2);
     Us[0] = rho; Us[1] = rho * vn; Us[2] = rho * vt1; Us[3] = rho * vt2; Us[4] = E;
     Us[5] = bt1; Us[6] = bt2;
     Fs[0] = rho * vn;
@@ -186,10 +189,11 @@ static void hll(const double WL[8], const double WR[8], int d, double gamma, dou
   double SL = fmin(vnL - cL, vnR - cR);
   double SR = fmax(vnL + cL, vnR + cR);
   double Fr[7];
+  double inv = 1.0 / (SR - SL);
   for (int c = 0; c < 7; c++) {
     if (SL >= 0.0) Fr[c] = FL[c];
     else if (SR <= 0.0) Fr[c] = FR[c];
-    else Fr[c] = (SR * FL[c] - SL * FR[c] + SL * SR * (UR[c] - UL[c])) / (SR - SL);
+    else Fr[c] = (SR * FL[c] - SL * FR[c] + SL * SR * (UR[c] - UL[c])) * inv;
   }
   F[0] = Fr[0];
   F[1 + d] = Fr[1];
@@ -239,7 +243,7 @@ void orc_prim(const double *u, const double *faces, double gamma, double *W) {
   prim(u, faces[0], faces[1], faces[2], faces[3], faces[4], faces[5], gamma, W);
 }
 double orc_cfast(double gamma, double rho, double p, double bn, double bt1, double bt2) {
-  return cfast(gamma, rho, p, bn, bt1, bt2);
+  return cfast(gamma, 1.0 / rho, p, bn, bt1, bt2);
 }
 double orc_mc(double dl, double dr) { return mc(dl, dr); }
 void orc_predict(const double *W, const double *dX, const double *dY, const double *dZ, double gamma,
@@ -388,9 +392,10 @@ static double slice_smax(orc_ctx *c, opatch *P, int s, int *bad) {
         double bzr = P->bz[s][((int64_t)(k + 1) * ny + j) * nx + i];
         prim(u, bxl, bxr, byl, byr, bzl, bzr, c->gamma, W);
         if (!(W[RHO] > 0.0) || !(W[PR] > 0.0)) *bad = 1;
-        double cx = cfast(c->gamma, W[RHO], W[PR], W[BX], W[BY], W[BZ]);
-        double cy = cfast(c->gamma, W[RHO], W[PR], W[BY], W[BZ], W[BX]);
-        double cz = cfast(c->gamma, W[RHO], W[PR], W[BZ], W[BX], W[BY]);
+        double ir = 1.0 / W[RHO];
+        double cx = cfast(c->gamma, ir, W[PR], W[BX], W[BY], W[BZ]);
+        double cy = cfast(c->gamma, ir, W[PR], W[BY], W[BZ], W[BX]);
+        double cz = cfast(c->gamma, ir, W[PR], W[BZ], W[BX], W[BY]);
         double sum = (fabs(W[VX]) + cx) + (fabs(W[VY]) + cy) + (fabs(W[VZ]) + cz);
         if (sum > m) m = sum;
       }
@@ -796,9 +801,10 @@ static int update_patch(orc_ctx *c, int ip, double dt, double *oU, double *obx, 
                oby[((int64_t)k * (ny + 1) + j) * nx + i], oby[((int64_t)k * (ny + 1) + j + 1) * nx + i],
                obz[((int64_t)k * ny + j) * nx + i], obz[((int64_t)(k + 1) * ny + j) * nx + i], gamma, w8);
           if (!(w8[RHO] > 0.0) || !(w8[PR] > 0.0)) bad = 1;
-          double cx = cfast(gamma, w8[RHO], w8[PR], w8[BX], w8[BY], w8[BZ]);
-          double cy = cfast(gamma, w8[RHO], w8[PR], w8[BY], w8[BZ], w8[BX]);
-          double cz = cfast(gamma, w8[RHO], w8[PR], w8[BZ], w8[BX], w8[BY]);
+          double ir = 1.0 / w8[RHO];
+          double cx = cfast(gamma, ir, w8[PR], w8[BX], w8[BY], w8[BZ]);
+          double cy = cfast(gamma, ir, w8[PR], w8[BY], w8[BZ], w8[BX]);
+          double cz = cfast(gamma, ir, w8[PR], w8[BZ], w8[BX], w8[BY]);
           double sum = (fabs(w8[VX]) + cx) + (fabs(w8[VY]) + cy) + (fabs(w8[VZ]) + cz);
           if (sum > m) m = sum;
         }
