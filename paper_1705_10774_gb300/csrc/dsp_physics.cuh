@@ -26,12 +26,13 @@ template <typename T>
 __device__ __forceinline__ void prim(T rho, T mx, T my, T mz, T E, T bxl, T bxr, T byl, T byr, T bzl, T bzr,
                                      T gamma, T W[8]) {
   const T h = T(0.5);
+  T irho = T(1) / rho;
   T Bx = h * (bxl + bxr);
   T By = h * (byl + byr);
   T Bz = h * (bzl + bzr);
-  T vx = mx / rho;
-  T vy = my / rho;
-  T vz = mz / rho;
+  T vx = mx * irho;
+  T vy = my * irho;
+  T vz = mz * irho;
   T ke = h * rho * (vx * vx + vy * vy + vz * vz);
   T me = h * (Bx * Bx + By * By + Bz * Bz);
   T p = (gamma - T(1)) * (E - ke - me);
@@ -39,12 +40,13 @@ __device__ __forceinline__ void prim(T rho, T mx, T my, T mz, T E, T bxl, T bxr,
   W[BX] = Bx; W[BY] = By; W[BZ] = Bz;
 }
 
-// Fast magnetosonic speed along the axis whose field component is bn.
+// Fast magnetosonic speed along the axis whose field component is bn
+// (irho = 1/rho).
 template <typename T>
-__device__ __forceinline__ T cfast(T gamma, T rho, T p, T bn, T bt1, T bt2) {
-  T a2 = gamma * p / rho;
-  T bb = (bn * bn + bt1 * bt1 + bt2 * bt2) / rho;
-  T ca2 = bn * bn / rho;
+__device__ __forceinline__ T cfast(T gamma, T irho, T p, T bn, T bt1, T bt2) {
+  T a2 = gamma * p * irho;
+  T bb = (bn * bn + bt1 * bt1 + bt2 * bt2) * irho;
+  T ca2 = bn * bn * irho;
   T s = a2 + bb;
   T disc = s * s - T(4) * a2 * ca2;
   if (disc < T(0)) disc = T(0);
@@ -54,9 +56,10 @@ __device__ __forceinline__ T cfast(T gamma, T rho, T p, T bn, T bt1, T bt2) {
 // Sum over axes of |v_d| + c_f,d: the signal speed that sets the Courant step.
 template <typename T>
 __device__ __forceinline__ T signal_sum(const T W[8], T gamma) {
-  T cx = cfast(gamma, W[RHO], W[PR], W[BX], W[BY], W[BZ]);
-  T cy = cfast(gamma, W[RHO], W[PR], W[BY], W[BZ], W[BX]);
-  T cz = cfast(gamma, W[RHO], W[PR], W[BZ], W[BX], W[BY]);
+  T ir = T(1) / W[RHO];
+  T cx = cfast(gamma, ir, W[PR], W[BX], W[BY], W[BZ]);
+  T cy = cfast(gamma, ir, W[PR], W[BY], W[BZ], W[BX]);
+  T cz = cfast(gamma, ir, W[PR], W[BZ], W[BX], W[BY]);
   return (tabs(W[VX]) + cx) + (tabs(W[VY]) + cy) + (tabs(W[VZ]) + cz);
 }
 
@@ -74,6 +77,7 @@ __device__ __forceinline__ void predict(const T W[8], const T dX[8], const T dY[
                                         T Ws[8]) {
   T rho = W[RHO], vx = W[VX], vy = W[VY], vz = W[VZ], p = W[PR];
   T Bx = W[BX], By = W[BY], Bz = W[BZ];
+  T irho = T(1) / rho;
   T divv = dX[VX] + dY[VY] + dZ[VZ];
   T r_rho = -(vx * dX[RHO] + vy * dY[RHO] + vz * dZ[RHO]) - rho * divv;
   T gpx = dX[PR] + (Bx * dX[BX] + By * dX[BY] + Bz * dX[BZ]);
@@ -82,9 +86,9 @@ __device__ __forceinline__ void predict(const T W[8], const T dX[8], const T dY[
   T tx = Bx * dX[BX] + By * dY[BX] + Bz * dZ[BX];
   T ty = Bx * dX[BY] + By * dY[BY] + Bz * dZ[BY];
   T tz = Bx * dX[BZ] + By * dY[BZ] + Bz * dZ[BZ];
-  T r_vx = -(vx * dX[VX] + vy * dY[VX] + vz * dZ[VX]) - (gpx - tx) / rho;
-  T r_vy = -(vx * dX[VY] + vy * dY[VY] + vz * dZ[VY]) - (gpy - ty) / rho;
-  T r_vz = -(vx * dX[VZ] + vy * dY[VZ] + vz * dZ[VZ]) - (gpz - tz) / rho;
+  T r_vx = -(vx * dX[VX] + vy * dY[VX] + vz * dZ[VX]) - (gpx - tx) * irho;
+  T r_vy = -(vx * dX[VY] + vy * dY[VY] + vz * dZ[VY]) - (gpy - ty) * irho;
+  T r_vz = -(vx * dX[VZ] + vy * dY[VZ] + vz * dZ[VZ]) - (gpz - tz) * irho;
   T r_p = -(vx * dX[PR] + vy * dY[PR] + vz * dZ[PR]) - gamma * p * divv;
   T r_bx = (Bx * dX[VX] + By * dY[VX] + Bz * dZ[VX]) - (vx * dX[BX] + vy * dY[BX] + vz * dZ[BX]) - Bx * divv;
   T r_by = (Bx * dX[VY] + By * dY[VY] + Bz * dZ[VY]) - (vx * dX[BY] + vy * dY[BY] + vz * dZ[BY]) - By * divv;
@@ -99,13 +103,13 @@ __device__ __forceinline__ void predict(const T W[8], const T dX[8], const T dY[
   Ws[BZ] = Bz + h * r_bz;
 }
 
-// HLL flux through a face with normal axis D (compile-time), Davis speeds.
+// HLL flux through a face with normal axis D (compile-time), Davis speeds;
+// igm1 = 1/(gamma-1).
 // WL/WR: lab-frame primitive states.  F[0..4]: lab-frame mass, momentum
 // x,y,z, energy fluxes.  SL, SR: the two signal speeds.
 template <typename T, int D>
-__device__ __forceinline__ void hll(const T WL[8], const T WR[8], T gamma, T F[5], T &SL, T &SR) {
+__device__ __forceinline__ void hll(const T WL[8], const T WR[8], T gamma, T igm1, T F[5], T &SL, T &SR) {
   constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
-  const T gm1 = gamma - T(1);
   const T h = T(0.5);
   T bn = h * (WL[BX + D] + WR[BX + D]);
   T FL[5], FR[5], UL[5], UR[5], cL, cR, vnL, vnR;
@@ -117,10 +121,10 @@ __device__ __forceinline__ void hll(const T WL[8], const T WR[8], T gamma, T F[5
     T bt1 = W[BX + t1], bt2 = W[BX + t2];
     T v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
     T B2 = bn * bn + bt1 * bt1 + bt2 * bt2;
-    T E = p / gm1 + h * rho * v2 + h * B2;
+    T E = p * igm1 + h * rho * v2 + h * B2;
     T PT = p + h * B2;
     T vB = vn * bn + vt1 * bt1 + vt2 * bt2;
-    T cf = cfast(gamma, rho, p, bn, bt1, bt2);
+    T cf = cfast(gamma, T(1) / rho, p, bn, bt1, bt2);
     T *Us = side ? UR : UL;
     T *Fs = side ? FR : FL;
     Us[0] = rho; Us[1] = rho * vn; Us[2] = rho * vt1; Us[3] = rho * vt2; Us[4] = E;
@@ -134,11 +138,12 @@ __device__ __forceinline__ void hll(const T WL[8], const T WR[8], T gamma, T F[5
   SL = tmin(vnL - cL, vnR - cR);
   SR = tmax(vnL + cL, vnR + cR);
   T Fr[5];
+  const T inv = T(1) / (SR - SL);
 #pragma unroll
   for (int q = 0; q < 5; q++) {
     if (SL >= T(0)) Fr[q] = FL[q];
     else if (SR <= T(0)) Fr[q] = FR[q];
-    else Fr[q] = (SR * FL[q] - SL * FR[q] + SL * SR * (UR[q] - UL[q])) / (SR - SL);
+    else Fr[q] = (SR * FL[q] - SL * FR[q] + SL * SR * (UR[q] - UL[q])) * inv;
   }
   F[0] = Fr[0];
   F[1 + D] = Fr[1];

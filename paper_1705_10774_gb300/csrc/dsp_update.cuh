@@ -33,9 +33,10 @@ template <int TX, int TY>
 struct Lay {
   static constexpr int H2N = (TX + 4) * (TY + 4);
   static constexpr int H1N = (TX + 2) * (TY + 2);
+  static constexpr int FPN = (TX + 5) * (TY + 5);
   static constexpr int oW = 0;                 // [3 planes][8][H2N] primitive ring
-  static constexpr int oFB = oW + 24 * H2N;    // [3 planes][3][H2N] low faces ring
-  static constexpr int oWS = oFB + 9 * H2N;    // [8][H1N] predicted state W*
+  static constexpr int oFB = oW + 24 * H2N;    // [2 planes][4][FPN] faces: x-low, y-low, z-low, z-high
+  static constexpr int oWS = oFB + 8 * FPN;    // [8][H1N] predicted state W*
   static constexpr int oDX = oWS + 8 * H1N;    // [8][H1N] slopes along x
   static constexpr int oDY = oDX + 8 * H1N;
   static constexpr int oDZ = oDY + 8 * H1N;
@@ -67,11 +68,11 @@ __device__ __forceinline__ void set_error(const DevCtx &c, int code, int P, long
   }
 }
 
-template <typename T, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT, 1) update_kernel(DevCtx c) {
+template <typename T, int TX, int TY, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
   static_assert(TX * TY <= NT, "one updated cell per thread");
   using L = Lay<TX, TY>;
-  constexpr int H2N = L::H2N, H1N = L::H1N;
+  constexpr int H2N = L::H2N, H1N = L::H1N, FPN = L::FPN;
   extern __shared__ __align__(16) unsigned char smraw[];
   T *sm = reinterpret_cast<T *>(smraw);
   T *const Wr = sm + L::oW;
@@ -107,11 +108,13 @@ __global__ void __launch_bounds__(NT, 1) update_kernel(DevCtx c) {
   const int nx = c.nx, ny = c.ny, nz = c.nz;
   const long long nc = c.nc, ofy = 5 * c.nc + c.nfx, ofz = 5 * c.nc + c.nfx + c.nfy, ofx = 5 * c.nc;
   const T gamma = (T)c.gamma;
+  const T igm1 = (T)(1.0 / (c.gamma - 1.0));
   const T half = T(0.5);
   const long long nwork = (long long)c.ctl[CTL_NREADY] * c.tiles;
 
 #define H2(i, j) (((j) + 2) * (TX + 4) + ((i) + 2))
 #define H1(i, j) (((j) + 1) * (TX + 2) + ((i) + 1))
+#define F5(i, j) (((j) + 2) * (TX + 5) + ((i) + 2))
 
   for (long long w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int r = (int)(w / c.tiles), tile = (int)(w % c.tiles);
@@ -179,51 +182,80 @@ __global__ void __launch_bounds__(NT, 1) update_kernel(DevCtx c) {
     // lies on one of its interior cells, else the face of the patch that owns
     // cell (x,y,z).
     auto facex = [&](int x, int y, int z) -> T {
-      const bool ownf = x >= 0 && x <= nx && y >= 0 && y < ny && z >= 0 && z < nz;
-      const int ox = ownf ? 1 : off1(x, nx), oy = ownf ? 1 : off1(y, ny), oz = ownf ? 1 : off1(z, nz);
+      if (x >= 0 && x <= nx && y >= 0 && y < ny && z >= 0 && z < nz)
+        return own[ofx + ((long long)z * ny + y) * (nx + 1) + x];
+      const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
       const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
       return val((oz * 3 + oy) * 3 + ox, ofx + ((long long)lz * ny + ly) * (nx + 1) + lx);
     };
     auto facey = [&](int x, int y, int z) -> T {
-      const bool ownf = x >= 0 && x < nx && y >= 0 && y <= ny && z >= 0 && z < nz;
-      const int ox = ownf ? 1 : off1(x, nx), oy = ownf ? 1 : off1(y, ny), oz = ownf ? 1 : off1(z, nz);
+      if (x >= 0 && x < nx && y >= 0 && y <= ny && z >= 0 && z < nz)
+        return own[ofy + ((long long)z * (ny + 1) + y) * nx + x];
+      const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
       const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
       return val((oz * 3 + oy) * 3 + ox, ofy + ((long long)lz * (ny + 1) + ly) * nx + lx);
     };
     auto facez = [&](int x, int y, int z) -> T {
-      const bool ownf = x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z <= nz;
-      const int ox = ownf ? 1 : off1(x, nx), oy = ownf ? 1 : off1(y, ny), oz = ownf ? 1 : off1(z, nz);
+      if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z <= nz)
+        return own[ofz + ((long long)z * ny + y) * nx + x];
+      const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
       const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
       return val((oz * 3 + oy) * 3 + ox, ofz + ((long long)lz * ny + ly) * nx + lx);
     };
 
-    // ---- A: gather plane q of the radius-2 padded tile, to primitives
+    // ---- A: gather plane q of the radius-2 padded tile: the raw conserved
+    // values and the faces (x- and y-faces below each cell, both z-faces),
+    // then the primitive variables from shared memory.
     auto load_plane = [&](int q) {
-      const int rs = (q - z0 + 3) % 3;
+      const int rs = (q - z0 + 3) % 3, fs = (q - z0 + 2) & 1;
       T *Wq = Wr + rs * 8 * H2N;
-      T *Fq = FB + rs * 3 * H2N;
-      const int nxx = tx + 4, ncell = (tx + 4) * (ty + 4);
+      T *Fq = FB + fs * 4 * FPN;
+      const int oz = off1(q, nz), lz = q - (oz - 1) * nz;
+      const int nxx = tx + 5, ncell = (tx + 5) * (ty + 5);
       for (int ci = tid; ci < ncell; ci += NT) {
         const int i = ci % nxx - 2, j = ci / nxx - 2;
         const int x = x0 + i, y = y0 + j;
-        const T u0 = cellv(x, y, q, 0), u1 = cellv(x, y, q, 1), u2 = cellv(x, y, q, 2);
-        const T u3 = cellv(x, y, q, 3), u4 = cellv(x, y, q, 4);
-        const T bxl = facex(x, y, q), bxr = facex(x + 1, y, q);
-        const T byl = facey(x, y, q), byr = facey(x, y + 1, q);
-        const T bzl = facez(x, y, q), bzr = facez(x, y, q + 1);
+        const int f = F5(i, j);
+        if (j <= ty + 1) Fq[f] = facex(x, y, q);
+        if (i <= tx + 1) Fq[FPN + f] = facey(x, y, q);
+        if (i <= tx + 1 && j <= ty + 1) {
+          Fq[2 * FPN + f] = facez(x, y, q);
+          Fq[3 * FPN + f] = facez(x, y, q + 1);
+          const int ox = off1(x, nx), oy = off1(y, ny);
+          const int o = (oz * 3 + oy) * 3 + ox;
+          const long long cid = ((long long)lz * ny + (y - (oy - 1) * ny)) * nx + (x - (ox - 1) * nx);
+          const int h = H2(i, j);
+          if (o == 13) {
+#pragma unroll
+            for (int k = 0; k < 5; k++) Wq[k * H2N + h] = own[k * nc + cid];
+          } else {
+#pragma unroll
+            for (int k = 0; k < 5; k++) Wq[k * H2N + h] = val(o, k * nc + cid);
+          }
+        }
+      }
+    };
+    auto prim_plane = [&](int q) {
+      const int rs = (q - z0 + 3) % 3, fs = (q - z0 + 2) & 1;
+      T *Wq = Wr + rs * 8 * H2N;
+      const T *Fq = FB + fs * 4 * FPN;
+      const int nxx = tx + 4, ncell = (tx + 4) * (ty + 4);
+      for (int ci = tid; ci < ncell; ci += NT) {
+        const int i = ci % nxx - 2, j = ci / nxx - 2;
+        const int h = H2(i, j), f = F5(i, j);
         T Wt[8];
-        prim(u0, u1, u2, u3, u4, bxl, bxr, byl, byr, bzl, bzr, gamma, Wt);
-        const int h = H2(i, j);
+        prim(Wq[h], Wq[H2N + h], Wq[2 * H2N + h], Wq[3 * H2N + h], Wq[4 * H2N + h], Fq[f], Fq[F5(i + 1, j)],
+             Fq[FPN + f], Fq[FPN + F5(i, j + 1)], Fq[2 * FPN + f], Fq[3 * FPN + f], gamma, Wt);
 #pragma unroll
         for (int k = 0; k < 8; k++) Wq[k * H2N + h] = Wt[k];
-        Fq[h] = bxl;
-        Fq[H2N + h] = byl;
-        Fq[2 * H2N + h] = bzl;
       }
     };
 
     load_plane(z0 - 2);
     load_plane(z0 - 1);
+    __syncthreads();
+    prim_plane(z0 - 2);
+    prim_plane(z0 - 1);
     __syncthreads();
 
     T smax_t = T(0);
@@ -242,12 +274,14 @@ __global__ void __launch_bounds__(NT, 1) update_kernel(DevCtx c) {
       // ---- A
       load_plane(p + 1);
       __syncthreads();
+      prim_plane(p + 1);
+      __syncthreads();
 
       // ---- B: slopes and predictor on the H1 region of plane p
       {
         const int rm = (p - 1 - z0 + 3) % 3, r0 = (p - z0 + 3) % 3, rp = (p + 1 - z0 + 3) % 3;
         const T *Wm = Wr + rm * 8 * H2N, *W0 = Wr + r0 * 8 * H2N, *Wp = Wr + rp * 8 * H2N;
-        const T *F0 = FB + r0 * 3 * H2N, *Fp = FB + rp * 3 * H2N;
+        const T *F0 = FB + ((p - z0 + 2) & 1) * 4 * FPN;
         const int nxx = tx + 2, ncell = (tx + 2) * (ty + 2);
         for (int ci = tid; ci < ncell; ci += NT) {
           const int i = ci % nxx - 1, j = ci / nxx - 1;
@@ -257,11 +291,11 @@ __global__ void __launch_bounds__(NT, 1) update_kernel(DevCtx c) {
           for (int k = 0; k < 8; k++) w8[k] = W0[k * H2N + h];
 #pragma unroll
           for (int k = 0; k < 8; k++) {
-            if (k == BX) dX[k] = F0[H2(i + 1, j)] - F0[h];
+            if (k == BX) dX[k] = F0[F5(i + 1, j)] - F0[F5(i, j)];
             else dX[k] = mc(w8[k] - W0[k * H2N + H2(i - 1, j)], W0[k * H2N + H2(i + 1, j)] - w8[k]);
-            if (k == BY) dY[k] = F0[H2N + H2(i, j + 1)] - F0[H2N + h];
+            if (k == BY) dY[k] = F0[FPN + F5(i, j + 1)] - F0[FPN + F5(i, j)];
             else dY[k] = mc(w8[k] - W0[k * H2N + H2(i, j - 1)], W0[k * H2N + H2(i, j + 1)] - w8[k]);
-            if (k == BZ) dZ[k] = Fp[2 * H2N + h] - F0[2 * H2N + h];
+            if (k == BZ) dZ[k] = F0[3 * FPN + F5(i, j)] - F0[2 * FPN + F5(i, j)];
             else dZ[k] = mc(w8[k] - Wm[k * H2N + h], Wp[k * H2N + h] - w8[k]);
           }
           predict(w8, dX, dY, dZ, gamma, hdt, ws);
@@ -303,7 +337,7 @@ __global__ void __launch_bounds__(NT, 1) update_kernel(DevCtx c) {
             WL[k] = Sws[k * H1N + hl] + half * SdX[k * H1N + hl];
             WR[k] = Sws[k * H1N + hr] - half * SdX[k * H1N + hr];
           }
-          hll<T, 0>(WL, WR, gamma, F, SL, SR);
+          hll<T, 0>(WL, WR, gamma, igm1, F, SL, SR);
           SXc[hr] = SL;
           SXc[H1N + hr] = SR;
           if (j >= 0 && j < ty) {
@@ -322,7 +356,7 @@ __global__ void __launch_bounds__(NT, 1) update_kernel(DevCtx c) {
             WL[k] = Sws[k * H1N + hl] + half * SdY[k * H1N + hl];
             WR[k] = Sws[k * H1N + hr] - half * SdY[k * H1N + hr];
           }
-          hll<T, 1>(WL, WR, gamma, F, SL, SR);
+          hll<T, 1>(WL, WR, gamma, igm1, F, SL, SR);
           SYc[hr] = SL;
           SYc[H1N + hr] = SR;
           if (i >= 0 && i < tx) {
@@ -342,7 +376,7 @@ __global__ void __launch_bounds__(NT, 1) update_kernel(DevCtx c) {
               WL[k] = ZP[k * H1N + h];
               WR[k] = Sws[k * H1N + h] - half * SdZ[k * H1N + h];
             }
-            hll<T, 2>(WL, WR, gamma, F, SL, SR);
+            hll<T, 2>(WL, WR, gamma, igm1, F, SL, SR);
             SZ[h] = SL;
             SZ[H1N + h] = SR;
             if (i >= 0 && i < tx && j >= 0 && j < ty) {
@@ -567,30 +601,31 @@ __global__ void __launch_bounds__(NT, 1) update_kernel(DevCtx c) {
   }
 #undef H2
 #undef H1
+#undef F5
 }
 
-template <typename T, int TX, int TY, int NT>
+template <typename T, int TX, int TY, int NT, int MINB>
 int launch_update(const DevCtx &c, int grid, void *stream) {
   const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
   static bool configured = false;
   if (!configured) {
-    if (cudaFuncSetAttribute(update_kernel<T, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(update_kernel<T, TX, TY, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return DSP_ERR_CUDA;
     configured = true;
   }
-  update_kernel<T, TX, TY, NT><<<grid, NT, smem, (cudaStream_t)stream>>>(c);
+  update_kernel<T, TX, TY, NT, MINB><<<grid, NT, smem, (cudaStream_t)stream>>>(c);
   return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
 }
 
-template <typename T, int TX, int TY, int NT>
+template <typename T, int TX, int TY, int NT, int MINB>
 int update_grid(const DevCtx &c) {
   const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
-  cudaFuncSetAttribute(update_kernel<T, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(update_kernel<T, TX, TY, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, update_kernel<T, TX, TY, NT>, NT, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, update_kernel<T, TX, TY, NT, MINB>, NT, smem);
   if (per < 1) per = 1;
   long long maxwork = (long long)c.np * c.tiles;
   long long g = (long long)nsm * per;
