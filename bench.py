@@ -150,9 +150,9 @@ def sum_over_ranks(td, x):
     return float(t.item())
 
 
-def make_input():
+def make_input(patches=PATCHES):
     from paper_1705_10774_gb300 import ics
-    lay, f = ics.config_turbulence(seed=10774, patches=PATCHES, n=NCELL, mach=2.0)
+    lay, f = ics.config_turbulence(seed=10774, patches=patches, n=NCELL, mach=2.0)
     return lay, f, ics.to_patches(lay, f)
 
 
@@ -189,17 +189,19 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     from paper_1705_10774_gb300 import dispatch as D
     D.load()
-    lay, f, state = make_input()
+    lay, f, state = make_input(args.patches if args.form != "both" else PATCHES)
     state_dev = [torch.from_numpy(a).cuda() for a in state]
     ncells = int(np.prod(lay.base_cells))
     peak, peak_kind = measured_peaks()
 
-    if args.form == "f32":
-        state32 = [a.float() for a in state_dev]
-        g, st, ms = run_form(lay, state32, 1, args.steps, args.warmup, td)
+    if args.form != "both":
+        prec = 1 if args.form == "f32" else 0
+        sd = [a.float() for a in state_dev] if prec else state_dev
+        g, st, ms = run_form(lay, sd, prec, args.steps, args.warmup, td)
         if rank == 0:
-            print(json.dumps({"form": "f32", "ms_per_step": ms / args.steps,
-                              "kernel_ms_avg": st["kernel_ms"] / max(st["kernel_launches"], 1)}))
+            print(json.dumps({"form": args.form, "patches": lay.npatch, "ms_per_step": ms / args.steps,
+                              "kernel_ms_avg": st["kernel_ms"] / max(st["kernel_launches"], 1),
+                              "cell_updates_per_s": st["cell_updates"] / (ms * 1e-3)}))
         return
     with Clocks(local) as clk:
         g, st, ms = run_form(lay, state_dev, 0, args.steps, args.warmup, td)
@@ -362,7 +364,9 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-f32", action="store_true")
     ap.add_argument("--form", default="both", choices=["both", "f64", "f32"],
-                    help="f32: time only the FP32-state form (profiling runs)")
+                    help="f64 / f32: time only that form and print a short line (profiling runs)")
+    ap.add_argument("--patches", type=int, default=PATCHES,
+                    help="patches per axis for --form runs (profiling on a smaller box)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
