@@ -345,3 +345,32 @@ def test_linear_wave_second_order_convergence(kind):
     e = [_wave_error(kind, N) for N in (16, 32, 64)]
     order = np.log2(e[1] / e[2])
     assert order >= 1.8, (kind, e)
+
+
+def test_guard_time_interpolation_weight_and_direction():
+    """A neighbour holding slices at t_a = 0 and t_b = 4h, read by a patch at
+    t = h: the guard value must be S_a + (1/4)(S_b - S_a).  With S_a = 1 and
+    S_b = 2 the patch's own uniform interior (density 1.25) then sees a
+    uniform state and its update leaves it exactly unchanged; a reversed or
+    wrongly scaled weight makes the guards differ and the state move."""
+    lay = ics.cartesian((2, 1, 1), (6, 6, 6))
+    g = 5.0 / 3.0
+    W = lambda rho: [rho, 0.0, 0.0, 0.0, 0.6, 0.0, 0.0, 0.0]
+    def patch_state(rho):
+        f = ics.config_uniform(ics.cartesian(1, 6), W(rho), g)
+        return ics.to_patches(ics.cartesian(1, 6), f)
+    h = 2.0 ** -10
+    o = Oracle(lay.n, lay.lo, gamma=g, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len, time_mode=1)
+    o.set_state(*[np.concatenate([a, a]) for a in patch_state(1.25)])
+    o.set_slot(0, 0, h, *patch_state(1.25))     # the patch at t = h
+    o.set_latest(0, 0)
+    o.set_slot(1, 0, 0.0, *patch_state(1.0))    # neighbour: t_a = 0 ...
+    o.set_slot(1, 1, 4 * h, *patch_state(2.0))  # ... and t_b = 4h (newest)
+    o.set_latest(1, 1)
+    U, bx, by, bz, _ = o.update_patch(0, h)
+    U0 = patch_state(1.25)[0]
+    assert np.array_equal(U, U0)
+    # the same patch next to a neighbour whose interpolated value differs moves
+    o.set_slot(1, 1, 4 * h, *patch_state(3.0))
+    U2 = o.update_patch(0, h)[0]
+    assert not np.array_equal(U2, U0)
