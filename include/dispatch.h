@@ -156,6 +156,30 @@ DSP_API int dsp_get_schedule(dsp_ctx *ctx, dsp_sched_entry *buf, int64_t cap, in
 
 DSP_API int dsp_diagnostics(dsp_ctx *ctx, dsp_diag *out);
 
+/* Maximum number of patches dsp_diagnostics_noalloc accepts. */
+#define DSP_NOALLOC_MAX_PATCHES 16384
+
+/* The same diagnostics as dsp_diagnostics, computed from a state held in the
+ * caller's own device arrays (the dsp_set_state layout: U, bx, by, bz
+ * concatenated over npatch patches of n[0] x n[1] x n[2] cells, cell size dx;
+ * dtype 0 = float64, 1 = float32), without allocating any device memory.
+ * This entry point has no counterpart in the paper; it exists for callers
+ * that cannot call cudaMalloc: a host application that hands all device
+ * memory to its own pool allocator and forbids raw allocations, or a
+ * latency-sensitive loop sharing the GPU with other streams, where
+ * cudaMalloc's implicit device-wide synchronisation would stall the other
+ * work.  Its scratch is a fixed file-scope device array sized for
+ * DSP_NOALLOC_MAX_PATCHES patches (about 1.3 MB on every GPU that loads the
+ * library, held until the process exits).  npatch above that limit, or any
+ * invalid argument, returns DSP_ERR_INVALID_ARG before any work is issued.
+ * The first call on a device looks up the array's device address (that
+ * device must be current; make this first call before any stream capture).
+ * Work is issued on `stream` (a cudaStream_t) and the call returns after it
+ * finished, writing *out on the host.  All calls share the scratch array:
+ * calls whose kernels overlap on one GPU race and may return wrong values. */
+DSP_API int dsp_diagnostics_noalloc(const void *U, const void *bx, const void *by, const void *bz, int32_t dtype,
+                                    int32_t npatch, const int32_t *n, double dx, void *stream, dsp_diag *out);
+
 /* Save the whole dispatcher state (every slice, its time and signal speed,
  * the newest-slice index and last step of every patch) into host memory.
  * With buf == NULL only *used (the required size) is written.  dsp_load

@@ -22,6 +22,7 @@ SOURCES = [
     ("dsp_host.cu", ["-fmad=false"]),
     ("dsp_update_f64.cu", ["-fmad=false"]),
     ("dsp_update_f32.cu", ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]),
+    ("dsp_noalloc.cu", ["-fmad=false"]),
 ]
 
 

@@ -30,7 +30,9 @@ ERRORS = {v: k for k, v in globals().items() if k.startswith("DSP_ERR_")}
 
 EXPORTS = ["dsp_create", "dsp_set_state", "dsp_advance", "dsp_get_state", "dsp_get_times",
            "dsp_get_schedule", "dsp_diagnostics", "dsp_save", "dsp_load", "dsp_last_error",
-           "dsp_destroy"]
+           "dsp_destroy", "dsp_diagnostics_noalloc"]
+
+DSP_NOALLOC_MAX_PATCHES = 16384
 
 
 class dsp_patch_desc(ctypes.Structure):
@@ -100,6 +102,9 @@ def load(build_if_missing: bool = True):
         L.dsp_last_error.restype = ctypes.c_char_p
         L.dsp_destroy.argtypes = [VP]
         L.dsp_destroy.restype = None
+        L.dsp_diagnostics_noalloc.argtypes = [VP, VP, VP, VP, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int32), ctypes.c_double, VP,
+                                              ctypes.POINTER(dsp_diag)]
         for name in EXPORTS:
             if name not in ("dsp_last_error", "dsp_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -232,3 +237,19 @@ class Dispatch:
 
     def load_state(self, blob: bytes):
         self._check(load().dsp_load(self._h, blob, len(blob)))
+
+
+def diagnostics_noalloc(U, bx, by, bz, npatch, n, dx, stream=None):
+    """dsp_diagnostics_noalloc on caller-owned device arrays (torch CUDA
+    tensors in the dsp_set_state layout): the library allocates nothing."""
+    L = load()
+    ptrs = [_addr(a) for a in (U, bx, by, bz)]
+    dt = ptrs[0][2]
+    nn = (ctypes.c_int32 * 3)(*[int(x) for x in n])
+    d = dsp_diag()
+    rc = L.dsp_diagnostics_noalloc(*[p[0] for p in ptrs], dt, int(npatch), nn, float(dx), VP(stream or 0),
+                                   ctypes.byref(d))
+    if rc != 0:
+        raise DispatchError(rc, "dsp_diagnostics_noalloc failed")
+    return dict(mass=d.mass, mom=np.array(d.mom[:]), energy=d.energy, bmean=np.array(d.bmean[:]),
+                max_divb=d.max_divb, max_b=d.max_b)
