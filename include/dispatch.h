@@ -74,8 +74,10 @@ typedef struct {
  *   base_cells   level-0 cells per axis
  *   nguard       guard zones per side (>= 2; the stencil reads two)
  *   nslices      time slices per patch (>= 3)
- *   precision    0: all state and arithmetic in FP64;
- *                1: FP32 state and stencil arithmetic, FP64 times and steps
+ *   precision    0: all state and arithmetic in FP64, no fused multiply-add
+ *                   (bit-identical to a plain FP64 evaluation);
+ *                1: FP32 state and stencil arithmetic, FP64 times and steps;
+ *                2: FP64 state and arithmetic with fused multiply-adds
  *   time_mode    0: one global step per sweep (the smallest patch step);
  *                1: local steps, each patch its own
  *   dt_pow2      must be 1: steps are powers of two, so times are exact

@@ -21,6 +21,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
 SOURCES = [
     ("dsp_host.cu", ["-fmad=false"]),
     ("dsp_update_f64.cu", ["-fmad=false"]),
+    ("dsp_update_f64f.cu", []),
     ("dsp_update_f32.cu", ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]),
     ("dsp_noalloc.cu", ["-fmad=false"]),
 ]

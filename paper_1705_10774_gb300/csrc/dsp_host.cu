@@ -356,6 +356,7 @@ __global__ void diag_kernel(DevCtx c, double *out) {
 
 int launch_update(dsp_ctx *c) {
   if (c->precision == 0) return launch_update_f64(c->d, c->grid_update, c->stream);
+  if (c->precision == 2) return launch_update_f64f(c->d, c->grid_update, c->stream);
   return launch_update_f32(c->d, c->grid_update, c->stream);
 }
 
@@ -409,7 +410,7 @@ int transfer(dsp_ctx *c, int first, int count, const void *U, const void *bx, co
       CK(cudaMemcpyAsync(dZ, bz, es * nZ, cudaMemcpyHostToDevice, c->stream));
     }
   }
-  int rc = c->precision == 0 ? run_xfer<double>(c, first, count, dU, dX, dY, dZ, dtype, dir)
+  int rc = c->precision != 1 ? run_xfer<double>(c, first, count, dU, dX, dY, dZ, dtype, dir)
                              : run_xfer<float>(c, first, count, dU, dX, dY, dZ, dtype, dir);
   if (rc) return rc;
   if (!on_device && dir == 1) {
@@ -440,7 +441,7 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   *out = nullptr;
   if (!patches || !prm || npatch <= 0) return DSP_ERR_INVALID_ARG;
   if (prm->grace != 0.0 || prm->dt_pow2 != 1 || prm->dispatcher != 1) return DSP_ERR_UNSUPPORTED;
-  if (prm->nguard < 2 || prm->nslices < 3 || (prm->precision != 0 && prm->precision != 1) ||
+  if (prm->nguard < 2 || prm->nslices < 3 || prm->precision < 0 || prm->precision > 2 ||
       (prm->time_mode != 0 && prm->time_mode != 1) || !(prm->cfl > 0.0) || !(prm->gamma > 1.0))
     return DSP_ERR_INVALID_ARG;
   const int nx = patches[0].n[0], ny = patches[0].n[1], nz = patches[0].n[2];
@@ -470,7 +471,7 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   c->prm = *prm;
   c->stream = (cudaStream_t)stream;
   c->precision = prm->precision;
-  c->esize = prm->precision == 0 ? 8 : 4;
+  c->esize = prm->precision == 1 ? 4 : 8;
   c->poisoned = 0;
   c->nev = 0;
   DevCtx &d = c->d;
@@ -488,8 +489,8 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.dx = dx;
   d.dt_max = prm->dt_max;
   int TX, TY;
-  if (c->precision == 0) update_tile_f64(&TX, &TY);
-  else update_tile_f32(&TX, &TY);
+  if (c->precision == 1) update_tile_f32(&TX, &TY);
+  else update_tile_f64(&TX, &TY);
   d.tx = TX;
   d.ty = TY;
   d.tz = prm->tile_z > 0 ? std::min(prm->tile_z, nz) : nz;
@@ -570,7 +571,7 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
     delete c;
     return DSP_ERR_CUDA;
   }
-  c->grid_update = c->precision == 0 ? update_grid_f64(d) : update_grid_f32(d);
+  c->grid_update = c->precision == 0 ? update_grid_f64(d) : c->precision == 2 ? update_grid_f64f(d) : update_grid_f32(d);
   *out = c;
   return DSP_OK;
 }
@@ -587,7 +588,7 @@ extern "C" int dsp_set_state(dsp_ctx *c, int32_t first, int32_t count, const voi
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(c->ctl, 0, sizeof(int) * CTL_COUNT, c->stream));
   CK(cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_COUNT, c->stream));
-  if (c->precision == 0) smax_kernel<double><<<count, 256, 0, c->stream>>>(c->d, 0, first, count);
+  if (c->precision != 1) smax_kernel<double><<<count, 256, 0, c->stream>>>(c->d, 0, first, count);
   else smax_kernel<float><<<count, 256, 0, c->stream>>>(c->d, 0, first, count);
   CK(cudaGetLastError());
   rc = read_status(c);
@@ -720,7 +721,7 @@ extern "C" int dsp_diagnostics(dsp_ctx *c, dsp_diag *out) {
   const int np = c->d.np;
   double *dd = nullptr;
   CK(cudaMalloc(&dd, sizeof(double) * 10 * np));
-  if (c->precision == 0) diag_kernel<double><<<np, 256, 0, c->stream>>>(c->d, dd);
+  if (c->precision != 1) diag_kernel<double><<<np, 256, 0, c->stream>>>(c->d, dd);
   else diag_kernel<float><<<np, 256, 0, c->stream>>>(c->d, dd);
   cudaError_t e = cudaGetLastError();
   std::vector<double> h((size_t)10 * np);

@@ -58,6 +58,8 @@ struct DevCtx {
 // Launchers implemented in the precision-specific translation units.
 int launch_update_f64(const DevCtx &c, int grid, void *stream);
 int launch_update_f32(const DevCtx &c, int grid, void *stream);
+int launch_update_f64f(const DevCtx &c, int grid, void *stream);
+int update_grid_f64f(const DevCtx &c);
 int update_grid_f64(const DevCtx &c);
 int update_grid_f32(const DevCtx &c);
 void update_tile_f64(int *tx, int *ty);

@@ -152,6 +152,19 @@ __device__ __forceinline__ void hll(const T WL[8], const T WR[8], T gamma, T igm
   F[4] = Fr[4];
 }
 
+// The two HLL signal speeds of a face alone (same arithmetic as in hll), for
+// faces whose flux is not needed.
+template <typename T, int D>
+__device__ __forceinline__ void hll_speeds(const T WL[8], const T WR[8], T gamma, T &SL, T &SR) {
+  constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
+  const T h = T(0.5);
+  T bn = h * (WL[BX + D] + WR[BX + D]);
+  T cL = cfast(gamma, T(1) / WL[RHO], WL[PR], bn, WL[BX + t1], WL[BX + t2]);
+  T cR = cfast(gamma, T(1) / WR[RHO], WR[PR], bn, WR[BX + t1], WR[BX + t2]);
+  SL = tmin(WL[VX + D] - cL, WR[VX + D] - cR);
+  SR = tmax(WL[VX + D] + cL, WR[VX + D] + cR);
+}
+
 // Upwind HLL edge EMF from the four corner values around an edge (LL: low
 // a and low b side, RL: high a / low b, LR: low a / high b, RR: high/high),
 // with ap/am = max(0, +-S) over the faces touching the edge.

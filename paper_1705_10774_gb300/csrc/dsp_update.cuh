@@ -68,7 +68,9 @@ __device__ __forceinline__ void set_error(const DevCtx &c, int code, int P, long
   }
 }
 
-template <typename T, int TX, int TY, int NT, int MINB>
+// VARIANT only tells apart instantiations compiled with different
+// floating-point contraction flags (FP64 with and without FMA).
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
 __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
   static_assert(TX * TY <= NT, "one updated cell per thread");
   using L = Lay<TX, TY>;
@@ -211,9 +213,9 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
       T *Wq = Wr + rs * 8 * H2N;
       T *Fq = FB + fs * 4 * FPN;
       const int oz = off1(q, nz), lz = q - (oz - 1) * nz;
-      const int nxx = tx + 5, ncell = (tx + 5) * (ty + 5);
-      for (int ci = tid; ci < ncell; ci += NT) {
-        const int i = ci % nxx - 2, j = ci / nxx - 2;
+      for (int ci = tid; ci < (TX + 5) * (TY + 5); ci += NT) {
+        const int i = ci % (TX + 5) - 2, j = ci / (TX + 5) - 2;
+        if (i > tx + 2 || j > ty + 2) continue;
         const int x = x0 + i, y = y0 + j;
         const int f = F5(i, j);
         if (j <= ty + 1) Fq[f] = facex(x, y, q);
@@ -239,9 +241,9 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
       const int rs = (q - z0 + 3) % 3, fs = (q - z0 + 2) & 1;
       T *Wq = Wr + rs * 8 * H2N;
       const T *Fq = FB + fs * 4 * FPN;
-      const int nxx = tx + 4, ncell = (tx + 4) * (ty + 4);
-      for (int ci = tid; ci < ncell; ci += NT) {
-        const int i = ci % nxx - 2, j = ci / nxx - 2;
+      for (int ci = tid; ci < (TX + 4) * (TY + 4); ci += NT) {
+        const int i = ci % (TX + 4) - 2, j = ci / (TX + 4) - 2;
+        if (i > tx + 1 || j > ty + 1) continue;
         const int h = H2(i, j), f = F5(i, j);
         T Wt[8];
         prim(Wq[h], Wq[H2N + h], Wq[2 * H2N + h], Wq[3 * H2N + h], Wq[4 * H2N + h], Fq[f], Fq[F5(i + 1, j)],
@@ -282,9 +284,9 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
         const int rm = (p - 1 - z0 + 3) % 3, r0 = (p - z0 + 3) % 3, rp = (p + 1 - z0 + 3) % 3;
         const T *Wm = Wr + rm * 8 * H2N, *W0 = Wr + r0 * 8 * H2N, *Wp = Wr + rp * 8 * H2N;
         const T *F0 = FB + ((p - z0 + 2) & 1) * 4 * FPN;
-        const int nxx = tx + 2, ncell = (tx + 2) * (ty + 2);
-        for (int ci = tid; ci < ncell; ci += NT) {
-          const int i = ci % nxx - 1, j = ci / nxx - 1;
+        for (int ci = tid; ci < (TX + 2) * (TY + 2); ci += NT) {
+          const int i = ci % (TX + 2) - 1, j = ci / (TX + 2) - 1;
+          if (i > tx || j > ty) continue;
           const int h = H2(i, j);
           T w8[8], dX[8], dY[8], dZ[8], ws[8];
 #pragma unroll
@@ -326,10 +328,21 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
 
       // ---- C: face fluxes
       {
-        // x-faces (i-1/2, j) of plane p, i in [0,tx], j in [-1,ty]
-        const int nxx = tx + 1, n1 = (tx + 1) * (ty + 2);
-        for (int ci = tid; ci < n1; ci += NT) {
-          const int i = ci % nxx, j = ci / nxx - 1;
+        // x-faces (i-1/2, j) of plane p, i in [0,tx]: rows j in [0,ty) need
+        // fluxes and speeds, the halo rows j = -1 and j = ty speeds only
+        for (int ci = tid; ci < (TX + 1) * (TY + 2); ci += NT) {
+          int i, j;
+          const bool full = ci < (TX + 1) * TY;
+          if (full) {
+            i = ci % (TX + 1);
+            j = ci / (TX + 1);
+            if (j >= ty) continue;
+          } else {
+            const int k = ci - (TX + 1) * TY;
+            i = k % (TX + 1);
+            j = k / (TX + 1) == 0 ? -1 : ty;
+          }
+          if (i > tx) continue;
           const int hl = H1(i - 1, j), hr = H1(i, j);
           T WL[8], WR[8], F[5], SL, SR;
 #pragma unroll
@@ -337,18 +350,31 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
             WL[k] = Sws[k * H1N + hl] + half * SdX[k * H1N + hl];
             WR[k] = Sws[k * H1N + hr] - half * SdX[k * H1N + hr];
           }
-          hll<T, 0>(WL, WR, gamma, igm1, F, SL, SR);
-          SXc[hr] = SL;
-          SXc[H1N + hr] = SR;
-          if (j >= 0 && j < ty) {
+          if (full) {
+            hll<T, 0>(WL, WR, gamma, igm1, F, SL, SR);
 #pragma unroll
             for (int k = 0; k < 5; k++) FX[k * H1N + hr] = F[k];
+          } else {
+            hll_speeds<T, 0>(WL, WR, gamma, SL, SR);
           }
+          SXc[hr] = SL;
+          SXc[H1N + hr] = SR;
         }
-        // y-faces (i, j-1/2) of plane p, i in [-1,tx], j in [0,ty]
-        const int nxy = tx + 2, n2 = (tx + 2) * (ty + 1);
-        for (int ci = tid; ci < n2; ci += NT) {
-          const int i = ci % nxy - 1, j = ci / nxy;
+        // y-faces (i, j-1/2) of plane p, j in [0,ty]: columns i in [0,tx)
+        // need fluxes, the halo columns i = -1 and i = tx speeds only
+        for (int ci = tid; ci < (TX + 2) * (TY + 1); ci += NT) {
+          int i, j;
+          const bool full = ci < TX * (TY + 1);
+          if (full) {
+            i = ci % TX;
+            j = ci / TX;
+            if (i >= tx) continue;
+          } else {
+            const int k = ci - TX * (TY + 1);
+            i = k / (TY + 1) == 0 ? -1 : tx;
+            j = k % (TY + 1);
+          }
+          if (j > ty) continue;
           const int hl = H1(i, j - 1), hr = H1(i, j);
           T WL[8], WR[8], F[5], SL, SR;
 #pragma unroll
@@ -356,19 +382,39 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
             WL[k] = Sws[k * H1N + hl] + half * SdY[k * H1N + hl];
             WR[k] = Sws[k * H1N + hr] - half * SdY[k * H1N + hr];
           }
-          hll<T, 1>(WL, WR, gamma, igm1, F, SL, SR);
-          SYc[hr] = SL;
-          SYc[H1N + hr] = SR;
-          if (i >= 0 && i < tx) {
+          if (full) {
+            hll<T, 1>(WL, WR, gamma, igm1, F, SL, SR);
 #pragma unroll
             for (int k = 0; k < 5; k++) FY[k * H1N + hr] = F[k];
+          } else {
+            hll_speeds<T, 1>(WL, WR, gamma, SL, SR);
           }
+          SYc[hr] = SL;
+          SYc[H1N + hr] = SR;
         }
-        // z-faces (i, j, p-1/2) on the H1 region
+        // z-faces (i, j, p-1/2) on the H1 region: the tile's own faces need
+        // fluxes, the ring around them speeds only
         if (it > 0) {
-          const int nxz = tx + 2, n3 = (tx + 2) * (ty + 2);
-          for (int ci = tid; ci < n3; ci += NT) {
-            const int i = ci % nxz - 1, j = ci / nxz - 1;
+          for (int ci = tid; ci < (TX + 2) * (TY + 2); ci += NT) {
+            int i, j;
+            const bool full = ci < TX * TY;
+            if (full) {
+              i = ci % TX;
+              j = ci / TX;
+              if (i >= tx || j >= ty) continue;
+            } else {
+              const int k = ci - TX * TY;
+              if (k < 2 * (TX + 2)) {
+                i = k % (TX + 2) - 1;
+                j = k / (TX + 2) == 0 ? -1 : ty;
+                if (i > tx) continue;
+              } else {
+                const int k2 = k - 2 * (TX + 2);
+                i = k2 / TY == 0 ? -1 : tx;
+                j = k2 % TY;
+                if (j >= ty) continue;
+              }
+            }
             const int h = H1(i, j);
             T WL[8], WR[8], F[5], SL, SR;
 #pragma unroll
@@ -376,13 +422,15 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
               WL[k] = ZP[k * H1N + h];
               WR[k] = Sws[k * H1N + h] - half * SdZ[k * H1N + h];
             }
-            hll<T, 2>(WL, WR, gamma, igm1, F, SL, SR);
-            SZ[h] = SL;
-            SZ[H1N + h] = SR;
-            if (i >= 0 && i < tx && j >= 0 && j < ty) {
+            if (full) {
+              hll<T, 2>(WL, WR, gamma, igm1, F, SL, SR);
 #pragma unroll
               for (int k = 0; k < 5; k++) FZc[k * H1N + h] = F[k];
+            } else {
+              hll_speeds<T, 2>(WL, WR, gamma, SL, SR);
             }
+            SZ[h] = SL;
+            SZ[H1N + h] = SR;
           }
         }
       }
@@ -391,9 +439,9 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
       // ---- D: x- and y-edge EMFs at p-1/2, in-plane divergence of plane p
       if (it > 0) {
         // x-edges (i, j-1/2, p-1/2): i in [0,tx), j in [0,ty]; a = y, b = z
-        const int n1 = tx * (ty + 1);
-        for (int ci = tid; ci < n1; ci += NT) {
-          const int i = ci % tx, j = ci / tx;
+        for (int ci = tid; ci < TX * (TY + 1); ci += NT) {
+          const int i = ci % TX, j = ci / TX;
+          if (i >= tx || j > ty) continue;
           const int hm = H1(i, j - 1), h0 = H1(i, j);
           const T Ell = CX[0 * H1N + hm], Ba_ll = CX[1 * H1N + hm], Bb_ll = CX[2 * H1N + hm];
           const T Erl = CX[3 * H1N + h0], Ba_rl = CX[4 * H1N + h0], Bb_rl = CX[5 * H1N + h0];
@@ -414,9 +462,9 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
           EXc[h0] = emf(Ell, Erl, Elr, Err, Ba_ll, Ba_rl, lr_by, rr_by, Bb_ll, Bb_rl, lr_bz, rr_bz, apa, ama, apb, amb);
         }
         // y-edges (i-1/2, j, p-1/2): i in [0,tx], j in [0,ty); a = z, b = x
-        const int nxx = tx + 1, n2 = (tx + 1) * ty;
-        for (int ci = tid; ci < n2; ci += NT) {
-          const int i = ci % nxx, j = ci / nxx;
+        for (int ci = tid; ci < (TX + 1) * TY; ci += NT) {
+          const int i = ci % (TX + 1), j = ci / (TX + 1);
+          if (i > tx || j >= ty) continue;
           const int hm = H1(i - 1, j), h0 = H1(i, j);
           const T Ell = CY[0 * H1N + hm], Ba_ll = CY[1 * H1N + hm], Bb_ll = CY[2 * H1N + hm];
           const T Elr = CY[3 * H1N + h0], Ba_lr = CY[4 * H1N + h0], Bb_lr = CY[5 * H1N + h0];
@@ -437,9 +485,9 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
           EYc[h0] = emf(Ell, Erl, Elr, Err, Ba_ll, rl_bz, Ba_lr, rr_bz, Bb_ll, rl_bx, Bb_lr, rr_bx, apa, ama, apb, amb);
         }
         if (p < z0 + tz) {
-          const int n3 = tx * ty;
-          for (int ci = tid; ci < n3; ci += NT) {
-            const int i = ci % tx, j = ci / tx;
+          for (int ci = tid; ci < TX * TY; ci += NT) {
+            const int i = ci % TX, j = ci / TX;
+            if (i >= tx || j >= ty) continue;
             const int h = H1(i, j), hx = H1(i + 1, j), hy = H1(i, j + 1);
 #pragma unroll
             for (int k = 0; k < 5; k++)
@@ -451,8 +499,10 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
 
       // ---- E: update plane p-1 and the z-faces at p-1/2
       const bool upd = it >= 2;
-      if (upd && tid < tx * ty) {
-        const int i = tid % tx, j = tid / tx, h = H1(i, j);
+      const int ui = tid % TX, uj = tid / TX;
+      const bool mine = tid < TX * TY && ui < tx && uj < ty;
+      if (upd && mine) {
+        const int i = ui, j = uj, h = H1(i, j);
         const long long ci = ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i);
 #pragma unroll
         for (int k = 0; k < 5; k++) {
@@ -463,17 +513,17 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
       }
       if (upd) {
         const int k = p - 1;
-        const int nxx = tx + 1, n1 = (tx + 1) * ty;
-        for (int ci = tid; ci < n1; ci += NT) {
-          const int i = ci % nxx, j = ci / nxx, h = H1(i, j);
+        for (int ci = tid; ci < (TX + 1) * TY; ci += NT) {
+          const int i = ci % (TX + 1), j = ci / (TX + 1), h = H1(i, j);
+          if (i > tx || j >= ty) continue;
           const long long id = ((long long)k * ny + (y0 + j)) * (nx + 1) + (x0 + i);
           const T b = own[ofx + id] - dtdx * ((EZ[H1(i, j + 1)] - EZ[h]) - (EYc[h] - EYp[h]));
           NBX[h] = b;
           dst[ofx + id] = b;
         }
-        const int n2 = tx * (ty + 1);
-        for (int ci = tid; ci < n2; ci += NT) {
-          const int i = ci % tx, j = ci / tx, h = H1(i, j);
+        for (int ci = tid; ci < TX * (TY + 1); ci += NT) {
+          const int i = ci % TX, j = ci / TX, h = H1(i, j);
+          if (i >= tx || j > ty) continue;
           const long long id = ((long long)k * (ny + 1) + (y0 + j)) * nx + (x0 + i);
           const T b = own[ofy + id] - dtdx * ((EXc[h] - EXp[h]) - (EZ[H1(i + 1, j)] - EZ[h]));
           NBY[h] = b;
@@ -481,9 +531,9 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
         }
       }
       if (it >= 1) {
-        const int n3 = tx * ty;
-        for (int ci = tid; ci < n3; ci += NT) {
-          const int i = ci % tx, j = ci / tx, h = H1(i, j);
+        for (int ci = tid; ci < TX * TY; ci += NT) {
+          const int i = ci % TX, j = ci / TX, h = H1(i, j);
+          if (i >= tx || j >= ty) continue;
           const long long id = ((long long)p * ny + (y0 + j)) * nx + (x0 + i);
           const T b = own[ofz + id] - dtdx * ((EYc[H1(i + 1, j)] - EYc[h]) - (EXc[H1(i, j + 1)] - EXc[h]));
           NBZc[h] = b;
@@ -493,8 +543,8 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
       __syncthreads();
 
       // ---- F: signal speed of plane p-1, z-edge EMFs of plane p, carried values
-      if (upd && tid < tx * ty) {
-        const int i = tid % tx, j = tid / tx, h = H1(i, j);
+      if (upd && mine) {
+        const int i = ui, j = uj, h = H1(i, j);
         T Wn[8];
         prim(unew[0], unew[1], unew[2], unew[3], unew[4], NBX[h], NBX[H1(i + 1, j)], NBY[h], NBY[H1(i, j + 1)],
              NBZp[h], NBZc[h], gamma, Wn);
@@ -504,9 +554,9 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
       }
       if (p >= z0 && p < z0 + tz) {
         // z-edges (i-1/2, j-1/2, p): i in [0,tx], j in [0,ty]; a = x, b = y
-        const int nxx = tx + 1, n1 = (tx + 1) * (ty + 1);
-        for (int ci = tid; ci < n1; ci += NT) {
-          const int i = ci % nxx, j = ci / nxx;
+        for (int ci = tid; ci < (TX + 1) * (TY + 1); ci += NT) {
+          const int i = ci % (TX + 1), j = ci / (TX + 1);
+          if (i > tx || j > ty) continue;
           const int hll_ = H1(i - 1, j - 1), hrl = H1(i, j - 1), hlr = H1(i - 1, j), hrr = H1(i, j);
           const T ll_vx = (Sws[VX * H1N + hll_] + half * SdX[VX * H1N + hll_]) + half * SdY[VX * H1N + hll_];
           const T ll_vy = (Sws[VY * H1N + hll_] + half * SdX[VY * H1N + hll_]) + half * SdY[VY * H1N + hll_];
@@ -538,9 +588,9 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
       {
         // values of plane p carried to the next plane: its upper z-face
         // state and its +z corner values for the x- and y-edges above it
-        const int nxx = tx + 2, n2 = (tx + 2) * (ty + 2);
-        for (int ci = tid; ci < n2; ci += NT) {
-          const int i = ci % nxx - 1, j = ci / nxx - 1, h = H1(i, j);
+        for (int ci = tid; ci < (TX + 2) * (TY + 2); ci += NT) {
+          const int i = ci % (TX + 2) - 1, j = ci / (TX + 2) - 1, h = H1(i, j);
+          if (i > tx || j > ty) continue;
 #pragma unroll
           for (int k = 0; k < 8; k++) ZP[k * H1N + h] = Sws[k * H1N + h] + half * SdZ[k * H1N + h];
           {  // x-edges: a = y, b = z; corners (+y,+z) and (-y,+z)
@@ -604,28 +654,28 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
 #undef F5
 }
 
-template <typename T, int TX, int TY, int NT, int MINB>
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
 int launch_update(const DevCtx &c, int grid, void *stream) {
   const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
   static bool configured = false;
   if (!configured) {
-    if (cudaFuncSetAttribute(update_kernel<T, TX, TY, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(update_kernel<T, TX, TY, NT, MINB, VARIANT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return DSP_ERR_CUDA;
     configured = true;
   }
-  update_kernel<T, TX, TY, NT, MINB><<<grid, NT, smem, (cudaStream_t)stream>>>(c);
+  update_kernel<T, TX, TY, NT, MINB, VARIANT><<<grid, NT, smem, (cudaStream_t)stream>>>(c);
   return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
 }
 
-template <typename T, int TX, int TY, int NT, int MINB>
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
 int update_grid(const DevCtx &c) {
   const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
-  cudaFuncSetAttribute(update_kernel<T, TX, TY, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(update_kernel<T, TX, TY, NT, MINB, VARIANT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, update_kernel<T, TX, TY, NT, MINB>, NT, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, update_kernel<T, TX, TY, NT, MINB, VARIANT>, NT, smem);
   if (per < 1) per = 1;
   long long maxwork = (long long)c.np * c.tiles;
   long long g = (long long)nsm * per;

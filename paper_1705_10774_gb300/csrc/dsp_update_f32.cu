@@ -5,9 +5,9 @@
 namespace dsp {
 constexpr int TX32 = 16, TY32 = 8, NT32 = 256, MB32 = 2;
 int launch_update_f32(const DevCtx &c, int grid, void *stream) {
-  return launch_update<float, TX32, TY32, NT32, MB32>(c, grid, stream);
+  return launch_update<float, TX32, TY32, NT32, MB32, 0>(c, grid, stream);
 }
-int update_grid_f32(const DevCtx &c) { return update_grid<float, TX32, TY32, NT32, MB32>(c); }
+int update_grid_f32(const DevCtx &c) { return update_grid<float, TX32, TY32, NT32, MB32, 0>(c); }
 void update_tile_f32(int *tx, int *ty) {
   *tx = TX32;
   *ty = TY32;

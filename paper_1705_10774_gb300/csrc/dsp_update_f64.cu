@@ -5,9 +5,9 @@
 namespace dsp {
 constexpr int TX64 = 16, TY64 = 8, NT64 = 256, MB64 = 1;
 int launch_update_f64(const DevCtx &c, int grid, void *stream) {
-  return launch_update<double, TX64, TY64, NT64, MB64>(c, grid, stream);
+  return launch_update<double, TX64, TY64, NT64, MB64, 0>(c, grid, stream);
 }
-int update_grid_f64(const DevCtx &c) { return update_grid<double, TX64, TY64, NT64, MB64>(c); }
+int update_grid_f64(const DevCtx &c) { return update_grid<double, TX64, TY64, NT64, MB64, 0>(c); }
 void update_tile_f64(int *tx, int *ty) {
   *tx = TX64;
   *ty = TY64;

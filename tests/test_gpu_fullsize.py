@@ -28,13 +28,15 @@ def patch_slices(lay, arrays, P):
     return [a[P * s:(P + 1) * s] for a, s in zip(arrays, sizes)]
 
 
-def test_turbulence_256cubed_sampled_patches_fp64():
-    """512 patches of 32^3, global steps: after 3 steps the oracle takes the
-    GPU state, recomputes the global step and the 4th update of 8 patches."""
+@pytest.mark.parametrize("precision", [0, 2])
+def test_turbulence_256cubed_sampled_patches_fp64(precision):
+    """512 patches of 32^3, global steps, both FP64 builds: after 3 steps the
+    oracle takes the GPU state, recomputes the global step and the 4th update
+    of 8 patches."""
     lay, f = ics.config_turbulence(seed=10774, patches=8, n=32, mach=2.0)
     state = ics.to_patches(lay, f)
     kw = dict(gamma=f.gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
-    g = Dispatch(lay.n, lay.lo, time_mode=0, **kw)
+    g = Dispatch(lay.n, lay.lo, time_mode=0, precision=precision, **kw)
     g.set_state(*[torch.from_numpy(a).cuda() for a in state])
     g.advance(max_sweeps=3)
     snap = g.get_state()
@@ -112,3 +114,25 @@ def test_local_steps_4096_patches_sampled_sweep_fp64():
         got = patch_slices(lay, after, int(P))
         for a, b in zip(got, ref):
             assert rel_linf(a, b) <= TOL64
+
+
+def test_fp64_fma_build_after_100_steps_of_the_benchmark():
+    """The benchmark's 100 global steps of the 256^3 workload with both FP64
+    builds: the FMA-free build equals the oracle bit for bit (pinned above and
+    in the parity tests), so its result stands for the oracle's; the FMA build
+    must stay within 1e-11 relative L-infinity per field, with the same
+    steps."""
+    lay, f = ics.config_turbulence(seed=10774, patches=8, n=32, mach=2.0)
+    state = [torch.from_numpy(a).cuda() for a in ics.to_patches(lay, f)]
+    kw = dict(gamma=f.gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len, time_mode=0)
+    res = []
+    for prec in (0, 2):
+        g = Dispatch(lay.n, lay.lo, precision=prec, **kw)
+        g.set_state(*state)
+        g.advance(max_sweeps=100)
+        res.append((g.get_state(), g.times()))
+        g.close()
+    (a, ta), (b, tb) = res
+    assert np.array_equal(ta[0], tb[0]) and np.array_equal(ta[1], tb[1])
+    for x, y in zip(b, a):
+        assert rel_linf(x, y) <= TOL64

@@ -40,11 +40,25 @@ def pair(lay, f, gpu_extra=None, **common):
     return g, o
 
 
-def assert_same(g, o, tol=TOL64):
+def state_error(out, ref):
+    """Relative L-infinity over the whole conserved state: the largest
+    difference in any field over the largest magnitude of any field.  Used for
+    the FMA build on inputs whose momentum and transverse field are pure
+    1e-6 perturbations, where a per-field norm measures FP64 rounding of O(1)
+    flux terms against the perturbation."""
+    num = max(float(np.max(np.abs(a - b))) for a, b in zip(out, ref))
+    den = max(float(np.max(np.abs(b))) for b in ref)
+    return num / den
+
+
+def assert_same(g, o, tol=TOL64, whole_state=False):
     out = g.get_state()
     ref = o.get_state()
-    for name, a, b in zip(("U", "bx", "by", "bz"), out, ref):
-        assert rel_linf(a, b) <= tol, (name, rel_linf(a, b))
+    if whole_state:
+        assert state_error(out, ref) <= tol, state_error(out, ref)
+    else:
+        for name, a, b in zip(("U", "bx", "by", "bz"), out, ref):
+            assert rel_linf(a, b) <= tol, (name, rel_linf(a, b))
     assert np.array_equal(g.times()[0], o.get_times()[0])
 
 
@@ -90,6 +104,27 @@ def test_single_patch_is_its_own_neighbour():
     g.advance(max_sweeps=5)
     o.advance(max_sweeps=5)
     assert_same(g, o)
+
+
+@pytest.mark.parametrize("lts", [False, True])
+def test_fp64_fma_form_within_tolerance(lts):
+    """FP64 with fused multiply-adds (precision 2): rounding differs from the
+    oracle's; the result must stay within 1e-11 relative L-infinity (over the
+    whole state on the 1e-6-amplitude wave input, per field under local
+    steps) and the schedule must be identical."""
+    if lts:
+        lay, f = _lts_case()
+        common, run = dict(time_mode=1), dict(t_end=0.003)
+    else:
+        lay, f = ics.config_linear_waves()
+        common, run = dict(time_mode=0), dict(max_sweeps=20)
+    g, o = pair(lay, f, gpu_extra=dict(precision=2), **common)
+    g.advance(**run)
+    o.advance(**run)
+    assert_same(g, o, whole_state=not lts)
+    gp, gt, gd = g.schedule()
+    op, ot, od = o.schedule()
+    assert np.array_equal(gp, op) and np.array_equal(gt, ot) and np.array_equal(gd, od)
 
 
 def _lts_case():
