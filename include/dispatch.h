@@ -82,11 +82,17 @@ typedef struct {
  *                1: local steps, each patch its own
  *   dt_pow2      must be 1: steps are powers of two, so times are exact
  *   dispatcher   1: sweeps over the ready set (one kernel pair per sweep);
- *                0: reserved for a persistent device ready queue
+ *                0: persistent device ready queue (local steps only): one
+ *                   launch runs every update to t_end; blocks claim (patch,
+ *                   tile) work, and the block finishing a patch publishes it
+ *                   and queues every neighbour it made ready
  *   tile_x, tile_y, tile_z   update tile in cells (0 = defaults)
  *   sched_capacity  entries kept in the schedule log (0 = no log)
  *   timing       1: time every update-kernel launch with CUDA events on the
- *                context's stream and report the total in dsp_stats */
+ *                context's stream and report the total in dsp_stats
+ *   wait_budget  ready-queue dispatcher only: SM clock cycles a device wait
+ *                may spin without progress before the run stops with
+ *                DSP_ERR_TIMEOUT (0 = default, about two seconds) */
 typedef struct {
   double gamma, cfl, t0, dt_max, grace;
   double box_lo[3], box_len[3];
@@ -95,6 +101,7 @@ typedef struct {
   int32_t tile_x, tile_y, tile_z;
   int64_t sched_capacity;
   int32_t timing;
+  int64_t wait_budget;
 } dsp_params;
 
 /* Counters of one dsp_advance call.  kernel_ms and kernel_launches are the

@@ -23,6 +23,7 @@
 #include <string>
 #include <vector>
 
+#include "dsp_dispatch.cuh"
 #include "dsp_internal.h"
 #include "dsp_physics.cuh"
 
@@ -45,6 +46,9 @@ struct dsp_ctx {
   unsigned long long *smax_new;
   long long *cnt;
   dsp_sched_entry *sched;
+  int *q_patch, *q_reads, *p_state, *tiles_done;
+  double *q_dt;
+  unsigned long long *q_seq, *q_free, *q_ctl;
   void *staging;
   size_t staging_bytes;
   int *h_ctl;  // pinned
@@ -78,47 +82,6 @@ int fail(dsp_ctx *c, int code, const char *fmt, ...) {
   } while (0)
 
 // ------------------------------------------------------------------ kernels
-
-// Local Courant step of patch P at time t (all FP64): the signal speed is the
-// largest over P's newest slice and every neighbour slice its guard fill
-// reads; the step is the power of two not above C dx / s, capped by dt_max,
-// halved until it divides t, and clipped to t_end.
-__device__ int patch_dt(const DevCtx &c, int P, double t, double t_end, double *out) {
-  const int ns = c.ns;
-  double M = c.smax_slot[(long long)P * ns + c.latest[P]];
-  for (int k = c.nbl_off[P]; k < c.nbl_off[P + 1]; k++) {
-    const int N = c.nbl[k];
-    const int L = c.latest[N];
-    const double tq = c.t_slot[(long long)N * ns + L];
-    if (tq == t) {
-      M = fmax(M, c.smax_slot[(long long)N * ns + L]);
-    } else {
-      const int Pv = (L + ns - 1) % ns;
-      const double ta = c.t_slot[(long long)N * ns + Pv];
-      if (ta == t) {
-        M = fmax(M, c.smax_slot[(long long)N * ns + Pv]);
-      } else if (ta < t && t < tq) {
-        M = fmax(M, c.smax_slot[(long long)N * ns + Pv]);
-        M = fmax(M, c.smax_slot[(long long)N * ns + L]);
-      } else {
-        return DSP_ERR_BRACKET;
-      }
-    }
-  }
-  const double dtc = c.cfl * c.dx / M;
-  int e;
-  frexp(dtc, &e);
-  double dt = ldexp(1.0, e - 1);
-  if (c.dt_max > 0.0 && dt > c.dt_max) dt = c.dt_max;
-  int guard = 0;
-  while (fmod(t, dt) != 0.0) {
-    dt = dt * 0.5;
-    if (++guard > 1200 || !(dt > 0.0)) return DSP_ERR_INVALID_ARG;
-  }
-  if (dt > t_end - t) dt = t_end - t;
-  *out = dt;
-  return DSP_OK;
-}
 
 __device__ void set_status(const DevCtx &c, int code, int P) {
   if (atomicCAS(&c.ctl[CTL_STATUS], 0, code) == 0) c.ctl[CTL_ERRP] = P;
@@ -175,13 +138,9 @@ __global__ void __launch_bounds__(PLAN_NT) plan_kernel(DevCtx c, double t_end, i
       const double t = c.t_slot[(long long)P * ns + c.latest[P]];
       if (t < t_end) {
         s_notdone = 1;
-        bool ready = true;
-        for (int k = c.nbl_off[P]; k < c.nbl_off[P + 1]; k++) {
-          const int N = c.nbl[k];
-          if (!(t <= c.t_slot[(long long)N * ns + c.latest[N]])) { ready = false; break; }
-        }
-        if (ready) {
-          const int rc = patch_dt(c, P, t, t_end, &dtP);
+        double tr;
+        if (is_ready<false>(c, P, t_end, &tr)) {
+          const int rc = patch_dt<false>(c, P, t, t_end, &dtP);
           if (rc != DSP_OK) set_status(c, rc, P);
           else flag = 1;
         }
@@ -292,6 +251,42 @@ __global__ void reset_times_kernel(DevCtx c, int first, int count, double t0) {
   }
 }
 
+// Seeds the persistent ready queue from the ready list the plan kernel just
+// built, and resets the queue's control words (one block).
+__global__ void queue_init_kernel(DevCtx c, double t_end) {
+  const int C = 2 * c.np;
+  const int nr = c.ctl[CTL_NREADY];
+  for (int s = threadIdx.x; s < C; s += blockDim.x) {
+    c.q_free[s] = (unsigned long long)s;
+    c.q_seq[s] = ~0ull;
+    c.q_reads[s] = 0;
+  }
+  for (int P = threadIdx.x; P < c.np; P += blockDim.x) {
+    c.p_state[P] = 0;
+    c.tiles_done[P] = 0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+    c.q_patch[r] = c.R[r];
+    c.q_dt[r] = c.dtR[r];
+    c.q_seq[r] = (unsigned long long)r;
+    c.p_state[c.R[r]] = 1;
+  }
+  __shared__ int done;
+  if (threadIdx.x == 0) done = 0;
+  __syncthreads();
+  for (int P = threadIdx.x; P < c.np; P += blockDim.x)
+    if (!(c.t_slot[(long long)P * c.ns + c.latest[P]] < t_end)) atomicAdd(&done, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c.q_ctl[0] = 0;
+    c.q_ctl[1] = (unsigned long long)nr;
+    c.q_ctl[2] = (unsigned long long)done;
+    c.ctl[CTL_NREADY] = 0;
+    if (nr == 0 && done < c.np) set_status(c, DSP_ERR_DEADLOCK, -1);
+  }
+}
+
 struct NSum {
   double s, c;
 };
@@ -352,6 +347,12 @@ __global__ void diag_kernel(DevCtx c, double *out) {
     out[(long long)P * 10 + 8] = md;
     out[(long long)P * 10 + 9] = mm;
   }
+}
+
+int launch_queue(dsp_ctx *c, double t_end) {
+  if (c->precision == 0) return launch_queue_f64(c->d, c->grid_update, t_end, c->stream);
+  if (c->precision == 2) return launch_queue_f64f(c->d, c->grid_update, t_end, c->stream);
+  return launch_queue_f32(c->d, c->grid_update, t_end, c->stream);
 }
 
 int launch_update(dsp_ctx *c) {
@@ -424,8 +425,10 @@ int transfer(dsp_ctx *c, int first, int count, const void *U, const void *bx, co
 }
 
 void free_all(dsp_ctx *c) {
-  void *ptrs[] = {c->slab,  c->t_slot, c->smax_slot, c->dt_last, c->dtR,      c->latest, c->nb27_d, c->nbl_off_d,
-                  c->nbl_d, c->R,      c->ctl,       c->smax_new, c->cnt,     c->sched,  c->staging};
+  void *ptrs[] = {c->slab,    c->t_slot,  c->smax_slot, c->dt_last, c->dtR,     c->latest,  c->nb27_d,
+                  c->nbl_off_d, c->nbl_d, c->R,       c->ctl,     c->smax_new, c->cnt,    c->sched,
+                  c->staging, c->q_patch, c->q_reads, c->p_state, c->tiles_done, c->q_dt, c->q_seq,
+                  c->q_free,  c->q_ctl};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
@@ -440,7 +443,9 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   if (!out) return DSP_ERR_INVALID_ARG;
   *out = nullptr;
   if (!patches || !prm || npatch <= 0) return DSP_ERR_INVALID_ARG;
-  if (prm->grace != 0.0 || prm->dt_pow2 != 1 || prm->dispatcher != 1) return DSP_ERR_UNSUPPORTED;
+  if (prm->grace != 0.0 || prm->dt_pow2 != 1) return DSP_ERR_UNSUPPORTED;
+  if (prm->dispatcher != 0 && prm->dispatcher != 1) return DSP_ERR_INVALID_ARG;
+  if (prm->dispatcher == 0 && prm->time_mode != 1) return DSP_ERR_UNSUPPORTED;  // a global step needs sweeps
   if (prm->nguard < 2 || prm->nslices < 3 || prm->precision < 0 || prm->precision > 2 ||
       (prm->time_mode != 0 && prm->time_mode != 1) || !(prm->cfl > 0.0) || !(prm->gamma > 1.0))
     return DSP_ERR_INVALID_ARG;
@@ -532,6 +537,14 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
             alloc((void **)&c->smax_new, sizeof(unsigned long long) * npatch) &&
             alloc((void **)&c->cnt, sizeof(long long) * CNT_COUNT) &&
             alloc((void **)&c->sched, sizeof(dsp_sched_entry) * std::max<long long>(1, cap));
+  if (ok && prm->dispatcher == 0) {
+    const size_t C = 2 * (size_t)npatch;
+    ok = alloc((void **)&c->q_patch, sizeof(int) * C) && alloc((void **)&c->q_dt, sizeof(double) * C) &&
+         alloc((void **)&c->q_seq, sizeof(unsigned long long) * C) &&
+         alloc((void **)&c->q_free, sizeof(unsigned long long) * C) && alloc((void **)&c->q_reads, sizeof(int) * C) &&
+         alloc((void **)&c->q_ctl, sizeof(unsigned long long) * 4) && alloc((void **)&c->p_state, sizeof(int) * npatch) &&
+         alloc((void **)&c->tiles_done, sizeof(int) * npatch);
+  }
   if (ok && cudaMallocHost((void **)&c->h_ctl, sizeof(int) * CTL_COUNT) != cudaSuccess) ok = false;
   if (!ok) {
     free_all(c);
@@ -553,6 +566,15 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.cnt = c->cnt;
   d.sched = c->sched;
   d.sched_cap = cap;
+  d.q_patch = c->q_patch;
+  d.q_dt = c->q_dt;
+  d.q_seq = c->q_seq;
+  d.q_free = c->q_free;
+  d.q_reads = c->q_reads;
+  d.q_ctl = c->q_ctl;
+  d.p_state = c->p_state;
+  d.tiles_done = c->tiles_done;
+  d.wait_budget = prm->wait_budget > 0 ? prm->wait_budget : 4000000000ll;  // ~2 s of SM clock
   cudaError_t e = cudaMemcpyAsync(c->nb27_d, c->nb27.data(), sizeof(int) * c->nb27.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->nbl_off_d, c->nbl_off.data(), sizeof(int) * c->nbl_off.size(), cudaMemcpyHostToDevice, c->stream);
@@ -598,6 +620,59 @@ extern "C" int dsp_set_state(dsp_ctx *c, int32_t first, int32_t count, const voi
   return DSP_OK;
 }
 
+// Persistent ready-queue dispatcher: one plan step seeds the queue with the
+// patches ready now, then one persistent launch runs every update until all
+// patches reach t_end; each finishing patch publishes its new slice and
+// queues itself and any neighbour it made ready.
+int advance_queue(dsp_ctx *c, double t_end, const long long *c0, dsp_stats *out) {
+  if (!(t_end < INFINITY)) return fail(c, DSP_ERR_INVALID_ARG, "the ready-queue dispatcher needs a finite t_end");
+  const bool timing = c->prm.timing != 0;
+  if (timing && c->nev == 0) {
+    for (int i = 0; i < 2; i++) CK(cudaEventCreate(&c->ev[i]));
+    c->nev = 2;
+  }
+  plan_kernel<<<1, PLAN_NT, 0, c->stream>>>(c->d, t_end, 0, 0);
+  CK(cudaGetLastError());
+  queue_init_kernel<<<1, 1024, 0, c->stream>>>(c->d, t_end);
+  CK(cudaGetLastError());
+  if (timing) CK(cudaEventRecord(c->ev[0], c->stream));
+  int rc = launch_queue(c, t_end);
+  if (rc) return fail(c, rc, "queue kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  if (timing) CK(cudaEventRecord(c->ev[1], c->stream));
+  rc = read_status(c);
+  if (rc) return rc;
+  float ms = 0.f;
+  if (timing) CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+  long long c1[CNT_COUNT];
+  CK(cudaMemcpyAsync(c1, c->cnt, sizeof c1, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const int st = c->h_ctl[CTL_STATUS];
+  if (out) {
+    out->patch_updates = c1[CNT_PATCH_UPDATES] - c0[CNT_PATCH_UPDATES];
+    out->cell_updates = c1[CNT_CELL_UPDATES] - c0[CNT_CELL_UPDATES];
+    out->sweeps = 0;
+    out->fallbacks = c1[CNT_FALLBACKS] - c0[CNT_FALLBACKS];
+    out->status = st;
+    out->kernel_ms = timing ? ms : 0.0;
+    out->kernel_launches = 1;
+    out->plan_launches = 2;
+    std::vector<double> t((size_t)c->d.np);
+    if (dsp_get_times(c, t.data(), nullptr) == DSP_OK) {
+      out->t_min = *std::min_element(t.begin(), t.end());
+      out->t_max = *std::max_element(t.begin(), t.end());
+    }
+  }
+  if (st != 0) {
+    const char *what = st == DSP_ERR_UNPHYSICAL ? "rho <= 0 or p <= 0 in a new state"
+                       : st == DSP_ERR_TIMEOUT   ? "a ready-queue wait ran out of its budget"
+                       : st == DSP_ERR_DEADLOCK  ? "no patch is ready but some are behind t_end"
+                       : st == DSP_ERR_BRACKET   ? "neighbour slices do not bracket a guard-zone time"
+                                                 : "device error";
+    return fail(c, st, "%s (patch %d, cell %d)", what, c->h_ctl[CTL_ERRP], c->h_ctl[CTL_ERRC]);
+  }
+  return DSP_OK;
+}
+
 extern "C" int dsp_advance(dsp_ctx *c, double t_end, int64_t max_sweeps, dsp_stats *out) {
   if (!c) return DSP_ERR_INVALID_ARG;
   if (c->poisoned) return fail(c, DSP_ERR_INVALID_ARG, "context is poisoned by an earlier error");
@@ -607,6 +682,7 @@ extern "C" int dsp_advance(dsp_ctx *c, double t_end, int64_t max_sweeps, dsp_sta
   CK(cudaMemcpyAsync(c0, c->cnt, sizeof c0, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemsetAsync(c->ctl + CTL_DONE, 0, sizeof(int), c->stream));
   const int global_mode = c->prm.time_mode == 0;
+  if (c->prm.dispatcher == 0) return advance_queue(c, t_end, c0, out);
   const int batch = 32;
   long long done_sweeps = 0, plans = 0, kl = 0;
   double kms = 0.0;

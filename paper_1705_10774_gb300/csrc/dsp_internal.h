@@ -53,6 +53,16 @@ struct DevCtx {
   long long *cnt;          // [CNT_COUNT]
   dsp_sched_entry *sched;  // [sched_cap]
   long long sched_cap;
+  // persistent ready queue (dispatcher 0): a ring of np entries
+  int *q_patch;                    // [np] patch of each ring slot
+  double *q_dt;                    // [np] its step
+  unsigned long long *q_seq;       // [np] sequence number published in the slot
+  unsigned long long *q_free;      // [np] sequence number the slot may take next
+  int *q_reads;                    // [np] tiles of the slot's entry claimed so far
+  unsigned long long *q_ctl;       // [4]: 0 next work item, 1 next entry, 2 patches done
+  int *p_state;                    // [np] 0 idle, 1 queued or being updated
+  int *tiles_done;                 // [np]
+  long long wait_budget;           // clock64 cycles a wait may spin before DSP_ERR_TIMEOUT
 };
 
 // Launchers implemented in the precision-specific translation units.
@@ -60,6 +70,9 @@ int launch_update_f64(const DevCtx &c, int grid, void *stream);
 int launch_update_f32(const DevCtx &c, int grid, void *stream);
 int launch_update_f64f(const DevCtx &c, int grid, void *stream);
 int update_grid_f64f(const DevCtx &c);
+int launch_queue_f64(const DevCtx &c, int grid, double t_end, void *stream);
+int launch_queue_f64f(const DevCtx &c, int grid, double t_end, void *stream);
+int launch_queue_f32(const DevCtx &c, int grid, double t_end, void *stream);
 int update_grid_f64(const DevCtx &c);
 int update_grid_f32(const DevCtx &c);
 void update_tile_f64(int *tx, int *ty);

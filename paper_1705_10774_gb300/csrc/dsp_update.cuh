@@ -24,6 +24,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "dsp_dispatch.cuh"
 #include "dsp_internal.h"
 #include "dsp_physics.cuh"
 
@@ -68,15 +69,25 @@ __device__ __forceinline__ void set_error(const DevCtx &c, int code, int P, long
   }
 }
 
-// VARIANT only tells apart instantiations compiled with different
-// floating-point contraction flags (FP64 with and without FMA).
-template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
-__global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
+// Small per-block scratch shared by all tiles a block processes.
+template <typename T, int NT>
+struct TileShared {
+  const T *srcA[27];
+  const T *srcB[27];
+  T wgt[27];
+  double red[NT / 32];
+  int fallback;
+};
+
+// Advance one tile of patch P by dt (all threads of the block take part).
+// On return the tile's new cells, faces and signal speed are written.  CONC:
+// other blocks publish patch times concurrently (ready-queue dispatcher).
+template <typename T, int TX, int TY, int NT, bool CONC>
+__device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const double dt, const int tile, T *sm,
+                                             TileShared<T, NT> &S) {
   static_assert(TX * TY <= NT, "one updated cell per thread");
   using L = Lay<TX, TY>;
   constexpr int H2N = L::H2N, H1N = L::H1N, FPN = L::FPN;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T *sm = reinterpret_cast<T *>(smraw);
   T *const Wr = sm + L::oW;
   T *const FB = sm + L::oFB;
   T *const Sws = sm + L::oWS;
@@ -100,11 +111,11 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
   T *const NBY = sm + L::oNBY;
   T *const NBZ = sm + L::oNBZ;
 
-  __shared__ const T *srcA[27];
-  __shared__ const T *srcB[27];
-  __shared__ T wgt[27];
-  __shared__ double red[NT / 32];
-  __shared__ int s_fallback;
+  const T **srcA = S.srcA;
+  const T **srcB = S.srcB;
+  T *wgt = S.wgt;
+  double *red = S.red;
+  int &s_fallback = S.fallback;
 
   const int tid = threadIdx.x;
   const int nx = c.nx, ny = c.ny, nz = c.nz;
@@ -112,548 +123,694 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
   const T gamma = (T)c.gamma;
   const T igm1 = (T)(1.0 / (c.gamma - 1.0));
   const T half = T(0.5);
-  const long long nwork = (long long)c.ctl[CTL_NREADY] * c.tiles;
 
 #define H2(i, j) (((j) + 2) * (TX + 4) + ((i) + 2))
 #define H1(i, j) (((j) + 1) * (TX + 2) + ((i) + 1))
 #define F5(i, j) (((j) + 2) * (TX + 5) + ((i) + 2))
 
-  for (long long w = blockIdx.x; w < nwork; w += gridDim.x) {
-    const int r = (int)(w / c.tiles), tile = (int)(w % c.tiles);
-    const int P = c.R[r];
-    const double dt = c.dtR[r];
-    const T hdt = (T)(0.5 * dt / c.dx);
-    const T dtdx = (T)(dt / c.dx);
-    const int tix = tile % c.ntx, tiy = (tile / c.ntx) % c.nty, tiz = tile / (c.ntx * c.nty);
-    const int x0 = tix * TX, y0 = tiy * TY, z0 = tiz * c.tz;
-    const int tx = min(TX, nx - x0), ty = min(TY, ny - y0), tz = min(c.tz, nz - z0);
-    const int Lp = c.latest[P];
-    const double tP = c.t_slot[(long long)P * c.ns + Lp];
-    T *const dst = (T *)c.slab + (long long)((Lp + 1) % c.ns) * c.slot_stride + (long long)P * c.patch_len;
+  const T hdt = (T)(0.5 * dt / c.dx);
+  const T dtdx = (T)(dt / c.dx);
+  const int tix = tile % c.ntx, tiy = (tile / c.ntx) % c.nty, tiz = tile / (c.ntx * c.nty);
+  const int x0 = tix * TX, y0 = tiy * TY, z0 = tiz * c.tz;
+  const int tx = min(TX, nx - x0), ty = min(TY, ny - y0), tz = min(c.tz, nz - z0);
+  const int Lp = newest<CONC>(c, P);
+  const double tP = slot_time<CONC>(c, (long long)P * c.ns + Lp);
+  T *const dst = (T *)c.slab + (long long)((Lp + 1) % c.ns) * c.slot_stride + (long long)P * c.patch_len;
 
-    // Which slices of each of the 27 neighbours (self at 13) supply time tP:
-    // an exact-time slice is copied, else the two newest are interpolated.
-    if (tid < 27) {
-      const int Q = c.nb27[(long long)P * 27 + tid];
-      const int Lq = c.latest[Q];
-      const double tq = c.t_slot[(long long)Q * c.ns + Lq];
-      const T *base = (const T *)c.slab + (long long)Q * c.patch_len;
-      const T *A;
-      const T *B = nullptr;
-      T wv = T(0);
-      if (tq == tP) {
-        A = base + (long long)Lq * c.slot_stride;
+  // Which slices of each of the 27 neighbours (self at 13) supply time tP:
+  // an exact-time slice is copied, else the two newest are interpolated.
+  if (tid < 27) {
+    const int Q = c.nb27[(long long)P * 27 + tid];
+    const int Lq = newest<CONC>(c, Q);
+    const double tq = slot_time<CONC>(c, (long long)Q * c.ns + Lq);
+    const T *base = (const T *)c.slab + (long long)Q * c.patch_len;
+    const T *A;
+    const T *B = nullptr;
+    T wv = T(0);
+    if (tq == tP) {
+      A = base + (long long)Lq * c.slot_stride;
+    } else {
+      const int Pv = (Lq + c.ns - 1) % c.ns;
+      const double ta = slot_time<CONC>(c, (long long)Q * c.ns + Pv);
+      if (ta == tP) {
+        A = base + (long long)Pv * c.slot_stride;
+      } else if (ta < tP && tP < tq) {
+        A = base + (long long)Pv * c.slot_stride;
+        B = base + (long long)Lq * c.slot_stride;
+        wv = (T)((tP - ta) / (tq - ta));
       } else {
-        const int Pv = (Lq + c.ns - 1) % c.ns;
-        const double ta = c.t_slot[(long long)Q * c.ns + Pv];
-        if (ta == tP) {
-          A = base + (long long)Pv * c.slot_stride;
-        } else if (ta < tP && tP < tq) {
-          A = base + (long long)Pv * c.slot_stride;
-          B = base + (long long)Lq * c.slot_stride;
-          wv = (T)((tP - ta) / (tq - ta));
-        } else {
-          A = base + (long long)Lq * c.slot_stride;
-          set_error(c, DSP_ERR_BRACKET, P, -1);
-        }
+        A = base + (long long)Lq * c.slot_stride;
+        set_error(c, DSP_ERR_BRACKET, P, -1);
       }
-      srcA[tid] = A;
-      srcB[tid] = B;
-      wgt[tid] = wv;
     }
-    if (tid == 0) s_fallback = 0;
-    __syncthreads();
-    const T *const own = srcA[13];
+    srcA[tid] = A;
+    srcB[tid] = B;
+    wgt[tid] = wv;
+  }
+  if (tid == 0) s_fallback = 0;
+  __syncthreads();
+  const T *const own = srcA[13];
 
-    auto val = [&](int o, long long idx) -> T {
-      T a = srcA[o][idx];
-      const T *B = srcB[o];
-      if (B) {
-        T b = B[idx];
-        a = a + wgt[o] * (b - a);
-      }
-      return a;
-    };
-    // Cell-centred component q of patch-local cell (x,y,z), |offset| <= 2.
-    auto cellv = [&](int x, int y, int z, long long q) -> T {
-      const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
-      const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
-      return val((oz * 3 + oy) * 3 + ox, q * nc + ((long long)lz * ny + ly) * nx + lx);
-    };
-    // Face below cell (x,y,z) along each axis: the patch's own face when it
-    // lies on one of its interior cells, else the face of the patch that owns
-    // cell (x,y,z).
-    auto facex = [&](int x, int y, int z) -> T {
-      if (x >= 0 && x <= nx && y >= 0 && y < ny && z >= 0 && z < nz)
-        return own[ofx + ((long long)z * ny + y) * (nx + 1) + x];
-      const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
-      const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
-      return val((oz * 3 + oy) * 3 + ox, ofx + ((long long)lz * ny + ly) * (nx + 1) + lx);
-    };
-    auto facey = [&](int x, int y, int z) -> T {
-      if (x >= 0 && x < nx && y >= 0 && y <= ny && z >= 0 && z < nz)
-        return own[ofy + ((long long)z * (ny + 1) + y) * nx + x];
-      const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
-      const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
-      return val((oz * 3 + oy) * 3 + ox, ofy + ((long long)lz * (ny + 1) + ly) * nx + lx);
-    };
-    auto facez = [&](int x, int y, int z) -> T {
-      if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z <= nz)
-        return own[ofz + ((long long)z * ny + y) * nx + x];
-      const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
-      const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
-      return val((oz * 3 + oy) * 3 + ox, ofz + ((long long)lz * ny + ly) * nx + lx);
-    };
+  auto val = [&](int o, long long idx) -> T {
+    T a = srcA[o][idx];
+    const T *B = srcB[o];
+    if (B) {
+      T b = B[idx];
+      a = a + wgt[o] * (b - a);
+    }
+    return a;
+  };
+  // Cell-centred component q of patch-local cell (x,y,z), |offset| <= 2.
+  auto cellv = [&](int x, int y, int z, long long q) -> T {
+    const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
+    const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
+    return val((oz * 3 + oy) * 3 + ox, q * nc + ((long long)lz * ny + ly) * nx + lx);
+  };
+  // Face below cell (x,y,z) along each axis: the patch's own face when it
+  // lies on one of its interior cells, else the face of the patch that owns
+  // cell (x,y,z).
+  auto facex = [&](int x, int y, int z) -> T {
+    if (x >= 0 && x <= nx && y >= 0 && y < ny && z >= 0 && z < nz)
+      return own[ofx + ((long long)z * ny + y) * (nx + 1) + x];
+    const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
+    const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
+    return val((oz * 3 + oy) * 3 + ox, ofx + ((long long)lz * ny + ly) * (nx + 1) + lx);
+  };
+  auto facey = [&](int x, int y, int z) -> T {
+    if (x >= 0 && x < nx && y >= 0 && y <= ny && z >= 0 && z < nz)
+      return own[ofy + ((long long)z * (ny + 1) + y) * nx + x];
+    const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
+    const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
+    return val((oz * 3 + oy) * 3 + ox, ofy + ((long long)lz * (ny + 1) + ly) * nx + lx);
+  };
+  auto facez = [&](int x, int y, int z) -> T {
+    if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z <= nz)
+      return own[ofz + ((long long)z * ny + y) * nx + x];
+    const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
+    const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
+    return val((oz * 3 + oy) * 3 + ox, ofz + ((long long)lz * ny + ly) * nx + lx);
+  };
 
-    // ---- A: gather plane q of the radius-2 padded tile: the raw conserved
-    // values and the faces (x- and y-faces below each cell, both z-faces),
-    // then the primitive variables from shared memory.
-    auto load_plane = [&](int q) {
-      const int rs = (q - z0 + 3) % 3, fs = (q - z0 + 2) & 1;
-      T *Wq = Wr + rs * 8 * H2N;
-      T *Fq = FB + fs * 4 * FPN;
-      const int oz = off1(q, nz), lz = q - (oz - 1) * nz;
-      for (int ci = tid; ci < (TX + 5) * (TY + 5); ci += NT) {
-        const int i = ci % (TX + 5) - 2, j = ci / (TX + 5) - 2;
-        if (i > tx + 2 || j > ty + 2) continue;
-        const int x = x0 + i, y = y0 + j;
-        const int f = F5(i, j);
-        if (j <= ty + 1) Fq[f] = facex(x, y, q);
-        if (i <= tx + 1) Fq[FPN + f] = facey(x, y, q);
-        if (i <= tx + 1 && j <= ty + 1) {
-          Fq[2 * FPN + f] = facez(x, y, q);
-          Fq[3 * FPN + f] = facez(x, y, q + 1);
-          const int ox = off1(x, nx), oy = off1(y, ny);
-          const int o = (oz * 3 + oy) * 3 + ox;
-          const long long cid = ((long long)lz * ny + (y - (oy - 1) * ny)) * nx + (x - (ox - 1) * nx);
-          const int h = H2(i, j);
-          if (o == 13) {
+  // ---- A: gather plane q of the radius-2 padded tile: the raw conserved
+  // values and the faces (x- and y-faces below each cell, both z-faces),
+  // then the primitive variables from shared memory.
+  auto load_plane = [&](int q) {
+    const int rs = (q - z0 + 3) % 3, fs = (q - z0 + 2) & 1;
+    T *Wq = Wr + rs * 8 * H2N;
+    T *Fq = FB + fs * 4 * FPN;
+    const int oz = off1(q, nz), lz = q - (oz - 1) * nz;
+    for (int ci = tid; ci < (TX + 5) * (TY + 5); ci += NT) {
+      const int i = ci % (TX + 5) - 2, j = ci / (TX + 5) - 2;
+      if (i > tx + 2 || j > ty + 2) continue;
+      const int x = x0 + i, y = y0 + j;
+      const int f = F5(i, j);
+      if (j <= ty + 1) Fq[f] = facex(x, y, q);
+      if (i <= tx + 1) Fq[FPN + f] = facey(x, y, q);
+      if (i <= tx + 1 && j <= ty + 1) {
+        Fq[2 * FPN + f] = facez(x, y, q);
+        Fq[3 * FPN + f] = facez(x, y, q + 1);
+        const int ox = off1(x, nx), oy = off1(y, ny);
+        const int o = (oz * 3 + oy) * 3 + ox;
+        const long long cid = ((long long)lz * ny + (y - (oy - 1) * ny)) * nx + (x - (ox - 1) * nx);
+        const int h = H2(i, j);
+        if (o == 13) {
 #pragma unroll
-            for (int k = 0; k < 5; k++) Wq[k * H2N + h] = own[k * nc + cid];
-          } else {
+          for (int k = 0; k < 5; k++) Wq[k * H2N + h] = own[k * nc + cid];
+        } else {
 #pragma unroll
-            for (int k = 0; k < 5; k++) Wq[k * H2N + h] = val(o, k * nc + cid);
-          }
+          for (int k = 0; k < 5; k++) Wq[k * H2N + h] = val(o, k * nc + cid);
         }
       }
-    };
-    auto prim_plane = [&](int q) {
-      const int rs = (q - z0 + 3) % 3, fs = (q - z0 + 2) & 1;
-      T *Wq = Wr + rs * 8 * H2N;
-      const T *Fq = FB + fs * 4 * FPN;
-      for (int ci = tid; ci < (TX + 4) * (TY + 4); ci += NT) {
-        const int i = ci % (TX + 4) - 2, j = ci / (TX + 4) - 2;
-        if (i > tx + 1 || j > ty + 1) continue;
-        const int h = H2(i, j), f = F5(i, j);
-        T Wt[8];
-        prim(Wq[h], Wq[H2N + h], Wq[2 * H2N + h], Wq[3 * H2N + h], Wq[4 * H2N + h], Fq[f], Fq[F5(i + 1, j)],
-             Fq[FPN + f], Fq[FPN + F5(i, j + 1)], Fq[2 * FPN + f], Fq[3 * FPN + f], gamma, Wt);
+    }
+  };
+  auto prim_plane = [&](int q) {
+    const int rs = (q - z0 + 3) % 3, fs = (q - z0 + 2) & 1;
+    T *Wq = Wr + rs * 8 * H2N;
+    const T *Fq = FB + fs * 4 * FPN;
+    for (int ci = tid; ci < (TX + 4) * (TY + 4); ci += NT) {
+      const int i = ci % (TX + 4) - 2, j = ci / (TX + 4) - 2;
+      if (i > tx + 1 || j > ty + 1) continue;
+      const int h = H2(i, j), f = F5(i, j);
+      T Wt[8];
+      prim(Wq[h], Wq[H2N + h], Wq[2 * H2N + h], Wq[3 * H2N + h], Wq[4 * H2N + h], Fq[f], Fq[F5(i + 1, j)],
+           Fq[FPN + f], Fq[FPN + F5(i, j + 1)], Fq[2 * FPN + f], Fq[3 * FPN + f], gamma, Wt);
 #pragma unroll
-        for (int k = 0; k < 8; k++) Wq[k * H2N + h] = Wt[k];
+      for (int k = 0; k < 8; k++) Wq[k * H2N + h] = Wt[k];
+    }
+  };
+
+  load_plane(z0 - 2);
+  load_plane(z0 - 1);
+  __syncthreads();
+  prim_plane(z0 - 2);
+  prim_plane(z0 - 1);
+  __syncthreads();
+
+  T smax_t = T(0);
+  T unew[5];
+  for (int it = 0; it <= tz + 1; it++) {
+    const int p = z0 - 1 + it;
+    const int par = it & 1;
+    T *const SXc = SX + par * 2 * H1N, *const SXp = SX + (par ^ 1) * 2 * H1N;
+    T *const SYc = SY + par * 2 * H1N, *const SYp = SY + (par ^ 1) * 2 * H1N;
+    T *const FZc = FZ + par * 5 * H1N, *const FZp = FZ + (par ^ 1) * 5 * H1N;
+    T *const DUc = DU + par * 5 * H1N, *const DUp = DU + (par ^ 1) * 5 * H1N;
+    T *const EXc = EX + par * H1N, *const EXp = EX + (par ^ 1) * H1N;
+    T *const EYc = EY + par * H1N, *const EYp = EY + (par ^ 1) * H1N;
+    T *const NBZc = NBZ + par * H1N, *const NBZp = NBZ + (par ^ 1) * H1N;
+
+    // ---- A
+    load_plane(p + 1);
+    __syncthreads();
+    prim_plane(p + 1);
+    __syncthreads();
+
+    // ---- B: slopes and predictor on the H1 region of plane p
+    {
+      const int rm = (p - 1 - z0 + 3) % 3, r0 = (p - z0 + 3) % 3, rp = (p + 1 - z0 + 3) % 3;
+      const T *Wm = Wr + rm * 8 * H2N, *W0 = Wr + r0 * 8 * H2N, *Wp = Wr + rp * 8 * H2N;
+      const T *F0 = FB + ((p - z0 + 2) & 1) * 4 * FPN;
+      for (int ci = tid; ci < (TX + 2) * (TY + 2); ci += NT) {
+        const int i = ci % (TX + 2) - 1, j = ci / (TX + 2) - 1;
+        if (i > tx || j > ty) continue;
+        const int h = H2(i, j);
+        T w8[8], dX[8], dY[8], dZ[8], ws[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) w8[k] = W0[k * H2N + h];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          if (k == BX) dX[k] = F0[F5(i + 1, j)] - F0[F5(i, j)];
+          else dX[k] = mc(w8[k] - W0[k * H2N + H2(i - 1, j)], W0[k * H2N + H2(i + 1, j)] - w8[k]);
+          if (k == BY) dY[k] = F0[FPN + F5(i, j + 1)] - F0[FPN + F5(i, j)];
+          else dY[k] = mc(w8[k] - W0[k * H2N + H2(i, j - 1)], W0[k * H2N + H2(i, j + 1)] - w8[k]);
+          if (k == BZ) dZ[k] = F0[3 * FPN + F5(i, j)] - F0[2 * FPN + F5(i, j)];
+          else dZ[k] = mc(w8[k] - Wm[k * H2N + h], Wp[k * H2N + h] - w8[k]);
+        }
+        predict(w8, dX, dY, dZ, gamma, hdt, ws);
+        bool bad = false;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          const T *d3 = d == 0 ? dX : d == 1 ? dY : dZ;
+          const T rp_ = ws[RHO] + half * d3[RHO], rm_ = ws[RHO] - half * d3[RHO];
+          const T pp_ = ws[PR] + half * d3[PR], pm_ = ws[PR] - half * d3[PR];
+          if (!(rp_ > T(0)) || !(rm_ > T(0)) || !(pp_ > T(0)) || !(pm_ > T(0))) bad = true;
+        }
+        if (bad) {
+          atomicAdd(&s_fallback, 1);
+#pragma unroll
+          for (int k = 0; k < 8; k++) { dX[k] = T(0); dY[k] = T(0); dZ[k] = T(0); ws[k] = w8[k]; }
+        }
+        const int g = H1(i, j);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          Sws[k * H1N + g] = ws[k];
+          SdX[k * H1N + g] = dX[k];
+          SdY[k * H1N + g] = dY[k];
+          SdZ[k * H1N + g] = dZ[k];
+        }
       }
-    };
-
-    load_plane(z0 - 2);
-    load_plane(z0 - 1);
-    __syncthreads();
-    prim_plane(z0 - 2);
-    prim_plane(z0 - 1);
+    }
     __syncthreads();
 
-    T smax_t = T(0);
-    T unew[5];
-    for (int it = 0; it <= tz + 1; it++) {
-      const int p = z0 - 1 + it;
-      const int par = it & 1;
-      T *const SXc = SX + par * 2 * H1N, *const SXp = SX + (par ^ 1) * 2 * H1N;
-      T *const SYc = SY + par * 2 * H1N, *const SYp = SY + (par ^ 1) * 2 * H1N;
-      T *const FZc = FZ + par * 5 * H1N, *const FZp = FZ + (par ^ 1) * 5 * H1N;
-      T *const DUc = DU + par * 5 * H1N, *const DUp = DU + (par ^ 1) * 5 * H1N;
-      T *const EXc = EX + par * H1N, *const EXp = EX + (par ^ 1) * H1N;
-      T *const EYc = EY + par * H1N, *const EYp = EY + (par ^ 1) * H1N;
-      T *const NBZc = NBZ + par * H1N, *const NBZp = NBZ + (par ^ 1) * H1N;
-
-      // ---- A
-      load_plane(p + 1);
-      __syncthreads();
-      prim_plane(p + 1);
-      __syncthreads();
-
-      // ---- B: slopes and predictor on the H1 region of plane p
-      {
-        const int rm = (p - 1 - z0 + 3) % 3, r0 = (p - z0 + 3) % 3, rp = (p + 1 - z0 + 3) % 3;
-        const T *Wm = Wr + rm * 8 * H2N, *W0 = Wr + r0 * 8 * H2N, *Wp = Wr + rp * 8 * H2N;
-        const T *F0 = FB + ((p - z0 + 2) & 1) * 4 * FPN;
+    // ---- C: face fluxes
+    {
+      // x-faces (i-1/2, j) of plane p, i in [0,tx]: rows j in [0,ty) need
+      // fluxes and speeds, the halo rows j = -1 and j = ty speeds only
+      for (int ci = tid; ci < (TX + 1) * (TY + 2); ci += NT) {
+        int i, j;
+        const bool full = ci < (TX + 1) * TY;
+        if (full) {
+          i = ci % (TX + 1);
+          j = ci / (TX + 1);
+          if (j >= ty) continue;
+        } else {
+          const int k = ci - (TX + 1) * TY;
+          i = k % (TX + 1);
+          j = k / (TX + 1) == 0 ? -1 : ty;
+        }
+        if (i > tx) continue;
+        const int hl = H1(i - 1, j), hr = H1(i, j);
+        T WL[8], WR[8], F[5], SL, SR;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          WL[k] = Sws[k * H1N + hl] + half * SdX[k * H1N + hl];
+          WR[k] = Sws[k * H1N + hr] - half * SdX[k * H1N + hr];
+        }
+        if (full) {
+          hll<T, 0>(WL, WR, gamma, igm1, F, SL, SR);
+#pragma unroll
+          for (int k = 0; k < 5; k++) FX[k * H1N + hr] = F[k];
+        } else {
+          hll_speeds<T, 0>(WL, WR, gamma, SL, SR);
+        }
+        SXc[hr] = SL;
+        SXc[H1N + hr] = SR;
+      }
+      // y-faces (i, j-1/2) of plane p, j in [0,ty]: columns i in [0,tx)
+      // need fluxes, the halo columns i = -1 and i = tx speeds only
+      for (int ci = tid; ci < (TX + 2) * (TY + 1); ci += NT) {
+        int i, j;
+        const bool full = ci < TX * (TY + 1);
+        if (full) {
+          i = ci % TX;
+          j = ci / TX;
+          if (i >= tx) continue;
+        } else {
+          const int k = ci - TX * (TY + 1);
+          i = k / (TY + 1) == 0 ? -1 : tx;
+          j = k % (TY + 1);
+        }
+        if (j > ty) continue;
+        const int hl = H1(i, j - 1), hr = H1(i, j);
+        T WL[8], WR[8], F[5], SL, SR;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          WL[k] = Sws[k * H1N + hl] + half * SdY[k * H1N + hl];
+          WR[k] = Sws[k * H1N + hr] - half * SdY[k * H1N + hr];
+        }
+        if (full) {
+          hll<T, 1>(WL, WR, gamma, igm1, F, SL, SR);
+#pragma unroll
+          for (int k = 0; k < 5; k++) FY[k * H1N + hr] = F[k];
+        } else {
+          hll_speeds<T, 1>(WL, WR, gamma, SL, SR);
+        }
+        SYc[hr] = SL;
+        SYc[H1N + hr] = SR;
+      }
+      // z-faces (i, j, p-1/2) on the H1 region: the tile's own faces need
+      // fluxes, the ring around them speeds only
+      if (it > 0) {
         for (int ci = tid; ci < (TX + 2) * (TY + 2); ci += NT) {
-          const int i = ci % (TX + 2) - 1, j = ci / (TX + 2) - 1;
-          if (i > tx || j > ty) continue;
-          const int h = H2(i, j);
-          T w8[8], dX[8], dY[8], dZ[8], ws[8];
-#pragma unroll
-          for (int k = 0; k < 8; k++) w8[k] = W0[k * H2N + h];
-#pragma unroll
-          for (int k = 0; k < 8; k++) {
-            if (k == BX) dX[k] = F0[F5(i + 1, j)] - F0[F5(i, j)];
-            else dX[k] = mc(w8[k] - W0[k * H2N + H2(i - 1, j)], W0[k * H2N + H2(i + 1, j)] - w8[k]);
-            if (k == BY) dY[k] = F0[FPN + F5(i, j + 1)] - F0[FPN + F5(i, j)];
-            else dY[k] = mc(w8[k] - W0[k * H2N + H2(i, j - 1)], W0[k * H2N + H2(i, j + 1)] - w8[k]);
-            if (k == BZ) dZ[k] = F0[3 * FPN + F5(i, j)] - F0[2 * FPN + F5(i, j)];
-            else dZ[k] = mc(w8[k] - Wm[k * H2N + h], Wp[k * H2N + h] - w8[k]);
-          }
-          predict(w8, dX, dY, dZ, gamma, hdt, ws);
-          bool bad = false;
-#pragma unroll
-          for (int d = 0; d < 3; d++) {
-            const T *d3 = d == 0 ? dX : d == 1 ? dY : dZ;
-            const T rp_ = ws[RHO] + half * d3[RHO], rm_ = ws[RHO] - half * d3[RHO];
-            const T pp_ = ws[PR] + half * d3[PR], pm_ = ws[PR] - half * d3[PR];
-            if (!(rp_ > T(0)) || !(rm_ > T(0)) || !(pp_ > T(0)) || !(pm_ > T(0))) bad = true;
-          }
-          if (bad) {
-            atomicAdd(&s_fallback, 1);
-#pragma unroll
-            for (int k = 0; k < 8; k++) { dX[k] = T(0); dY[k] = T(0); dZ[k] = T(0); ws[k] = w8[k]; }
-          }
-          const int g = H1(i, j);
-#pragma unroll
-          for (int k = 0; k < 8; k++) {
-            Sws[k * H1N + g] = ws[k];
-            SdX[k * H1N + g] = dX[k];
-            SdY[k * H1N + g] = dY[k];
-            SdZ[k * H1N + g] = dZ[k];
-          }
-        }
-      }
-      __syncthreads();
-
-      // ---- C: face fluxes
-      {
-        // x-faces (i-1/2, j) of plane p, i in [0,tx]: rows j in [0,ty) need
-        // fluxes and speeds, the halo rows j = -1 and j = ty speeds only
-        for (int ci = tid; ci < (TX + 1) * (TY + 2); ci += NT) {
           int i, j;
-          const bool full = ci < (TX + 1) * TY;
-          if (full) {
-            i = ci % (TX + 1);
-            j = ci / (TX + 1);
-            if (j >= ty) continue;
-          } else {
-            const int k = ci - (TX + 1) * TY;
-            i = k % (TX + 1);
-            j = k / (TX + 1) == 0 ? -1 : ty;
-          }
-          if (i > tx) continue;
-          const int hl = H1(i - 1, j), hr = H1(i, j);
-          T WL[8], WR[8], F[5], SL, SR;
-#pragma unroll
-          for (int k = 0; k < 8; k++) {
-            WL[k] = Sws[k * H1N + hl] + half * SdX[k * H1N + hl];
-            WR[k] = Sws[k * H1N + hr] - half * SdX[k * H1N + hr];
-          }
-          if (full) {
-            hll<T, 0>(WL, WR, gamma, igm1, F, SL, SR);
-#pragma unroll
-            for (int k = 0; k < 5; k++) FX[k * H1N + hr] = F[k];
-          } else {
-            hll_speeds<T, 0>(WL, WR, gamma, SL, SR);
-          }
-          SXc[hr] = SL;
-          SXc[H1N + hr] = SR;
-        }
-        // y-faces (i, j-1/2) of plane p, j in [0,ty]: columns i in [0,tx)
-        // need fluxes, the halo columns i = -1 and i = tx speeds only
-        for (int ci = tid; ci < (TX + 2) * (TY + 1); ci += NT) {
-          int i, j;
-          const bool full = ci < TX * (TY + 1);
+          const bool full = ci < TX * TY;
           if (full) {
             i = ci % TX;
             j = ci / TX;
-            if (i >= tx) continue;
+            if (i >= tx || j >= ty) continue;
           } else {
-            const int k = ci - TX * (TY + 1);
-            i = k / (TY + 1) == 0 ? -1 : tx;
-            j = k % (TY + 1);
+            const int k = ci - TX * TY;
+            if (k < 2 * (TX + 2)) {
+              i = k % (TX + 2) - 1;
+              j = k / (TX + 2) == 0 ? -1 : ty;
+              if (i > tx) continue;
+            } else {
+              const int k2 = k - 2 * (TX + 2);
+              i = k2 / TY == 0 ? -1 : tx;
+              j = k2 % TY;
+              if (j >= ty) continue;
+            }
           }
-          if (j > ty) continue;
-          const int hl = H1(i, j - 1), hr = H1(i, j);
+          const int h = H1(i, j);
           T WL[8], WR[8], F[5], SL, SR;
 #pragma unroll
           for (int k = 0; k < 8; k++) {
-            WL[k] = Sws[k * H1N + hl] + half * SdY[k * H1N + hl];
-            WR[k] = Sws[k * H1N + hr] - half * SdY[k * H1N + hr];
+            WL[k] = ZP[k * H1N + h];
+            WR[k] = Sws[k * H1N + h] - half * SdZ[k * H1N + h];
           }
           if (full) {
-            hll<T, 1>(WL, WR, gamma, igm1, F, SL, SR);
+            hll<T, 2>(WL, WR, gamma, igm1, F, SL, SR);
 #pragma unroll
-            for (int k = 0; k < 5; k++) FY[k * H1N + hr] = F[k];
+            for (int k = 0; k < 5; k++) FZc[k * H1N + h] = F[k];
           } else {
-            hll_speeds<T, 1>(WL, WR, gamma, SL, SR);
+            hll_speeds<T, 2>(WL, WR, gamma, SL, SR);
           }
-          SYc[hr] = SL;
-          SYc[H1N + hr] = SR;
-        }
-        // z-faces (i, j, p-1/2) on the H1 region: the tile's own faces need
-        // fluxes, the ring around them speeds only
-        if (it > 0) {
-          for (int ci = tid; ci < (TX + 2) * (TY + 2); ci += NT) {
-            int i, j;
-            const bool full = ci < TX * TY;
-            if (full) {
-              i = ci % TX;
-              j = ci / TX;
-              if (i >= tx || j >= ty) continue;
-            } else {
-              const int k = ci - TX * TY;
-              if (k < 2 * (TX + 2)) {
-                i = k % (TX + 2) - 1;
-                j = k / (TX + 2) == 0 ? -1 : ty;
-                if (i > tx) continue;
-              } else {
-                const int k2 = k - 2 * (TX + 2);
-                i = k2 / TY == 0 ? -1 : tx;
-                j = k2 % TY;
-                if (j >= ty) continue;
-              }
-            }
-            const int h = H1(i, j);
-            T WL[8], WR[8], F[5], SL, SR;
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-              WL[k] = ZP[k * H1N + h];
-              WR[k] = Sws[k * H1N + h] - half * SdZ[k * H1N + h];
-            }
-            if (full) {
-              hll<T, 2>(WL, WR, gamma, igm1, F, SL, SR);
-#pragma unroll
-              for (int k = 0; k < 5; k++) FZc[k * H1N + h] = F[k];
-            } else {
-              hll_speeds<T, 2>(WL, WR, gamma, SL, SR);
-            }
-            SZ[h] = SL;
-            SZ[H1N + h] = SR;
-          }
+          SZ[h] = SL;
+          SZ[H1N + h] = SR;
         }
       }
-      __syncthreads();
+    }
+    __syncthreads();
 
-      // ---- D: x- and y-edge EMFs at p-1/2, in-plane divergence of plane p
-      if (it > 0) {
-        // x-edges (i, j-1/2, p-1/2): i in [0,tx), j in [0,ty]; a = y, b = z
-        for (int ci = tid; ci < TX * (TY + 1); ci += NT) {
-          const int i = ci % TX, j = ci / TX;
-          if (i >= tx || j > ty) continue;
-          const int hm = H1(i, j - 1), h0 = H1(i, j);
-          const T Ell = CX[0 * H1N + hm], Ba_ll = CX[1 * H1N + hm], Bb_ll = CX[2 * H1N + hm];
-          const T Erl = CX[3 * H1N + h0], Ba_rl = CX[4 * H1N + h0], Bb_rl = CX[5 * H1N + h0];
-          const T lr_vy = (Sws[VY * H1N + hm] + half * SdY[VY * H1N + hm]) - half * SdZ[VY * H1N + hm];
-          const T lr_vz = (Sws[VZ * H1N + hm] + half * SdY[VZ * H1N + hm]) - half * SdZ[VZ * H1N + hm];
-          const T lr_by = (Sws[BY * H1N + hm] + half * SdY[BY * H1N + hm]) - half * SdZ[BY * H1N + hm];
-          const T lr_bz = (Sws[BZ * H1N + hm] + half * SdY[BZ * H1N + hm]) - half * SdZ[BZ * H1N + hm];
-          const T rr_vy = (Sws[VY * H1N + h0] - half * SdY[VY * H1N + h0]) - half * SdZ[VY * H1N + h0];
-          const T rr_vz = (Sws[VZ * H1N + h0] - half * SdY[VZ * H1N + h0]) - half * SdZ[VZ * H1N + h0];
-          const T rr_by = (Sws[BY * H1N + h0] - half * SdY[BY * H1N + h0]) - half * SdZ[BY * H1N + h0];
-          const T rr_bz = (Sws[BZ * H1N + h0] - half * SdY[BZ * H1N + h0]) - half * SdZ[BZ * H1N + h0];
-          const T Elr = lr_vz * lr_by - lr_vy * lr_bz;
-          const T Err = rr_vz * rr_by - rr_vy * rr_bz;
-          const T apa = tmax(T(0), tmax(SYp[H1N + h0], SYc[H1N + h0]));
-          const T ama = tmax(T(0), tmax(-SYp[h0], -SYc[h0]));
-          const T apb = tmax(T(0), tmax(SZ[H1N + hm], SZ[H1N + h0]));
-          const T amb = tmax(T(0), tmax(-SZ[hm], -SZ[h0]));
-          EXc[h0] = emf(Ell, Erl, Elr, Err, Ba_ll, Ba_rl, lr_by, rr_by, Bb_ll, Bb_rl, lr_bz, rr_bz, apa, ama, apb, amb);
-        }
-        // y-edges (i-1/2, j, p-1/2): i in [0,tx], j in [0,ty); a = z, b = x
-        for (int ci = tid; ci < (TX + 1) * TY; ci += NT) {
-          const int i = ci % (TX + 1), j = ci / (TX + 1);
-          if (i > tx || j >= ty) continue;
-          const int hm = H1(i - 1, j), h0 = H1(i, j);
-          const T Ell = CY[0 * H1N + hm], Ba_ll = CY[1 * H1N + hm], Bb_ll = CY[2 * H1N + hm];
-          const T Elr = CY[3 * H1N + h0], Ba_lr = CY[4 * H1N + h0], Bb_lr = CY[5 * H1N + h0];
-          const T rl_vz = (Sws[VZ * H1N + hm] - half * SdZ[VZ * H1N + hm]) + half * SdX[VZ * H1N + hm];
-          const T rl_vx = (Sws[VX * H1N + hm] - half * SdZ[VX * H1N + hm]) + half * SdX[VX * H1N + hm];
-          const T rl_bz = (Sws[BZ * H1N + hm] - half * SdZ[BZ * H1N + hm]) + half * SdX[BZ * H1N + hm];
-          const T rl_bx = (Sws[BX * H1N + hm] - half * SdZ[BX * H1N + hm]) + half * SdX[BX * H1N + hm];
-          const T rr_vz = (Sws[VZ * H1N + h0] - half * SdZ[VZ * H1N + h0]) - half * SdX[VZ * H1N + h0];
-          const T rr_vx = (Sws[VX * H1N + h0] - half * SdZ[VX * H1N + h0]) - half * SdX[VX * H1N + h0];
-          const T rr_bz = (Sws[BZ * H1N + h0] - half * SdZ[BZ * H1N + h0]) - half * SdX[BZ * H1N + h0];
-          const T rr_bx = (Sws[BX * H1N + h0] - half * SdZ[BX * H1N + h0]) - half * SdX[BX * H1N + h0];
-          const T Erl = rl_vx * rl_bz - rl_vz * rl_bx;
-          const T Err = rr_vx * rr_bz - rr_vz * rr_bx;
-          const T apa = tmax(T(0), tmax(SZ[H1N + hm], SZ[H1N + h0]));
-          const T ama = tmax(T(0), tmax(-SZ[hm], -SZ[h0]));
-          const T apb = tmax(T(0), tmax(SXp[H1N + h0], SXc[H1N + h0]));
-          const T amb = tmax(T(0), tmax(-SXp[h0], -SXc[h0]));
-          EYc[h0] = emf(Ell, Erl, Elr, Err, Ba_ll, rl_bz, Ba_lr, rr_bz, Bb_ll, rl_bx, Bb_lr, rr_bx, apa, ama, apb, amb);
-        }
-        if (p < z0 + tz) {
-          for (int ci = tid; ci < TX * TY; ci += NT) {
-            const int i = ci % TX, j = ci / TX;
-            if (i >= tx || j >= ty) continue;
-            const int h = H1(i, j), hx = H1(i + 1, j), hy = H1(i, j + 1);
-#pragma unroll
-            for (int k = 0; k < 5; k++)
-              DUc[k * H1N + h] = (FX[k * H1N + hx] - FX[k * H1N + h]) + (FY[k * H1N + hy] - FY[k * H1N + h]);
-          }
-        }
+    // ---- D: x- and y-edge EMFs at p-1/2, in-plane divergence of plane p
+    if (it > 0) {
+      // x-edges (i, j-1/2, p-1/2): i in [0,tx), j in [0,ty]; a = y, b = z
+      for (int ci = tid; ci < TX * (TY + 1); ci += NT) {
+        const int i = ci % TX, j = ci / TX;
+        if (i >= tx || j > ty) continue;
+        const int hm = H1(i, j - 1), h0 = H1(i, j);
+        const T Ell = CX[0 * H1N + hm], Ba_ll = CX[1 * H1N + hm], Bb_ll = CX[2 * H1N + hm];
+        const T Erl = CX[3 * H1N + h0], Ba_rl = CX[4 * H1N + h0], Bb_rl = CX[5 * H1N + h0];
+        const T lr_vy = (Sws[VY * H1N + hm] + half * SdY[VY * H1N + hm]) - half * SdZ[VY * H1N + hm];
+        const T lr_vz = (Sws[VZ * H1N + hm] + half * SdY[VZ * H1N + hm]) - half * SdZ[VZ * H1N + hm];
+        const T lr_by = (Sws[BY * H1N + hm] + half * SdY[BY * H1N + hm]) - half * SdZ[BY * H1N + hm];
+        const T lr_bz = (Sws[BZ * H1N + hm] + half * SdY[BZ * H1N + hm]) - half * SdZ[BZ * H1N + hm];
+        const T rr_vy = (Sws[VY * H1N + h0] - half * SdY[VY * H1N + h0]) - half * SdZ[VY * H1N + h0];
+        const T rr_vz = (Sws[VZ * H1N + h0] - half * SdY[VZ * H1N + h0]) - half * SdZ[VZ * H1N + h0];
+        const T rr_by = (Sws[BY * H1N + h0] - half * SdY[BY * H1N + h0]) - half * SdZ[BY * H1N + h0];
+        const T rr_bz = (Sws[BZ * H1N + h0] - half * SdY[BZ * H1N + h0]) - half * SdZ[BZ * H1N + h0];
+        const T Elr = lr_vz * lr_by - lr_vy * lr_bz;
+        const T Err = rr_vz * rr_by - rr_vy * rr_bz;
+        const T apa = tmax(T(0), tmax(SYp[H1N + h0], SYc[H1N + h0]));
+        const T ama = tmax(T(0), tmax(-SYp[h0], -SYc[h0]));
+        const T apb = tmax(T(0), tmax(SZ[H1N + hm], SZ[H1N + h0]));
+        const T amb = tmax(T(0), tmax(-SZ[hm], -SZ[h0]));
+        EXc[h0] = emf(Ell, Erl, Elr, Err, Ba_ll, Ba_rl, lr_by, rr_by, Bb_ll, Bb_rl, lr_bz, rr_bz, apa, ama, apb, amb);
       }
-      __syncthreads();
-
-      // ---- E: update plane p-1 and the z-faces at p-1/2
-      const bool upd = it >= 2;
-      const int ui = tid % TX, uj = tid / TX;
-      const bool mine = tid < TX * TY && ui < tx && uj < ty;
-      if (upd && mine) {
-        const int i = ui, j = uj, h = H1(i, j);
-        const long long ci = ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i);
-#pragma unroll
-        for (int k = 0; k < 5; k++) {
-          const T fz = FZc[k * H1N + h] - FZp[k * H1N + h];
-          unew[k] = own[k * nc + ci] - dtdx * (DUp[k * H1N + h] + fz);
-          dst[k * nc + ci] = unew[k];
-        }
+      // y-edges (i-1/2, j, p-1/2): i in [0,tx], j in [0,ty); a = z, b = x
+      for (int ci = tid; ci < (TX + 1) * TY; ci += NT) {
+        const int i = ci % (TX + 1), j = ci / (TX + 1);
+        if (i > tx || j >= ty) continue;
+        const int hm = H1(i - 1, j), h0 = H1(i, j);
+        const T Ell = CY[0 * H1N + hm], Ba_ll = CY[1 * H1N + hm], Bb_ll = CY[2 * H1N + hm];
+        const T Elr = CY[3 * H1N + h0], Ba_lr = CY[4 * H1N + h0], Bb_lr = CY[5 * H1N + h0];
+        const T rl_vz = (Sws[VZ * H1N + hm] - half * SdZ[VZ * H1N + hm]) + half * SdX[VZ * H1N + hm];
+        const T rl_vx = (Sws[VX * H1N + hm] - half * SdZ[VX * H1N + hm]) + half * SdX[VX * H1N + hm];
+        const T rl_bz = (Sws[BZ * H1N + hm] - half * SdZ[BZ * H1N + hm]) + half * SdX[BZ * H1N + hm];
+        const T rl_bx = (Sws[BX * H1N + hm] - half * SdZ[BX * H1N + hm]) + half * SdX[BX * H1N + hm];
+        const T rr_vz = (Sws[VZ * H1N + h0] - half * SdZ[VZ * H1N + h0]) - half * SdX[VZ * H1N + h0];
+        const T rr_vx = (Sws[VX * H1N + h0] - half * SdZ[VX * H1N + h0]) - half * SdX[VX * H1N + h0];
+        const T rr_bz = (Sws[BZ * H1N + h0] - half * SdZ[BZ * H1N + h0]) - half * SdX[BZ * H1N + h0];
+        const T rr_bx = (Sws[BX * H1N + h0] - half * SdZ[BX * H1N + h0]) - half * SdX[BX * H1N + h0];
+        const T Erl = rl_vx * rl_bz - rl_vz * rl_bx;
+        const T Err = rr_vx * rr_bz - rr_vz * rr_bx;
+        const T apa = tmax(T(0), tmax(SZ[H1N + hm], SZ[H1N + h0]));
+        const T ama = tmax(T(0), tmax(-SZ[hm], -SZ[h0]));
+        const T apb = tmax(T(0), tmax(SXp[H1N + h0], SXc[H1N + h0]));
+        const T amb = tmax(T(0), tmax(-SXp[h0], -SXc[h0]));
+        EYc[h0] = emf(Ell, Erl, Elr, Err, Ba_ll, rl_bz, Ba_lr, rr_bz, Bb_ll, rl_bx, Bb_lr, rr_bx, apa, ama, apb, amb);
       }
-      if (upd) {
-        const int k = p - 1;
-        for (int ci = tid; ci < (TX + 1) * TY; ci += NT) {
-          const int i = ci % (TX + 1), j = ci / (TX + 1), h = H1(i, j);
-          if (i > tx || j >= ty) continue;
-          const long long id = ((long long)k * ny + (y0 + j)) * (nx + 1) + (x0 + i);
-          const T b = own[ofx + id] - dtdx * ((EZ[H1(i, j + 1)] - EZ[h]) - (EYc[h] - EYp[h]));
-          NBX[h] = b;
-          dst[ofx + id] = b;
-        }
-        for (int ci = tid; ci < TX * (TY + 1); ci += NT) {
-          const int i = ci % TX, j = ci / TX, h = H1(i, j);
-          if (i >= tx || j > ty) continue;
-          const long long id = ((long long)k * (ny + 1) + (y0 + j)) * nx + (x0 + i);
-          const T b = own[ofy + id] - dtdx * ((EXc[h] - EXp[h]) - (EZ[H1(i + 1, j)] - EZ[h]));
-          NBY[h] = b;
-          dst[ofy + id] = b;
-        }
-      }
-      if (it >= 1) {
+      if (p < z0 + tz) {
         for (int ci = tid; ci < TX * TY; ci += NT) {
-          const int i = ci % TX, j = ci / TX, h = H1(i, j);
+          const int i = ci % TX, j = ci / TX;
           if (i >= tx || j >= ty) continue;
-          const long long id = ((long long)p * ny + (y0 + j)) * nx + (x0 + i);
-          const T b = own[ofz + id] - dtdx * ((EYc[H1(i + 1, j)] - EYc[h]) - (EXc[H1(i, j + 1)] - EXc[h]));
-          NBZc[h] = b;
-          dst[ofz + id] = b;
-        }
-      }
-      __syncthreads();
-
-      // ---- F: signal speed of plane p-1, z-edge EMFs of plane p, carried values
-      if (upd && mine) {
-        const int i = ui, j = uj, h = H1(i, j);
-        T Wn[8];
-        prim(unew[0], unew[1], unew[2], unew[3], unew[4], NBX[h], NBX[H1(i + 1, j)], NBY[h], NBY[H1(i, j + 1)],
-             NBZp[h], NBZc[h], gamma, Wn);
-        if (!(Wn[RHO] > T(0)) || !(Wn[PR] > T(0)))
-          set_error(c, DSP_ERR_UNPHYSICAL, P, ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i));
-        smax_t = tmax(smax_t, signal_sum(Wn, gamma));
-      }
-      if (p >= z0 && p < z0 + tz) {
-        // z-edges (i-1/2, j-1/2, p): i in [0,tx], j in [0,ty]; a = x, b = y
-        for (int ci = tid; ci < (TX + 1) * (TY + 1); ci += NT) {
-          const int i = ci % (TX + 1), j = ci / (TX + 1);
-          if (i > tx || j > ty) continue;
-          const int hll_ = H1(i - 1, j - 1), hrl = H1(i, j - 1), hlr = H1(i - 1, j), hrr = H1(i, j);
-          const T ll_vx = (Sws[VX * H1N + hll_] + half * SdX[VX * H1N + hll_]) + half * SdY[VX * H1N + hll_];
-          const T ll_vy = (Sws[VY * H1N + hll_] + half * SdX[VY * H1N + hll_]) + half * SdY[VY * H1N + hll_];
-          const T ll_bx = (Sws[BX * H1N + hll_] + half * SdX[BX * H1N + hll_]) + half * SdY[BX * H1N + hll_];
-          const T ll_by = (Sws[BY * H1N + hll_] + half * SdX[BY * H1N + hll_]) + half * SdY[BY * H1N + hll_];
-          const T rl_vx = (Sws[VX * H1N + hrl] - half * SdX[VX * H1N + hrl]) + half * SdY[VX * H1N + hrl];
-          const T rl_vy = (Sws[VY * H1N + hrl] - half * SdX[VY * H1N + hrl]) + half * SdY[VY * H1N + hrl];
-          const T rl_bx = (Sws[BX * H1N + hrl] - half * SdX[BX * H1N + hrl]) + half * SdY[BX * H1N + hrl];
-          const T rl_by = (Sws[BY * H1N + hrl] - half * SdX[BY * H1N + hrl]) + half * SdY[BY * H1N + hrl];
-          const T lr_vx = (Sws[VX * H1N + hlr] + half * SdX[VX * H1N + hlr]) - half * SdY[VX * H1N + hlr];
-          const T lr_vy = (Sws[VY * H1N + hlr] + half * SdX[VY * H1N + hlr]) - half * SdY[VY * H1N + hlr];
-          const T lr_bx = (Sws[BX * H1N + hlr] + half * SdX[BX * H1N + hlr]) - half * SdY[BX * H1N + hlr];
-          const T lr_by = (Sws[BY * H1N + hlr] + half * SdX[BY * H1N + hlr]) - half * SdY[BY * H1N + hlr];
-          const T rr_vx = (Sws[VX * H1N + hrr] - half * SdX[VX * H1N + hrr]) - half * SdY[VX * H1N + hrr];
-          const T rr_vy = (Sws[VY * H1N + hrr] - half * SdX[VY * H1N + hrr]) - half * SdY[VY * H1N + hrr];
-          const T rr_bx = (Sws[BX * H1N + hrr] - half * SdX[BX * H1N + hrr]) - half * SdY[BX * H1N + hrr];
-          const T rr_by = (Sws[BY * H1N + hrr] - half * SdX[BY * H1N + hrr]) - half * SdY[BY * H1N + hrr];
-          const T Ell = ll_vy * ll_bx - ll_vx * ll_by;
-          const T Erl = rl_vy * rl_bx - rl_vx * rl_by;
-          const T Elr = lr_vy * lr_bx - lr_vx * lr_by;
-          const T Err = rr_vy * rr_bx - rr_vx * rr_by;
-          const T apa = tmax(T(0), tmax(SXc[H1N + hrl], SXc[H1N + hrr]));
-          const T ama = tmax(T(0), tmax(-SXc[hrl], -SXc[hrr]));
-          const T apb = tmax(T(0), tmax(SYc[H1N + hlr], SYc[H1N + hrr]));
-          const T amb = tmax(T(0), tmax(-SYc[hlr], -SYc[hrr]));
-          EZ[hrr] = emf(Ell, Erl, Elr, Err, ll_bx, rl_bx, lr_bx, rr_bx, ll_by, rl_by, lr_by, rr_by, apa, ama, apb, amb);
-        }
-      }
-      {
-        // values of plane p carried to the next plane: its upper z-face
-        // state and its +z corner values for the x- and y-edges above it
-        for (int ci = tid; ci < (TX + 2) * (TY + 2); ci += NT) {
-          const int i = ci % (TX + 2) - 1, j = ci / (TX + 2) - 1, h = H1(i, j);
-          if (i > tx || j > ty) continue;
+          const int h = H1(i, j), hx = H1(i + 1, j), hy = H1(i, j + 1);
 #pragma unroll
-          for (int k = 0; k < 8; k++) ZP[k * H1N + h] = Sws[k * H1N + h] + half * SdZ[k * H1N + h];
-          {  // x-edges: a = y, b = z; corners (+y,+z) and (-y,+z)
-            const T py_vy = (Sws[VY * H1N + h] + half * SdY[VY * H1N + h]) + half * SdZ[VY * H1N + h];
-            const T py_vz = (Sws[VZ * H1N + h] + half * SdY[VZ * H1N + h]) + half * SdZ[VZ * H1N + h];
-            const T py_by = (Sws[BY * H1N + h] + half * SdY[BY * H1N + h]) + half * SdZ[BY * H1N + h];
-            const T py_bz = (Sws[BZ * H1N + h] + half * SdY[BZ * H1N + h]) + half * SdZ[BZ * H1N + h];
-            const T my_vy = (Sws[VY * H1N + h] - half * SdY[VY * H1N + h]) + half * SdZ[VY * H1N + h];
-            const T my_vz = (Sws[VZ * H1N + h] - half * SdY[VZ * H1N + h]) + half * SdZ[VZ * H1N + h];
-            const T my_by = (Sws[BY * H1N + h] - half * SdY[BY * H1N + h]) + half * SdZ[BY * H1N + h];
-            const T my_bz = (Sws[BZ * H1N + h] - half * SdY[BZ * H1N + h]) + half * SdZ[BZ * H1N + h];
-            CX[0 * H1N + h] = py_vz * py_by - py_vy * py_bz;
-            CX[1 * H1N + h] = py_by;
-            CX[2 * H1N + h] = py_bz;
-            CX[3 * H1N + h] = my_vz * my_by - my_vy * my_bz;
-            CX[4 * H1N + h] = my_by;
-            CX[5 * H1N + h] = my_bz;
-          }
-          {  // y-edges: a = z, b = x; corners (+z,+x) and (+z,-x)
-            const T px_vz = (Sws[VZ * H1N + h] + half * SdZ[VZ * H1N + h]) + half * SdX[VZ * H1N + h];
-            const T px_vx = (Sws[VX * H1N + h] + half * SdZ[VX * H1N + h]) + half * SdX[VX * H1N + h];
-            const T px_bz = (Sws[BZ * H1N + h] + half * SdZ[BZ * H1N + h]) + half * SdX[BZ * H1N + h];
-            const T px_bx = (Sws[BX * H1N + h] + half * SdZ[BX * H1N + h]) + half * SdX[BX * H1N + h];
-            const T mx_vz = (Sws[VZ * H1N + h] + half * SdZ[VZ * H1N + h]) - half * SdX[VZ * H1N + h];
-            const T mx_vx = (Sws[VX * H1N + h] + half * SdZ[VX * H1N + h]) - half * SdX[VX * H1N + h];
-            const T mx_bz = (Sws[BZ * H1N + h] + half * SdZ[BZ * H1N + h]) - half * SdX[BZ * H1N + h];
-            const T mx_bx = (Sws[BX * H1N + h] + half * SdZ[BX * H1N + h]) - half * SdX[BX * H1N + h];
-            CY[0 * H1N + h] = px_vx * px_bz - px_vz * px_bx;
-            CY[1 * H1N + h] = px_bz;
-            CY[2 * H1N + h] = px_bx;
-            CY[3 * H1N + h] = mx_vx * mx_bz - mx_vz * mx_bx;
-            CY[4 * H1N + h] = mx_bz;
-            CY[5 * H1N + h] = mx_bx;
-          }
+          for (int k = 0; k < 5; k++)
+            DUc[k * H1N + h] = (FX[k * H1N + hx] - FX[k * H1N + h]) + (FY[k * H1N + hy] - FY[k * H1N + h]);
         }
       }
-      __syncthreads();
     }
+    __syncthreads();
 
-    // signal speed of the new slice: block max, then the patch max
+    // ---- E: update plane p-1 and the z-faces at p-1/2
+    const bool upd = it >= 2;
+    const int ui = tid % TX, uj = tid / TX;
+    const bool mine = tid < TX * TY && ui < tx && uj < ty;
+    if (upd && mine) {
+      const int i = ui, j = uj, h = H1(i, j);
+      const long long ci = ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i);
+#pragma unroll
+      for (int k = 0; k < 5; k++) {
+        const T fz = FZc[k * H1N + h] - FZp[k * H1N + h];
+        unew[k] = own[k * nc + ci] - dtdx * (DUp[k * H1N + h] + fz);
+        dst[k * nc + ci] = unew[k];
+      }
+    }
+    if (upd) {
+      const int k = p - 1;
+      for (int ci = tid; ci < (TX + 1) * TY; ci += NT) {
+        const int i = ci % (TX + 1), j = ci / (TX + 1), h = H1(i, j);
+        if (i > tx || j >= ty) continue;
+        const long long id = ((long long)k * ny + (y0 + j)) * (nx + 1) + (x0 + i);
+        const T b = own[ofx + id] - dtdx * ((EZ[H1(i, j + 1)] - EZ[h]) - (EYc[h] - EYp[h]));
+        NBX[h] = b;
+        dst[ofx + id] = b;
+      }
+      for (int ci = tid; ci < TX * (TY + 1); ci += NT) {
+        const int i = ci % TX, j = ci / TX, h = H1(i, j);
+        if (i >= tx || j > ty) continue;
+        const long long id = ((long long)k * (ny + 1) + (y0 + j)) * nx + (x0 + i);
+        const T b = own[ofy + id] - dtdx * ((EXc[h] - EXp[h]) - (EZ[H1(i + 1, j)] - EZ[h]));
+        NBY[h] = b;
+        dst[ofy + id] = b;
+      }
+    }
+    if (it >= 1) {
+      for (int ci = tid; ci < TX * TY; ci += NT) {
+        const int i = ci % TX, j = ci / TX, h = H1(i, j);
+        if (i >= tx || j >= ty) continue;
+        const long long id = ((long long)p * ny + (y0 + j)) * nx + (x0 + i);
+        const T b = own[ofz + id] - dtdx * ((EYc[H1(i + 1, j)] - EYc[h]) - (EXc[H1(i, j + 1)] - EXc[h]));
+        NBZc[h] = b;
+        dst[ofz + id] = b;
+      }
+    }
+    __syncthreads();
+
+    // ---- F: signal speed of plane p-1, z-edge EMFs of plane p, carried values
+    if (upd && mine) {
+      const int i = ui, j = uj, h = H1(i, j);
+      T Wn[8];
+      prim(unew[0], unew[1], unew[2], unew[3], unew[4], NBX[h], NBX[H1(i + 1, j)], NBY[h], NBY[H1(i, j + 1)],
+           NBZp[h], NBZc[h], gamma, Wn);
+      if (!(Wn[RHO] > T(0)) || !(Wn[PR] > T(0)))
+        set_error(c, DSP_ERR_UNPHYSICAL, P, ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i));
+      smax_t = tmax(smax_t, signal_sum(Wn, gamma));
+    }
+    if (p >= z0 && p < z0 + tz) {
+      // z-edges (i-1/2, j-1/2, p): i in [0,tx], j in [0,ty]; a = x, b = y
+      for (int ci = tid; ci < (TX + 1) * (TY + 1); ci += NT) {
+        const int i = ci % (TX + 1), j = ci / (TX + 1);
+        if (i > tx || j > ty) continue;
+        const int hll_ = H1(i - 1, j - 1), hrl = H1(i, j - 1), hlr = H1(i - 1, j), hrr = H1(i, j);
+        const T ll_vx = (Sws[VX * H1N + hll_] + half * SdX[VX * H1N + hll_]) + half * SdY[VX * H1N + hll_];
+        const T ll_vy = (Sws[VY * H1N + hll_] + half * SdX[VY * H1N + hll_]) + half * SdY[VY * H1N + hll_];
+        const T ll_bx = (Sws[BX * H1N + hll_] + half * SdX[BX * H1N + hll_]) + half * SdY[BX * H1N + hll_];
+        const T ll_by = (Sws[BY * H1N + hll_] + half * SdX[BY * H1N + hll_]) + half * SdY[BY * H1N + hll_];
+        const T rl_vx = (Sws[VX * H1N + hrl] - half * SdX[VX * H1N + hrl]) + half * SdY[VX * H1N + hrl];
+        const T rl_vy = (Sws[VY * H1N + hrl] - half * SdX[VY * H1N + hrl]) + half * SdY[VY * H1N + hrl];
+        const T rl_bx = (Sws[BX * H1N + hrl] - half * SdX[BX * H1N + hrl]) + half * SdY[BX * H1N + hrl];
+        const T rl_by = (Sws[BY * H1N + hrl] - half * SdX[BY * H1N + hrl]) + half * SdY[BY * H1N + hrl];
+        const T lr_vx = (Sws[VX * H1N + hlr] + half * SdX[VX * H1N + hlr]) - half * SdY[VX * H1N + hlr];
+        const T lr_vy = (Sws[VY * H1N + hlr] + half * SdX[VY * H1N + hlr]) - half * SdY[VY * H1N + hlr];
+        const T lr_bx = (Sws[BX * H1N + hlr] + half * SdX[BX * H1N + hlr]) - half * SdY[BX * H1N + hlr];
+        const T lr_by = (Sws[BY * H1N + hlr] + half * SdX[BY * H1N + hlr]) - half * SdY[BY * H1N + hlr];
+        const T rr_vx = (Sws[VX * H1N + hrr] - half * SdX[VX * H1N + hrr]) - half * SdY[VX * H1N + hrr];
+        const T rr_vy = (Sws[VY * H1N + hrr] - half * SdX[VY * H1N + hrr]) - half * SdY[VY * H1N + hrr];
+        const T rr_bx = (Sws[BX * H1N + hrr] - half * SdX[BX * H1N + hrr]) - half * SdY[BX * H1N + hrr];
+        const T rr_by = (Sws[BY * H1N + hrr] - half * SdX[BY * H1N + hrr]) - half * SdY[BY * H1N + hrr];
+        const T Ell = ll_vy * ll_bx - ll_vx * ll_by;
+        const T Erl = rl_vy * rl_bx - rl_vx * rl_by;
+        const T Elr = lr_vy * lr_bx - lr_vx * lr_by;
+        const T Err = rr_vy * rr_bx - rr_vx * rr_by;
+        const T apa = tmax(T(0), tmax(SXc[H1N + hrl], SXc[H1N + hrr]));
+        const T ama = tmax(T(0), tmax(-SXc[hrl], -SXc[hrr]));
+        const T apb = tmax(T(0), tmax(SYc[H1N + hlr], SYc[H1N + hrr]));
+        const T amb = tmax(T(0), tmax(-SYc[hlr], -SYc[hrr]));
+        EZ[hrr] = emf(Ell, Erl, Elr, Err, ll_bx, rl_bx, lr_bx, rr_bx, ll_by, rl_by, lr_by, rr_by, apa, ama, apb, amb);
+      }
+    }
     {
-      double v = (double)smax_t;
+      // values of plane p carried to the next plane: its upper z-face
+      // state and its +z corner values for the x- and y-edges above it
+      for (int ci = tid; ci < (TX + 2) * (TY + 2); ci += NT) {
+        const int i = ci % (TX + 2) - 1, j = ci / (TX + 2) - 1, h = H1(i, j);
+        if (i > tx || j > ty) continue;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if ((tid & 31) == 0) red[tid >> 5] = v;
-      __syncthreads();
-      if (tid < 32) {
-        double u = tid < NT / 32 ? red[tid] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) u = fmax(u, __shfl_xor_sync(0xffffffffu, u, o));
-        if (tid == 0) {
-          atomicMax(&c.smax_new[P], (unsigned long long)__double_as_longlong(u));
-          if (s_fallback) atomicAdd((unsigned long long *)&c.cnt[CNT_FALLBACKS], (unsigned long long)s_fallback);
+        for (int k = 0; k < 8; k++) ZP[k * H1N + h] = Sws[k * H1N + h] + half * SdZ[k * H1N + h];
+        {  // x-edges: a = y, b = z; corners (+y,+z) and (-y,+z)
+          const T py_vy = (Sws[VY * H1N + h] + half * SdY[VY * H1N + h]) + half * SdZ[VY * H1N + h];
+          const T py_vz = (Sws[VZ * H1N + h] + half * SdY[VZ * H1N + h]) + half * SdZ[VZ * H1N + h];
+          const T py_by = (Sws[BY * H1N + h] + half * SdY[BY * H1N + h]) + half * SdZ[BY * H1N + h];
+          const T py_bz = (Sws[BZ * H1N + h] + half * SdY[BZ * H1N + h]) + half * SdZ[BZ * H1N + h];
+          const T my_vy = (Sws[VY * H1N + h] - half * SdY[VY * H1N + h]) + half * SdZ[VY * H1N + h];
+          const T my_vz = (Sws[VZ * H1N + h] - half * SdY[VZ * H1N + h]) + half * SdZ[VZ * H1N + h];
+          const T my_by = (Sws[BY * H1N + h] - half * SdY[BY * H1N + h]) + half * SdZ[BY * H1N + h];
+          const T my_bz = (Sws[BZ * H1N + h] - half * SdY[BZ * H1N + h]) + half * SdZ[BZ * H1N + h];
+          CX[0 * H1N + h] = py_vz * py_by - py_vy * py_bz;
+          CX[1 * H1N + h] = py_by;
+          CX[2 * H1N + h] = py_bz;
+          CX[3 * H1N + h] = my_vz * my_by - my_vy * my_bz;
+          CX[4 * H1N + h] = my_by;
+          CX[5 * H1N + h] = my_bz;
+        }
+        {  // y-edges: a = z, b = x; corners (+z,+x) and (+z,-x)
+          const T px_vz = (Sws[VZ * H1N + h] + half * SdZ[VZ * H1N + h]) + half * SdX[VZ * H1N + h];
+          const T px_vx = (Sws[VX * H1N + h] + half * SdZ[VX * H1N + h]) + half * SdX[VX * H1N + h];
+          const T px_bz = (Sws[BZ * H1N + h] + half * SdZ[BZ * H1N + h]) + half * SdX[BZ * H1N + h];
+          const T px_bx = (Sws[BX * H1N + h] + half * SdZ[BX * H1N + h]) + half * SdX[BX * H1N + h];
+          const T mx_vz = (Sws[VZ * H1N + h] + half * SdZ[VZ * H1N + h]) - half * SdX[VZ * H1N + h];
+          const T mx_vx = (Sws[VX * H1N + h] + half * SdZ[VX * H1N + h]) - half * SdX[VX * H1N + h];
+          const T mx_bz = (Sws[BZ * H1N + h] + half * SdZ[BZ * H1N + h]) - half * SdX[BZ * H1N + h];
+          const T mx_bx = (Sws[BX * H1N + h] + half * SdZ[BX * H1N + h]) - half * SdX[BX * H1N + h];
+          CY[0 * H1N + h] = px_vx * px_bz - px_vz * px_bx;
+          CY[1 * H1N + h] = px_bz;
+          CY[2 * H1N + h] = px_bx;
+          CY[3 * H1N + h] = mx_vx * mx_bz - mx_vz * mx_bx;
+          CY[4 * H1N + h] = mx_bz;
+          CY[5 * H1N + h] = mx_bx;
         }
       }
-      __syncthreads();
     }
+    __syncthreads();
+  }
+
+  // signal speed of the new slice: block max, then the patch max
+  {
+    double v = (double)smax_t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+      double u = tid < NT / 32 ? red[tid] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) u = fmax(u, __shfl_xor_sync(0xffffffffu, u, o));
+      if (tid == 0) {
+        atomicMax(&c.smax_new[P], (unsigned long long)__double_as_longlong(u));
+        if (s_fallback) atomicAdd((unsigned long long *)&c.cnt[CNT_FALLBACKS], (unsigned long long)s_fallback);
+      }
+    }
+    __syncthreads();
   }
 #undef H2
 #undef H1
 #undef F5
 }
 
+// Sweep dispatcher: every (ready patch, tile) work item of the current ready
+// list, grid-strided over a persistent grid.
+// VARIANT only tells apart instantiations compiled with different
+// floating-point contraction flags (FP64 with and without FMA).
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
+__global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ TileShared<T, NT> S;
+  const long long nwork = (long long)c.ctl[CTL_NREADY] * c.tiles;
+  for (long long w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int r = (int)(w / c.tiles), tile = (int)(w % c.tiles);
+    process_tile<T, TX, TY, NT, false>(c, c.R[r], c.dtR[r], tile, reinterpret_cast<T *>(smraw), S);
+  }
+}
+
+// ---------------------------------------------------------------- ready queue
+// The ring holds 2*np slots; entry e lives in slot e % (2*np).  A producer
+// may fill slot s with entry e once q_free[s] == e; a consumer may read it
+// once q_seq[s] == e.  Every wait is bounded by c.wait_budget clock cycles,
+// after which the waiter records DSP_ERR_TIMEOUT and the kernel winds down.
+
+static __device__ __forceinline__ void queue_push(const DevCtx &c, int Q, double dt) {
+  const unsigned long long C = 2ull * (unsigned long long)c.np;
+  const unsigned long long e = atomicAdd(&c.q_ctl[1], 1ull);
+  const int slot = (int)(e % C);
+  const long long t0 = clock64();
+  while (ld_acquire(&c.q_free[slot]) != e) {
+    if (clock64() - t0 > c.wait_budget || ld_acquire(&c.ctl[CTL_STATUS]) != 0) {
+      set_error(c, DSP_ERR_TIMEOUT, Q, -1);
+      return;
+    }
+    __nanosleep(100);
+  }
+  c.q_patch[slot] = Q;
+  c.q_dt[slot] = dt;
+  st_release(&c.q_seq[slot], e);
+}
+
+// Queue Q if it is idle and ready; the claim (p_state 0 -> 1) makes sure only
+// one of the patches that finish around the same time queues it.
+static __device__ void try_queue(const DevCtx &c, int Q, double t_end) {
+  for (int attempt = 0; attempt < 8; attempt++) {
+    if (ld_acquire(&c.p_state[Q]) != 0) return;
+    double tq;
+    if (!is_ready<true>(c, Q, t_end, &tq)) return;
+    if (atomicCAS(&c.p_state[Q], 0, 1) != 0) return;
+    __threadfence();
+    if (is_ready<true>(c, Q, t_end, &tq)) {
+      double dt;
+      const int rc = patch_dt<true>(c, Q, tq, t_end, &dt);
+      if (rc != DSP_OK) {
+        set_error(c, rc, Q, -1);
+        return;
+      }
+      atomicExch(&c.smax_new[Q], 0ull);
+      __threadfence();
+      queue_push(c, Q, dt);
+      return;
+    }
+    // Q moved on between the test and the claim: release and look again
+    atomicExch(&c.p_state[Q], 0);
+    __threadfence();
+  }
+}
+
+// The last tile of P is done: publish P's new slice (time, signal speed,
+// schedule entry, newest index with release), then queue P and every
+// neighbour that became ready.
+static __device__ void publish_and_queue(const DevCtx &c, int P, double dt, double t_end) {
+  const int ns = c.ns;
+  const int L = ld_acquire(c.latest + P), Ln = (L + 1) % ns;
+  const double t = __ldcg(c.t_slot + (long long)P * ns + L);
+  const double tn = t + dt;
+  c.t_slot[(long long)P * ns + Ln] = tn;
+  c.smax_slot[(long long)P * ns + Ln] = __longlong_as_double((long long)atomicAdd(&c.smax_new[P], 0ull));
+  c.dt_last[P] = dt;
+  const unsigned long long e = atomicAdd((unsigned long long *)&c.cnt[CNT_NSCHED], 1ull);
+  if ((long long)e < c.sched_cap) {
+    c.sched[e].patch = P;
+    c.sched[e].t_start = t;
+    c.sched[e].dt = dt;
+  }
+  atomicAdd((unsigned long long *)&c.cnt[CNT_PATCH_UPDATES], 1ull);
+  atomicAdd((unsigned long long *)&c.cnt[CNT_CELL_UPDATES], (unsigned long long)c.nc);
+  __threadfence();
+  st_release(c.latest + P, Ln);
+  __threadfence();
+  if (!(tn < t_end)) atomicAdd(&c.q_ctl[2], 1ull);
+  st_release(&c.p_state[P], 0);
+  __threadfence();
+  try_queue(c, P, t_end);
+  for (int k = c.nbl_off[P]; k < c.nbl_off[P + 1]; k++) try_queue(c, c.nbl[k], t_end);
+}
+
+// Persistent ready-queue dispatcher (one block per resident slot): claim the
+// next (entry, tile) work item, wait for the entry, update the tile; the block
+// that finishes a patch's last tile publishes it and queues what became ready.
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
+__global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ TileShared<T, NT> S;
+  __shared__ int s_P, s_tile, s_exit;
+  __shared__ double s_dt;
+  const int tid = threadIdx.x;
+  const unsigned long long C = 2ull * (unsigned long long)c.np;
+  for (;;) {
+    if (tid == 0) {
+      s_exit = 0;
+      const unsigned long long w = atomicAdd(&c.q_ctl[0], 1ull);
+      const unsigned long long e = w / (unsigned long long)c.tiles;
+      const int slot = (int)(e % C);
+      const long long t0 = clock64();
+      while (ld_acquire(&c.q_seq[slot]) != e) {
+        if (ld_acquire(&c.q_ctl[2]) >= (unsigned long long)c.np || ld_acquire(&c.ctl[CTL_STATUS]) != 0) {
+          s_exit = 1;
+          break;
+        }
+        if (clock64() - t0 > c.wait_budget) {
+          set_error(c, DSP_ERR_TIMEOUT, -1, -1);
+          s_exit = 1;
+          break;
+        }
+        __nanosleep(200);
+      }
+      if (!s_exit) {
+        s_P = __ldcg(c.q_patch + slot);
+        s_dt = __ldcg(c.q_dt + slot);
+        s_tile = (int)(w % (unsigned long long)c.tiles);
+        const int r = atomicAdd(&c.q_reads[slot], 1);
+        if (r == c.tiles - 1) {
+          c.q_reads[slot] = 0;
+          st_release(&c.q_free[slot], e + C);
+        }
+      }
+    }
+    __syncthreads();
+    if (s_exit) return;
+    const int P = s_P, tile = s_tile;
+    const double dt = s_dt;
+    process_tile<T, TX, TY, NT, true>(c, P, dt, tile, reinterpret_cast<T *>(smraw), S);
+    if (tid == 0) {
+      __threadfence();
+      const int k = atomicAdd(&c.tiles_done[P], 1);
+      if (k == c.tiles - 1) {
+        __threadfence();
+        c.tiles_done[P] = 0;
+        publish_and_queue(c, P, dt, t_end);
+      }
+    }
+    __syncthreads();
+  }
+}
 template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
 int launch_update(const DevCtx &c, int grid, void *stream) {
   const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
@@ -665,6 +822,28 @@ int launch_update(const DevCtx &c, int grid, void *stream) {
     configured = true;
   }
   update_kernel<T, TX, TY, NT, MINB, VARIANT><<<grid, NT, smem, (cudaStream_t)stream>>>(c);
+  return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
+}
+
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
+int launch_queue(const DevCtx &c, int grid, double t_end, void *stream) {
+  const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
+  static bool configured = false;
+  if (!configured) {
+    if (cudaFuncSetAttribute(queue_kernel<T, TX, TY, NT, MINB, VARIANT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return DSP_ERR_CUDA;
+    configured = true;
+  }
+  // one block per resident slot, so that every waiting block is co-resident
+  // with the blocks it waits for
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, queue_kernel<T, TX, TY, NT, MINB, VARIANT>, NT, smem);
+  if (per < 1) return DSP_ERR_CUDA;
+  const int g = nsm * per < grid ? nsm * per : grid;
+  queue_kernel<T, TX, TY, NT, MINB, VARIANT><<<g, NT, smem, (cudaStream_t)stream>>>(c, t_end);
   return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
 }
 

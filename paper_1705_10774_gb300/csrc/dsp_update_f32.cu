@@ -12,4 +12,7 @@ void update_tile_f32(int *tx, int *ty) {
   *tx = TX32;
   *ty = TY32;
 }
+int launch_queue_f32(const DevCtx &c, int grid, double t_end, void *stream) {
+  return launch_queue<float, TX32, TY32, NT32, MB32, 0>(c, grid, t_end, stream);
+}
 }  // namespace dsp

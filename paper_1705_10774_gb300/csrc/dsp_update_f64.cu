@@ -12,4 +12,7 @@ void update_tile_f64(int *tx, int *ty) {
   *tx = TX64;
   *ty = TY64;
 }
+int launch_queue_f64(const DevCtx &c, int grid, double t_end, void *stream) {
+  return launch_queue<double, TX64, TY64, NT64, MB64, 0>(c, grid, t_end, stream);
+}
 }  // namespace dsp

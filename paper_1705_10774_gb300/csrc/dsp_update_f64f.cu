@@ -9,4 +9,7 @@ int launch_update_f64f(const DevCtx &c, int grid, void *stream) {
   return launch_update<double, TXF, TYF, NTF, MBF, 1>(c, grid, stream);
 }
 int update_grid_f64f(const DevCtx &c) { return update_grid<double, TXF, TYF, NTF, MBF, 1>(c); }
+int launch_queue_f64f(const DevCtx &c, int grid, double t_end, void *stream) {
+  return launch_queue<double, TXF, TYF, NTF, MBF, 1>(c, grid, t_end, stream);
+}
 }  // namespace dsp

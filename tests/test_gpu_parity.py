@@ -245,6 +245,9 @@ def test_rejected_inputs():
         Dispatch(lay.n, lay.lo, **base, dispatcher=7)
     assert e.value.code in (DSP_ERR_UNSUPPORTED, DSP_ERR_INVALID_ARG)
     with pytest.raises(DispatchError) as e:
+        Dispatch(lay.n, lay.lo, **base, dispatcher=0, time_mode=0)   # a global step needs sweeps
+    assert e.value.code == DSP_ERR_UNSUPPORTED
+    with pytest.raises(DispatchError) as e:
         Dispatch(lay.n[:-1], lay.lo[:-1], **base)           # does not tile the box
     assert e.value.code == DSP_ERR_INVALID_ARG
     f = ics.config_uniform(lay, [1.0, 0, 0, 0, 0.6, 0, 0, 0], 5.0 / 3.0)
@@ -254,3 +257,51 @@ def test_rejected_inputs():
     with pytest.raises(DispatchError) as e:
         g.set_state(U, bx, by, bz)
     assert e.value.code == DSP_ERR_UNPHYSICAL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ready_queue_dispatcher_matches_sweeps_and_oracle(precision):
+    """The persistent ready-queue kernel (blocks claim work, publish patches
+    and queue ready neighbours concurrently) gives the same schedule, as a
+    set, as the sweep dispatcher and the oracle's time-sorted queue, and the
+    same state bit for bit."""
+    lay, f = _lts_case()
+    state = ics.to_patches(lay, f)
+    kw = kw_of(lay, f, time_mode=1)
+    q = Dispatch(lay.n, lay.lo, **kw, precision=precision, dispatcher=0, sched_capacity=1 << 20)
+    w = Dispatch(lay.n, lay.lo, **kw, precision=precision, dispatcher=1, sched_capacity=1 << 20)
+    for g in (q, w):
+        g.set_state(*state)
+        g.advance(t_end=0.003)
+    key = lambda s: sorted(zip(*(x.tolist() for x in s)))
+    assert key(q.schedule()) == key(w.schedule())
+    for a, b in zip(q.get_state(), w.get_state()):
+        assert np.array_equal(a, b)
+    assert np.all(q.times()[0] == 0.003)
+    if precision == 0:
+        o = Oracle(lay.n, lay.lo, **kw_of(lay, f, time_mode=1, dispatcher=0))
+        o.set_state(*state)
+        o.advance(t_end=0.003)
+        assert key(q.schedule()) == key(o.schedule())
+        for a, b in zip(q.get_state(), o.get_state()):
+            assert np.array_equal(a, b)
+
+
+def test_ready_queue_wait_budget_ends_in_timeout_not_a_hang():
+    """A wait budget of a few hundred cycles is too short for any update to
+    finish: the blocks' waits run out, the kernel returns DSP_ERR_TIMEOUT,
+    the context is poisoned and the GPU stays usable."""
+    from paper_1705_10774_gb300.dispatch import DSP_ERR_TIMEOUT
+    lay, f = _lts_case()
+    state = ics.to_patches(lay, f)
+    g = Dispatch(lay.n, lay.lo, **kw_of(lay, f, time_mode=1), dispatcher=0, wait_budget=200)
+    g.set_state(*state)
+    with pytest.raises(DispatchError) as e:
+        g.advance(t_end=0.003)
+    assert e.value.code == DSP_ERR_TIMEOUT
+    with pytest.raises(DispatchError):
+        g.advance(t_end=0.003)          # poisoned
+    g.close()
+    h = Dispatch(lay.n, lay.lo, **kw_of(lay, f, time_mode=1), dispatcher=1)
+    h.set_state(*state)
+    h.advance(t_end=0.001)              # the device still works
