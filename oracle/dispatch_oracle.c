@@ -44,6 +44,11 @@
 
 enum { RHO = 0, VX = 1, VY = 2, VZ = 3, PR = 4, BX = 5, BY = 6, BZ = 7 };
 
+/* Pressure floor of the primitive recovery, p >= PFLOOR * rho (a sound-speed
+ * floor of 1e-10 in code units), as in the RAMSES solvers the paper ported
+ * (Sec. 4.1).  The conserved energy is never modified. */
+#define PFLOOR 1e-20
+
 typedef struct {
   int n[3];
   int64_t lo[3];
@@ -92,6 +97,7 @@ static void prim(const double u[5], double bxl, double bxr, double byl, double b
   double ke = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
   double me = 0.5 * (Bx * Bx + By * By + Bz * Bz);
   double p = (gamma - 1.0) * (u[4] - ke - me);
+  p = fmax(p, PFLOOR * rho);
   W[RHO] = rho; W[VX] = vx; W[VY] = vy; W[VZ] = vz; W[PR] = p;
   W[BX] = Bx; W[BY] = By; W[BZ] = Bz;
 }
