@@ -11,6 +11,11 @@ namespace dsp {
 
 enum { RHO = 0, VX = 1, VY = 2, VZ = 3, PR = 4, BX = 5, BY = 6, BZ = 7 };
 
+// Pressure floor of the primitive recovery, p >= PFLOOR * rho (a sound-speed
+// floor of 1e-10), as in RAMSES-type solvers; the conserved energy is never
+// modified.
+constexpr double PFLOOR = 1e-20;
+
 template <typename T> __device__ __forceinline__ T tmin(T a, T b);
 template <typename T> __device__ __forceinline__ T tmax(T a, T b);
 template <> __device__ __forceinline__ double tmin<double>(double a, double b) { return fmin(a, b); }
@@ -36,6 +41,7 @@ __device__ __forceinline__ void prim(T rho, T mx, T my, T mz, T E, T bxl, T bxr,
   T ke = h * rho * (vx * vx + vy * vy + vz * vz);
   T me = h * (Bx * Bx + By * By + Bz * Bz);
   T p = (gamma - T(1)) * (E - ke - me);
+  p = tmax(p, T(PFLOOR) * rho);
   W[RHO] = rho; W[VX] = vx; W[VY] = vy; W[VZ] = vz; W[PR] = p;
   W[BX] = Bx; W[BY] = By; W[BZ] = Bz;
 }

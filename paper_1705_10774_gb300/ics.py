@@ -297,12 +297,13 @@ def gaussian_filtered_noise(shape, box, sigma_f, rng):
 
 
 def config_lts(seed=17051, patches=16, n=16, sigma_ln=1.5, hot_radius=0.1, hot_factor=1000.0,
-               mach=1.0, beta=10.0):
+               mach=1.0, beta=10.0, edge_cells=2.0):
     """Local-time-step stress input: log-normal density (sigma_ln = 1.5,
     Gaussian-filtered noise, filter width 1/16 of the box) in pressure
     equilibrium p = 0.6, a central sphere of radius 0.1 at 1000x temperature
-    (density / 1000), random solenoidal velocity at rms Mach 1, uniform B
-    along x at beta = 10."""
+    (density / 1000, the edge smoothed over 2 cells), random solenoidal
+    velocity at rms Mach 1 with the local sound speed (volume rms of
+    |v|/c_s = 1), uniform B along x at beta = 10."""
     rng = np.random.default_rng(seed)
     lay = cartesian(patches, n)
     X, Y, Z = lay.base_cells
@@ -313,9 +314,19 @@ def config_lts(seed=17051, patches=16, n=16, sigma_ln=1.5, hot_radius=0.1, hot_f
     zz, yy, xx = np.meshgrid(zc, y, x, indexing="ij")
     c = np.array(lay.box_len) / 2
     r2 = (xx - c[0]) ** 2 + (yy - c[1]) ** 2 + (zz - c[2]) ** 2
-    rho = np.where(r2 < hot_radius ** 2, rho / hot_factor, rho)
-    v = solenoidal_velocity(shape, lay.box_len, 1.0, 4.0, mach, rng)
+    # temperature contrast hot_factor inside the sphere, its edge smoothed
+    # over `edge_cells` cells with a tanh profile (in log density)
+    if edge_cells > 0:
+        w = 0.5 * (1.0 - np.tanh((np.sqrt(r2) - hot_radius) / (edge_cells * lay.dx)))
+        rho = rho * np.exp(-np.log(hot_factor) * w)
+    else:
+        rho = np.where(r2 < hot_radius ** 2, rho / hot_factor, rho)
     p = np.full(shape, 0.6)
+    # rms Mach number taken with the local sound speed: scale the solenoidal
+    # field so that the volume rms of |v| / c_s(x) is `mach`
+    v = solenoidal_velocity(shape, lay.box_len, 1.0, 4.0, 1.0, rng)
+    cs = np.sqrt(5.0 / 3.0 * p / rho)
+    v *= mach / np.sqrt(np.mean((v[0] ** 2 + v[1] ** 2 + v[2] ** 2) / cs ** 2))
     B0 = np.sqrt(2 * 0.6 / beta)
     f = Fields(rho=rho, v=v, p=p, bx=np.full(shape, B0), by=np.zeros(shape), bz=np.zeros(shape),
                gamma=5.0 / 3.0)
