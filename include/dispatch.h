@@ -92,7 +92,9 @@ typedef struct {
  *                context's stream and report the total in dsp_stats
  *   wait_budget  ready-queue dispatcher only: SM clock cycles a device wait
  *                may spin without progress before the run stops with
- *                DSP_ERR_TIMEOUT (0 = default, about two seconds) */
+ *                DSP_ERR_TIMEOUT (0 = default, about two seconds)
+ *   graph        sweep dispatcher only: 1 = capture batches of 32 sweeps
+ *                (plan + update kernels) in a CUDA graph and replay it */
 typedef struct {
   double gamma, cfl, t0, dt_max, grace;
   double box_lo[3], box_len[3];
@@ -102,6 +104,7 @@ typedef struct {
   int64_t sched_capacity;
   int32_t timing;
   int64_t wait_budget;
+  int32_t graph;
 } dsp_params;
 
 /* Counters of one dsp_advance call.  kernel_ms and kernel_launches are the

@@ -55,6 +55,9 @@ struct dsp_ctx {
   int grid_update;
   cudaEvent_t ev[2 * 32];
   int nev;
+  cudaGraphExec_t graph_exec;  // a captured batch of sweeps
+  double graph_t_end;
+  int graph_timing;
 };
 
 namespace {
@@ -692,18 +695,46 @@ extern "C" int dsp_advance(dsp_ctx *c, double t_end, int64_t max_sweeps, dsp_sta
     for (int i = 0; i < 2 * batch; i++) CK(cudaEventCreate(&c->ev[i]));
     c->nev = 2 * batch;
   }
-  for (;;) {
-    long long nb = batch;
-    if (max_sweeps > 0) nb = std::min<long long>(nb, max_sweeps - done_sweeps);
+  // one batch of sweeps: plan + update kernels, optionally replayed from a
+  // CUDA graph captured once per (t_end, timing) setting
+  auto issue_batch = [&](long long nb) -> int {
     for (long long s = 0; s < nb; s++) {
       plan_kernel<<<1, PLAN_NT, 0, c->stream>>>(c->d, t_end, global_mode, 0);
       CK(cudaGetLastError());
-      plans++;
       if (timing) CK(cudaEventRecord(c->ev[2 * s], c->stream));
-      rc = launch_update(c);
-      if (rc) return fail(c, rc, "update kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+      const int r2 = launch_update(c);
+      if (r2) return fail(c, r2, "update kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
       if (timing) CK(cudaEventRecord(c->ev[2 * s + 1], c->stream));
     }
+    return DSP_OK;
+  };
+  for (;;) {
+    long long nb = batch;
+    if (max_sweeps > 0) nb = std::min<long long>(nb, max_sweeps - done_sweeps);
+    if (c->prm.graph && nb == batch) {
+      if (c->graph_exec && (c->graph_t_end != t_end || c->graph_timing != (int)timing)) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+      }
+      if (!c->graph_exec) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        const int r1 = issue_batch(nb);
+        cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+        if (r1) return r1;
+        if (ee != cudaSuccess) return fail(c, DSP_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ee));
+        ee = cudaGraphInstantiate(&c->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ee != cudaSuccess) return fail(c, DSP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ee));
+        c->graph_t_end = t_end;
+        c->graph_timing = (int)timing;
+      }
+      CK(cudaGraphLaunch(c->graph_exec, c->stream));
+    } else {
+      rc = issue_batch(nb);
+      if (rc) return rc;
+    }
+    plans += nb;
     done_sweeps += nb;
     rc = read_status(c);
     if (rc) return rc;
@@ -903,6 +934,7 @@ extern "C" const char *dsp_last_error(dsp_ctx *c) { return c ? c->err.c_str() : 
 extern "C" void dsp_destroy(dsp_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   for (int i = 0; i < c->nev; i++) cudaEventDestroy(c->ev[i]);
   free_all(c);
   delete c;

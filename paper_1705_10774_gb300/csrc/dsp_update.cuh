@@ -813,14 +813,9 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
 }
 template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
 int launch_update(const DevCtx &c, int grid, void *stream) {
+  // the shared-memory attribute was set by update_grid when the context was
+  // created (a launch may be inside a stream capture)
   const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
-  static bool configured = false;
-  if (!configured) {
-    if (cudaFuncSetAttribute(update_kernel<T, TX, TY, NT, MINB, VARIANT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return DSP_ERR_CUDA;
-    configured = true;
-  }
   update_kernel<T, TX, TY, NT, MINB, VARIANT><<<grid, NT, smem, (cudaStream_t)stream>>>(c);
   return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
 }

@@ -305,3 +305,29 @@ def test_ready_queue_wait_budget_ends_in_timeout_not_a_hang():
     h = Dispatch(lay.n, lay.lo, **kw_of(lay, f, time_mode=1), dispatcher=1)
     h.set_state(*state)
     h.advance(t_end=0.001)              # the device still works
+
+
+@pytest.mark.parametrize("lts", [False, True])
+def test_graph_replay_of_sweeps_is_identical(lts):
+    """Sweeps replayed from a captured CUDA graph (batches of 32) give the
+    same state and schedule as sweeps launched one by one."""
+    if lts:
+        lay, f = _lts_case()
+        common, run = dict(time_mode=1), dict(t_end=0.003)
+    else:
+        lay, f = ics.config_linear_waves(n=8, amplitude=1e-3)
+        common, run = dict(time_mode=0), dict(max_sweeps=70)
+    state = ics.to_patches(lay, f)
+    res = []
+    for graph in (0, 1):
+        g = Dispatch(lay.n, lay.lo, **kw_of(lay, f, **common), graph=graph, sched_capacity=1 << 20)
+        g.set_state(*state)
+        st = g.advance(**run)
+        res.append((g.get_state(), g.schedule(), st))
+    (a, sa, _), (b, sb, stb) = res
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x, y)
+    if not lts:
+        assert stb["sweeps"] == 70
