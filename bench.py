@@ -369,6 +369,90 @@ def reference_arm(args):
     }))
 
 
+def lts_arm(args):
+    """Local time steps on the 4096-patch input (16^3 patches of 16^3 cells,
+    log-normal density, hot sphere): both dispatchers, FP64 (FMA) and FP32,
+    to t_end; and the same input with one global step per sweep, for the
+    ratio of cell-updates needed (the paper's local-time-step advantage)."""
+    import torch
+    from paper_1705_10774_gb300 import ics
+    from paper_1705_10774_gb300.dispatch import Dispatch
+    lay, f = ics.config_lts(patches=16, n=16)
+    state = [torch.from_numpy(a).cuda() for a in ics.to_patches(lay, f)]
+    stream = torch.cuda.current_stream()
+    kw = dict(gamma=f.gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len, stream=stream.cuda_stream)
+    out = {"workload": "local steps, 4096 patches of 16^3 (256^3), log-normal rho, hot sphere", "t_end": args.t_end}
+    for name, prec, disp, mode in [("f64_queue", F64_PRECISION, 0, 1), ("f64_sweep_graph", F64_PRECISION, 1, 1),
+                                   ("f32_queue", 1, 0, 1), ("f32_sweep_graph", 1, 1, 1), ("f32_global", 1, 1, 0)]:
+        st_in = [a.float() for a in state] if prec == 1 else state
+        g = Dispatch(lay.n, lay.lo, precision=prec, dispatcher=disp, time_mode=mode, graph=1, timing=1,
+                     sched_capacity=1 << 24 if mode == 1 and disp == 1 else 0, **kw)
+        g.set_state(*st_in)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = g.advance(t_end=args.t_end)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        r = {"ms": ms, "cell_updates": st["cell_updates"], "patch_updates": st["patch_updates"],
+             "sweeps": st["sweeps"], "cell_updates_per_s": st["cell_updates"] / (ms * 1e-3)}
+        if name == "f64_sweep_graph" or name == "f32_sweep_graph":
+            _, _, dts = g.schedule()
+            lv, cnt = np.unique(dts, return_counts=True)
+            r["dt_levels"] = int(len(lv))
+            r["dt_ratio_max_min"] = float(lv.max() / lv.min())
+        out[name] = r
+        g.close()
+    out["lts_over_global_cell_updates"] = out["f32_queue"]["cell_updates"] / out["f32_global"]["cell_updates"]
+    print(json.dumps(out))
+
+
+def orszag_tang_arm(args):
+    """3-D Orszag-Tang vortex: FP32 state against FP64 on the same GPU, from
+    the same input to the same time: relative L1 of density, momentum,
+    energy and field, conservation drift, max div B (per max |B|)."""
+    import torch
+    from paper_1705_10774_gb300 import ics
+    from paper_1705_10774_gb300.dispatch import Dispatch
+    lay, f = ics.config_orszag_tang(patches=args.patches, n=NCELL)
+    state = ics.to_patches(lay, f)
+    del f
+    stream = torch.cuda.current_stream()
+    kw = dict(gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len, time_mode=0,
+              stream=stream.cuda_stream)
+    res = {}
+    for name, prec in (("f64", F64_PRECISION), ("f32", 1)):
+        g = Dispatch(lay.n, lay.lo, precision=prec, **kw)
+        g.set_state(*state)
+        d0 = g.diagnostics()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = g.advance(t_end=args.t_end)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        d1 = g.diagnostics()
+        res[name] = dict(state=g.get_state(), d0=d0, d1=d1, st=st, s=el)
+        g.close()
+    a, b = res["f64"]["state"], res["f32"]["state"]
+    npch = lay.npatch
+    A, B = a[0].reshape(npch, 5, -1), b[0].reshape(npch, 5, -1)
+    l1 = lambda x, y: float(np.sum(np.abs(x - y)) / np.sum(np.abs(x)))
+    errs = {"rho": l1(A[:, 0], B[:, 0]), "mom": l1(A[:, 1:4], B[:, 1:4]), "E": l1(A[:, 4], B[:, 4]),
+            "b": l1(np.concatenate(a[1:]), np.concatenate(b[1:]))}
+    drift = {}
+    for name in ("f64", "f32"):
+        d0, d1 = res[name]["d0"], res[name]["d1"]
+        drift[name] = {"mass": abs(d1["mass"] - d0["mass"]) / abs(d0["mass"]),
+                       "energy": abs(d1["energy"] - d0["energy"]) / abs(d0["energy"]),
+                       "max_divb_over_max_b": d1["max_divb"] / d1["max_b"],
+                       "steps": res[name]["st"]["sweeps"], "seconds": res[name]["s"],
+                       "cell_updates_per_s": res[name]["st"]["cell_updates"] / res[name]["s"]}
+    print(json.dumps({"workload": "Orszag-Tang %d^3 (%d patches of %d^3)" % (lay.base_cells[0], npch, NCELL),
+                      "t_end": args.t_end, "f32_vs_f64_relative_L1": errs, "per_form": drift}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -383,9 +467,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="turbulence", choices=["turbulence", "lts", "orszag-tang"],
+                    help="lts / orszag-tang: side measurements (one JSON line each), not the benchmark line")
+    ap.add_argument("--t-end", type=float, default=0.01, help="end time of the lts / orszag-tang runs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "lts":
+        return lts_arm(args)
+    if args.workload == "orszag-tang":
+        return orszag_tang_arm(args)
     if args.impl == "reference":
         reference_arm(args)
     else:
