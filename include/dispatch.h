@@ -94,7 +94,9 @@ typedef struct {
  *                may spin without progress before the run stops with
  *                DSP_ERR_TIMEOUT (0 = default, about two seconds)
  *   graph        sweep dispatcher only: 1 = capture batches of 32 sweeps
- *                (plan + update kernels) in a CUDA graph and replay it */
+ *                (plan + update kernels) in a CUDA graph and replay it; with
+ *                a NULL stream the context then creates its own blocking
+ *                stream (the legacy stream cannot be captured) */
 typedef struct {
   double gamma, cfl, t0, dt_max, grace;
   double box_lo[3], box_len[3];

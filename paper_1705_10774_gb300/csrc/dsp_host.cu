@@ -58,6 +58,7 @@ struct dsp_ctx {
   cudaGraphExec_t graph_exec;  // a captured batch of sweeps
   double graph_t_end;
   int graph_timing;
+  int own_stream;  // the context created its stream (graph capture needs one)
 };
 
 namespace {
@@ -71,6 +72,7 @@ int fail(dsp_ctx *c, int code, const char *fmt, ...) {
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
     c->err = buf;
+    if (code == DSP_ERR_CUDA) (void)cudaGetLastError();  // do not leak the error into later calls
     if (code == DSP_ERR_CUDA || code == DSP_ERR_UNPHYSICAL || code == DSP_ERR_TIMEOUT || code == DSP_ERR_DEADLOCK ||
         code == DSP_ERR_BRACKET)
       c->poisoned = 1;
@@ -478,6 +480,16 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   memset(&c->d, 0, sizeof c->d);
   c->prm = *prm;
   c->stream = (cudaStream_t)stream;
+  if (!c->stream && prm->graph) {
+    // the legacy default stream cannot be captured: use a blocking stream of
+    // our own, which the legacy stream orders with the caller's work
+    if (cudaStreamCreate(&c->stream) != cudaSuccess) {
+      (void)cudaGetLastError();
+      delete c;
+      return DSP_ERR_CUDA;
+    }
+    c->own_stream = 1;
+  }
   c->precision = prm->precision;
   c->esize = prm->precision == 1 ? 4 : 8;
   c->poisoned = 0;
@@ -550,7 +562,9 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   }
   if (ok && cudaMallocHost((void **)&c->h_ctl, sizeof(int) * CTL_COUNT) != cudaSuccess) ok = false;
   if (!ok) {
+    (void)cudaGetLastError();
     free_all(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return DSP_ERR_OOM;
   }
@@ -592,7 +606,9 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
+    (void)cudaGetLastError();
     free_all(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return DSP_ERR_CUDA;
   }
@@ -937,5 +953,6 @@ extern "C" void dsp_destroy(dsp_ctx *c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   for (int i = 0; i < c->nev; i++) cudaEventDestroy(c->ev[i]);
   free_all(c);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
