@@ -713,14 +713,16 @@ extern "C" int dsp_advance(dsp_ctx *c, double t_end, int64_t max_sweeps, dsp_sta
   }
   // one batch of sweeps: plan + update kernels, optionally replayed from a
   // CUDA graph captured once per (t_end, timing) setting
-  auto issue_batch = [&](long long nb) -> int {
+  // per-launch events are recorded only outside graphs; a replayed graph is
+  // timed as a whole (its plan kernels are a few microseconds each)
+  auto issue_batch = [&](long long nb, bool events) -> int {
     for (long long s = 0; s < nb; s++) {
       plan_kernel<<<1, PLAN_NT, 0, c->stream>>>(c->d, t_end, global_mode, 0);
       CK(cudaGetLastError());
-      if (timing) CK(cudaEventRecord(c->ev[2 * s], c->stream));
+      if (events) CK(cudaEventRecord(c->ev[2 * s], c->stream));
       const int r2 = launch_update(c);
       if (r2) return fail(c, r2, "update kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-      if (timing) CK(cudaEventRecord(c->ev[2 * s + 1], c->stream));
+      if (events) CK(cudaEventRecord(c->ev[2 * s + 1], c->stream));
     }
     return DSP_OK;
   };
@@ -735,7 +737,7 @@ extern "C" int dsp_advance(dsp_ctx *c, double t_end, int64_t max_sweeps, dsp_sta
       if (!c->graph_exec) {
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        const int r1 = issue_batch(nb);
+        const int r1 = issue_batch(nb, false);
         cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
         if (r1) return r1;
         if (ee != cudaSuccess) return fail(c, DSP_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ee));
@@ -745,16 +747,23 @@ extern "C" int dsp_advance(dsp_ctx *c, double t_end, int64_t max_sweeps, dsp_sta
         c->graph_t_end = t_end;
         c->graph_timing = (int)timing;
       }
+      if (timing) CK(cudaEventRecord(c->ev[0], c->stream));
       CK(cudaGraphLaunch(c->graph_exec, c->stream));
+      if (timing) CK(cudaEventRecord(c->ev[1], c->stream));
     } else {
-      rc = issue_batch(nb);
+      rc = issue_batch(nb, timing);
       if (rc) return rc;
     }
+    const bool graphed = c->prm.graph && nb == batch;
     plans += nb;
     done_sweeps += nb;
     rc = read_status(c);
     if (rc) return rc;
-    if (timing) {
+    if (timing && graphed) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+      kms += ms;
+    } else if (timing) {
       for (long long s = 0; s < nb; s++) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->ev[2 * s], c->ev[2 * s + 1]));
