@@ -453,6 +453,45 @@ def orszag_tang_arm(args):
                       "t_end": args.t_end, "f32_vs_f64_relative_L1": errs, "per_form": drift}))
 
 
+def mixed_arm(args):
+    """Mixed patch sizes on one level (the coarse level of the uneven batched
+    solve): 512^3 cut into 96^3 super-blocks of 16^3, 24^3 or 32^3 patches
+    (seeded, ~40/30/30 % by count) plus 32^3 remainder slabs; turbulence input
+    as the benchmark's (Mach 2, beta 1); FP32 state, local steps, sweeps
+    replayed from CUDA graphs."""
+    import torch
+    from paper_1705_10774_gb300 import ics
+    from paper_1705_10774_gb300.dispatch import Dispatch
+    lay = ics.mixed_blocks(args.blocks, 96, remainder=32, seed=17)
+    X, Y, Z = lay.base_cells
+    rng = np.random.default_rng(10774)
+    v = ics.solenoidal_velocity((Z, Y, X), lay.box_len, 1.0, 4.0, 2.0, rng)
+    f = ics.Fields(rho=np.ones((Z, Y, X)), v=v, p=np.full((Z, Y, X), 0.6), bx=np.full((Z, Y, X), np.sqrt(1.2)),
+                   by=np.zeros((Z, Y, X)), bz=np.zeros((Z, Y, X)), gamma=5.0 / 3.0)
+    state = [torch.from_numpy(a.astype(np.float32)).cuda() for a in ics.to_patches(lay, f)]
+    del f, v
+    stream = torch.cuda.current_stream()
+    g = Dispatch(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
+                 precision=1, time_mode=1, graph=1, timing=1, stream=stream.cuda_stream)
+    g.set_state(*state)
+    g.advance(t_end=args.t_end / 4)           # warm-up
+    g.set_state(*state)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = g.advance(t_end=args.t_end)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sizes, counts = np.unique(lay.n[:, 0], return_counts=True)
+    print(json.dumps({"workload": "mixed 16/24/32 patches, %d^3, %d patches" % (X, lay.npatch),
+                      "patch_sizes": dict(zip(map(int, sizes), map(int, counts))), "t_end": args.t_end,
+                      "ms": ms, "cell_updates": st["cell_updates"], "sweeps": st["sweeps"],
+                      "cell_updates_per_s": st["cell_updates"] / (ms * 1e-3)}))
+    g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -467,9 +506,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="turbulence", choices=["turbulence", "lts", "orszag-tang"],
+    ap.add_argument("--workload", default="turbulence", choices=["turbulence", "lts", "orszag-tang", "mixed"],
                     help="lts / orszag-tang: side measurements (one JSON line each), not the benchmark line")
-    ap.add_argument("--t-end", type=float, default=0.01, help="end time of the lts / orszag-tang runs")
+    ap.add_argument("--t-end", type=float, default=0.01, help="end time of the lts / orszag-tang / mixed runs")
+    ap.add_argument("--blocks", type=int, default=5, help="96^3 super-blocks per axis of the mixed run")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -477,6 +517,8 @@ def main():
         return lts_arm(args)
     if args.workload == "orszag-tang":
         return orszag_tang_arm(args)
+    if args.workload == "mixed":
+        return mixed_arm(args)
     if args.impl == "reference":
         reference_arm(args)
     else:

@@ -38,11 +38,15 @@ struct dsp_ctx {
   std::string err;
   int poisoned;
   // host copies of the tables
-  std::vector<int> nb27, nbl_off, nbl;
+  std::vector<int> nbl_off, nbl;
+  std::vector<PatchGeo> geo;
+  std::vector<long long> coff;  // [4][np+1]
   // device allocations
   void *slab;
   double *t_slot, *smax_slot, *dt_last, *dtR;
-  int *latest, *nb27_d, *nbl_off_d, *nbl_d, *R, *ctl;
+  int *latest, *nbl_off_d, *nbl_d, *R, *ctl, *map_d, *work_off_d;
+  PatchGeo *geo_d;
+  long long *coff_d;
   unsigned long long *smax_new;
   long long *cnt;
   dsp_sched_entry *sched;
@@ -101,10 +105,14 @@ __global__ void __launch_bounds__(PLAN_NT) plan_kernel(DevCtx c, double t_end, i
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int ns = c.ns;
   // 1. publish the previous sweep
+  __shared__ unsigned long long s_cells;
+  if (tid == 0) s_cells = 0;
+  __syncthreads();
   const int nprev = c.ctl[CTL_NREADY];
   const long long s0 = c.cnt[CNT_NSCHED];
   for (int r = tid; r < nprev; r += PLAN_NT) {
     const int P = c.R[r];
+    atomicAdd(&s_cells, (unsigned long long)c.geo[P].n[0] * c.geo[P].n[1] * c.geo[P].n[2]);
     const double dt = c.dtR[r];
     const int L = c.latest[P], Ln = (L + 1) % ns;
     const double t = c.t_slot[(long long)P * ns + L];
@@ -124,7 +132,7 @@ __global__ void __launch_bounds__(PLAN_NT) plan_kernel(DevCtx c, double t_end, i
     if (nprev > 0) {
       c.cnt[CNT_NSCHED] += nprev;
       c.cnt[CNT_PATCH_UPDATES] += nprev;
-      c.cnt[CNT_CELL_UPDATES] += (long long)nprev * c.nc;
+      c.cnt[CNT_CELL_UPDATES] += (long long)s_cells;
       c.cnt[CNT_SWEEPS] += 1;
     }
     c.ctl[CTL_NREADY] = 0;
@@ -182,6 +190,39 @@ __global__ void __launch_bounds__(PLAN_NT) plan_kernel(DevCtx c, double t_end, i
     const double dtg = __longlong_as_double((long long)s_dtmin);
     for (int r = tid; r < nr; r += PLAN_NT) c.dtR[r] = dtg;
   }
+  // work offsets: ready patch r owns update work items [work_off[r], work_off[r+1])
+  __shared__ int s_woff;
+  if (tid == 0) s_woff = 0;
+  __syncthreads();
+  for (int chunk = 0; chunk < nr; chunk += PLAN_NT) {
+    const int r = chunk + tid;
+    const int v = r < nr ? c.geo[c.R[r]].tiles : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) s_wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      const int wv = s_wsum[lane];
+      int wi = wv;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += u;
+      }
+      s_wsum[lane] = wi - wv;
+      if (lane == 31) s_total = wi;
+    }
+    __syncthreads();
+    if (r < nr) c.work_off[r] = s_woff + s_wsum[wid] + incl - v;
+    __syncthreads();
+    if (tid == 0) s_woff += s_total;
+    __syncthreads();
+  }
+  if (tid == 0) c.work_off[nr] = s_woff;
   if (tid == 0) {
     if (c.ctl[CTL_STATUS] != 0) {
       c.ctl[CTL_NREADY] = 0;
@@ -200,10 +241,11 @@ template <typename T>
 __global__ void smax_kernel(DevCtx c, int slot, int first, int count) {
   const int P = first + blockIdx.x;
   if (P >= first + count) return;
-  const T *base = (const T *)c.slab + (long long)slot * c.slot_stride + (long long)P * c.patch_len;
-  const int nx = c.nx, ny = c.ny, nz = c.nz;
-  const long long nc = c.nc;
-  const T *bxa = base + 5 * nc, *bya = bxa + c.nfx, *bza = bya + c.nfy;
+  const PatchGeo &g = c.geo[P];
+  const T *base = (const T *)c.slab + (long long)slot * c.slot_stride + g.off;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const long long nc = (long long)nx * ny * nz;
+  const T *bxa = base + 5 * nc, *bya = bxa + (long long)(nx + 1) * ny * nz, *bza = bya + (long long)nx * (ny + 1) * nz;
   const T gamma = (T)c.gamma;
   double m = 0.0;
   for (long long id = threadIdx.x; id < nc; id += blockDim.x) {
@@ -231,19 +273,22 @@ __global__ void smax_kernel(DevCtx c, int slot, int first, int count) {
 // the slices: dir 0 loads slot 0, dir 1 stores each patch's newest slot.
 template <typename TS, typename TU>
 __global__ void xfer_kernel(DevCtx c, int first, int count, TU *U, TU *bx, TU *by, TU *bz, int dir) {
-  const long long per[4] = {5 * c.nc, c.nfx, c.nfy, c.nfz};
-  const long long off[4] = {0, 5 * c.nc, 5 * c.nc + c.nfx, 5 * c.nc + c.nfx + c.nfy};
   TU *arr[4] = {U, bx, by, bz};
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (int f = 0; f < 4; f++) {
-    const long long n = per[f] * count;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-      const int P = first + (int)(e / per[f]);
-      const long long l = e % per[f];
-      const int s = dir == 0 ? 0 : c.latest[P];
-      TS *slot = (TS *)c.slab + (long long)s * c.slot_stride + (long long)P * c.patch_len + off[f];
-      if (dir == 0) slot[l] = (TS)arr[f][e];
-      else arr[f][e] = (TU)slot[l];
+  for (int P = first + blockIdx.x; P < first + count; P += gridDim.x) {
+    const PatchGeo &g = c.geo[P];
+    const long long nc = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long per[4] = {5 * nc, (long long)(g.n[0] + 1) * g.n[1] * g.n[2],
+                              (long long)g.n[0] * (g.n[1] + 1) * g.n[2], (long long)g.n[0] * g.n[1] * (g.n[2] + 1)};
+    const int s = dir == 0 ? 0 : c.latest[P];
+    TS *slot = (TS *)c.slab + (long long)s * c.slot_stride + g.off;
+    long long so = 0;
+    for (int f = 0; f < 4; f++) {
+      TU *a = arr[f] + (c.coff[f * (c.np + 1) + P] - c.coff[f * (c.np + 1) + first]);
+      for (long long l = threadIdx.x; l < per[f]; l += blockDim.x) {
+        if (dir == 0) slot[so + l] = (TS)a[l];
+        else a[l] = (TU)slot[so + l];
+      }
+      so += per[f];
     }
   }
 }
@@ -308,11 +353,13 @@ template <typename T>
 __global__ void diag_kernel(DevCtx c, double *out) {
   const int P = blockIdx.x;
   const int s = c.latest[P];
-  const T *base = (const T *)c.slab + (long long)s * c.slot_stride + (long long)P * c.patch_len;
-  const int nx = c.nx, ny = c.ny;
-  const long long nc = c.nc;
-  const T *bxa = base + 5 * nc, *bya = bxa + c.nfx, *bza = bya + c.nfy;
+  const PatchGeo &g = c.geo[P];
+  const T *base = (const T *)c.slab + (long long)s * c.slot_stride + g.off;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const long long nc = (long long)nx * ny * nz;
+  const T *bxa = base + 5 * nc, *bya = bxa + (long long)(nx + 1) * ny * nz, *bza = bya + (long long)nx * (ny + 1) * nz;
   const double dV = c.dx * c.dx * c.dx;
+  (void)nz;
   NSum acc[8];
   for (int q = 0; q < 8; q++) acc[q].s = acc[q].c = 0.0;
   double mdiv = 0.0, mb = 0.0;
@@ -384,7 +431,7 @@ int ensure_staging(dsp_ctx *c, size_t bytes) {
 
 template <typename TS>
 int run_xfer(dsp_ctx *c, int first, int count, void *U, void *bx, void *by, void *bz, int dtype, int dir) {
-  const int grid = 1184;
+  const int grid = std::min(count, 4096);
   if (dtype == 0)
     xfer_kernel<TS, double><<<grid, 256, 0, c->stream>>>(c->d, first, count, (double *)U, (double *)bx, (double *)by,
                                                        (double *)bz, dir);
@@ -398,8 +445,9 @@ int run_xfer(dsp_ctx *c, int first, int count, void *U, void *bx, void *by, void
 int transfer(dsp_ctx *c, int first, int count, const void *U, const void *bx, const void *by, const void *bz, int dtype,
              int on_device, int dir) {
   const size_t es = dtype == 0 ? 8 : 4;
-  const size_t nU = (size_t)5 * c->d.nc * count, nX = (size_t)c->d.nfx * count, nY = (size_t)c->d.nfy * count,
-               nZ = (size_t)c->d.nfz * count;
+  const int np1 = c->d.np + 1;
+  auto span = [&](int f) { return (size_t)(c->coff[f * np1 + first + count] - c->coff[f * np1 + first]); };
+  const size_t nU = span(0), nX = span(1), nY = span(2), nZ = span(3);
   void *dU = (void *)U, *dX = (void *)bx, *dY = (void *)by, *dZ = (void *)bz;
   if (!on_device) {
     int rc = ensure_staging(c, es * (nU + nX + nY + nZ));
@@ -430,7 +478,8 @@ int transfer(dsp_ctx *c, int first, int count, const void *U, const void *bx, co
 }
 
 void free_all(dsp_ctx *c) {
-  void *ptrs[] = {c->slab,    c->t_slot,  c->smax_slot, c->dt_last, c->dtR,     c->latest,  c->nb27_d,
+  void *ptrs[] = {c->slab,    c->t_slot,  c->smax_slot, c->dt_last, c->dtR,     c->latest,  c->map_d,
+                  c->work_off_d, c->geo_d, c->coff_d,
                   c->nbl_off_d, c->nbl_d, c->R,       c->ctl,     c->smax_new, c->cnt,    c->sched,
                   c->staging, c->q_patch, c->q_reads, c->p_state, c->tiles_done, c->q_dt, c->q_seq,
                   c->q_free,  c->q_ctl};
@@ -454,28 +503,96 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   if (prm->nguard < 2 || prm->nslices < 3 || prm->precision < 0 || prm->precision > 2 ||
       (prm->time_mode != 0 && prm->time_mode != 1) || !(prm->cfl > 0.0) || !(prm->gamma > 1.0))
     return DSP_ERR_INVALID_ARG;
-  const int nx = patches[0].n[0], ny = patches[0].n[1], nz = patches[0].n[2];
   for (int d = 0; d < 3; d++)
     if (prm->base_cells[d] <= 0 || !(prm->box_len[d] > 0.0)) return DSP_ERR_INVALID_ARG;
   const double dx = prm->box_len[0] / prm->base_cells[0];
   for (int d = 1; d < 3; d++)
     if (std::fabs(prm->box_len[d] / prm->base_cells[d] - dx) > 1e-12 * dx) return DSP_ERR_INVALID_ARG;
-  if (nx <= prm->nguard || ny <= prm->nguard || nz <= prm->nguard) return DSP_ERR_INVALID_ARG;
-  if (prm->base_cells[0] % nx || prm->base_cells[1] % ny || prm->base_cells[2] % nz) return DSP_ERR_INVALID_ARG;
-  const int px = prm->base_cells[0] / nx, py = prm->base_cells[1] / ny, pz = prm->base_cells[2] / nz;
-  if ((long long)px * py * pz != npatch) return DSP_ERR_INVALID_ARG;
-  std::vector<int> grid((size_t)npatch, -1);
+  // Geometry: every patch on level 0, wider than its guard depth, inside the
+  // box; together they must tile the periodic box exactly.  The level map
+  // uses blocks of bsz cells, bsz = gcd of the box, every patch size and
+  // every patch origin per axis.
+  int bsz[3];
+  for (int d = 0; d < 3; d++) bsz[d] = prm->base_cells[d];
+  auto gcd = [](long long a, long long b) {
+    while (b) {
+      const long long t = a % b;
+      a = b;
+      b = t;
+    }
+    return a;
+  };
   for (int i = 0; i < npatch; i++) {
     const dsp_patch_desc &p = patches[i];
     if (p.level != 0) return DSP_ERR_UNSUPPORTED;
-    if (p.n[0] != nx || p.n[1] != ny || p.n[2] != nz) return DSP_ERR_UNSUPPORTED;
-    if (p.lo[0] % nx || p.lo[1] % ny || p.lo[2] % nz) return DSP_ERR_INVALID_ARG;
-    const long long gx = p.lo[0] / nx, gy = p.lo[1] / ny, gz = p.lo[2] / nz;
-    if (gx < 0 || gy < 0 || gz < 0 || gx >= px || gy >= py || gz >= pz) return DSP_ERR_INVALID_ARG;
-    int &slot = grid[(size_t)((gz * py + gy) * px + gx)];
-    if (slot >= 0) return DSP_ERR_INVALID_ARG;
-    slot = i;
+    for (int d = 0; d < 3; d++) {
+      if (p.n[d] <= prm->nguard || p.lo[d] < 0 || p.lo[d] + p.n[d] > prm->base_cells[d]) return DSP_ERR_INVALID_ARG;
+      bsz[d] = (int)gcd(bsz[d], gcd(p.n[d], p.lo[d]));
+    }
   }
+  int mapd[3];
+  for (int d = 0; d < 3; d++) {
+    mapd[d] = prm->base_cells[d] / bsz[d];
+    // the kernels divide level coordinates by bsz through a float product
+    if (prm->base_cells[d] + 8 > (1 << 20) / std::max(bsz[d], 1)) return DSP_ERR_UNSUPPORTED;
+  }
+  const long long nmap = (long long)mapd[0] * mapd[1] * mapd[2];
+  if (nmap > (1ll << 28)) return DSP_ERR_UNSUPPORTED;
+  std::vector<int> map((size_t)nmap, -1);
+  for (int i = 0; i < npatch; i++) {
+    const dsp_patch_desc &p = patches[i];
+    for (long long bz = p.lo[2] / bsz[2]; bz < (p.lo[2] + p.n[2]) / bsz[2]; bz++)
+      for (long long by = p.lo[1] / bsz[1]; by < (p.lo[1] + p.n[1]) / bsz[1]; by++)
+        for (long long bx = p.lo[0] / bsz[0]; bx < (p.lo[0] + p.n[0]) / bsz[0]; bx++) {
+          int &m = map[(size_t)((bz * mapd[1] + by) * mapd[0] + bx)];
+          if (m >= 0) return DSP_ERR_INVALID_ARG;  // overlap
+          m = i;
+        }
+  }
+  for (long long k = 0; k < nmap; k++)
+    if (map[(size_t)k] < 0) return DSP_ERR_INVALID_ARG;  // not a tiling
+  int TX, TY;
+  if (prm->precision == 1) update_tile_f32(&TX, &TY);
+  else update_tile_f64(&TX, &TY);
+  int tz = prm->tile_z;
+  if (tz <= 0)
+    for (int i = 0; i < npatch; i++) tz = std::max(tz, patches[i].n[2]);
+  std::vector<PatchGeo> geo((size_t)npatch);
+  long long off = 0, total_tiles = 0;
+  int tiles0 = -1;
+  bool same_tiles = true;
+  for (int i = 0; i < npatch; i++) {
+    PatchGeo &g = geo[(size_t)i];
+    for (int d = 0; d < 3; d++) {
+      g.n[d] = patches[i].n[d];
+      g.lo[d] = (int)patches[i].lo[d];
+    }
+    g.nt[0] = (g.n[0] + TX - 1) / TX;
+    g.nt[1] = (g.n[1] + TY - 1) / TY;
+    g.nt[2] = (g.n[2] + tz - 1) / tz;
+    g.tiles = g.nt[0] * g.nt[1] * g.nt[2];
+    g.off = off;
+    const long long nc = (long long)g.n[0] * g.n[1] * g.n[2];
+    off += 5 * nc + (long long)(g.n[0] + 1) * g.n[1] * g.n[2] + (long long)g.n[0] * (g.n[1] + 1) * g.n[2] +
+           (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
+    total_tiles += g.tiles;
+    if (tiles0 < 0) tiles0 = g.tiles;
+    if (g.tiles != tiles0) same_tiles = false;
+    // the owner table of every tile must fit the kernel's shared table
+    auto fdiv = [](long long a, long long b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+    for (int kz = 0; kz < g.nt[2]; kz++)
+      for (int ky = 0; ky < g.nt[1]; ky++)
+        for (int kx = 0; kx < g.nt[0]; kx++) {
+          const int x0 = kx * TX, y0 = ky * TY, z0 = kz * tz;
+          const int ext[3] = {std::min(TX, g.n[0] - x0), std::min(TY, g.n[1] - y0), std::min(tz, g.n[2] - z0)};
+          const int org[3] = {x0, y0, z0};
+          long long ne = 1;
+          for (int d = 0; d < 3; d++)
+            ne *= fdiv(g.lo[d] + org[d] + ext[d] + 2, bsz[d]) - fdiv(g.lo[d] + org[d] - 2, bsz[d]) + 1;
+          if (ne > TABMAX) return DSP_ERR_UNSUPPORTED;
+        }
+  }
+  if (prm->dispatcher == 0 && !same_tiles) return DSP_ERR_UNSUPPORTED;  // the ready queue needs equal tile counts
   dsp_ctx *c = new dsp_ctx();
   memset(&c->d, 0, sizeof c->d);
   c->prm = *prm;
@@ -494,47 +611,64 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   c->esize = prm->precision == 1 ? 4 : 8;
   c->poisoned = 0;
   c->nev = 0;
+  c->geo = geo;
   DevCtx &d = c->d;
   d.np = npatch;
   d.ns = prm->nslices;
-  d.nx = nx; d.ny = ny; d.nz = nz;
-  d.nc = (long long)nx * ny * nz;
-  d.nfx = (long long)(nx + 1) * ny * nz;
-  d.nfy = (long long)nx * (ny + 1) * nz;
-  d.nfz = (long long)nx * ny * (nz + 1);
-  d.patch_len = 5 * d.nc + d.nfx + d.nfy + d.nfz;
-  d.slot_stride = d.patch_len * npatch;
+  d.tz = tz;
+  d.uniform_tiles = same_tiles ? tiles0 : 0;
+  d.total_tiles = total_tiles;
+  d.slot_stride = off;
+  for (int k = 0; k < 3; k++) {
+    d.bsz[k] = bsz[k];
+    d.mapd[k] = mapd[k];
+    d.L[k] = prm->base_cells[k];
+    d.binv[k] = 1.0f / (float)bsz[k];
+  }
   d.gamma = prm->gamma;
   d.cfl = prm->cfl;
   d.dx = dx;
   d.dt_max = prm->dt_max;
-  int TX, TY;
-  if (c->precision == 1) update_tile_f32(&TX, &TY);
-  else update_tile_f64(&TX, &TY);
-  d.tx = TX;
-  d.ty = TY;
-  d.tz = prm->tile_z > 0 ? std::min(prm->tile_z, nz) : nz;
-  d.ntx = (nx + TX - 1) / TX;
-  d.nty = (ny + TY - 1) / TY;
-  d.ntz = (nz + d.tz - 1) / d.tz;
-  d.tiles = d.ntx * d.nty * d.ntz;
-  // neighbour tables
-  c->nb27.resize((size_t)npatch * 27);
+  // neighbours: every patch owning a block of the padded box (periodic
+  // images), the patch itself excluded
   c->nbl_off.assign((size_t)npatch + 1, 0);
+  {
+    std::vector<int> seen((size_t)npatch, -1);
+    const int g = prm->nguard;
+    for (int i = 0; i < npatch; i++) {
+      const dsp_patch_desc &p = patches[i];
+      std::vector<int> uniq;
+      long long b0[3], b1[3];
+      for (int k = 0; k < 3; k++) {
+        const long long a = p.lo[k] - g, b = p.lo[k] + p.n[k] + g - 1;
+        b0[k] = a >= 0 ? a / bsz[k] : -((-a + bsz[k] - 1) / bsz[k]);
+        b1[k] = b / bsz[k];
+      }
+      for (long long bz = b0[2]; bz <= b1[2]; bz++)
+        for (long long by = b0[1]; by <= b1[1]; by++)
+          for (long long bx = b0[0]; bx <= b1[0]; bx++) {
+            const long long wx = ((bx % mapd[0]) + mapd[0]) % mapd[0];
+            const long long wy = ((by % mapd[1]) + mapd[1]) % mapd[1];
+            const long long wz = ((bz % mapd[2]) + mapd[2]) % mapd[2];
+            const int q = map[(size_t)((wz * mapd[1] + wy) * mapd[0] + wx)];
+            if (q != i && seen[(size_t)q] != i) {
+              seen[(size_t)q] = i;
+              uniq.push_back(q);
+            }
+          }
+      std::sort(uniq.begin(), uniq.end());
+      c->nbl_off[i + 1] = c->nbl_off[i] + (int)uniq.size();
+      c->nbl.insert(c->nbl.end(), uniq.begin(), uniq.end());
+    }
+  }
+  // offsets of each patch in the caller's four arrays
+  c->coff.assign(4 * ((size_t)npatch + 1), 0);
   for (int i = 0; i < npatch; i++) {
-    const int gx = (int)(patches[i].lo[0] / nx), gy = (int)(patches[i].lo[1] / ny), gz = (int)(patches[i].lo[2] / nz);
-    std::vector<int> uniq;
-    for (int oz = -1; oz <= 1; oz++)
-      for (int oy = -1; oy <= 1; oy++)
-        for (int ox = -1; ox <= 1; ox++) {
-          const int qx = (gx + ox + px) % px, qy = (gy + oy + py) % py, qz = (gz + oz + pz) % pz;
-          const int q = grid[(size_t)((qz * py + qy) * px + qx)];
-          c->nb27[(size_t)i * 27 + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] = q;
-          if (q != i && std::find(uniq.begin(), uniq.end(), q) == uniq.end()) uniq.push_back(q);
-        }
-    std::sort(uniq.begin(), uniq.end());
-    c->nbl_off[i + 1] = c->nbl_off[i] + (int)uniq.size();
-    c->nbl.insert(c->nbl.end(), uniq.begin(), uniq.end());
+    const PatchGeo &gg = geo[(size_t)i];
+    const long long nc = (long long)gg.n[0] * gg.n[1] * gg.n[2];
+    const long long per[4] = {5 * nc, (long long)(gg.n[0] + 1) * gg.n[1] * gg.n[2],
+                              (long long)gg.n[0] * (gg.n[1] + 1) * gg.n[2], (long long)gg.n[0] * gg.n[1] * (gg.n[2] + 1)};
+    for (int f = 0; f < 4; f++) c->coff[(size_t)f * (npatch + 1) + i + 1] = c->coff[(size_t)f * (npatch + 1) + i] + per[f];
   }
   auto alloc = [&](void **p, size_t bytes) {
     if (cudaMalloc(p, bytes ? bytes : 1) != cudaSuccess) return false;
@@ -545,7 +679,10 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   bool ok = alloc(&c->slab, slab_bytes) && alloc((void **)&c->t_slot, sizeof(double) * npatch * d.ns) &&
             alloc((void **)&c->smax_slot, sizeof(double) * npatch * d.ns) &&
             alloc((void **)&c->dt_last, sizeof(double) * npatch) && alloc((void **)&c->dtR, sizeof(double) * npatch) &&
-            alloc((void **)&c->latest, sizeof(int) * npatch) && alloc((void **)&c->nb27_d, sizeof(int) * npatch * 27) &&
+            alloc((void **)&c->latest, sizeof(int) * npatch) && alloc((void **)&c->map_d, sizeof(int) * nmap) &&
+            alloc((void **)&c->geo_d, sizeof(PatchGeo) * npatch) &&
+            alloc((void **)&c->coff_d, sizeof(long long) * c->coff.size()) &&
+            alloc((void **)&c->work_off_d, sizeof(int) * (npatch + 1)) &&
             alloc((void **)&c->nbl_off_d, sizeof(int) * (npatch + 1)) &&
             alloc((void **)&c->nbl_d, sizeof(int) * std::max<size_t>(1, c->nbl.size())) &&
             alloc((void **)&c->R, sizeof(int) * npatch) && alloc((void **)&c->ctl, sizeof(int) * CTL_COUNT) &&
@@ -573,7 +710,10 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.smax_slot = c->smax_slot;
   d.latest = c->latest;
   d.dt_last = c->dt_last;
-  d.nb27 = c->nb27_d;
+  d.geo = c->geo_d;
+  d.map = c->map_d;
+  d.coff = c->coff_d;
+  d.work_off = c->work_off_d;
   d.nbl_off = c->nbl_off_d;
   d.nbl = c->nbl_d;
   d.R = c->R;
@@ -592,11 +732,16 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.p_state = c->p_state;
   d.tiles_done = c->tiles_done;
   d.wait_budget = prm->wait_budget > 0 ? prm->wait_budget : 4000000000ll;  // ~2 s of SM clock
-  cudaError_t e = cudaMemcpyAsync(c->nb27_d, c->nb27.data(), sizeof(int) * c->nb27.size(), cudaMemcpyHostToDevice, c->stream);
+  cudaError_t e = cudaMemcpyAsync(c->map_d, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->geo_d, geo.data(), sizeof(PatchGeo) * geo.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->coff_d, c->coff.data(), sizeof(long long) * c->coff.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->nbl_off_d, c->nbl_off.data(), sizeof(int) * c->nbl_off.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess && !c->nbl.empty())
     e = cudaMemcpyAsync(c->nbl_d, c->nbl.data(), sizeof(int) * c->nbl.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->work_off_d, 0, sizeof(int) * (npatch + 1), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl, 0, sizeof(int) * CTL_COUNT, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_COUNT, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->slab, 0, slab_bytes, c->stream);
@@ -908,7 +1053,7 @@ extern "C" int dsp_save(dsp_ctx *c, void *buf, size_t cap, size_t *used) {
   h.np = np;
   h.ns = ns;
   h.precision = c->precision;
-  h.patch_len = c->d.patch_len;
+  h.patch_len = 0;
   h.slot_stride = c->d.slot_stride;
   memcpy(p, &h, sizeof h);
   p += sizeof h;
@@ -934,7 +1079,7 @@ extern "C" int dsp_load(dsp_ctx *c, const void *buf, size_t size) {
   SaveHeader h;
   memcpy(&h, buf, sizeof h);
   if (memcmp(h.magic, "DSPSAVE", 8) || h.version != 1 || h.np != np || h.ns != ns || h.precision != c->precision ||
-      h.patch_len != c->d.patch_len)
+      h.slot_stride != c->d.slot_stride)
     return fail(c, DSP_ERR_INVALID_ARG, "saved state does not match this context");
   const char *p = (const char *)buf + sizeof h;
   CK(cudaMemcpyAsync(c->t_slot, p, sizeof(double) * np * ns, cudaMemcpyHostToDevice, c->stream));

@@ -26,24 +26,41 @@ enum Cnt : int {
   CNT_COUNT = 8
 };
 
-// Everything a kernel needs, passed by value.  Slices are stored slice-major:
-// slice s of patch P starts at slab + s * slot_stride + P * patch_len
-// (elements of the context's precision), and holds U[5][nz][ny][nx],
-// bx[nz][ny][nx+1], by[nz][ny+1][nx], bz[nz+1][ny][nx].
+// Per-patch geometry (device memory).  Slice s of patch P starts at
+// slab + s * slot_stride + off, and holds U[5][nz][ny][nx],
+// bx[nz][ny][nx+1], by[nz][ny+1][nx], bz[nz+1][ny][nx] (elements of the
+// context's precision).
+struct PatchGeo {
+  int n[3];       // interior cells per axis
+  int nt[3];      // update tiles per axis
+  int tiles;      // nt[0] * nt[1] * nt[2]
+  int lo[3];      // first interior cell in the level's index space
+  long long off;  // offset of the patch inside a slice
+};
+
+// Largest number of map blocks one work item's padded tile may touch.
+constexpr int TABMAX = 128;
+
+// Everything a kernel needs, passed by value.
 struct DevCtx {
   int np, ns;
-  int nx, ny, nz;
-  int tx, ty, tz;          // tile extents in cells
-  int ntx, nty, ntz;       // tiles per axis
-  int tiles;               // tiles per patch
-  long long nc, nfx, nfy, nfz, patch_len, slot_stride;
+  int tz;                  // z run of a work item (cells)
+  int uniform_tiles;       // tiles per patch when all patches have the same size, else 0
+  long long total_tiles;   // tiles of all patches
+  long long slot_stride;   // elements of one slice of all patches
+  const PatchGeo *geo;     // [np]
+  // level map: blocks of bsz cells tiling the periodic box; map[] = patch
+  const int *map;
+  int bsz[3], mapd[3], L[3];
+  float binv[3];
+  const long long *coff;   // [4][np+1] offsets of each patch in the caller's U, bx, by, bz arrays
+  int *work_off;           // [np+1] first work item of each ready patch (prefix of tiles)
   double gamma, cfl, dx, dt_max;
   void *slab;
   double *t_slot;          // [np][ns]
   double *smax_slot;       // [np][ns]
   int *latest;             // [np]
   double *dt_last;         // [np]
-  const int *nb27;         // [np][27] patch at offset (ox,oy,oz) in {-1,0,1}^3, index (oz+1)*9+(oy+1)*3+(ox+1)
   const int *nbl_off;      // [np+1] CSR of distinct neighbours (self excluded)
   const int *nbl;
   int *R;                  // [np] ready list of the current sweep
@@ -53,12 +70,12 @@ struct DevCtx {
   long long *cnt;          // [CNT_COUNT]
   dsp_sched_entry *sched;  // [sched_cap]
   long long sched_cap;
-  // persistent ready queue (dispatcher 0): a ring of np entries
-  int *q_patch;                    // [np] patch of each ring slot
-  double *q_dt;                    // [np] its step
-  unsigned long long *q_seq;       // [np] sequence number published in the slot
-  unsigned long long *q_free;      // [np] sequence number the slot may take next
-  int *q_reads;                    // [np] tiles of the slot's entry claimed so far
+  // persistent ready queue (dispatcher 0): a ring of 2*np entries
+  int *q_patch;                    // [2np] patch of each ring slot
+  double *q_dt;                    // [2np] its step
+  unsigned long long *q_seq;       // [2np] sequence number published in the slot
+  unsigned long long *q_free;      // [2np] sequence number the slot may take next
+  int *q_reads;                    // [2np] tiles of the slot's entry claimed so far
   unsigned long long *q_ctl;       // [4]: 0 next work item, 1 next entry, 2 patches done
   int *p_state;                    // [np] 0 idle, 1 queued or being updated
   int *tiles_done;                 // [np]

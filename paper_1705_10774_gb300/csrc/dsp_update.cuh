@@ -60,7 +60,6 @@ struct Lay {
   static constexpr int total = oNBZ + 2 * H1N;
 };
 
-__device__ __forceinline__ int off1(int x, int n) { return x < 0 ? 0 : (x >= n ? 2 : 1); }
 
 __device__ __forceinline__ void set_error(const DevCtx &c, int code, int P, long long cell) {
   if (atomicCAS(&c.ctl[CTL_STATUS], 0, code) == 0) {
@@ -69,15 +68,23 @@ __device__ __forceinline__ void set_error(const DevCtx &c, int code, int P, long
   }
 }
 
-// Small per-block scratch shared by all tiles a block processes.
+// Small per-block scratch shared by all tiles a block processes: the owner
+// table of the work item's padded tile (one entry per map block it touches:
+// the owning patch's slice(s) at the tile's time, interpolation weight, the
+// periodic image of its first cell, its size), and reduction space.
 template <typename T, int NT>
 struct TileShared {
-  const T *srcA[27];
-  const T *srcB[27];
-  T wgt[27];
+  const T *srcA[TABMAX];
+  const T *srcB[TABMAX];
+  T wgt[TABMAX];
+  int lo[3][TABMAX];
+  int n[3][TABMAX];
   double red[NT / 32];
   int fallback;
 };
+
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__device__ __forceinline__ int posmod(int a, int b) { const int r = a % b; return r < 0 ? r + b : r; }
 
 // Advance one tile of patch P by dt (all threads of the block take part).
 // On return the tile's new cells, faces and signal speed are written.  CONC:
@@ -118,8 +125,11 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
   int &s_fallback = S.fallback;
 
   const int tid = threadIdx.x;
-  const int nx = c.nx, ny = c.ny, nz = c.nz;
-  const long long nc = c.nc, ofy = 5 * c.nc + c.nfx, ofz = 5 * c.nc + c.nfx + c.nfy, ofx = 5 * c.nc;
+  const PatchGeo &gp = c.geo[P];
+  const int nx = gp.n[0], ny = gp.n[1], nz = gp.n[2];
+  const int lox = gp.lo[0], loy = gp.lo[1], loz = gp.lo[2];
+  const long long nc = (long long)nx * ny * nz;
+  const long long ofx = 5 * nc, ofy = ofx + (long long)(nx + 1) * ny * nz, ofz = ofy + (long long)nx * (ny + 1) * nz;
   const T gamma = (T)c.gamma;
   const T igm1 = (T)(1.0 / (c.gamma - 1.0));
   const T half = T(0.5);
@@ -130,20 +140,37 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
 
   const T hdt = (T)(0.5 * dt / c.dx);
   const T dtdx = (T)(dt / c.dx);
-  const int tix = tile % c.ntx, tiy = (tile / c.ntx) % c.nty, tiz = tile / (c.ntx * c.nty);
+  const int tix = tile % gp.nt[0], tiy = (tile / gp.nt[0]) % gp.nt[1], tiz = tile / (gp.nt[0] * gp.nt[1]);
   const int x0 = tix * TX, y0 = tiy * TY, z0 = tiz * c.tz;
   const int tx = min(TX, nx - x0), ty = min(TY, ny - y0), tz = min(c.tz, nz - z0);
   const int Lp = newest<CONC>(c, P);
   const double tP = slot_time<CONC>(c, (long long)P * c.ns + Lp);
-  T *const dst = (T *)c.slab + (long long)((Lp + 1) % c.ns) * c.slot_stride + (long long)P * c.patch_len;
+  const T *const own = (const T *)c.slab + (long long)Lp * c.slot_stride + gp.off;
+  T *const dst = (T *)c.slab + (long long)((Lp + 1) % c.ns) * c.slot_stride + gp.off;
 
-  // Which slices of each of the 27 neighbours (self at 13) supply time tP:
-  // an exact-time slice is copied, else the two newest are interpolated.
-  if (tid < 27) {
-    const int Q = c.nb27[(long long)P * 27 + tid];
+  // Owner table of the padded tile: every map block that cells in
+  // [x0-2, x0+tx+2] x [y0-2, y0+ty+2] x [z0-2, z0+tz+2] fall in, with the
+  // slices of its owning patch that supply time tP (a slice at exactly tP is
+  // copied, else the newest two are interpolated).
+  const int bx0 = floordiv(lox + x0 - 2, c.bsz[0]), by0 = floordiv(loy + y0 - 2, c.bsz[1]),
+            bz0 = floordiv(loz + z0 - 2, c.bsz[2]);
+  const int nbx = floordiv(lox + x0 + tx + 2, c.bsz[0]) - bx0 + 1;
+  const int nby = floordiv(loy + y0 + ty + 2, c.bsz[1]) - by0 + 1;
+  const int nbz = floordiv(loz + z0 + tz + 2, c.bsz[2]) - bz0 + 1;
+  for (int e = tid; e < nbx * nby * nbz; e += NT) {
+    const int bx = bx0 + e % nbx, by = by0 + (e / nbx) % nby, bz = bz0 + e / (nbx * nby);
+    const int wx = posmod(bx, c.mapd[0]), wy = posmod(by, c.mapd[1]), wz = posmod(bz, c.mapd[2]);
+    const int Q = c.map[((long long)wz * c.mapd[1] + wy) * c.mapd[0] + wx];
+    const PatchGeo &gq = c.geo[Q];
+    S.lo[0][e] = gq.lo[0] + (bx - wx) * c.bsz[0];
+    S.lo[1][e] = gq.lo[1] + (by - wy) * c.bsz[1];
+    S.lo[2][e] = gq.lo[2] + (bz - wz) * c.bsz[2];
+    S.n[0][e] = gq.n[0];
+    S.n[1][e] = gq.n[1];
+    S.n[2][e] = gq.n[2];
     const int Lq = newest<CONC>(c, Q);
     const double tq = slot_time<CONC>(c, (long long)Q * c.ns + Lq);
-    const T *base = (const T *)c.slab + (long long)Q * c.patch_len;
+    const T *base = (const T *)c.slab + gq.off;
     const T *A;
     const T *B = nullptr;
     T wv = T(0);
@@ -163,13 +190,12 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         set_error(c, DSP_ERR_BRACKET, P, -1);
       }
     }
-    srcA[tid] = A;
-    srcB[tid] = B;
-    wgt[tid] = wv;
+    srcA[e] = A;
+    srcB[e] = B;
+    wgt[e] = wv;
   }
   if (tid == 0) s_fallback = 0;
   __syncthreads();
-  const T *const own = srcA[13];
 
   auto val = [&](int o, long long idx) -> T {
     T a = srcA[o][idx];
@@ -180,11 +206,25 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     }
     return a;
   };
-  // Cell-centred component q of patch-local cell (x,y,z), |offset| <= 2.
+  // Table entry of the level cell (gx, gy, gz) of the padded tile (floor of
+  // a small integer quotient through a rounded-up float product: exact for
+  // level extents far below 2^20 cells).
+  auto entry = [&](int gx, int gy, int gz) -> int {
+    const int ex = __float2int_rd(((float)gx + 0.5f) * c.binv[0]) - bx0;
+    const int ey = __float2int_rd(((float)gy + 0.5f) * c.binv[1]) - by0;
+    const int ez = __float2int_rd(((float)gz + 0.5f) * c.binv[2]) - bz0;
+    return (ez * nby + ey) * nbx + ex;
+  };
+  // Cell-centred component q of patch-local cell (x,y,z) (radius <= 2
+  // outside the patch).
   auto cellv = [&](int x, int y, int z, long long q) -> T {
-    const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
-    const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
-    return val((oz * 3 + oy) * 3 + ox, q * nc + ((long long)lz * ny + ly) * nx + lx);
+    if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz)
+      return own[q * nc + ((long long)z * ny + y) * nx + x];
+    const int gx = lox + x, gy = loy + y, gz = loz + z;
+    const int e = entry(gx, gy, gz);
+    const int mx = S.n[0][e], my = S.n[1][e], mz = S.n[2][e];
+    const int lx = gx - S.lo[0][e], ly = gy - S.lo[1][e], lz = gz - S.lo[2][e];
+    return val(e, q * ((long long)mx * my * mz) + ((long long)lz * my + ly) * mx + lx);
   };
   // Face below cell (x,y,z) along each axis: the patch's own face when it
   // lies on one of its interior cells, else the face of the patch that owns
@@ -192,23 +232,32 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
   auto facex = [&](int x, int y, int z) -> T {
     if (x >= 0 && x <= nx && y >= 0 && y < ny && z >= 0 && z < nz)
       return own[ofx + ((long long)z * ny + y) * (nx + 1) + x];
-    const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
-    const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
-    return val((oz * 3 + oy) * 3 + ox, ofx + ((long long)lz * ny + ly) * (nx + 1) + lx);
+    const int gx = lox + x, gy = loy + y, gz = loz + z;
+    const int e = entry(gx, gy, gz);
+    const int mx = S.n[0][e], my = S.n[1][e], mz = S.n[2][e];
+    const int lx = gx - S.lo[0][e], ly = gy - S.lo[1][e], lz = gz - S.lo[2][e];
+    return val(e, 5 * ((long long)mx * my * mz) + ((long long)lz * my + ly) * (mx + 1) + lx);
   };
   auto facey = [&](int x, int y, int z) -> T {
     if (x >= 0 && x < nx && y >= 0 && y <= ny && z >= 0 && z < nz)
       return own[ofy + ((long long)z * (ny + 1) + y) * nx + x];
-    const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
-    const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
-    return val((oz * 3 + oy) * 3 + ox, ofy + ((long long)lz * (ny + 1) + ly) * nx + lx);
+    const int gx = lox + x, gy = loy + y, gz = loz + z;
+    const int e = entry(gx, gy, gz);
+    const int mx = S.n[0][e], my = S.n[1][e], mz = S.n[2][e];
+    const int lx = gx - S.lo[0][e], ly = gy - S.lo[1][e], lz = gz - S.lo[2][e];
+    const long long m = (long long)mx * my * mz;
+    return val(e, 5 * m + (long long)(mx + 1) * my * mz + ((long long)lz * (my + 1) + ly) * mx + lx);
   };
   auto facez = [&](int x, int y, int z) -> T {
     if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z <= nz)
       return own[ofz + ((long long)z * ny + y) * nx + x];
-    const int ox = off1(x, nx), oy = off1(y, ny), oz = off1(z, nz);
-    const int lx = x - (ox - 1) * nx, ly = y - (oy - 1) * ny, lz = z - (oz - 1) * nz;
-    return val((oz * 3 + oy) * 3 + ox, ofz + ((long long)lz * ny + ly) * nx + lx);
+    const int gx = lox + x, gy = loy + y, gz = loz + z;
+    const int e = entry(gx, gy, gz);
+    const int mx = S.n[0][e], my = S.n[1][e], mz = S.n[2][e];
+    const int lx = gx - S.lo[0][e], ly = gy - S.lo[1][e], lz = gz - S.lo[2][e];
+    const long long m = (long long)mx * my * mz;
+    return val(e, 5 * m + (long long)(mx + 1) * my * mz + (long long)mx * (my + 1) * mz +
+                      ((long long)lz * my + ly) * mx + lx);
   };
 
   // ---- A: gather plane q of the radius-2 padded tile: the raw conserved
@@ -218,7 +267,6 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     const int rs = (q - z0 + 3) % 3, fs = (q - z0 + 2) & 1;
     T *Wq = Wr + rs * 8 * H2N;
     T *Fq = FB + fs * 4 * FPN;
-    const int oz = off1(q, nz), lz = q - (oz - 1) * nz;
     for (int ci = tid; ci < (TX + 5) * (TY + 5); ci += NT) {
       const int i = ci % (TX + 5) - 2, j = ci / (TX + 5) - 2;
       if (i > tx + 2 || j > ty + 2) continue;
@@ -229,16 +277,14 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
       if (i <= tx + 1 && j <= ty + 1) {
         Fq[2 * FPN + f] = facez(x, y, q);
         Fq[3 * FPN + f] = facez(x, y, q + 1);
-        const int ox = off1(x, nx), oy = off1(y, ny);
-        const int o = (oz * 3 + oy) * 3 + ox;
-        const long long cid = ((long long)lz * ny + (y - (oy - 1) * ny)) * nx + (x - (ox - 1) * nx);
         const int h = H2(i, j);
-        if (o == 13) {
+        if (x >= 0 && x < nx && y >= 0 && y < ny && q >= 0 && q < nz) {
+          const long long cid = ((long long)q * ny + y) * nx + x;
 #pragma unroll
           for (int k = 0; k < 5; k++) Wq[k * H2N + h] = own[k * nc + cid];
         } else {
 #pragma unroll
-          for (int k = 0; k < 5; k++) Wq[k * H2N + h] = val(o, k * nc + cid);
+          for (int k = 0; k < 5; k++) Wq[k * H2N + h] = cellv(x, y, q, k);
         }
       }
     }
@@ -667,10 +713,17 @@ template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
 __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ TileShared<T, NT> S;
-  const long long nwork = (long long)c.ctl[CTL_NREADY] * c.tiles;
-  for (long long w = blockIdx.x; w < nwork; w += gridDim.x) {
-    const int r = (int)(w / c.tiles), tile = (int)(w % c.tiles);
-    process_tile<T, TX, TY, NT, false>(c, c.R[r], c.dtR[r], tile, reinterpret_cast<T *>(smraw), S);
+  const int nr = c.ctl[CTL_NREADY];
+  const int nwork = c.work_off[nr];
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    // ready patch r owns work items [work_off[r], work_off[r+1])
+    int lo = 0, hi = nr - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (c.work_off[mid] <= w) lo = mid;
+      else hi = mid - 1;
+    }
+    process_tile<T, TX, TY, NT, false>(c, c.R[lo], c.dtR[lo], w - c.work_off[lo], reinterpret_cast<T *>(smraw), S);
   }
 }
 
@@ -742,7 +795,8 @@ static __device__ void publish_and_queue(const DevCtx &c, int P, double dt, doub
     c.sched[e].dt = dt;
   }
   atomicAdd((unsigned long long *)&c.cnt[CNT_PATCH_UPDATES], 1ull);
-  atomicAdd((unsigned long long *)&c.cnt[CNT_CELL_UPDATES], (unsigned long long)c.nc);
+  atomicAdd((unsigned long long *)&c.cnt[CNT_CELL_UPDATES],
+            (unsigned long long)c.geo[P].n[0] * c.geo[P].n[1] * c.geo[P].n[2]);
   __threadfence();
   st_release(c.latest + P, Ln);
   __threadfence();
@@ -768,7 +822,7 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
     if (tid == 0) {
       s_exit = 0;
       const unsigned long long w = atomicAdd(&c.q_ctl[0], 1ull);
-      const unsigned long long e = w / (unsigned long long)c.tiles;
+      const unsigned long long e = w / (unsigned long long)c.uniform_tiles;
       const int slot = (int)(e % C);
       const long long t0 = clock64();
       while (ld_acquire(&c.q_seq[slot]) != e) {
@@ -786,9 +840,9 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
       if (!s_exit) {
         s_P = __ldcg(c.q_patch + slot);
         s_dt = __ldcg(c.q_dt + slot);
-        s_tile = (int)(w % (unsigned long long)c.tiles);
+        s_tile = (int)(w % (unsigned long long)c.uniform_tiles);
         const int r = atomicAdd(&c.q_reads[slot], 1);
-        if (r == c.tiles - 1) {
+        if (r == c.uniform_tiles - 1) {
           c.q_reads[slot] = 0;
           st_release(&c.q_free[slot], e + C);
         }
@@ -802,7 +856,7 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
     if (tid == 0) {
       __threadfence();
       const int k = atomicAdd(&c.tiles_done[P], 1);
-      if (k == c.tiles - 1) {
+      if (k == c.uniform_tiles - 1) {
         __threadfence();
         c.tiles_done[P] = 0;
         publish_and_queue(c, P, dt, t_end);
@@ -851,7 +905,7 @@ int update_grid(const DevCtx &c) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, update_kernel<T, TX, TY, NT, MINB, VARIANT>, NT, smem);
   if (per < 1) per = 1;
-  long long maxwork = (long long)c.np * c.tiles;
+  const long long maxwork = c.total_tiles;  // every patch ready
   long long g = (long long)nsm * per;
   return (int)(g < maxwork ? g : maxwork);
 }

@@ -165,9 +165,10 @@ class Dispatch:
         self._h = h
         self.n = n
         self.precision = precision
-        nc = int(n[0, 0] * n[0, 1] * n[0, 2])
-        self.sizes = (5 * nc * self.np, int((n[0, 0] + 1) * n[0, 1] * n[0, 2]) * self.np,
-                      int(n[0, 0] * (n[0, 1] + 1) * n[0, 2]) * self.np, int(n[0, 0] * n[0, 1] * (n[0, 2] + 1)) * self.np)
+        nx, ny, nz = n[:, 0], n[:, 1], n[:, 2]
+        per = np.stack([5 * nx * ny * nz, (nx + 1) * ny * nz, nx * (ny + 1) * nz, nx * ny * (nz + 1)], axis=1)
+        self.per_patch = per                      # (np, 4) values of U, bx, by, bz per patch
+        self.sizes = tuple(int(x) for x in per.sum(axis=0))
 
     def _check(self, rc):
         if rc != 0 and rc != DSP_ERR_SCHEDULE_OVERFLOW:
@@ -195,8 +196,8 @@ class Dispatch:
     def get_state(self, out=None, dtype=np.float64, first=0, count=None):
         count = self.np - first if count is None else count
         if out is None:
-            f = count / self.np
-            out = [np.empty(int(s * f), dtype=dtype) for s in self.sizes]
+            sz = self.per_patch[first:first + count].sum(axis=0)
+            out = [np.empty(int(s), dtype=dtype) for s in sz]
         ptrs = [_addr(a) for a in out]
         self._check(load().dsp_get_state(self._h, first, count, *[p[0] for p in ptrs], ptrs[0][2], int(ptrs[0][1])))
         return out

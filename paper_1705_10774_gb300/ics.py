@@ -57,6 +57,41 @@ def cartesian(patches_per_axis, cells_per_patch, dx=None):
     return Layout(n=n, lo=lo, base_cells=base, box_len=box)
 
 
+def mixed_blocks(n_blocks, block=96, sizes=(16, 24, 32), probs=(0.105, 0.266, 0.629), remainder=0,
+                 rem_size=32, seed=1, dx=None):
+    """Mixed patch sizes on one level: the box is cut into super-blocks of
+    `block` cells per axis, each tiled by cubes of one seeded size (volume
+    probabilities `probs`; with 16/24/32 and the default probabilities that is
+    about 40/30/30 % by patch count); an optional remainder slab of
+    `remainder` cells on the high side of every axis is tiled by rem_size
+    cubes.  Patches are ordered by super-block, then x fastest inside it."""
+    rng = np.random.default_rng(seed)
+    L = n_blocks * block + remainder
+    if dx is None:
+        dx = 1.0 / L
+    # the axis segments: super-blocks then the remainder slab
+    segs = [(b * block, block) for b in range(n_blocks)]
+    if remainder:
+        segs.append((n_blocks * block, remainder))
+    los, ns = [], []
+    for sz_, (z0, zl) in enumerate(segs):
+        for (y0, yl) in segs:
+            for (x0, xl) in segs:
+                if xl == block and yl == block and zl == block:
+                    s_ = int(rng.choice(sizes, p=np.asarray(probs) / np.sum(probs)))
+                else:
+                    s_ = rem_size
+                s3 = [s_ if l == block else rem_size for l in (xl, yl, zl)]
+                for kz in range(zl // s3[2]):
+                    for ky in range(yl // s3[1]):
+                        for kx in range(xl // s3[0]):
+                            los.append((x0 + kx * s3[0], y0 + ky * s3[1], z0 + kz * s3[2]))
+                            ns.append(s3)
+    lo = np.array(los, dtype=np.int64)
+    n = np.array(ns, dtype=np.int32)
+    return Layout(n=n, lo=lo, base_cells=(L, L, L), box_len=(L * dx,) * 3)
+
+
 @dataclass
 class Fields:
     """A global periodic state on the level grid (index order z, y, x)."""
