@@ -196,6 +196,12 @@ DSP_API int dsp_diagnostics_noalloc(const void *U, const void *bx, const void *b
 
 /* Save the whole dispatcher state (every slice, its time and signal speed,
  * the newest-slice index and last step of every patch) into host memory.
+ * Layout: a 40-byte header (char magic[8] = "DSPSAVE", int32 version = 1,
+ * npatch, nslices, precision, int64 reserved, int64 slot_stride), then
+ * double t[npatch][nslices], double smax[npatch][nslices], int32
+ * newest[npatch], double dt_last[npatch], and the slices: nslices blocks of
+ * slot_stride values (float64, or float32 for precision 1), each the
+ * concatenation over patches of U, bx, by, bz in the dsp_set_state layout.
  * With buf == NULL only *used (the required size) is written.  dsp_load
  * restores a state saved from a context with the same layout and parameters;
  * a run resumed from it is bit-identical to the uninterrupted run. */

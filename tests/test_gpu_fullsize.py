@@ -60,13 +60,14 @@ def parse_save(blob, lay, nslot):
     magic = blob[:8]
     assert magic.startswith(b"DSPSAVE")
     version, npch, ns, prec = struct.unpack_from("<4i", blob, 8)
-    patch_len, slot_stride = struct.unpack_from("<2q", blob, 24)
+    _, slot_stride = struct.unpack_from("<2q", blob, 24)
     off = 40
     ts = np.frombuffer(blob, np.float64, npch * ns, off).reshape(npch, ns); off += 8 * npch * ns
     sm = np.frombuffer(blob, np.float64, npch * ns, off).reshape(npch, ns); off += 8 * npch * ns
     latest = np.frombuffer(blob, np.int32, npch, off); off += 4 * npch
     dtl = np.frombuffer(blob, np.float64, npch, off); off += 8 * npch
-    slab = np.frombuffer(blob, np.float64, ns * slot_stride, off).reshape(ns, npch, patch_len)
+    # slices are stored slice-major; these patches all have the same size
+    slab = np.frombuffer(blob, np.float64, ns * slot_stride, off).reshape(ns, npch, slot_stride // npch)
     return ts, sm, latest, dtl, slab
 
 
