@@ -93,6 +93,8 @@ typedef struct {
  *   wait_budget  ready-queue dispatcher only: SM clock cycles a device wait
  *                may spin without progress before the run stops with
  *                DSP_ERR_TIMEOUT (0 = default, about two seconds)
+ *   variant      id of a compiled update-kernel variant of this precision to
+ *                use (-1 = the default; see dsp_autotune)
  *   graph        sweep dispatcher only: 1 = capture batches of 32 sweeps
  *                (plan + update kernels) in a CUDA graph and replay it; with
  *                a NULL stream the context then creates its own blocking
@@ -107,6 +109,7 @@ typedef struct {
   int32_t timing;
   int64_t wait_budget;
   int32_t graph;
+  int32_t variant;
 } dsp_params;
 
 /* Counters of one dsp_advance call.  kernel_ms and kernel_launches are the
@@ -169,6 +172,17 @@ DSP_API int dsp_get_times(dsp_ctx *ctx, double *t, double *dt_last);
 DSP_API int dsp_get_schedule(dsp_ctx *ctx, dsp_sched_entry *buf, int64_t cap, int64_t *n);
 
 DSP_API int dsp_diagnostics(dsp_ctx *ctx, dsp_diag *out);
+
+/* Autotuner: time every compiled variant of the update kernel that fits this
+ * context (tile shape, threads per block, blocks per SM) on the next sweep's
+ * real ready list, `reps` launches each, and keep the fastest.  Nothing is
+ * published and the state is unchanged (the update writes only the patches'
+ * next slot); all variants compute bit-identical results.  Call after
+ * dsp_set_state, before dsp_advance.  Writes the chosen variant id, and for
+ * up to cap candidates their ids and average milliseconds per launch; *n
+ * receives the number of candidates timed.  Any output pointer may be NULL. */
+DSP_API int dsp_autotune(dsp_ctx *ctx, int32_t reps, int32_t *chosen, double *ms, int32_t *ids, int32_t cap,
+                         int32_t *n);
 
 /* Maximum number of patches dsp_diagnostics_noalloc accepts. */
 #define DSP_NOALLOC_MAX_PATCHES 16384

@@ -7,6 +7,7 @@ fused multiply-adds.
 from __future__ import annotations
 
 import os
+import re
 import subprocess
 import sys
 
@@ -20,11 +21,28 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 SOURCES = [
     ("dsp_host.cu", ["-fmad=false"]),
-    ("dsp_update_f64.cu", ["-fmad=false"]),
-    ("dsp_update_f64f.cu", []),
-    ("dsp_update_f32.cu", ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]),
     ("dsp_noalloc.cu", ["-fmad=false"]),
 ]
+# floating-point flags of each precision code: FP64 without contraction
+# (parity with the oracle), FP32 with fast division and square root, FP64
+# with fused multiply-adds
+PREC_FLAGS = {0: ["-fmad=false"], 1: ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"], 2: []}
+
+
+def variants():
+    """Rows of csrc/dsp_variants.h: (id, type, tx, ty, nt, mb, precision)."""
+    txt = open(os.path.join(CSRC, "dsp_variants.h")).read()
+    rows = re.findall(r"X\((\d+),\s*(\w+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", txt)
+    return [(int(a), b, int(c), int(d), int(e), int(f), int(g)) for a, b, c, d, e, f, g in rows]
+
+
+def units():
+    out = [(src, src.replace(".cu", ".o"), flags) for src, flags in SOURCES]
+    for vid, t, tx, ty, nt, mb, prec in variants():
+        defs = ["-DV_ID=%d" % vid, "-DV_T=%s" % t, "-DV_TX=%d" % tx, "-DV_TY=%d" % ty, "-DV_NT=%d" % nt,
+                "-DV_MB=%d" % mb, "-DV_PREC=%d" % prec]
+        out.append(("dsp_variant.cu", "dsp_variant_%d.o" % vid, defs + PREC_FLAGS[prec]))
+    return out
 
 
 def _nvcc():
@@ -55,8 +73,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     nvcc = _nvcc()
     procs = []
     objs = []
-    for src, flags in SOURCES:
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+    for src, oname, flags in units():
+        obj = os.path.join(OUT_DIR, oname)
         objs.append(obj)
         cmd = [nvcc, *COMMON, *ARCH, *flags, *extra, "-I", os.path.join(ROOT, "include"), "-c",
                os.path.join(CSRC, src), "-o", obj]

@@ -63,6 +63,8 @@ struct dsp_ctx {
   double graph_t_end;
   int graph_timing;
   int own_stream;  // the context created its stream (graph capture needs one)
+  const KernelVariant *var;  // the update-kernel variant in use
+  std::vector<dsp_patch_desc> patches;
 };
 
 namespace {
@@ -401,16 +403,56 @@ __global__ void diag_kernel(DevCtx c, double *out) {
   }
 }
 
-int launch_queue(dsp_ctx *c, double t_end) {
-  if (c->precision == 0) return launch_queue_f64(c->d, c->grid_update, t_end, c->stream);
-  if (c->precision == 2) return launch_queue_f64f(c->d, c->grid_update, t_end, c->stream);
-  return launch_queue_f32(c->d, c->grid_update, t_end, c->stream);
-}
+int launch_queue(dsp_ctx *c, double t_end) { return c->var->launch_queue(c->d, c->grid_update, t_end, c->stream); }
 
-int launch_update(dsp_ctx *c) {
-  if (c->precision == 0) return launch_update_f64(c->d, c->grid_update, c->stream);
-  if (c->precision == 2) return launch_update_f64f(c->d, c->grid_update, c->stream);
-  return launch_update_f32(c->d, c->grid_update, c->stream);
+int launch_update(dsp_ctx *c) { return c->var->launch_update(c->d, c->grid_update, c->stream); }
+
+#define DSP_VARIANT_ENTRY(id, T, TX, TY, NT, MB, PREC) variant_##id,
+const KernelVariant *(*const kVariants[])() = {DSP_VARIANT_LIST(DSP_VARIANT_ENTRY)};
+#undef DSP_VARIANT_ENTRY
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+// Per-patch tiles and offsets for the variant's tile shape; false if some
+// tile's owner table would not fit the kernel's table.
+bool make_geometry(const std::vector<dsp_patch_desc> &patches, int TX, int TY, int tz, const int bsz[3],
+                   std::vector<PatchGeo> &geo, long long &off, long long &total_tiles, int &uniform_tiles) {
+  const int npatch = (int)patches.size();
+  geo.assign((size_t)npatch, PatchGeo());
+  off = 0;
+  total_tiles = 0;
+  int tiles0 = -1;
+  bool same_tiles = true;
+  auto fdiv = [](long long a, long long b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+  for (int i = 0; i < npatch; i++) {
+    PatchGeo &g = geo[(size_t)i];
+    for (int d = 0; d < 3; d++) {
+      g.n[d] = patches[(size_t)i].n[d];
+      g.lo[d] = (int)patches[(size_t)i].lo[d];
+    }
+    g.nt[0] = (g.n[0] + TX - 1) / TX;
+    g.nt[1] = (g.n[1] + TY - 1) / TY;
+    g.nt[2] = (g.n[2] + tz - 1) / tz;
+    g.tiles = g.nt[0] * g.nt[1] * g.nt[2];
+    g.off = off;
+    const long long nc = (long long)g.n[0] * g.n[1] * g.n[2];
+    off += 5 * nc + (long long)(g.n[0] + 1) * g.n[1] * g.n[2] + (long long)g.n[0] * (g.n[1] + 1) * g.n[2] +
+           (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
+    total_tiles += g.tiles;
+    if (tiles0 < 0) tiles0 = g.tiles;
+    if (g.tiles != tiles0) same_tiles = false;
+    for (int kz = 0; kz < g.nt[2]; kz++)
+      for (int ky = 0; ky < g.nt[1]; ky++)
+        for (int kx = 0; kx < g.nt[0]; kx++) {
+          const int org[3] = {kx * TX, ky * TY, kz * tz};
+          const int ext[3] = {std::min(TX, g.n[0] - org[0]), std::min(TY, g.n[1] - org[1]), std::min(tz, g.n[2] - org[2])};
+          long long ne = 1;
+          for (int d = 0; d < 3; d++)
+            ne *= fdiv(g.lo[d] + org[d] + ext[d] + 2, bsz[d]) - fdiv(g.lo[d] + org[d] - 2, bsz[d]) + 1;
+          if (ne > TABMAX) return false;
+        }
+  }
+  uniform_tiles = same_tiles ? tiles0 : 0;
+  return true;
 }
 
 int read_status(dsp_ctx *c) {
@@ -551,47 +593,23 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   }
   for (long long k = 0; k < nmap; k++)
     if (map[(size_t)k] < 0) return DSP_ERR_INVALID_ARG;  // not a tiling
-  int TX, TY;
-  if (prm->precision == 1) update_tile_f32(&TX, &TY);
-  else update_tile_f64(&TX, &TY);
+  // the update-kernel variant: the requested one, else the first of this precision
+  const KernelVariant *var = nullptr;
+  for (int k = 0; k < kNumVariants; k++) {
+    const KernelVariant *v = kVariants[k]();
+    if (v->precision != prm->precision) continue;
+    if (prm->variant >= 0 ? v->id == prm->variant : !var) var = v;
+  }
+  if (!var) return DSP_ERR_INVALID_ARG;
   int tz = prm->tile_z;
   if (tz <= 0)
     for (int i = 0; i < npatch; i++) tz = std::max(tz, patches[i].n[2]);
-  std::vector<PatchGeo> geo((size_t)npatch);
+  std::vector<dsp_patch_desc> pvec(patches, patches + npatch);
+  std::vector<PatchGeo> geo;
   long long off = 0, total_tiles = 0;
-  int tiles0 = -1;
-  bool same_tiles = true;
-  for (int i = 0; i < npatch; i++) {
-    PatchGeo &g = geo[(size_t)i];
-    for (int d = 0; d < 3; d++) {
-      g.n[d] = patches[i].n[d];
-      g.lo[d] = (int)patches[i].lo[d];
-    }
-    g.nt[0] = (g.n[0] + TX - 1) / TX;
-    g.nt[1] = (g.n[1] + TY - 1) / TY;
-    g.nt[2] = (g.n[2] + tz - 1) / tz;
-    g.tiles = g.nt[0] * g.nt[1] * g.nt[2];
-    g.off = off;
-    const long long nc = (long long)g.n[0] * g.n[1] * g.n[2];
-    off += 5 * nc + (long long)(g.n[0] + 1) * g.n[1] * g.n[2] + (long long)g.n[0] * (g.n[1] + 1) * g.n[2] +
-           (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
-    total_tiles += g.tiles;
-    if (tiles0 < 0) tiles0 = g.tiles;
-    if (g.tiles != tiles0) same_tiles = false;
-    // the owner table of every tile must fit the kernel's shared table
-    auto fdiv = [](long long a, long long b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
-    for (int kz = 0; kz < g.nt[2]; kz++)
-      for (int ky = 0; ky < g.nt[1]; ky++)
-        for (int kx = 0; kx < g.nt[0]; kx++) {
-          const int x0 = kx * TX, y0 = ky * TY, z0 = kz * tz;
-          const int ext[3] = {std::min(TX, g.n[0] - x0), std::min(TY, g.n[1] - y0), std::min(tz, g.n[2] - z0)};
-          const int org[3] = {x0, y0, z0};
-          long long ne = 1;
-          for (int d = 0; d < 3; d++)
-            ne *= fdiv(g.lo[d] + org[d] + ext[d] + 2, bsz[d]) - fdiv(g.lo[d] + org[d] - 2, bsz[d]) + 1;
-          if (ne > TABMAX) return DSP_ERR_UNSUPPORTED;
-        }
-  }
+  int uniform_tiles = 0;
+  if (!make_geometry(pvec, var->tx, var->ty, tz, bsz, geo, off, total_tiles, uniform_tiles)) return DSP_ERR_UNSUPPORTED;
+  const bool same_tiles = uniform_tiles > 0;
   if (prm->dispatcher == 0 && !same_tiles) return DSP_ERR_UNSUPPORTED;  // the ready queue needs equal tile counts
   dsp_ctx *c = new dsp_ctx();
   memset(&c->d, 0, sizeof c->d);
@@ -612,11 +630,13 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   c->poisoned = 0;
   c->nev = 0;
   c->geo = geo;
+  c->var = var;
+  c->patches = pvec;
   DevCtx &d = c->d;
   d.np = npatch;
   d.ns = prm->nslices;
   d.tz = tz;
-  d.uniform_tiles = same_tiles ? tiles0 : 0;
+  d.uniform_tiles = uniform_tiles;
   d.total_tiles = total_tiles;
   d.slot_stride = off;
   for (int k = 0; k < 3; k++) {
@@ -757,7 +777,7 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
     delete c;
     return DSP_ERR_CUDA;
   }
-  c->grid_update = c->precision == 0 ? update_grid_f64(d) : c->precision == 2 ? update_grid_f64f(d) : update_grid_f32(d);
+  c->grid_update = var->grid(d);
   *out = c;
   return DSP_OK;
 }
@@ -1096,6 +1116,84 @@ extern "C" int dsp_load(dsp_ctx *c, const void *buf, size_t size) {
   CK(cudaStreamSynchronize(c->stream));
   c->poisoned = 0;
   c->err.clear();
+  return DSP_OK;
+}
+
+extern "C" int dsp_autotune(dsp_ctx *c, int32_t reps, int32_t *chosen, double *ms, int32_t *ids, int32_t cap,
+                            int32_t *n) {
+  if (!c || reps < 1) return DSP_ERR_INVALID_ARG;
+  if (c->poisoned) return fail(c, DSP_ERR_INVALID_ARG, "context is poisoned by an earlier error");
+  const KernelVariant *best = nullptr;
+  double best_ms = 0.0;
+  int count = 0;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const std::vector<PatchGeo> geo_orig = c->geo;
+  const KernelVariant *var_orig = c->var;
+  const long long tt_orig = c->d.total_tiles;
+  const int ut_orig = c->d.uniform_tiles;
+  auto install = [&](const KernelVariant *v, const std::vector<PatchGeo> &geo, long long tt, int ut) -> int {
+    c->var = v;
+    c->geo = geo;
+    c->d.total_tiles = tt;
+    c->d.uniform_tiles = ut;
+    CK(cudaMemcpyAsync(c->geo_d, geo.data(), sizeof(PatchGeo) * geo.size(), cudaMemcpyHostToDevice, c->stream));
+    c->grid_update = v->grid(c->d);
+    return DSP_OK;
+  };
+  int rc = DSP_OK;
+  for (int k = 0; k < kNumVariants && rc == DSP_OK; k++) {
+    const KernelVariant *v = kVariants[k]();
+    if (v->precision != c->precision) continue;
+    std::vector<PatchGeo> geo;
+    long long off = 0, tt = 0;
+    int ut = 0;
+    if (!make_geometry(c->patches, v->tx, v->ty, c->d.tz, c->d.bsz, geo, off, tt, ut)) continue;
+    if (c->prm.dispatcher == 0 && ut == 0) continue;
+    rc = install(v, geo, tt, ut);
+    if (rc) break;
+    // plan the next sweep (nothing is published: the ready list is dropped
+    // afterwards, and the update kernel only writes the patches' next slot)
+    CK(cudaMemsetAsync(c->ctl + CTL_NREADY, 0, sizeof(int), c->stream));
+    plan_kernel<<<1, PLAN_NT, 0, c->stream>>>(c->d, INFINITY, c->prm.time_mode == 0, 0);
+    CK(cudaGetLastError());
+    rc = launch_update(c);
+    if (rc) break;
+    CK(cudaEventRecord(e0, c->stream));
+    for (int r = 0; r < reps && rc == DSP_OK; r++) rc = launch_update(c);
+    CK(cudaEventRecord(e1, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    const double per = t / reps;
+    if (count < cap) {
+      if (ms) ms[count] = per;
+      if (ids) ids[count] = v->id;
+    }
+    count++;
+    if (!best || per < best_ms) {
+      best = v;
+      best_ms = per;
+    }
+  }
+  CK(cudaMemsetAsync(c->ctl + CTL_NREADY, 0, sizeof(int), c->stream));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == DSP_OK && !best) rc = fail(c, DSP_ERR_UNSUPPORTED, "no kernel variant fits this layout");
+  if (rc != DSP_OK) {
+    install(var_orig, geo_orig, tt_orig, ut_orig);
+    return rc;
+  }
+  std::vector<PatchGeo> geo;
+  long long off = 0, tt = 0;
+  int ut = 0;
+  make_geometry(c->patches, best->tx, best->ty, c->d.tz, c->d.bsz, geo, off, tt, ut);
+  rc = install(best, geo, tt, ut);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  if (chosen) *chosen = best->id;
+  if (n) *n = count;
   return DSP_OK;
 }
 

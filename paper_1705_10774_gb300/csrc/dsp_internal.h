@@ -3,6 +3,7 @@
 #include <cstdint>
 
 #include "../../include/dispatch.h"
+#include "dsp_variants.h"
 
 namespace dsp {
 
@@ -82,17 +83,18 @@ struct DevCtx {
   long long wait_budget;           // clock64 cycles a wait may spin before DSP_ERR_TIMEOUT
 };
 
-// Launchers implemented in the precision-specific translation units.
-int launch_update_f64(const DevCtx &c, int grid, void *stream);
-int launch_update_f32(const DevCtx &c, int grid, void *stream);
-int launch_update_f64f(const DevCtx &c, int grid, void *stream);
-int update_grid_f64f(const DevCtx &c);
-int launch_queue_f64(const DevCtx &c, int grid, double t_end, void *stream);
-int launch_queue_f64f(const DevCtx &c, int grid, double t_end, void *stream);
-int launch_queue_f32(const DevCtx &c, int grid, double t_end, void *stream);
-int update_grid_f64(const DevCtx &c);
-int update_grid_f32(const DevCtx &c);
-void update_tile_f64(int *tx, int *ty);
-void update_tile_f32(int *tx, int *ty);
+// A compiled variant of the update kernels (see dsp_variants.h).
+struct KernelVariant {
+  int id, precision;  // precision code of dsp_params
+  int tx, ty, nt;     // tile and threads per block
+  const char *name;
+  int (*launch_update)(const DevCtx &c, int grid, void *stream);
+  int (*launch_queue)(const DevCtx &c, int grid, double t_end, void *stream);
+  int (*grid)(const DevCtx &c);
+};
+
+#define DSP_DECLARE_VARIANT(id, T, TX, TY, NT, MB, PREC) const KernelVariant *variant_##id();
+DSP_VARIANT_LIST(DSP_DECLARE_VARIANT)
+#undef DSP_DECLARE_VARIANT
 
 }  // namespace dsp

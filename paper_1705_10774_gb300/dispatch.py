@@ -30,7 +30,7 @@ ERRORS = {v: k for k, v in globals().items() if k.startswith("DSP_ERR_")}
 
 EXPORTS = ["dsp_create", "dsp_set_state", "dsp_advance", "dsp_get_state", "dsp_get_times",
            "dsp_get_schedule", "dsp_diagnostics", "dsp_save", "dsp_load", "dsp_last_error",
-           "dsp_destroy", "dsp_diagnostics_noalloc"]
+           "dsp_destroy", "dsp_diagnostics_noalloc", "dsp_autotune"]
 
 DSP_NOALLOC_MAX_PATCHES = 16384
 
@@ -48,7 +48,7 @@ class dsp_params(ctypes.Structure):
                 ("time_mode", ctypes.c_int32), ("dt_pow2", ctypes.c_int32), ("dispatcher", ctypes.c_int32),
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
                 ("sched_capacity", ctypes.c_int64), ("timing", ctypes.c_int32), ("wait_budget", ctypes.c_int64),
-                ("graph", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
 
 class dsp_stats(ctypes.Structure):
@@ -103,6 +103,8 @@ def load(build_if_missing: bool = True):
         L.dsp_last_error.restype = ctypes.c_char_p
         L.dsp_destroy.argtypes = [VP]
         L.dsp_destroy.restype = None
+        L.dsp_autotune.argtypes = [VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), VP, VP, ctypes.c_int32,
+                                   ctypes.POINTER(ctypes.c_int32)]
         L.dsp_diagnostics_noalloc.argtypes = [VP, VP, VP, VP, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.POINTER(ctypes.c_int32), ctypes.c_double, VP,
                                               ctypes.POINTER(dsp_diag)]
@@ -132,7 +134,7 @@ class Dispatch:
 
     def __init__(self, n, lo, *, gamma, cfl, base_cells, box_len=(1.0, 1.0, 1.0), t0=0.0, dt_max=0.0,
                  nguard=3, nslices=3, precision=0, time_mode=0, dispatcher=1, tile_z=0,
-                 sched_capacity=0, timing=0, wait_budget=0, graph=0, stream=None):
+                 sched_capacity=0, timing=0, wait_budget=0, graph=0, variant=-1, stream=None):
         L = load()
         n = np.asarray(n, dtype=np.int64).reshape(-1, 3)
         lo = np.asarray(lo, dtype=np.int64).reshape(-1, 3)
@@ -157,6 +159,7 @@ class Dispatch:
         p.timing = timing
         p.wait_budget = wait_budget
         p.graph = graph
+        p.variant = variant
         self.params = p
         h = VP()
         rc = L.dsp_create(descs, self.np, ctypes.byref(p), VP(stream or 0), ctypes.byref(h))
@@ -231,6 +234,17 @@ class Dispatch:
         self._check(load().dsp_diagnostics(self._h, ctypes.byref(d)))
         return dict(mass=d.mass, mom=np.array(d.mom[:]), energy=d.energy, bmean=np.array(d.bmean[:]),
                     max_divb=d.max_divb, max_b=d.max_b)
+
+    def autotune(self, reps=3):
+        """dsp_autotune: returns (chosen variant id, {variant id: ms per launch})."""
+        chosen = ctypes.c_int32()
+        n = ctypes.c_int32()
+        ms = np.zeros(32)
+        ids = np.zeros(32, np.int32)
+        self._check(load().dsp_autotune(self._h, reps, ctypes.byref(chosen), ms.ctypes.data_as(VP),
+                                        ids.ctypes.data_as(VP), 32, ctypes.byref(n)))
+        k = min(n.value, 32)
+        return chosen.value, {int(i): float(m) for i, m in zip(ids[:k], ms[:k])}
 
     def save(self) -> bytes:
         used = ctypes.c_size_t()

@@ -365,3 +365,30 @@ def test_mixed_patch_sizes(lts):
     assert_same(g, o)
     key = lambda s: sorted(zip(*(x.tolist() for x in s)))
     assert key(g.schedule()) == key(o.schedule())
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_every_kernel_variant_gives_identical_results(precision):
+    """The compiled variants of one precision (tile shape, threads per block)
+    spread the same arithmetic differently over threads: bit-identical
+    states, and the autotuner's choice changes nothing either."""
+    import re
+    from paper_1705_10774_gb300 import build as B
+    ids = [v[0] for v in B.variants() if v[6] == precision]
+    assert len(ids) >= 2
+    lay, f = _mixed_case(seed=4) if precision != 0 else ics.config_linear_waves(n=16, amplitude=1e-3)
+    state = ics.to_patches(lay, f)
+    outs = []
+    for vid in ids + [None]:
+        g = Dispatch(lay.n, lay.lo, **kw_of(lay, f, time_mode=1), precision=precision,
+                     variant=-1 if vid is None else vid)
+        g.set_state(*state)
+        if vid is None:
+            chosen, table = g.autotune(reps=1)
+            assert chosen in ids and set(table) <= set(ids)
+        g.advance(t_end=0.002)
+        outs.append(g.get_state())
+        g.close()
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert np.array_equal(a, b)
