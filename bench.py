@@ -42,6 +42,13 @@ HBM_FALLBACK_GBS = 6800.0
 # the oracle bit for bit is timed too and reported as forms.f64_exact
 F64_PRECISION = 2
 
+# DRAM bytes (read + write) per update-kernel launch of the full workload,
+# from ncu's dram__bytes_read.sum + dram__bytes_write.sum on a 216-patch
+# capture of the same kernel, scaled by cells; None until taken on the
+# current kernel.
+TRAFFIC_F64 = (547.797504e6 + 422.244352e6) * 512 / 216   # variant 3 (FP64 FMA)
+TRAFFIC_F32 = 588.490240e6 + 508.069120e6                  # variant 5, full workload
+
 
 def radius2_guard_fraction(n):
     return ((n + 4) ** 3 - n ** 3) / n ** 3
@@ -53,6 +60,28 @@ def alg_bytes_per_cell(n, esize, sbar=1.0):
     from sbar neighbour slices."""
     V = 8
     return esize * (2 * V + sbar * radius2_guard_fraction(n) * V)
+
+
+# Algorithmic floating-point operations per cell-update (add, subtract,
+# multiply, divide and square root count one each; min, max, abs and compares
+# count none), from the per-cell arithmetic of the step as defined: primitive
+# recovery; 21 MC-limited slopes (two differences each) and 3 face
+# differences for the normal field; the Hancock predictor; its positivity
+# test; 3 faces of left and right states (8 components each); 3 HLL fluxes
+# (5 components, subsonic branch); 3 edge EMFs from 4 corner states of 4
+# components each; the conservative and constrained-transport update; the
+# signal speed of the new state.  Guard-zone interpolation is not counted
+# (global steps copy neighbour slices).
+ALG_FLOPS = {"primitives": 28, "slopes": 21 * 7 + 3, "predictor": 130, "positivity": 18, "face_states": 3 * 32,
+             "hll": 3 * 176, "edge_emf": 3 * 111, "update": 5 * 7 + 3 * 5, "signal_speed": 28 + 63}
+ALG_FLOPS_PER_CELL = sum(ALG_FLOPS.values())
+
+# Arithmetic peaks derived from unit counts and the maximum SM clock:
+# 152 SMs at 2.07 GHz; FP64: 2 fused multiply-adds per SM per cycle (the
+# GB300 FP64 rate, 1.26 TFLOP/s); FP32: 128 lanes per SM.
+SMS, SM_GHZ = 152, 2.07
+FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_GHZ / 1e3
+FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_GHZ / 1e3
 
 
 def measured_peaks():
@@ -160,15 +189,39 @@ def make_input(patches=PATCHES):
     return lay, f, ics.to_patches(lay, f)
 
 
-def run_form(lay, state_dev, precision, steps, warmup, td):
+def rooflines(ncells, esize, kernel_ms, hbm_peak, peak_kind):
+    """The update kernel against its two roofs: HBM bandwidth (algorithmic
+    bytes) and arithmetic (algorithmic flops against the FP64 or FP32 peak).
+    The bound named first is the one the kernel is limited by (FP64: the
+    FP64 pipe; FP32: neither, it is issue-bound, and the HBM figure is the
+    benchmark's metric)."""
+    bpl = alg_bytes_per_cell(NCELL, esize) * ncells
+    gbs = bpl / (kernel_ms * 1e-3) / 1e9
+    fpl = ALG_FLOPS_PER_CELL * ncells
+    tfs = fpl / (kernel_ms * 1e-3) / 1e12
+    fpeak = FP64_PEAK_TFLOPS if esize == 8 else FP32_PEAK_TFLOPS
+    hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+           "alg_bytes_per_launch": bpl, "peak_kind": peak_kind}
+    alu = {"bound": "alu", "achieved": tfs, "peak": fpeak, "unit": "TFLOP/s", "frac": tfs / fpeak,
+           "alg_flops_per_launch": fpl, "alg_flops_per_cell": ALG_FLOPS_PER_CELL,
+           "peak_kind": "derived: 152 SMs x %s x 2.07 GHz" % ("2 FP64 FMA/cycle" if esize == 8 else "128 FP32 lanes")}
+    if esize == 8:
+        return dict(alu, hbm=hbm)
+    return dict(hbm, alu=alu)
+
+
+def run_form(lay, state_dev, precision, steps, warmup, td, variant=-1):
     """Time `steps` global steps of one precision form from the initial state."""
     import torch
     from paper_1705_10774_gb300.dispatch import Dispatch
     stream = torch.cuda.current_stream()
     g = Dispatch(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
-                 precision=precision, time_mode=0, timing=1, stream=stream.cuda_stream)
+                 precision=precision, time_mode=0, timing=1, variant=variant, stream=stream.cuda_stream)
     g.set_state(*state_dev)
-    g.tuned = g.autotune(reps=2)          # pick the fastest compiled variant (untimed set-up)
+    if variant < 0:
+        g.tuned = g.autotune(reps=2)      # pick the fastest compiled variant (untimed set-up)
+    else:
+        g.tuned = (variant, {})
     if warmup:
         g.advance(max_sweeps=warmup)
     g.set_state(*state_dev)
@@ -202,7 +255,7 @@ def gpu_arm(args):
     if args.form != "both":
         prec = {"f32": 1, "f64": F64_PRECISION, "f64_exact": 0}[args.form]
         sd = [a.float() for a in state_dev] if prec else state_dev
-        g, st, ms = run_form(lay, sd, prec, args.steps, args.warmup, td)
+        g, st, ms = run_form(lay, sd, prec, args.steps, args.warmup, td, args.variant)
         if rank == 0:
             print(json.dumps({"form": args.form, "patches": lay.npatch, "ms_per_step": ms / args.steps,
                               "kernel_ms_avg": st["kernel_ms"] / max(st["kernel_launches"], 1),
@@ -214,12 +267,9 @@ def gpu_arm(args):
     cells_all = sum_over_ranks(td, float(st["cell_updates"]))
     value = cells_all / (ms_max * 1e-3)
     kavg = st["kernel_ms"] / max(st["kernel_launches"], 1)
-    bpl = alg_bytes_per_cell(NCELL, 8) * ncells
-    achieved = bpl / (kavg * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "update_kernel variant %d" % g.tuned[0], "kernel_ms_avg": kavg,
-            "alg_bytes_per_launch": bpl, "peak_kind": peak_kind,
-            "autotune_ms_per_variant": g.tuned[1]}
+    roof = rooflines(ncells, 8, kavg, peak, peak_kind)
+    roof.update({"traffic": TRAFFIC_F64, "kernel": "update_kernel variant %d" % g.tuned[0], "kernel_ms_avg": kavg,
+                 "autotune_ms_per_variant": g.tuned[1]})
     g.close()
 
     forms = {}
@@ -238,11 +288,10 @@ def gpu_arm(args):
         ms32_max = max_over_ranks(td, ms32)
         v32 = sum_over_ranks(td, float(st32["cell_updates"])) / (ms32_max * 1e-3)
         k32 = st32["kernel_ms"] / max(st32["kernel_launches"], 1)
-        b32 = alg_bytes_per_cell(NCELL, 4) * ncells
-        a32 = b32 / (k32 * 1e-3) / 1e9
-        forms["f32"] = {"value": v32, "ms_per_step": ms32_max / args.steps, "dtype": "f32",
-                        "roofline": {"bound": "hbm", "achieved": a32, "peak": peak, "unit": "GB/s",
-                                     "frac": a32 / peak, "kernel_ms_avg": k32, "alg_bytes_per_launch": b32}}
+        r32 = rooflines(ncells, 4, k32, peak, peak_kind)
+        r32.update({"traffic": TRAFFIC_F32, "kernel": "update_kernel variant %d" % g32.tuned[0],
+                    "kernel_ms_avg": k32, "autotune_ms_per_variant": g32.tuned[1]})
+        forms["f32"] = {"value": v32, "ms_per_step": ms32_max / args.steps, "dtype": "f32", "roofline": r32}
         g32.close()
         del state32
 
@@ -285,10 +334,12 @@ def e2e_measure(lay, state, steps, td):
     outs = [torch.empty_like(a).pin_memory() for a in pinned]
     stream = torch.cuda.current_stream()
     g = Dispatch(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
-                 precision=0, time_mode=0, stream=stream.cuda_stream)
+                 precision=F64_PRECISION, time_mode=0, stream=stream.cuda_stream)
     h_in = sum(a.numel() * a.element_size() for a in pinned)
     h_out = sum(a.numel() * a.element_size() for a in outs)
     g.set_state(*[a.numpy() for a in pinned])   # allocate the staging buffer before timing
+    g.autotune(reps=2)
+    g.set_state(*[a.numpy() for a in pinned])
     g.advance(max_sweeps=1)
     g.get_state(out=[a.numpy() for a in outs])
     torch.cuda.synchronize()
@@ -505,6 +556,8 @@ def main():
                     help="f64 / f32: time only that form and print a short line (profiling runs)")
     ap.add_argument("--patches", type=int, default=PATCHES,
                     help="patches per axis for --form runs (profiling on a smaller box)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="--form runs: use this compiled kernel variant instead of autotuning")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
