@@ -7,7 +7,10 @@
  *
  * What it computes (DISPATCH I, Nordlund et al. 2018):
  *   - patches with guard zones on a periodic Cartesian level (Sec. 2.3,
- *     "cartesian" component; task/patch data types, Sec. 2.1);
+ *     "cartesian" component; task/patch data types, Sec. 2.1), optionally
+ *     with a second level at half the cell size: guard values across the
+ *     resolution jump by conservative interpolation (prolongation) and
+ *     averaging (restriction), Sec. 3 A;
  *   - a circular buffer of time slices per patch; a new state overwrites the
  *     oldest slice (Sec. 3 A, single-task view);
  *   - guard zones filled by linear interpolation in time from the neighbours'
@@ -50,8 +53,9 @@ enum { RHO = 0, VX = 1, VY = 2, VZ = 3, PR = 4, BX = 5, BY = 6, BZ = 7 };
 #define PFLOOR 1e-20
 
 typedef struct {
+  int level;  /* refinement level: 0, or 1 at half the cell size */
   int n[3];
-  int64_t lo[3];
+  int64_t lo[3]; /* first interior cell in the level's index space */
   int nslot;
   double **U, **bx, **by, **bz; /* [slot] -> interior arrays */
   double *ts;                   /* time of each slot (NAN = empty) */
@@ -65,8 +69,9 @@ typedef struct {
 typedef struct {
   int np;
   opatch *p;
-  double gamma, cfl, t0, dt_max, dx;
-  int64_t L[3];
+  double gamma, cfl, t0, dt_max, dx; /* dx: level-0 cell size */
+  int64_t L[2][3];                   /* cells per axis of the periodic box on each level */
+  int nlev;                          /* 1, or 2 when level-1 patches exist */
   int g, nslot, time_mode, disp_mode;
   int64_t nsched, capsched;
   int64_t *s_patch;
@@ -277,36 +282,69 @@ static int64_t nfx(const opatch *P) { return (int64_t)(P->n[0] + 1) * P->n[1] * 
 static int64_t nfy(const opatch *P) { return (int64_t)P->n[0] * (P->n[1] + 1) * P->n[2]; }
 static int64_t nfz(const opatch *P) { return (int64_t)P->n[0] * P->n[1] * (P->n[2] + 1); }
 
-/* Does some periodic image of [qlo, qlo+qn) intersect [plo-g, plo+pn+g)?
- * Writes the set of intersecting image shifts as a bit mask (-L, 0, +L). */
-static int axis_hit(int64_t plo, int pn, int64_t qlo, int qn, int g, int64_t L) {
+/* Floor of a / b for b > 0. */
+static int64_t fdiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+/* Does some periodic image of [qlo, qlo+qn) intersect [a, b)?  Writes the
+ * set of intersecting image shifts as a bit mask (-L, 0, +L). */
+static int ival_hit(int64_t a, int64_t b, int64_t qlo, int qn, int64_t L) {
   int mask = 0;
   for (int s = -1; s <= 1; s++) {
-    int64_t a = qlo + s * L, b = a + qn;
-    if (a < plo + pn + g && b > plo - g) mask |= 1 << (s + 1);
+    int64_t qa = qlo + s * L, qb = qa + qn;
+    if (qa < b && qb > a) mask |= 1 << (s + 1);
   }
   return mask;
 }
 
+/* The cells of the other level that patch P may read, along one axis, as a
+ * half-open interval in that level's index space.  A level-1 patch reads
+ * level-0 cells through prolongation: the parents of its padded cells and
+ * one more coarse cell on each side (the limited slopes).  A level-0 patch
+ * reads level-1 cells through restriction: the children of its padded cells
+ * and of the cell above the top guard face. */
+static void cross_interval(const opatch *P, int d, int g, int64_t *a, int64_t *b) {
+  if (P->level == 1) {
+    *a = fdiv(P->lo[d] - g, 2) - 1;
+    *b = fdiv(P->lo[d] + P->n[d] + g - 1, 2) + 2;
+  } else {
+    *a = 2 * (P->lo[d] - g);
+    *b = 2 * (P->lo[d] + P->n[d] + g) + 2;
+  }
+}
+
 void orc_destroy(orc_ctx *c);
 
-orc_ctx *orc_create(int np, const int32_t *n, const int64_t *lo, double gamma, double cfl, double t0,
-                    double dt_max, const double *box_len, const int32_t *base, int nguard, int nslot,
+orc_ctx *orc_create(int np, const int32_t *n, const int64_t *lo, const int32_t *level, double gamma, double cfl,
+                    double t0, double dt_max, const double *box_len, const int32_t *base, int nguard, int nslot,
                     int time_mode, int disp_mode) {
   if (np <= 0 || nguard < 2 || nslot < 3) return NULL;
   /* a patch must be wider than its guard depth so that every guard cell and
    * guard face lies in one of the adjacent patches */
   for (int i = 0; i < 3 * np; i++)
     if (n[i] <= nguard) return NULL;
+  /* level-1 patches cover whole level-0 cells */
+  for (int i = 0; i < np; i++) {
+    int l = level ? level[i] : 0;
+    if (l < 0 || l > 1) return NULL;
+    if (l == 1)
+      for (int d = 0; d < 3; d++)
+        if ((n[3 * i + d] & 1) || (lo[3 * i + d] & 1)) return NULL;
+  }
   orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
   c->np = np;
   c->gamma = gamma; c->cfl = cfl; c->t0 = t0; c->dt_max = dt_max;
   c->g = nguard; c->nslot = nslot; c->time_mode = time_mode; c->disp_mode = disp_mode;
   c->dx = box_len[0] / base[0];
-  for (int d = 0; d < 3; d++) c->L[d] = base[d];
+  for (int d = 0; d < 3; d++) {
+    c->L[0][d] = base[d];
+    c->L[1][d] = 2 * (int64_t)base[d];
+  }
+  c->nlev = 1;
   c->p = (opatch *)calloc(np, sizeof(opatch));
   for (int i = 0; i < np; i++) {
     opatch *P = &c->p[i];
+    P->level = level ? level[i] : 0;
+    if (P->level == 1) c->nlev = 2;
     for (int d = 0; d < 3; d++) { P->n[d] = n[3 * i + d]; P->lo[d] = lo[3 * i + d]; }
     P->nslot = nslot;
     P->U = (double **)calloc(nslot, sizeof(double *));
@@ -326,29 +364,46 @@ orc_ctx *orc_create(int np, const int32_t *n, const int64_t *lo, double gamma, d
     P->latest = 0;
     P->dt_last = 0.0;
   }
-  /* neighbours: every patch with an interior that some periodic image puts
-   * inside this patch's padded box (the patch itself counts only through a
-   * non-trivial image) */
-  int *tmp = (int *)malloc(sizeof(int) * np);
+  /* neighbours.  Same level: every patch with an interior that some periodic
+   * image puts inside this patch's padded box (the patch itself counts only
+   * through a non-trivial image).  Other level: every patch whose interior
+   * meets the cells this patch may read on that level (cross_interval), and,
+   * so that the relation is symmetric, every patch that may read this one. */
+  char *rel = (char *)calloc((size_t)np * np, 1);
   for (int i = 0; i < np; i++) {
     opatch *P = &c->p[i];
-    int cnt = 0;
     for (int j = 0; j < np; j++) {
       opatch *Q = &c->p[j];
       int m[3], ok = 1;
       for (int d = 0; d < 3; d++) {
-        m[d] = axis_hit(P->lo[d], P->n[d], Q->lo[d], Q->n[d], nguard, c->L[d]);
+        int64_t a, b;
+        if (Q->level == P->level) {
+          a = P->lo[d] - nguard;
+          b = P->lo[d] + P->n[d] + nguard;
+        } else {
+          cross_interval(P, d, nguard, &a, &b);
+        }
+        m[d] = ival_hit(a, b, Q->lo[d], Q->n[d], c->L[Q->level][d]);
         if (!m[d]) ok = 0;
       }
       if (!ok) continue;
       if (j == i && m[0] == 2 && m[1] == 2 && m[2] == 2) continue;
-      tmp[cnt++] = j;
+      rel[(size_t)i * np + j] = 1;
+      rel[(size_t)j * np + i] = 1;
     }
+  }
+  int *tmp = (int *)malloc(sizeof(int) * np);
+  for (int i = 0; i < np; i++) {
+    opatch *P = &c->p[i];
+    int cnt = 0;
+    for (int j = 0; j < np; j++)
+      if (rel[(size_t)i * np + j]) tmp[cnt++] = j;
     P->nnb = cnt;
     P->nb = (int *)malloc(sizeof(int) * (cnt > 0 ? cnt : 1));
     memcpy(P->nb, tmp, sizeof(int) * cnt);
   }
   free(tmp);
+  free(rel);
   return c;
 }
 
@@ -506,22 +561,148 @@ static double tval(const double *A, const double *B, int64_t idx, double w) {
   return A[idx] + w * (B[idx] - A[idx]);
 }
 
-/* Locate the patch among P's neighbours (or P itself) whose interior holds
- * the level cell (gx, gy, gz) (periodic), and the local cell index there. */
-static int owner(orc_ctx *c, opatch *P, int ip, int64_t gx, int64_t gy, int64_t gz, int loc[3]) {
-  int64_t g[3] = {gx, gy, gz};
+/* Locate the patch of level lev among P's neighbours (or P itself) whose
+ * interior holds the level-lev cell g (periodic), and the local cell index
+ * there; -1 if none. */
+static int owner(orc_ctx *c, opatch *P, int ip, int lev, const int64_t g[3], int loc[3]) {
   for (int q = -1; q < P->nnb; q++) {
     int iq = q < 0 ? ip : P->nb[q];
     opatch *Q = &c->p[iq];
+    if (Q->level != lev) continue;
     int in = 1;
     for (int d = 0; d < 3; d++) {
-      int64_t r = imod(g[d] - Q->lo[d], c->L[d]);
+      int64_t r = imod(g[d] - Q->lo[d], c->L[lev][d]);
       if (r >= Q->n[d]) { in = 0; break; }
       loc[d] = (int)r;
     }
     if (in) return iq;
   }
   return -1;
+}
+
+/* Conserved values u[5] of level-lev cell g at time t, from the patch of
+ * that level that owns it (copied or interpolated in time). */
+static int cell_at(orc_ctx *c, opatch *P, int ip, int lev, const int64_t g[3], double t, double u[5]) {
+  int loc[3], sa, sb;
+  double w;
+  int iq = owner(c, P, ip, lev, g, loc);
+  if (iq < 0) return ORC_EINVAL;
+  opatch *Q = &c->p[iq];
+  if (pick(c, Q, t, &sa, &sb, &w) != ORC_OK) return ORC_EBRACKET;
+  int64_t qc = ncell(Q);
+  int64_t id = ((int64_t)loc[2] * Q->n[1] + loc[1]) * Q->n[0] + loc[0];
+  for (int q = 0; q < 5; q++) u[q] = tval(Q->U[sa] + q * qc, sb >= 0 ? Q->U[sb] + q * qc : NULL, id, w);
+  return ORC_OK;
+}
+
+/* Face along axis ax on the low side of level-lev cell g at time t, from
+ * the patch of that level that owns the cell; `up` = 1 takes the face on the
+ * cell's high side instead (the same patch owns both). */
+static int face_at(orc_ctx *c, opatch *P, int ip, int lev, int ax, const int64_t g[3], int up, double t,
+                   double *out) {
+  int loc[3], sa, sb;
+  double w;
+  int iq = owner(c, P, ip, lev, g, loc);
+  if (iq < 0) return ORC_EINVAL;
+  opatch *Q = &c->p[iq];
+  if (pick(c, Q, t, &sa, &sb, &w) != ORC_OK) return ORC_EBRACKET;
+  loc[ax] += up;
+  int qx = Q->n[0], qy = Q->n[1];
+  int64_t id = ax == 0 ? ((int64_t)loc[2] * qy + loc[1]) * (qx + 1) + loc[0]
+             : ax == 1 ? ((int64_t)loc[2] * (qy + 1) + loc[1]) * qx + loc[0]
+                       : ((int64_t)loc[2] * qy + loc[1]) * qx + loc[0];
+  double **arr = ax == 0 ? Q->bx : ax == 1 ? Q->by : Q->bz;
+  *out = tval(arr[sa], sb >= 0 ? arr[sb] : NULL, id, w);
+  return ORC_OK;
+}
+
+/* Is level-0 cell C covered by level 1 (its children lie in a level-1
+ * patch; level-1 patches cover whole level-0 cells)? */
+static int covered(orc_ctx *c, opatch *P, int ip, const int64_t C[3]) {
+  int64_t f[3] = {2 * C[0], 2 * C[1], 2 * C[2]};
+  int loc[3];
+  return owner(c, P, ip, 1, f, loc) >= 0;
+}
+
+/* Restriction (Sec. 3 A: guard values in space from a neighbour of other
+ * resolution, by conservative averaging): the conserved values of level-0 cell C are the mean of its 8
+ * level-1 children, summed z-, y-, x-child in that order. */
+static int restrict_cell(orc_ctx *c, opatch *P, int ip, const int64_t C[3], double t, double u[5]) {
+  double s[5] = {0, 0, 0, 0, 0}, v[5];
+  for (int kz = 0; kz < 2; kz++)
+    for (int ky = 0; ky < 2; ky++)
+      for (int kx = 0; kx < 2; kx++) {
+        int64_t f[3] = {2 * C[0] + kx, 2 * C[1] + ky, 2 * C[2] + kz};
+        int rc = cell_at(c, P, ip, 1, f, t, v);
+        if (rc) return rc;
+        for (int q = 0; q < 5; q++) s[q] = s[q] + v[q];
+      }
+  for (int q = 0; q < 5; q++) u[q] = 0.125 * s[q];
+  return ORC_OK;
+}
+
+/* The face along ax on the low side of level-0 cell C: the mean of the 4
+ * level-1 faces on it (the children's low faces), the two transverse child
+ * offsets looped in z, y, x order. */
+static int restrict_face(orc_ctx *c, opatch *P, int ip, int ax, const int64_t C[3], double t, double *out) {
+  double s = 0.0, v;
+  for (int kz = 0; kz < 2; kz++)
+    for (int ky = 0; ky < 2; ky++)
+      for (int kx = 0; kx < 2; kx++) {
+        int k3[3] = {kx, ky, kz};
+        if (k3[ax]) continue;
+        int64_t f[3] = {2 * C[0] + kx, 2 * C[1] + ky, 2 * C[2] + kz};
+        int rc = face_at(c, P, ip, 1, ax, f, 0, t, &v);
+        if (rc) return rc;
+        s = s + v;
+      }
+  *out = 0.25 * s;
+  return ORC_OK;
+}
+
+/* Prolongation (Sec. 3 A: conservative interpolation from a coarser
+ * neighbour): level-1 cell f
+ * takes its level-0 parent C's conserved values plus a quarter of the
+ * MC-limited slopes of C (one per axis, from C's two level-0 neighbours on
+ * that axis), signed by the child's side: u = u_C + (s_x sx + s_y sy +
+ * s_z sz)/4.  The 8 children of C average to u_C.  Level-0 values are read
+ * as stored, also under the refined region. */
+static int prolong_cell(orc_ctx *c, opatch *P, int ip, const int64_t f[3], double t, double u[5]) {
+  int64_t C[3] = {fdiv(f[0], 2), fdiv(f[1], 2), fdiv(f[2], 2)};
+  double uc[5], ul[5], ur[5], sl[3][5];
+  int rc = cell_at(c, P, ip, 0, C, t, uc);
+  if (rc) return rc;
+  for (int d = 0; d < 3; d++) {
+    int64_t Cm[3] = {C[0], C[1], C[2]}, Cp[3] = {C[0], C[1], C[2]};
+    Cm[d] -= 1;
+    Cp[d] += 1;
+    if ((rc = cell_at(c, P, ip, 0, Cm, t, ul))) return rc;
+    if ((rc = cell_at(c, P, ip, 0, Cp, t, ur))) return rc;
+    for (int q = 0; q < 5; q++) sl[d][q] = mc(uc[q] - ul[q], ur[q] - uc[q]);
+  }
+  for (int q = 0; q < 5; q++) {
+    double a = (f[0] - 2 * C[0]) ? sl[0][q] : -sl[0][q];
+    double b = (f[1] - 2 * C[1]) ? sl[1][q] : -sl[1][q];
+    double e = (f[2] - 2 * C[2]) ? sl[2][q] : -sl[2][q];
+    u[q] = uc[q] + 0.25 * ((a + b) + e);
+  }
+  return ORC_OK;
+}
+
+/* The face along ax on the low side of level-1 cell f, from level 0: a
+ * level-1 face on a level-0 face takes that face's value; a level-1 face
+ * inside a level-0 cell takes the mean of that cell's two faces along ax.
+ * Piecewise constant along the face, so every level-1 cell inside one
+ * level-0 cell keeps that cell's divergence. */
+static int prolong_face(orc_ctx *c, opatch *P, int ip, int ax, const int64_t f[3], double t, double *out) {
+  int64_t C[3] = {fdiv(f[0], 2), fdiv(f[1], 2), fdiv(f[2], 2)};
+  double lo, hi;
+  int rc = face_at(c, P, ip, 0, ax, C, 0, t, &lo);
+  if (rc) return rc;
+  if (f[ax] == 2 * C[ax]) { *out = lo; return ORC_OK; }
+  if ((rc = face_at(c, P, ip, 0, ax, C, 1, t, &hi))) return rc;
+  *out = 0.5 * (lo + hi);
+  return ORC_OK;
 }
 
 typedef struct {
@@ -536,12 +717,14 @@ typedef struct {
 #define PFZ(pd, i, j, k) ((((int64_t)(k) + g) * (pd)->N[1] + ((j) + g)) * (pd)->N[0] + ((i) + g))
 
 /* Fill the padded box of patch ip at its current time.  Cell-centred values
- * of guard cells come from the neighbour owning the cell.  A face on one of
- * P's interior cells is P's own; any other face is taken from the patch that
- * owns the cell on the face's upper side. */
+ * of guard cells come from the neighbour of the same level owning the cell;
+ * on level 0 a guard cell covered by level 1 is restricted from there, and
+ * on level 1 a guard cell no level-1 patch owns is prolonged from level 0.
+ * A face on one of P's interior cells is P's own; any other face is taken by
+ * the same rules from the cell on the face's upper side. */
 static int fill_padded(orc_ctx *c, int ip, padded *pd) {
   opatch *P = &c->p[ip];
-  int g = c->g;
+  int g = c->g, lev = P->level;
   int nx = P->n[0], ny = P->n[1], nz = P->n[2];
   int Nx = nx + 2 * g, Ny = ny + 2 * g, Nz = nz + 2 * g;
   int64_t Nc = (int64_t)Nx * Ny * Nz;
@@ -558,16 +741,15 @@ static int fill_padded(orc_ctx *c, int ip, padded *pd) {
           for (int q = 0; q < 5; q++) pd->U[q * Nc + pi] = P->U[s0][q * nc + id];
           continue;
         }
-        int loc[3], sa, sb;
-        double w;
-        int iq = owner(c, P, ip, P->lo[0] + i, P->lo[1] + j, P->lo[2] + k, loc);
-        if (iq < 0) return ORC_EINVAL;
-        opatch *Q = &c->p[iq];
-        if (pick(c, Q, t, &sa, &sb, &w) != ORC_OK) return ORC_EBRACKET;
-        int64_t qc = ncell(Q);
-        int64_t id = ((int64_t)loc[2] * Q->n[1] + loc[1]) * Q->n[0] + loc[0];
-        for (int q = 0; q < 5; q++)
-          pd->U[q * Nc + pi] = tval(Q->U[sa] + q * qc, sb >= 0 ? Q->U[sb] + q * qc : NULL, id, w);
+        int64_t gc[3] = {P->lo[0] + i, P->lo[1] + j, P->lo[2] + k};
+        double u[5];
+        int loc[3], rc;
+        if (lev == 0 && c->nlev > 1 && covered(c, P, ip, gc)) rc = restrict_cell(c, P, ip, gc, t, u);
+        else if (owner(c, P, ip, lev, gc, loc) >= 0) rc = cell_at(c, P, ip, lev, gc, t, u);
+        else if (lev == 1) rc = prolong_cell(c, P, ip, gc, t, u);
+        else rc = ORC_EINVAL;
+        if (rc) return rc;
+        for (int q = 0; q < 5; q++) pd->U[q * Nc + pi] = u[q];
       }
   /* faces, one axis at a time */
   for (int ax = 0; ax < 3; ax++) {
@@ -585,21 +767,27 @@ static int fill_padded(orc_ctx *c, int ip, padded *pd) {
             dst[pi] = (ax == 0 ? P->bx[s0] : ax == 1 ? P->by[s0] : P->bz[s0])[id];
             continue;
           }
-          int loc[3], sa, sb;
-          double w;
-          int iq = owner(c, P, ip, P->lo[0] + i, P->lo[1] + j, P->lo[2] + k, loc);
-          if (iq < 0) return ORC_EINVAL;
-          opatch *Q = &c->p[iq];
-          if (pick(c, Q, t, &sa, &sb, &w) != ORC_OK) return ORC_EBRACKET;
-          int qx = Q->n[0], qy = Q->n[1];
-          int64_t id = ax == 0 ? ((int64_t)loc[2] * qy + loc[1]) * (qx + 1) + loc[0]
-                     : ax == 1 ? ((int64_t)loc[2] * (qy + 1) + loc[1]) * qx + loc[0]
-                               : ((int64_t)loc[2] * qy + loc[1]) * qx + loc[0];
-          double **arr = ax == 0 ? Q->bx : ax == 1 ? Q->by : Q->bz;
-          dst[pi] = tval(arr[sa], sb >= 0 ? arr[sb] : NULL, id, w);
+          int64_t gc[3] = {P->lo[0] + i, P->lo[1] + j, P->lo[2] + k};
+          int loc[3], rc;
+          double v;
+          if (lev == 0 && c->nlev > 1 && covered(c, P, ip, gc)) rc = restrict_face(c, P, ip, ax, gc, t, &v);
+          else if (owner(c, P, ip, lev, gc, loc) >= 0) rc = face_at(c, P, ip, lev, ax, gc, 0, t, &v);
+          else if (lev == 1) rc = prolong_face(c, P, ip, ax, gc, t, &v);
+          else rc = ORC_EINVAL;
+          if (rc) return rc;
+          dst[pi] = v;
         }
   }
   return ORC_OK;
+}
+
+/* The padded box of patch ip at its current time, as the update reads it
+ * (guard depth g): U[5][Nz][Ny][Nx], bx[Nz][Ny][Nx+1], by[Nz][Ny+1][Nx],
+ * bz[Nz+1][Ny][Nx] with N = n + 2g; for checking the guard fill alone. */
+int orc_fill_padded(orc_ctx *c, int ip, double *U, double *bx, double *by, double *bz) {
+  padded pd;
+  pd.U = U; pd.bx = bx; pd.by = by; pd.bz = bz;
+  return fill_padded(c, ip, &pd);
 }
 
 /* ------------------------------------------------------------------ */
@@ -636,8 +824,9 @@ static int update_patch(orc_ctx *c, int ip, double dt, double *oU, double *obx, 
   if (rc != ORC_OK) goto done;
 
   double gamma = c->gamma;
-  double h = 0.5 * dt / c->dx;
-  double dtdx = dt / c->dx;
+  double dxl = ldexp(c->dx, -P->level);
+  double h = 0.5 * dt / dxl;
+  double dtdx = dt / dxl;
 
   /* A4: primitives on every padded cell */
   for (int k = -g; k < nz + g; k++)
@@ -858,7 +1047,7 @@ static int patch_dt(orc_ctx *c, int ip, double t_end, double *dt_out) {
     M = fmax(M, Q->smax[sa]);
     if (sb >= 0) M = fmax(M, Q->smax[sb]);
   }
-  double dtc = c->cfl * c->dx / M;
+  double dtc = c->cfl * ldexp(c->dx, -P->level) / M;
   double dt = pow2_floor(dtc);
   if (c->dt_max > 0.0 && dt > c->dt_max) dt = c->dt_max;
   while (fmod(t, dt) != 0.0) dt = dt * 0.5;
@@ -1045,17 +1234,20 @@ static void nadd(nsum *a, double x) {
   a->s = t;
 }
 
-/* out[0..4]: volume integrals of rho, m_x, m_y, m_z, E (Neumaier sums);
+/* Every patch's cells count with their own level's cell volume (with two
+ * levels, level-0 cells under the refined region count too).
+ * out[0..4]: volume integrals of rho, m_x, m_y, m_z, E (Neumaier sums);
  * out[5..7]: volume integrals of the face fields, each face counted once
  * (the low face of every cell); out[8]: max over cells of |sum_d Delta_d b|;
  * out[9]: max |b| over faces. */
 void orc_diagnostics(orc_ctx *c, double *out) {
   nsum acc[8];
   memset(acc, 0, sizeof acc);
-  double dV = c->dx * c->dx * c->dx;
   double mdiv = 0.0, mb = 0.0;
   for (int ip = 0; ip < c->np; ip++) {
     opatch *P = &c->p[ip];
+    double dxl = ldexp(c->dx, -P->level);
+    double dV = dxl * dxl * dxl;
     int s = P->latest, nx = P->n[0], ny = P->n[1], nz = P->n[2];
     int64_t nc = ncell(P);
     for (int k = 0; k < nz; k++)

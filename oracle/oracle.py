@@ -54,7 +54,7 @@ def lib():
             path = build()
             L = ctypes.CDLL(path)
             L.orc_create.restype = P
-            L.orc_create.argtypes = [ctypes.c_int, P, P, D, D, D, D, P, P,
+            L.orc_create.argtypes = [ctypes.c_int, P, P, P, D, D, D, D, P, P,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.orc_destroy.argtypes = [P]
             L.orc_set_state.argtypes = [P, P, P, P, P]
@@ -70,6 +70,7 @@ def lib():
             L.orc_patch_dt.argtypes = [P, ctypes.c_int, D, P]
             L.orc_update_patch.argtypes = [P, ctypes.c_int, D, P, P, P, P, P]
             L.orc_num_nbors.argtypes = [P, ctypes.c_int, P]
+            L.orc_fill_padded.argtypes = [P, ctypes.c_int, P, P, P, P]
             L.orc_last_error.restype = ctypes.c_char_p
             L.orc_last_error.argtypes = [P]
             L.orc_prim.argtypes = [P, P, D, P]
@@ -96,22 +97,26 @@ def _f64(a) -> np.ndarray:
 
 
 class Oracle:
-    """One oracle context: a set of patches on one periodic level.
+    """One oracle context: a set of patches on a periodic box, on level 0
+    and optionally level 1 (half the cell size).
 
     ``n`` and ``lo`` are (npatch, 3) integer arrays (cells per axis, first
-    interior cell in the level's index space, axis order x, y, z).
+    interior cell in the patch's level's index space, axis order x, y, z);
+    ``level`` is an optional (npatch,) array of 0 / 1.
     """
 
-    def __init__(self, n, lo, *, gamma, cfl, base_cells, box_len=(1.0, 1.0, 1.0), t0=0.0,
+    def __init__(self, n, lo, *, level=None, gamma, cfl, base_cells, box_len=(1.0, 1.0, 1.0), t0=0.0,
                  dt_max=0.0, nguard=3, nslices=3, time_mode=0, dispatcher=1):
         L = lib()
         self.n = np.ascontiguousarray(n, dtype=np.int32).reshape(-1, 3)
         self.lo = np.ascontiguousarray(lo, dtype=np.int64).reshape(-1, 3)
         self.np = self.n.shape[0]
+        self.level = (np.zeros(self.np, dtype=np.int32) if level is None
+                      else np.ascontiguousarray(level, dtype=np.int32).reshape(-1))
         bl = _f64(box_len)
         bc = np.ascontiguousarray(base_cells, dtype=np.int32)
-        h = L.orc_create(self.np, _ptr(self.n), _ptr(self.lo), gamma, cfl, t0, dt_max, _ptr(bl),
-                         _ptr(bc), nguard, nslices, time_mode, dispatcher)
+        h = L.orc_create(self.np, _ptr(self.n), _ptr(self.lo), _ptr(self.level), gamma, cfl, t0, dt_max,
+                         _ptr(bl), _ptr(bc), nguard, nslices, time_mode, dispatcher)
         if not h:
             raise ValueError("oracle rejected the layout or parameters")
         self._h = h
@@ -198,6 +203,18 @@ class Oracle:
         sm = np.zeros(1)
         self._check(lib().orc_update_patch(self._h, ip, dt, _ptr(U), _ptr(bx), _ptr(by), _ptr(bz), _ptr(sm)))
         return U, bx, by, bz, float(sm[0])
+
+    def fill_padded(self, ip, nguard=3):
+        """The padded box of patch ip at its current time (guard depth
+        nguard): U (5, Nz, Ny, Nx), bx (Nz, Ny, Nx+1), by (Nz, Ny+1, Nx),
+        bz (Nz+1, Ny, Nx)."""
+        nx, ny, nz = (int(a) + 2 * nguard for a in self.n[ip])
+        U = np.zeros((5, nz, ny, nx))
+        bx = np.zeros((nz, ny, nx + 1))
+        by = np.zeros((nz, ny + 1, nx))
+        bz = np.zeros((nz + 1, ny, nx))
+        self._check(lib().orc_fill_padded(self._h, ip, _ptr(U), _ptr(bx), _ptr(by), _ptr(bz)))
+        return U, bx, by, bz
 
     def nbors(self, ip):
         buf = np.zeros(self.np + 1, np.int32)

@@ -26,13 +26,18 @@ class Layout:
     """Uniform Cartesian decomposition of a periodic box (DISPATCH I,
     Sec. 2.3, the 'cartesian' component)."""
     n: np.ndarray          # (npatch, 3) int32 cells per axis
-    lo: np.ndarray         # (npatch, 3) int64 first interior cell
+    lo: np.ndarray         # (npatch, 3) int64 first interior cell (in its level's index space)
     base_cells: tuple      # level-0 cells per axis (x, y, z)
     box_len: tuple         # box length per axis
+    level: np.ndarray = None   # (npatch,) int32 refinement level (0, or 1 at dx/2); None: all 0
 
     @property
     def npatch(self):
         return self.n.shape[0]
+
+    @property
+    def levels(self):
+        return np.zeros(self.npatch, np.int32) if self.level is None else np.asarray(self.level, np.int32)
 
     @property
     def dx(self):
@@ -90,6 +95,77 @@ def mixed_blocks(n_blocks, block=96, sizes=(16, 24, 32), probs=(0.105, 0.266, 0.
     lo = np.array(los, dtype=np.int64)
     n = np.array(ns, dtype=np.int32)
     return Layout(n=n, lo=lo, base_cells=(L, L, L), box_len=(L * dx,) * 3)
+
+
+def two_level(coarse: Layout, fine_lo, fine_cells, fine_patch=None, fine_n=None, fine_los=None):
+    """Two refinement levels (DISPATCH I, Sec. 3 A: patches of differing
+    resolution): the level-0 patches of `coarse` and level-1 patches (cell
+    size dx/2) tiling the box [fine_lo, fine_lo + fine_cells) given in
+    level-0 cells (so every level-1 patch covers whole level-0 cells).  The
+    level-1 tiling is either cubes of `fine_patch` cells or explicit
+    (fine_n, fine_los) in level-1 cells relative to the box's corner.
+    Level-0 patches come first, then level-1 patches (x fastest)."""
+    flo = np.broadcast_to(np.asarray(fine_lo, np.int64), (3,))
+    fc = np.broadcast_to(np.asarray(fine_cells, np.int64), (3,))
+    if fine_n is None:
+        m = int(fine_patch)
+        assert m % 2 == 0 and all((2 * c) % m == 0 for c in fc)
+        los = []
+        for kz in range(2 * fc[2] // m):
+            for ky in range(2 * fc[1] // m):
+                for kx in range(2 * fc[0] // m):
+                    los.append((kx * m, ky * m, kz * m))
+        fine_los = np.array(los, np.int64)
+        fine_n = np.full((len(los), 3), m, np.int32)
+    fine_los = np.asarray(fine_los, np.int64).reshape(-1, 3) + 2 * flo
+    fine_n = np.asarray(fine_n, np.int32).reshape(-1, 3)
+    n = np.concatenate([coarse.n, fine_n]).astype(np.int32)
+    lo = np.concatenate([coarse.lo, fine_los]).astype(np.int64)
+    level = np.concatenate([coarse.levels, np.ones(len(fine_n), np.int32)])
+    return Layout(n=n, lo=lo, base_cells=coarse.base_cells, box_len=coarse.box_len, level=level)
+
+
+def patches_from_functions(layout: Layout, rho, vel, p, gamma, faces=None, potential=None, dtype=np.float64):
+    """Interior-only patch arrays from functions of position, each patch
+    sampled on its own level's grid (cell size dx / 2**level): rho(x, y, z),
+    vel(x, y, z) -> (vx, vy, vz), p(x, y, z) at cell centres; face fields
+    either from `faces` = (bx, by, bz) functions at face centres, or from an
+    edge vector potential `potential` = (Ax, Ay, Az) by the discrete curl
+    (zero divergence per cell to round-off)."""
+    dx0 = layout.dx
+    Us, bxs, bys, bzs = [], [], [], []
+    for (nx, ny, nz), lo, lev in zip(layout.n, layout.lo, layout.levels):
+        h = dx0 / 2 ** int(lev)
+        ci = [(lo[d] + np.arange(m) + 0.5) * h for d, m in enumerate((nx, ny, nz))]
+        fi = [(lo[d] + np.arange(m + 1)) * h for d, m in enumerate((nx, ny, nz))]
+        Z, Y, X = np.meshgrid(ci[2], ci[1], ci[0], indexing="ij")
+        r = np.broadcast_to(rho(X, Y, Z), X.shape)
+        v = [np.broadcast_to(c, X.shape) for c in vel(X, Y, Z)]
+        pr = np.broadcast_to(p(X, Y, Z), X.shape)
+        if faces is not None:
+            g = lambda a, b, c: np.meshgrid(c, b, a, indexing="ij")[::-1]
+            bx = np.broadcast_to(faces[0](*g(fi[0], ci[1], ci[2])), (nz, ny, nx + 1))
+            by = np.broadcast_to(faces[1](*g(ci[0], fi[1], ci[2])), (nz, ny + 1, nx))
+            bz = np.broadcast_to(faces[2](*g(ci[0], ci[1], fi[2])), (nz + 1, ny, nx))
+        else:
+            Ax, Ay, Az = potential
+            g = lambda a, b, c: np.meshgrid(c, b, a, indexing="ij")[::-1]
+            # x-faces: (Az(y+) - Az(y-)) - (Ay(z+) - Ay(z-)), over h
+            bx = ((Az(*g(fi[0], fi[1][1:], ci[2])) - Az(*g(fi[0], fi[1][:-1], ci[2])))
+                  - (Ay(*g(fi[0], ci[1], fi[2][1:])) - Ay(*g(fi[0], ci[1], fi[2][:-1])))) / h
+            by = ((Ax(*g(ci[0], fi[1], fi[2][1:])) - Ax(*g(ci[0], fi[1], fi[2][:-1])))
+                  - (Az(*g(fi[0][1:], fi[1], ci[2])) - Az(*g(fi[0][:-1], fi[1], ci[2])))) / h
+            bz = ((Ay(*g(fi[0][1:], ci[1], fi[2])) - Ay(*g(fi[0][:-1], ci[1], fi[2])))
+                  - (Ax(*g(ci[0], fi[1][1:], fi[2])) - Ax(*g(ci[0], fi[1][:-1], fi[2])))) / h
+        Bc = (0.5 * (bx[:, :, :-1] + bx[:, :, 1:]), 0.5 * (by[:, :-1] + by[:, 1:]), 0.5 * (bz[:-1] + bz[1:]))
+        v2 = v[0] ** 2 + v[1] ** 2 + v[2] ** 2
+        E = pr / (gamma - 1.0) + 0.5 * r * v2 + 0.5 * (Bc[0] ** 2 + Bc[1] ** 2 + Bc[2] ** 2)
+        Us.append(np.stack([r, r * v[0], r * v[1], r * v[2], E]).ravel())
+        bxs.append(np.ascontiguousarray(bx).ravel())
+        bys.append(np.ascontiguousarray(by).ravel())
+        bzs.append(np.ascontiguousarray(bz).ravel())
+    cat = lambda a: np.concatenate(a).astype(dtype)
+    return cat(Us), cat(bxs), cat(bys), cat(bzs)
 
 
 @dataclass
