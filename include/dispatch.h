@@ -56,8 +56,18 @@ typedef struct dsp_ctx dsp_ctx;
 
 /* One patch (Sec. 2.1, the patch data type): its refinement level, its
  * interior cells per axis (x, y, z) and the index of its first interior cell
- * in the level's cell index space.  All patches of one context must have the
- * same n, with n > nguard on every axis, and must tile the periodic box. */
+ * in the level's cell index space (level l has base_cells * 2^l cells per
+ * axis, cell size dx / 2^l).  Every patch has n > nguard on every axis.
+ * Level-0 patches (sizes may differ) must tile the periodic box exactly.
+ * Level-1 patches are optional: disjoint, each covering whole level-0 cells
+ * (even lo and n).  Guard values across the resolution jump follow Sec. 3 A
+ * (interpolation in space as well as in time): a level-1 guard cell that no
+ * level-1 patch owns is its level-0 parent plus a quarter of the parent's
+ * MC-limited slopes signed by the child's side; a level-1 guard face is the
+ * level-0 face it lies on, or the mean of the parent's two faces along its
+ * axis; a level-0 guard cell covered by level 1 is the mean of its 8
+ * children, a face the mean of the 4 level-1 faces on it.  Level-0 patches
+ * under the refined region are still advanced. */
 typedef struct {
   int32_t level;
   int32_t n[3];
@@ -139,7 +149,12 @@ typedef struct {
 /* Create a context: validates the layout, builds the neighbour tables,
  * allocates every slice on the current CUDA device.  stream is a
  * cudaStream_t (NULL = legacy default stream).  On success *out owns all
- * device memory until dsp_destroy. */
+ * device memory until dsp_destroy.  Neighbours are symmetric: on the same
+ * level, patches whose interior meets the padded box; across levels,
+ * patches whose interior meets the cells a patch may read on the other
+ * level.  Returns DSP_ERR_INVALID_ARG for a layout that breaks the rules of
+ * dsp_patch_desc, DSP_ERR_UNSUPPORTED for levels other than 0 and 1, for two
+ * levels with the ready-queue dispatcher, or for grace != 0. */
 DSP_API int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const dsp_params *params, void *stream,
                dsp_ctx **out);
 

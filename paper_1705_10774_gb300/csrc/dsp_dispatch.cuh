@@ -43,7 +43,8 @@ __device__ __forceinline__ double slot_smax(const DevCtx &c, long long i) {
 
 // Local Courant step of patch P at time t (all FP64): the signal speed is the
 // largest over P's newest slice and every neighbour slice its guard fill
-// reads; the step is the power of two not above C dx / s, capped by dt_max,
+// reads; the step is the power of two not above C dx / s (dx of P's level),
+// capped by dt_max,
 // halved until it divides t, and clipped to t_end.
 template <bool CONC>
 __device__ int patch_dt(const DevCtx &c, int P, double t, double t_end, double *out) {
@@ -68,7 +69,7 @@ __device__ int patch_dt(const DevCtx &c, int P, double t, double t_end, double *
       }
     }
   }
-  const double dtc = c.cfl * c.dx / M;
+  const double dtc = c.cfl * ldexp(c.dx, -c.geo[P].level) / M;
   int e;
   frexp(dtc, &e);
   double dt = ldexp(1.0, e - 1);

@@ -25,6 +25,7 @@
 
 #include "dsp_dispatch.cuh"
 #include "dsp_internal.h"
+#include "dsp_levels.cuh"
 #include "dsp_physics.cuh"
 
 using namespace dsp;
@@ -44,7 +45,9 @@ struct dsp_ctx {
   // device allocations
   void *slab;
   double *t_slot, *smax_slot, *dt_last, *dtR;
-  int *latest, *nbl_off_d, *nbl_d, *R, *ctl, *map_d, *work_off_d;
+  int *latest, *nbl_off_d, *nbl_d, *R, *ctl, *omap_d[2], *gmap0_d, *work_off_d;
+  long long *gofs_d;
+  void *gbuf;
   PatchGeo *geo_d;
   long long *coff_d;
   unsigned long long *smax_new;
@@ -64,6 +67,7 @@ struct dsp_ctx {
   int graph_timing;
   int own_stream;  // the context created its stream (graph capture needs one)
   const KernelVariant *var;  // the update-kernel variant in use
+  int n_xlevel;              // patches with a cross-level guard buffer
   std::vector<dsp_patch_desc> patches;
 };
 
@@ -360,7 +364,8 @@ __global__ void diag_kernel(DevCtx c, double *out) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const long long nc = (long long)nx * ny * nz;
   const T *bxa = base + 5 * nc, *bya = bxa + (long long)(nx + 1) * ny * nz, *bza = bya + (long long)nx * (ny + 1) * nz;
-  const double dV = c.dx * c.dx * c.dx;
+  const double dxl = ldexp(c.dx, -g.level);
+  const double dV = dxl * dxl * dxl;
   (void)nz;
   NSum acc[8];
   for (int q = 0; q < 8; q++) acc[q].s = acc[q].c = 0.0;
@@ -407,6 +412,16 @@ int launch_queue(dsp_ctx *c, double t_end) { return c->var->launch_queue(c->d, c
 
 int launch_update(dsp_ctx *c) { return c->var->launch_update(c->d, c->grid_update, c->stream); }
 
+// Cross-level guard values of the ready patches that have some (two levels
+// only), after the plan kernel and before the update kernel of a sweep.
+int launch_xlevel(dsp_ctx *c) {
+  if (c->d.nlev < 2) return DSP_OK;
+  const int grid = std::max(1, std::min(c->n_xlevel, 4096));
+  if (c->precision == 1) xlevel_kernel<float><<<grid, 256, 0, c->stream>>>(c->d);
+  else xlevel_kernel<double><<<grid, 256, 0, c->stream>>>(c->d);
+  return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
+}
+
 #define DSP_VARIANT_ENTRY(id, T, TX, TY, NT, MB, PREC) variant_##id,
 const KernelVariant *(*const kVariants[])() = {DSP_VARIANT_LIST(DSP_VARIANT_ENTRY)};
 #undef DSP_VARIANT_ENTRY
@@ -414,7 +429,7 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 // Per-patch tiles and offsets for the variant's tile shape; false if some
 // tile's owner table would not fit the kernel's table.
-bool make_geometry(const std::vector<dsp_patch_desc> &patches, int TX, int TY, int tz, const int bsz[3],
+bool make_geometry(const std::vector<dsp_patch_desc> &patches, int TX, int TY, int tz, const int bszl[2][3],
                    std::vector<PatchGeo> &geo, long long &off, long long &total_tiles, int &uniform_tiles) {
   const int npatch = (int)patches.size();
   geo.assign((size_t)npatch, PatchGeo());
@@ -429,6 +444,8 @@ bool make_geometry(const std::vector<dsp_patch_desc> &patches, int TX, int TY, i
       g.n[d] = patches[(size_t)i].n[d];
       g.lo[d] = (int)patches[(size_t)i].lo[d];
     }
+    g.level = patches[(size_t)i].level;
+    const int *bsz = bszl[g.level];
     g.nt[0] = (g.n[0] + TX - 1) / TX;
     g.nt[1] = (g.n[1] + TY - 1) / TY;
     g.nt[2] = (g.n[2] + tz - 1) / tz;
@@ -520,7 +537,8 @@ int transfer(dsp_ctx *c, int first, int count, const void *U, const void *bx, co
 }
 
 void free_all(dsp_ctx *c) {
-  void *ptrs[] = {c->slab,    c->t_slot,  c->smax_slot, c->dt_last, c->dtR,     c->latest,  c->map_d,
+  void *ptrs[] = {c->slab,    c->t_slot,  c->smax_slot, c->dt_last, c->dtR,     c->latest,  c->omap_d[0],
+                  c->omap_d[1], c->gmap0_d, c->gofs_d, c->gbuf,
                   c->work_off_d, c->geo_d, c->coff_d,
                   c->nbl_off_d, c->nbl_d, c->R,       c->ctl,     c->smax_new, c->cnt,    c->sched,
                   c->staging, c->q_patch, c->q_reads, c->p_state, c->tiles_done, c->q_dt, c->q_seq,
@@ -550,12 +568,13 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   const double dx = prm->box_len[0] / prm->base_cells[0];
   for (int d = 1; d < 3; d++)
     if (std::fabs(prm->box_len[d] / prm->base_cells[d] - dx) > 1e-12 * dx) return DSP_ERR_INVALID_ARG;
-  // Geometry: every patch on level 0, wider than its guard depth, inside the
-  // box; together they must tile the periodic box exactly.  The level map
-  // uses blocks of bsz cells, bsz = gcd of the box, every patch size and
-  // every patch origin per axis.
-  int bsz[3];
-  for (int d = 0; d < 3; d++) bsz[d] = prm->base_cells[d];
+  // Geometry.  Level 0: patches wider than their guard depth that tile the
+  // periodic box exactly.  Level 1 (optional, half the cell size): disjoint
+  // patches inside the level-1 box, each covering whole level-0 cells (even
+  // origin and size).  The map of level l cuts its box into blocks of
+  // bsz[l] cells: the gcd of the box and every patch size and origin of that
+  // level; level 0's is reduced further until every block is either wholly
+  // covered by level 1 or not at all.
   auto gcd = [](long long a, long long b) {
     while (b) {
       const long long t = a % b;
@@ -564,35 +583,100 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
     }
     return a;
   };
+  int nlev = 1;
+  long long Lv[2][3];
+  int bsz[2][3];
+  for (int d = 0; d < 3; d++) {
+    Lv[0][d] = prm->base_cells[d];
+    Lv[1][d] = 2ll * prm->base_cells[d];
+    bsz[0][d] = prm->base_cells[d];
+    bsz[1][d] = 2 * prm->base_cells[d];
+  }
   for (int i = 0; i < npatch; i++) {
     const dsp_patch_desc &p = patches[i];
-    if (p.level != 0) return DSP_ERR_UNSUPPORTED;
+    if (p.level < 0 || p.level > 1) return DSP_ERR_UNSUPPORTED;
+    if (p.level == 1) nlev = 2;
     for (int d = 0; d < 3; d++) {
-      if (p.n[d] <= prm->nguard || p.lo[d] < 0 || p.lo[d] + p.n[d] > prm->base_cells[d]) return DSP_ERR_INVALID_ARG;
-      bsz[d] = (int)gcd(bsz[d], gcd(p.n[d], p.lo[d]));
+      if (p.n[d] <= prm->nguard || p.lo[d] < 0 || p.lo[d] + p.n[d] > Lv[p.level][d]) return DSP_ERR_INVALID_ARG;
+      if (p.level == 1 && ((p.n[d] & 1) || (p.lo[d] & 1))) return DSP_ERR_INVALID_ARG;
+      bsz[p.level][d] = (int)gcd(bsz[p.level][d], gcd(p.n[d], p.lo[d]));
     }
   }
-  int mapd[3];
-  for (int d = 0; d < 3; d++) {
-    mapd[d] = prm->base_cells[d] / bsz[d];
-    // the kernels divide level coordinates by bsz through a float product
-    if (prm->base_cells[d] + 8 > (1 << 20) / std::max(bsz[d], 1)) return DSP_ERR_UNSUPPORTED;
+  for (int pass = 0; nlev == 2; pass++) {
+    // level-1 cells over each level-0 block (level-1 patches are disjoint)
+    int md[3];
+    long long nb = 1;
+    for (int d = 0; d < 3; d++) {
+      md[d] = (int)(Lv[0][d] / bsz[0][d]);
+      nb *= md[d];
+    }
+    if (nb > (1ll << 28)) return DSP_ERR_UNSUPPORTED;
+    std::vector<long long> cov((size_t)nb, 0);
+    for (int i = 0; i < npatch; i++) {
+      const dsp_patch_desc &p = patches[i];
+      if (p.level != 1) continue;
+      long long a[3], b[3];
+      for (int d = 0; d < 3; d++) {
+        a[d] = p.lo[d] / 2;
+        b[d] = (p.lo[d] + p.n[d]) / 2;
+      }
+      for (long long bz = a[2] / bsz[0][2]; bz <= (b[2] - 1) / bsz[0][2]; bz++)
+        for (long long by = a[1] / bsz[0][1]; by <= (b[1] - 1) / bsz[0][1]; by++)
+          for (long long bx = a[0] / bsz[0][0]; bx <= (b[0] - 1) / bsz[0][0]; bx++) {
+            const long long bb[3] = {bx, by, bz};
+            long long v = 1;
+            for (int d = 0; d < 3; d++)
+              v *= std::min(b[d], (bb[d] + 1) * bsz[0][d]) - std::max(a[d], bb[d] * bsz[0][d]);
+            cov[(size_t)((bz * md[1] + by) * md[0] + bx)] += v;
+          }
+    }
+    const long long full = (long long)bsz[0][0] * bsz[0][1] * bsz[0][2];
+    bool partial = false;
+    for (long long k = 0; k < nb && !partial; k++)
+      if (cov[(size_t)k] != 0 && cov[(size_t)k] != full) partial = true;
+    if (!partial) break;
+    if (bsz[0][0] == 1 && bsz[0][1] == 1 && bsz[0][2] == 1) return DSP_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; d++) bsz[0][d] = bsz[0][d] % 2 == 0 ? bsz[0][d] / 2 : 1;
   }
-  const long long nmap = (long long)mapd[0] * mapd[1] * mapd[2];
-  if (nmap > (1ll << 28)) return DSP_ERR_UNSUPPORTED;
-  std::vector<int> map((size_t)nmap, -1);
+  if (nlev == 2 && prm->dispatcher == 0) return DSP_ERR_UNSUPPORTED;  // the ready queue runs one level
+  int mapd[2][3];
+  long long nmap[2] = {1, 1};
+  std::vector<int> omap[2], gmap0;
+  for (int l = 0; l < nlev; l++) {
+    for (int d = 0; d < 3; d++) {
+      mapd[l][d] = (int)(Lv[l][d] / bsz[l][d]);
+      // the kernels divide level coordinates by bsz through a float product
+      if (Lv[l][d] + 8 > (1 << 20) / std::max(bsz[l][d], 1)) return DSP_ERR_UNSUPPORTED;
+      nmap[l] *= mapd[l][d];
+    }
+    if (nmap[l] > (1ll << 28)) return DSP_ERR_UNSUPPORTED;
+    omap[l].assign((size_t)nmap[l], -1);
+  }
   for (int i = 0; i < npatch; i++) {
     const dsp_patch_desc &p = patches[i];
-    for (long long bz = p.lo[2] / bsz[2]; bz < (p.lo[2] + p.n[2]) / bsz[2]; bz++)
-      for (long long by = p.lo[1] / bsz[1]; by < (p.lo[1] + p.n[1]) / bsz[1]; by++)
-        for (long long bx = p.lo[0] / bsz[0]; bx < (p.lo[0] + p.n[0]) / bsz[0]; bx++) {
-          int &m = map[(size_t)((bz * mapd[1] + by) * mapd[0] + bx)];
+    const int l = p.level;
+    const int *bs = bsz[l], *md = mapd[l];
+    for (long long bz = p.lo[2] / bs[2]; bz < (p.lo[2] + p.n[2]) / bs[2]; bz++)
+      for (long long by = p.lo[1] / bs[1]; by < (p.lo[1] + p.n[1]) / bs[1]; by++)
+        for (long long bx = p.lo[0] / bs[0]; bx < (p.lo[0] + p.n[0]) / bs[0]; bx++) {
+          int &m = omap[l][(size_t)((bz * md[1] + by) * md[0] + bx)];
           if (m >= 0) return DSP_ERR_INVALID_ARG;  // overlap
           m = i;
         }
   }
-  for (long long k = 0; k < nmap; k++)
-    if (map[(size_t)k] < 0) return DSP_ERR_INVALID_ARG;  // not a tiling
+  for (long long k = 0; k < nmap[0]; k++)
+    if (omap[0][(size_t)k] < 0) return DSP_ERR_INVALID_ARG;  // level 0 is not a tiling
+  // the gather map of level 0: blocks covered by level 1 come from there
+  gmap0 = omap[0];
+  for (int i = 0; i < npatch; i++) {
+    const dsp_patch_desc &p = patches[i];
+    if (p.level != 1) continue;
+    // every block a level-1 patch touches is wholly covered (see above)
+    for (long long bz = p.lo[2] / 2 / bsz[0][2]; bz <= ((p.lo[2] + p.n[2]) / 2 - 1) / bsz[0][2]; bz++)
+      for (long long by = p.lo[1] / 2 / bsz[0][1]; by <= ((p.lo[1] + p.n[1]) / 2 - 1) / bsz[0][1]; by++)
+        for (long long bx = p.lo[0] / 2 / bsz[0][0]; bx <= ((p.lo[0] + p.n[0]) / 2 - 1) / bsz[0][0]; bx++)
+          gmap0[(size_t)((bz * mapd[0][1] + by) * mapd[0][0] + bx)] = -1;
+  }
   // the update-kernel variant: the requested one, else the first of this precision
   const KernelVariant *var = nullptr;
   for (int k = 0; k < kNumVariants; k++) {
@@ -632,6 +716,7 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   c->geo = geo;
   c->var = var;
   c->patches = pvec;
+  c->n_xlevel = 0;
   DevCtx &d = c->d;
   d.np = npatch;
   d.ns = prm->nslices;
@@ -639,46 +724,106 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.uniform_tiles = uniform_tiles;
   d.total_tiles = total_tiles;
   d.slot_stride = off;
-  for (int k = 0; k < 3; k++) {
-    d.bsz[k] = bsz[k];
-    d.mapd[k] = mapd[k];
-    d.L[k] = prm->base_cells[k];
-    d.binv[k] = 1.0f / (float)bsz[k];
-  }
+  d.nlev = nlev;
+  for (int l = 0; l < 2; l++)
+    for (int k = 0; k < 3; k++) {
+      d.bsz[l][k] = bsz[l][k];
+      d.mapd[l][k] = l < nlev ? mapd[l][k] : 1;
+      d.L[l][k] = (int)Lv[l][k];
+      d.binv[l][k] = 1.0f / (float)bsz[l][k];
+    }
   d.gamma = prm->gamma;
   d.cfl = prm->cfl;
   d.dx = dx;
   d.dt_max = prm->dt_max;
-  // neighbours: every patch owning a block of the padded box (periodic
-  // images), the patch itself excluded
-  c->nbl_off.assign((size_t)npatch + 1, 0);
+  // Neighbours (symmetric).  Same level: every patch owning a block of the
+  // padded box (periodic images), the patch itself excluded.  Other level:
+  // every patch owning a block of the cells this patch may read there -- a
+  // level-1 patch reads the level-0 parents of its padded cells and one
+  // more level-0 cell on each side (limited slopes); a level-0 patch reads
+  // the level-1 children of its padded cells and of the cell above its top
+  // guard face -- and every patch that may read this one.
+  const int g = prm->nguard;
+  auto fdivl = [](long long a, long long b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+  std::vector<std::vector<int>> nbs((size_t)npatch);
   {
     std::vector<int> seen((size_t)npatch, -1);
-    const int g = prm->nguard;
     for (int i = 0; i < npatch; i++) {
       const dsp_patch_desc &p = patches[i];
-      std::vector<int> uniq;
+      for (int l = 0; l < nlev; l++) {
+        long long a[3], b[3];  // half-open cell interval on level l
+        for (int k = 0; k < 3; k++) {
+          if (l == p.level) {
+            a[k] = p.lo[k] - g;
+            b[k] = p.lo[k] + p.n[k] + g;
+          } else if (p.level == 1) {
+            a[k] = fdivl(p.lo[k] - g, 2) - 1;
+            b[k] = fdivl(p.lo[k] + p.n[k] + g - 1, 2) + 2;
+          } else {
+            a[k] = 2 * (p.lo[k] - g);
+            b[k] = 2 * (p.lo[k] + p.n[k] + g) + 2;
+          }
+        }
+        long long b0[3], b1[3];
+        for (int k = 0; k < 3; k++) {
+          b0[k] = fdivl(a[k], bsz[l][k]);
+          b1[k] = fdivl(b[k] - 1, bsz[l][k]);
+        }
+        for (long long bz = b0[2]; bz <= b1[2]; bz++)
+          for (long long by = b0[1]; by <= b1[1]; by++)
+            for (long long bx = b0[0]; bx <= b1[0]; bx++) {
+              const long long wx = ((bx % mapd[l][0]) + mapd[l][0]) % mapd[l][0];
+              const long long wy = ((by % mapd[l][1]) + mapd[l][1]) % mapd[l][1];
+              const long long wz = ((bz % mapd[l][2]) + mapd[l][2]) % mapd[l][2];
+              const int q = omap[l][(size_t)((wz * mapd[l][1] + wy) * mapd[l][0] + wx)];
+              if (q >= 0 && q != i && seen[(size_t)q] != i) {
+                seen[(size_t)q] = i;
+                nbs[(size_t)i].push_back(q);
+              }
+            }
+      }
+    }
+    for (int i = 0; i < npatch; i++)
+      for (int q : std::vector<int>(nbs[(size_t)i]))
+        if (patches[q].level != patches[i].level) nbs[(size_t)q].push_back(i);
+  }
+  c->nbl_off.assign((size_t)npatch + 1, 0);
+  for (int i = 0; i < npatch; i++) {
+    std::vector<int> &u = nbs[(size_t)i];
+    std::sort(u.begin(), u.end());
+    u.erase(std::unique(u.begin(), u.end()), u.end());
+    c->nbl_off[i + 1] = c->nbl_off[i] + (int)u.size();
+    c->nbl.insert(c->nbl.end(), u.begin(), u.end());
+  }
+  // cross-level guard buffers: every patch whose radius-2 padded box (and
+  // the cells above its top faces) meets a block its gather takes from the
+  // other level
+  std::vector<long long> gofs((size_t)npatch, -1);
+  long long gtotal = 0;
+  if (nlev == 2) {
+    for (int i = 0; i < npatch; i++) {
+      const dsp_patch_desc &p = patches[i];
+      const int l = p.level;
+      const std::vector<int> &gm = l == 0 ? gmap0 : omap[1];
       long long b0[3], b1[3];
       for (int k = 0; k < 3; k++) {
-        const long long a = p.lo[k] - g, b = p.lo[k] + p.n[k] + g - 1;
-        b0[k] = a >= 0 ? a / bsz[k] : -((-a + bsz[k] - 1) / bsz[k]);
-        b1[k] = b / bsz[k];
+        b0[k] = fdivl(p.lo[k] - 2, bsz[l][k]);
+        b1[k] = fdivl(p.lo[k] + p.n[k] + 2, bsz[l][k]);
       }
-      for (long long bz = b0[2]; bz <= b1[2]; bz++)
-        for (long long by = b0[1]; by <= b1[1]; by++)
-          for (long long bx = b0[0]; bx <= b1[0]; bx++) {
-            const long long wx = ((bx % mapd[0]) + mapd[0]) % mapd[0];
-            const long long wy = ((by % mapd[1]) + mapd[1]) % mapd[1];
-            const long long wz = ((bz % mapd[2]) + mapd[2]) % mapd[2];
-            const int q = map[(size_t)((wz * mapd[1] + wy) * mapd[0] + wx)];
-            if (q != i && seen[(size_t)q] != i) {
-              seen[(size_t)q] = i;
-              uniq.push_back(q);
-            }
+      bool need = false;
+      for (long long bz = b0[2]; bz <= b1[2] && !need; bz++)
+        for (long long by = b0[1]; by <= b1[1] && !need; by++)
+          for (long long bx = b0[0]; bx <= b1[0] && !need; bx++) {
+            const long long wx = ((bx % mapd[l][0]) + mapd[l][0]) % mapd[l][0];
+            const long long wy = ((by % mapd[l][1]) + mapd[l][1]) % mapd[l][1];
+            const long long wz = ((bz % mapd[l][2]) + mapd[l][2]) % mapd[l][2];
+            if (gm[(size_t)((wz * mapd[l][1] + wy) * mapd[l][0] + wx)] < 0) need = true;
           }
-      std::sort(uniq.begin(), uniq.end());
-      c->nbl_off[i + 1] = c->nbl_off[i] + (int)uniq.size();
-      c->nbl.insert(c->nbl.end(), uniq.begin(), uniq.end());
+      if (!need) continue;
+      const long long m0 = p.n[0] + 4, m1 = p.n[1] + 4, m2 = p.n[2] + 4;
+      gofs[(size_t)i] = gtotal;
+      c->n_xlevel++;
+      gtotal += 5 * m0 * m1 * m2 + (m0 + 1) * m1 * m2 + m0 * (m1 + 1) * m2 + m0 * m1 * (m2 + 1);
     }
   }
   // offsets of each patch in the caller's four arrays
@@ -699,7 +844,11 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   bool ok = alloc(&c->slab, slab_bytes) && alloc((void **)&c->t_slot, sizeof(double) * npatch * d.ns) &&
             alloc((void **)&c->smax_slot, sizeof(double) * npatch * d.ns) &&
             alloc((void **)&c->dt_last, sizeof(double) * npatch) && alloc((void **)&c->dtR, sizeof(double) * npatch) &&
-            alloc((void **)&c->latest, sizeof(int) * npatch) && alloc((void **)&c->map_d, sizeof(int) * nmap) &&
+            alloc((void **)&c->latest, sizeof(int) * npatch) && alloc((void **)&c->omap_d[0], sizeof(int) * nmap[0]) &&
+            (nlev < 2 || alloc((void **)&c->omap_d[1], sizeof(int) * nmap[1])) &&
+            (nlev < 2 || alloc((void **)&c->gmap0_d, sizeof(int) * nmap[0])) &&
+            alloc((void **)&c->gofs_d, sizeof(long long) * npatch) &&
+            (gtotal == 0 || alloc(&c->gbuf, c->esize * (size_t)gtotal)) &&
             alloc((void **)&c->geo_d, sizeof(PatchGeo) * npatch) &&
             alloc((void **)&c->coff_d, sizeof(long long) * c->coff.size()) &&
             alloc((void **)&c->work_off_d, sizeof(int) * (npatch + 1)) &&
@@ -731,7 +880,12 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.latest = c->latest;
   d.dt_last = c->dt_last;
   d.geo = c->geo_d;
-  d.map = c->map_d;
+  d.omap[0] = c->omap_d[0];
+  d.omap[1] = nlev == 2 ? c->omap_d[1] : c->omap_d[0];
+  d.gmap[0] = nlev == 2 ? c->gmap0_d : c->omap_d[0];
+  d.gmap[1] = d.omap[1];
+  d.gofs = c->gofs_d;
+  d.gbuf = c->gbuf;
   d.coff = c->coff_d;
   d.work_off = c->work_off_d;
   d.nbl_off = c->nbl_off_d;
@@ -752,7 +906,14 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.p_state = c->p_state;
   d.tiles_done = c->tiles_done;
   d.wait_budget = prm->wait_budget > 0 ? prm->wait_budget : 4000000000ll;  // ~2 s of SM clock
-  cudaError_t e = cudaMemcpyAsync(c->map_d, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, c->stream);
+  cudaError_t e = cudaMemcpyAsync(c->omap_d[0], omap[0].data(), sizeof(int) * omap[0].size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && nlev == 2)
+    e = cudaMemcpyAsync(c->omap_d[1], omap[1].data(), sizeof(int) * omap[1].size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && nlev == 2)
+    e = cudaMemcpyAsync(c->gmap0_d, gmap0.data(), sizeof(int) * gmap0.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->gofs_d, gofs.data(), sizeof(long long) * gofs.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && gtotal > 0) e = cudaMemsetAsync(c->gbuf, 0, c->esize * (size_t)gtotal, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->geo_d, geo.data(), sizeof(PatchGeo) * geo.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
@@ -884,6 +1045,7 @@ extern "C" int dsp_advance(dsp_ctx *c, double t_end, int64_t max_sweeps, dsp_sta
     for (long long s = 0; s < nb; s++) {
       plan_kernel<<<1, PLAN_NT, 0, c->stream>>>(c->d, t_end, global_mode, 0);
       CK(cudaGetLastError());
+      if (launch_xlevel(c)) return fail(c, DSP_ERR_CUDA, "cross-level guard kernel launch failed");
       if (events) CK(cudaEventRecord(c->ev[2 * s], c->stream));
       const int r2 = launch_update(c);
       if (r2) return fail(c, r2, "update kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1158,6 +1320,8 @@ extern "C" int dsp_autotune(dsp_ctx *c, int32_t reps, int32_t *chosen, double *m
     CK(cudaMemsetAsync(c->ctl + CTL_NREADY, 0, sizeof(int), c->stream));
     plan_kernel<<<1, PLAN_NT, 0, c->stream>>>(c->d, INFINITY, c->prm.time_mode == 0, 0);
     CK(cudaGetLastError());
+    rc = launch_xlevel(c);
+    if (rc) break;
     rc = launch_update(c);
     if (rc) break;
     CK(cudaEventRecord(e0, c->stream));

@@ -36,6 +36,7 @@ struct PatchGeo {
   int nt[3];      // update tiles per axis
   int tiles;      // nt[0] * nt[1] * nt[2]
   int lo[3];      // first interior cell in the level's index space
+  int level;      // refinement level (0, or 1 at half the cell size)
   long long off;  // offset of the patch inside a slice
 };
 
@@ -50,10 +51,21 @@ struct DevCtx {
   long long total_tiles;   // tiles of all patches
   long long slot_stride;   // elements of one slice of all patches
   const PatchGeo *geo;     // [np]
-  // level map: blocks of bsz cells tiling the periodic box; map[] = patch
-  const int *map;
-  int bsz[3], mapd[3], L[3];
-  float binv[3];
+  // per level l: the periodic box of L[l] cells per axis cut into blocks of
+  // bsz[l] cells.  omap[l][block] = the level-l patch owning the block, or -1
+  // (level 1 outside the refined region).  gmap[l] is what a level-l patch's
+  // guard gather uses: omap[l] except -1 wherever the value comes from the
+  // other level (level 0: blocks covered by level 1; level 1: uncovered).
+  int nlev;
+  const int *omap[2];
+  const int *gmap[2];
+  int bsz[2][3], mapd[2][3], L[2][3];
+  float binv[2][3];
+  // cross-level guard values of each patch that has some (-1 otherwise):
+  // a padded box of n + 4 cells per axis starting at lo - 2, laid out like a
+  // patch slice, refilled before every update of the patch
+  void *gbuf;
+  const long long *gofs;   // [np] element offset into gbuf, or -1
   const long long *coff;   // [4][np+1] offsets of each patch in the caller's U, bx, by, bz arrays
   int *work_off;           // [np+1] first work item of each ready patch (prefix of tiles)
   double gamma, cfl, dx, dt_max;

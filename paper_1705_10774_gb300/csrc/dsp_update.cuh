@@ -138,8 +138,10 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
 #define H1(i, j) (((j) + 1) * (TX + 2) + ((i) + 1))
 #define F5(i, j) (((j) + 2) * (TX + 5) + ((i) + 2))
 
-  const T hdt = (T)(0.5 * dt / c.dx);
-  const T dtdx = (T)(dt / c.dx);
+  const int lev = gp.level;
+  const double dxl = ldexp(c.dx, -lev);
+  const T hdt = (T)(0.5 * dt / dxl);
+  const T dtdx = (T)(dt / dxl);
   const int tix = tile % gp.nt[0], tiy = (tile / gp.nt[0]) % gp.nt[1], tiz = tile / (gp.nt[0] * gp.nt[1]);
   const int x0 = tix * TX, y0 = tiy * TY, z0 = tiz * c.tz;
   const int tx = min(TX, nx - x0), ty = min(TY, ny - y0), tz = min(c.tz, nz - z0);
@@ -148,23 +150,41 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
   const T *const own = (const T *)c.slab + (long long)Lp * c.slot_stride + gp.off;
   T *const dst = (T *)c.slab + (long long)((Lp + 1) % c.ns) * c.slot_stride + gp.off;
 
-  // Owner table of the padded tile: every map block that cells in
-  // [x0-2, x0+tx+2] x [y0-2, y0+ty+2] x [z0-2, z0+tz+2] fall in, with the
-  // slices of its owning patch that supply time tP (a slice at exactly tP is
-  // copied, else the newest two are interpolated).
-  const int bx0 = floordiv(lox + x0 - 2, c.bsz[0]), by0 = floordiv(loy + y0 - 2, c.bsz[1]),
-            bz0 = floordiv(loz + z0 - 2, c.bsz[2]);
-  const int nbx = floordiv(lox + x0 + tx + 2, c.bsz[0]) - bx0 + 1;
-  const int nby = floordiv(loy + y0 + ty + 2, c.bsz[1]) - by0 + 1;
-  const int nbz = floordiv(loz + z0 + tz + 2, c.bsz[2]) - bz0 + 1;
+  // Owner table of the padded tile: every block of the level's map that
+  // cells in [x0-2, x0+tx+2] x [y0-2, y0+ty+2] x [z0-2, z0+tz+2] fall in, with
+  // the slices of its owning patch that supply time tP (a slice at exactly tP
+  // is copied, else the newest two are interpolated).  A block whose values
+  // come from the other level points at the patch's cross-level guard
+  // buffer, filled for time tP just before this update.
+  const int *const gmap = c.gmap[lev];
+  const int *const bsz = c.bsz[lev];
+  const int *const mapd = c.mapd[lev];
+  const float *const binv = c.binv[lev];
+  const int bx0 = floordiv(lox + x0 - 2, bsz[0]), by0 = floordiv(loy + y0 - 2, bsz[1]),
+            bz0 = floordiv(loz + z0 - 2, bsz[2]);
+  const int nbx = floordiv(lox + x0 + tx + 2, bsz[0]) - bx0 + 1;
+  const int nby = floordiv(loy + y0 + ty + 2, bsz[1]) - by0 + 1;
+  const int nbz = floordiv(loz + z0 + tz + 2, bsz[2]) - bz0 + 1;
   for (int e = tid; e < nbx * nby * nbz; e += NT) {
     const int bx = bx0 + e % nbx, by = by0 + (e / nbx) % nby, bz = bz0 + e / (nbx * nby);
-    const int wx = posmod(bx, c.mapd[0]), wy = posmod(by, c.mapd[1]), wz = posmod(bz, c.mapd[2]);
-    const int Q = c.map[((long long)wz * c.mapd[1] + wy) * c.mapd[0] + wx];
+    const int wx = posmod(bx, mapd[0]), wy = posmod(by, mapd[1]), wz = posmod(bz, mapd[2]);
+    const int Q = gmap[((long long)wz * mapd[1] + wy) * mapd[0] + wx];
+    if (Q < 0) {
+      // the cross-level guard buffer: a patch of n+4 cells at lo-2, in P's
+      // own (unwrapped) coordinates
+      for (int d = 0; d < 3; d++) {
+        S.lo[d][e] = gp.lo[d] - 2;
+        S.n[d][e] = gp.n[d] + 4;
+      }
+      srcA[e] = (const T *)c.gbuf + c.gofs[P];
+      srcB[e] = nullptr;
+      wgt[e] = T(0);
+      continue;
+    }
     const PatchGeo &gq = c.geo[Q];
-    S.lo[0][e] = gq.lo[0] + (bx - wx) * c.bsz[0];
-    S.lo[1][e] = gq.lo[1] + (by - wy) * c.bsz[1];
-    S.lo[2][e] = gq.lo[2] + (bz - wz) * c.bsz[2];
+    S.lo[0][e] = gq.lo[0] + (bx - wx) * bsz[0];
+    S.lo[1][e] = gq.lo[1] + (by - wy) * bsz[1];
+    S.lo[2][e] = gq.lo[2] + (bz - wz) * bsz[2];
     S.n[0][e] = gq.n[0];
     S.n[1][e] = gq.n[1];
     S.n[2][e] = gq.n[2];
@@ -210,9 +230,9 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
   // a small integer quotient through a rounded-up float product: exact for
   // level extents far below 2^20 cells).
   auto entry = [&](int gx, int gy, int gz) -> int {
-    const int ex = __float2int_rd(((float)gx + 0.5f) * c.binv[0]) - bx0;
-    const int ey = __float2int_rd(((float)gy + 0.5f) * c.binv[1]) - by0;
-    const int ez = __float2int_rd(((float)gz + 0.5f) * c.binv[2]) - bz0;
+    const int ex = __float2int_rd(((float)gx + 0.5f) * binv[0]) - bx0;
+    const int ey = __float2int_rd(((float)gy + 0.5f) * binv[1]) - by0;
+    const int ez = __float2int_rd(((float)gz + 0.5f) * binv[2]) - bz0;
     return (ez * nby + ey) * nbx + ex;
   };
   // Cell-centred component q of patch-local cell (x,y,z) (radius <= 2

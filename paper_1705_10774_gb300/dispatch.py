@@ -130,18 +130,20 @@ def _addr(a):
 
 
 class Dispatch:
-    """A context of patches on one periodic level (one GPU)."""
+    """A context of patches on a periodic box (level 0, optionally a level 1
+    at half the cell size), on one GPU."""
 
     def __init__(self, n, lo, *, gamma, cfl, base_cells, box_len=(1.0, 1.0, 1.0), t0=0.0, dt_max=0.0,
                  nguard=3, nslices=3, precision=0, time_mode=0, dispatcher=1, tile_z=0,
-                 sched_capacity=0, timing=0, wait_budget=0, graph=0, variant=-1, stream=None):
+                 sched_capacity=0, timing=0, wait_budget=0, graph=0, variant=-1, stream=None, level=None):
         L = load()
         n = np.asarray(n, dtype=np.int64).reshape(-1, 3)
         lo = np.asarray(lo, dtype=np.int64).reshape(-1, 3)
         self.np = n.shape[0]
+        lev = np.zeros(self.np, np.int64) if level is None else np.asarray(level, np.int64).reshape(-1)
         descs = (dsp_patch_desc * self.np)()
         for i in range(self.np):
-            descs[i].level = 0
+            descs[i].level = int(lev[i])
             for d in range(3):
                 descs[i].n[d] = int(n[i, d])
                 descs[i].lo[d] = int(lo[i, d])

@@ -75,3 +75,35 @@ def test_no_cpu_fallback_in_product_path():
             if fn.endswith(".py"):
                 txt = open(os.path.join(dirpath, fn)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), fn
+
+
+def test_layout_rules_are_checked_on_the_host():
+    """dsp_create rejects bad layouts before touching the device: a level-1
+    patch with an odd origin or size, overlapping level-1 patches, a level-0
+    set that does not tile the box, a level other than 0 and 1, and two
+    levels with the ready-queue dispatcher."""
+    import numpy as np
+    from paper_1705_10774_gb300 import ics
+    coarse = ics.cartesian(2, 8)
+    kw = dict(gamma=5 / 3, cfl=0.4, base_cells=coarse.base_cells, box_len=coarse.box_len)
+
+    def code(n, lo, level, **extra):
+        with __import__("pytest").raises(D.DispatchError) as e:
+            D.Dispatch(n, lo, level=level, **kw, **extra)
+        return e.value.code
+
+    two = ics.two_level(coarse, 4, 8, fine_patch=8)
+    lo_odd = two.lo.copy()
+    lo_odd[-1, 0] += 1
+    assert code(two.n, lo_odd, two.levels) == D.DSP_ERR_INVALID_ARG
+    lo_ovl = two.lo.copy()
+    lo_ovl[-1] = lo_ovl[-2]
+    assert code(two.n, lo_ovl, two.levels) == D.DSP_ERR_INVALID_ARG
+    assert code(coarse.n[:-1], coarse.lo[:-1], None) == D.DSP_ERR_INVALID_ARG
+    lev2 = two.levels.copy()
+    lev2[-1] = 2
+    assert code(two.n, two.lo, lev2) == D.DSP_ERR_UNSUPPORTED
+    assert code(two.n, two.lo, two.levels, dispatcher=0, time_mode=1) == D.DSP_ERR_UNSUPPORTED
+    n_odd = two.n.copy()
+    n_odd[-1] = (7, 8, 8)
+    assert code(n_odd, two.lo, two.levels) == D.DSP_ERR_INVALID_ARG
