@@ -545,6 +545,53 @@ def mixed_arm(args):
     g.close()
 
 
+def amr_arm(args):
+    """Two refinement levels with mixed patch sizes (the uneven batched solve
+    of Sec. 5.2 stood in for by synthetic data): level 0 = 512^3 over the box
+    in 96^3 super-blocks of 16^3 / 24^3 / 32^3 patches plus 32^3 remainder
+    slabs; level 1 = 256^3 cells at dx/2 over [3/8, 5/8]^3, tiled the same
+    way (remainder 64 cells in 32^3 patches).  The benchmark's turbulence
+    input on level 0 (rms |v| = 2, beta = 1); level-1 cells take their
+    level-0 parent's velocity.  FP32 state, local steps, sweeps replayed from
+    CUDA graphs, autotuned."""
+    import torch
+    from paper_1705_10774_gb300 import ics
+    from paper_1705_10774_gb300.dispatch import Dispatch
+    lay, arrays = ics.config_two_level(args.blocks)
+    state = [torch.from_numpy(a).cuda() for a in arrays]
+    del arrays
+    stream = torch.cuda.current_stream()
+    g = Dispatch(lay.n, lay.lo, level=lay.levels, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells,
+                 box_len=lay.box_len, precision=1, time_mode=1, graph=1, timing=1, stream=stream.cuda_stream,
+                 sched_capacity=1 << 22)
+    g.set_state(*state)
+    tuned = g.autotune(reps=2)
+    g.set_state(*state)
+    g.advance(t_end=args.t_end / 4)           # warm-up
+    g.set_state(*state)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = g.advance(t_end=args.t_end)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    p, _, dts = g.schedule()
+    lev = lay.levels[p]
+    cells = np.prod(lay.n, axis=1)[p]
+    out = {"workload": "two levels: 512^3 level 0 + 256^3 level 1 over [3/8,5/8]^3, mixed 16/24/32 patches",
+           "patches": int(lay.npatch), "patches_per_level": [int((lay.levels == l).sum()) for l in (0, 1)],
+           "cells": int(np.prod(lay.n, axis=1).sum()), "t_end": args.t_end, "ms": ms,
+           "cell_updates": st["cell_updates"], "sweeps": st["sweeps"],
+           "cell_updates_per_level": [int(cells[lev == l].sum()) for l in (0, 1)],
+           "dt_per_level": [sorted(set(np.unique(dts[lev == l]).tolist()))[:4] for l in (0, 1)],
+           "cell_updates_per_s": st["cell_updates"] / (ms * 1e-3), "variant": tuned[0],
+           "kernel_ms": st["kernel_ms"]}
+    print(json.dumps(out))
+    g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -561,7 +608,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="turbulence", choices=["turbulence", "lts", "orszag-tang", "mixed"],
+    ap.add_argument("--workload", default="turbulence",
+                    choices=["turbulence", "lts", "orszag-tang", "mixed", "amr"],
                     help="lts / orszag-tang: side measurements (one JSON line each), not the benchmark line")
     ap.add_argument("--t-end", type=float, default=0.01, help="end time of the lts / orszag-tang / mixed runs")
     ap.add_argument("--blocks", type=int, default=5, help="96^3 super-blocks per axis of the mixed run")
@@ -574,6 +622,8 @@ def main():
         return orszag_tang_arm(args)
     if args.workload == "mixed":
         return mixed_arm(args)
+    if args.workload == "amr":
+        return amr_arm(args)
     if args.impl == "reference":
         reference_arm(args)
     else:

@@ -255,6 +255,14 @@ class Dispatch:
         self._check(load().dsp_save(self._h, buf, used.value, ctypes.byref(used)))
         return buf.raw
 
+    def save_array(self) -> np.ndarray:
+        """dsp_save into a numpy byte array (no second copy of a large state)."""
+        used = ctypes.c_size_t()
+        self._check(load().dsp_save(self._h, None, 0, ctypes.byref(used)))
+        buf = np.empty(used.value, np.uint8)
+        self._check(load().dsp_save(self._h, buf.ctypes.data_as(ctypes.c_void_p), used.value, ctypes.byref(used)))
+        return buf
+
     def load_state(self, blob: bytes):
         self._check(load().dsp_load(self._h, blob, len(blob)))
 

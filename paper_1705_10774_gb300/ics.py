@@ -168,6 +168,39 @@ def patches_from_functions(layout: Layout, rho, vel, p, gamma, faces=None, poten
     return cat(Us), cat(bxs), cat(bys), cat(bzs)
 
 
+def config_two_level(blocks=5, seed=10774, layout_seeds=(17, 18), dtype=np.float32):
+    """The uneven batched solve on two levels: level 0 = (96 blocks + 32)^3
+    cells (512^3 for blocks = 5) in 96^3 super-blocks of 16^3 / 24^3 / 32^3
+    patches plus 32^3 remainder slabs; level 1 at dx/2 over the central
+    quarter-width cube [3/8, 5/8]^3, tiled the same way with its remainder in
+    32^3 patches.  Level 0 carries the turbulence input (solenoidal
+    E(k) ~ k^-2 on 1 <= |k|/2pi <= 4, rms |v| = 2, rho = 1, p = 0.6, uniform B
+    along x at beta = 1); level-1 cells take their level-0 parent's
+    velocity.  Returns the layout and the patch arrays (U, bx, by, bz)."""
+    coarse = mixed_blocks(blocks, 96, remainder=32, seed=layout_seeds[0])
+    X, Y, Z = coarse.base_cells
+    fine_lo, fine_cells = 3 * X // 8, X // 4
+    fb = 2 * fine_cells // 96
+    fine = mixed_blocks(fb, 96, remainder=2 * fine_cells - 96 * fb, seed=layout_seeds[1])
+    lay = two_level(coarse, fine_lo, fine_cells, fine_n=fine.n, fine_los=fine.lo)
+    rng = np.random.default_rng(seed)
+    v = solenoidal_velocity((Z, Y, X), coarse.box_len, 1.0, 4.0, 2.0, rng).astype(np.float32)
+    b0 = np.sqrt(1.2)
+    f = Fields(rho=np.ones((Z, Y, X)), v=v, p=np.full((Z, Y, X), 0.6), bx=np.full((Z, Y, X), b0),
+               by=np.zeros((Z, Y, X)), bz=np.zeros((Z, Y, X)), gamma=5.0 / 3.0)
+    s0 = to_patches(coarse, f, dtype=dtype)
+    del f
+    dx0 = coarse.dx
+    par = lambda a: np.clip((a / dx0).astype(np.int64), 0, X - 1)
+    vel = lambda x, y, z: (v[0][par(z), par(y), par(x)], v[1][par(z), par(y), par(x)], v[2][par(z), par(y), par(x)])
+    fl = Layout(n=fine.n, lo=fine.lo + 2 * fine_lo, base_cells=coarse.base_cells, box_len=coarse.box_len,
+                level=np.ones(fine.npatch, np.int32))
+    s1 = patches_from_functions(fl, lambda x, y, z: 1.0 + 0 * x, vel, lambda x, y, z: 0.6 + 0 * x, 5.0 / 3.0,
+                                faces=(lambda x, y, z: b0 + 0 * x, lambda x, y, z: 0 * x, lambda x, y, z: 0 * x),
+                                dtype=dtype)
+    return lay, tuple(np.concatenate([a, b]) for a, b in zip(s0, s1))
+
+
 @dataclass
 class Fields:
     """A global periodic state on the level grid (index order z, y, x)."""
@@ -210,15 +243,26 @@ def to_patches(layout: Layout, f: Fields, dtype=np.float64):
     E = f.p / (f.gamma - 1.0) + 0.5 * f.rho * v2 + 0.5 * (Bxc ** 2 + Byc ** 2 + Bzc ** 2)
     Ug = np.stack([f.rho, f.rho * f.v[0], f.rho * f.v[1], f.rho * f.v[2], E])
     Z, Y, X = f.rho.shape
+
+    def cut(a, starts, lens):
+        """a[..., z0:z0+lz, y0:y0+ly, x0:x0+lx] on the periodic grid (views
+        unless an axis wraps)."""
+        nd = a.ndim
+        for ax, (s0, ln) in enumerate(zip(starts, lens)):
+            axis = nd - 3 + ax
+            N = a.shape[axis]
+            if s0 + ln <= N:
+                a = a[(slice(None),) * axis + (slice(s0, s0 + ln),)]
+            else:
+                a = np.take(a, np.arange(s0, s0 + ln) % N, axis=axis)
+        return a
+
     Us, bxs, bys, bzs = [], [], [], []
     for (nx, ny, nz), (x0, y0, z0) in zip(layout.n, layout.lo):
-        zi = np.arange(z0, z0 + nz) % Z
-        yi = np.arange(y0, y0 + ny) % Y
-        xi = np.arange(x0, x0 + nx) % X
-        Us.append(Ug[:, zi][:, :, yi][:, :, :, xi].ravel())
-        bxs.append(f.bx[zi][:, yi][:, :, np.arange(x0, x0 + nx + 1) % X].ravel())
-        bys.append(f.by[zi][:, np.arange(y0, y0 + ny + 1) % Y][:, :, xi].ravel())
-        bzs.append(f.bz[np.arange(z0, z0 + nz + 1) % Z][:, yi][:, :, xi].ravel())
+        Us.append(cut(Ug, (z0, y0, x0), (nz, ny, nx)).ravel())
+        bxs.append(cut(f.bx, (z0, y0, x0), (nz, ny, nx + 1)).ravel())
+        bys.append(cut(f.by, (z0, y0, x0), (nz, ny + 1, nx)).ravel())
+        bzs.append(cut(f.bz, (z0, y0, x0), (nz + 1, ny, nx)).ravel())
     cat = lambda a: np.concatenate(a).astype(dtype)
     return cat(Us), cat(bxs), cat(bys), cat(bzs)
 

@@ -161,3 +161,103 @@ def test_local_steps_4096_patches_queue_equals_sweeps(precision):
     assert st_q["cell_updates"] == st_s["cell_updates"]
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+def parse_save_any(blob):
+    """Times, signal speeds, newest-slot indices, last steps and the slab
+    (slice-major, any patch sizes) of a dsp_save blob."""
+    assert bytes(blob[:8]).startswith(b"DSPSAVE")
+    version, npch, ns, prec = struct.unpack_from("<4i", blob, 8)
+    _, slot_stride = struct.unpack_from("<2q", blob, 24)
+    off = 40
+    ts = np.frombuffer(blob, np.float64, npch * ns, off).reshape(npch, ns); off += 8 * npch * ns
+    sm = np.frombuffer(blob, np.float64, npch * ns, off).reshape(npch, ns); off += 8 * npch * ns
+    latest = np.frombuffer(blob, np.int32, npch, off); off += 4 * npch
+    dtl = np.frombuffer(blob, np.float64, npch, off); off += 8 * npch
+    dt = np.float32 if prec == 1 else np.float64
+    slab = np.frombuffer(blob, dt, ns * slot_stride, off).reshape(ns, slot_stride)
+    return ts, latest, dtl, slab
+
+
+def _patch_lengths(n):
+    n = n.astype(np.int64)
+    nc = n[:, 0] * n[:, 1] * n[:, 2]
+    parts = np.stack([5 * nc, (n[:, 0] + 1) * n[:, 1] * n[:, 2], n[:, 0] * (n[:, 1] + 1) * n[:, 2],
+                      n[:, 0] * n[:, 1] * (n[:, 2] + 1)], axis=1)
+    return parts, np.concatenate([[0], np.cumsum(parts.sum(axis=1))])
+
+
+def _around(lay, P, margin):
+    """Patches whose box meets patch P's box widened by `margin` level-0
+    cells (periodic), in level-1 cell units: a superset of P's neighbours."""
+    s = (2 // 2 ** lay.levels)[:, None]
+    lo, hi = lay.lo * s, (lay.lo + lay.n) * s
+    L = 2 * np.array(lay.base_cells)
+    a, b = lo[P] - 2 * margin, hi[P] + 2 * margin
+    hit = np.ones(lay.npatch, bool)
+    for d in range(3):
+        ax = np.zeros(lay.npatch, bool)
+        for sh in (-L[d], 0, L[d]):
+            ax |= (lo[:, d] + sh < b[d]) & (hi[:, d] + sh > a[d])
+        hit &= ax
+    return np.flatnonzero(hit)
+
+
+def test_two_levels_full_size_sampled_updates_fp32():
+    """The uneven two-level solve at full size (8.3k patches of 16^3 / 24^3 /
+    32^3, 1.5e8 cells) in the benchmark's launch configuration (FP32 state,
+    local steps, sweeps replayed from CUDA graphs, autotuned).  After 32
+    sweeps the oracle takes the GPU's slices around sampled ready patches --
+    level-1 patches at the edge of the refined region (prolonged guards) and
+    level-0 patches next to or under it (restricted guards) -- and reproduces
+    their steps and their next updates in FP64 from the same FP32 inputs."""
+    lay, arrays = ics.config_two_level(5)
+    kw = dict(gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
+    g = Dispatch(lay.n, lay.lo, level=lay.levels, time_mode=1, precision=1, graph=1, sched_capacity=1 << 22, **kw)
+    g.set_state(*[torch.from_numpy(a).cuda() for a in arrays])
+    del arrays
+    g.autotune(reps=1)
+    g.advance(t_end=1.0, max_sweeps=32)
+    parts, offs = _patch_lengths(lay.n)
+    X = lay.base_cells[0]
+    r1 = (2 * (3 * X // 8), 2 * (5 * X // 8))        # refined region in level-1 cells
+    s = (2 // 2 ** lay.levels)[:, None]
+    lo1, hi1 = lay.lo * s, (lay.lo + lay.n) * s
+    edge_fine = (lay.levels == 1) & np.any((lo1 == r1[0]) | (hi1 == r1[1]), axis=1)
+    near = np.all((hi1 > r1[0] - 8) & (lo1 < r1[1] + 8), axis=1)
+    coarse_near = (lay.levels == 0) & near
+    seen = {"fine": 0, "coarse": 0}
+    rng = np.random.default_rng(1)
+    for _ in range(4):
+        blob = g.save_array()
+        n_before = len(g.schedule()[0])
+        g.advance(t_end=1.0, max_sweeps=1)
+        sp, st_, sdt = (x[n_before:] for x in g.schedule())
+        ts, latest, dtl, slab = parse_save_any(blob)
+        picks = []
+        for name, mask in (("fine", edge_fine), ("coarse", coarse_near)):
+            cand = [int(P) for P in sp if mask[P]]
+            picks += [(name, P) for P in rng.permutation(cand)[:2]]
+        for name, P in picks:
+            S = _around(lay, P, 6)
+            o = Oracle(lay.n[S], lay.lo[S], level=lay.levels[S], time_mode=1, **kw)
+            for k, Q in enumerate(S):
+                for sl in range(3):
+                    seg = slab[sl, offs[Q]:offs[Q + 1]].astype(np.float64)
+                    U, bx, by, bz = np.split(seg, np.cumsum(parts[Q])[:3])
+                    o.set_slot(k, sl, float(ts[Q, sl]), U, bx, by, bz)
+                o.set_latest(k, int(latest[Q]), float(dtl[Q]))
+            k = int(np.flatnonzero(S == P)[0])
+            j = int(np.flatnonzero(sp == P)[0])
+            assert st_[j] == ts[P, latest[P]]
+            assert o.patch_dt(k, 1.0) == sdt[j]
+            ref = o.update_patch(k, float(sdt[j]))[:4]
+            got = g.get_state(first=P, count=1)
+            scale = max(float(np.max(np.abs(b))) for b in ref)
+            for a, b in zip(got, ref):
+                assert float(np.max(np.abs(a - b))) <= 1e-5 * scale, (name, P)
+            seen[name] += 1
+        del blob, slab
+        if seen["fine"] >= 2 and seen["coarse"] >= 2:
+            break
+    assert seen["fine"] >= 2 and seen["coarse"] >= 2, seen
