@@ -24,6 +24,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "dsp_dispatch.cuh"
 #include "dsp_internal.h"
 #include "dsp_physics.cuh"
@@ -57,9 +59,35 @@ struct Lay {
   static constexpr int oNBX = oEZ + H1N;       // [H1N] new x-faces of the updated plane
   static constexpr int oNBY = oNBX + H1N;      // [H1N] new y-faces
   static constexpr int oNBZ = oNBY + H1N;      // [2 parity][H1N] new z-faces
-  static constexpr int total = oNBZ + 2 * H1N;
+  // the old values phase E updates, copied in ahead of time: U of the tile's
+  // cells, their x- and y-faces, the z-faces below them
+  static constexpr int oOLD = oNBZ + 2 * H1N;
+  static constexpr int OLDU = 0, OLDX = 5 * TX * TY, OLDY = OLDX + (TX + 1) * TY, OLDZ = OLDY + TX * (TY + 1);
+  static constexpr int total = oOLD + OLDZ + TX * TY;
 };
 
+
+// Asynchronous global-to-shared copies of single elements (cp.async, no
+// registers held while in flight): one per gathered value, committed as a
+// group per plane and waited for before the plane is used.
+enum { GATHER_NOW = 0, GATHER_ISSUE = 1, GATHER_BLEND = 2 };
+template <int M>
+using GatherMode = std::integral_constant<int, M>;
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ void set_error(const DevCtx &c, int code, int P, long long cell) {
   if (atomicCAS(&c.ctl[CTL_STATUS], 0, code) == 0) {
@@ -165,6 +193,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
   const int nbx = floordiv(lox + x0 + tx + 2, bsz[0]) - bx0 + 1;
   const int nby = floordiv(loy + y0 + ty + 2, bsz[1]) - by0 + 1;
   const int nbz = floordiv(loz + z0 + tz + 2, bsz[2]) - bz0 + 1;
+  int my_blend = 0;
   for (int e = tid; e < nbx * nby * nbz; e += NT) {
     const int bx = bx0 + e % nbx, by = by0 + (e / nbx) % nby, bz = bz0 + e / (nbx * nby);
     const int wx = posmod(bx, mapd[0]), wy = posmod(by, mapd[1]), wz = posmod(bz, mapd[2]);
@@ -213,16 +242,28 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     srcA[e] = A;
     srcB[e] = B;
     wgt[e] = wv;
+    if (B) my_blend = 1;
   }
   if (tid == 0) s_fallback = 0;
-  __syncthreads();
+  const int any_blend = __syncthreads_or(my_blend);
 
-  auto val = [&](int o, long long idx) -> T {
-    T a = srcA[o][idx];
-    const T *B = srcB[o];
-    if (B) {
-      T b = B[idx];
-      a = a + wgt[o] * (b - a);
+  // Where a gathered value lives: its address in the source slice (the
+  // patch's own newest slice, a neighbour's slice, or the cross-level guard
+  // buffer) and its owner-table entry (-1 on the patch's own interior).  An
+  // entry with a second slice B blends A[idx] + w (B[idx] - A[idx]).
+  struct Loc {
+    const T *p;
+    int e;
+  };
+  auto blended = [&](const Loc &l) -> bool { return l.e >= 0 && srcB[l.e] != nullptr; };
+  auto fetch = [&](const Loc &l) -> T {
+    T a = *l.p;
+    if (l.e >= 0) {
+      const T *B = srcB[l.e];
+      if (B) {
+        T b = B[l.p - srcA[l.e]];
+        a = a + wgt[l.e] * (b - a);
+      }
     }
     return a;
   };
@@ -237,77 +278,121 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
   };
   // Cell-centred component q of patch-local cell (x,y,z) (radius <= 2
   // outside the patch).
-  auto cellv = [&](int x, int y, int z, long long q) -> T {
+  auto cell_loc = [&](int x, int y, int z, long long q) -> Loc {
     if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz)
-      return own[q * nc + ((long long)z * ny + y) * nx + x];
+      return {own + q * nc + ((long long)z * ny + y) * nx + x, -1};
     const int gx = lox + x, gy = loy + y, gz = loz + z;
     const int e = entry(gx, gy, gz);
     const int mx = S.n[0][e], my = S.n[1][e], mz = S.n[2][e];
     const int lx = gx - S.lo[0][e], ly = gy - S.lo[1][e], lz = gz - S.lo[2][e];
-    return val(e, q * ((long long)mx * my * mz) + ((long long)lz * my + ly) * mx + lx);
+    return {srcA[e] + q * ((long long)mx * my * mz) + ((long long)lz * my + ly) * mx + lx, e};
   };
   // Face below cell (x,y,z) along each axis: the patch's own face when it
   // lies on one of its interior cells, else the face of the patch that owns
   // cell (x,y,z).
-  auto facex = [&](int x, int y, int z) -> T {
+  auto facex_loc = [&](int x, int y, int z) -> Loc {
     if (x >= 0 && x <= nx && y >= 0 && y < ny && z >= 0 && z < nz)
-      return own[ofx + ((long long)z * ny + y) * (nx + 1) + x];
+      return {own + ofx + ((long long)z * ny + y) * (nx + 1) + x, -1};
     const int gx = lox + x, gy = loy + y, gz = loz + z;
     const int e = entry(gx, gy, gz);
     const int mx = S.n[0][e], my = S.n[1][e], mz = S.n[2][e];
     const int lx = gx - S.lo[0][e], ly = gy - S.lo[1][e], lz = gz - S.lo[2][e];
-    return val(e, 5 * ((long long)mx * my * mz) + ((long long)lz * my + ly) * (mx + 1) + lx);
+    return {srcA[e] + 5 * ((long long)mx * my * mz) + ((long long)lz * my + ly) * (mx + 1) + lx, e};
   };
-  auto facey = [&](int x, int y, int z) -> T {
+  auto facey_loc = [&](int x, int y, int z) -> Loc {
     if (x >= 0 && x < nx && y >= 0 && y <= ny && z >= 0 && z < nz)
-      return own[ofy + ((long long)z * (ny + 1) + y) * nx + x];
+      return {own + ofy + ((long long)z * (ny + 1) + y) * nx + x, -1};
     const int gx = lox + x, gy = loy + y, gz = loz + z;
     const int e = entry(gx, gy, gz);
     const int mx = S.n[0][e], my = S.n[1][e], mz = S.n[2][e];
     const int lx = gx - S.lo[0][e], ly = gy - S.lo[1][e], lz = gz - S.lo[2][e];
     const long long m = (long long)mx * my * mz;
-    return val(e, 5 * m + (long long)(mx + 1) * my * mz + ((long long)lz * (my + 1) + ly) * mx + lx);
+    return {srcA[e] + 5 * m + (long long)(mx + 1) * my * mz + ((long long)lz * (my + 1) + ly) * mx + lx, e};
   };
-  auto facez = [&](int x, int y, int z) -> T {
+  auto facez_loc = [&](int x, int y, int z) -> Loc {
     if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z <= nz)
-      return own[ofz + ((long long)z * ny + y) * nx + x];
+      return {own + ofz + ((long long)z * ny + y) * nx + x, -1};
     const int gx = lox + x, gy = loy + y, gz = loz + z;
     const int e = entry(gx, gy, gz);
     const int mx = S.n[0][e], my = S.n[1][e], mz = S.n[2][e];
     const int lx = gx - S.lo[0][e], ly = gy - S.lo[1][e], lz = gz - S.lo[2][e];
     const long long m = (long long)mx * my * mz;
-    return val(e, 5 * m + (long long)(mx + 1) * my * mz + (long long)mx * (my + 1) * mz +
-                      ((long long)lz * my + ly) * mx + lx);
+    return {srcA[e] + 5 * m + (long long)(mx + 1) * my * mz + (long long)mx * (my + 1) * mz +
+                ((long long)lz * my + ly) * mx + lx,
+            e};
   };
 
   // ---- A: gather plane q of the radius-2 padded tile: the raw conserved
-  // values and the faces (x- and y-faces below each cell, both z-faces),
-  // then the primitive variables from shared memory.
-  auto load_plane = [&](int q) {
+  // values and the faces (x- and y-faces below each cell, both z-faces).
+  // Mode GATHER_NOW loads every value; GATHER_ISSUE starts an asynchronous
+  // copy (cp.async) of every value that is a plain copy and leaves the
+  // blended ones; GATHER_BLEND computes only the blended ones (after the
+  // copies have landed).
+  auto gather_plane = [&](int q, auto mode) {
+    constexpr int M = decltype(mode)::value;
     const int rs = (q - z0 + 3) % 3, fs = (q - z0 + 2) & 1;
     T *Wq = Wr + rs * 8 * H2N;
     T *Fq = FB + fs * 4 * FPN;
+    auto put = [&](T *dst, const Loc &l) {
+      if constexpr (M == GATHER_NOW) {
+        *dst = fetch(l);
+      } else if constexpr (M == GATHER_ISSUE) {
+        if (!blended(l)) cp_async_elem(dst, l.p);
+      } else {
+        if (blended(l)) *dst = fetch(l);
+      }
+    };
     for (int ci = tid; ci < (TX + 5) * (TY + 5); ci += NT) {
       const int i = ci % (TX + 5) - 2, j = ci / (TX + 5) - 2;
       if (i > tx + 2 || j > ty + 2) continue;
       const int x = x0 + i, y = y0 + j;
       const int f = F5(i, j);
-      if (j <= ty + 1) Fq[f] = facex(x, y, q);
-      if (i <= tx + 1) Fq[FPN + f] = facey(x, y, q);
+      const bool inside = x >= 0 && x < nx && y >= 0 && y < ny && q >= 0 && q < nz;
+      if (M == GATHER_BLEND && inside) continue;  // every value of this column is the patch's own
+      if (j <= ty + 1) put(Fq + f, facex_loc(x, y, q));
+      if (i <= tx + 1) put(Fq + FPN + f, facey_loc(x, y, q));
       if (i <= tx + 1 && j <= ty + 1) {
-        Fq[2 * FPN + f] = facez(x, y, q);
-        Fq[3 * FPN + f] = facez(x, y, q + 1);
+        put(Fq + 2 * FPN + f, facez_loc(x, y, q));
+        put(Fq + 3 * FPN + f, facez_loc(x, y, q + 1));
         const int h = H2(i, j);
-        if (x >= 0 && x < nx && y >= 0 && y < ny && q >= 0 && q < nz) {
-          const long long cid = ((long long)q * ny + y) * nx + x;
 #pragma unroll
-          for (int k = 0; k < 5; k++) Wq[k * H2N + h] = own[k * nc + cid];
-        } else {
-#pragma unroll
-          for (int k = 0; k < 5; k++) Wq[k * H2N + h] = cellv(x, y, q, k);
-        }
+        for (int k = 0; k < 5; k++) put(Wq + k * H2N + h, cell_loc(x, y, q, k));
       }
     }
+    if constexpr (M == GATHER_ISSUE) cp_async_commit();
+  };
+  // Start the copies of the old values phase E reads in iteration `it`
+  // (plane p-1's U and x-/y-faces once it >= 2, the z-faces at p-1/2 once
+  // it >= 1); each thread copies exactly the values it will update.
+  T *const OLD = sm + L::oOLD;
+  auto prefetch_old = [&](int it, int p) {
+    if (it >= 2) {
+      for (int ci = tid; ci < TX * TY; ci += NT) {
+        const int i = ci % TX, j = ci / TX;
+        if (i >= tx || j >= ty) continue;
+        const long long id = ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i);
+#pragma unroll
+        for (int k = 0; k < 5; k++) cp_async_elem(OLD + L::OLDU + k * TX * TY + ci, own + k * nc + id);
+      }
+      for (int ci = tid; ci < (TX + 1) * TY; ci += NT) {
+        const int i = ci % (TX + 1), j = ci / (TX + 1);
+        if (i > tx || j >= ty) continue;
+        cp_async_elem(OLD + L::OLDX + ci, own + ofx + ((long long)(p - 1) * ny + (y0 + j)) * (nx + 1) + (x0 + i));
+      }
+      for (int ci = tid; ci < TX * (TY + 1); ci += NT) {
+        const int i = ci % TX, j = ci / TX;
+        if (i >= tx || j > ty) continue;
+        cp_async_elem(OLD + L::OLDY + ci, own + ofy + ((long long)(p - 1) * (ny + 1) + (y0 + j)) * nx + (x0 + i));
+      }
+    }
+    if (it >= 1) {
+      for (int ci = tid; ci < TX * TY; ci += NT) {
+        const int i = ci % TX, j = ci / TX;
+        if (i >= tx || j >= ty) continue;
+        cp_async_elem(OLD + L::OLDZ + ci, own + ofz + ((long long)p * ny + (y0 + j)) * nx + (x0 + i));
+      }
+    }
+    cp_async_commit();
   };
   auto prim_plane = [&](int q) {
     const int rs = (q - z0 + 3) % 3, fs = (q - z0 + 2) & 1;
@@ -325,8 +410,8 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     }
   };
 
-  load_plane(z0 - 2);
-  load_plane(z0 - 1);
+  gather_plane(z0 - 2, GatherMode<GATHER_NOW>{});
+  gather_plane(z0 - 1, GatherMode<GATHER_NOW>{});
   __syncthreads();
   prim_plane(z0 - 2);
   prim_plane(z0 - 1);
@@ -345,8 +430,16 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     T *const EYc = EY + par * H1N, *const EYp = EY + (par ^ 1) * H1N;
     T *const NBZc = NBZ + par * H1N, *const NBZp = NBZ + (par ^ 1) * H1N;
 
-    // ---- A
-    load_plane(p + 1);
+    // ---- A: plane p+1 -- gathered now (first plane, or with concurrent
+    // publishers), else its copies were started one iteration earlier and
+    // only the blended values remain
+    if (!CONC) prefetch_old(it, p);
+    if (CONC || it == 0) {
+      gather_plane(p + 1, GatherMode<GATHER_NOW>{});
+    } else {
+      cp_async_wait<1>();  // every copy but the old values just started
+      if (any_blend) gather_plane(p + 1, GatherMode<GATHER_BLEND>{});
+    }
     __syncthreads();
     prim_plane(p + 1);
     __syncthreads();
@@ -397,6 +490,12 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
       }
     }
     __syncthreads();
+    // plane p-1's primitive ring slot and plane p's faces are dead now: start
+    // the copies of plane p+2 into them, to land while C..F run
+    if (!CONC) {
+      if (p + 2 <= z0 + tz + 1) gather_plane(p + 2, GatherMode<GATHER_ISSUE>{});
+      else cp_async_commit();  // an empty group keeps the wait counts in step
+    }
 
     // ---- C: face fluxes
     {
@@ -573,13 +672,15 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     const bool upd = it >= 2;
     const int ui = tid % TX, uj = tid / TX;
     const bool mine = tid < TX * TY && ui < tx && uj < ty;
+    if (!CONC) cp_async_wait<1>();  // this thread's old values (not plane p+2's copies)
+    auto old_u = [&](int k, long long ci) -> T { return CONC ? own[k * nc + ci] : OLD[L::OLDU + k * TX * TY + tid]; };
     if (upd && mine) {
       const int i = ui, j = uj, h = H1(i, j);
       const long long ci = ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i);
 #pragma unroll
       for (int k = 0; k < 5; k++) {
         const T fz = FZc[k * H1N + h] - FZp[k * H1N + h];
-        unew[k] = own[k * nc + ci] - dtdx * (DUp[k * H1N + h] + fz);
+        unew[k] = old_u(k, ci) - dtdx * (DUp[k * H1N + h] + fz);
         dst[k * nc + ci] = unew[k];
       }
     }
@@ -589,7 +690,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const int i = ci % (TX + 1), j = ci / (TX + 1), h = H1(i, j);
         if (i > tx || j >= ty) continue;
         const long long id = ((long long)k * ny + (y0 + j)) * (nx + 1) + (x0 + i);
-        const T b = own[ofx + id] - dtdx * ((EZ[H1(i, j + 1)] - EZ[h]) - (EYc[h] - EYp[h]));
+        const T b = (CONC ? own[ofx + id] : OLD[L::OLDX + ci]) - dtdx * ((EZ[H1(i, j + 1)] - EZ[h]) - (EYc[h] - EYp[h]));
         NBX[h] = b;
         dst[ofx + id] = b;
       }
@@ -597,7 +698,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const int i = ci % TX, j = ci / TX, h = H1(i, j);
         if (i >= tx || j > ty) continue;
         const long long id = ((long long)k * (ny + 1) + (y0 + j)) * nx + (x0 + i);
-        const T b = own[ofy + id] - dtdx * ((EXc[h] - EXp[h]) - (EZ[H1(i + 1, j)] - EZ[h]));
+        const T b = (CONC ? own[ofy + id] : OLD[L::OLDY + ci]) - dtdx * ((EXc[h] - EXp[h]) - (EZ[H1(i + 1, j)] - EZ[h]));
         NBY[h] = b;
         dst[ofy + id] = b;
       }
@@ -607,7 +708,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const int i = ci % TX, j = ci / TX, h = H1(i, j);
         if (i >= tx || j >= ty) continue;
         const long long id = ((long long)p * ny + (y0 + j)) * nx + (x0 + i);
-        const T b = own[ofz + id] - dtdx * ((EYc[H1(i + 1, j)] - EYc[h]) - (EXc[H1(i, j + 1)] - EXc[h]));
+        const T b = (CONC ? own[ofz + id] : OLD[L::OLDZ + ci]) - dtdx * ((EYc[H1(i + 1, j)] - EYc[h]) - (EXc[H1(i, j + 1)] - EXc[h]));
         NBZc[h] = b;
         dst[ofz + id] = b;
       }
