@@ -46,8 +46,8 @@ F64_PRECISION = 2
 # from ncu's dram__bytes_read.sum + dram__bytes_write.sum on a 216-patch
 # capture of the same kernel, scaled by cells; None until taken on the
 # current kernel.
-TRAFFIC_F64 = (547.797504e6 + 422.244352e6) * 512 / 216   # variant 3 (FP64 FMA)
-TRAFFIC_F32 = 588.490240e6 + 508.069120e6                  # variant 5, full workload
+TRAFFIC_F64 = (551.541504e6 + 421.864960e6) * 512 / 216   # variant 3 (FP64 FMA)
+TRAFFIC_F32 = 631.432960e6 + 510.070528e6                  # variant 5, full workload
 
 
 def radius2_guard_fraction(n):

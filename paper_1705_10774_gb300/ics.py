@@ -138,18 +138,19 @@ def patches_from_functions(layout: Layout, rho, vel, p, gamma, faces=None, poten
         h = dx0 / 2 ** int(lev)
         ci = [(lo[d] + np.arange(m) + 0.5) * h for d, m in enumerate((nx, ny, nz))]
         fi = [(lo[d] + np.arange(m + 1)) * h for d, m in enumerate((nx, ny, nz))]
-        Z, Y, X = np.meshgrid(ci[2], ci[1], ci[0], indexing="ij")
-        r = np.broadcast_to(rho(X, Y, Z), X.shape)
-        v = [np.broadcast_to(c, X.shape) for c in vel(X, Y, Z)]
-        pr = np.broadcast_to(p(X, Y, Z), X.shape)
+        # coordinates as broadcastable (sparse) grids: functions act elementwise
+        Z, Y, X = np.meshgrid(ci[2], ci[1], ci[0], indexing="ij", sparse=True)
+        shp = (nz, ny, nx)
+        r = np.broadcast_to(rho(X, Y, Z), shp)
+        v = [np.broadcast_to(c, shp) for c in vel(X, Y, Z)]
+        pr = np.broadcast_to(p(X, Y, Z), shp)
+        g = lambda a, b, c: np.meshgrid(c, b, a, indexing="ij", sparse=True)[::-1]
         if faces is not None:
-            g = lambda a, b, c: np.meshgrid(c, b, a, indexing="ij")[::-1]
             bx = np.broadcast_to(faces[0](*g(fi[0], ci[1], ci[2])), (nz, ny, nx + 1))
             by = np.broadcast_to(faces[1](*g(ci[0], fi[1], ci[2])), (nz, ny + 1, nx))
             bz = np.broadcast_to(faces[2](*g(ci[0], ci[1], fi[2])), (nz + 1, ny, nx))
         else:
             Ax, Ay, Az = potential
-            g = lambda a, b, c: np.meshgrid(c, b, a, indexing="ij")[::-1]
             # x-faces: (Az(y+) - Az(y-)) - (Ay(z+) - Ay(z-)), over h
             bx = ((Az(*g(fi[0], fi[1][1:], ci[2])) - Az(*g(fi[0], fi[1][:-1], ci[2])))
                   - (Ay(*g(fi[0], ci[1], fi[2][1:])) - Ay(*g(fi[0], ci[1], fi[2][:-1])))) / h
@@ -157,6 +158,9 @@ def patches_from_functions(layout: Layout, rho, vel, p, gamma, faces=None, poten
                   - (Az(*g(fi[0][1:], fi[1], ci[2])) - Az(*g(fi[0][:-1], fi[1], ci[2])))) / h
             bz = ((Ay(*g(fi[0][1:], ci[1], fi[2])) - Ay(*g(fi[0][:-1], ci[1], fi[2])))
                   - (Ax(*g(ci[0], fi[1][1:], fi[2])) - Ax(*g(ci[0], fi[1][:-1], fi[2])))) / h
+            bx = np.broadcast_to(bx, (nz, ny, nx + 1))
+            by = np.broadcast_to(by, (nz, ny + 1, nx))
+            bz = np.broadcast_to(bz, (nz + 1, ny, nx))
         Bc = (0.5 * (bx[:, :, :-1] + bx[:, :, 1:]), 0.5 * (by[:, :-1] + by[:, 1:]), 0.5 * (bz[:-1] + bz[1:]))
         v2 = v[0] ** 2 + v[1] ** 2 + v[2] ** 2
         E = pr / (gamma - 1.0) + 0.5 * r * v2 + 0.5 * (Bc[0] ** 2 + Bc[1] ** 2 + Bc[2] ** 2)

@@ -104,6 +104,7 @@ def test_layout_rules_are_checked_on_the_host():
     lev2[-1] = 2
     assert code(two.n, two.lo, lev2) == D.DSP_ERR_UNSUPPORTED
     assert code(two.n, two.lo, two.levels, dispatcher=0, time_mode=1) == D.DSP_ERR_UNSUPPORTED
+    assert code(np.zeros((0, 3), np.int32), np.zeros((0, 3), np.int64), None) == D.DSP_ERR_INVALID_ARG  # empty
     n_odd = two.n.copy()
     n_odd[-1] = (7, 8, 8)
     assert code(n_odd, two.lo, two.levels) == D.DSP_ERR_INVALID_ARG

@@ -261,3 +261,52 @@ def test_two_levels_full_size_sampled_updates_fp32():
         if seen["fine"] >= 2 and seen["coarse"] >= 2:
             break
     assert seen["fine"] >= 2 and seen["coarse"] >= 2, seen
+
+
+def test_largest_box_1024cubed_fp32_sampled_first_step():
+    """The largest box the tests run: 1024^3 cells as 32^3 patches of 32^3
+    in FP32 (3 slices, 104 GB on the device; slice offsets of the later
+    patches exceed 2^32 elements).  One global step from a smooth analytic
+    state uploaded in chunks; the oracle reproduces the updates of patches at
+    both ends of the patch range from the same FP32 initial values."""
+    lay = ics.cartesian(32, 32)
+    # separable smooth fields (cheap to sample: 1-D factors broadcast); each
+    # face component is independent of its own normal coordinate, so the
+    # discrete divergence is exactly zero
+    tp = 2 * np.pi
+    X1 = lambda x: x[:1, :1, :]
+    Y1 = lambda y: y[:1, :, :1]
+    Z1 = lambda z: z[:, :1, :1]
+    rho = lambda x, y, z: 1.0 + 0.2 * np.sin(tp * X1(x) + 0.3) * np.sin(tp * Z1(z) + 1.1)
+    vel = lambda x, y, z: (0.5 * np.sin(tp * Y1(y) + 0.7) * np.cos(tp * Z1(z)), 0.4 * np.sin(2 * tp * X1(x) + 0.2),
+                           0.3 * np.cos(tp * X1(x)) * np.sin(tp * Y1(y) + 1.9))
+    pre = lambda x, y, z: 0.6 + 0 * X1(x)
+    faces = (lambda x, y, z: 0.8 + 0.05 * np.sin(tp * Y1(y)) * np.cos(tp * Z1(z)),
+             lambda x, y, z: 0.05 * np.sin(tp * Z1(z) + 0.4) + 0 * X1(x),
+             lambda x, y, z: 0.05 * np.cos(tp * X1(x) + 0.9) * np.sin(tp * Y1(y)))
+
+    def arrays(ids):
+        sub = ics.Layout(n=lay.n[ids], lo=lay.lo[ids], base_cells=lay.base_cells, box_len=lay.box_len)
+        return ics.patches_from_functions(sub, rho, vel, pre, 5.0 / 3.0, faces=faces, dtype=np.float32)
+
+    kw = dict(gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
+    g = Dispatch(lay.n, lay.lo, time_mode=0, precision=1, **kw)
+    chunk = 1024
+    for first in range(0, lay.npatch, chunk):
+        ids = np.arange(first, min(first + chunk, lay.npatch))
+        g.set_state(*[torch.from_numpy(a).cuda() for a in arrays(ids)], first=first, count=len(ids))
+    st = g.advance(max_sweeps=1)
+    assert st["cell_updates"] == 1024 ** 3
+    t, dt = g.times()
+    assert np.all(dt == dt[0]) and dt[0] > 0
+    for P in (0, 1023, 16400, lay.npatch - 1):
+        S = _around(lay, P, 4)
+        o = Oracle(lay.n[S], lay.lo[S], time_mode=0, **kw)
+        o.set_state(*[a.astype(np.float64) for a in arrays(S)])
+        kP = int(np.flatnonzero(S == P)[0])
+        ref = o.update_patch(kP, float(dt[0]))[:4]
+        got = g.get_state(first=P, count=1)
+        scale = max(float(np.max(np.abs(b))) for b in ref)
+        for a, b in zip(got, ref):
+            assert float(np.max(np.abs(a - b))) <= 1e-5 * scale, P
+    g.close()
