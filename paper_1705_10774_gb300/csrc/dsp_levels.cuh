@@ -31,6 +31,14 @@ __device__ __forceinline__ int xl_posmod(int a, int b) {
   return r < 0 ? r + b : r;
 }
 
+// Map block of a wrapped level-lev cell (floor of a small integer quotient
+// through a float product, exact for level extents far below 2^20 cells).
+__device__ __forceinline__ long long xl_block(const DevCtx &c, int lev, const int w[3]) {
+  int b[3];
+  for (int d = 0; d < 3; d++) b[d] = __float2int_rd(((float)w[d] + 0.5f) * c.binv[lev][d]);
+  return ((long long)b[2] * c.mapd[lev][1] + b[1]) * c.mapd[lev][0] + b[0];
+}
+
 // The slices of patch Q that supply time t: a slice at exactly t is copied;
 // otherwise the newest two must bracket t and are blended with weight w.
 template <typename T>
@@ -46,9 +54,7 @@ template <typename T>
 __device__ int xl_source(const DevCtx &c, int lev, const int g[3], double t, XSrc<T> &s) {
   int w[3];
   for (int d = 0; d < 3; d++) w[d] = xl_posmod(g[d], c.L[lev][d]);
-  const long long b = ((long long)(w[2] / c.bsz[lev][2]) * c.mapd[lev][1] + w[1] / c.bsz[lev][1]) * c.mapd[lev][0] +
-                      w[0] / c.bsz[lev][0];
-  const int Q = c.omap[lev][b];
+  const int Q = c.omap[lev][xl_block(c, lev, w)];
   if (Q < 0) return DSP_ERR_INVALID_ARG;
   const PatchGeo &gq = c.geo[Q];
   for (int d = 0; d < 3; d++) s.loc[d] = w[d] - gq.lo[d];
@@ -119,92 +125,69 @@ __device__ int xl_face(const DevCtx &c, int lev, int ax, const int g[3], int up,
   return DSP_OK;
 }
 
-// Level-1 cell f (not owned on level 1) prolonged from its level-0 parent.
-template <typename T>
-__device__ int xl_prolong_cell(const DevCtx &c, const int f[3], double t, T u[5]) {
-  const int C[3] = {xl_floordiv(f[0], 2), xl_floordiv(f[1], 2), xl_floordiv(f[2], 2)};
-  T uc[5], ul[5], ur[5], sl[3][5];
-  int rc = xl_cell<T>(c, 0, C, t, uc);
-  if (rc) return rc;
-  for (int d = 0; d < 3; d++) {
-    int Cm[3] = {C[0], C[1], C[2]}, Cp[3] = {C[0], C[1], C[2]};
-    Cm[d] -= 1;
-    Cp[d] += 1;
-    if ((rc = xl_cell<T>(c, 0, Cm, t, ul))) return rc;
-    if ((rc = xl_cell<T>(c, 0, Cp, t, ur))) return rc;
-    for (int q = 0; q < 5; q++) sl[d][q] = mc(uc[q] - ul[q], ur[q] - uc[q]);
-  }
-  for (int q = 0; q < 5; q++) {
-    const T a = (f[0] - 2 * C[0]) ? sl[0][q] : -sl[0][q];
-    const T b = (f[1] - 2 * C[1]) ? sl[1][q] : -sl[1][q];
-    const T e = (f[2] - 2 * C[2]) ? sl[2][q] : -sl[2][q];
-    u[q] = uc[q] + T(0.25) * ((a + b) + e);
-  }
-  return DSP_OK;
-}
-
-// Face along ax on the low side of level-1 cell f, from level 0.
-template <typename T>
-__device__ int xl_prolong_face(const DevCtx &c, int ax, const int f[3], double t, T *out) {
-  const int C[3] = {xl_floordiv(f[0], 2), xl_floordiv(f[1], 2), xl_floordiv(f[2], 2)};
-  T lo, hi;
-  int rc = xl_face<T>(c, 0, ax, C, 0, t, &lo);
-  if (rc) return rc;
-  if (f[ax] == 2 * C[ax]) {
-    *out = lo;
-    return DSP_OK;
-  }
-  if ((rc = xl_face<T>(c, 0, ax, C, 1, t, &hi))) return rc;
-  *out = T(0.5) * (lo + hi);
-  return DSP_OK;
-}
-
-// Level-0 cell C (covered by level 1) restricted from its 8 children.
+// Level-0 cell C (covered by level 1) restricted from its 8 children (one
+// level-1 patch holds all of them: level-1 patches cover whole level-0
+// cells).
 template <typename T>
 __device__ int xl_restrict_cell(const DevCtx &c, const int C[3], double t, T u[5]) {
-  T s[5] = {T(0), T(0), T(0), T(0), T(0)}, v[5];
+  const int f0[3] = {2 * C[0], 2 * C[1], 2 * C[2]};
+  XSrc<T> s;
+  const int rc = xl_source<T>(c, 1, f0, t, s);
+  if (rc) return rc;
+  const PatchGeo &gq = c.geo[s.Q];
+  const long long nc = (long long)gq.n[0] * gq.n[1] * gq.n[2];
+  T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
   for (int kz = 0; kz < 2; kz++)
     for (int ky = 0; ky < 2; ky++)
       for (int kx = 0; kx < 2; kx++) {
-        const int f[3] = {2 * C[0] + kx, 2 * C[1] + ky, 2 * C[2] + kz};
-        const int rc = xl_cell<T>(c, 1, f, t, v);
-        if (rc) return rc;
-        for (int q = 0; q < 5; q++) s[q] = s[q] + v[q];
+        const long long id = ((long long)(s.loc[2] + kz) * gq.n[1] + s.loc[1] + ky) * gq.n[0] + s.loc[0] + kx;
+        for (int q = 0; q < 5; q++) acc[q] = acc[q] + xl_val(s, q * nc + id);
       }
-  for (int q = 0; q < 5; q++) u[q] = T(0.125) * s[q];
+  for (int q = 0; q < 5; q++) u[q] = T(0.125) * acc[q];
   return DSP_OK;
 }
 
 // Face along ax on the low side of level-0 cell C, the mean of the 4 level-1
-// faces on it.
+// faces on it (the children's low faces, in one level-1 patch).
 template <typename T>
 __device__ int xl_restrict_face(const DevCtx &c, int ax, const int C[3], double t, T *out) {
-  T s = T(0), v;
+  const int f0[3] = {2 * C[0], 2 * C[1], 2 * C[2]};
+  XSrc<T> s;
+  const int rc = xl_source<T>(c, 1, f0, t, s);
+  if (rc) return rc;
+  const PatchGeo &gq = c.geo[s.Q];
+  const int qx = gq.n[0], qy = gq.n[1], qz = gq.n[2];
+  const long long nc = (long long)qx * qy * qz;
+  T acc = T(0);
   for (int kz = 0; kz < 2; kz++)
     for (int ky = 0; ky < 2; ky++)
       for (int kx = 0; kx < 2; kx++) {
         const int k3[3] = {kx, ky, kz};
         if (k3[ax]) continue;
-        const int f[3] = {2 * C[0] + kx, 2 * C[1] + ky, 2 * C[2] + kz};
-        const int rc = xl_face<T>(c, 1, ax, f, 0, t, &v);
-        if (rc) return rc;
-        s = s + v;
+        const int l0 = s.loc[0] + kx, l1 = s.loc[1] + ky, l2 = s.loc[2] + kz;
+        long long idx;
+        if (ax == 0) idx = 5 * nc + ((long long)l2 * qy + l1) * (qx + 1) + l0;
+        else if (ax == 1) idx = 5 * nc + (long long)(qx + 1) * qy * qz + ((long long)l2 * (qy + 1) + l1) * qx + l0;
+        else
+          idx = 5 * nc + (long long)(qx + 1) * qy * qz + (long long)qx * (qy + 1) * qz + ((long long)l2 * qy + l1) * qx + l0;
+        acc = acc + xl_val(s, idx);
       }
-  *out = T(0.25) * s;
+  *out = T(0.25) * acc;
   return DSP_OK;
 }
 
 // Does the guard gather of a level-lev patch take level-lev cell g from the
 // other level?
 __device__ __forceinline__ bool xl_cross(const DevCtx &c, int lev, const int g[3]) {
-  int b[3];
-  for (int d = 0; d < 3; d++) b[d] = xl_posmod(g[d], c.L[lev][d]) / c.bsz[lev][d];
-  return c.gmap[lev][((long long)b[2] * c.mapd[lev][1] + b[1]) * c.mapd[lev][0] + b[0]] < 0;
+  int w[3];
+  for (int d = 0; d < 3; d++) w[d] = xl_posmod(g[d], c.L[lev][d]);
+  return c.gmap[lev][xl_block(c, lev, w)] < 0;
 }
 
 // Fill patch P's cross-level guard buffer for its current time (all threads
 // of the block).  The buffer is laid out like a slice of a patch of m = n+4
-// cells per axis whose first cell is P's cell lo-2.
+// cells per axis whose first cell is P's cell lo-2: cells x in [-2, n+2),
+// faces along an axis at x in [-2, n+2] (relative to lo).
 template <typename T>
 __device__ void fill_cross_level(const DevCtx &c, int P) {
   const PatchGeo &gp = c.geo[P];
@@ -214,42 +197,139 @@ __device__ void fill_cross_level(const DevCtx &c, int P) {
   const double t = c.t_slot[(long long)P * c.ns + c.latest[P]];
   T *const buf = (T *)c.gbuf + c.gofs[P];
   const long long mc3 = (long long)m[0] * m[1] * m[2];
-  for (long long id = threadIdx.x; id < mc3; id += blockDim.x) {
-    const int x = (int)(id % m[0]) - 2, y = (int)((id / m[0]) % m[1]) - 2, z = (int)(id / ((long long)m[0] * m[1])) - 2;
-    if (x >= 0 && x < n[0] && y >= 0 && y < n[1] && z >= 0 && z < n[2]) continue;
-    const int g[3] = {gp.lo[0] + x, gp.lo[1] + y, gp.lo[2] + z};
-    if (!xl_cross(c, lev, g)) continue;
-    T u[5];
-    const int rc = lev == 1 ? xl_prolong_cell<T>(c, g, t, u) : xl_restrict_cell<T>(c, g, t, u);
-    if (rc) {
-      xl_status(c, rc, P);
-      return;
-    }
-    for (int q = 0; q < 5; q++) buf[q * mc3 + id] = u[q];
-  }
-  long long base = 5 * mc3;
-  for (int ax = 0; ax < 3; ax++) {
-    const int f0 = m[0] + (ax == 0), f1 = m[1] + (ax == 1), f2 = m[2] + (ax == 2);
-    const long long nf = (long long)f0 * f1 * f2;
-    for (long long id = threadIdx.x; id < nf; id += blockDim.x) {
-      const int x = (int)(id % f0) - 2, y = (int)((id / f0) % f1) - 2, z = (int)(id / ((long long)f0 * f1)) - 2;
-      // P's own faces: every face of its interior cells
-      const int xy[3] = {x, y, z};
-      bool own = true;
-      for (int d = 0; d < 3; d++)
-        if (xy[d] < 0 || xy[d] > n[d] - (d != ax)) own = false;
-      if (own) continue;
-      const int g[3] = {gp.lo[0] + x, gp.lo[1] + y, gp.lo[2] + z};
-      if (!xl_cross(c, lev, g)) continue;
-      T v;
-      const int rc = lev == 1 ? xl_prolong_face<T>(c, ax, g, t, &v) : xl_restrict_face<T>(c, ax, g, t, &v);
+  const long long fofs[3] = {5 * mc3, 5 * mc3 + (long long)(m[0] + 1) * m[1] * m[2],
+                             5 * mc3 + (long long)(m[0] + 1) * m[1] * m[2] + (long long)m[0] * (m[1] + 1) * m[2]};
+  auto interior = [&](const int x[3]) {
+    return x[0] >= 0 && x[0] < n[0] && x[1] >= 0 && x[1] < n[1] && x[2] >= 0 && x[2] < n[2];
+  };
+  // a face along ax at the low side of patch cell x: P's own, and is it in the buffer?
+  auto own_face = [&](int ax, const int x[3]) {
+    for (int d = 0; d < 3; d++)
+      if (x[d] < 0 || x[d] > n[d] - (d != ax)) return false;
+    return true;
+  };
+  auto face_in_buf = [&](int ax, const int x[3]) {
+    for (int d = 0; d < 3; d++)
+      if (x[d] < -2 || x[d] > n[d] + 1 + (d == ax)) return false;
+    return true;
+  };
+  auto face_index = [&](int ax, const int x[3]) -> long long {
+    const int f0 = m[0] + (ax == 0), f1 = m[1] + (ax == 1);
+    return fofs[ax] + ((long long)(x[2] + 2) * f1 + (x[1] + 2)) * f0 + (x[0] + 2);
+  };
+  if (lev == 0) {
+    // restriction: guard cells and faces whose cell is covered by level 1
+    for (long long id = threadIdx.x; id < mc3; id += blockDim.x) {
+      const int x[3] = {(int)(id % m[0]) - 2, (int)((id / m[0]) % m[1]) - 2, (int)(id / ((long long)m[0] * m[1])) - 2};
+      if (interior(x)) continue;
+      const int g[3] = {gp.lo[0] + x[0], gp.lo[1] + x[1], gp.lo[2] + x[2]};
+      if (!xl_cross(c, 0, g)) continue;
+      T u[5];
+      const int rc = xl_restrict_cell<T>(c, g, t, u);
       if (rc) {
         xl_status(c, rc, P);
         return;
       }
-      buf[base + id] = v;
+      for (int q = 0; q < 5; q++) buf[q * mc3 + id] = u[q];
     }
-    base += nf;
+    for (int ax = 0; ax < 3; ax++) {
+      const int f0 = m[0] + (ax == 0), f1 = m[1] + (ax == 1), f2 = m[2] + (ax == 2);
+      const long long nf = (long long)f0 * f1 * f2;
+      for (long long id = threadIdx.x; id < nf; id += blockDim.x) {
+        const int x[3] = {(int)(id % f0) - 2, (int)((id / f0) % f1) - 2, (int)(id / ((long long)f0 * f1)) - 2};
+        if (own_face(ax, x)) continue;
+        const int g[3] = {gp.lo[0] + x[0], gp.lo[1] + x[1], gp.lo[2] + x[2]};
+        if (!xl_cross(c, 0, g)) continue;
+        T v;
+        const int rc = xl_restrict_face<T>(c, ax, g, t, &v);
+        if (rc) {
+          xl_status(c, rc, P);
+          return;
+        }
+        buf[fofs[ax] + id] = v;
+      }
+    }
+    return;
+  }
+  // prolongation: one thread per level-0 parent of the buffer's cells and
+  // faces; the parent's slopes and faces serve all its children
+  int c0[3], cn[3];
+  for (int d = 0; d < 3; d++) {
+    c0[d] = xl_floordiv(gp.lo[d] - 2, 2);
+    cn[d] = xl_floordiv(gp.lo[d] + n[d] + 2, 2) - c0[d] + 1;
+  }
+  const long long npar = (long long)cn[0] * cn[1] * cn[2];
+  for (long long id = threadIdx.x; id < npar; id += blockDim.x) {
+    const int C[3] = {c0[0] + (int)(id % cn[0]), c0[1] + (int)((id / cn[0]) % cn[1]),
+                      c0[2] + (int)(id / ((long long)cn[0] * cn[1]))};
+    const int f0[3] = {2 * C[0], 2 * C[1], 2 * C[2]};
+    // children in patch coordinates; all 8 share one level-1 block
+    const int xb[3] = {f0[0] - gp.lo[0], f0[1] - gp.lo[1], f0[2] - gp.lo[2]};
+    bool all_inside = true;
+    for (int d = 0; d < 3; d++)
+      if (xb[d] < 0 || xb[d] + 1 >= n[d]) all_inside = false;
+    if (all_inside || !xl_cross(c, 1, f0)) continue;
+    // cells: the parent and its slopes, once
+    bool any_cell = false;
+    for (int k = 0; k < 8; k++) {
+      const int x[3] = {xb[0] + (k & 1), xb[1] + ((k >> 1) & 1), xb[2] + (k >> 2)};
+      if (x[0] >= -2 && x[0] < n[0] + 2 && x[1] >= -2 && x[1] < n[1] + 2 && x[2] >= -2 && x[2] < n[2] + 2 &&
+          !interior(x))
+        any_cell = true;
+    }
+    int rc = DSP_OK;
+    if (any_cell) {
+      T uc[5], ul[5], ur[5], sl[3][5];
+      rc = xl_cell<T>(c, 0, C, t, uc);
+      for (int d = 0; d < 3 && rc == DSP_OK; d++) {
+        int Cm[3] = {C[0], C[1], C[2]}, Cp[3] = {C[0], C[1], C[2]};
+        Cm[d] -= 1;
+        Cp[d] += 1;
+        rc = xl_cell<T>(c, 0, Cm, t, ul);
+        if (rc == DSP_OK) rc = xl_cell<T>(c, 0, Cp, t, ur);
+        if (rc == DSP_OK)
+          for (int q = 0; q < 5; q++) sl[d][q] = mc(uc[q] - ul[q], ur[q] - uc[q]);
+      }
+      if (rc) {
+        xl_status(c, rc, P);
+        return;
+      }
+      for (int k = 0; k < 8; k++) {
+        const int x[3] = {xb[0] + (k & 1), xb[1] + ((k >> 1) & 1), xb[2] + (k >> 2)};
+        if (x[0] < -2 || x[0] >= n[0] + 2 || x[1] < -2 || x[1] >= n[1] + 2 || x[2] < -2 || x[2] >= n[2] + 2 ||
+            interior(x))
+          continue;
+        const long long bi = ((long long)(x[2] + 2) * m[1] + (x[1] + 2)) * m[0] + (x[0] + 2);
+        for (int q = 0; q < 5; q++) {
+          const T a = (k & 1) ? sl[0][q] : -sl[0][q];
+          const T b = ((k >> 1) & 1) ? sl[1][q] : -sl[1][q];
+          const T e = (k >> 2) ? sl[2][q] : -sl[2][q];
+          buf[q * mc3 + bi] = uc[q] + T(0.25) * ((a + b) + e);
+        }
+      }
+    }
+    // faces: the parent's two faces per axis (one owner patch), once
+    for (int ax = 0; ax < 3; ax++) {
+      bool any_face = false;
+      for (int k = 0; k < 8; k++) {
+        const int x[3] = {xb[0] + (k & 1), xb[1] + ((k >> 1) & 1), xb[2] + (k >> 2)};
+        if (face_in_buf(ax, x) && !own_face(ax, x)) any_face = true;
+      }
+      if (!any_face) continue;
+      T lo, hi;
+      rc = xl_face<T>(c, 0, ax, C, 0, t, &lo);
+      if (rc == DSP_OK) rc = xl_face<T>(c, 0, ax, C, 1, t, &hi);
+      if (rc) {
+        xl_status(c, rc, P);
+        return;
+      }
+      for (int k = 0; k < 8; k++) {
+        const int kk[3] = {k & 1, (k >> 1) & 1, k >> 2};
+        const int x[3] = {xb[0] + kk[0], xb[1] + kk[1], xb[2] + kk[2]};
+        if (!face_in_buf(ax, x) || own_face(ax, x)) continue;
+        buf[face_index(ax, x)] = kk[ax] ? T(0.5) * (lo + hi) : lo;
+      }
+    }
   }
 }
 
