@@ -124,7 +124,8 @@ typedef struct {
 
 /* Counters of one dsp_advance call.  kernel_ms and kernel_launches are the
  * summed device time and the number of launches of the update kernel (only
- * when timing was requested); plan_launches counts the dispatcher kernels. */
+ * when timing was requested); plan_launches counts the dispatcher kernels
+ * (three per sweep) and, with two levels, the cross-level guard kernel. */
 typedef struct {
   int64_t patch_updates, cell_updates, sweeps, fallbacks;
   double t_min, t_max;

@@ -1,13 +1,13 @@
 // dsp_host.cu -- the C ABI (include/dispatch.h): context set-up, the sweep
 // dispatcher, state transfer, diagnostics and save/load.
 //
-// Dispatcher (DISPATCH I, Sec. 3 B): each sweep runs one plan kernel and one
-// update kernel on the context's stream.  The plan kernel first publishes the
+// Dispatcher (DISPATCH I, Sec. 3 B): each sweep runs three dispatcher kernels
+// and the update kernel on the context's stream.  The first publishes the
 // previous sweep (new slice becomes the newest, patch time += dt, schedule log
-// entry), then finds every patch that is ready by Eq. (1) with grace 0
-// (t_P < t_end and t_P <= t_N for every neighbour N), gives it its local
-// Courant step, and compacts the ready patches in index order.  The update
-// kernel then advances every ready patch from the pre-sweep slices.  Because
+// entry), the second finds every patch that is ready by Eq. (1) with grace 0
+// (t_P < t_end and t_P <= t_N for every neighbour N) and gives it its local
+// Courant step, the third compacts the ready patches in index order.  The
+// update kernel then advances every ready patch from the pre-sweep slices.  Because
 // ready neighbours share their time and every read touches only a
 // neighbour's two newest slices, any order of execution inside a sweep gives
 // the same result, and sweeping gives the same per-patch schedule as a
@@ -45,7 +45,8 @@ struct dsp_ctx {
   // device allocations
   void *slab;
   double *t_slot, *smax_slot, *dt_last, *dtR;
-  int *latest, *nbl_off_d, *nbl_d, *R, *ctl, *omap_d[2], *gmap0_d, *work_off_d;
+  int *latest, *nbl_off_d, *nbl_d, *R, *ctl, *omap_d[2], *gmap0_d, *work_off_d, *rflag;
+  double *rdt;
   long long *gofs_d;
   void *gbuf;
   PatchGeo *geo_d;
@@ -103,20 +104,22 @@ __device__ void set_status(const DevCtx &c, int code, int P) {
 }
 
 constexpr int PLAN_NT = 1024;
+constexpr int EVAL_NT = 256;
 
-__global__ void __launch_bounds__(PLAN_NT) plan_kernel(DevCtx c, double t_end, int global_mode, int publish_only) {
-  __shared__ int s_wsum[PLAN_NT / 32];
-  __shared__ int s_base, s_notdone, s_total;
-  __shared__ unsigned long long s_dtmin;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int ns = c.ns;
-  // 1. publish the previous sweep
-  __shared__ unsigned long long s_cells;
-  if (tid == 0) s_cells = 0;
-  __syncthreads();
+// Dispatcher step, part 1 (one thread per patch of the previous ready list):
+// publish the previous sweep -- the new slice becomes the newest, its time
+// is t + dt, its signal speed the one the update kernel reduced, and the
+// schedule log gets (P, t, dt).  Cell counts are summed into the counters;
+// the other counters move in part 3, after every entry is written.
+__global__ void __launch_bounds__(EVAL_NT) plan_publish_kernel(DevCtx c) {
   const int nprev = c.ctl[CTL_NREADY];
   const long long s0 = c.cnt[CNT_NSCHED];
-  for (int r = tid; r < nprev; r += PLAN_NT) {
+  const int ns = c.ns;
+  __shared__ unsigned long long s_cells;
+  if (threadIdx.x == 0) s_cells = 0;
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nprev) {
     const int P = c.R[r];
     atomicAdd(&s_cells, (unsigned long long)c.geo[P].n[0] * c.geo[P].n[1] * c.geo[P].n[2]);
     const double dt = c.dtR[r];
@@ -134,37 +137,59 @@ __global__ void __launch_bounds__(PLAN_NT) plan_kernel(DevCtx c, double t_end, i
     }
   }
   __syncthreads();
+  if (threadIdx.x == 0 && s_cells) atomicAdd((unsigned long long *)&c.cnt[CNT_CELL_UPDATES], s_cells);
+}
+
+// Part 2 (one thread per patch): Eq. (1) with grace 0 and the local step of
+// every ready patch; rflag/rdt per patch, and whether any patch is behind
+// t_end.
+__global__ void __launch_bounds__(EVAL_NT) plan_ready_kernel(DevCtx c, double t_end) {
+  if (c.ctl[CTL_STATUS] != 0) return;
+  const int P = blockIdx.x * blockDim.x + threadIdx.x;
+  if (P >= c.np) return;
+  int flag = 0;
+  double dtP = 0.0;
+  const double t = c.t_slot[(long long)P * c.ns + c.latest[P]];
+  if (t < t_end) {
+    c.ctl[CTL_NOTDONE] = 1;
+    double tr;
+    if (is_ready<false>(c, P, t_end, &tr)) {
+      const int rc = patch_dt<false>(c, P, t, t_end, &dtP);
+      if (rc != DSP_OK) set_status(c, rc, P);
+      else flag = 1;
+    }
+  }
+  c.rflag[P] = flag;
+  c.rdt[P] = dtP;
+}
+
+// Part 3 (one block): counters of the published sweep; the ready list in
+// patch order (ballot/popc scan), the global step (smallest ready step) in
+// global-step mode, the work offsets, and done / deadlock.
+__global__ void __launch_bounds__(PLAN_NT) plan_compact_kernel(DevCtx c, int global_mode, int publish_only) {
+  __shared__ int s_wsum[PLAN_NT / 32];
+  __shared__ int s_base, s_total;
+  __shared__ unsigned long long s_dtmin;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) {
+    const int nprev = c.ctl[CTL_NREADY];
     if (nprev > 0) {
       c.cnt[CNT_NSCHED] += nprev;
       c.cnt[CNT_PATCH_UPDATES] += nprev;
-      c.cnt[CNT_CELL_UPDATES] += (long long)s_cells;
       c.cnt[CNT_SWEEPS] += 1;
     }
     c.ctl[CTL_NREADY] = 0;
     s_base = 0;
-    s_notdone = 0;
     s_dtmin = 0x7ff0000000000000ull;  // +inf
   }
   __syncthreads();
+  const int notdone = c.ctl[CTL_NOTDONE];
+  __syncthreads();
+  if (tid == 0) c.ctl[CTL_NOTDONE] = 0;
   if (publish_only || c.ctl[CTL_STATUS] != 0) return;
-  // 2. ready set, steps, compaction in patch order
   for (int chunk = 0; chunk < c.np; chunk += PLAN_NT) {
     const int P = chunk + tid;
-    int flag = 0;
-    double dtP = 0.0;
-    if (P < c.np) {
-      const double t = c.t_slot[(long long)P * ns + c.latest[P]];
-      if (t < t_end) {
-        s_notdone = 1;
-        double tr;
-        if (is_ready<false>(c, P, t_end, &tr)) {
-          const int rc = patch_dt<false>(c, P, t, t_end, &dtP);
-          if (rc != DSP_OK) set_status(c, rc, P);
-          else flag = 1;
-        }
-      }
-    }
+    const int flag = P < c.np ? c.rflag[P] : 0;
     const unsigned bal = __ballot_sync(0xffffffffu, flag);
     if (lane == 0) s_wsum[wid] = __popc(bal);
     __syncthreads();
@@ -181,6 +206,7 @@ __global__ void __launch_bounds__(PLAN_NT) plan_kernel(DevCtx c, double t_end, i
     }
     __syncthreads();
     if (flag) {
+      const double dtP = c.rdt[P];
       const int idx = s_base + s_wsum[wid] + __popc(bal & ((1u << lane) - 1u));
       c.R[idx] = P;
       c.dtR[idx] = dtP;
@@ -235,7 +261,7 @@ __global__ void __launch_bounds__(PLAN_NT) plan_kernel(DevCtx c, double t_end, i
     } else {
       c.ctl[CTL_NREADY] = nr;
       if (nr == 0) {
-        if (!s_notdone) c.ctl[CTL_DONE] = 1;
+        if (!notdone) c.ctl[CTL_DONE] = 1;
         else set_status(c, DSP_ERR_DEADLOCK, -1);
       }
     }
@@ -412,6 +438,16 @@ int launch_queue(dsp_ctx *c, double t_end) { return c->var->launch_queue(c->d, c
 
 int launch_update(dsp_ctx *c) { return c->var->launch_update(c->d, c->grid_update, c->stream); }
 
+// One dispatcher step: publish the previous sweep, then (unless
+// publish_only) find the next ready list and its steps.
+int launch_plan(dsp_ctx *c, double t_end, int global_mode, int publish_only) {
+  const int np = c->d.np;
+  plan_publish_kernel<<<(np + EVAL_NT - 1) / EVAL_NT, EVAL_NT, 0, c->stream>>>(c->d);
+  if (!publish_only) plan_ready_kernel<<<(np + EVAL_NT - 1) / EVAL_NT, EVAL_NT, 0, c->stream>>>(c->d, t_end);
+  plan_compact_kernel<<<1, PLAN_NT, 0, c->stream>>>(c->d, global_mode, publish_only);
+  return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
+}
+
 // Cross-level guard values of the ready patches that have some (two levels
 // only), after the plan kernel and before the update kernel of a sweep.
 int launch_xlevel(dsp_ctx *c) {
@@ -538,7 +574,7 @@ int transfer(dsp_ctx *c, int first, int count, const void *U, const void *bx, co
 
 void free_all(dsp_ctx *c) {
   void *ptrs[] = {c->slab,    c->t_slot,  c->smax_slot, c->dt_last, c->dtR,     c->latest,  c->omap_d[0],
-                  c->omap_d[1], c->gmap0_d, c->gofs_d, c->gbuf,
+                  c->omap_d[1], c->gmap0_d, c->gofs_d, c->gbuf, c->rflag, c->rdt,
                   c->work_off_d, c->geo_d, c->coff_d,
                   c->nbl_off_d, c->nbl_d, c->R,       c->ctl,     c->smax_new, c->cnt,    c->sched,
                   c->staging, c->q_patch, c->q_reads, c->p_state, c->tiles_done, c->q_dt, c->q_seq,
@@ -855,6 +891,7 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
             alloc((void **)&c->nbl_off_d, sizeof(int) * (npatch + 1)) &&
             alloc((void **)&c->nbl_d, sizeof(int) * std::max<size_t>(1, c->nbl.size())) &&
             alloc((void **)&c->R, sizeof(int) * npatch) && alloc((void **)&c->ctl, sizeof(int) * CTL_COUNT) &&
+            alloc((void **)&c->rflag, sizeof(int) * npatch) && alloc((void **)&c->rdt, sizeof(double) * npatch) &&
             alloc((void **)&c->smax_new, sizeof(unsigned long long) * npatch) &&
             alloc((void **)&c->cnt, sizeof(long long) * CNT_COUNT) &&
             alloc((void **)&c->sched, sizeof(dsp_sched_entry) * std::max<long long>(1, cap));
@@ -891,6 +928,8 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.nbl_off = c->nbl_off_d;
   d.nbl = c->nbl_d;
   d.R = c->R;
+  d.rflag = c->rflag;
+  d.rdt = c->rdt;
   d.dtR = c->dtR;
   d.smax_new = c->smax_new;
   d.ctl = c->ctl;
@@ -976,8 +1015,7 @@ int advance_queue(dsp_ctx *c, double t_end, const long long *c0, dsp_stats *out)
     for (int i = 0; i < 2; i++) CK(cudaEventCreate(&c->ev[i]));
     c->nev = 2;
   }
-  plan_kernel<<<1, PLAN_NT, 0, c->stream>>>(c->d, t_end, 0, 0);
-  CK(cudaGetLastError());
+  if (launch_plan(c, t_end, 0, 0)) return fail(c, DSP_ERR_CUDA, "dispatcher kernel launch failed");
   queue_init_kernel<<<1, 1024, 0, c->stream>>>(c->d, t_end);
   CK(cudaGetLastError());
   if (timing) CK(cudaEventRecord(c->ev[0], c->stream));
@@ -1000,7 +1038,7 @@ int advance_queue(dsp_ctx *c, double t_end, const long long *c0, dsp_stats *out)
     out->status = st;
     out->kernel_ms = timing ? ms : 0.0;
     out->kernel_launches = 1;
-    out->plan_launches = 2;
+    out->plan_launches = 4;  // the three dispatcher kernels and the queue set-up
     std::vector<double> t((size_t)c->d.np);
     if (dsp_get_times(c, t.data(), nullptr) == DSP_OK) {
       out->t_min = *std::min_element(t.begin(), t.end());
@@ -1043,8 +1081,7 @@ extern "C" int dsp_advance(dsp_ctx *c, double t_end, int64_t max_sweeps, dsp_sta
   // timed as a whole (its plan kernels are a few microseconds each)
   auto issue_batch = [&](long long nb, bool events) -> int {
     for (long long s = 0; s < nb; s++) {
-      plan_kernel<<<1, PLAN_NT, 0, c->stream>>>(c->d, t_end, global_mode, 0);
-      CK(cudaGetLastError());
+      if (launch_plan(c, t_end, global_mode, 0)) return fail(c, DSP_ERR_CUDA, "dispatcher kernel launch failed");
       if (launch_xlevel(c)) return fail(c, DSP_ERR_CUDA, "cross-level guard kernel launch failed");
       if (events) CK(cudaEventRecord(c->ev[2 * s], c->stream));
       const int r2 = launch_update(c);
@@ -1082,7 +1119,7 @@ extern "C" int dsp_advance(dsp_ctx *c, double t_end, int64_t max_sweeps, dsp_sta
       if (rc) return rc;
     }
     const bool graphed = c->prm.graph && nb == batch;
-    plans += nb;
+    plans += nb * (c->d.nlev > 1 ? 4 : 3);  // publish, readiness, compaction (+ cross-level guards)
     done_sweeps += nb;
     rc = read_status(c);
     if (rc) return rc;
@@ -1101,9 +1138,8 @@ extern "C" int dsp_advance(dsp_ctx *c, double t_end, int64_t max_sweeps, dsp_sta
     if (c->h_ctl[CTL_STATUS] != 0 || c->h_ctl[CTL_DONE]) break;
     if (max_sweeps > 0 && done_sweeps >= max_sweeps) break;
   }
-  plan_kernel<<<1, PLAN_NT, 0, c->stream>>>(c->d, t_end, global_mode, 1);
-  CK(cudaGetLastError());
-  plans++;
+  if (launch_plan(c, t_end, global_mode, 1)) return fail(c, DSP_ERR_CUDA, "dispatcher kernel launch failed");
+  plans += 2;  // publish and compaction
   rc = read_status(c);
   if (rc) return rc;
   long long c1[CNT_COUNT];
@@ -1318,8 +1354,10 @@ extern "C" int dsp_autotune(dsp_ctx *c, int32_t reps, int32_t *chosen, double *m
     // plan the next sweep (nothing is published: the ready list is dropped
     // afterwards, and the update kernel only writes the patches' next slot)
     CK(cudaMemsetAsync(c->ctl + CTL_NREADY, 0, sizeof(int), c->stream));
-    plan_kernel<<<1, PLAN_NT, 0, c->stream>>>(c->d, INFINITY, c->prm.time_mode == 0, 0);
-    CK(cudaGetLastError());
+    if (launch_plan(c, INFINITY, c->prm.time_mode == 0, 0)) {
+      rc = fail(c, DSP_ERR_CUDA, "dispatcher kernel launch failed");
+      break;
+    }
     rc = launch_xlevel(c);
     if (rc) break;
     rc = launch_update(c);

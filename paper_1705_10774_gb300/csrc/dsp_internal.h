@@ -14,6 +14,7 @@ enum Ctl : int {
   CTL_DONE = 2,     // 1 once no patch is behind t_end
   CTL_ERRP = 3,     // patch of the first error
   CTL_ERRC = 4,     // cell (linear, patch-local) of the first error
+  CTL_NOTDONE = 5,  // set by the readiness pass when some patch is behind t_end
   CTL_COUNT = 8
 };
 
@@ -77,6 +78,8 @@ struct DevCtx {
   const int *nbl_off;      // [np+1] CSR of distinct neighbours (self excluded)
   const int *nbl;
   int *R;                  // [np] ready list of the current sweep
+  int *rflag;              // [np] readiness of each patch (dispatcher scratch)
+  double *rdt;             // [np] its step
   double *dtR;             // [np] step of each ready patch
   unsigned long long *smax_new;  // [np] signal speed of the slice being written (double bits)
   int *ctl;                // [CTL_COUNT]
