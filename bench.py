@@ -43,11 +43,12 @@ HBM_FALLBACK_GBS = 6800.0
 F64_PRECISION = 2
 
 # DRAM bytes (read + write) per update-kernel launch of the full workload,
-# from ncu's dram__bytes_read.sum + dram__bytes_write.sum on a 216-patch
-# capture of the same kernel, scaled by cells; None until taken on the
-# current kernel.
-TRAFFIC_F64 = (551.541504e6 + 421.864960e6) * 512 / 216   # variant 3 (FP64 FMA)
-TRAFFIC_F32 = 631.432960e6 + 510.070528e6                  # variant 5, full workload
+# by compiled variant, from ncu's dram__bytes_read.sum + dram__bytes_write.sum
+# (FP64: a 216-patch capture of the same kernel, scaled by cells; FP32: the
+# full workload); a variant without an entry reports null.
+TRAFFIC_F64 = {2: (550.418176e6 + 420.959488e6) * 512 / 216, 3: (551.541504e6 + 421.864960e6) * 512 / 216,
+               4: (550.655744e6 + 421.330688e6) * 512 / 216}
+TRAFFIC_F32 = {5: 631.432960e6 + 510.070528e6}
 
 
 def radius2_guard_fraction(n):
@@ -268,7 +269,8 @@ def gpu_arm(args):
     value = cells_all / (ms_max * 1e-3)
     kavg = st["kernel_ms"] / max(st["kernel_launches"], 1)
     roof = rooflines(ncells, 8, kavg, peak, peak_kind)
-    roof.update({"traffic": TRAFFIC_F64, "kernel": "update_kernel variant %d" % g.tuned[0], "kernel_ms_avg": kavg,
+    roof.update({"traffic": TRAFFIC_F64.get(g.tuned[0]), "kernel": "update_kernel variant %d" % g.tuned[0],
+                 "kernel_ms_avg": kavg,
                  "autotune_ms_per_variant": g.tuned[1]})
     g.close()
 
@@ -289,7 +291,7 @@ def gpu_arm(args):
         v32 = sum_over_ranks(td, float(st32["cell_updates"])) / (ms32_max * 1e-3)
         k32 = st32["kernel_ms"] / max(st32["kernel_launches"], 1)
         r32 = rooflines(ncells, 4, k32, peak, peak_kind)
-        r32.update({"traffic": TRAFFIC_F32, "kernel": "update_kernel variant %d" % g32.tuned[0],
+        r32.update({"traffic": TRAFFIC_F32.get(g32.tuned[0]), "kernel": "update_kernel variant %d" % g32.tuned[0],
                     "kernel_ms_avg": k32, "autotune_ms_per_variant": g32.tuned[1]})
         forms["f32"] = {"value": v32, "ms_per_step": ms32_max / args.steps, "dtype": "f32", "roofline": r32}
         g32.close()
