@@ -458,6 +458,8 @@ def lts_arm(args):
             lv, cnt = np.unique(dts, return_counts=True)
             r["dt_levels"] = int(len(lv))
             r["dt_ratio_max_min"] = float(lv.max() / lv.min())
+            # patch updates per step size (the clipped last steps to t_end included)
+            r["updates_per_dt"] = {"%.6e" % a: int(b) for a, b in zip(lv, cnt)}
         out[name] = r
         g.close()
     out["lts_over_global_cell_updates"] = out["f32_queue"]["cell_updates"] / out["f32_global"]["cell_updates"]
@@ -476,7 +478,7 @@ def orszag_tang_arm(args):
     del f
     stream = torch.cuda.current_stream()
     kw = dict(gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len, time_mode=0,
-              stream=stream.cuda_stream)
+              graph=1, stream=stream.cuda_stream)
     res = {}
     for name, prec in (("f64", F64_PRECISION), ("f32", 1)):
         g = Dispatch(lay.n, lay.lo, precision=prec, **kw)
