@@ -120,9 +120,12 @@ static double cfast(double gamma, double irho, double p, double bn, double bt1, 
   return sqrt(0.5 * (s + sqrt(disc)));
 }
 
-/* Monotonised-central limited slope. */
+/* Monotonised-central limited slope: zero when the one-sided differences
+ * have opposite signs or one of them is zero (a sign test, so no product is
+ * formed that could underflow), else the smallest of twice either difference
+ * and their mean, with their sign. */
 static double mc(double dl, double dr) {
-  if (dl * dr <= 0.0) return 0.0;
+  if ((dl > 0.0 && dr < 0.0) || (dl < 0.0 && dr > 0.0) || dl == 0.0 || dr == 0.0) return 0.0;
   double s = fmin(fmin(2.0 * fabs(dl), 2.0 * fabs(dr)), 0.5 * fabs(dl + dr));
   return dl > 0.0 ? s : -s;
 }

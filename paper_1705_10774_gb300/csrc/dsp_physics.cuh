@@ -22,7 +22,53 @@ template <> __device__ __forceinline__ double tmin<double>(double a, double b) {
 template <> __device__ __forceinline__ double tmax<double>(double a, double b) { return fmax(a, b); }
 template <> __device__ __forceinline__ float tmin<float>(float a, float b) { return fminf(a, b); }
 template <> __device__ __forceinline__ float tmax<float>(float a, float b) { return fmaxf(a, b); }
-template <typename T> __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
+// Sign-bit and ordering tests on the bit patterns of floating-point values,
+// done with integer instructions: on GB300 every FP64 compare, min or max
+// takes a slot of the (narrow) FP64 pipe, while these run on the integer
+// units.  Each gives exactly the result of the floating-point form it
+// replaces, for every input stated beside it.
+template <typename T>
+struct FBits;
+template <>
+struct FBits<double> {
+  using I = long long;
+  static __device__ __forceinline__ I of(double x) { return __double_as_longlong(x); }
+  static __device__ __forceinline__ double to(I i) { return __longlong_as_double(i); }
+  static constexpr I MAG = 0x7fffffffffffffffll, INF = 0x7ff0000000000000ll;
+};
+template <>
+struct FBits<float> {
+  using I = int;
+  static __device__ __forceinline__ I of(float x) { return __float_as_int(x); }
+  static __device__ __forceinline__ float to(I i) { return __int_as_float(i); }
+  static constexpr I MAG = 0x7fffffff, INF = 0x7f800000;
+};
+// |a| (as fabs: the sign bit cleared, for every input)
+template <typename T>
+__device__ __forceinline__ T tabs(T a) {
+  using B = FBits<T>;
+  return B::to(B::of(a) & B::MAG);
+}
+// a > 0 (for every input, NaN included)
+template <typename T>
+__device__ __forceinline__ bool tpos(T a) {
+  using B = FBits<T>;
+  const typename B::I i = B::of(a);
+  return i > 0 && i <= B::INF;
+}
+// a < 0 (for every input, NaN included)
+template <typename T>
+__device__ __forceinline__ bool tneg(T a) {
+  using B = FBits<T>;
+  const typename B::I i = B::of(a), m = i & B::MAG;
+  return i < 0 && m != 0 && m <= B::INF;
+}
+// min(a, b) for a, b >= +0 or NaN (as fmin: a NaN operand yields the other)
+template <typename T>
+__device__ __forceinline__ T tmin_nonneg(T a, T b) {
+  using B = FBits<T>;
+  return B::of(a) <= B::of(b) ? a : b;
+}
 __device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ float tsqrt(float a) { return sqrtf(a); }
 
@@ -55,7 +101,7 @@ __device__ __forceinline__ T cfast(T gamma, T irho, T p, T bn, T bt1, T bt2) {
   T ca2 = bn * bn * irho;
   T s = a2 + bb;
   T disc = s * s - T(4) * a2 * ca2;
-  if (disc < T(0)) disc = T(0);
+  if (tneg(disc)) disc = T(0);
   return tsqrt(T(0.5) * (s + tsqrt(disc)));
 }
 
@@ -69,12 +115,17 @@ __device__ __forceinline__ T signal_sum(const T W[8], T gamma) {
   return (tabs(W[VX]) + cx) + (tabs(W[VY]) + cy) + (tabs(W[VZ]) + cz);
 }
 
-// Monotonised-central limited slope.
+// Monotonised-central limited slope: zero when the one-sided differences
+// have opposite signs or one is zero, else the smallest of twice either and
+// their mean, with their sign.  The tests are on sign bits (the same result
+// as comparisons for every non-NaN input).
 template <typename T>
 __device__ __forceinline__ T mc(T dl, T dr) {
-  if (dl * dr <= T(0)) return T(0);
-  T s = tmin(tmin(T(2) * tabs(dl), T(2) * tabs(dr)), T(0.5) * tabs(dl + dr));
-  return dl > T(0) ? s : -s;
+  using B = FBits<T>;
+  const typename B::I a = B::of(dl), b = B::of(dr);
+  if ((a & B::MAG) == 0 || (b & B::MAG) == 0 || (a ^ b) < 0) return T(0);
+  const T s = tmin_nonneg(tmin_nonneg(T(2) * tabs(dl), T(2) * tabs(dr)), T(0.5) * tabs(dl + dr));
+  return a < 0 ? B::to(B::of(s) ^ ~B::MAG) : s;
 }
 
 // Hancock half-step predictor in primitive form with d/dx_d -> dW_d, h = dt/(2dx).

@@ -472,7 +472,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
           const T *d3 = d == 0 ? dX : d == 1 ? dY : dZ;
           const T rp_ = ws[RHO] + half * d3[RHO], rm_ = ws[RHO] - half * d3[RHO];
           const T pp_ = ws[PR] + half * d3[PR], pm_ = ws[PR] - half * d3[PR];
-          if (!(rp_ > T(0)) || !(rm_ > T(0)) || !(pp_ > T(0)) || !(pm_ > T(0))) bad = true;
+          if (!tpos(rp_) || !tpos(rm_) || !tpos(pp_) || !tpos(pm_)) bad = true;
         }
         if (bad) {
           atomicAdd(&s_fallback, 1);

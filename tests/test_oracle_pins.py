@@ -374,3 +374,15 @@ def test_guard_time_interpolation_weight_and_direction():
     o.set_slot(1, 1, 4 * h, *patch_state(3.0))
     U2 = o.update_patch(0, h)[0]
     assert not np.array_equal(U2, U0)
+
+
+def test_mc_limiter_sign_test_does_not_underflow():
+    """Differences of one sign whose product would underflow to zero still
+    get a limited slope (the extremum test is a sign test), and the result
+    scales with them."""
+    for scale in (1e-170, 1e-200, 1e-300):
+        s = O.mc(1.0 * scale, 2.0 * scale)
+        assert s == 1.5 * scale
+        assert O.mc(-1.0 * scale, -3.0 * scale) == -2.0 * scale
+    assert O.mc(1e-200, -1e-200) == 0.0
+    assert O.mc(-0.0, 1.0) == 0.0 and O.mc(1.0, -0.0) == 0.0
