@@ -46,9 +46,9 @@ F64_PRECISION = 2
 # by compiled variant, from ncu's dram__bytes_read.sum + dram__bytes_write.sum
 # (FP64: a 216-patch capture of the same kernel, scaled by cells; FP32: the
 # full workload); a variant without an entry reports null.
-TRAFFIC_F64 = {2: (550.418176e6 + 420.959488e6) * 512 / 216, 3: (551.541504e6 + 421.864960e6) * 512 / 216,
-               4: (550.655744e6 + 421.330688e6) * 512 / 216}
-TRAFFIC_F32 = {5: 631.432960e6 + 510.070528e6}
+TRAFFIC_F64 = {2: (550.253568e6 + 420.952832e6) * 512 / 216, 3: (547.967488e6 + 420.902144e6) * 512 / 216,
+               4: (549.530368e6 + 420.683776e6) * 512 / 216}
+TRAFFIC_F32 = {5: 624.325888e6 + 509.780992e6}
 
 
 def radius2_guard_fraction(n):
