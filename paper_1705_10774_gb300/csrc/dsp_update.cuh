@@ -3,10 +3,11 @@
 // One work item is a tile of one ready patch: TX x TY columns of cells and a
 // run of tz planes along z.  The block marches through the planes; for each
 // plane it
-//   A  gathers the next plane of the padded tile (radius 2) from the patch's
+//   A  takes the next plane of the padded tile (radius 2) from the patch's
 //      own newest slice and its neighbours' slices, interpolating linearly in
 //      time where a neighbour is ahead (DISPATCH I, Sec. 3 A), and converts to
-//      primitive variables;
+//      primitive variables (the plane's copies were started asynchronously
+//      one plane earlier, so only the time blends remain to compute);
 //   B  computes MC-limited slopes and the Hancock half-step predictor;
 //   C  computes HLL fluxes through the x- and y-faces of the plane and the
 //      z-faces below it;
