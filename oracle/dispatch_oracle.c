@@ -73,6 +73,7 @@ typedef struct {
   int64_t L[2][3];                   /* cells per axis of the periodic box on each level */
   int nlev;                          /* 1, or 2 when level-1 patches exist */
   int g, nslot, time_mode, disp_mode;
+  int riemann; /* face flux: 0 HLL, 1 HLLD */
   int64_t nsched, capsched;
   int64_t *s_patch;
   double *s_t, *s_dt;
@@ -220,6 +221,140 @@ static void hll(const double WL[8], const double WR[8], int d, double gamma, dou
   S[1] = SR;
 }
 
+/* HLLD flux (Miyoshi & Kusano 2005) through a face with normal axis d: the
+ * HLL outer speeds S_L, S_R (Davis estimates from the fast speeds, as in
+ * hll), a contact at S_M with one total pressure pT* across the fan, two
+ * rotational (Alfven) waves at S_M -+ |Bn|/sqrt(rho*), and the flux of the
+ * region of the fan that holds x/t = 0.  Components as in hll (lab-frame
+ * mass, momentum, energy, then the two tangential induction fluxes); S[0..1]
+ * are S_L, S_R.  In the normal frame a state is (rho, u, v, w, p) with
+ * tangential field (By, Bz) and the common normal field Bx.  Where
+ * rho_a (S_a - u_a)(S_a - S_M) - Bx^2 vanishes (to 1e-12 of
+ * rho_a (S_a - u_a)^2 + Bx^2) the star state keeps the tangential velocity
+ * and field of its side. */
+static void hlld_fan(const double WL[8], const double WR[8], int d, double gamma, double F[7], double S[2],
+                     double *fan) {
+  int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  double igm1 = 1.0 / (gamma - 1.0);
+  double bx = 0.5 * (WL[BX + d] + WR[BX + d]);
+  double rho[2], u[2], v[2], w[2], by[2], bz[2], E[2], PT[2], vB[2], c[2];
+  double Fs[2][7], Us[2][7];
+  for (int a = 0; a < 2; a++) {
+    const double *W = a ? WR : WL;
+    rho[a] = W[RHO]; u[a] = W[VX + d]; v[a] = W[VX + t1]; w[a] = W[VX + t2];
+    by[a] = W[BX + t1]; bz[a] = W[BX + t2];
+    double p = W[PR];
+    double v2 = u[a] * u[a] + v[a] * v[a] + w[a] * w[a];
+    double B2 = bx * bx + by[a] * by[a] + bz[a] * bz[a];
+    E[a] = p * igm1 + 0.5 * rho[a] * v2 + 0.5 * B2;
+    PT[a] = p + 0.5 * B2;
+    vB[a] = u[a] * bx + v[a] * by[a] + w[a] * bz[a];
+    c[a] = cfast(gamma, 1.0 / rho[a], p, bx, by[a], bz[a]);
+    Us[a][0] = rho[a]; Us[a][1] = rho[a] * u[a]; Us[a][2] = rho[a] * v[a]; Us[a][3] = rho[a] * w[a];
+    Us[a][4] = E[a]; Us[a][5] = by[a]; Us[a][6] = bz[a];
+    Fs[a][0] = rho[a] * u[a];
+    Fs[a][1] = rho[a] * u[a] * u[a] + PT[a] - bx * bx;
+    Fs[a][2] = rho[a] * u[a] * v[a] - bx * by[a];
+    Fs[a][3] = rho[a] * u[a] * w[a] - bx * bz[a];
+    Fs[a][4] = (E[a] + PT[a]) * u[a] - bx * vB[a];
+    Fs[a][5] = u[a] * by[a] - v[a] * bx;
+    Fs[a][6] = u[a] * bz[a] - w[a] * bx;
+  }
+  double SL = fmin(u[0] - c[0], u[1] - c[1]);
+  double SR = fmax(u[0] + c[0], u[1] + c[1]);
+  double Fr[7];
+  if (SL >= 0.0) {
+    for (int k = 0; k < 7; k++) Fr[k] = Fs[0][k];
+  } else if (SR <= 0.0) {
+    for (int k = 0; k < 7; k++) Fr[k] = Fs[1][k];
+  } else {
+    double Sa[2] = {SL, SR};
+    double dl = (SL - u[0]) * rho[0], dr = (SR - u[1]) * rho[1];
+    double iden = 1.0 / (dr - dl);
+    double SM = ((dr * u[1] - dl * u[0]) - PT[1] + PT[0]) * iden;
+    double PTs = ((dr * PT[0] - dl * PT[1]) + dl * dr * (u[1] - u[0])) * iden;
+    double rs[2], vs[2], ws[2], bys[2], bzs[2], Es[2], sr[2];
+    for (int a = 0; a < 2; a++) {
+      double su = Sa[a] - u[a];
+      rs[a] = rho[a] * su / (Sa[a] - SM);
+      double den = rho[a] * su * (Sa[a] - SM) - bx * bx;
+      double ref = rho[a] * su * su + bx * bx;
+      if (fabs(den) <= 1e-12 * ref) {
+        vs[a] = v[a]; ws[a] = w[a]; bys[a] = by[a]; bzs[a] = bz[a];
+      } else {
+        double iv = 1.0 / den;
+        double fv = bx * (SM - u[a]) * iv;
+        double fb = (rho[a] * su * su - bx * bx) * iv;
+        vs[a] = v[a] - by[a] * fv;
+        ws[a] = w[a] - bz[a] * fv;
+        bys[a] = by[a] * fb;
+        bzs[a] = bz[a] * fb;
+      }
+      double vBs = SM * bx + vs[a] * bys[a] + ws[a] * bzs[a];
+      Es[a] = ((su * E[a] - PT[a] * u[a] + PTs * SM) + bx * (vB[a] - vBs)) / (Sa[a] - SM);
+      sr[a] = sqrt(rs[a]);
+    }
+    double aB = fabs(bx);
+    double SsL = SM - aB / sr[0], SsR = SM + aB / sr[1];
+    /* star states */
+    double Ust[2][7];
+    for (int a = 0; a < 2; a++) {
+      Ust[a][0] = rs[a]; Ust[a][1] = rs[a] * SM; Ust[a][2] = rs[a] * vs[a]; Ust[a][3] = rs[a] * ws[a];
+      Ust[a][4] = Es[a]; Ust[a][5] = bys[a]; Ust[a][6] = bzs[a];
+    }
+    /* double-star states (between the rotational waves) */
+    double sg = bx > 0.0 ? 1.0 : bx < 0.0 ? -1.0 : 0.0;
+    double isum = 1.0 / (sr[0] + sr[1]);
+    double vss = ((sr[0] * vs[0] + sr[1] * vs[1]) + (bys[1] - bys[0]) * sg) * isum;
+    double wss = ((sr[0] * ws[0] + sr[1] * ws[1]) + (bzs[1] - bzs[0]) * sg) * isum;
+    double byss = ((sr[0] * bys[1] + sr[1] * bys[0]) + sr[0] * sr[1] * (vs[1] - vs[0]) * sg) * isum;
+    double bzss = ((sr[0] * bzs[1] + sr[1] * bzs[0]) + sr[0] * sr[1] * (ws[1] - ws[0]) * sg) * isum;
+    double vBss = SM * bx + vss * byss + wss * bzss;
+    double Uss[2][7];
+    for (int a = 0; a < 2; a++) {
+      double vBsa = SM * bx + vs[a] * bys[a] + ws[a] * bzs[a];
+      double Ess = a == 0 ? Es[0] - sr[0] * (vBsa - vBss) * sg : Es[1] + sr[1] * (vBsa - vBss) * sg;
+      Uss[a][0] = rs[a]; Uss[a][1] = rs[a] * SM; Uss[a][2] = rs[a] * vss; Uss[a][3] = rs[a] * wss;
+      Uss[a][4] = Ess; Uss[a][5] = byss; Uss[a][6] = bzss;
+    }
+    if (fan) {
+      /* the whole fan, for checking: speeds S_L, S*_L, S_M, S*_R, S_R, the
+       * normal-frame states U*_L, U**_L, U**_R, U*_R, and pT* */
+      fan[0] = SL; fan[1] = SsL; fan[2] = SM; fan[3] = SsR; fan[4] = SR;
+      fan[33] = PTs;
+      for (int k = 0; k < 7; k++) {
+        fan[5 + k] = Ust[0][k];
+        fan[12 + k] = Uss[0][k];
+        fan[19 + k] = Uss[1][k];
+        fan[26 + k] = Ust[1][k];
+      }
+    }
+    if (SsL >= 0.0) {
+      for (int k = 0; k < 7; k++) Fr[k] = Fs[0][k] + SL * (Ust[0][k] - Us[0][k]);
+    } else if (SsR <= 0.0) {
+      for (int k = 0; k < 7; k++) Fr[k] = Fs[1][k] + SR * (Ust[1][k] - Us[1][k]);
+    } else {
+      int a = SM >= 0.0 ? 0 : 1;
+      double Sst = a == 0 ? SsL : SsR;
+      for (int k = 0; k < 7; k++)
+        Fr[k] = ((Fs[a][k] + Sst * Uss[a][k]) - (Sst - Sa[a]) * Ust[a][k]) - Sa[a] * Us[a][k];
+    }
+  }
+  F[0] = Fr[0];
+  F[1 + d] = Fr[1];
+  F[1 + t1] = Fr[2];
+  F[1 + t2] = Fr[3];
+  F[4] = Fr[4];
+  F[5] = Fr[5];
+  F[6] = Fr[6];
+  S[0] = SL;
+  S[1] = SR;
+}
+
+static void hlld(const double WL[8], const double WR[8], int d, double gamma, double F[7], double S[2]) {
+  hlld_fan(WL, WR, d, gamma, F, S, NULL);
+}
+
 /* Upwind HLL edge EMF (two-dimensional HLL average of the four corner
  * states around an edge along axis e; a and b are the next two axes in cyclic
  * order).  Corner LL is the corner of the cell on the low side of both a and
@@ -266,6 +401,17 @@ void orc_predict(const double *W, const double *dX, const double *dY, const doub
 }
 void orc_hll(const double *WL, const double *WR, int d, double gamma, double *F, double *S) {
   hll(WL, WR, d, gamma, F, S);
+}
+void orc_hlld(const double *WL, const double *WR, int d, double gamma, double *F, double *S) {
+  hlld(WL, WR, d, gamma, F, S);
+}
+/* The HLLD fan (34 values, see hlld_fan) when S_L < 0 < S_R; returns 0 then,
+ * 1 when the flux is a single side's. */
+int orc_hlld_fan(const double *WL, const double *WR, int d, double gamma, double *fan) {
+  double F[7], S[2];
+  fan[0] = NAN;
+  hlld_fan(WL, WR, d, gamma, F, S, fan);
+  return isnan(fan[0]) ? 1 : 0;
 }
 double orc_emf(const double *Wll, const double *Wrl, const double *Wlr, const double *Wrr, int e,
                double apa, double ama, double apb, double amb) {
@@ -426,6 +572,13 @@ void orc_destroy(orc_ctx *c) {
   free(c->p);
   free(c->s_patch); free(c->s_t); free(c->s_dt);
   free(c);
+}
+
+/* Face flux of every later update: 0 HLL (the default), 1 HLLD. */
+int orc_set_riemann(orc_ctx *c, int riemann) {
+  if (riemann != 0 && riemann != 1) return ORC_EINVAL;
+  c->riemann = riemann;
+  return ORC_OK;
 }
 
 int orc_num_nbors(orc_ctx *c, int P, int *out) {
@@ -899,7 +1052,8 @@ static int update_patch(orc_ctx *c, int ip, double dt, double *oU, double *obx, 
             WL[q] = Ws[q * Nc + pl] + 0.5 * dW[(d * 8 + q) * Nc + pl];
             WR[q] = Ws[q * Nc + pr] - 0.5 * dW[(d * 8 + q) * Nc + pr];
           }
-          hll(WL, WR, d, gamma, f7, s2);
+          if (c->riemann) hlld(WL, WR, d, gamma, f7, s2);
+          else hll(WL, WR, d, gamma, f7, s2);
           int64_t e = EI(i, j, k);
           for (int q = 0; q < 5; q++) F[d][q * Ne + e] = f7[q];
           S[d][e] = s2[0];

@@ -71,6 +71,9 @@ def lib():
             L.orc_update_patch.argtypes = [P, ctypes.c_int, D, P, P, P, P, P]
             L.orc_num_nbors.argtypes = [P, ctypes.c_int, P]
             L.orc_fill_padded.argtypes = [P, ctypes.c_int, P, P, P, P]
+            L.orc_set_riemann.argtypes = [P, ctypes.c_int]
+            L.orc_hlld.argtypes = [P, P, ctypes.c_int, D, P, P]
+            L.orc_hlld_fan.argtypes = [P, P, ctypes.c_int, D, P]
             L.orc_last_error.restype = ctypes.c_char_p
             L.orc_last_error.argtypes = [P]
             L.orc_prim.argtypes = [P, P, D, P]
@@ -106,7 +109,7 @@ class Oracle:
     """
 
     def __init__(self, n, lo, *, level=None, gamma, cfl, base_cells, box_len=(1.0, 1.0, 1.0), t0=0.0,
-                 dt_max=0.0, nguard=3, nslices=3, time_mode=0, dispatcher=1):
+                 dt_max=0.0, nguard=3, nslices=3, time_mode=0, dispatcher=1, riemann=0):
         L = lib()
         self.n = np.ascontiguousarray(n, dtype=np.int32).reshape(-1, 3)
         self.lo = np.ascontiguousarray(lo, dtype=np.int64).reshape(-1, 3)
@@ -120,6 +123,7 @@ class Oracle:
         if not h:
             raise ValueError("oracle rejected the layout or parameters")
         self._h = h
+        self._check(L.orc_set_riemann(h, riemann))
         self.gamma = gamma
         self.nslices = nslices
         nc = self.n[:, 0].astype(np.int64) * self.n[:, 1] * self.n[:, 2]
@@ -252,6 +256,25 @@ def hll(WL, WR, d, gamma):
     S = np.empty(2)
     lib().orc_hll(_ptr(WL), _ptr(WR), d, gamma, _ptr(F), _ptr(S))
     return F, S
+
+
+def hlld(WL, WR, d, gamma):
+    WL, WR = _f64(WL), _f64(WR)
+    F = np.empty(7)
+    S = np.empty(2)
+    lib().orc_hlld(_ptr(WL), _ptr(WR), d, gamma, _ptr(F), _ptr(S))
+    return F, S
+
+
+def hlld_fan(WL, WR, d, gamma):
+    """(speeds S_L, S*_L, S_M, S*_R, S_R; states U*_L, U**_L, U**_R, U*_R in
+    the normal frame: rho, rho u, rho v, rho w, E, By, Bz; the total pressure
+    pT* of the fan), or None when the flux is a single side's."""
+    WL, WR = _f64(WL), _f64(WR)
+    fan = np.empty(34)
+    if lib().orc_hlld_fan(_ptr(WL), _ptr(WR), d, gamma, _ptr(fan)):
+        return None
+    return fan[:5], fan[5:33].reshape(4, 7), float(fan[33])
 
 
 def emf(Wll, Wrl, Wlr, Wrr, e, apa, ama, apb, amb):
