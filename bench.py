@@ -7,8 +7,9 @@ Courant step per sweep (C = 0.4), seeded solenoidal Mach-2 velocity with
 E(k) ~ k^-2 on 1 <= |k|/2pi <= 4, uniform B along x at beta = 1.  A bench
 "step" is one sweep: every patch fills its guard zones, advances one step and
 publishes it.  The state (1.07 GB per slice in FP64) is larger than L2, so no
-flush is needed between steps.  The FP32-state form of the same run is
-measured too and reported under "forms".
+flush is needed between steps.  The FP32-state form of the same run, and
+both forms with HLLD face fluxes, are measured too and reported under
+"forms".
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
 
@@ -49,6 +50,9 @@ F64_PRECISION = 2
 TRAFFIC_F64 = {2: (550.253568e6 + 420.952832e6) * 512 / 216, 3: (547.967488e6 + 420.902144e6) * 512 / 216,
                4: (549.530368e6 + 420.683776e6) * 512 / 216}
 TRAFFIC_F32 = {5: 624.325888e6 + 509.780992e6}
+# the same for the HLLD variants (FP64 FMA: the 216-patch capture, scaled)
+TRAFFIC_F64_HLLD = {10: (537.724160e6 + 421.700608e6) * 512 / 216}
+TRAFFIC_F32_HLLD = {}
 
 
 def radius2_guard_fraction(n):
@@ -76,6 +80,13 @@ def alg_bytes_per_cell(n, esize, sbar=1.0):
 ALG_FLOPS = {"primitives": 28, "slopes": 21 * 7 + 3, "predictor": 130, "positivity": 18, "face_states": 3 * 32,
              "hll": 3 * 176, "edge_emf": 3 * 111, "update": 5 * 7 + 3 * 5, "signal_speed": 28 + 63}
 ALG_FLOPS_PER_CELL = sum(ALG_FLOPS.values())
+# With HLLD faces (double-star branch, both star states regular), each face
+# replaces the 37 flops of the HLL blend (5 components and the reciprocal of
+# SR - SL) by 170: the contact speed and total pressure (20), per side the
+# star density, velocity, field and energy and sqrt(rho*) (2 x 34, plus Bn^2),
+# and the double-star states, their energy and the flux of the region (81).
+ALG_FLOPS_HLLD = dict(ALG_FLOPS, hll=0, hlld=3 * (176 - 37 + 170))
+ALG_FLOPS_PER_CELL_HLLD = sum(ALG_FLOPS_HLLD.values())
 
 # Arithmetic peaks derived from unit counts and the maximum SM clock:
 # 152 SMs at 2.07 GHz; FP64: 2 fused multiply-adds per SM per cycle (the
@@ -190,7 +201,7 @@ def make_input(patches=PATCHES):
     return lay, f, ics.to_patches(lay, f)
 
 
-def rooflines(ncells, esize, kernel_ms, hbm_peak, peak_kind):
+def rooflines(ncells, esize, kernel_ms, hbm_peak, peak_kind, flops_per_cell=ALG_FLOPS_PER_CELL):
     """The update kernel against its two roofs: HBM bandwidth (algorithmic
     bytes) and arithmetic (algorithmic flops against the FP64 or FP32 peak).
     The bound named first is the one the kernel is limited by (FP64: the
@@ -198,26 +209,28 @@ def rooflines(ncells, esize, kernel_ms, hbm_peak, peak_kind):
     benchmark's metric)."""
     bpl = alg_bytes_per_cell(NCELL, esize) * ncells
     gbs = bpl / (kernel_ms * 1e-3) / 1e9
-    fpl = ALG_FLOPS_PER_CELL * ncells
+    fpl = flops_per_cell * ncells
     tfs = fpl / (kernel_ms * 1e-3) / 1e12
     fpeak = FP64_PEAK_TFLOPS if esize == 8 else FP32_PEAK_TFLOPS
     hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
            "alg_bytes_per_launch": bpl, "peak_kind": peak_kind}
     alu = {"bound": "alu", "achieved": tfs, "peak": fpeak, "unit": "TFLOP/s", "frac": tfs / fpeak,
-           "alg_flops_per_launch": fpl, "alg_flops_per_cell": ALG_FLOPS_PER_CELL,
+           "alg_flops_per_launch": fpl, "alg_flops_per_cell": flops_per_cell,
            "peak_kind": "derived: 152 SMs x %s x 2.07 GHz" % ("2 FP64 FMA/cycle" if esize == 8 else "128 FP32 lanes")}
     if esize == 8:
         return dict(alu, hbm=hbm)
     return dict(hbm, alu=alu)
 
 
-def run_form(lay, state_dev, precision, steps, warmup, td, variant=-1):
-    """Time `steps` global steps of one precision form from the initial state."""
+def run_form(lay, state_dev, precision, steps, warmup, td, variant=-1, riemann=0):
+    """Time `steps` global steps of one precision form (HLL or HLLD face
+    fluxes) from the initial state."""
     import torch
     from paper_1705_10774_gb300.dispatch import Dispatch
     stream = torch.cuda.current_stream()
     g = Dispatch(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
-                 precision=precision, time_mode=0, timing=1, variant=variant, stream=stream.cuda_stream)
+                 precision=precision, time_mode=0, timing=1, variant=variant, riemann=riemann,
+                 stream=stream.cuda_stream)
     g.set_state(*state_dev)
     if variant < 0:
         g.tuned = g.autotune(reps=2)      # pick the fastest compiled variant (untimed set-up)
@@ -256,9 +269,10 @@ def gpu_arm(args):
     if args.form != "both":
         prec = {"f32": 1, "f64": F64_PRECISION, "f64_exact": 0}[args.form]
         sd = [a.float() for a in state_dev] if prec else state_dev
-        g, st, ms = run_form(lay, sd, prec, args.steps, args.warmup, td, args.variant)
+        g, st, ms = run_form(lay, sd, prec, args.steps, args.warmup, td, args.variant, args.riemann)
         if rank == 0:
-            print(json.dumps({"form": args.form, "patches": lay.npatch, "ms_per_step": ms / args.steps,
+            print(json.dumps({"form": args.form, "riemann": args.riemann, "variant": g.tuned[0],
+                              "patches": lay.npatch, "ms_per_step": ms / args.steps,
                               "kernel_ms_avg": st["kernel_ms"] / max(st["kernel_launches"], 1),
                               "cell_updates_per_s": st["cell_updates"] / (ms * 1e-3)}))
         return
@@ -296,6 +310,24 @@ def gpu_arm(args):
         forms["f32"] = {"value": v32, "ms_per_step": ms32_max / args.steps, "dtype": "f32", "roofline": r32}
         g32.close()
         del state32
+
+    if not args.no_hlld and args.form == "both":
+        # the same run with HLLD face fluxes (edge EMFs stay upwind HLL)
+        for name, prec in (("f64_hlld", F64_PRECISION), ("f32_hlld", 1)):
+            if prec == 1 and args.no_f32:
+                continue
+            sd = [a.float() for a in state_dev] if prec == 1 else state_dev
+            gh, sth, msh = run_form(lay, sd, prec, args.steps, args.warmup, td, riemann=1)
+            msh = max_over_ranks(td, msh)
+            kh = sth["kernel_ms"] / max(sth["kernel_launches"], 1)
+            rh = rooflines(ncells, 4 if prec == 1 else 8, kh, peak, peak_kind, ALG_FLOPS_PER_CELL_HLLD)
+            rh.update({"traffic": (TRAFFIC_F32_HLLD if prec == 1 else TRAFFIC_F64_HLLD).get(gh.tuned[0]),
+                       "kernel": "update_kernel variant %d" % gh.tuned[0], "kernel_ms_avg": kh})
+            forms[name] = {"value": sum_over_ranks(td, float(sth["cell_updates"])) / (msh * 1e-3),
+                           "ms_per_step": msh / args.steps, "dtype": "f32" if prec == 1 else "f64",
+                           "roofline": rh, "note": "HLLD face fluxes (Miyoshi & Kusano 2005)"}
+            gh.close()
+            del sd
 
     e2e = None
     if not args.no_e2e:
@@ -609,6 +641,9 @@ def main():
                     help="patches per axis for --form runs (profiling on a smaller box)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="--form runs: use this compiled kernel variant instead of autotuning")
+    ap.add_argument("--riemann", type=int, default=0, choices=[0, 1],
+                    help="--form runs: face fluxes, 0 = HLL, 1 = HLLD")
+    ap.add_argument("--no-hlld", action="store_true", help="skip the HLLD forms of the benchmark line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")

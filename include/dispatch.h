@@ -103,12 +103,17 @@ typedef struct {
  *   wait_budget  ready-queue dispatcher only: SM clock cycles a device wait
  *                may spin without progress before the run stops with
  *                DSP_ERR_TIMEOUT (0 = default, about two seconds)
- *   variant      id of a compiled update-kernel variant of this precision to
- *                use (-1 = the default; see dsp_autotune)
+ *   variant      id of a compiled update-kernel variant of this precision and
+ *                Riemann solver to use (-1 = the default; see dsp_autotune)
  *   graph        sweep dispatcher only: 1 = capture batches of 32 sweeps
  *                (plan + update kernels) in a CUDA graph and replay it; with
  *                a NULL stream the context then creates its own blocking
- *                stream (the legacy stream cannot be captured) */
+ *                stream (the legacy stream cannot be captured)
+ *   riemann      face fluxes: 0 = HLL, 1 = HLLD (Miyoshi & Kusano 2005; the
+ *                MHD solver whose cell-update cost Sec. 5.3 compares with
+ *                RAMSES), which resolves isolated contacts and rotational
+ *                discontinuities exactly; the edge EMFs stay the upwind HLL
+ *                ones.  Any other value: DSP_ERR_INVALID_ARG */
 typedef struct {
   double gamma, cfl, t0, dt_max, grace;
   double box_lo[3], box_len[3];
@@ -120,6 +125,7 @@ typedef struct {
   int64_t wait_budget;
   int32_t graph;
   int32_t variant;
+  int32_t riemann;
 } dsp_params;
 
 /* Counters of one dsp_advance call.  kernel_ms and kernel_launches are the

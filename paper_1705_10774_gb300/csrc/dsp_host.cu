@@ -458,7 +458,7 @@ int launch_xlevel(dsp_ctx *c) {
   return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
 }
 
-#define DSP_VARIANT_ENTRY(id, T, TX, TY, NT, MB, PREC) variant_##id,
+#define DSP_VARIANT_ENTRY(id, T, TX, TY, NT, MB, PREC, RS) variant_##id,
 const KernelVariant *(*const kVariants[])() = {DSP_VARIANT_LIST(DSP_VARIANT_ENTRY)};
 #undef DSP_VARIANT_ENTRY
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -596,6 +596,7 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   if (prm->grace != 0.0 || prm->dt_pow2 != 1) return DSP_ERR_UNSUPPORTED;
   if (prm->dispatcher != 0 && prm->dispatcher != 1) return DSP_ERR_INVALID_ARG;
   if (prm->dispatcher == 0 && prm->time_mode != 1) return DSP_ERR_UNSUPPORTED;  // a global step needs sweeps
+  if (prm->riemann != 0 && prm->riemann != 1) return DSP_ERR_INVALID_ARG;
   if (prm->nguard < 2 || prm->nslices < 3 || prm->precision < 0 || prm->precision > 2 ||
       (prm->time_mode != 0 && prm->time_mode != 1) || !(prm->cfl > 0.0) || !(prm->gamma > 1.0))
     return DSP_ERR_INVALID_ARG;
@@ -717,7 +718,7 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   const KernelVariant *var = nullptr;
   for (int k = 0; k < kNumVariants; k++) {
     const KernelVariant *v = kVariants[k]();
-    if (v->precision != prm->precision) continue;
+    if (v->precision != prm->precision || v->riemann != prm->riemann) continue;
     if (prm->variant >= 0 ? v->id == prm->variant : !var) var = v;
   }
   if (!var) return DSP_ERR_INVALID_ARG;
@@ -1343,7 +1344,7 @@ extern "C" int dsp_autotune(dsp_ctx *c, int32_t reps, int32_t *chosen, double *m
   int rc = DSP_OK;
   for (int k = 0; k < kNumVariants && rc == DSP_OK; k++) {
     const KernelVariant *v = kVariants[k]();
-    if (v->precision != c->precision) continue;
+    if (v->precision != c->precision || v->riemann != c->prm.riemann) continue;
     std::vector<PatchGeo> geo;
     long long off = 0, tt = 0;
     int ut = 0;

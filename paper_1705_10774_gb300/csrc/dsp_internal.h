@@ -101,6 +101,7 @@ struct DevCtx {
 // A compiled variant of the update kernels (see dsp_variants.h).
 struct KernelVariant {
   int id, precision;  // precision code of dsp_params
+  int riemann;        // Riemann solver of the face fluxes (dsp_params.riemann)
   int tx, ty, nt;     // tile and threads per block
   const char *name;
   int (*launch_update)(const DevCtx &c, int grid, void *stream);
@@ -108,7 +109,7 @@ struct KernelVariant {
   int (*grid)(const DevCtx &c);
 };
 
-#define DSP_DECLARE_VARIANT(id, T, TX, TY, NT, MB, PREC) const KernelVariant *variant_##id();
+#define DSP_DECLARE_VARIANT(id, T, TX, TY, NT, MB, PREC, RS) const KernelVariant *variant_##id();
 DSP_VARIANT_LIST(DSP_DECLARE_VARIANT)
 #undef DSP_DECLARE_VARIANT
 

@@ -118,7 +118,7 @@ __device__ __forceinline__ int posmod(int a, int b) { const int r = a % b; retur
 // Advance one tile of patch P by dt (all threads of the block take part).
 // On return the tile's new cells, faces and signal speed are written.  CONC:
 // other blocks publish patch times concurrently (ready-queue dispatcher).
-template <typename T, int TX, int TY, int NT, bool CONC>
+template <typename T, int TX, int TY, int NT, bool CONC, int RS>
 __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const double dt, const int tile, T *sm,
                                              TileShared<T, NT> &S) {
   static_assert(TX * TY <= NT, "one updated cell per thread");
@@ -523,7 +523,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
           WR[k] = Sws[k * H1N + hr] - half * SdX[k * H1N + hr];
         }
         if (full) {
-          hll<T, 0>(WL, WR, gamma, igm1, F, SL, SR);
+          face_flux<T, 0, RS>(WL, WR, gamma, igm1, F, SL, SR);
 #pragma unroll
           for (int k = 0; k < 5; k++) FX[k * H1N + hr] = F[k];
         } else {
@@ -555,7 +555,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
           WR[k] = Sws[k * H1N + hr] - half * SdY[k * H1N + hr];
         }
         if (full) {
-          hll<T, 1>(WL, WR, gamma, igm1, F, SL, SR);
+          face_flux<T, 1, RS>(WL, WR, gamma, igm1, F, SL, SR);
 #pragma unroll
           for (int k = 0; k < 5; k++) FY[k * H1N + hr] = F[k];
         } else {
@@ -595,7 +595,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
             WR[k] = Sws[k * H1N + h] - half * SdZ[k * H1N + h];
           }
           if (full) {
-            hll<T, 2>(WL, WR, gamma, igm1, F, SL, SR);
+            face_flux<T, 2, RS>(WL, WR, gamma, igm1, F, SL, SR);
 #pragma unroll
             for (int k = 0; k < 5; k++) FZc[k * H1N + h] = F[k];
           } else {
@@ -830,8 +830,9 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
 // Sweep dispatcher: every (ready patch, tile) work item of the current ready
 // list, grid-strided over a persistent grid.
 // VARIANT only tells apart instantiations compiled with different
-// floating-point contraction flags (FP64 with and without FMA).
-template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
+// floating-point contraction flags (FP64 with and without FMA); RS is the
+// Riemann solver of the face fluxes (0 HLL, 1 HLLD).
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS>
 __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ TileShared<T, NT> S;
@@ -845,7 +846,7 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
       if (c.work_off[mid] <= w) lo = mid;
       else hi = mid - 1;
     }
-    process_tile<T, TX, TY, NT, false>(c, c.R[lo], c.dtR[lo], w - c.work_off[lo], reinterpret_cast<T *>(smraw), S);
+    process_tile<T, TX, TY, NT, false, RS>(c, c.R[lo], c.dtR[lo], w - c.work_off[lo], reinterpret_cast<T *>(smraw), S);
   }
 }
 
@@ -932,7 +933,7 @@ static __device__ void publish_and_queue(const DevCtx &c, int P, double dt, doub
 // Persistent ready-queue dispatcher (one block per resident slot): claim the
 // next (entry, tile) work item, wait for the entry, update the tile; the block
 // that finishes a patch's last tile publishes it and queues what became ready.
-template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS>
 __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ TileShared<T, NT> S;
@@ -974,7 +975,7 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
     if (s_exit) return;
     const int P = s_P, tile = s_tile;
     const double dt = s_dt;
-    process_tile<T, TX, TY, NT, true>(c, P, dt, tile, reinterpret_cast<T *>(smraw), S);
+    process_tile<T, TX, TY, NT, true, RS>(c, P, dt, tile, reinterpret_cast<T *>(smraw), S);
     if (tid == 0) {
       __threadfence();
       const int k = atomicAdd(&c.tiles_done[P], 1);
@@ -987,21 +988,21 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
     __syncthreads();
   }
 }
-template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS>
 int launch_update(const DevCtx &c, int grid, void *stream) {
   // the shared-memory attribute was set by update_grid when the context was
   // created (a launch may be inside a stream capture)
   const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
-  update_kernel<T, TX, TY, NT, MINB, VARIANT><<<grid, NT, smem, (cudaStream_t)stream>>>(c);
+  update_kernel<T, TX, TY, NT, MINB, VARIANT, RS><<<grid, NT, smem, (cudaStream_t)stream>>>(c);
   return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
 }
 
-template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS>
 int launch_queue(const DevCtx &c, int grid, double t_end, void *stream) {
   const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
   static bool configured = false;
   if (!configured) {
-    if (cudaFuncSetAttribute(queue_kernel<T, TX, TY, NT, MINB, VARIANT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(queue_kernel<T, TX, TY, NT, MINB, VARIANT, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return DSP_ERR_CUDA;
     configured = true;
@@ -1011,21 +1012,21 @@ int launch_queue(const DevCtx &c, int grid, double t_end, void *stream) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, queue_kernel<T, TX, TY, NT, MINB, VARIANT>, NT, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, queue_kernel<T, TX, TY, NT, MINB, VARIANT, RS>, NT, smem);
   if (per < 1) return DSP_ERR_CUDA;
   const int g = nsm * per < grid ? nsm * per : grid;
-  queue_kernel<T, TX, TY, NT, MINB, VARIANT><<<g, NT, smem, (cudaStream_t)stream>>>(c, t_end);
+  queue_kernel<T, TX, TY, NT, MINB, VARIANT, RS><<<g, NT, smem, (cudaStream_t)stream>>>(c, t_end);
   return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
 }
 
-template <typename T, int TX, int TY, int NT, int MINB, int VARIANT>
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS>
 int update_grid(const DevCtx &c) {
   const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
-  cudaFuncSetAttribute(update_kernel<T, TX, TY, NT, MINB, VARIANT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(update_kernel<T, TX, TY, NT, MINB, VARIANT, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, update_kernel<T, TX, TY, NT, MINB, VARIANT>, NT, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, update_kernel<T, TX, TY, NT, MINB, VARIANT, RS>, NT, smem);
   if (per < 1) per = 1;
   const long long maxwork = c.total_tiles;  // every patch ready
   long long g = (long long)nsm * per;

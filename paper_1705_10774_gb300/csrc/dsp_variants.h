@@ -3,18 +3,22 @@
 // Each row is compiled from dsp_variant.cu into its own object (the build
 // reads this list): id, element type, tile TX x TY, threads per block,
 // minimum resident blocks per SM, precision code of dsp_params (0 FP64
-// without FMA, 1 FP32, 2 FP64 with FMA).  All variants of one precision
-// compute bit-identical results; they differ only in how the work is spread
-// over threads, so dsp_autotune may pick any of them.
+// without FMA, 1 FP32, 2 FP64 with FMA), Riemann solver of the face fluxes
+// (0 HLL, 1 HLLD).  All variants of one precision and solver compute
+// bit-identical results; they differ only in how the work is spread over
+// threads, so dsp_autotune may pick any of them.
 #pragma once
 
-#define DSP_VARIANT_LIST(X)         \
-  X(0, double, 16, 8, 256, 1, 0)    \
-  X(1, double, 16, 8, 384, 1, 0)    \
-  X(2, double, 16, 8, 256, 1, 2)    \
-  X(3, double, 16, 8, 384, 1, 2)    \
-  X(4, double, 16, 8, 512, 1, 2)    \
-  X(5, float, 16, 8, 256, 2, 1)     \
-  X(6, float, 16, 8, 512, 1, 1)     \
-  X(7, float, 32, 8, 256, 1, 1)     \
-  X(8, float, 16, 16, 256, 1, 1)
+#define DSP_VARIANT_LIST(X)            \
+  X(0, double, 16, 8, 256, 1, 0, 0)    \
+  X(1, double, 16, 8, 384, 1, 0, 0)    \
+  X(2, double, 16, 8, 256, 1, 2, 0)    \
+  X(3, double, 16, 8, 384, 1, 2, 0)    \
+  X(4, double, 16, 8, 512, 1, 2, 0)    \
+  X(5, float, 16, 8, 256, 2, 1, 0)     \
+  X(6, float, 16, 8, 512, 1, 1, 0)     \
+  X(7, float, 32, 8, 256, 1, 1, 0)     \
+  X(8, float, 16, 16, 256, 1, 1, 0)    \
+  X(9, double, 16, 8, 256, 1, 0, 1)    \
+  X(10, double, 16, 8, 256, 1, 2, 1)   \
+  X(11, float, 16, 8, 256, 2, 1, 1)

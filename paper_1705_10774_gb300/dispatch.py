@@ -48,7 +48,7 @@ class dsp_params(ctypes.Structure):
                 ("time_mode", ctypes.c_int32), ("dt_pow2", ctypes.c_int32), ("dispatcher", ctypes.c_int32),
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
                 ("sched_capacity", ctypes.c_int64), ("timing", ctypes.c_int32), ("wait_budget", ctypes.c_int64),
-                ("graph", ctypes.c_int32), ("variant", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("variant", ctypes.c_int32), ("riemann", ctypes.c_int32)]
 
 
 class dsp_stats(ctypes.Structure):
@@ -135,7 +135,8 @@ class Dispatch:
 
     def __init__(self, n, lo, *, gamma, cfl, base_cells, box_len=(1.0, 1.0, 1.0), t0=0.0, dt_max=0.0,
                  nguard=3, nslices=3, precision=0, time_mode=0, dispatcher=1, tile_z=0,
-                 sched_capacity=0, timing=0, wait_budget=0, graph=0, variant=-1, stream=None, level=None):
+                 sched_capacity=0, timing=0, wait_budget=0, graph=0, variant=-1, stream=None, level=None,
+                 riemann=0):
         L = load()
         n = np.asarray(n, dtype=np.int64).reshape(-1, 3)
         lo = np.asarray(lo, dtype=np.int64).reshape(-1, 3)
@@ -162,6 +163,7 @@ class Dispatch:
         p.wait_budget = wait_budget
         p.graph = graph
         p.variant = variant
+        p.riemann = riemann
         self.params = p
         h = VP()
         rc = L.dsp_create(descs, self.np, ctypes.byref(p), VP(stream or 0), ctypes.byref(h))
