@@ -74,6 +74,10 @@ typedef struct {
   int nlev;                          /* 1, or 2 when level-1 patches exist */
   int g, nslot, time_mode, disp_mode;
   int riemann; /* face flux: 0 HLL, 1 HLLD */
+  /* non-ideal MHD (Sec. 4.3): Ohmic resistivity eta, ambipolar drift
+   * coefficient gamma_AD (gad) with ion density rho_i, and the Courant-like
+   * factors of their step limits; a term is off when its coefficient is 0 */
+  double eta, gad, rhoi, cohm, cad;
   int64_t nsched, capsched;
   int64_t *s_patch;
   double *s_t, *s_dt;
@@ -581,6 +585,32 @@ int orc_set_riemann(orc_ctx *c, int riemann) {
   return ORC_OK;
 }
 
+/* Non-ideal terms of every later update (Sec. 4.3): E_Ohm = eta J (Eq. 2)
+ * and E_AD = -v_D x B with v_D = J x B / (gamma_AD rho rho_i) (Eqs. 5-6),
+ * step limits C_Ohm dx^2 / eta (Eq. 4) and C_AD gamma_AD rho_i rho dx^2 / B^2
+ * (Eq. 8).  eta = 0 or gamma_AD = 0 turns that term off. */
+int orc_set_nonideal(orc_ctx *c, double eta, double gamma_ad, double rho_i, double c_ohm, double c_ad) {
+  if (!(eta >= 0.0) || !(gamma_ad >= 0.0) || !(c_ohm > 0.0) || !(c_ad > 0.0)) return ORC_EINVAL;
+  if (gamma_ad > 0.0 && !(rho_i > 0.0)) return ORC_EINVAL;
+  c->eta = eta; c->gad = gamma_ad; c->rhoi = rho_i; c->cohm = c_ohm; c->cad = c_ad;
+  return ORC_OK;
+}
+
+/* The diffusive step limits as a signal speed: dt = cfl dx / s equals
+ * C_Ohm dx^2 / eta for s = cfl eta / (C_Ohm dx), and C_AD gamma_AD rho_i rho
+ * dx^2 / B^2 for s = cfl B^2 / (C_AD gamma_AD rho_i rho dx); the larger of the
+ * two (0 with both terms off).  W: primitive cell state, dxl: cell size. */
+static double nonideal_speed(const orc_ctx *c, const double W[8], double dxl) {
+  double s = 0.0;
+  if (c->eta > 0.0) s = c->cfl * c->eta / (c->cohm * dxl);
+  if (c->gad > 0.0) {
+    double B2 = W[BX] * W[BX] + W[BY] * W[BY] + W[BZ] * W[BZ];
+    double sad = c->cfl * B2 / ((((c->cad * c->gad) * c->rhoi) * W[RHO]) * dxl);
+    s = fmax(s, sad);
+  }
+  return s;
+}
+
 int orc_num_nbors(orc_ctx *c, int P, int *out) {
   if (out) memcpy(out, c->p[P].nb, sizeof(int) * c->p[P].nnb);
   return c->p[P].nnb;
@@ -614,6 +644,7 @@ static double slice_smax(orc_ctx *c, opatch *P, int s, int *bad) {
         double cy = cfast(c->gamma, ir, W[PR], W[BY], W[BZ], W[BX]);
         double cz = cfast(c->gamma, ir, W[PR], W[BZ], W[BX], W[BY]);
         double sum = (fabs(W[VX]) + cx) + (fabs(W[VY]) + cy) + (fabs(W[VZ]) + cz);
+        sum = fmax(sum, nonideal_speed(c, W, ldexp(c->dx, -P->level)));
         if (sum > m) m = sum;
       }
   return m;
@@ -974,8 +1005,14 @@ static int update_patch(orc_ctx *c, int ip, double dt, double *oU, double *obx, 
     F[d] = (double *)malloc(sizeof(double) * 5 * Ne);
     S[d] = (double *)malloc(sizeof(double) * 2 * Ne);
   }
-  double *E[3];
+  double *E[3], *J[3] = {NULL, NULL, NULL}, *Eni[3] = {NULL, NULL, NULL};
   for (int d = 0; d < 3; d++) E[d] = (double *)malloc(sizeof(double) * Ne);
+  int nonideal = c->eta > 0.0 || c->gad > 0.0;
+  if (nonideal)
+    for (int d = 0; d < 3; d++) {
+      J[d] = (double *)malloc(sizeof(double) * Ne);
+      Eni[d] = (double *)malloc(sizeof(double) * Ne);
+    }
   int rc = fill_padded(c, ip, pd);
   if (rc != ORC_OK) goto done;
 
@@ -1104,6 +1141,95 @@ static int update_patch(orc_ctx *c, int ip, double dt, double *oU, double *obx, 
         }
   }
 
+  /* Non-ideal EMFs (Sec. 4.3), from the state at the start of the step.
+   * Currents live on the edges, as the EMFs do: J_e at edge o (axis e, low
+   * corner of cell o in a = e+1 and b = e+2) is the discrete curl of the
+   * four faces around it, (f_b(o) - f_b(o - a)) - (f_a(o) - f_a(o - b)), over
+   * dx.  E_Ohm = eta J_e (Eq. 8).  E_AD = (J B^2 - B (B.J)) / (gamma_AD rho
+   * rho_i), which is -v_D x B of Eqs. 5-6, with the edge's B_a and B_b the
+   * means of the two faces on the edge, B_e and rho the means over the four
+   * cells around it (cell-centred B), and J_a, J_b the means of the four
+   * nearest a- and b-edges.  The EMF of the induction equation becomes
+   * E_ideal + E_Ohm + E_AD, and the energy flux through each face gains the
+   * Poynting flux (E_Ohm + E_AD) x B (edge EMFs and cell-centred B averaged
+   * to the face), so total energy stays conserved and the magnetic energy
+   * the terms remove, the heating Q of Eqs. 9 and 13, goes into the
+   * internal energy. */
+  if (nonideal) {
+    double idx = 1.0 / dxl;
+#define FACE(ax, i, j, k) ((ax) == 0 ? pd->bx[PFX(pd, i, j, k)] : (ax) == 1 ? pd->by[PFY(pd, i, j, k)] : pd->bz[PFZ(pd, i, j, k)])
+    for (int e = 0; e < 3; e++) {
+      int a = (e + 1) % 3, b = (e + 2) % 3;
+      for (int k = -1; k <= nz + 1; k++)
+        for (int j = -1; j <= ny + 1; j++)
+          for (int i = -1; i <= nx + 1; i++) {
+            int o[3] = {i, j, k}, oa[3] = {i, j, k}, ob[3] = {i, j, k};
+            oa[a] -= 1;
+            ob[b] -= 1;
+            double dbb = FACE(b, o[0], o[1], o[2]) - FACE(b, oa[0], oa[1], oa[2]);
+            double dba = FACE(a, o[0], o[1], o[2]) - FACE(a, ob[0], ob[1], ob[2]);
+            J[e][EI(i, j, k)] = (dbb - dba) * idx;
+          }
+    }
+    for (int e = 0; e < 3; e++) {
+      int a = (e + 1) % 3, b = (e + 2) % 3;
+      int hi3[3] = {nx, ny, nz};
+      hi3[a] += 1; hi3[b] += 1;
+      for (int k = 0; k < hi3[2]; k++)
+        for (int j = 0; j < hi3[1]; j++)
+          for (int i = 0; i < hi3[0]; i++) {
+            int o[3] = {i, j, k};
+            double en = 0.0;
+            if (c->eta > 0.0) en = c->eta * J[e][EI(i, j, k)];
+            if (c->gad > 0.0) {
+              int oa[3] = {i, j, k}, ob[3] = {i, j, k}, oab[3] = {i, j, k};
+              oa[a] -= 1; ob[b] -= 1; oab[a] -= 1; oab[b] -= 1;
+              int64_t c0 = PC(pd, o[0], o[1], o[2]), ca = PC(pd, oa[0], oa[1], oa[2]);
+              int64_t cb = PC(pd, ob[0], ob[1], ob[2]), cab = PC(pd, oab[0], oab[1], oab[2]);
+              double Ba = 0.5 * (FACE(a, o[0], o[1], o[2]) + FACE(a, ob[0], ob[1], ob[2]));
+              double Bb = 0.5 * (FACE(b, o[0], o[1], o[2]) + FACE(b, oa[0], oa[1], oa[2]));
+              double Be = 0.25 * ((W[(BX + e) * Nc + c0] + W[(BX + e) * Nc + ca]) +
+                                  (W[(BX + e) * Nc + cb] + W[(BX + e) * Nc + cab]));
+              double re = 0.25 * ((W[RHO * Nc + c0] + W[RHO * Nc + ca]) + (W[RHO * Nc + cb] + W[RHO * Nc + cab]));
+              /* a-edges at a = o_a - 1, o_a and e = o_e, o_e + 1; b-edges alike */
+              int ae[3] = {i, j, k}, aae[3] = {i, j, k}, be[3] = {i, j, k}, bbe[3] = {i, j, k};
+              ae[e] += 1; aae[a] -= 1; aae[e] += 1;
+              be[e] += 1; bbe[b] -= 1; bbe[e] += 1;
+              double Ja = 0.25 * ((J[a][EI(i, j, k)] + J[a][EI(oa[0], oa[1], oa[2])]) +
+                                  (J[a][EI(ae[0], ae[1], ae[2])] + J[a][EI(aae[0], aae[1], aae[2])]));
+              double Jb = 0.25 * ((J[b][EI(i, j, k)] + J[b][EI(ob[0], ob[1], ob[2])]) +
+                                  (J[b][EI(be[0], be[1], be[2])] + J[b][EI(bbe[0], bbe[1], bbe[2])]));
+              double Je = J[e][EI(i, j, k)];
+              double B2 = (Be * Be + Ba * Ba) + Bb * Bb;
+              double BJ = (Be * Je + Ba * Ja) + Bb * Jb;
+              en = en + (Je * B2 - Be * BJ) / ((c->gad * re) * c->rhoi);
+            }
+            Eni[e][EI(i, j, k)] = en;
+            E[e][EI(i, j, k)] = E[e][EI(i, j, k)] + en;
+          }
+    }
+    /* Poynting flux of the non-ideal EMF through the update's faces */
+    for (int d = 0; d < 3; d++) {
+      int a = (d + 1) % 3, b = (d + 2) % 3;
+      int hi3[3] = {nx, ny, nz};
+      hi3[d] += 1;
+      for (int k = 0; k < hi3[2]; k++)
+        for (int j = 0; j < hi3[1]; j++)
+          for (int i = 0; i < hi3[0]; i++) {
+            int ob[3] = {i, j, k}, oa[3] = {i, j, k}, od[3] = {i, j, k};
+            ob[b] += 1; oa[a] += 1; od[d] -= 1;
+            double Ea = 0.5 * (Eni[a][EI(i, j, k)] + Eni[a][EI(ob[0], ob[1], ob[2])]);
+            double Eb = 0.5 * (Eni[b][EI(i, j, k)] + Eni[b][EI(oa[0], oa[1], oa[2])]);
+            int64_t cl = PC(pd, od[0], od[1], od[2]), cr = PC(pd, i, j, k);
+            double Ba = 0.5 * (W[(BX + a) * Nc + cl] + W[(BX + a) * Nc + cr]);
+            double Bb = 0.5 * (W[(BX + b) * Nc + cl] + W[(BX + b) * Nc + cr]);
+            int64_t f = 4 * Ne + EI(i, j, k);
+            F[d][f] = F[d][f] + (Ea * Bb - Eb * Ba);
+          }
+    }
+#undef FACE
+  }
+
   /* A9: conservative update of U and constrained-transport update of b */
   int64_t nc = ncell(P);
   const double *U0 = P->U[P->latest];
@@ -1158,6 +1284,7 @@ static int update_patch(orc_ctx *c, int ip, double dt, double *oU, double *obx, 
           double cy = cfast(gamma, ir, w8[PR], w8[BY], w8[BZ], w8[BX]);
           double cz = cfast(gamma, ir, w8[PR], w8[BZ], w8[BX], w8[BY]);
           double sum = (fabs(w8[VX]) + cx) + (fabs(w8[VY]) + cy) + (fabs(w8[VZ]) + cz);
+          sum = fmax(sum, nonideal_speed(c, w8, dxl));
           if (sum > m) m = sum;
         }
     *smax_out = m;
@@ -1167,7 +1294,7 @@ static int update_patch(orc_ctx *c, int ip, double dt, double *oU, double *obx, 
 done:
   free(pd->U); free(pd->bx); free(pd->by); free(pd->bz);
   free(W); free(Ws); free(dW);
-  for (int d = 0; d < 3; d++) { free(F[d]); free(S[d]); free(E[d]); }
+  for (int d = 0; d < 3; d++) { free(F[d]); free(S[d]); free(E[d]); free(J[d]); free(Eni[d]); }
   return rc;
 }
 

@@ -10,7 +10,8 @@ filled by linear time interpolation (Sec. 3 A), readiness by Eq. (1) with
 grace 0, a time-sorted ready queue (Sec. 3 B) and local Courant steps
 (Sec. 5.1); the MHD step is MUSCL-Hancock with HLL fluxes and constrained
 transport (Secs. 4.1 and 4.3 name the solver family; the scheme itself is the
-textbook one).
+textbook one), optionally HLLD fluxes and the non-ideal Ohmic and ambipolar
+terms of Sec. 4.3.
 """
 from __future__ import annotations
 
@@ -72,6 +73,7 @@ def lib():
             L.orc_num_nbors.argtypes = [P, ctypes.c_int, P]
             L.orc_fill_padded.argtypes = [P, ctypes.c_int, P, P, P, P]
             L.orc_set_riemann.argtypes = [P, ctypes.c_int]
+            L.orc_set_nonideal.argtypes = [P, D, D, D, D, D]
             L.orc_hlld.argtypes = [P, P, ctypes.c_int, D, P, P]
             L.orc_hlld_fan.argtypes = [P, P, ctypes.c_int, D, P]
             L.orc_last_error.restype = ctypes.c_char_p
@@ -109,7 +111,8 @@ class Oracle:
     """
 
     def __init__(self, n, lo, *, level=None, gamma, cfl, base_cells, box_len=(1.0, 1.0, 1.0), t0=0.0,
-                 dt_max=0.0, nguard=3, nslices=3, time_mode=0, dispatcher=1, riemann=0):
+                 dt_max=0.0, nguard=3, nslices=3, time_mode=0, dispatcher=1, riemann=0, eta=0.0,
+                 gamma_ad=0.0, rho_i=1.0, c_ohm=0.1, c_ad=0.1):
         L = lib()
         self.n = np.ascontiguousarray(n, dtype=np.int32).reshape(-1, 3)
         self.lo = np.ascontiguousarray(lo, dtype=np.int64).reshape(-1, 3)
@@ -124,6 +127,9 @@ class Oracle:
             raise ValueError("oracle rejected the layout or parameters")
         self._h = h
         self._check(L.orc_set_riemann(h, riemann))
+        # non-ideal MHD (Sec. 4.3): Ohmic resistivity eta, ambipolar drift
+        # coefficient gamma_ad with ion density rho_i; 0 turns a term off
+        self._check(L.orc_set_nonideal(h, eta, gamma_ad, rho_i, c_ohm, c_ad))
         self.gamma = gamma
         self.nslices = nslices
         nc = self.n[:, 0].astype(np.int64) * self.n[:, 1] * self.n[:, 2]
