@@ -113,7 +113,21 @@ typedef struct {
  *                MHD solver whose cell-update cost Sec. 5.3 compares with
  *                RAMSES), which resolves isolated contacts and rotational
  *                discontinuities exactly; the edge EMFs stay the upwind HLL
- *                ones.  Any other value: DSP_ERR_INVALID_ARG */
+ *                ones.  Any other value: DSP_ERR_INVALID_ARG
+ *   eta          Ohmic resistivity eta_Ohm >= 0 (0 = no Ohmic term): the EMF
+ *                gains eta J, J = curl B on the cell edges (DISPATCH I,
+ *                Sec. 4.3, Eq. 2), and the step is limited to
+ *                c_ohm dx^2 / eta (Eq. 4)
+ *   gamma_ad     ambipolar drift coefficient gamma_AD >= 0 (0 = no ambipolar
+ *                term): the EMF gains -v_D x B with v_D = J x B /
+ *                (gamma_AD rho rho_i) (Eqs. 5-6), the step is limited to
+ *                c_ad gamma_AD rho_i rho dx^2 / B^2 (Eq. 8)
+ *   rho_i        ion density of the ambipolar term (> 0 when gamma_ad > 0)
+ *   c_ohm, c_ad  Courant-like factors of the two limits (0 = 0.1, the
+ *                paper's value).  The Poynting flux of the non-ideal EMF
+ *                joins the energy flux, so total energy stays conserved and
+ *                the heating of Eqs. 3 and 7 goes into the internal energy.
+ *                A negative or non-finite coefficient: DSP_ERR_INVALID_ARG */
 typedef struct {
   double gamma, cfl, t0, dt_max, grace;
   double box_lo[3], box_len[3];
@@ -126,6 +140,7 @@ typedef struct {
   int32_t graph;
   int32_t variant;
   int32_t riemann;
+  double eta, gamma_ad, rho_i, c_ohm, c_ad;
 } dsp_params;
 
 /* Counters of one dsp_advance call.  kernel_ms and kernel_launches are the

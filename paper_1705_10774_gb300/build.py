@@ -30,17 +30,17 @@ PREC_FLAGS = {0: ["-fmad=false"], 1: ["-ftz=true", "-prec-div=false", "-prec-sqr
 
 
 def variants():
-    """Rows of csrc/dsp_variants.h: (id, type, tx, ty, nt, mb, precision, riemann)."""
+    """Rows of csrc/dsp_variants.h: (id, type, tx, ty, nt, mb, precision, riemann, nonideal)."""
     txt = open(os.path.join(CSRC, "dsp_variants.h")).read()
-    rows = re.findall(r"X\((\d+),\s*(\w+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", txt)
-    return [(int(a), b, int(c), int(d), int(e), int(f), int(g), int(r)) for a, b, c, d, e, f, g, r in rows]
+    rows = re.findall(r"X\((\d+),\s*(\w+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", txt)
+    return [(int(a), b, int(c), int(d), int(e), int(f), int(g), int(r), int(n)) for a, b, c, d, e, f, g, r, n in rows]
 
 
 def units():
     out = [(src, src.replace(".cu", ".o"), flags) for src, flags in SOURCES]
-    for vid, t, tx, ty, nt, mb, prec, rs in variants():
+    for vid, t, tx, ty, nt, mb, prec, rs, ni in variants():
         defs = ["-DV_ID=%d" % vid, "-DV_T=%s" % t, "-DV_TX=%d" % tx, "-DV_TY=%d" % ty, "-DV_NT=%d" % nt,
-                "-DV_MB=%d" % mb, "-DV_PREC=%d" % prec, "-DV_RS=%d" % rs]
+                "-DV_MB=%d" % mb, "-DV_PREC=%d" % prec, "-DV_RS=%d" % rs, "-DV_NI=%d" % ni]
         out.append(("dsp_variant.cu", "dsp_variant_%d.o" % vid, defs + PREC_FLAGS[prec]))
     return out
 

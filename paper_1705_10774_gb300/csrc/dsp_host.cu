@@ -288,7 +288,10 @@ __global__ void smax_kernel(DevCtx c, int slot, int first, int count) {
          bya[((long long)k * (ny + 1) + j) * nx + i], bya[((long long)k * (ny + 1) + j + 1) * nx + i],
          bza[((long long)k * ny + j) * nx + i], bza[((long long)(k + 1) * ny + j) * nx + i], gamma, W);
     if (!(W[RHO] > T(0)) || !(W[PR] > T(0))) set_status(c, DSP_ERR_UNPHYSICAL, P);
-    m = fmax(m, (double)signal_sum(W, gamma));
+    T sig = signal_sum(W, gamma);
+    if (c.eta > 0.0 || c.gad > 0.0)
+      sig = tmax(sig, nonideal_speed(W, c.cfl, c.eta, c.gad, c.rhoi, c.cohm, c.cad, ldexp(c.dx, -g.level)));
+    m = fmax(m, (double)sig);
   }
   __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -458,7 +461,7 @@ int launch_xlevel(dsp_ctx *c) {
   return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
 }
 
-#define DSP_VARIANT_ENTRY(id, T, TX, TY, NT, MB, PREC, RS) variant_##id,
+#define DSP_VARIANT_ENTRY(id, T, TX, TY, NT, MB, PREC, RS, NI) variant_##id,
 const KernelVariant *(*const kVariants[])() = {DSP_VARIANT_LIST(DSP_VARIANT_ENTRY)};
 #undef DSP_VARIANT_ENTRY
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -597,6 +600,12 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   if (prm->dispatcher != 0 && prm->dispatcher != 1) return DSP_ERR_INVALID_ARG;
   if (prm->dispatcher == 0 && prm->time_mode != 1) return DSP_ERR_UNSUPPORTED;  // a global step needs sweeps
   if (prm->riemann != 0 && prm->riemann != 1) return DSP_ERR_INVALID_ARG;
+  // non-ideal MHD: coefficients >= 0 (0 = off), an ion density with the
+  // ambipolar term, Courant-like factors > 0 (0 = the paper's 0.1)
+  if (!(prm->eta >= 0.0) || !(prm->gamma_ad >= 0.0) || !(prm->eta < INFINITY) || !(prm->gamma_ad < INFINITY) ||
+      !(prm->c_ohm >= 0.0) || !(prm->c_ad >= 0.0) || (prm->gamma_ad > 0.0 && !(prm->rho_i > 0.0)))
+    return DSP_ERR_INVALID_ARG;
+  const int nonideal = prm->eta > 0.0 || prm->gamma_ad > 0.0;
   if (prm->nguard < 2 || prm->nslices < 3 || prm->precision < 0 || prm->precision > 2 ||
       (prm->time_mode != 0 && prm->time_mode != 1) || !(prm->cfl > 0.0) || !(prm->gamma > 1.0))
     return DSP_ERR_INVALID_ARG;
@@ -718,7 +727,7 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   const KernelVariant *var = nullptr;
   for (int k = 0; k < kNumVariants; k++) {
     const KernelVariant *v = kVariants[k]();
-    if (v->precision != prm->precision || v->riemann != prm->riemann) continue;
+    if (v->precision != prm->precision || v->riemann != prm->riemann || v->nonideal != nonideal) continue;
     if (prm->variant >= 0 ? v->id == prm->variant : !var) var = v;
   }
   if (!var) return DSP_ERR_INVALID_ARG;
@@ -773,6 +782,11 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.cfl = prm->cfl;
   d.dx = dx;
   d.dt_max = prm->dt_max;
+  d.eta = prm->eta;
+  d.gad = prm->gamma_ad;
+  d.rhoi = prm->gamma_ad > 0.0 ? prm->rho_i : 1.0;
+  d.cohm = prm->c_ohm > 0.0 ? prm->c_ohm : 0.1;
+  d.cad = prm->c_ad > 0.0 ? prm->c_ad : 0.1;
   // Neighbours (symmetric).  Same level: every patch owning a block of the
   // padded box (periodic images), the patch itself excluded.  Other level:
   // every patch owning a block of the cells this patch may read there -- a
@@ -1342,9 +1356,10 @@ extern "C" int dsp_autotune(dsp_ctx *c, int32_t reps, int32_t *chosen, double *m
     return DSP_OK;
   };
   int rc = DSP_OK;
+  const int nonideal = c->var->nonideal;
   for (int k = 0; k < kNumVariants && rc == DSP_OK; k++) {
     const KernelVariant *v = kVariants[k]();
-    if (v->precision != c->precision || v->riemann != c->prm.riemann) continue;
+    if (v->precision != c->precision || v->riemann != c->prm.riemann || v->nonideal != nonideal) continue;
     std::vector<PatchGeo> geo;
     long long off = 0, tt = 0;
     int ut = 0;

@@ -70,6 +70,9 @@ struct DevCtx {
   const long long *coff;   // [4][np+1] offsets of each patch in the caller's U, bx, by, bz arrays
   int *work_off;           // [np+1] first work item of each ready patch (prefix of tiles)
   double gamma, cfl, dx, dt_max;
+  // non-ideal MHD (Sec. 4.3): Ohmic resistivity, ambipolar drift coefficient
+  // and ion density, Courant-like factors of their step limits (0 = off)
+  double eta, gad, rhoi, cohm, cad;
   void *slab;
   double *t_slot;          // [np][ns]
   double *smax_slot;       // [np][ns]
@@ -102,6 +105,7 @@ struct DevCtx {
 struct KernelVariant {
   int id, precision;  // precision code of dsp_params
   int riemann;        // Riemann solver of the face fluxes (dsp_params.riemann)
+  int nonideal;       // 1: with the non-ideal Ohmic and ambipolar terms
   int tx, ty, nt;     // tile and threads per block
   const char *name;
   int (*launch_update)(const DevCtx &c, int grid, void *stream);
@@ -109,7 +113,7 @@ struct KernelVariant {
   int (*grid)(const DevCtx &c);
 };
 
-#define DSP_DECLARE_VARIANT(id, T, TX, TY, NT, MB, PREC, RS) const KernelVariant *variant_##id();
+#define DSP_DECLARE_VARIANT(id, T, TX, TY, NT, MB, PREC, RS, NI) const KernelVariant *variant_##id();
 DSP_VARIANT_LIST(DSP_DECLARE_VARIANT)
 #undef DSP_DECLARE_VARIANT
 

@@ -105,6 +105,23 @@ __device__ __forceinline__ T cfast(T gamma, T irho, T p, T bn, T bt1, T bt2) {
   return tsqrt(T(0.5) * (s + tsqrt(disc)));
 }
 
+// The non-ideal step limits of DISPATCH I, Sec. 4.3, as a signal speed s of
+// a cell state W, so that cfl dx / s is the limit: C_Ohm dx^2 / eta (Eq. 4)
+// for s = cfl eta / (C_Ohm dx), and C_AD gamma_AD rho_i rho dx^2 / B^2 (Eq. 8)
+// for s = cfl B^2 / (C_AD gamma_AD rho_i rho dx); the larger of the terms
+// that are on (eta > 0, gad > 0), else 0.
+template <typename T>
+__device__ __forceinline__ T nonideal_speed(const T W[8], double cfl, double eta, double gad, double rhoi, double cohm,
+                                            double cad, double dxl) {
+  T sp = T(0);
+  if (eta > 0.0) sp = (T)cfl * (T)eta / ((T)cohm * (T)dxl);
+  if (gad > 0.0) {
+    const T B2 = W[BX] * W[BX] + W[BY] * W[BY] + W[BZ] * W[BZ];
+    sp = tmax(sp, (T)cfl * B2 / (((((T)cad * (T)gad) * (T)rhoi) * W[RHO]) * (T)dxl));
+  }
+  return sp;
+}
+
 // Sum over axes of |v_d| + c_f,d: the signal speed that sets the Courant step.
 template <typename T>
 __device__ __forceinline__ T signal_sum(const T W[8], T gamma) {

@@ -33,14 +33,15 @@
 
 namespace dsp {
 
-template <int TX, int TY>
+template <int TX, int TY, int NI = 0>
 struct Lay {
   static constexpr int H2N = (TX + 4) * (TY + 4);
   static constexpr int H1N = (TX + 2) * (TY + 2);
   static constexpr int FPN = (TX + 5) * (TY + 5);
+  static constexpr int NFB = NI ? 3 : 2;       // face planes held (three for the non-ideal currents)
   static constexpr int oW = 0;                 // [3 planes][8][H2N] primitive ring
-  static constexpr int oFB = oW + 24 * H2N;    // [2 planes][4][FPN] faces: x-low, y-low, z-low, z-high
-  static constexpr int oWS = oFB + 8 * FPN;    // [8][H1N] predicted state W*
+  static constexpr int oFB = oW + 24 * H2N;    // [NFB planes][4][FPN] faces: x-low, y-low, z-low, z-high
+  static constexpr int oWS = oFB + NFB * 4 * FPN;  // [8][H1N] predicted state W*
   static constexpr int oDX = oWS + 8 * H1N;    // [8][H1N] slopes along x
   static constexpr int oDY = oDX + 8 * H1N;
   static constexpr int oDZ = oDY + 8 * H1N;
@@ -64,7 +65,15 @@ struct Lay {
   // cells, their x- and y-faces, the z-faces below them
   static constexpr int oOLD = oNBZ + 2 * H1N;
   static constexpr int OLDU = 0, OLDX = 5 * TX * TY, OLDY = OLDX + (TX + 1) * TY, OLDZ = OLDY + TX * (TY + 1);
-  static constexpr int total = oOLD + OLDZ + TX * TY;
+  // non-ideal terms only: the non-ideal EMFs of the x- and y-edges (two
+  // levels, by parity), of the z-edges of the previous plane, and the ideal
+  // energy fluxes of the x- and y-faces of the last two planes (by parity)
+  static constexpr int oENX = oOLD + OLDZ + TX * TY;
+  static constexpr int oENY = oENX + (NI ? 2 * H1N : 0);
+  static constexpr int oENZ = oENY + (NI ? 2 * H1N : 0);
+  static constexpr int oFXE = oENZ + (NI ? H1N : 0);
+  static constexpr int oFYE = oFXE + (NI ? 2 * H1N : 0);
+  static constexpr int total = oFYE + (NI ? 2 * H1N : 0);
 };
 
 
@@ -118,11 +127,18 @@ __device__ __forceinline__ int posmod(int a, int b) { const int r = a % b; retur
 // Advance one tile of patch P by dt (all threads of the block take part).
 // On return the tile's new cells, faces and signal speed are written.  CONC:
 // other blocks publish patch times concurrently (ready-queue dispatcher).
-template <typename T, int TX, int TY, int NT, bool CONC, int RS>
+// RS: Riemann solver of the face fluxes (0 HLL, 1 HLLD).  NI: add the
+// non-ideal Ohmic and ambipolar EMFs (DISPATCH I, Sec. 4.3) and their
+// Poynting flux; these variants gather each plane synchronously (no copies
+// in flight) and hold three planes of faces.
+template <typename T, int TX, int TY, int NT, bool CONC, int RS, int NI>
 __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const double dt, const int tile, T *sm,
                                              TileShared<T, NT> &S) {
   static_assert(TX * TY <= NT, "one updated cell per thread");
-  using L = Lay<TX, TY>;
+  using L = Lay<TX, TY, NI>;
+  // asynchronous copies of the next plane and of the old values (sweep
+  // dispatcher, ideal MHD)
+  constexpr bool ASYNC = !CONC && !NI;
   constexpr int H2N = L::H2N, H1N = L::H1N, FPN = L::FPN;
   T *const Wr = sm + L::oW;
   T *const FB = sm + L::oFB;
@@ -329,9 +345,11 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
   // copy (cp.async) of every value that is a plain copy and leaves the
   // blended ones; GATHER_BLEND computes only the blended ones (after the
   // copies have landed).
+  // ring slot of plane q's faces: two planes, or three with non-ideal terms
+  auto fslot = [&](int q) -> int { return NI ? (q - z0 + 3) % 3 : (q - z0 + 2) & 1; };
   auto gather_plane = [&](int q, auto mode) {
     constexpr int M = decltype(mode)::value;
-    const int rs = (q - z0 + 3) % 3, fs = (q - z0 + 2) & 1;
+    const int rs = (q - z0 + 3) % 3, fs = fslot(q);
     T *Wq = Wr + rs * 8 * H2N;
     T *Fq = FB + fs * 4 * FPN;
     auto put = [&](T *dst, const Loc &l) {
@@ -396,7 +414,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     cp_async_commit();
   };
   auto prim_plane = [&](int q) {
-    const int rs = (q - z0 + 3) % 3, fs = (q - z0 + 2) & 1;
+    const int rs = (q - z0 + 3) % 3, fs = fslot(q);
     T *Wq = Wr + rs * 8 * H2N;
     const T *Fq = FB + fs * 4 * FPN;
     for (int ci = tid; ci < (TX + 4) * (TY + 4); ci += NT) {
@@ -418,6 +436,77 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
   prim_plane(z0 - 1);
   __syncthreads();
 
+  // ---- Non-ideal MHD (Sec. 4.3), from the state at the start of the step,
+  // in the FP64 oracle's operation order.  Currents live on the edges: J_e
+  // at the edge on the low corner of cell (i,j,q) is the discrete curl of the
+  // four faces around it over dx.  E_Ohm = eta J (Eq. 2); E_AD = (J B^2 -
+  // B (B.J)) / (gamma_AD rho rho_i) = -v_D x B (Eqs. 5-6) with the edge's
+  // two face-normal B components the means of the faces on the edge, B_e and
+  // rho the means over the four cells around it, and the other two current
+  // components the means of the four nearest edges of their own axes.
+  const T idx = (T)(1.0 / dxl);
+  const T eta_t = (T)c.eta, gad_t = (T)c.gad, rhoi_t = (T)c.rhoi;
+  auto fpl = [&](int q) -> const T * { return FB + fslot(q) * 4 * FPN; };
+  auto wpl = [&](int q) -> const T * { return Wr + ((q - z0 + 3) % 3) * 8 * H2N; };
+  auto fxq = [&](int i, int j, int q) -> T { return fpl(q)[F5(i, j)]; };
+  auto fyq = [&](int i, int j, int q) -> T { return fpl(q)[FPN + F5(i, j)]; };
+  auto fzq = [&](int i, int j, int q) -> T { return fpl(q)[2 * FPN + F5(i, j)]; };
+  auto wc = [&](int k, int i, int j, int q) -> T { return wpl(q)[k * H2N + H2(i, j)]; };
+  auto Jx = [&](int i, int j, int q) -> T { return ((fzq(i, j, q) - fzq(i, j - 1, q)) - (fyq(i, j, q) - fyq(i, j, q - 1))) * idx; };
+  auto Jy = [&](int i, int j, int q) -> T { return ((fxq(i, j, q) - fxq(i, j, q - 1)) - (fzq(i, j, q) - fzq(i - 1, j, q))) * idx; };
+  auto Jz = [&](int i, int j, int q) -> T { return ((fyq(i, j, q) - fyq(i - 1, j, q)) - (fxq(i, j, q) - fxq(i, j - 1, q))) * idx; };
+  auto ni_law = [&](T Je, T Ba, T Bb, T Be, T re, T Ja, T Jb) -> T {
+    T en = T(0);
+    if (c.eta > 0.0) en = eta_t * Je;
+    if (c.gad > 0.0) {
+      const T B2 = (Be * Be + Ba * Ba) + Bb * Bb;
+      const T BJ = (Be * Je + Ba * Ja) + Bb * Jb;
+      en = en + (Je * B2 - Be * BJ) / ((gad_t * re) * rhoi_t);
+    }
+    return en;
+  };
+  // x-edge (i, j-1/2, q-1/2): e = x, a = y, b = z
+  auto eni_x = [&](int i, int j, int q) -> T {
+    const T Je = Jx(i, j, q);
+    if (!(c.gad > 0.0)) return ni_law(Je, T(0), T(0), T(0), T(0), T(0), T(0));
+    const T Ba = half * (fyq(i, j, q) + fyq(i, j, q - 1));
+    const T Bb = half * (fzq(i, j, q) + fzq(i, j - 1, q));
+    const T Be = T(0.25) * ((wc(BX, i, j, q) + wc(BX, i, j - 1, q)) + (wc(BX, i, j, q - 1) + wc(BX, i, j - 1, q - 1)));
+    const T re = T(0.25) * ((wc(RHO, i, j, q) + wc(RHO, i, j - 1, q)) + (wc(RHO, i, j, q - 1) + wc(RHO, i, j - 1, q - 1)));
+    const T Ja = T(0.25) * ((Jy(i, j, q) + Jy(i, j - 1, q)) + (Jy(i + 1, j, q) + Jy(i + 1, j - 1, q)));
+    const T Jb = T(0.25) * ((Jz(i, j, q) + Jz(i, j, q - 1)) + (Jz(i + 1, j, q) + Jz(i + 1, j, q - 1)));
+    return ni_law(Je, Ba, Bb, Be, re, Ja, Jb);
+  };
+  // y-edge (i-1/2, j, q-1/2): e = y, a = z, b = x
+  auto eni_y = [&](int i, int j, int q) -> T {
+    const T Je = Jy(i, j, q);
+    if (!(c.gad > 0.0)) return ni_law(Je, T(0), T(0), T(0), T(0), T(0), T(0));
+    const T Ba = half * (fzq(i, j, q) + fzq(i - 1, j, q));
+    const T Bb = half * (fxq(i, j, q) + fxq(i, j, q - 1));
+    const T Be = T(0.25) * ((wc(BY, i, j, q) + wc(BY, i, j, q - 1)) + (wc(BY, i - 1, j, q) + wc(BY, i - 1, j, q - 1)));
+    const T re = T(0.25) * ((wc(RHO, i, j, q) + wc(RHO, i, j, q - 1)) + (wc(RHO, i - 1, j, q) + wc(RHO, i - 1, j, q - 1)));
+    const T Ja = T(0.25) * ((Jz(i, j, q) + Jz(i, j, q - 1)) + (Jz(i, j + 1, q) + Jz(i, j + 1, q - 1)));
+    const T Jb = T(0.25) * ((Jx(i, j, q) + Jx(i - 1, j, q)) + (Jx(i, j + 1, q) + Jx(i - 1, j + 1, q)));
+    return ni_law(Je, Ba, Bb, Be, re, Ja, Jb);
+  };
+  // z-edge (i-1/2, j-1/2, q): e = z, a = x, b = y
+  auto eni_z = [&](int i, int j, int q) -> T {
+    const T Je = Jz(i, j, q);
+    if (!(c.gad > 0.0)) return ni_law(Je, T(0), T(0), T(0), T(0), T(0), T(0));
+    const T Ba = half * (fxq(i, j, q) + fxq(i, j - 1, q));
+    const T Bb = half * (fyq(i, j, q) + fyq(i - 1, j, q));
+    const T Be = T(0.25) * ((wc(BZ, i, j, q) + wc(BZ, i - 1, j, q)) + (wc(BZ, i, j - 1, q) + wc(BZ, i - 1, j - 1, q)));
+    const T re = T(0.25) * ((wc(RHO, i, j, q) + wc(RHO, i - 1, j, q)) + (wc(RHO, i, j - 1, q) + wc(RHO, i - 1, j - 1, q)));
+    const T Ja = T(0.25) * ((Jx(i, j, q) + Jx(i - 1, j, q)) + (Jx(i, j, q + 1) + Jx(i - 1, j, q + 1)));
+    const T Jb = T(0.25) * ((Jy(i, j, q) + Jy(i, j - 1, q)) + (Jy(i, j, q + 1) + Jy(i, j - 1, q + 1)));
+    return ni_law(Je, Ba, Bb, Be, re, Ja, Jb);
+  };
+  T *const ENX = sm + L::oENX;
+  T *const ENY = sm + L::oENY;
+  T *const ENZ = sm + L::oENZ;
+  T *const FXE = sm + L::oFXE;
+  T *const FYE = sm + L::oFYE;
+
   T smax_t = T(0);
   T unew[5];
   for (int it = 0; it <= tz + 1; it++) {
@@ -434,8 +523,8 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     // ---- A: plane p+1 -- gathered now (first plane, or with concurrent
     // publishers), else its copies were started one iteration earlier and
     // only the blended values remain
-    if (!CONC) prefetch_old(it, p);
-    if (CONC || it == 0) {
+    if (ASYNC) prefetch_old(it, p);
+    if (!ASYNC || it == 0) {
       gather_plane(p + 1, GatherMode<GATHER_NOW>{});
     } else {
       cp_async_wait<1>();  // every copy but the old values just started
@@ -449,7 +538,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     {
       const int rm = (p - 1 - z0 + 3) % 3, r0 = (p - z0 + 3) % 3, rp = (p + 1 - z0 + 3) % 3;
       const T *Wm = Wr + rm * 8 * H2N, *W0 = Wr + r0 * 8 * H2N, *Wp = Wr + rp * 8 * H2N;
-      const T *F0 = FB + ((p - z0 + 2) & 1) * 4 * FPN;
+      const T *F0 = FB + fslot(p) * 4 * FPN;
       for (int ci = tid; ci < (TX + 2) * (TY + 2); ci += NT) {
         const int i = ci % (TX + 2) - 1, j = ci / (TX + 2) - 1;
         if (i > tx || j > ty) continue;
@@ -493,7 +582,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     __syncthreads();
     // plane p-1's primitive ring slot and plane p's faces are dead now: start
     // the copies of plane p+2 into them, to land while C..F run
-    if (!CONC) {
+    if (ASYNC) {
       if (p + 2 <= z0 + tz + 1) gather_plane(p + 2, GatherMode<GATHER_ISSUE>{});
       else cp_async_commit();  // an empty group keeps the wait counts in step
     }
@@ -631,7 +720,13 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const T ama = tmax(T(0), tmax(-SYp[h0], -SYc[h0]));
         const T apb = tmax(T(0), tmax(SZ[H1N + hm], SZ[H1N + h0]));
         const T amb = tmax(T(0), tmax(-SZ[hm], -SZ[h0]));
-        EXc[h0] = emf(Ell, Erl, Elr, Err, Ba_ll, Ba_rl, lr_by, rr_by, Bb_ll, Bb_rl, lr_bz, rr_bz, apa, ama, apb, amb);
+        T ex = emf(Ell, Erl, Elr, Err, Ba_ll, Ba_rl, lr_by, rr_by, Bb_ll, Bb_rl, lr_bz, rr_bz, apa, ama, apb, amb);
+        if constexpr (NI != 0) {
+          const T en = eni_x(i, j, p);
+          ENX[par * H1N + h0] = en;
+          ex = ex + en;
+        }
+        EXc[h0] = ex;
       }
       // y-edges (i-1/2, j, p-1/2): i in [0,tx], j in [0,ty); a = z, b = x
       for (int ci = tid; ci < (TX + 1) * TY; ci += NT) {
@@ -654,27 +749,90 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const T ama = tmax(T(0), tmax(-SZ[hm], -SZ[h0]));
         const T apb = tmax(T(0), tmax(SXp[H1N + h0], SXc[H1N + h0]));
         const T amb = tmax(T(0), tmax(-SXp[h0], -SXc[h0]));
-        EYc[h0] = emf(Ell, Erl, Elr, Err, Ba_ll, rl_bz, Ba_lr, rr_bz, Bb_ll, rl_bx, Bb_lr, rr_bx, apa, ama, apb, amb);
+        T ey = emf(Ell, Erl, Elr, Err, Ba_ll, rl_bz, Ba_lr, rr_bz, Bb_ll, rl_bx, Bb_lr, rr_bx, apa, ama, apb, amb);
+        if constexpr (NI != 0) {
+          const T en = eni_y(i, j, p);
+          ENY[par * H1N + h0] = en;
+          ey = ey + en;
+        }
+        EYc[h0] = ey;
       }
       if (p < z0 + tz) {
+        // with non-ideal terms the energy part waits for the Poynting flux,
+        // which needs the edges above this plane: keep the ideal energy
+        // fluxes of the plane's x- and y-faces instead
+        constexpr int KD = NI ? 4 : 5;
         for (int ci = tid; ci < TX * TY; ci += NT) {
           const int i = ci % TX, j = ci / TX;
           if (i >= tx || j >= ty) continue;
           const int h = H1(i, j), hx = H1(i + 1, j), hy = H1(i, j + 1);
 #pragma unroll
-          for (int k = 0; k < 5; k++)
+          for (int k = 0; k < KD; k++)
             DUc[k * H1N + h] = (FX[k * H1N + hx] - FX[k * H1N + h]) + (FY[k * H1N + hy] - FY[k * H1N + h]);
+        }
+        if constexpr (NI != 0) {
+          for (int ci = tid; ci < (TX + 1) * (TY + 1); ci += NT) {
+            const int i = ci % (TX + 1), j = ci / (TX + 1), h = H1(i, j);
+            if (i <= tx && j < ty) FXE[par * H1N + h] = FX[4 * H1N + h];
+            if (i < tx && j <= ty) FYE[par * H1N + h] = FY[4 * H1N + h];
+          }
         }
       }
     }
     __syncthreads();
 
+    // ---- Non-ideal energy flux: the Poynting flux (E_Ohm + E_AD) x B
+    // through the z-faces at p-1/2 joins their energy flux, and plane p-1's
+    // energy divergence is formed from its x- and y-faces' ideal fluxes plus
+    // theirs (edge EMFs averaged to the face, cell-centred B averaged over
+    // the two cells of the face)
+    if constexpr (NI != 0) {
+      if (it >= 1) {
+        // z-faces (i, j, p-1/2): d = z, a = x, b = y
+        for (int ci = tid; ci < TX * TY; ci += NT) {
+          const int i = ci % TX, j = ci / TX;
+          if (i >= tx || j >= ty) continue;
+          const int h = H1(i, j);
+          const T Ea = half * (ENX[par * H1N + h] + ENX[par * H1N + H1(i, j + 1)]);
+          const T Eb = half * (ENY[par * H1N + h] + ENY[par * H1N + H1(i + 1, j)]);
+          const T Ba = half * (wc(BX, i, j, p - 1) + wc(BX, i, j, p));
+          const T Bb = half * (wc(BY, i, j, p - 1) + wc(BY, i, j, p));
+          FZc[4 * H1N + h] = FZc[4 * H1N + h] + (Ea * Bb - Eb * Ba);
+        }
+      }
+      if (it >= 2) {
+        const int q = p - 1, pr = par ^ 1;
+        // x-face (i-1/2, j, q): d = x, a = y (levels q-1/2, q+1/2), b = z
+        auto ftx = [&](int i, int j) -> T {
+          const T Ea = half * (ENY[pr * H1N + H1(i, j)] + ENY[par * H1N + H1(i, j)]);
+          const T Eb = half * (ENZ[H1(i, j)] + ENZ[H1(i, j + 1)]);
+          const T Ba = half * (wc(BY, i - 1, j, q) + wc(BY, i, j, q));
+          const T Bb = half * (wc(BZ, i - 1, j, q) + wc(BZ, i, j, q));
+          return FXE[pr * H1N + H1(i, j)] + (Ea * Bb - Eb * Ba);
+        };
+        // y-face (i, j-1/2, q): d = y, a = z, b = x (levels q-1/2, q+1/2)
+        auto fty = [&](int i, int j) -> T {
+          const T Ea = half * (ENZ[H1(i, j)] + ENZ[H1(i + 1, j)]);
+          const T Eb = half * (ENX[pr * H1N + H1(i, j)] + ENX[par * H1N + H1(i, j)]);
+          const T Ba = half * (wc(BZ, i, j - 1, q) + wc(BZ, i, j, q));
+          const T Bb = half * (wc(BX, i, j - 1, q) + wc(BX, i, j, q));
+          return FYE[pr * H1N + H1(i, j)] + (Ea * Bb - Eb * Ba);
+        };
+        for (int ci = tid; ci < TX * TY; ci += NT) {
+          const int i = ci % TX, j = ci / TX;
+          if (i >= tx || j >= ty) continue;
+          DUp[4 * H1N + H1(i, j)] = (ftx(i + 1, j) - ftx(i, j)) + (fty(i, j + 1) - fty(i, j));
+        }
+      }
+      __syncthreads();
+    }
+
     // ---- E: update plane p-1 and the z-faces at p-1/2
     const bool upd = it >= 2;
     const int ui = tid % TX, uj = tid / TX;
     const bool mine = tid < TX * TY && ui < tx && uj < ty;
-    if (!CONC) cp_async_wait<1>();  // this thread's old values (not plane p+2's copies)
-    auto old_u = [&](int k, long long ci) -> T { return CONC ? own[k * nc + ci] : OLD[L::OLDU + k * TX * TY + tid]; };
+    if (ASYNC) cp_async_wait<1>();  // this thread's old values (not plane p+2's copies)
+    auto old_u = [&](int k, long long ci) -> T { return !ASYNC ? own[k * nc + ci] : OLD[L::OLDU + k * TX * TY + tid]; };
     if (upd && mine) {
       const int i = ui, j = uj, h = H1(i, j);
       const long long ci = ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i);
@@ -691,7 +849,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const int i = ci % (TX + 1), j = ci / (TX + 1), h = H1(i, j);
         if (i > tx || j >= ty) continue;
         const long long id = ((long long)k * ny + (y0 + j)) * (nx + 1) + (x0 + i);
-        const T b = (CONC ? own[ofx + id] : OLD[L::OLDX + ci]) - dtdx * ((EZ[H1(i, j + 1)] - EZ[h]) - (EYc[h] - EYp[h]));
+        const T b = (!ASYNC ? own[ofx + id] : OLD[L::OLDX + ci]) - dtdx * ((EZ[H1(i, j + 1)] - EZ[h]) - (EYc[h] - EYp[h]));
         NBX[h] = b;
         dst[ofx + id] = b;
       }
@@ -699,7 +857,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const int i = ci % TX, j = ci / TX, h = H1(i, j);
         if (i >= tx || j > ty) continue;
         const long long id = ((long long)k * (ny + 1) + (y0 + j)) * nx + (x0 + i);
-        const T b = (CONC ? own[ofy + id] : OLD[L::OLDY + ci]) - dtdx * ((EXc[h] - EXp[h]) - (EZ[H1(i + 1, j)] - EZ[h]));
+        const T b = (!ASYNC ? own[ofy + id] : OLD[L::OLDY + ci]) - dtdx * ((EXc[h] - EXp[h]) - (EZ[H1(i + 1, j)] - EZ[h]));
         NBY[h] = b;
         dst[ofy + id] = b;
       }
@@ -709,7 +867,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const int i = ci % TX, j = ci / TX, h = H1(i, j);
         if (i >= tx || j >= ty) continue;
         const long long id = ((long long)p * ny + (y0 + j)) * nx + (x0 + i);
-        const T b = (CONC ? own[ofz + id] : OLD[L::OLDZ + ci]) - dtdx * ((EYc[H1(i + 1, j)] - EYc[h]) - (EXc[H1(i, j + 1)] - EXc[h]));
+        const T b = (!ASYNC ? own[ofz + id] : OLD[L::OLDZ + ci]) - dtdx * ((EYc[H1(i + 1, j)] - EYc[h]) - (EXc[H1(i, j + 1)] - EXc[h]));
         NBZc[h] = b;
         dst[ofz + id] = b;
       }
@@ -724,7 +882,9 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
            NBZp[h], NBZc[h], gamma, Wn);
       if (!(Wn[RHO] > T(0)) || !(Wn[PR] > T(0)))
         set_error(c, DSP_ERR_UNPHYSICAL, P, ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i));
-      smax_t = tmax(smax_t, signal_sum(Wn, gamma));
+      if constexpr (NI != 0)
+        smax_t = tmax(smax_t, tmax(signal_sum(Wn, gamma), nonideal_speed(Wn, c.cfl, c.eta, c.gad, c.rhoi, c.cohm, c.cad, dxl)));
+      else smax_t = tmax(smax_t, signal_sum(Wn, gamma));
     }
     if (p >= z0 && p < z0 + tz) {
       // z-edges (i-1/2, j-1/2, p): i in [0,tx], j in [0,ty]; a = x, b = y
@@ -756,7 +916,13 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const T ama = tmax(T(0), tmax(-SXc[hrl], -SXc[hrr]));
         const T apb = tmax(T(0), tmax(SYc[H1N + hlr], SYc[H1N + hrr]));
         const T amb = tmax(T(0), tmax(-SYc[hlr], -SYc[hrr]));
-        EZ[hrr] = emf(Ell, Erl, Elr, Err, ll_bx, rl_bx, lr_bx, rr_bx, ll_by, rl_by, lr_by, rr_by, apa, ama, apb, amb);
+        T ez = emf(Ell, Erl, Elr, Err, ll_bx, rl_bx, lr_bx, rr_bx, ll_by, rl_by, lr_by, rr_by, apa, ama, apb, amb);
+        if constexpr (NI != 0) {
+          const T en = eni_z(i, j, p);
+          ENZ[hrr] = en;
+          ez = ez + en;
+        }
+        EZ[hrr] = ez;
       }
     }
     {
@@ -832,7 +998,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
 // VARIANT only tells apart instantiations compiled with different
 // floating-point contraction flags (FP64 with and without FMA); RS is the
 // Riemann solver of the face fluxes (0 HLL, 1 HLLD).
-template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS>
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS, int NI>
 __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ TileShared<T, NT> S;
@@ -846,7 +1012,8 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
       if (c.work_off[mid] <= w) lo = mid;
       else hi = mid - 1;
     }
-    process_tile<T, TX, TY, NT, false, RS>(c, c.R[lo], c.dtR[lo], w - c.work_off[lo], reinterpret_cast<T *>(smraw), S);
+    process_tile<T, TX, TY, NT, false, RS, NI>(c, c.R[lo], c.dtR[lo], w - c.work_off[lo], reinterpret_cast<T *>(smraw),
+                                               S);
   }
 }
 
@@ -933,7 +1100,7 @@ static __device__ void publish_and_queue(const DevCtx &c, int P, double dt, doub
 // Persistent ready-queue dispatcher (one block per resident slot): claim the
 // next (entry, tile) work item, wait for the entry, update the tile; the block
 // that finishes a patch's last tile publishes it and queues what became ready.
-template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS>
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS, int NI>
 __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ TileShared<T, NT> S;
@@ -975,7 +1142,7 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
     if (s_exit) return;
     const int P = s_P, tile = s_tile;
     const double dt = s_dt;
-    process_tile<T, TX, TY, NT, true, RS>(c, P, dt, tile, reinterpret_cast<T *>(smraw), S);
+    process_tile<T, TX, TY, NT, true, RS, NI>(c, P, dt, tile, reinterpret_cast<T *>(smraw), S);
     if (tid == 0) {
       __threadfence();
       const int k = atomicAdd(&c.tiles_done[P], 1);
@@ -988,21 +1155,21 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
     __syncthreads();
   }
 }
-template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS>
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS, int NI>
 int launch_update(const DevCtx &c, int grid, void *stream) {
   // the shared-memory attribute was set by update_grid when the context was
   // created (a launch may be inside a stream capture)
-  const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
-  update_kernel<T, TX, TY, NT, MINB, VARIANT, RS><<<grid, NT, smem, (cudaStream_t)stream>>>(c);
+  const size_t smem = sizeof(T) * (size_t)Lay<TX, TY, NI>::total;
+  update_kernel<T, TX, TY, NT, MINB, VARIANT, RS, NI><<<grid, NT, smem, (cudaStream_t)stream>>>(c);
   return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
 }
 
-template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS>
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS, int NI>
 int launch_queue(const DevCtx &c, int grid, double t_end, void *stream) {
-  const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
+  const size_t smem = sizeof(T) * (size_t)Lay<TX, TY, NI>::total;
   static bool configured = false;
   if (!configured) {
-    if (cudaFuncSetAttribute(queue_kernel<T, TX, TY, NT, MINB, VARIANT, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(queue_kernel<T, TX, TY, NT, MINB, VARIANT, RS, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return DSP_ERR_CUDA;
     configured = true;
@@ -1012,21 +1179,21 @@ int launch_queue(const DevCtx &c, int grid, double t_end, void *stream) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, queue_kernel<T, TX, TY, NT, MINB, VARIANT, RS>, NT, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, queue_kernel<T, TX, TY, NT, MINB, VARIANT, RS, NI>, NT, smem);
   if (per < 1) return DSP_ERR_CUDA;
   const int g = nsm * per < grid ? nsm * per : grid;
-  queue_kernel<T, TX, TY, NT, MINB, VARIANT, RS><<<g, NT, smem, (cudaStream_t)stream>>>(c, t_end);
+  queue_kernel<T, TX, TY, NT, MINB, VARIANT, RS, NI><<<g, NT, smem, (cudaStream_t)stream>>>(c, t_end);
   return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
 }
 
-template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS>
+template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS, int NI>
 int update_grid(const DevCtx &c) {
-  const size_t smem = sizeof(T) * (size_t)Lay<TX, TY>::total;
-  cudaFuncSetAttribute(update_kernel<T, TX, TY, NT, MINB, VARIANT, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = sizeof(T) * (size_t)Lay<TX, TY, NI>::total;
+  cudaFuncSetAttribute(update_kernel<T, TX, TY, NT, MINB, VARIANT, RS, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, update_kernel<T, TX, TY, NT, MINB, VARIANT, RS>, NT, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, update_kernel<T, TX, TY, NT, MINB, VARIANT, RS, NI>, NT, smem);
   if (per < 1) per = 1;
   const long long maxwork = c.total_tiles;  // every patch ready
   long long g = (long long)nsm * per;

@@ -1,6 +1,6 @@
 // dsp_variant.cu -- one compiled variant of the update and ready-queue
 // kernels.  The build compiles this file once per row of dsp_variants.h,
-// defining V_ID, V_T, V_TX, V_TY, V_NT, V_MB, V_PREC and V_RS (and the
+// defining V_ID, V_T, V_TX, V_TY, V_NT, V_MB, V_PREC, V_RS and V_NI (and the
 // floating-point flags of the precision: no FMA for FP64 parity, fast
 // division and square root for FP32).
 #include "dsp_update.cuh"
@@ -12,12 +12,12 @@
 
 namespace dsp {
 namespace {
-int lu(const DevCtx &c, int grid, void *s) { return launch_update<V_T, V_TX, V_TY, V_NT, V_MB, V_ID, V_RS>(c, grid, s); }
+int lu(const DevCtx &c, int grid, void *s) { return launch_update<V_T, V_TX, V_TY, V_NT, V_MB, V_ID, V_RS, V_NI>(c, grid, s); }
 int lq(const DevCtx &c, int grid, double t, void *s) {
-  return launch_queue<V_T, V_TX, V_TY, V_NT, V_MB, V_ID, V_RS>(c, grid, t, s);
+  return launch_queue<V_T, V_TX, V_TY, V_NT, V_MB, V_ID, V_RS, V_NI>(c, grid, t, s);
 }
-int gr(const DevCtx &c) { return update_grid<V_T, V_TX, V_TY, V_NT, V_MB, V_ID, V_RS>(c); }
-const KernelVariant kv = {V_ID, V_PREC, V_RS, V_TX, V_TY, V_NT,
+int gr(const DevCtx &c) { return update_grid<V_T, V_TX, V_TY, V_NT, V_MB, V_ID, V_RS, V_NI>(c); }
+const KernelVariant kv = {V_ID, V_PREC, V_RS, V_NI, V_TX, V_TY, V_NT,
                           DSP_STR(V_T) " " DSP_STR(V_TX) "x" DSP_STR(V_TY) " " DSP_STR(V_NT) "t", lu, lq, gr};
 }  // namespace
 const KernelVariant *DSP_CAT(variant_, V_ID)() { return &kv; }

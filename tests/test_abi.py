@@ -50,9 +50,10 @@ def test_binding_struct_layout_matches_c(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(dsp_patch_desc), sizeof(dsp_params), sizeof(dsp_stats),
          sizeof(dsp_sched_entry), sizeof(dsp_diag));
-  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(dsp_params, base_cells), offsetof(dsp_params, sched_capacity),
-         offsetof(dsp_stats, status), offsetof(dsp_params, wait_budget), offsetof(dsp_params, variant),
-         offsetof(dsp_params, riemann));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", offsetof(dsp_params, base_cells),
+         offsetof(dsp_params, sched_capacity), offsetof(dsp_stats, status), offsetof(dsp_params, wait_budget),
+         offsetof(dsp_params, variant), offsetof(dsp_params, riemann), offsetof(dsp_params, eta),
+         offsetof(dsp_params, c_ad));
   return 0;
 }
 ''')
@@ -64,7 +65,8 @@ int main(void) {
     assert sizes == [ctypes.sizeof(s) for s in (D.dsp_patch_desc, D.dsp_params, D.dsp_stats,
                                                D.dsp_sched_entry, D.dsp_diag)]
     assert offs == [D.dsp_params.base_cells.offset, D.dsp_params.sched_capacity.offset, D.dsp_stats.status.offset,
-                    D.dsp_params.wait_budget.offset, D.dsp_params.variant.offset, D.dsp_params.riemann.offset]
+                    D.dsp_params.wait_budget.offset, D.dsp_params.variant.offset, D.dsp_params.riemann.offset,
+                    D.dsp_params.eta.offset, D.dsp_params.c_ad.offset]
 
 
 def test_no_cpu_fallback_in_product_path():

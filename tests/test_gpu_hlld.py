@@ -183,8 +183,8 @@ def test_hlld_variant_selection():
     or an unknown solver is rejected."""
     lay, f = ics.config_linear_waves(n=8, amplitude=1e-3)
     state = ics.to_patches(lay, f)
-    hlld_ids = [v[0] for v in B.variants() if v[6] == 0 and v[7] == HLLD]
-    hll_ids = [v[0] for v in B.variants() if v[6] == 0 and v[7] == 0]
+    hlld_ids = [v[0] for v in B.variants() if v[6] == 0 and v[7] == HLLD and v[8] == 0]
+    hll_ids = [v[0] for v in B.variants() if v[6] == 0 and v[7] == 0 and v[8] == 0]
     g = Dispatch(lay.n, lay.lo, **kw_of(lay, f.gamma, time_mode=1), riemann=HLLD)
     g.set_state(*state)
     chosen, table = g.autotune(reps=1)

@@ -101,7 +101,7 @@ def test_two_levels_graph_replay_and_variants_identical():
     lay = layouts()["mixed_level1"]
     state = smooth_state(lay, seed=9)
     outs = []
-    ids = [v[0] for v in B.variants() if v[6] == 0 and v[7] == 0]
+    ids = [v[0] for v in B.variants() if v[6] == 0 and v[7] == 0 and v[8] == 0]
     for graph, variant in [(0, -1), (1, -1)] + [(1, i) for i in ids]:
         g = Dispatch(lay.n, lay.lo, level=lay.levels, gamma=G53, cfl=0.4, base_cells=lay.base_cells,
                      box_len=lay.box_len, time_mode=1, graph=graph, variant=variant)

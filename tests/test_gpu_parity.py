@@ -374,7 +374,7 @@ def test_every_kernel_variant_gives_identical_results(precision):
     states, and the autotuner's choice changes nothing either."""
     import re
     from paper_1705_10774_gb300 import build as B
-    ids = [v[0] for v in B.variants() if v[6] == precision and v[7] == 0]
+    ids = [v[0] for v in B.variants() if v[6] == precision and v[7] == 0 and v[8] == 0]
     assert len(ids) >= 2
     lay, f = _mixed_case(seed=4) if precision != 0 else ics.config_linear_waves(n=16, amplitude=1e-3)
     state = ics.to_patches(lay, f)

@@ -72,14 +72,12 @@ def test_cshock_ode_joins_the_table1_states(name):
     assert np.all(np.abs(got - want) / np.abs(want) < 1e-3), (got, want)
 
 
-def cshock_run(name, ncell, t_end=0.05, Lx=2.0, xs=1.25, pol=1, lines=False):
-    """The steady profile centred at xs on a periodic box of length Lx
-    (5 patches along x, 4 x 4 cells across), advanced to t_end with local
-    steps; returns the relative L1 change of the transverse field and rho
-    within 0.3 of the shock, where the disturbance from the periodic wrap
-    has not arrived.  pol = 2 turns the transverse velocity and field from
-    y to z (the same problem rotated by 90 degrees about x); lines=True
-    returns the final x-lines of rho and the transverse field instead."""
+def cshock_setup(name, ncell, Lx=2.0, xs=1.25, pol=1):
+    """The steady C-shock profile of case `name` centred at xs on a periodic
+    box of length Lx (5 patches along x, 4 x 4 cells across), transverse
+    velocity and field along y (pol = 1) or z (pol = 2): returns the layout,
+    the fields, gamma, the non-ideal keyword arguments, the cell centres and
+    the pre- and post-shock rows."""
     rows = table1()
     pre_n, post_n, gamma, law, coef, iso = CASES[name]
     pre, post = rows[pre_n], rows[post_n]
@@ -99,8 +97,19 @@ def cshock_run(name, ncell, t_end=0.05, Lx=2.0, xs=1.25, pol=1, lines=False):
     vt[pol - 1], bt[pol - 1] = bc(st[:, 2]), bc(By)
     f = ics.Fields(rho=bc(st[:, 0]), v=np.stack([bc(st[:, 1]), vt[0], vt[1]]), p=bc(st[:, 3]),
                    bx=bc(0 * xc + pre[3]), by=bt[0], bz=bt[1], gamma=gamma)
+    return lay, f, gamma, law_kw(law, coef), xc, pre, post
+
+
+def cshock_run(name, ncell, t_end=0.05, Lx=2.0, xs=1.25, pol=1, lines=False):
+    """The steady profile (cshock_setup) advanced to t_end with local steps;
+    returns the relative L1 change of the transverse field and rho within
+    0.3 of the shock, where the disturbance from the periodic wrap has not
+    arrived.  pol = 2 turns the transverse velocity and field from y to z
+    (the same problem rotated by 90 degrees about x); lines=True returns the
+    final x-lines of rho and the transverse field instead."""
+    lay, f, gamma, kw, xc, pre, post = cshock_setup(name, ncell, Lx, xs, pol)
     o = Oracle(lay.n, lay.lo, gamma=gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
-               time_mode=1, **law_kw(law, coef))
+               time_mode=1, **kw)
     s0 = ics.to_patches(lay, f)
     o.set_state(*s0)
     o.advance(t_end=t_end)
