@@ -7,9 +7,9 @@ Courant step per sweep (C = 0.4), seeded solenoidal Mach-2 velocity with
 E(k) ~ k^-2 on 1 <= |k|/2pi <= 4, uniform B along x at beta = 1.  A bench
 "step" is one sweep: every patch fills its guard zones, advances one step and
 publishes it.  The state (1.07 GB per slice in FP64) is larger than L2, so no
-flush is needed between steps.  The FP32-state form of the same run, and
-both forms with HLLD face fluxes, are measured too and reported under
-"forms".
+flush is needed between steps.  The FP32-state form of the same run, both
+forms with HLLD face fluxes and both with the non-ideal Ohmic and ambipolar
+terms are measured too and reported under "forms".
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
 
@@ -42,6 +42,9 @@ HBM_FALLBACK_GBS = 6800.0
 # (checked against the FP64 oracle to 1e-11); the FMA-free build that matches
 # the oracle bit for bit is timed too and reported as forms.f64_exact
 F64_PRECISION = 2
+# coefficients of the non-ideal forms: Ohmic resistivity, and the C-shock
+# experiment's ambipolar drift coefficient and ion density (Sec. 5.4)
+NONIDEAL = dict(eta=1e-4, gamma_ad=75.0, rho_i=1.0)
 
 # DRAM bytes (read + write) per update-kernel launch of the full workload,
 # by compiled variant, from ncu's dram__bytes_read.sum + dram__bytes_write.sum
@@ -222,15 +225,15 @@ def rooflines(ncells, esize, kernel_ms, hbm_peak, peak_kind, flops_per_cell=ALG_
     return dict(hbm, alu=alu)
 
 
-def run_form(lay, state_dev, precision, steps, warmup, td, variant=-1, riemann=0):
+def run_form(lay, state_dev, precision, steps, warmup, td, variant=-1, riemann=0, nonideal=None):
     """Time `steps` global steps of one precision form (HLL or HLLD face
-    fluxes) from the initial state."""
+    fluxes, optionally with the non-ideal terms) from the initial state."""
     import torch
     from paper_1705_10774_gb300.dispatch import Dispatch
     stream = torch.cuda.current_stream()
     g = Dispatch(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
                  precision=precision, time_mode=0, timing=1, variant=variant, riemann=riemann,
-                 stream=stream.cuda_stream)
+                 stream=stream.cuda_stream, **(nonideal or {}))
     g.set_state(*state_dev)
     if variant < 0:
         g.tuned = g.autotune(reps=2)      # pick the fastest compiled variant (untimed set-up)
@@ -269,7 +272,8 @@ def gpu_arm(args):
     if args.form != "both":
         prec = {"f32": 1, "f64": F64_PRECISION, "f64_exact": 0}[args.form]
         sd = [a.float() for a in state_dev] if prec else state_dev
-        g, st, ms = run_form(lay, sd, prec, args.steps, args.warmup, td, args.variant, args.riemann)
+        g, st, ms = run_form(lay, sd, prec, args.steps, args.warmup, td, args.variant, args.riemann,
+                             NONIDEAL if args.nonideal else None)
         if rank == 0:
             print(json.dumps({"form": args.form, "riemann": args.riemann, "variant": g.tuned[0],
                               "patches": lay.npatch, "ms_per_step": ms / args.steps,
@@ -327,6 +331,22 @@ def gpu_arm(args):
                            "ms_per_step": msh / args.steps, "dtype": "f32" if prec == 1 else "f64",
                            "roofline": rh, "note": "HLLD face fluxes (Miyoshi & Kusano 2005)"}
             gh.close()
+            del sd
+
+    if not args.no_nonideal and args.form == "both":
+        # the same run with the non-ideal Ohmic and ambipolar terms (Sec. 4.3)
+        for name, prec in (("f64_nonideal", F64_PRECISION), ("f32_nonideal", 1)):
+            if prec == 1 and args.no_f32:
+                continue
+            sd = [a.float() for a in state_dev] if prec == 1 else state_dev
+            gn, stn, msn = run_form(lay, sd, prec, args.steps, args.warmup, td, nonideal=NONIDEAL)
+            msn = max_over_ranks(td, msn)
+            forms[name] = {"value": sum_over_ranks(td, float(stn["cell_updates"])) / (msn * 1e-3),
+                           "ms_per_step": msn / args.steps, "dtype": "f32" if prec == 1 else "f64",
+                           "kernel": "update_kernel variant %d" % gn.tuned[0],
+                           "kernel_ms_avg": stn["kernel_ms"] / max(stn["kernel_launches"], 1),
+                           "note": "Ohmic and ambipolar EMFs and their Poynting flux, %s" % NONIDEAL}
+            gn.close()
             del sd
 
     e2e = None
@@ -542,6 +562,42 @@ def orszag_tang_arm(args):
                       "t_end": args.t_end, "f32_vs_f64_relative_L1": errs, "per_form": drift}))
 
 
+def cshock_arm(args):
+    """Sec. 5.4's non-ideal C-shock experiments on the GPU (FP64 without
+    FMA, bit-identical to the oracle): from the Table 1 discontinuity on a
+    periodic box of 4 (300 cells, patches of 30 x 4 x 4; the shock at 3,
+    far enough from the wrap), local steps and CUDA graphs, to t = 0.2
+    (ambipolar) and 0.3 (Ohmic).  Reports the mean distance of B_y from the
+    steady C-shock profile (the ODE of the conservation laws, aligned at the
+    mid-value) over the jump, and the ratio of the largest to the smallest
+    per-patch step."""
+    import torch
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from cshock_ode import jump_input, most_common_steps, profile_error
+    from paper_1705_10774_gb300 import ics
+    from paper_1705_10774_gb300.dispatch import Dispatch
+    out = {}
+    for name, t_end in (("ad_iso", 0.2), ("ad_noniso", 0.2), ("ohm", 0.3)):
+        lay, f, gamma, kw, xc = jump_input(name)
+        g = Dispatch(lay.n, lay.lo, gamma=gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
+                     time_mode=1, graph=1, precision=0, sched_capacity=1 << 22, **kw)
+        g.set_state(*ics.to_patches(lay, f))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = g.advance(t_end=t_end)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        By = ics.from_patches(lay, *g.get_state())[2][0, 0]
+        steps = most_common_steps(g.schedule(), lay.npatch)
+        out[name] = {"t_end": t_end, "profile_error": profile_error(name, xc, By, 3.0),
+                     "step_ratio_between_patches": float(steps.max() / steps.min()),
+                     "patch_updates": st["patch_updates"], "sweeps": st["sweeps"], "seconds": el,
+                     "cell_updates_per_s": st["cell_updates"] / el, "coefficients": kw}
+        g.close()
+    print(json.dumps({"workload": "non-ideal C-shocks of Table 1, 300 cells over 4, 10 patches of 30x4x4",
+                      "cases": out}))
+
+
 def mixed_arm(args):
     """Mixed patch sizes on one level (the coarse level of the uneven batched
     solve): 512^3 cut into 96^3 super-blocks of 16^3, 24^3 or 32^3 patches
@@ -644,11 +700,14 @@ def main():
     ap.add_argument("--riemann", type=int, default=0, choices=[0, 1],
                     help="--form runs: face fluxes, 0 = HLL, 1 = HLLD")
     ap.add_argument("--no-hlld", action="store_true", help="skip the HLLD forms of the benchmark line")
+    ap.add_argument("--no-nonideal", action="store_true", help="skip the non-ideal forms of the benchmark line")
+    ap.add_argument("--nonideal", action="store_true",
+                    help="--form runs: with the non-ideal terms of the benchmark's non-ideal forms")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="turbulence",
-                    choices=["turbulence", "lts", "orszag-tang", "mixed", "amr"],
+                    choices=["turbulence", "lts", "orszag-tang", "mixed", "amr", "cshock"],
                     help="lts / orszag-tang: side measurements (one JSON line each), not the benchmark line")
     ap.add_argument("--t-end", type=float, default=0.01, help="end time of the lts / orszag-tang / mixed runs")
     ap.add_argument("--blocks", type=int, default=5, help="96^3 super-blocks per axis of the mixed run")
@@ -663,6 +722,8 @@ def main():
         return mixed_arm(args)
     if args.workload == "amr":
         return amr_arm(args)
+    if args.workload == "cshock":
+        return cshock_arm(args)
     if args.impl == "reference":
         reference_arm(args)
     else:

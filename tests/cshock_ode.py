@@ -97,3 +97,67 @@ class CShock:
         from scipy.integrate import solve_ivp
         return solve_ivp(self.rhs, (0.0, length), [self.pre[4] * (1.0 + 1e-8)], rtol=1e-12, atol=1e-14,
                          dense_output=True, max_step=0.005)
+
+
+# The three experiments of Sec. 5.4: Table 1 rows, gamma, law and coefficient
+# (gamma_AD = 75, eta = 0.1, rho_i = 1), isothermal or not.
+CASES = {
+    "ad_iso": ("ad_pre", "ad_iso_post", 1.0 + 1e-7, "ad", 75.0, True),
+    "ad_noniso": ("ad_pre", "ad_noniso_post", 5.0 / 3.0, "ad", 75.0, False),
+    "ohm": ("ohm_pre", "ohm_post", 5.0 / 3.0, "ohm", 0.1, False),
+}
+
+
+def law_kw(law, coef):
+    """Keyword arguments of the non-ideal term of a case."""
+    return dict(eta=coef) if law == "ohm" else dict(gamma_ad=coef, rho_i=1.0)
+
+
+def jump_input(name, ncell=300, Lx=4.0, xs=3.0):
+    """Sec. 5.4's initial condition: the Table 1 pre-shock state for x < xs,
+    the post-shock state beyond, on a periodic box of length Lx cut into
+    patches of 30 x 4 x 4 cells (dx = Lx / ncell).  Returns the layout, the
+    fields, gamma, the non-ideal keyword arguments and the cell centres."""
+    from paper_1705_10774_gb300 import ics
+    rows = table1()
+    pre_n, post_n, gamma, law, coef, iso = CASES[name]
+    pre, post = rows[pre_n], rows[post_n]
+    dx = Lx / ncell
+    lay = ics.cartesian((ncell // 30, 1, 1), (30, 4, 4), dx=dx)
+    X, Y, Z = lay.base_cells
+    xc = (np.arange(X) + 0.5) * dx
+    up = xc < xs
+    shape = (Z, Y, X)
+    bc = lambda a: np.broadcast_to(a, shape).copy()
+    sel = lambda k: np.where(up, pre[k], post[k])
+    f = ics.Fields(rho=bc(sel(0)), v=np.stack([bc(sel(1)), bc(sel(2)), bc(0 * xc)]), p=bc(sel(5)),
+                   bx=bc(0 * xc + pre[3]), by=bc(sel(4)), bz=bc(0 * xc), gamma=gamma)
+    return lay, f, gamma, law_kw(law, coef), xc
+
+
+def profile_error(name, xc, By, xs):
+    """Mean |B_y - steady profile| within 0.3 of the shock over the jump in
+    B_y, the steady profile aligned with B_y at its mid-value crossing near
+    xs."""
+    rows = table1()
+    pre_n, post_n, gamma, law, coef, iso = CASES[name]
+    pre, post = rows[pre_n], rows[post_n]
+    sol = CShock(pre, gamma, law, coef, isothermal=iso).solve()
+    mid = 0.5 * (pre[4] + post[4])
+    dx = xc[1] - xc[0]
+    i = np.where((np.abs(xc - xs) < 0.6) & (By > mid))[0][0]
+    xcross = xc[i - 1] + (mid - By[i - 1]) / (By[i] - By[i - 1]) * dx
+    s = xc - xcross + sol.t[np.argmax(sol.y[0] > mid)]
+    ode = np.where(s <= 0, pre[4], sol.sol(np.clip(s, 0, sol.t[-1]))[0])
+    w = np.abs(xc - xcross) < 0.3
+    return float(np.abs(By - ode)[w].mean() / abs(post[4] - pre[4]))
+
+
+def most_common_steps(schedule, npatch):
+    """Each patch's most frequent step in a schedule (patch, t, dt)."""
+    sp, _, sd = schedule
+    out = []
+    for P in range(npatch):
+        vals, cnt = np.unique(sd[sp == P], return_counts=True)
+        out.append(vals[np.argmax(cnt)])
+    return np.array(out)
