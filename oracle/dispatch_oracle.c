@@ -15,7 +15,9 @@
  *     oldest slice (Sec. 3 A, single-task view);
  *   - guard zones filled by linear interpolation in time from the neighbours'
  *     slices (Sec. 3 A and the closing paragraph of Sec. 3 B);
- *   - readiness by Eq. (1), t_self <= t_nbor + g dt_nbor, with grace g = 0;
+ *   - readiness by Eq. (1), t_self <= t_nbor + g dt_nbor, with grace g >= 0
+ *     (guard values then extrapolated in time past a neighbour's newest
+ *     slice), linear or quadratic time inter- and extrapolation (Sec. 3 B);
  *   - a dispatcher in two forms: a time-sorted ready queue (Sec. 3 B, mode i)
  *     and a sweep over the ready set (same schedule, see below);
  *   - local Courant time steps per patch (Sec. 5.1), quantised to powers of
@@ -78,6 +80,10 @@ typedef struct {
    * coefficient gamma_AD (gad) with ion density rho_i, and the Courant-like
    * factors of their step limits; a term is off when its coefficient is 0 */
   double eta, gad, rhoi, cohm, cad;
+  /* grace g of Eq. 1 (0 <= g < 1) and the order of the time inter- and
+   * extrapolation of guard values (1 linear, 2 quadratic), Sec. 3 B */
+  double grace;
+  int torder;
   int64_t nsched, capsched;
   int64_t *s_patch;
   double *s_t, *s_dt;
@@ -487,6 +493,7 @@ orc_ctx *orc_create(int np, const int32_t *n, const int64_t *lo, const int32_t *
   c->np = np;
   c->gamma = gamma; c->cfl = cfl; c->t0 = t0; c->dt_max = dt_max;
   c->g = nguard; c->nslot = nslot; c->time_mode = time_mode; c->disp_mode = disp_mode;
+  c->torder = 1;
   c->dx = box_len[0] / base[0];
   for (int d = 0; d < 3; d++) {
     c->L[0][d] = base[d];
@@ -582,6 +589,21 @@ void orc_destroy(orc_ctx *c) {
 int orc_set_riemann(orc_ctx *c, int riemann) {
   if (riemann != 0 && riemann != 1) return ORC_EINVAL;
   c->riemann = riemann;
+  return ORC_OK;
+}
+
+/* Grace g of Eq. 1 (0 <= g < 1) and the order of the time inter- and
+ * extrapolation of guard values (1 linear, 2 quadratic; Sec. 3 B).  g > 0
+ * is taken with the sweep dispatcher only (a sweep updates every ready
+ * patch from the slices before it, so the result does not depend on the
+ * order of updates), and quadratic extrapolation (g > 0, order 2) needs
+ * four slices so that the oldest patch can always step. */
+int orc_set_time(orc_ctx *c, double grace, int order) {
+  if (!(grace >= 0.0) || !(grace < 1.0) || (order != 1 && order != 2)) return ORC_EINVAL;
+  if (grace > 0.0 && c->time_mode == 1 && c->disp_mode == 0) return ORC_EINVAL;
+  if (grace > 0.0 && order == 2 && c->nslot < 4) return ORC_EINVAL;
+  c->grace = grace;
+  c->torder = order;
   return ORC_OK;
 }
 
@@ -728,24 +750,75 @@ int orc_get_times(orc_ctx *c, double *t, double *dt_last, double *smax) {
 /* Guard fill (time interpolation)                                     */
 /* ------------------------------------------------------------------ */
 
-/* Which stored slices of patch Q supply values at time t: a slice at exactly
- * t is copied; otherwise the two newest slices must bracket t and are
- * interpolated linearly with weight w = (t - t_a)/(t_b - t_a). */
-static int pick(orc_ctx *c, opatch *Q, double t, int *sa, int *sb, double *w) {
-  int L = Q->latest, Pv = (Q->latest + c->nslot - 1) % c->nslot;
-  if (Q->ts[L] == t) { *sa = L; *sb = -1; *w = 0.0; return ORC_OK; }
-  if (Q->ts[Pv] == t) { *sa = Pv; *sb = -1; *w = 0.0; return ORC_OK; }
-  double ta = Q->ts[Pv], tb = Q->ts[L];
-  if (ta < t && t < tb) {
-    *sa = Pv; *sb = L; *w = (t - ta) / (tb - ta);
+/* The stored slices of a patch and the weights that give its values at
+ * time t (Sec. 3 A and B): n = 1, a slice at exactly t, copied; n = 2,
+ * linear inter- or extrapolation A + w (B - A) between two slices with
+ * w = (t - t_a)/(t_b - t_a); n = 3, quadratic (Lagrange) inter- or
+ * extrapolation (w_a A + w_b B) + w_c C through three slices.  Slots s[] are
+ * ordered from older to newer. */
+typedef struct {
+  int n;
+  int s[3];
+  double w[3];
+} tpick;
+
+/* Which slices supply time t.  The stored slices, newest first, have
+ * strictly decreasing times.  A slice at t is copied.  Past the newest
+ * slice (a neighbour that is behind, allowed by the grace of Eq. 1) the
+ * newest two (linear) or three (quadratic) are extrapolated.  Otherwise t
+ * lies between two consecutive slices, which are interpolated; the
+ * quadratic form adds the next older slice, or the next newer one where
+ * there is no older one, and stays linear with only two slices. */
+static int pick(orc_ctx *c, opatch *Q, double t, tpick *pk) {
+  int ns = c->nslot, sl[64], cnt = 0;
+  for (int k = 0; k < ns && k < 64; k++) {
+    int s = (Q->latest - k + ns) % ns;
+    if (isnan(Q->ts[s])) break;
+    sl[cnt++] = s;
+  }
+  for (int k = 0; k < cnt; k++)
+    if (Q->ts[sl[k]] == t) {
+      pk->n = 1; pk->s[0] = sl[k]; pk->w[0] = 1.0;
+      return ORC_OK;
+    }
+  int ka, kb, kc = -1; /* indices into sl (larger = older) */
+  if (t > Q->ts[sl[0]]) {
+    if (cnt < 2) return ORC_EBRACKET;
+    ka = 1; kb = 0;
+    if (c->torder == 2 && cnt >= 3) { kc = 0; kb = 1; ka = 2; }
+  } else {
+    int k = 1;
+    while (k < cnt && !(Q->ts[sl[k]] < t)) k++;
+    if (k >= cnt) return ORC_EBRACKET;
+    ka = k; kb = k - 1;
+    if (c->torder == 2) {
+      if (k + 1 < cnt) { kc = k - 1; kb = k; ka = k + 1; }
+      else if (k - 2 >= 0) { kc = k - 2; }
+    }
+  }
+  if (kc < 0) {
+    double ta = Q->ts[sl[ka]], tb = Q->ts[sl[kb]];
+    pk->n = 2; pk->s[0] = sl[ka]; pk->s[1] = sl[kb];
+    pk->w[0] = (t - ta) / (tb - ta);
     return ORC_OK;
   }
-  return ORC_EBRACKET;
+  double ta = Q->ts[sl[ka]], tb = Q->ts[sl[kb]], tc = Q->ts[sl[kc]];
+  pk->n = 3; pk->s[0] = sl[ka]; pk->s[1] = sl[kb]; pk->s[2] = sl[kc];
+  pk->w[0] = ((t - tb) * (t - tc)) / ((ta - tb) * (ta - tc));
+  pk->w[1] = ((t - ta) * (t - tc)) / ((tb - ta) * (tb - tc));
+  pk->w[2] = ((t - ta) * (t - tb)) / ((tc - ta) * (tc - tb));
+  return ORC_OK;
 }
 
-static double tval(const double *A, const double *B, int64_t idx, double w) {
-  if (!B) return A[idx];
-  return A[idx] + w * (B[idx] - A[idx]);
+/* Value at index idx of the array arr[slot] (one array per slice) at the
+ * picked time. */
+static double tval(double *const *arr, int64_t off, const tpick *pk, int64_t idx) {
+  double a = arr[pk->s[0]][off + idx];
+  if (pk->n == 1) return a;
+  double b = arr[pk->s[1]][off + idx];
+  if (pk->n == 2) return a + pk->w[0] * (b - a);
+  double cc = arr[pk->s[2]][off + idx];
+  return (pk->w[0] * a + pk->w[1] * b) + pk->w[2] * cc;
 }
 
 /* Locate the patch of level lev among P's neighbours (or P itself) whose
@@ -770,15 +843,15 @@ static int owner(orc_ctx *c, opatch *P, int ip, int lev, const int64_t g[3], int
 /* Conserved values u[5] of level-lev cell g at time t, from the patch of
  * that level that owns it (copied or interpolated in time). */
 static int cell_at(orc_ctx *c, opatch *P, int ip, int lev, const int64_t g[3], double t, double u[5]) {
-  int loc[3], sa, sb;
-  double w;
+  int loc[3];
+  tpick pk;
   int iq = owner(c, P, ip, lev, g, loc);
   if (iq < 0) return ORC_EINVAL;
   opatch *Q = &c->p[iq];
-  if (pick(c, Q, t, &sa, &sb, &w) != ORC_OK) return ORC_EBRACKET;
+  if (pick(c, Q, t, &pk) != ORC_OK) return ORC_EBRACKET;
   int64_t qc = ncell(Q);
   int64_t id = ((int64_t)loc[2] * Q->n[1] + loc[1]) * Q->n[0] + loc[0];
-  for (int q = 0; q < 5; q++) u[q] = tval(Q->U[sa] + q * qc, sb >= 0 ? Q->U[sb] + q * qc : NULL, id, w);
+  for (int q = 0; q < 5; q++) u[q] = tval(Q->U, q * qc, &pk, id);
   return ORC_OK;
 }
 
@@ -787,19 +860,19 @@ static int cell_at(orc_ctx *c, opatch *P, int ip, int lev, const int64_t g[3], d
  * cell's high side instead (the same patch owns both). */
 static int face_at(orc_ctx *c, opatch *P, int ip, int lev, int ax, const int64_t g[3], int up, double t,
                    double *out) {
-  int loc[3], sa, sb;
-  double w;
+  int loc[3];
+  tpick pk;
   int iq = owner(c, P, ip, lev, g, loc);
   if (iq < 0) return ORC_EINVAL;
   opatch *Q = &c->p[iq];
-  if (pick(c, Q, t, &sa, &sb, &w) != ORC_OK) return ORC_EBRACKET;
+  if (pick(c, Q, t, &pk) != ORC_OK) return ORC_EBRACKET;
   loc[ax] += up;
   int qx = Q->n[0], qy = Q->n[1];
   int64_t id = ax == 0 ? ((int64_t)loc[2] * qy + loc[1]) * (qx + 1) + loc[0]
              : ax == 1 ? ((int64_t)loc[2] * (qy + 1) + loc[1]) * qx + loc[0]
                        : ((int64_t)loc[2] * qy + loc[1]) * qx + loc[0];
   double **arr = ax == 0 ? Q->bx : ax == 1 ? Q->by : Q->bz;
-  *out = tval(arr[sa], sb >= 0 ? arr[sb] : NULL, id, w);
+  *out = tval(arr, 0, &pk, id);
   return ORC_OK;
 }
 
@@ -1302,16 +1375,41 @@ done:
 /* Time steps, readiness and the dispatcher                            */
 /* ------------------------------------------------------------------ */
 
-/* Eq. (1) with g = 0: ready iff t_self < t_end and t_self <= t_nbor for all
- * neighbours. */
+/* May patch ip overwrite its oldest slice?  Not while a neighbour that may
+ * be updated before ip's next slice exists (its time at most ip's time plus
+ * g times ip's last step) still takes values from that slice.  With g = 0
+ * this never binds: a ready patch is at or behind every neighbour, and
+ * neighbours at or past its newest slice read only its newest two (three,
+ * quadratic) slices.  An empty slot is always free. */
+static int slot_free(orc_ctx *c, int ip) {
+  opatch *P = &c->p[ip];
+  int oldest = (P->latest + 1) % c->nslot;
+  if (isnan(P->ts[oldest])) return 1;
+  double lim = P->ts[P->latest] + c->grace * P->dt_last;
+  for (int q = 0; q < P->nnb; q++) {
+    opatch *Q = &c->p[P->nb[q]];
+    double tq = Q->ts[Q->latest];
+    if (!(tq <= lim)) continue;
+    tpick pk;
+    if (pick(c, P, tq, &pk) != ORC_OK) continue;
+    for (int k = 0; k < pk.n; k++)
+      if (pk.s[k] == oldest) return 0;
+  }
+  return 1;
+}
+
+/* Eq. (1): ready iff t_self < t_end and t_self <= t_nbor + g dt_nbor for all
+ * neighbours (dt_nbor: the neighbour's last step, 0 before its first), and,
+ * with g > 0, the patch's oldest slice is free (slot_free). */
 static int ready(orc_ctx *c, int ip, double t_end) {
   opatch *P = &c->p[ip];
   double t = P->ts[P->latest];
   if (!(t < t_end)) return 0;
   for (int q = 0; q < P->nnb; q++) {
     opatch *Q = &c->p[P->nb[q]];
-    if (!(t <= Q->ts[Q->latest])) return 0;
+    if (!(t <= Q->ts[Q->latest] + c->grace * Q->dt_last)) return 0;
   }
+  if (c->grace > 0.0 && !slot_free(c, ip)) return 0;
   return 1;
 }
 
@@ -1325,11 +1423,9 @@ static int patch_dt(orc_ctx *c, int ip, double t_end, double *dt_out) {
   double M = P->smax[P->latest];
   for (int q = 0; q < P->nnb; q++) {
     opatch *Q = &c->p[P->nb[q]];
-    int sa, sb;
-    double w;
-    if (pick(c, Q, t, &sa, &sb, &w) != ORC_OK) return ORC_EBRACKET;
-    M = fmax(M, Q->smax[sa]);
-    if (sb >= 0) M = fmax(M, Q->smax[sb]);
+    tpick pk;
+    if (pick(c, Q, t, &pk) != ORC_OK) return ORC_EBRACKET;
+    for (int k = 0; k < pk.n; k++) M = fmax(M, Q->smax[pk.s[k]]);
   }
   double dtc = c->cfl * ldexp(c->dx, -P->level) / M;
   double dt = pow2_floor(dtc);

@@ -74,6 +74,7 @@ def lib():
             L.orc_fill_padded.argtypes = [P, ctypes.c_int, P, P, P, P]
             L.orc_set_riemann.argtypes = [P, ctypes.c_int]
             L.orc_set_nonideal.argtypes = [P, D, D, D, D, D]
+            L.orc_set_time.argtypes = [P, D, ctypes.c_int]
             L.orc_hlld.argtypes = [P, P, ctypes.c_int, D, P, P]
             L.orc_hlld_fan.argtypes = [P, P, ctypes.c_int, D, P]
             L.orc_last_error.restype = ctypes.c_char_p
@@ -112,7 +113,7 @@ class Oracle:
 
     def __init__(self, n, lo, *, level=None, gamma, cfl, base_cells, box_len=(1.0, 1.0, 1.0), t0=0.0,
                  dt_max=0.0, nguard=3, nslices=3, time_mode=0, dispatcher=1, riemann=0, eta=0.0,
-                 gamma_ad=0.0, rho_i=1.0, c_ohm=0.1, c_ad=0.1):
+                 gamma_ad=0.0, rho_i=1.0, c_ohm=0.1, c_ad=0.1, grace=0.0, time_order=1):
         L = lib()
         self.n = np.ascontiguousarray(n, dtype=np.int32).reshape(-1, 3)
         self.lo = np.ascontiguousarray(lo, dtype=np.int64).reshape(-1, 3)
@@ -130,6 +131,8 @@ class Oracle:
         # non-ideal MHD (Sec. 4.3): Ohmic resistivity eta, ambipolar drift
         # coefficient gamma_ad with ion density rho_i; 0 turns a term off
         self._check(L.orc_set_nonideal(h, eta, gamma_ad, rho_i, c_ohm, c_ad))
+        # grace of Eq. 1 and the order of the time inter- and extrapolation
+        self._check(L.orc_set_time(h, grace, time_order))
         self.gamma = gamma
         self.nslices = nslices
         nc = self.n[:, 0].astype(np.int64) * self.n[:, 1] * self.n[:, 2]
