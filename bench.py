@@ -518,6 +518,46 @@ def lts_arm(args):
     print(json.dumps(out))
 
 
+def grace_arm(args):
+    """Eq. 1's grace and the order of the time inter- and extrapolation of
+    guard values (Sec. 3 B) on the local-step input (4096 patches of 16^3),
+    FP64 with FMA, sweeps replayed from CUDA graphs, to t_end: sweeps,
+    updates, time and the state's relative L1 distance from g = 0 with
+    linear interpolation."""
+    import torch
+    from paper_1705_10774_gb300 import ics
+    from paper_1705_10774_gb300.dispatch import Dispatch
+    lay, f = ics.config_lts(patches=16, n=16)
+    state = [torch.from_numpy(a).cuda() for a in ics.to_patches(lay, f)]
+    stream = torch.cuda.current_stream()
+    kw = dict(gamma=f.gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len, stream=stream.cuda_stream,
+              precision=F64_PRECISION, dispatcher=1, time_mode=1, graph=1)
+    out = {"workload": "local steps, 4096 patches of 16^3 (256^3), log-normal rho, hot sphere", "t_end": args.t_end,
+           "runs": []}
+    ref = None
+    for grace, order, ns in ((0.0, 1, 3), (0.05, 1, 3), (0.3, 1, 3), (0.6, 1, 3), (0.0, 2, 3), (0.6, 2, 4)):
+        g = Dispatch(lay.n, lay.lo, grace=grace, time_order=order, nslices=ns, **kw)
+        g.set_state(*state)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = g.advance(t_end=args.t_end)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        s1 = g.get_state()
+        if ref is None:
+            ref = s1
+        num = sum(float(np.abs(a - b).sum()) for a, b in zip(s1, ref))
+        den = sum(float(np.abs(b).sum()) for b in ref)
+        out["runs"].append({"grace": grace, "time_order": order, "nslices": ns, "sweeps": st["sweeps"],
+                            "patch_updates": st["patch_updates"], "ms": ms,
+                            "cell_updates_per_s": st["cell_updates"] / (ms * 1e-3), "relative_L1_vs_first": num / den})
+        g.close()
+    print(json.dumps(out))
+
+
 def orszag_tang_arm(args):
     """3-D Orszag-Tang vortex: FP32 state against FP64 on the same GPU, from
     the same input to the same time: relative L1 of density, momentum,
@@ -707,7 +747,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="turbulence",
-                    choices=["turbulence", "lts", "orszag-tang", "mixed", "amr", "cshock"],
+                    choices=["turbulence", "lts", "orszag-tang", "mixed", "amr", "cshock", "grace"],
                     help="lts / orszag-tang: side measurements (one JSON line each), not the benchmark line")
     ap.add_argument("--t-end", type=float, default=0.01, help="end time of the lts / orszag-tang / mixed runs")
     ap.add_argument("--blocks", type=int, default=5, help="96^3 super-blocks per axis of the mixed run")
@@ -724,6 +764,8 @@ def main():
         return amr_arm(args)
     if args.workload == "cshock":
         return cshock_arm(args)
+    if args.workload == "grace":
+        return grace_arm(args)
     if args.impl == "reference":
         reference_arm(args)
     else:

@@ -7,11 +7,12 @@
  *
  *   - each patch is a task with a position, a size, guard zones and a circular
  *     buffer of time slices (Sec. 2.1; Sec. 3 A);
- *   - before an update its guard zones are filled by linear interpolation in
- *     time from its neighbours' slices (Sec. 3 A; closing paragraph of
- *     Sec. 3 B);
- *   - a patch is ready when Eq. (1) holds for every neighbour with grace
- *     g = 0: t_self <= t_nbor;
+ *   - before an update its guard zones are filled by linear (or quadratic)
+ *     interpolation in time from its neighbours' slices, or extrapolation
+ *     past a neighbour's newest slice when the grace allows it (Sec. 3 A;
+ *     closing paragraph of Sec. 3 B);
+ *   - a patch is ready when Eq. (1) holds for every neighbour:
+ *     t_self <= t_nbor + g dt_nbor;
  *   - the update is one local Courant step (Sec. 5.1) of a MUSCL-Hancock
  *     scheme with HLL fluxes and constrained transport of face-centred B
  *     (Secs. 4.1 and 4.3 name the solver family; the paper prints no scheme);
@@ -79,11 +80,17 @@ typedef struct {
  *   cfl          Courant number C of the local step dt = C dx / s_max
  *   t0           time of the initial state
  *   dt_max       upper bound on any step (0 = none); use a power of two
- *   grace        g of Eq. (1); only 0 is supported (DSP_ERR_UNSUPPORTED otherwise)
+ *   grace        g of Eq. (1), 0 <= g < 1: a patch may step while up to g times
+ *                a neighbour's last step ahead of it, that neighbour's guard
+ *                values then extrapolated in time; a patch keeps its oldest
+ *                slice while a neighbour that may step first still needs it.
+ *                g > 0 needs the sweep dispatcher (DSP_ERR_UNSUPPORTED with
+ *                the ready queue, whose result would depend on timing)
  *   box_lo, box_len   the periodic box; cells must be cubic
  *   base_cells   level-0 cells per axis
  *   nguard       guard zones per side (>= 2; the stencil reads two)
- *   nslices      time slices per patch (>= 3)
+ *   nslices      time slices per patch (3 to 16; 4 or more for quadratic
+ *                extrapolation with g > 0)
  *   precision    0: all state and arithmetic in FP64, no fused multiply-add
  *                   (bit-identical to a plain FP64 evaluation);
  *                1: FP32 state and stencil arithmetic, FP64 times and steps;
@@ -127,7 +134,14 @@ typedef struct {
  *                paper's value).  The Poynting flux of the non-ideal EMF
  *                joins the energy flux, so total energy stays conserved and
  *                the heating of Eqs. 3 and 7 goes into the internal energy.
- *                A negative or non-finite coefficient: DSP_ERR_INVALID_ARG */
+ *                A negative or non-finite coefficient: DSP_ERR_INVALID_ARG
+ *   time_order   order of the time inter- and extrapolation of guard values:
+ *                1 (or 0) linear between the two slices around the time (the
+ *                newest two past the newest slice); 2 quadratic through those
+ *                and the next older slice (the next newer where none is
+ *                older; the newest three past the newest), which the closing
+ *                paragraph of Sec. 3 B allows; any other value:
+ *                DSP_ERR_INVALID_ARG */
 typedef struct {
   double gamma, cfl, t0, dt_max, grace;
   double box_lo[3], box_len[3];
@@ -141,6 +155,7 @@ typedef struct {
   int32_t variant;
   int32_t riemann;
   double eta, gamma_ad, rho_i, c_ohm, c_ad;
+  int32_t time_order;
 } dsp_params;
 
 /* Counters of one dsp_advance call.  kernel_ms and kernel_launches are the
@@ -176,7 +191,8 @@ typedef struct {
  * patches whose interior meets the cells a patch may read on the other
  * level.  Returns DSP_ERR_INVALID_ARG for a layout that breaks the rules of
  * dsp_patch_desc, DSP_ERR_UNSUPPORTED for levels other than 0 and 1, for two
- * levels with the ready-queue dispatcher, or for grace != 0. */
+ * levels with the ready-queue dispatcher, or for grace > 0 with the
+ * ready-queue dispatcher. */
 DSP_API int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const dsp_params *params, void *stream,
                dsp_ctx **out);
 

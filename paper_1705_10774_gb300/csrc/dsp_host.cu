@@ -596,7 +596,14 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   if (!out) return DSP_ERR_INVALID_ARG;
   *out = nullptr;
   if (!patches || !prm || npatch <= 0) return DSP_ERR_INVALID_ARG;
-  if (prm->grace != 0.0 || prm->dt_pow2 != 1) return DSP_ERR_UNSUPPORTED;
+  if (prm->dt_pow2 != 1) return DSP_ERR_UNSUPPORTED;
+  // grace (Eq. 1) in [0, 1); with g > 0 only the sweep dispatcher (whose
+  // result does not depend on the order of updates); time order 1 or 2
+  // (0 = 1); quadratic extrapolation needs four slices; at most 16 slices
+  if (!(prm->grace >= 0.0) || !(prm->grace < 1.0)) return DSP_ERR_INVALID_ARG;
+  if (prm->grace > 0.0 && prm->dispatcher == 0) return DSP_ERR_UNSUPPORTED;
+  if (prm->time_order < 0 || prm->time_order > 2 || prm->nslices > 16) return DSP_ERR_INVALID_ARG;
+  if (prm->grace > 0.0 && prm->time_order == 2 && prm->nslices < 4) return DSP_ERR_INVALID_ARG;
   if (prm->dispatcher != 0 && prm->dispatcher != 1) return DSP_ERR_INVALID_ARG;
   if (prm->dispatcher == 0 && prm->time_mode != 1) return DSP_ERR_UNSUPPORTED;  // a global step needs sweeps
   if (prm->riemann != 0 && prm->riemann != 1) return DSP_ERR_INVALID_ARG;
@@ -787,6 +794,8 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.rhoi = prm->gamma_ad > 0.0 ? prm->rho_i : 1.0;
   d.cohm = prm->c_ohm > 0.0 ? prm->c_ohm : 0.1;
   d.cad = prm->c_ad > 0.0 ? prm->c_ad : 0.1;
+  d.grace = prm->grace;
+  d.torder = prm->time_order == 2 ? 2 : 1;
   // Neighbours (symmetric).  Same level: every patch owning a block of the
   // padded box (periodic images), the patch itself excluded.  Other level:
   // every patch owning a block of the cells this patch may read there -- a

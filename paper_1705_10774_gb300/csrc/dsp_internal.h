@@ -73,6 +73,10 @@ struct DevCtx {
   // non-ideal MHD (Sec. 4.3): Ohmic resistivity, ambipolar drift coefficient
   // and ion density, Courant-like factors of their step limits (0 = off)
   double eta, gad, rhoi, cohm, cad;
+  // grace g of Eq. (1) and the order of the time inter- and extrapolation of
+  // guard values (1 linear, 2 quadratic)
+  double grace;
+  int torder;
   void *slab;
   double *t_slot;          // [np][ns]
   double *smax_slot;       // [np][ns]

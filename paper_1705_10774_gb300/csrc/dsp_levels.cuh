@@ -16,6 +16,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "dsp_dispatch.cuh"
 #include "dsp_internal.h"
 #include "dsp_physics.cuh"
 
@@ -39,12 +40,12 @@ __device__ __forceinline__ long long xl_block(const DevCtx &c, int lev, const in
   return ((long long)b[2] * c.mapd[lev][1] + b[1]) * c.mapd[lev][0] + b[0];
 }
 
-// The slices of patch Q that supply time t: a slice at exactly t is copied;
-// otherwise the newest two must bracket t and are blended with weight w.
+// The slices of patch Q that supply time t (pick_slices): A alone (a copy),
+// A + w0 (B - A), or (w0 A + w1 B) + w2 C.
 template <typename T>
 struct XSrc {
-  const T *A, *B;
-  T w;
+  const T *A, *B, *C;
+  T w[3];
   int Q, loc[3];
 };
 
@@ -60,33 +61,20 @@ __device__ int xl_source(const DevCtx &c, int lev, const int g[3], double t, XSr
   for (int d = 0; d < 3; d++) s.loc[d] = w[d] - gq.lo[d];
   s.Q = Q;
   const T *base = (const T *)c.slab + gq.off;
-  const int ns = c.ns, L = c.latest[Q];
-  const double tq = c.t_slot[(long long)Q * ns + L];
-  s.B = nullptr;
-  s.w = T(0);
-  if (tq == t) {
-    s.A = base + (long long)L * c.slot_stride;
-    return DSP_OK;
-  }
-  const int Pv = (L + ns - 1) % ns;
-  const double ta = c.t_slot[(long long)Q * ns + Pv];
-  if (ta == t) {
-    s.A = base + (long long)Pv * c.slot_stride;
-    return DSP_OK;
-  }
-  if (ta < t && t < tq) {
-    s.A = base + (long long)Pv * c.slot_stride;
-    s.B = base + (long long)L * c.slot_stride;
-    s.w = (T)((t - ta) / (tq - ta));
-    return DSP_OK;
-  }
-  return DSP_ERR_BRACKET;
+  SlicePick pk;
+  if (pick_slices<false>(c, Q, t, pk) != DSP_OK) return DSP_ERR_BRACKET;
+  s.A = base + (long long)pk.s[0] * c.slot_stride;
+  s.B = pk.n >= 2 ? base + (long long)pk.s[1] * c.slot_stride : nullptr;
+  s.C = pk.n == 3 ? base + (long long)pk.s[2] * c.slot_stride : nullptr;
+  for (int q = 0; q < 3; q++) s.w[q] = q < pk.n ? (T)pk.w[q] : T(0);
+  return DSP_OK;
 }
 
 template <typename T>
 __device__ __forceinline__ T xl_val(const XSrc<T> &s, long long idx) {
   T a = s.A[idx];
-  if (s.B) a = a + s.w * (s.B[idx] - a);
+  if (s.C) a = (s.w[0] * a + s.w[1] * s.B[idx]) + s.w[2] * s.C[idx];
+  else if (s.B) a = a + s.w[0] * (s.B[idx] - a);
   return a;
 }
 

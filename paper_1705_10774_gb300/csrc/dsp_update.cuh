@@ -108,13 +108,16 @@ __device__ __forceinline__ void set_error(const DevCtx &c, int code, int P, long
 
 // Small per-block scratch shared by all tiles a block processes: the owner
 // table of the work item's padded tile (one entry per map block it touches:
-// the owning patch's slice(s) at the tile's time, interpolation weight, the
-// periodic image of its first cell, its size), and reduction space.
+// the owning patch's slice(s) at the tile's time -- the first slice's
+// address, the others as slot offsets from it packed in `blend` (0: a copy;
+// else n | (dB + 16) << 2 | (dC + 16) << 8 for n = 2 or 3 slices) -- their
+// weights, the periodic image of its first cell, its size), and reduction
+// space.
 template <typename T, int NT>
 struct TileShared {
   const T *srcA[TABMAX];
-  const T *srcB[TABMAX];
-  T wgt[TABMAX];
+  int blend[TABMAX];
+  T wgt[3][TABMAX];
   int lo[3][TABMAX];
   int n[3][TABMAX];
   double red[NT / 32];
@@ -164,8 +167,6 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
   T *const NBZ = sm + L::oNBZ;
 
   const T **srcA = S.srcA;
-  const T **srcB = S.srcB;
-  T *wgt = S.wgt;
   double *red = S.red;
   int &s_fallback = S.fallback;
 
@@ -223,8 +224,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         S.n[d][e] = gp.n[d] + 4;
       }
       srcA[e] = (const T *)c.gbuf + c.gofs[P];
-      srcB[e] = nullptr;
-      wgt[e] = T(0);
+      S.blend[e] = 0;
       continue;
     }
     const PatchGeo &gq = c.geo[Q];
@@ -234,32 +234,22 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     S.n[0][e] = gq.n[0];
     S.n[1][e] = gq.n[1];
     S.n[2][e] = gq.n[2];
-    const int Lq = newest<CONC>(c, Q);
-    const double tq = slot_time<CONC>(c, (long long)Q * c.ns + Lq);
     const T *base = (const T *)c.slab + gq.off;
-    const T *A;
-    const T *B = nullptr;
-    T wv = T(0);
-    if (tq == tP) {
-      A = base + (long long)Lq * c.slot_stride;
-    } else {
-      const int Pv = (Lq + c.ns - 1) % c.ns;
-      const double ta = slot_time<CONC>(c, (long long)Q * c.ns + Pv);
-      if (ta == tP) {
-        A = base + (long long)Pv * c.slot_stride;
-      } else if (ta < tP && tP < tq) {
-        A = base + (long long)Pv * c.slot_stride;
-        B = base + (long long)Lq * c.slot_stride;
-        wv = (T)((tP - ta) / (tq - ta));
-      } else {
-        A = base + (long long)Lq * c.slot_stride;
-        set_error(c, DSP_ERR_BRACKET, P, -1);
-      }
+    SlicePick pk;
+    if (pick_slices<CONC>(c, Q, tP, pk) != DSP_OK) {
+      pk.n = 1;
+      pk.s[0] = newest<CONC>(c, Q);
+      set_error(c, DSP_ERR_BRACKET, P, -1);
     }
-    srcA[e] = A;
-    srcB[e] = B;
-    wgt[e] = wv;
-    if (B) my_blend = 1;
+    srcA[e] = base + (long long)pk.s[0] * c.slot_stride;
+    int bl = 0;
+    if (pk.n >= 2) {
+      bl = pk.n | ((pk.s[1] - pk.s[0] + 16) << 2) | ((pk.n == 3 ? pk.s[2] - pk.s[0] + 16 : 16) << 8);
+      my_blend = 1;
+    }
+    S.blend[e] = bl;
+#pragma unroll
+    for (int q = 0; q < 3; q++) S.wgt[q][e] = q < pk.n ? (T)pk.w[q] : T(0);
   }
   if (tid == 0) s_fallback = 0;
   const int any_blend = __syncthreads_or(my_blend);
@@ -272,14 +262,19 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     const T *p;
     int e;
   };
-  auto blended = [&](const Loc &l) -> bool { return l.e >= 0 && srcB[l.e] != nullptr; };
+  auto blended = [&](const Loc &l) -> bool { return l.e >= 0 && S.blend[l.e] != 0; };
   auto fetch = [&](const Loc &l) -> T {
     T a = *l.p;
     if (l.e >= 0) {
-      const T *B = srcB[l.e];
-      if (B) {
-        T b = B[l.p - srcA[l.e]];
-        a = a + wgt[l.e] * (b - a);
+      const int bl = S.blend[l.e];
+      if (bl) {
+        const T b = l.p[(long long)(((bl >> 2) & 63) - 16) * c.slot_stride];
+        if ((bl & 3) == 2) {
+          a = a + S.wgt[0][l.e] * (b - a);
+        } else {
+          const T cc = l.p[(long long)(((bl >> 8) & 63) - 16) * c.slot_stride];
+          a = (S.wgt[0][l.e] * a + S.wgt[1][l.e] * b) + S.wgt[2][l.e] * cc;
+        }
       }
     }
     return a;

@@ -50,7 +50,7 @@ class dsp_params(ctypes.Structure):
                 ("sched_capacity", ctypes.c_int64), ("timing", ctypes.c_int32), ("wait_budget", ctypes.c_int64),
                 ("graph", ctypes.c_int32), ("variant", ctypes.c_int32), ("riemann", ctypes.c_int32),
                 ("eta", ctypes.c_double), ("gamma_ad", ctypes.c_double), ("rho_i", ctypes.c_double),
-                ("c_ohm", ctypes.c_double), ("c_ad", ctypes.c_double)]
+                ("c_ohm", ctypes.c_double), ("c_ad", ctypes.c_double), ("time_order", ctypes.c_int32)]
 
 
 class dsp_stats(ctypes.Structure):
@@ -138,7 +138,7 @@ class Dispatch:
     def __init__(self, n, lo, *, gamma, cfl, base_cells, box_len=(1.0, 1.0, 1.0), t0=0.0, dt_max=0.0,
                  nguard=3, nslices=3, precision=0, time_mode=0, dispatcher=1, tile_z=0,
                  sched_capacity=0, timing=0, wait_budget=0, graph=0, variant=-1, stream=None, level=None,
-                 riemann=0, eta=0.0, gamma_ad=0.0, rho_i=1.0, c_ohm=0.1, c_ad=0.1):
+                 riemann=0, eta=0.0, gamma_ad=0.0, rho_i=1.0, c_ohm=0.1, c_ad=0.1, grace=0.0, time_order=1):
         L = load()
         n = np.asarray(n, dtype=np.int64).reshape(-1, 3)
         lo = np.asarray(lo, dtype=np.int64).reshape(-1, 3)
@@ -151,7 +151,7 @@ class Dispatch:
                 descs[i].n[d] = int(n[i, d])
                 descs[i].lo[d] = int(lo[i, d])
         p = dsp_params()
-        p.gamma, p.cfl, p.t0, p.dt_max, p.grace = gamma, cfl, t0, dt_max, 0.0
+        p.gamma, p.cfl, p.t0, p.dt_max, p.grace = gamma, cfl, t0, dt_max, grace
         for d in range(3):
             p.box_lo[d] = 0.0
             p.box_len[d] = box_len[d]
@@ -169,6 +169,8 @@ class Dispatch:
         # non-ideal MHD (Sec. 4.3): Ohmic resistivity, ambipolar drift
         # coefficient and ion density (0 turns a term off)
         p.eta, p.gamma_ad, p.rho_i, p.c_ohm, p.c_ad = eta, gamma_ad, rho_i, c_ohm, c_ad
+        # grace of Eq. 1 and the order of the time inter- and extrapolation
+        p.time_order = time_order
         self.params = p
         h = VP()
         rc = L.dsp_create(descs, self.np, ctypes.byref(p), VP(stream or 0), ctypes.byref(h))

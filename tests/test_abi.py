@@ -53,7 +53,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", offsetof(dsp_params, base_cells),
          offsetof(dsp_params, sched_capacity), offsetof(dsp_stats, status), offsetof(dsp_params, wait_budget),
          offsetof(dsp_params, variant), offsetof(dsp_params, riemann), offsetof(dsp_params, eta),
-         offsetof(dsp_params, c_ad));
+         offsetof(dsp_params, time_order));
   return 0;
 }
 ''')
@@ -66,7 +66,7 @@ int main(void) {
                                                D.dsp_sched_entry, D.dsp_diag)]
     assert offs == [D.dsp_params.base_cells.offset, D.dsp_params.sched_capacity.offset, D.dsp_stats.status.offset,
                     D.dsp_params.wait_budget.offset, D.dsp_params.variant.offset, D.dsp_params.riemann.offset,
-                    D.dsp_params.eta.offset, D.dsp_params.c_ad.offset]
+                    D.dsp_params.eta.offset, D.dsp_params.time_order.offset]
 
 
 def test_no_cpu_fallback_in_product_path():
