@@ -29,4 +29,7 @@
   X(14, float, 16, 8, 256, 1, 1, 0, 1) \
   X(15, double, 16, 4, 256, 1, 2, 0, 1) \
   X(16, float, 16, 4, 128, 2, 1, 0, 1) \
-  X(17, double, 16, 4, 256, 1, 0, 0, 1)
+  X(17, double, 16, 4, 256, 1, 0, 0, 1) \
+  X(18, double, 16, 4, 256, 1, 0, 1, 1) \
+  X(19, double, 16, 4, 256, 1, 2, 1, 1) \
+  X(20, float, 16, 8, 256, 1, 1, 1, 1)

@@ -159,3 +159,23 @@ def test_nonideal_variant_selection_and_rejected_parameters():
         with pytest.raises(DispatchError) as e:
             Dispatch(lay.n, lay.lo, **base, **bad)
         assert e.value.code == DSP_ERR_INVALID_ARG
+
+
+def test_nonideal_with_hlld_faces():
+    """HLLD face fluxes together with both non-ideal terms: bit-identical to
+    the oracle with the same options (FP64 exact), FMA within 1e-11."""
+    lay, st, gamma = turbulent()
+    for prec in (0, 2):
+        base = dict(gamma=gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len, time_mode=1, riemann=1,
+                    **BOTH)
+        g = Dispatch(lay.n, lay.lo, **base, precision=prec, sched_capacity=1 << 20)
+        g.set_state(*st)
+        o = Oracle(lay.n, lay.lo, **base)
+        o.set_state(*st)
+        g.advance(t_end=0.004)
+        o.advance(t_end=0.004)
+        if prec == 0:
+            assert_bit_identical(g, o)
+        else:
+            for a, b in zip(g.get_state(), o.get_state()):
+                assert float(np.max(np.abs(a - b)) / np.max(np.abs(b))) <= 1e-11
