@@ -518,6 +518,52 @@ def lts_arm(args):
     print(json.dumps(out))
 
 
+def kitp_arm(args):
+    """Sec. 5.1's decaying-turbulence check on the benchmark's 256^3 input
+    (which stands in for the KITP snapshot): one patch of 256^3 against 512
+    patches of 32^3 with local steps, and the 512-patch run at another
+    Courant number, FP32, to t_end (default 0.2).  Reports the
+    root-mean-square velocity of each run, their relative differences, and
+    the cell-updates each needed (the local-time-step saving)."""
+    import torch
+    from paper_1705_10774_gb300 import ics
+    from paper_1705_10774_gb300.dispatch import Dispatch
+    lay512, f = ics.config_turbulence(seed=10774, patches=PATCHES, n=NCELL, mach=2.0)
+    lay1 = ics.cartesian(1, PATCHES * NCELL)
+    t_end = args.t_end if args.t_end != 0.01 else 0.2
+    runs = {}
+    for name, lay, cfl in (("1_patch", lay1, 0.4), ("512_patches", lay512, 0.4), ("512_patches_cfl0.3", lay512, 0.3)):
+        st = [torch.from_numpy(a).float().cuda() for a in ics.to_patches(lay, f)]
+        g = Dispatch(lay.n, lay.lo, gamma=f.gamma, cfl=cfl, base_cells=lay.base_cells, box_len=lay.box_len,
+                     time_mode=1, precision=1, graph=1)
+        g.set_state(*st)
+        del st
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = g.advance(t_end=t_end)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        U = g.get_state()[0]
+        g.close()
+        npch = lay.npatch
+        U = U.reshape(npch, 5, -1)
+        rho = U[:, 0].astype(np.float64)
+        v2 = (U[:, 1].astype(np.float64) ** 2 + U[:, 2] ** 2 + U[:, 3] ** 2) / rho ** 2
+        runs[name] = {"cfl": cfl, "v_rms": float(np.sqrt(v2.mean())), "cell_updates": res["cell_updates"],
+                      "sweeps": res["sweeps"], "seconds": el, "cell_updates_per_s": res["cell_updates"] / el,
+                      "rho_sorted": np.sort(rho.ravel())}
+    r1, r5, r3 = runs["1_patch"], runs["512_patches"], runs["512_patches_cfl0.3"]
+    out = {"workload": "decaying MHD turbulence 256^3 (Mach 2, beta 1), FP32, local steps, t = 0 to %g" % t_end,
+           "v_rms_rel_diff_1_vs_512_patches": abs(r5["v_rms"] - r1["v_rms"]) / r1["v_rms"],
+           "v_rms_rel_diff_cfl_0.4_vs_0.3": abs(r5["v_rms"] - r3["v_rms"]) / r5["v_rms"],
+           "cell_updates_512_over_1_patch": r5["cell_updates"] / r1["cell_updates"],
+           # the density distributions (cell order differs between layouts)
+           "density_quantile_rel_diff_1_vs_512": float(np.max(np.abs(r5["rho_sorted"] - r1["rho_sorted"]))
+                                                       / np.max(r1["rho_sorted"])),
+           "runs": {k: {q: v for q, v in r.items() if q != "rho_sorted"} for k, r in runs.items()}}
+    print(json.dumps(out))
+
+
 def grace_arm(args):
     """Eq. 1's grace and the order of the time inter- and extrapolation of
     guard values (Sec. 3 B) on the local-step input (4096 patches of 16^3),
@@ -747,7 +793,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="turbulence",
-                    choices=["turbulence", "lts", "orszag-tang", "mixed", "amr", "cshock", "grace"],
+                    choices=["turbulence", "lts", "orszag-tang", "mixed", "amr", "cshock", "grace", "kitp"],
                     help="lts / orszag-tang: side measurements (one JSON line each), not the benchmark line")
     ap.add_argument("--t-end", type=float, default=0.01, help="end time of the lts / orszag-tang / mixed runs")
     ap.add_argument("--blocks", type=int, default=5, help="96^3 super-blocks per axis of the mixed run")
@@ -766,6 +812,8 @@ def main():
         return cshock_arm(args)
     if args.workload == "grace":
         return grace_arm(args)
+    if args.workload == "kitp":
+        return kitp_arm(args)
     if args.impl == "reference":
         reference_arm(args)
     else:
