@@ -6,8 +6,9 @@ the tests, by the smoke check and by the CPU-baseline leg of the benchmark,
 never by the product path.
 
 The oracle follows DISPATCH I (Nordlund et al. 2018): patches with guard zones
-filled by linear time interpolation (Sec. 3 A), readiness by Eq. (1) with
-grace 0, a time-sorted ready queue (Sec. 3 B) and local Courant steps
+filled by linear (or quadratic) time inter- and extrapolation (Sec. 3 A and
+B), readiness by Eq. (1) with grace g, a time-sorted ready queue (Sec. 3 B)
+and local Courant steps
 (Sec. 5.1); the MHD step is MUSCL-Hancock with HLL fluxes and constrained
 transport (Secs. 4.1 and 4.3 name the solver family; the scheme itself is the
 textbook one), optionally HLLD fluxes and the non-ideal Ohmic and ambipolar

@@ -4,14 +4,14 @@
 // Dispatcher (DISPATCH I, Sec. 3 B): each sweep runs three dispatcher kernels
 // and the update kernel on the context's stream.  The first publishes the
 // previous sweep (new slice becomes the newest, patch time += dt, schedule log
-// entry), the second finds every patch that is ready by Eq. (1) with grace 0
-// (t_P < t_end and t_P <= t_N for every neighbour N) and gives it its local
-// Courant step, the third compacts the ready patches in index order.  The
-// update kernel then advances every ready patch from the pre-sweep slices.  Because
-// ready neighbours share their time and every read touches only a
-// neighbour's two newest slices, any order of execution inside a sweep gives
-// the same result, and sweeping gives the same per-patch schedule as a
-// time-sorted ready queue.
+// entry), the second finds every patch that is ready by Eq. (1) (t_P < t_end
+// and t_P <= t_N + g dt_N for every neighbour N, and with g > 0 its oldest
+// slice no longer needed) and gives it its local Courant step, the third
+// compacts the ready patches in index order.  The update kernel then
+// advances every ready patch from the pre-sweep slices, and no patch writes a
+// slice another ready patch reads, so any order of execution inside a sweep
+// gives the same result; with g = 0 sweeping also gives the same per-patch
+// schedule as a time-sorted ready queue.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(EVAL_NT) plan_publish_kernel(DevCtx c) {
   if (threadIdx.x == 0 && s_cells) atomicAdd((unsigned long long *)&c.cnt[CNT_CELL_UPDATES], s_cells);
 }
 
-// Part 2 (one thread per patch): Eq. (1) with grace 0 and the local step of
+// Part 2 (one thread per patch): Eq. (1) and the local step of
 // every ready patch; rflag/rdt per patch, and whether any patch is behind
 // t_end.
 __global__ void __launch_bounds__(EVAL_NT) plan_ready_kernel(DevCtx c, double t_end) {

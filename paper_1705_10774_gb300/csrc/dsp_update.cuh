@@ -198,8 +198,9 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
 
   // Owner table of the padded tile: every block of the level's map that
   // cells in [x0-2, x0+tx+2] x [y0-2, y0+ty+2] x [z0-2, z0+tz+2] fall in, with
-  // the slices of its owning patch that supply time tP (a slice at exactly tP
-  // is copied, else the newest two are interpolated).  A block whose values
+  // the slices of its owning patch that supply time tP (pick_slices: a slice
+  // at exactly tP is copied, else two or three are inter- or extrapolated in
+  // time).  A block whose values
   // come from the other level points at the patch's cross-level guard
   // buffer, filled for time tP just before this update.
   const int *const gmap = c.gmap[lev];
