@@ -29,13 +29,16 @@ def patch_slices(lay, arrays, P):
 
 
 @pytest.mark.parametrize("precision", [0, 2])
-def test_turbulence_256cubed_sampled_patches_fp64(precision):
-    """512 patches of 32^3, global steps, both FP64 builds: after 3 steps the
+@pytest.mark.parametrize("opts", [{}, dict(riemann=1), dict(eta=1e-4, gamma_ad=75.0, rho_i=1.0)],
+                         ids=["hll", "hlld", "nonideal"])
+def test_turbulence_256cubed_sampled_patches_fp64(precision, opts):
+    """512 patches of 32^3, global steps, both FP64 builds, in each of the
+    benchmark's forms (HLL, HLLD faces, non-ideal terms): after 3 steps the
     oracle takes the GPU state, recomputes the global step and the 4th update
     of 8 patches."""
     lay, f = ics.config_turbulence(seed=10774, patches=8, n=32, mach=2.0)
     state = ics.to_patches(lay, f)
-    kw = dict(gamma=f.gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
+    kw = dict(gamma=f.gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len, **opts)
     g = Dispatch(lay.n, lay.lo, time_mode=0, precision=precision, **kw)
     g.set_state(*[torch.from_numpy(a).cuda() for a in state])
     g.advance(max_sweeps=3)
