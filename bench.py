@@ -825,7 +825,7 @@ def main():
     ap.add_argument("--nonideal", action="store_true",
                     help="--form runs: with the non-ideal terms of the benchmark's non-ideal forms")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="turbulence",
                     choices=["turbulence", "lts", "orszag-tang", "mixed", "amr", "cshock", "grace", "kitp"],
