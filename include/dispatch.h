@@ -14,8 +14,10 @@
  *   - a patch is ready when Eq. (1) holds for every neighbour:
  *     t_self <= t_nbor + g dt_nbor;
  *   - the update is one local Courant step (Sec. 5.1) of a MUSCL-Hancock
- *     scheme with HLL fluxes and constrained transport of face-centred B
- *     (Secs. 4.1 and 4.3 name the solver family; the paper prints no scheme);
+ *     scheme with HLL (or HLLD) fluxes and constrained transport of
+ *     face-centred B (Secs. 4.1 and 4.3 name the solver family; the paper
+ *     prints no scheme), optionally with the Ohmic and ambipolar terms of
+ *     Sec. 4.3;
  *   - the new state overwrites the oldest slice (Sec. 3 A).
  *
  * Every call returns 0 on success or one of the negative DSP_ERR_* codes.

@@ -1148,7 +1148,7 @@ static int update_patch(orc_ctx *c, int ip, double dt, double *oU, double *obx, 
       }
 
 #define EI(i, j, k) ((((int64_t)(k) + g) * (Ny + 1) + ((j) + g)) * (Nx + 1) + ((i) + g))
-  /* A7: HLL fluxes.  Face index i on axis d is the face at i-1/2 between
+  /* A7: HLL (or HLLD) fluxes.  Face index i on axis d is the face at i-1/2 between
    * cells i-1 and i; computed for all faces whose two cells lie in [-1, n]. */
   for (int d = 0; d < 3; d++) {
     int ex = d == 0, ey = d == 1, ez = d == 2;

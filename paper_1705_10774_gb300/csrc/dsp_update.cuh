@@ -4,13 +4,14 @@
 // run of tz planes along z.  The block marches through the planes; for each
 // plane it
 //   A  takes the next plane of the padded tile (radius 2) from the patch's
-//      own newest slice and its neighbours' slices, interpolating linearly in
-//      time where a neighbour is ahead (DISPATCH I, Sec. 3 A), and converts to
+//      own newest slice and its neighbours' slices, inter- or extrapolating
+//      in time where a neighbour is not at the patch's time (DISPATCH I,
+//      Sec. 3 A and B), and converts to
 //      primitive variables (the plane's copies were started asynchronously
 //      one plane earlier, so only the time blends remain to compute);
 //   B  computes MC-limited slopes and the Hancock half-step predictor;
-//   C  computes HLL fluxes through the x- and y-faces of the plane and the
-//      z-faces below it;
+//   C  computes HLL (or HLLD) fluxes through the x- and y-faces of the
+//      plane and the z-faces below it;
 //   D  computes the upwind edge EMFs on the x- and y-edges below the plane and
 //      the in-plane part of the flux divergence;
 //   E  writes the conservative update of the plane below and the
@@ -18,6 +19,9 @@
 //      (the oldest slice is overwritten, Sec. 3 A);
 //   F  computes the z-edge EMFs of the plane, the signal speed of the freshly
 //      written cells, and the values carried to the next plane.
+// With the non-ideal terms (NI) phases D and F add the Ohmic and ambipolar
+// EMFs to the edges, and the Poynting flux of those EMFs joins the energy
+// flux before the update of the plane below (DISPATCH I, Sec. 4.3).
 // Every intermediate lives in shared memory; HBM sees the gathered input and
 // the written output only.  The arithmetic per cell, face and edge is the
 // same sequence of operations as the oracle's, so the FP64 build (no FMA
