@@ -50,12 +50,12 @@ NONIDEAL = dict(eta=1e-4, gamma_ad=75.0, rho_i=1.0)
 # by compiled variant, from ncu's dram__bytes_read.sum + dram__bytes_write.sum
 # (FP64: a 216-patch capture of the same kernel, scaled by cells; FP32: the
 # full workload); a variant without an entry reports null.
-TRAFFIC_F64 = {2: (550.253568e6 + 420.952832e6) * 512 / 216, 3: (547.967488e6 + 420.902144e6) * 512 / 216,
-               4: (549.530368e6 + 420.683776e6) * 512 / 216}
-TRAFFIC_F32 = {5: 624.325888e6 + 509.780992e6}
+TRAFFIC_F64 = {2: (550.772736e6 + 421.459712e6) * 512 / 216, 3: (551.252736e6 + 421.417472e6) * 512 / 216,
+               4: (552.264960e6 + 424.443648e6) * 512 / 216}
+TRAFFIC_F32 = {5: 626.309120e6 + 509.839360e6}
 # the same for the HLLD variants (FP64 FMA: the 216-patch capture, scaled)
-TRAFFIC_F64_HLLD = {10: (537.724160e6 + 421.700608e6) * 512 / 216}
-TRAFFIC_F32_HLLD = {}
+TRAFFIC_F64_HLLD = {10: (538.658560e6 + 421.405696e6) * 512 / 216}
+TRAFFIC_F32_HLLD = {11: 622.772736e6 + 510.983424e6}
 
 
 def radius2_guard_fraction(n):
