@@ -466,8 +466,17 @@ def cpu_baseline(lay, state, target_s=12.0):
             break
     dt = time.perf_counter() - t0
     cells = o.stats()["cell_updates"]
+    # one core: single patch updates (the oracle parallelises over patches only)
+    step = min(o.patch_dt(i) for i in range(lay.npatch))
+    t1 = time.perf_counter()
+    for P in range(8):
+        o.update_patch(P, step)
+    d1 = time.perf_counter() - t1
+    c1 = 8 * int(np.prod(lay.n[0]))
     return {"value": cells / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d global step(s) of the 256^3 / 512-patch workload (%d cell-updates, %.1f s)" % (n, cells, dt)}
+            "sample": "%d global step(s) of the 256^3 / 512-patch workload (%d cell-updates, %.1f s)" % (n, cells, dt),
+            "single_core": {"value": c1 / d1, "unit": UNIT, "cores": 1,
+                            "sample": "8 patch updates of 32^3 (%d cell-updates, %.2f s)" % (c1, d1)}}
 
 
 def reference_arm(args):
