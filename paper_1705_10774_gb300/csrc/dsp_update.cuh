@@ -77,7 +77,12 @@ struct Lay {
   static constexpr int oENZ = oENY + (NI ? 2 * H1N : 0);
   static constexpr int oFXE = oENZ + (NI ? H1N : 0);
   static constexpr int oFYE = oFXE + (NI ? 2 * H1N : 0);
-  static constexpr int total = oFYE + (NI ? 2 * H1N : 0);
+  // and the edge currents: x- and y-edges of the level below each of two
+  // planes, z-edges of two planes (rings by plane parity)
+  static constexpr int oJX = oFYE + (NI ? 2 * H1N : 0);
+  static constexpr int oJY = oJX + (NI ? 2 * H1N : 0);
+  static constexpr int oJZ = oJY + (NI ? 2 * H1N : 0);
+  static constexpr int total = oJZ + (NI ? 2 * H1N : 0);
 };
 
 
@@ -452,9 +457,28 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
   auto fyq = [&](int i, int j, int q) -> T { return fpl(q)[FPN + F5(i, j)]; };
   auto fzq = [&](int i, int j, int q) -> T { return fpl(q)[2 * FPN + F5(i, j)]; };
   auto wc = [&](int k, int i, int j, int q) -> T { return wpl(q)[k * H2N + H2(i, j)]; };
-  auto Jx = [&](int i, int j, int q) -> T { return ((fzq(i, j, q) - fzq(i, j - 1, q)) - (fyq(i, j, q) - fyq(i, j, q - 1))) * idx; };
-  auto Jy = [&](int i, int j, int q) -> T { return ((fxq(i, j, q) - fxq(i, j, q - 1)) - (fzq(i, j, q) - fzq(i - 1, j, q))) * idx; };
-  auto Jz = [&](int i, int j, int q) -> T { return ((fyq(i, j, q) - fyq(i - 1, j, q)) - (fxq(i, j, q) - fxq(i, j - 1, q))) * idx; };
+  // currents from faces (computed once per plane into rings, read by Jx/Jy/Jz)
+  auto Jx_f = [&](int i, int j, int q) -> T { return ((fzq(i, j, q) - fzq(i, j - 1, q)) - (fyq(i, j, q) - fyq(i, j, q - 1))) * idx; };
+  auto Jy_f = [&](int i, int j, int q) -> T { return ((fxq(i, j, q) - fxq(i, j, q - 1)) - (fzq(i, j, q) - fzq(i - 1, j, q))) * idx; };
+  auto Jz_f = [&](int i, int j, int q) -> T { return ((fyq(i, j, q) - fyq(i - 1, j, q)) - (fxq(i, j, q) - fxq(i, j - 1, q))) * idx; };
+  T *const JXr = sm + L::oJX;
+  T *const JYr = sm + L::oJY;
+  T *const JZr = sm + L::oJZ;
+  auto jring = [&](int q) -> int { return ((q - z0 + 2) & 1) * H1N; };
+  auto Jx = [&](int i, int j, int q) -> T { return JXr[jring(q) + H1(i, j)]; };
+  auto Jy = [&](int i, int j, int q) -> T { return JYr[jring(q) + H1(i, j)]; };
+  auto Jz = [&](int i, int j, int q) -> T { return JZr[jring(q) + H1(i, j)]; };
+  // x- and y-edge currents of the level below plane q and z-edge currents of
+  // plane q-1, over the H1 region (faces of planes q-1 and q)
+  auto currents = [&](int q) {
+    for (int ci = tid; ci < (TX + 2) * (TY + 2); ci += NT) {
+      const int i = ci % (TX + 2) - 1, j = ci / (TX + 2) - 1, h = H1(i, j);
+      if (i > tx || j > ty) continue;
+      JXr[jring(q) + h] = Jx_f(i, j, q);
+      JYr[jring(q) + h] = Jy_f(i, j, q);
+      JZr[jring(q - 1) + h] = Jz_f(i, j, q - 1);
+    }
+  };
   auto ni_law = [&](T Je, T Ba, T Bb, T Be, T re, T Ja, T Jb) -> T {
     T en = T(0);
     if (c.eta > 0.0) en = eta_t * Je;
@@ -532,6 +556,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     }
     __syncthreads();
     prim_plane(p + 1);
+    if constexpr (NI != 0) currents(p + 1);
     __syncthreads();
 
     // ---- B: slopes and predictor on the H1 region of plane p
