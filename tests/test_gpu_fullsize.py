@@ -59,6 +59,38 @@ def test_turbulence_256cubed_sampled_patches_fp64(precision, opts):
             assert rel_linf(a, b) <= TOL64
 
 
+@pytest.mark.parametrize("opts", [{}, dict(riemann=1), dict(eta=1e-4, gamma_ad=75.0, rho_i=1.0)],
+                         ids=["hll", "hlld", "nonideal"])
+def test_turbulence_256cubed_sampled_patches_fp32(opts):
+    """The benchmark's FP32 forms (autotuned, global steps) at full size:
+    after 3 steps the oracle takes the GPU's FP32 state (exactly, in FP64)
+    and recomputes the 4th update of 8 patches with the GPU's step, within
+    1e-5 of each patch's largest value; the step is the oracle's (the FP32
+    signal speeds may move it across a power of two only in rare ties)."""
+    lay, f = ics.config_turbulence(seed=10774, patches=8, n=32, mach=2.0)
+    state = ics.to_patches(lay, f)
+    kw = dict(gamma=f.gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len, **opts)
+    g = Dispatch(lay.n, lay.lo, time_mode=0, precision=1, **kw)
+    g.set_state(*[torch.from_numpy(a).float().cuda() for a in state])
+    g.autotune(reps=1)
+    g.advance(max_sweeps=3)
+    snap = g.get_state()
+    t3 = g.times()[0]
+    g.advance(max_sweeps=1)
+    after = g.get_state()
+    t4, dt4 = g.times()
+    dt = float(dt4[0])
+    o = Oracle(lay.n, lay.lo, t0=float(t3[0]), **kw)
+    o.set_state(*snap)
+    assert min(o.patch_dt(i) for i in range(lay.npatch)) == dt
+    for P in (0, 7, 63, 64, 200, 365, 448, 511):
+        ref = o.update_patch(P, dt)[:4]
+        got = patch_slices(lay, after, P)
+        scale = max(float(np.max(np.abs(b))) for b in ref)
+        for a, b in zip(got, ref):
+            assert float(np.max(np.abs(a - b))) <= 1e-5 * scale
+
+
 def parse_save(blob, lay, nslot):
     magic = blob[:8]
     assert magic.startswith(b"DSPSAVE")
