@@ -360,3 +360,32 @@ def test_cshock_from_the_table1_jump_reaches_the_steady_profile(name):
         assert ratio == 1.0
     else:
         assert ratio == 2.0, ratio
+
+
+def test_all_options_together_keep_div_b_zero_and_conserve():
+    """HLLD faces, both non-ideal terms, grace and quadratic time
+    interpolation at once: on one level mass, momentum and total energy stay
+    conserved to round-off under global steps; on two levels (local steps)
+    every patch keeps zero divergence of its own faces."""
+    opt = dict(riemann=1, eta=0.01, gamma_ad=50.0, rho_i=0.7, grace=0.3, time_order=2, nslices=4)
+    lay, f = ics.config_turbulence(seed=5, patches=2, n=8, mach=1.0)
+    o = Oracle(lay.n, lay.lo, gamma=f.gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len, time_mode=0,
+               **opt)
+    o.set_state(*ics.to_patches(lay, f))
+    d0 = o.diagnostics()
+    o.advance(max_sweeps=6)
+    d1 = o.diagnostics()
+    U = o.get_state()[0]
+    tol = 1e-13 * 6 * np.abs(U).sum() * lay.dx ** 3
+    assert abs(d1["mass"] - d0["mass"]) <= tol and abs(d1["energy"] - d0["energy"]) <= tol
+    assert np.all(np.abs(d1["mom"] - d0["mom"]) <= tol)
+    assert d1["max_divb"] <= 1e-13 * d1["max_b"]
+    from test_gpu_levels import layouts, smooth_state
+    lay2 = layouts()["mixed_level1"]
+    o2 = Oracle(lay2.n, lay2.lo, level=lay2.levels, gamma=G53, cfl=0.4, base_cells=lay2.base_cells,
+                box_len=lay2.box_len, time_mode=1, **opt)
+    o2.set_state(*smooth_state(lay2))
+    o2.advance(t_end=0.01)
+    d2 = o2.diagnostics()
+    assert d2["max_divb"] <= 1e-13 * d2["max_b"]
+    assert np.all(o2.get_times()[0] == 0.01)
