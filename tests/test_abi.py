@@ -111,3 +111,35 @@ def test_layout_rules_are_checked_on_the_host():
     n_odd = two.n.copy()
     n_odd[-1] = (7, 8, 8)
     assert code(n_odd, two.lo, two.levels) == D.DSP_ERR_INVALID_ARG
+
+
+def test_parameters_are_checked_on_the_host():
+    """dsp_create rejects bad physics and dispatcher parameters before
+    touching the device: grace outside [0, 1) or with the ready queue, an
+    unknown time order or Riemann solver, too many slices, quadratic
+    extrapolation with three slices, negative non-ideal coefficients or
+    factors, an ambipolar term without ion density, and a variant id of the
+    wrong solver or physics."""
+    from paper_1705_10774_gb300 import ics
+    lay = ics.cartesian(2, 8)
+    kw = dict(gamma=5 / 3, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len, time_mode=1)
+
+    def code(**extra):
+        with __import__("pytest").raises(D.DispatchError) as e:
+            D.Dispatch(lay.n, lay.lo, **kw, **extra)
+        return e.value.code
+
+    INV, UNS = D.DSP_ERR_INVALID_ARG, D.DSP_ERR_UNSUPPORTED
+    assert code(grace=1.0) == INV
+    assert code(grace=-0.1) == INV
+    assert code(grace=0.3, dispatcher=0) == UNS
+    assert code(time_order=3) == INV
+    assert code(nslices=17) == INV
+    assert code(grace=0.3, time_order=2, nslices=3) == INV
+    assert code(riemann=2) == INV
+    assert code(eta=-1.0) == INV
+    assert code(gamma_ad=-1.0) == INV
+    assert code(gamma_ad=2.0, rho_i=0.0) == INV
+    assert code(eta=0.1, c_ohm=-1.0) == INV
+    assert code(riemann=1, variant=0) == INV        # an HLL variant
+    assert code(eta=0.1, variant=2) == INV          # an ideal-MHD variant
