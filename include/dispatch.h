@@ -163,13 +163,18 @@ typedef struct {
 /* Counters of one dsp_advance call.  kernel_ms and kernel_launches are the
  * summed device time and the number of launches of the update kernel (only
  * when timing was requested); plan_launches counts the dispatcher kernels
- * (three per sweep) and, with two levels, the cross-level guard kernel. */
+ * (three per sweep) and, with two levels, the cross-level guard kernel.
+ * fallbacks counts cells whose reconstruction fell back to first order (a
+ * face state with rho <= 0 or p <= 0); floors counts cells of new slices
+ * whose pressure recovery took the floor p >= 1e-20 rho (both 0 on smooth
+ * inputs; the paper states neither, see dsp_params). */
 typedef struct {
   int64_t patch_updates, cell_updates, sweeps, fallbacks;
   double t_min, t_max;
   int32_t status;
   double kernel_ms;
   int64_t kernel_launches, plan_launches;
+  int64_t floors;
 } dsp_stats;
 
 /* One schedule entry: patch index, start time, step. */
@@ -185,8 +190,11 @@ typedef struct {
   double mass, mom[3], energy, bmean[3], max_divb, max_b;
 } dsp_diag;
 
-/* Create a context: validates the layout, builds the neighbour tables,
- * allocates every slice on the current CUDA device.  stream is a
+/* Create a context (the task list of Sec. 2.2 for a set of patches, each the
+ * patch data type of Sec. 2.1 laid out as by the "cartesian" component of
+ * Sec. 2.3, with nslices time slices of Sec. 3 A): validates the layout,
+ * builds the neighbour ("nbor") tables, allocates every slice on the current
+ * CUDA device.  stream is a
  * cudaStream_t (NULL = legacy default stream).  On success *out owns all
  * device memory until dsp_destroy.  Neighbours are symmetric: on the same
  * level, patches whose interior meets the padded box; across levels,
@@ -198,7 +206,9 @@ typedef struct {
 DSP_API int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const dsp_params *params, void *stream,
                dsp_ctx **out);
 
-/* Load the state of patches [first, first+count) into their first slice at
+/* Load the state of patches [first, first+count) (the interior state
+ * variables of Sec. 3 A; guard zones are never stored, they are filled from
+ * the neighbours' slices at each update) into their first slice at
  * time t0 (and reset every patch's time to t0 when first == 0 and count ==
  * npatch).  Arrays are the concatenation, in patch order, of each patch's
  * interior: U[5][nz][ny][nx] (rho, m_x, m_y, m_z, E), bx[nz][ny][nx+1],
@@ -209,28 +219,55 @@ DSP_API int dsp_set_state(dsp_ctx *ctx, int32_t first, int32_t count, const void
                   const void *bz, int32_t dtype, int32_t on_device);
 
 /* Advance until every patch has reached t_end, or until max_sweeps sweeps
- * have run (<= 0: no limit; then t_end must be finite).  Synchronous: returns
- * after the device work finished, with the status of the run.  out may be NULL. */
+ * have run (<= 0: no limit; then t_end must be finite): the task list's
+ * execute procedure of Sec. 2.2, which calls the update of Sec. 3 B (select
+ * the ready tasks by Eq. 1, update each, re-check its neighbours) until every
+ * task reached its final time.  Each patch update is the single-task cycle
+ * of Sec. 3 A: guard zones by time interpolation, one local Courant step
+ * (Sec. 5.1), the new state into the oldest slice.  Synchronous: returns
+ * after the device work finished, with the status of the run (a non-zero
+ * status also poisons the context, see above).  A sweep limit ends the call
+ * between sweeps, leaving a consistent state.  out may be NULL. */
 DSP_API int dsp_advance(dsp_ctx *ctx, double t_end, int64_t max_sweeps, dsp_stats *out);
 
-/* Copy the newest slice of patches [first, first+count) out, same layout and
- * dtype/on_device conventions as dsp_set_state. */
+/* Copy the newest slice (Sec. 3 A, the most recent state of the circular
+ * buffer) of patches [first, first+count) out, same layout and
+ * dtype/on_device conventions as dsp_set_state.  The caller owns the arrays;
+ * host arrays are staged through a library-owned device buffer.  Valid on a
+ * poisoned context. */
 DSP_API int dsp_get_state(dsp_ctx *ctx, int32_t first, int32_t count, void *U, void *bx, void *by, void *bz,
                   int32_t dtype, int32_t on_device);
 
-/* Per-patch time of the newest slice and last step (host arrays of npatch). */
+/* Per-patch time of the newest slice and last step (the task times and time
+ * steps of Sec. 2.1 that Eq. 1 compares), into host arrays of npatch values
+ * owned by the caller; dt_last may be NULL.  Valid on a poisoned context. */
 DSP_API int dsp_get_times(dsp_ctx *ctx, double *t, double *dt_last);
 
-/* Copy up to cap schedule entries, in execution order; *n receives the
- * total recorded so far.  Returns DSP_ERR_SCHEDULE_OVERFLOW if more updates
- * ran than the log's capacity (the first capacity entries are still valid). */
+/* Copy up to cap schedule entries (one per patch update: which task the
+ * dispatcher of Sec. 3 B updated, from which time, by which step), in
+ * execution order (patch order within a sweep), into the caller's host
+ * buffer; *n receives the total recorded so far.  Returns
+ * DSP_ERR_SCHEDULE_OVERFLOW if more updates ran than the log's capacity
+ * (dsp_params.sched_capacity; the first capacity entries are still valid).
+ * buf may be NULL to query *n.  Valid on a poisoned context. */
 DSP_API int dsp_get_schedule(dsp_ctx *ctx, dsp_sched_entry *buf, int64_t cap, int64_t *n);
 
+/* Diagnostics of the newest slices of every patch (see dsp_diag): the paper
+ * has no counterpart (its validation, Sec. 5, compares runs rather than
+ * sums); they serve the conservation and div B checks.  Every cell counts
+ * with its own level's cell volume (level-0 cells under a refined region
+ * too); each face counts once, as the low face of a cell; the sums are FP64
+ * Neumaier-compensated per patch in a fixed order, then over patches in patch
+ * order, so the result is deterministic.  Allocates a small device buffer
+ * (10 doubles per patch) for the per-patch partials; writes *out on the
+ * host.  Valid on a poisoned context. */
 DSP_API int dsp_diagnostics(dsp_ctx *ctx, dsp_diag *out);
 
 /* Autotuner: time every compiled variant of the update kernel that fits this
  * context (tile shape, threads per block, blocks per SM) on the next sweep's
- * real ready list, `reps` launches each, and keep the fastest.  Nothing is
+ * real ready list, `reps` launches each, and keep the fastest.  The paper has
+ * no autotuner; its Sec. 5.3 notes that the best patch size depends on the
+ * problem and the hardware, and on a GPU so does the tiling of a patch.  Nothing is
  * published and the state is unchanged (the update writes only the patches'
  * next slot); all variants compute bit-identical results.  Call after
  * dsp_set_state, before dsp_advance.  Writes the chosen variant id, and for
@@ -242,10 +279,13 @@ DSP_API int dsp_autotune(dsp_ctx *ctx, int32_t reps, int32_t *chosen, double *ms
 /* Maximum number of patches dsp_diagnostics_noalloc accepts. */
 #define DSP_NOALLOC_MAX_PATCHES 16384
 
-/* The same diagnostics as dsp_diagnostics, computed from a state held in the
+/* The diagnostics of dsp_diagnostics, computed from a state held in the
  * caller's own device arrays (the dsp_set_state layout: U, bx, by, bz
  * concatenated over npatch patches of n[0] x n[1] x n[2] cells, cell size dx;
  * dtype 0 = float64, 1 = float32), without allocating any device memory.
+ * Unlike dsp_diagnostics, every patch must have the same size n and the
+ * same cell size dx (one level, one patch size): mixed sizes or a second
+ * level need dsp_diagnostics.
  * This entry point has no counterpart in the paper; it exists for callers
  * that cannot call cudaMalloc: a host application that hands all device
  * memory to its own pool allocator and forbids raw allocations, or a
@@ -264,7 +304,9 @@ DSP_API int dsp_diagnostics_noalloc(const void *U, const void *bx, const void *b
                                     int32_t npatch, const int32_t *n, double dx, void *stream, dsp_diag *out);
 
 /* Save the whole dispatcher state (every slice, its time and signal speed,
- * the newest-slice index and last step of every patch) into host memory.
+ * the newest-slice index and last step of every patch) into host memory: a
+ * snapshot suitable for restarting, as the I/O view of Sec. 3 E asks of
+ * DISPATCH snapshots (one binary blob here, no file format).
  * Layout: a 40-byte header (char magic[8] = "DSPSAVE", int32 version = 1,
  * npatch, nslices, precision, int64 reserved, int64 slot_stride), then
  * double t[npatch][nslices], double smax[npatch][nslices], int32
@@ -278,9 +320,11 @@ DSP_API int dsp_save(dsp_ctx *ctx, void *buf, size_t cap, size_t *used);
 DSP_API int dsp_load(dsp_ctx *ctx, const void *buf, size_t size);
 
 /* Message of the last error on this context ("" if none).  Valid until the
- * next call on the context. */
+ * next call on the context.  No counterpart in the paper. */
 DSP_API const char *dsp_last_error(dsp_ctx *ctx);
 
+/* Release every device and host allocation of the context (after the
+ * context's stream has finished its work).  NULL is ignored. */
 DSP_API void dsp_destroy(dsp_ctx *ctx);
 
 #ifdef __cplusplus

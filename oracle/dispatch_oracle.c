@@ -88,6 +88,7 @@ typedef struct {
   int64_t *s_patch;
   double *s_t, *s_dt;
   int64_t n_updates, n_cells, n_sweeps, n_fallback;
+  int64_t n_floor; /* cells of new slices whose pressure recovery took the floor */
   int status;
   char err[256];
 } orc_ctx;
@@ -100,8 +101,8 @@ typedef struct {
  * cell.  Heaviside-Lorentz units (E = -v x B, J = curl B, Sec. 4.3): total
  * energy E = p/(gamma-1) + rho v^2/2 + B^2/2; cell-centred B is the mean of
  * the two faces. */
-static void prim(const double u[5], double bxl, double bxr, double byl, double byr,
-                 double bzl, double bzr, double gamma, double W[8]) {
+static int prim(const double u[5], double bxl, double bxr, double byl, double byr,
+                double bzl, double bzr, double gamma, double W[8]) {
   double rho = u[0];
   double irho = 1.0 / rho;
   double Bx = 0.5 * (bxl + bxr);
@@ -113,9 +114,11 @@ static void prim(const double u[5], double bxl, double bxr, double byl, double b
   double ke = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
   double me = 0.5 * (Bx * Bx + By * By + Bz * Bz);
   double p = (gamma - 1.0) * (u[4] - ke - me);
+  int floored = p < PFLOOR * rho;
   p = fmax(p, PFLOOR * rho);
   W[RHO] = rho; W[VX] = vx; W[VY] = vy; W[VZ] = vz; W[PR] = p;
   W[BX] = Bx; W[BY] = By; W[BZ] = Bz;
+  return floored; /* 1 if the pressure floor was taken */
 }
 
 /* Fast magnetosonic speed along the axis whose field component is bn:
@@ -693,7 +696,7 @@ int orc_set_state(orc_ctx *c, const double *U, const double *bx, const double *b
     if (bad) { snprintf(c->err, sizeof c->err, "non-positive rho or p in patch %d", i); return ORC_EUNPHYS; }
   }
   c->nsched = 0;
-  c->n_updates = c->n_cells = c->n_sweeps = c->n_fallback = 0;
+  c->n_updates = c->n_cells = c->n_sweeps = c->n_fallback = c->n_floor = 0;
   c->status = 0;
   return ORC_OK;
 }
@@ -1057,7 +1060,7 @@ int orc_fill_padded(orc_ctx *c, int ip, double *U, double *bx, double *by, doubl
 /* Advance patch ip by dt from its current time, writing the new interior
  * state into the given arrays and its signal-speed sum into *smax_out. */
 static int update_patch(orc_ctx *c, int ip, double dt, double *oU, double *obx, double *oby, double *obz,
-                        double *smax_out, int64_t *nfallback) {
+                        double *smax_out, int64_t *nfallback, int64_t *nfloor) {
   opatch *P = &c->p[ip];
   int g = c->g;
   int nx = P->n[0], ny = P->n[1], nz = P->n[2];
@@ -1348,9 +1351,9 @@ static int update_patch(orc_ctx *c, int ip, double dt, double *oU, double *obx, 
           int64_t id = ((int64_t)k * ny + j) * nx + i;
           double u[5], w8[8];
           for (int q = 0; q < 5; q++) u[q] = oU[q * nc + id];
-          prim(u, obx[((int64_t)k * ny + j) * (nx + 1) + i], obx[((int64_t)k * ny + j) * (nx + 1) + i + 1],
-               oby[((int64_t)k * (ny + 1) + j) * nx + i], oby[((int64_t)k * (ny + 1) + j + 1) * nx + i],
-               obz[((int64_t)k * ny + j) * nx + i], obz[((int64_t)(k + 1) * ny + j) * nx + i], gamma, w8);
+          *nfloor += prim(u, obx[((int64_t)k * ny + j) * (nx + 1) + i], obx[((int64_t)k * ny + j) * (nx + 1) + i + 1],
+                          oby[((int64_t)k * (ny + 1) + j) * nx + i], oby[((int64_t)k * (ny + 1) + j + 1) * nx + i],
+                          obz[((int64_t)k * ny + j) * nx + i], obz[((int64_t)(k + 1) * ny + j) * nx + i], gamma, w8);
           if (!(w8[RHO] > 0.0) || !(w8[PR] > 0.0)) bad = 1;
           double ir = 1.0 / w8[RHO];
           double cx = cfast(gamma, ir, w8[PR], w8[BX], w8[BY], w8[BZ]);
@@ -1467,8 +1470,8 @@ static void publish(orc_ctx *c, int ip, double dt, double smax) {
 /* Compute one update of patch ip by dt into caller arrays, without
  * publishing it (reproduces a single update for sampled comparisons). */
 int orc_update_patch(orc_ctx *c, int ip, double dt, double *U, double *bx, double *by, double *bz, double *smax) {
-  int64_t nf = 0;
-  return update_patch(c, ip, dt, U, bx, by, bz, smax, &nf);
+  int64_t nf = 0, nfl = 0;
+  return update_patch(c, ip, dt, U, bx, by, bz, smax, &nf, &nfl);
 }
 
 /* One sweep: snapshot every time, collect the ready set R, update every
@@ -1492,21 +1495,23 @@ static int sweep(orc_ctx *c, double t_end, int *nready) {
     for (int r = 1; r < nr; r++) m = fmin(m, dt[r]);
     for (int r = 0; r < nr; r++) dt[r] = m;
   }
-  int64_t nfb = 0;
+  int64_t nfb = 0, nfl = 0;
   int err = ORC_OK;
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nfb)
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nfb, nfl)
   for (int r = 0; r < nr; r++) {
     opatch *P = &c->p[R[r]];
     int ns = (P->latest + 1) % c->nslot;
-    int64_t f = 0;
-    int e = update_patch(c, R[r], dt[r], P->U[ns], P->bx[ns], P->by[ns], P->bz[ns], &sm[r], &f);
+    int64_t f = 0, fl = 0;
+    int e = update_patch(c, R[r], dt[r], P->U[ns], P->bx[ns], P->by[ns], P->bz[ns], &sm[r], &f, &fl);
     nfb += f;
+    nfl += fl;
     if (e) {
 #pragma omp critical
       err = e;
     }
   }
   c->n_fallback += nfb;
+  c->n_floor += nfl;
   if (err) { rc = err; goto out; }
   for (int r = 0; r < nr; r++) publish(c, R[r], dt[r], sm[r]);
   c->n_sweeps++;
@@ -1538,9 +1543,10 @@ static int queue_run(orc_ctx *c, double t_end) {
     rc = patch_dt(c, best, t_end, &dt);
     if (rc) break;
     int ns = (P->latest + 1) % c->nslot;
-    int64_t f = 0;
-    rc = update_patch(c, best, dt, P->U[ns], P->bx[ns], P->by[ns], P->bz[ns], &sm, &f);
+    int64_t f = 0, fl = 0;
+    rc = update_patch(c, best, dt, P->U[ns], P->bx[ns], P->by[ns], P->bz[ns], &sm, &f, &fl);
     c->n_fallback += f;
+    c->n_floor += fl;
     if (rc) break;
     publish(c, best, dt, sm);
     if (!queued[best] && ready(c, best, t_end)) queued[best] = 1;
@@ -1601,6 +1607,7 @@ void orc_stats(orc_ctx *c, int64_t *out) {
   out[1] = c->n_cells;
   out[2] = c->n_sweeps;
   out[3] = c->n_fallback;
+  out[4] = c->n_floor;
 }
 
 /* ------------------------------------------------------------------ */

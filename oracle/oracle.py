@@ -192,10 +192,10 @@ class Oracle:
         return p, t, dt
 
     def stats(self):
-        out = np.zeros(4, np.int64)
+        out = np.zeros(5, np.int64)
         lib().orc_stats(self._h, _ptr(out))
         return dict(patch_updates=int(out[0]), cell_updates=int(out[1]), sweeps=int(out[2]),
-                    fallbacks=int(out[3]))
+                    fallbacks=int(out[3]), floors=int(out[4]))
 
     def diagnostics(self):
         out = np.zeros(10)

@@ -23,6 +23,7 @@
 #include <string>
 #include <vector>
 
+#include "dsp_diag.cuh"
 #include "dsp_dispatch.cuh"
 #include "dsp_internal.h"
 #include "dsp_levels.cuh"
@@ -372,69 +373,18 @@ __global__ void queue_init_kernel(DevCtx c, double t_end) {
   }
 }
 
-struct NSum {
-  double s, c;
-};
-__device__ __forceinline__ void nadd(NSum &a, double x) {
-  const double t = a.s + x;
-  if (fabs(a.s) >= fabs(x)) a.c += (a.s - t) + x;
-  else a.c += (x - t) + a.s;
-  a.s = t;
-}
-
-// Per-patch compensated sums of the newest slice (deterministic order:
-// fixed strided assignment, then a fixed tree), plus max |div b| and max |b|.
+// Per-patch diagnostics of the newest slice (dsp_diag.cuh): one block per
+// patch, with the patch's own level's cell volume.
 template <typename T>
-__global__ void diag_kernel(DevCtx c, double *out) {
+__global__ void __launch_bounds__(DIAG_NT) diag_kernel(DevCtx c, double *out) {
   const int P = blockIdx.x;
-  const int s = c.latest[P];
   const PatchGeo &g = c.geo[P];
-  const T *base = (const T *)c.slab + (long long)s * c.slot_stride + g.off;
+  const T *base = (const T *)c.slab + (long long)c.latest[P] * c.slot_stride + g.off;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const long long nc = (long long)nx * ny * nz;
   const T *bxa = base + 5 * nc, *bya = bxa + (long long)(nx + 1) * ny * nz, *bza = bya + (long long)nx * (ny + 1) * nz;
   const double dxl = ldexp(c.dx, -g.level);
-  const double dV = dxl * dxl * dxl;
-  (void)nz;
-  NSum acc[8];
-  for (int q = 0; q < 8; q++) acc[q].s = acc[q].c = 0.0;
-  double mdiv = 0.0, mb = 0.0;
-  for (long long id = threadIdx.x; id < nc; id += blockDim.x) {
-    const int i = (int)(id % nx), j = (int)((id / nx) % ny), k = (int)(id / ((long long)nx * ny));
-    for (int q = 0; q < 5; q++) nadd(acc[q], (double)base[q * nc + id] * dV);
-    const double bxl = bxa[((long long)k * ny + j) * (nx + 1) + i], bxr = bxa[((long long)k * ny + j) * (nx + 1) + i + 1];
-    const double byl = bya[((long long)k * (ny + 1) + j) * nx + i], byr = bya[((long long)k * (ny + 1) + j + 1) * nx + i];
-    const double bzl = bza[((long long)k * ny + j) * nx + i], bzr = bza[((long long)(k + 1) * ny + j) * nx + i];
-    nadd(acc[5], bxl * dV);
-    nadd(acc[6], byl * dV);
-    nadd(acc[7], bzl * dV);
-    mdiv = fmax(mdiv, fabs((bxr - bxl) + (byr - byl) + (bzr - bzl)));
-    mb = fmax(mb, fmax(fabs(bxl), fmax(fabs(byl), fabs(bzl))));
-  }
-  __shared__ double sh[256][18];
-  for (int q = 0; q < 8; q++) {
-    sh[threadIdx.x][2 * q] = acc[q].s;
-    sh[threadIdx.x][2 * q + 1] = acc[q].c;
-  }
-  sh[threadIdx.x][16] = mdiv;
-  sh[threadIdx.x][17] = mb;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    NSum tot[8];
-    for (int q = 0; q < 8; q++) tot[q].s = tot[q].c = 0.0;
-    double md = 0.0, mm = 0.0;
-    for (int t = 0; t < (int)blockDim.x; t++) {
-      for (int q = 0; q < 8; q++) {
-        nadd(tot[q], sh[t][2 * q]);
-        nadd(tot[q], sh[t][2 * q + 1]);
-      }
-      md = fmax(md, sh[t][16]);
-      mm = fmax(mm, sh[t][17]);
-    }
-    for (int q = 0; q < 8; q++) out[(long long)P * 10 + q] = tot[q].s + tot[q].c;
-    out[(long long)P * 10 + 8] = md;
-    out[(long long)P * 10 + 9] = mm;
-  }
+  diag_patch<T>(base, bxa, bya, bza, nx, ny, nz, dxl * dxl * dxl, out + (long long)P * DIAG_PER);
 }
 
 int launch_queue(dsp_ctx *c, double t_end) { return c->var->launch_queue(c->d, c->grid_update, t_end, c->stream); }
@@ -1059,6 +1009,7 @@ int advance_queue(dsp_ctx *c, double t_end, const long long *c0, dsp_stats *out)
     out->cell_updates = c1[CNT_CELL_UPDATES] - c0[CNT_CELL_UPDATES];
     out->sweeps = 0;
     out->fallbacks = c1[CNT_FALLBACKS] - c0[CNT_FALLBACKS];
+    out->floors = c1[CNT_FLOORS] - c0[CNT_FLOORS];
     out->status = st;
     out->kernel_ms = timing ? ms : 0.0;
     out->kernel_launches = 1;
@@ -1175,6 +1126,7 @@ extern "C" int dsp_advance(dsp_ctx *c, double t_end, int64_t max_sweeps, dsp_sta
     out->cell_updates = c1[CNT_CELL_UPDATES] - c0[CNT_CELL_UPDATES];
     out->sweeps = c1[CNT_SWEEPS] - c0[CNT_SWEEPS];
     out->fallbacks = c1[CNT_FALLBACKS] - c0[CNT_FALLBACKS];
+    out->floors = c1[CNT_FLOORS] - c0[CNT_FLOORS];
     out->status = st;
     out->kernel_ms = timing ? kms : 0.0;
     out->kernel_launches = kl;
@@ -1239,35 +1191,23 @@ extern "C" int dsp_diagnostics(dsp_ctx *c, dsp_diag *out) {
   if (!c || !out) return DSP_ERR_INVALID_ARG;
   const int np = c->d.np;
   double *dd = nullptr;
-  CK(cudaMalloc(&dd, sizeof(double) * 10 * np));
-  if (c->precision != 1) diag_kernel<double><<<np, 256, 0, c->stream>>>(c->d, dd);
-  else diag_kernel<float><<<np, 256, 0, c->stream>>>(c->d, dd);
+  CK(cudaMalloc(&dd, sizeof(double) * DIAG_PER * np));
+  if (c->precision != 1) diag_kernel<double><<<np, DIAG_NT, 0, c->stream>>>(c->d, dd);
+  else diag_kernel<float><<<np, DIAG_NT, 0, c->stream>>>(c->d, dd);
   cudaError_t e = cudaGetLastError();
-  std::vector<double> h((size_t)10 * np);
+  std::vector<double> h((size_t)DIAG_PER * np);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), dd, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   cudaFree(dd);
   if (e != cudaSuccess) return fail(c, DSP_ERR_CUDA, "diagnostics: %s", cudaGetErrorString(e));
-  double s[8], cc[8];
-  for (int q = 0; q < 8; q++) s[q] = cc[q] = 0.0;
-  double md = 0.0, mb = 0.0;
-  for (int P = 0; P < np; P++) {
-    for (int q = 0; q < 8; q++) {
-      const double x = h[(size_t)P * 10 + q];
-      const double t = s[q] + x;
-      if (std::fabs(s[q]) >= std::fabs(x)) cc[q] += (s[q] - t) + x;
-      else cc[q] += (x - t) + s[q];
-      s[q] = t;
-    }
-    md = std::max(md, h[(size_t)P * 10 + 8]);
-    mb = std::max(mb, h[(size_t)P * 10 + 9]);
-  }
-  out->mass = s[0] + cc[0];
-  for (int d = 0; d < 3; d++) out->mom[d] = s[1 + d] + cc[1 + d];
-  out->energy = s[4] + cc[4];
-  for (int d = 0; d < 3; d++) out->bmean[d] = s[5 + d] + cc[5 + d];
-  out->max_divb = md;
-  out->max_b = mb;
+  double r[DIAG_PER];
+  diag_combine(h.data(), np, r);
+  out->mass = r[0];
+  for (int d = 0; d < 3; d++) out->mom[d] = r[1 + d];
+  out->energy = r[4];
+  for (int d = 0; d < 3; d++) out->bmean[d] = r[5 + d];
+  out->max_divb = r[8];
+  out->max_b = r[9];
   return DSP_OK;
 }
 

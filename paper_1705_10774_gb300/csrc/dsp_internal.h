@@ -25,6 +25,7 @@ enum Cnt : int {
   CNT_SWEEPS = 2,
   CNT_FALLBACKS = 3,
   CNT_NSCHED = 4,
+  CNT_FLOORS = 5,  // cells of new slices whose pressure recovery took the floor
   CNT_COUNT = 8
 };
 

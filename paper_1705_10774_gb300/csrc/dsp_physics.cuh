@@ -73,9 +73,10 @@ __device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ float tsqrt(float a) { return sqrtf(a); }
 
 // Primitive state (rho, v, p, B) from conserved (rho, m, E) and the six faces.
+// With `floored`, *floored tells whether the pressure floor was taken.
 template <typename T>
 __device__ __forceinline__ void prim(T rho, T mx, T my, T mz, T E, T bxl, T bxr, T byl, T byr, T bzl, T bzr,
-                                     T gamma, T W[8]) {
+                                     T gamma, T W[8], int *floored = nullptr) {
   const T h = T(0.5);
   T irho = T(1) / rho;
   T Bx = h * (bxl + bxr);
@@ -87,7 +88,9 @@ __device__ __forceinline__ void prim(T rho, T mx, T my, T mz, T E, T bxl, T bxr,
   T ke = h * rho * (vx * vx + vy * vy + vz * vz);
   T me = h * (Bx * Bx + By * By + Bz * Bz);
   T p = (gamma - T(1)) * (E - ke - me);
-  p = tmax(p, T(PFLOOR) * rho);
+  const T pf = T(PFLOOR) * rho;
+  if (floored) *floored = p < pf;
+  p = tmax(p, pf);
   W[RHO] = rho; W[VX] = vx; W[VY] = vy; W[VZ] = vz; W[PR] = p;
   W[BX] = Bx; W[BY] = By; W[BZ] = Bz;
 }

@@ -131,6 +131,7 @@ struct TileShared {
   int n[3][TABMAX];
   double red[NT / 32];
   int fallback;
+  int floors;  // new cells whose pressure recovery took the floor
 };
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -261,7 +262,10 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
 #pragma unroll
     for (int q = 0; q < 3; q++) S.wgt[q][e] = q < pk.n ? (T)pk.w[q] : T(0);
   }
-  if (tid == 0) s_fallback = 0;
+  if (tid == 0) {
+    s_fallback = 0;
+    S.floors = 0;
+  }
   const int any_blend = __syncthreads_or(my_blend);
 
   // Where a gathered value lives: its address in the source slice (the
@@ -903,8 +907,10 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     if (upd && mine) {
       const int i = ui, j = uj, h = H1(i, j);
       T Wn[8];
+      int floored = 0;
       prim(unew[0], unew[1], unew[2], unew[3], unew[4], NBX[h], NBX[H1(i + 1, j)], NBY[h], NBY[H1(i, j + 1)],
-           NBZp[h], NBZc[h], gamma, Wn);
+           NBZp[h], NBZc[h], gamma, Wn, &floored);
+      if (floored) atomicAdd(&S.floors, 1);
       if (!(Wn[RHO] > T(0)) || !(Wn[PR] > T(0)))
         set_error(c, DSP_ERR_UNPHYSICAL, P, ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i));
       if constexpr (NI != 0)
@@ -1009,6 +1015,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
       if (tid == 0) {
         atomicMax(&c.smax_new[P], (unsigned long long)__double_as_longlong(u));
         if (s_fallback) atomicAdd((unsigned long long *)&c.cnt[CNT_FALLBACKS], (unsigned long long)s_fallback);
+        if (S.floors) atomicAdd((unsigned long long *)&c.cnt[CNT_FLOORS], (unsigned long long)S.floors);
       }
     }
     __syncthreads();

@@ -58,7 +58,7 @@ class dsp_stats(ctypes.Structure):
                 ("sweeps", ctypes.c_int64), ("fallbacks", ctypes.c_int64),
                 ("t_min", ctypes.c_double), ("t_max", ctypes.c_double), ("status", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
-                ("plan_launches", ctypes.c_int64)]
+                ("plan_launches", ctypes.c_int64), ("floors", ctypes.c_int64)]
 
 
 class dsp_sched_entry(ctypes.Structure):
@@ -276,9 +276,44 @@ class Dispatch:
         self._check(load().dsp_load(self._h, blob, len(blob)))
 
 
+def _check_noalloc_arrays(arrays, npatch, n):
+    """The checks dsp_diagnostics_noalloc cannot make on raw pointers: four
+    contiguous CUDA tensors on the current device, one dtype (float64 or
+    float32), each holding exactly npatch patches of n[0] x n[1] x n[2] cells
+    in the dsp_set_state layout.  Raises ValueError before anything reaches
+    the device."""
+    if len(arrays) != 4:
+        raise ValueError("expected U, bx, by, bz")
+    nx, ny, nz = (int(x) for x in n)
+    if npatch < 0 or min(nx, ny, nz) < 1:
+        raise ValueError("npatch must be >= 0 and every n >= 1")
+    want = [npatch * 5 * nx * ny * nz, npatch * (nx + 1) * ny * nz, npatch * nx * (ny + 1) * nz,
+            npatch * nx * ny * (nz + 1)]
+    dtypes = set()
+    for name, a, w in zip(("U", "bx", "by", "bz"), arrays, want):
+        if not (hasattr(a, "is_cuda") and hasattr(a, "data_ptr")):
+            raise ValueError("%s must be a torch CUDA tensor (got %s)" % (name, type(a).__name__))
+        if not a.is_cuda:
+            raise ValueError("%s must be on a CUDA device" % name)
+        import torch
+        if a.device.index != torch.cuda.current_device():
+            raise ValueError("%s is on cuda:%s, not the current device" % (name, a.device.index))
+        if not a.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if a.numel() != w:
+            raise ValueError("%s holds %d values, expected %d for %d patches of %s cells"
+                             % (name, a.numel(), w, npatch, (nx, ny, nz)))
+        dtypes.add(str(a.dtype))
+    if len(dtypes) != 1 or dtypes.pop() not in ("torch.float64", "torch.float32"):
+        raise ValueError("U, bx, by, bz must share one dtype, float64 or float32")
+
+
 def diagnostics_noalloc(U, bx, by, bz, npatch, n, dx, stream=None):
     """dsp_diagnostics_noalloc on caller-owned device arrays (torch CUDA
-    tensors in the dsp_set_state layout): the library allocates nothing."""
+    tensors in the dsp_set_state layout, all patches of n cells and cell
+    size dx): the library allocates nothing.  The arrays are checked first
+    (ValueError); the library checks npatch against its limit and dx."""
+    _check_noalloc_arrays((U, bx, by, bz), int(npatch), n)
     L = load()
     ptrs = [_addr(a) for a in (U, bx, by, bz)]
     dt = ptrs[0][2]

@@ -143,3 +143,21 @@ def test_parameters_are_checked_on_the_host():
     assert code(eta=0.1, c_ohm=-1.0) == INV
     assert code(riemann=1, variant=0) == INV        # an HLL variant
     assert code(eta=0.1, variant=2) == INV          # an ideal-MHD variant
+
+
+def test_noalloc_binding_refuses_arrays_it_cannot_vouch_for():
+    """diagnostics_noalloc hands raw pointers to the library, which cannot
+    tell a host array, a short array or a mixed dtype from a valid one: the
+    binding must refuse them before any call reaches the device."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    n, npatch = (2, 3, 4), 2
+    sizes = [npatch * 5 * 24, npatch * 3 * 3 * 4, npatch * 2 * 4 * 4, npatch * 2 * 3 * 5]
+    host = [np.zeros(s) for s in sizes]
+    with pytest.raises(ValueError, match="torch CUDA tensor"):
+        D.diagnostics_noalloc(*host, npatch=npatch, n=n, dx=0.1)
+    cpu = [torch.zeros(s, dtype=torch.float64) for s in sizes]
+    with pytest.raises(ValueError, match="CUDA device"):
+        D.diagnostics_noalloc(*cpu, npatch=npatch, n=n, dx=0.1)
+    with pytest.raises(ValueError, match="every n"):
+        D.diagnostics_noalloc(*cpu, npatch=npatch, n=(0, 3, 4), dx=0.1)

@@ -386,3 +386,23 @@ def test_mc_limiter_sign_test_does_not_underflow():
         assert O.mc(-1.0 * scale, -3.0 * scale) == -2.0 * scale
     assert O.mc(1e-200, -1e-200) == 0.0
     assert O.mc(-0.0, 1.0) == 0.0 and O.mc(1.0, -0.0) == 0.0
+
+
+def test_pressure_floor_count():
+    """The oracle counts the cells of new slices whose pressure recovery took
+    the floor p >= 1e-20 rho.  A cold uniform state with dyadic values (p = 0
+    exactly, E = rho v^2 / 2, B = 0) stays exactly uniform, so every new cell
+    recovers p = 0 and takes the floor; a warm wave input never does."""
+    lay = ics.cartesian(2, 8)
+    f = ics.config_uniform(lay, [1.0, 0.5, -0.25, 0.125, 0.0, 0.0, 0.0, 0.0], 5.0 / 3.0)
+    o = Oracle(lay.n, lay.lo, gamma=f.gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
+    o.set_state(*ics.to_patches(lay, f))
+    o.advance(max_sweeps=3)
+    st = o.stats()
+    assert st["cell_updates"] == 3 * 8 * 8 ** 3
+    assert st["floors"] == st["cell_updates"]
+    lay, f = ics.config_linear_waves(n=8)
+    o = Oracle(lay.n, lay.lo, gamma=f.gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
+    o.set_state(*ics.to_patches(lay, f))
+    o.advance(max_sweeps=3)
+    assert o.stats()["floors"] == 0
