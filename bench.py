@@ -1,20 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the per-patch update: MHD cell-updates/s on one GB300.
 
-Workload (one line per run): decaying MHD turbulence on a periodic 256^3 box
-cut into 8^3 = 512 patches of 32^3 cells, FP64, one global power-of-two
-Courant step per sweep (C = 0.4), seeded solenoidal Mach-2 velocity with
-E(k) ~ k^-2 on 1 <= |k|/2pi <= 4, uniform B along x at beta = 1.  A bench
-"step" is one sweep: every patch fills its guard zones, advances one step and
-publishes it.  The state (1.07 GB per slice in FP64) is larger than L2, so no
-flush is needed between steps.  The FP32-state form of the same run, both
-forms with HLLD face fluxes and both with the non-ideal Ohmic and ambipolar
-terms are measured too and reported under "forms".
+Workload of the benchmark line: the 3-D Orszag-Tang vortex on a periodic
+512^3 box cut into 16^3 = 4096 patches of 32^3 cells (rho = 25/(36 pi),
+p = 5/(12 pi), v = (-sin 2 pi y, sin 2 pi x, 0), b from A_z, a seeded 1e-3
+random v_z), one global power-of-two Courant step per sweep (C = 0.4).  A
+bench "step" is one sweep: every patch fills its guard zones, advances one
+step and publishes it.  `value` is the FP64 form (fused multiply-adds,
+checked against the FP64 oracle to 1e-11 per field); `value_f32` and
+`forms.f32` the FP32-state form of the same run.  A slice (8.7 GB in FP64)
+is far larger than L2, so no flush is needed between steps.  Side forms on
+the 256^3 decaying-turbulence input (512 patches of 32^3): the FMA-free FP64
+build, HLLD faces and the non-ideal terms, in both precisions.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload (32 patch updates per step).
+sample of the same workload (32 patch updates of the 512^3 input per step).
 """
 from __future__ import annotations
 
@@ -35,9 +37,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MHD cell-updates/s (FP64 vs FP32 form) and % of GB300 HBM roofline"
 UNIT = "cell-updates/s"
-PATCHES, NCELL = 8, 32
-WORKLOAD = "decaying MHD turbulence, 256^3 periodic, 512 patches of 32^3, global dt, CFL 0.4"
+# the benchmark line: 16^3 patches of 32^3 (512^3); the side forms: 8^3 (256^3)
+PATCHES, NCELL = 16, 32
+SIDE_PATCHES = 8
 HBM_FALLBACK_GBS = 6800.0
+
+
+def workload(patches=PATCHES):
+    L = patches * NCELL
+    return ("Orszag-Tang vortex, %d^3 periodic, %d patches of 32^3, global dt, CFL 0.4" % (L, patches ** 3))
+
+
+SIDE_WORKLOAD = "decaying MHD turbulence, 256^3 periodic, 512 patches of 32^3, global dt, CFL 0.4"
 # the timed FP64 form: FP64 state and arithmetic with fused multiply-adds
 # (checked against the FP64 oracle to 1e-11); the FMA-free build that matches
 # the oracle bit for bit is timed too and reported as forms.f64_exact
@@ -46,28 +57,30 @@ F64_PRECISION = 2
 # experiment's ambipolar drift coefficient and ion density (Sec. 5.4)
 NONIDEAL = dict(eta=1e-4, gamma_ad=75.0, rho_i=1.0)
 
-# DRAM bytes (read + write) per update-kernel launch of the full workload,
-# by compiled variant, from ncu's dram__bytes_read.sum + dram__bytes_write.sum
-# (FP64: a 216-patch capture of the same kernel, scaled by cells; FP32: the
-# full workload); a variant without an entry reports null.
-TRAFFIC_F64 = {2: (550.772736e6 + 421.459712e6) * 512 / 216, 3: (551.252736e6 + 421.417472e6) * 512 / 216,
-               4: (552.264960e6 + 424.443648e6) * 512 / 216}
-TRAFFIC_F32 = {5: 626.309120e6 + 509.839360e6}
-# the same for the HLLD variants (FP64 FMA: the 216-patch capture, scaled)
-TRAFFIC_F64_HLLD = {10: (538.658560e6 + 421.405696e6) * 512 / 216}
-TRAFFIC_F32_HLLD = {11: 622.772736e6 + 510.983424e6}
+# DRAM bytes (read + write) per cell-update of the update kernel, by
+# compiled variant, from ncu's dram__bytes_read.sum + dram__bytes_write.sum
+# of one launch divided by the cells it updated (captures of smaller cases
+# of the same kernel: traffic grows in proportion to the cells); a variant
+# without an entry reports null.
+TRAFFIC_PER_CELL = {}
 
 
-def radius2_guard_fraction(n):
-    return ((n + 4) ** 3 - n ** 3) / n ** 3
+def guard_fraction(n, g):
+    """Guard cells per interior cell of an n^3 patch with g guard layers."""
+    return ((n + 2 * g) ** 3 - n ** 3) / n ** 3
 
 
-def alg_bytes_per_cell(n, esize, sbar=1.0):
+def alg_bytes_per_cell(n, esize, sbar=1.0, g=3):
     """Algorithmic HBM bytes per cell-update: read and write the 8 stored
-    fields once, plus the guard shell the stencil reads (radius 2), taken
-    from sbar neighbour slices."""
+    fields once, plus the guard shell of g layers taken from sbar neighbour
+    slices (g = 3 as the guard zones are specified; the stencil itself reads
+    g = 2, which alg_bytes_radius2 gives)."""
     V = 8
-    return esize * (2 * V + sbar * radius2_guard_fraction(n) * V)
+    return esize * (2 * V + sbar * guard_fraction(n, g) * V)
+
+
+def alg_bytes_radius2(n, esize, sbar=1.0):
+    return alg_bytes_per_cell(n, esize, sbar, g=2)
 
 
 # Algorithmic floating-point operations per cell-update (add, subtract,
@@ -199,9 +212,15 @@ def sum_over_ranks(td, x):
 
 
 def make_input(patches=PATCHES):
+    """The benchmark line's input: Orszag-Tang patch arrays (FP64, host)."""
+    from paper_1705_10774_gb300 import ics
+    return ics.orszag_tang_patches(seed=10775, patches=patches, n=NCELL)
+
+
+def make_side_input(patches=SIDE_PATCHES):
     from paper_1705_10774_gb300 import ics
     lay, f = ics.config_turbulence(seed=10774, patches=patches, n=NCELL, mach=2.0)
-    return lay, f, ics.to_patches(lay, f)
+    return lay, ics.to_patches(lay, f)
 
 
 def rooflines(ncells, esize, kernel_ms, hbm_peak, peak_kind, flops_per_cell=ALG_FLOPS_PER_CELL):
@@ -216,7 +235,9 @@ def rooflines(ncells, esize, kernel_ms, hbm_peak, peak_kind, flops_per_cell=ALG_
     tfs = fpl / (kernel_ms * 1e-3) / 1e12
     fpeak = FP64_PEAK_TFLOPS if esize == 8 else FP32_PEAK_TFLOPS
     hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-           "alg_bytes_per_launch": bpl, "peak_kind": peak_kind}
+           "alg_bytes_per_launch": bpl, "alg_bytes_per_cell": alg_bytes_per_cell(NCELL, esize),
+           "alg_bytes_per_cell_reading": "g = 3 guard layers from one neighbour slice (s = 1)",
+           "alg_bytes_per_cell_radius2": alg_bytes_radius2(NCELL, esize), "peak_kind": peak_kind}
     alu = {"bound": "alu", "achieved": tfs, "peak": fpeak, "unit": "TFLOP/s", "frac": tfs / fpeak,
            "alg_flops_per_launch": fpl, "alg_flops_per_cell": flops_per_cell,
            "peak_kind": "derived: 152 SMs x %s x 2.07 GHz" % ("2 FP64 FMA/cycle" if esize == 8 else "128 FP32 lanes")}
@@ -257,6 +278,51 @@ def run_form(lay, state_dev, precision, steps, warmup, td, variant=-1, riemann=0
     return g, st, ms
 
 
+def traffic_of(variant, ncells):
+    per = TRAFFIC_PER_CELL.get(variant)
+    return None if per is None else per * ncells
+
+
+def side_forms(args, td, peak, peak_kind):
+    """The side forms on the 256^3 turbulence input: FP64 with FMA and
+    without (bit-identical to the oracle), FP32, HLLD faces and the non-ideal
+    terms in both precisions."""
+    import torch
+    lay, state = make_side_input()
+    state_dev = [torch.from_numpy(a).cuda() for a in state]
+    ncells = int(np.prod(lay.base_cells))
+    forms = {}
+    runs = [("f64", F64_PRECISION, 0, None), ("f64_exact", 0, 0, None), ("f32", 1, 0, None)]
+    if not args.no_hlld:
+        runs += [("f64_hlld", F64_PRECISION, 1, None), ("f32_hlld", 1, 1, None)]
+    if not args.no_nonideal:
+        runs += [("f64_nonideal", F64_PRECISION, 0, NONIDEAL), ("f32_nonideal", 1, 0, NONIDEAL)]
+    for name, prec, rs, ni in runs:
+        if prec == 1 and args.no_f32:
+            continue
+        sd = [a.float() for a in state_dev] if prec == 1 else state_dev
+        g, st, ms = run_form(lay, sd, prec, args.steps, args.warmup, td, riemann=rs, nonideal=ni)
+        ms = max_over_ranks(td, ms)
+        k = st["kernel_ms"] / max(st["kernel_launches"], 1)
+        r = {"value": sum_over_ranks(td, float(st["cell_updates"])) / (ms * 1e-3), "ms_per_step": ms / args.steps,
+             "dtype": "f32" if prec == 1 else "f64", "kernel": "update_kernel variant %d" % g.tuned[0],
+             "kernel_ms_avg": k}
+        if ni is None:
+            r["roofline"] = rooflines(ncells, 4 if prec == 1 else 8, k, peak, peak_kind,
+                                      ALG_FLOPS_PER_CELL_HLLD if rs else ALG_FLOPS_PER_CELL)
+            r["roofline"]["traffic"] = traffic_of(g.tuned[0], ncells)
+        if name == "f64_exact":
+            r["note"] = "no FMA contraction; bit-identical to the FP64 oracle"
+        elif rs:
+            r["note"] = "HLLD face fluxes (Miyoshi & Kusano 2005)"
+        elif ni:
+            r["note"] = "Ohmic and ambipolar EMFs and their Poynting flux, %s" % NONIDEAL
+        forms[name] = r
+        g.close()
+        del sd
+    return {"workload": SIDE_WORKLOAD, "forms": forms}
+
+
 def gpu_arm(args):
     import torch
     td, rank, ws = dist()
@@ -264,12 +330,12 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     from paper_1705_10774_gb300 import dispatch as D
     D.load()
-    lay, f, state = make_input(args.patches if args.form != "both" else PATCHES)
-    state_dev = [torch.from_numpy(a).cuda() for a in state]
-    ncells = int(np.prod(lay.base_cells))
     peak, peak_kind = measured_peaks()
 
     if args.form != "both":
+        # profiling runs: one form on the 256^3 turbulence input (or --patches)
+        lay, state = make_side_input(args.patches or SIDE_PATCHES)
+        state_dev = [torch.from_numpy(a).cuda() for a in state]
         prec = {"f32": 1, "f64": F64_PRECISION, "f64_exact": 0}[args.form]
         sd = [a.float() for a in state_dev] if prec else state_dev
         g, st, ms = run_form(lay, sd, prec, args.steps, args.warmup, td, args.variant, args.riemann,
@@ -280,6 +346,11 @@ def gpu_arm(args):
                               "kernel_ms_avg": st["kernel_ms"] / max(st["kernel_launches"], 1),
                               "cell_updates_per_s": st["cell_updates"] / (ms * 1e-3)}))
         return
+
+    P = args.patches or PATCHES
+    lay, state = make_input(P)
+    ncells = int(np.prod(lay.base_cells))
+    state_dev = [torch.from_numpy(a).cuda() for a in state]
     with Clocks(local) as clk:
         g, st, ms = run_form(lay, state_dev, F64_PRECISION, args.steps, args.warmup, td)
     ms_max = max_over_ranks(td, ms)
@@ -287,67 +358,33 @@ def gpu_arm(args):
     value = cells_all / (ms_max * 1e-3)
     kavg = st["kernel_ms"] / max(st["kernel_launches"], 1)
     roof = rooflines(ncells, 8, kavg, peak, peak_kind)
-    roof.update({"traffic": TRAFFIC_F64.get(g.tuned[0]), "kernel": "update_kernel variant %d" % g.tuned[0],
-                 "kernel_ms_avg": kavg,
-                 "autotune_ms_per_variant": g.tuned[1]})
+    roof.update({"traffic": traffic_of(g.tuned[0], ncells), "kernel": "update_kernel variant %d" % g.tuned[0],
+                 "kernel_ms_avg": kavg, "autotune_ms_per_variant": g.tuned[1]})
+    launches = int(st["kernel_launches"] + st["plan_launches"])
     g.close()
 
-    forms = {}
-    if args.form == "both":
-        ge, ste, mse = run_form(lay, state_dev, 0, args.steps, args.warmup, td)
-        mse = max_over_ranks(td, mse)
-        forms["f64_exact"] = {"value": sum_over_ranks(td, float(ste["cell_updates"])) / (mse * 1e-3),
-                              "ms_per_step": mse / args.steps, "dtype": "f64",
-                              "kernel_ms_avg": ste["kernel_ms"] / max(ste["kernel_launches"], 1),
-                              "note": "no FMA contraction; bit-identical to the FP64 oracle"}
-        ge.close()
-
-    if not args.no_f32 and args.form == "both":
+    forms = {"f64": {"value": value, "ms_per_step": ms_max / args.steps, "dtype": "f64"}}
+    v32 = None
+    if not args.no_f32:
         state32 = [a.float() for a in state_dev]
+        del state_dev
+        torch.cuda.empty_cache()
         g32, st32, ms32 = run_form(lay, state32, 1, args.steps, args.warmup, td)
         ms32_max = max_over_ranks(td, ms32)
         v32 = sum_over_ranks(td, float(st32["cell_updates"])) / (ms32_max * 1e-3)
         k32 = st32["kernel_ms"] / max(st32["kernel_launches"], 1)
         r32 = rooflines(ncells, 4, k32, peak, peak_kind)
-        r32.update({"traffic": TRAFFIC_F32.get(g32.tuned[0]), "kernel": "update_kernel variant %d" % g32.tuned[0],
+        r32.update({"traffic": traffic_of(g32.tuned[0], ncells), "kernel": "update_kernel variant %d" % g32.tuned[0],
                     "kernel_ms_avg": k32, "autotune_ms_per_variant": g32.tuned[1]})
         forms["f32"] = {"value": v32, "ms_per_step": ms32_max / args.steps, "dtype": "f32", "roofline": r32}
         g32.close()
         del state32
+    else:
+        del state_dev
+    torch.cuda.empty_cache()
 
-    if not args.no_hlld and args.form == "both":
-        # the same run with HLLD face fluxes (edge EMFs stay upwind HLL)
-        for name, prec in (("f64_hlld", F64_PRECISION), ("f32_hlld", 1)):
-            if prec == 1 and args.no_f32:
-                continue
-            sd = [a.float() for a in state_dev] if prec == 1 else state_dev
-            gh, sth, msh = run_form(lay, sd, prec, args.steps, args.warmup, td, riemann=1)
-            msh = max_over_ranks(td, msh)
-            kh = sth["kernel_ms"] / max(sth["kernel_launches"], 1)
-            rh = rooflines(ncells, 4 if prec == 1 else 8, kh, peak, peak_kind, ALG_FLOPS_PER_CELL_HLLD)
-            rh.update({"traffic": (TRAFFIC_F32_HLLD if prec == 1 else TRAFFIC_F64_HLLD).get(gh.tuned[0]),
-                       "kernel": "update_kernel variant %d" % gh.tuned[0], "kernel_ms_avg": kh})
-            forms[name] = {"value": sum_over_ranks(td, float(sth["cell_updates"])) / (msh * 1e-3),
-                           "ms_per_step": msh / args.steps, "dtype": "f32" if prec == 1 else "f64",
-                           "roofline": rh, "note": "HLLD face fluxes (Miyoshi & Kusano 2005)"}
-            gh.close()
-            del sd
-
-    if not args.no_nonideal and args.form == "both":
-        # the same run with the non-ideal Ohmic and ambipolar terms (Sec. 4.3)
-        for name, prec in (("f64_nonideal", F64_PRECISION), ("f32_nonideal", 1)):
-            if prec == 1 and args.no_f32:
-                continue
-            sd = [a.float() for a in state_dev] if prec == 1 else state_dev
-            gn, stn, msn = run_form(lay, sd, prec, args.steps, args.warmup, td, nonideal=NONIDEAL)
-            msn = max_over_ranks(td, msn)
-            forms[name] = {"value": sum_over_ranks(td, float(stn["cell_updates"])) / (msn * 1e-3),
-                           "ms_per_step": msn / args.steps, "dtype": "f32" if prec == 1 else "f64",
-                           "kernel": "update_kernel variant %d" % gn.tuned[0],
-                           "kernel_ms_avg": stn["kernel_ms"] / max(stn["kernel_launches"], 1),
-                           "note": "Ohmic and ambipolar EMFs and their Poynting flux, %s" % NONIDEAL}
-            gn.close()
-            del sd
+    side = None if args.no_side else side_forms(args, td, peak, peak_kind)
+    torch.cuda.empty_cache()
 
     e2e = None
     if not args.no_e2e:
@@ -359,18 +396,20 @@ def gpu_arm(args):
 
     if rank == 0:
         out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": METRIC, "value": value, "value_f32": v32, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "patches": lay.npatch, "cells_per_patch": [NCELL] * 3,
-                       "cells": ncells, "time_mode": "global", "precision": "f64",
-                       "l2": "inputs larger than L2 (1.07 GB per slice)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+            "config": {"workload": workload(P), "patches": lay.npatch, "cells_per_patch": [NCELL] * 3,
+                       "cells": ncells, "time_mode": "global", "precision": "f64 (fused multiply-adds)",
+                       "l2": "inputs larger than L2 (%.1f GB per FP64 slice)" % (sum(a.nbytes for a in state) / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "roofline": roof,
-            "forms": {"f64": {"value": value, "ms_per_step": ms_max / args.steps}, **forms},
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": int(st["kernel_launches"] + st["plan_launches"]),
+            "gpu_launches": launches,
             "clocks": clk.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "forms": forms,
+            "side": side,
         }
         print(json.dumps(out))
     if td is not None:
@@ -379,120 +418,60 @@ def gpu_arm(args):
 
 
 def e2e_measure(lay, state, steps, td):
-    """Through the public API with host buffers: every step copies the input
-    state from pinned host memory to the device, loads it (dsp_set_state),
-    advances one global step and reads the new state back into pinned host
-    memory.  The copies run on a second CUDA stream into double-buffered
-    device staging arrays, so that step k+1's input and step k-1's result
-    cross the host link while step k's sweep runs; the loads, sweeps and
-    reads stay on the context's stream in order."""
+    """Through the library's own host-buffer path: every step loads the input
+    from pinned host memory with dsp_set_state(on_device = 0) -- the library
+    copies it into its device staging buffer and scatters it into the
+    slices --, advances one global step, and reads the new state back into
+    pinned host memory with dsp_get_state(on_device = 0) (gather kernel,
+    then the library's copy to the host).  Each call synchronises, so the
+    copies are in line with the sweeps."""
     import torch
     from paper_1705_10774_gb300.dispatch import Dispatch
     pinned = [torch.from_numpy(a).pin_memory() for a in state]
-    outs = [[torch.empty_like(a).pin_memory() for a in pinned] for _ in range(2)]
-    dev_in = [[torch.empty(a.shape, dtype=a.dtype, device="cuda") for a in pinned] for _ in range(2)]
-    dev_out = [[torch.empty(a.shape, dtype=a.dtype, device="cuda") for a in pinned] for _ in range(2)]
+    outs = [torch.empty_like(a).pin_memory() for a in pinned]
     stream = torch.cuda.current_stream()
-    copy = torch.cuda.Stream()
     g = Dispatch(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
                  precision=F64_PRECISION, time_mode=0, stream=stream.cuda_stream)
     h_in = sum(a.numel() * a.element_size() for a in pinned)
-    h_out = sum(a.numel() * a.element_size() for a in outs[0])
-    for buf in dev_in:
-        for d, h in zip(buf, pinned):
-            d.copy_(h)
-    g.set_state(*dev_in[0])                         # allocate the library's buffers before timing
+    h_out = sum(a.numel() * a.element_size() for a in outs)
+    g.set_state(*pinned)                    # allocates the library's staging buffer before timing
     g.autotune(reps=2)
-    g.set_state(*[a.numpy() for a in pinned])
+    g.set_state(*pinned)
     g.advance(max_sweeps=1)
-    g.get_state(out=dev_out[0])
+    g.get_state(out=outs)
     torch.cuda.synchronize()
     if td is not None:
         td.barrier()
-
-    def h2d(k):
-        with torch.cuda.stream(copy):
-            for d, h in zip(dev_in[k % 2], pinned):
-                d.copy_(h, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(copy)
-        return ev
-
     cells = 0
     t0 = time.perf_counter()
-    ev_in = {0: h2d(0)}
-    ev_out = {}
-    for k in range(steps):
-        if k + 1 < steps:
-            ev_in[k + 1] = h2d(k + 1)              # next input, while this step runs
-        stream.wait_event(ev_in.pop(k))
-        g.set_state(*dev_in[k % 2])
+    for _ in range(steps):
+        g.set_state(*pinned)
         st = g.advance(max_sweeps=1)
-        if k - 2 in ev_out:                         # the staging array's previous read is done
-            stream.wait_event(ev_out.pop(k - 2))
-        g.get_state(out=dev_out[k % 2])
-        done = torch.cuda.Event()
-        done.record(stream)
-        with torch.cuda.stream(copy):
-            copy.wait_event(done)
-            for h, d in zip(outs[k % 2], dev_out[k % 2]):
-                h.copy_(d, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(copy)
-            ev_out[k] = ev
+        g.get_state(out=outs)
         cells += st["cell_updates"]
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     dt = max_over_ranks(td, dt)
     cells = sum_over_ranks(td, cells)
     g.close()
+    del pinned, outs
     return {"value": cells / dt, "unit": UNIT, "h2d_bytes_per_step": h_in, "d2h_bytes_per_step": h_out,
-            "steps": steps, "copies": "pinned host <-> device on a second stream, overlapping the sweeps"}
+            "steps": steps,
+            "path": "dsp_set_state / dsp_advance(1 sweep) / dsp_get_state with pinned host pointers "
+                    "(on_device = 0): the library's own copies through its device staging buffer"}
 
 
-def cpu_baseline(lay, state, target_s=12.0):
-    """The FP64 oracle as it stands (OpenMP over the ready patches of a
-    sweep), on the host cores: whole global steps of the same workload."""
+def oracle_sample(lay, state, steps, warmup, per_step=32):
+    """The FP64 oracle as it stands on a bounded sample of the workload: each
+    step updates `per_step` patches (a fixed seeded permutation) from the
+    initial state with the global step, spread over the host cores (the
+    oracle's update releases the interpreter lock).  Returns (cell-updates/s,
+    seconds, cores, patch updates)."""
     from oracle import Oracle
-    o = Oracle(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
-    o.set_state(*state)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    t0 = time.perf_counter()
-    n = 0
-    while True:
-        o.advance(max_sweeps=1)
-        n += 1
-        if time.perf_counter() - t0 > target_s or n >= 8:
-            break
-    dt = time.perf_counter() - t0
-    cells = o.stats()["cell_updates"]
-    # one core: single patch updates (the oracle parallelises over patches only)
-    step = min(o.patch_dt(i) for i in range(lay.npatch))
-    t1 = time.perf_counter()
-    for P in range(8):
-        o.update_patch(P, step)
-    d1 = time.perf_counter() - t1
-    c1 = 8 * int(np.prod(lay.n[0]))
-    return {"value": cells / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d global step(s) of the 256^3 / 512-patch workload (%d cell-updates, %.1f s)" % (n, cells, dt),
-            "single_core": {"value": c1 / d1, "unit": UNIT, "cores": 1,
-                            "sample": "8 patch updates of 32^3 (%d cell-updates, %.2f s)" % (c1, d1)}}
-
-
-def reference_arm(args):
-    """The FP64 CPU oracle, timed on the host cores; each step is a bounded
-    sample of the workload: 32 patch updates (1.05M cell-updates) from the
-    initial state, spread over the cores."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    from oracle import Oracle
-    lay, f, state = make_input()
     o = Oracle(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len)
     o.set_state(*state)
     dt = min(o.patch_dt(i) for i in range(lay.npatch))
     cores = os.cpu_count() or 1
-    per_step = 32
     order = np.random.default_rng(1).permutation(lay.npatch)
     pool = ThreadPoolExecutor(max_workers=cores)
 
@@ -500,22 +479,49 @@ def reference_arm(args):
         ids = [int(order[(k * per_step + j) % lay.npatch]) for j in range(per_step)]
         list(pool.map(lambda i: o.update_patch(i, dt), ids))
 
-    for k in range(args.warmup):
+    for k in range(warmup):
         step(k)
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        step(args.warmup + k)
+    for k in range(steps):
+        step(warmup + k)
     el = time.perf_counter() - t0
-    cells = args.steps * per_step * NCELL ** 3
-    value = cells / el
+    pool.shutdown()
+    cells = steps * per_step * NCELL ** 3
+    # one core: the same updates one after another
+    t1 = time.perf_counter()
+    for j in range(4):
+        o.update_patch(int(order[j]), dt)
+    d1 = time.perf_counter() - t1
+    return cells / el, el, cores, steps * per_step, 4 * NCELL ** 3 / d1
+
+
+def cpu_baseline(lay, state, steps=16):
+    v, el, cores, nup, v1 = oracle_sample(lay, state, steps, 1)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d patch updates of 32^3 from the %d^3 input with its global step, over %d threads "
+                      "(%.1f s)" % (nup, lay.base_cells[0], cores, el),
+            "single_core": {"value": v1, "unit": UNIT, "cores": 1, "sample": "4 patch updates of 32^3 in sequence"}}
+
+
+def reference_arm(args):
+    """The FP64 CPU oracle, timed on the host cores; each step is a bounded
+    sample of the workload: 32 patch updates (1.05M cell-updates) of the
+    benchmark's input with its global step, spread over the cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    P = args.patches or PATCHES
+    lay, state = make_input(P)
+    value, el, cores, nup, _ = oracle_sample(lay, state, args.steps, args.warmup)
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "patches": lay.npatch, "cells_per_patch": [NCELL] * 3,
-                   "sample_per_step": "%d patch updates" % per_step},
+        "config": {"workload": workload(P), "patches": lay.npatch, "cells_per_patch": [NCELL] * 3,
+                   "sample_per_step": "32 patch updates"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "%d patch updates of 32^3 per step, %d steps" % (per_step, args.steps)},
+                         "sample": "32 patch updates of 32^3 per step, %d steps" % args.steps},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -548,7 +554,8 @@ def lts_arm(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         r = {"ms": ms, "cell_updates": st["cell_updates"], "patch_updates": st["patch_updates"],
-             "sweeps": st["sweeps"], "cell_updates_per_s": st["cell_updates"] / (ms * 1e-3)}
+             "sweeps": st["sweeps"], "cell_updates_per_s": st["cell_updates"] / (ms * 1e-3),
+             "pressure_floor_cells": st["floors"], "first_order_fallback_cells": st["fallbacks"]}
         if name == "f64_sweep_graph" or name == "f32_sweep_graph":
             _, _, dts = g.schedule()
             lv, cnt = np.unique(dts, return_counts=True)
@@ -572,8 +579,8 @@ def kitp_arm(args):
     import torch
     from paper_1705_10774_gb300 import ics
     from paper_1705_10774_gb300.dispatch import Dispatch
-    lay512, f = ics.config_turbulence(seed=10774, patches=PATCHES, n=NCELL, mach=2.0)
-    lay1 = ics.cartesian(1, PATCHES * NCELL)
+    lay512, f = ics.config_turbulence(seed=10774, patches=SIDE_PATCHES, n=NCELL, mach=2.0)
+    lay1 = ics.cartesian(1, SIDE_PATCHES * NCELL)
     t_end = args.t_end if args.t_end != 0.01 else 0.2
     runs = {}
     for name, lay, cfl in (("1_patch", lay1, 0.4), ("512_patches", lay512, 0.4), ("512_patches_cfl0.3", lay512, 0.3)):
@@ -655,9 +662,7 @@ def orszag_tang_arm(args):
     import torch
     from paper_1705_10774_gb300 import ics
     from paper_1705_10774_gb300.dispatch import Dispatch
-    lay, f = ics.config_orszag_tang(patches=args.patches, n=NCELL)
-    state = ics.to_patches(lay, f)
-    del f
+    lay, state = ics.orszag_tang_patches(patches=args.patches or PATCHES, n=NCELL)
     stream = torch.cuda.current_stream()
     kw = dict(gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len, time_mode=0,
               graph=1, stream=stream.cuda_stream)
@@ -678,8 +683,9 @@ def orszag_tang_arm(args):
     npch = lay.npatch
     A, B = a[0].reshape(npch, 5, -1), b[0].reshape(npch, 5, -1)
     l1 = lambda x, y: float(np.sum(np.abs(x - y)) / np.sum(np.abs(x)))
-    errs = {"rho": l1(A[:, 0], B[:, 0]), "mom": l1(A[:, 1:4], B[:, 1:4]), "E": l1(A[:, 4], B[:, 4]),
-            "b": l1(np.concatenate(a[1:]), np.concatenate(b[1:]))}
+    errs = {"rho": l1(A[:, 0], B[:, 0]), "m_x": l1(A[:, 1], B[:, 1]), "m_y": l1(A[:, 2], B[:, 2]),
+            "m_z": l1(A[:, 3], B[:, 3]), "E": l1(A[:, 4], B[:, 4]), "b_x": l1(a[1], b[1]), "b_y": l1(a[2], b[2]),
+            "b_z": l1(a[3], b[3]), "mom": l1(A[:, 1:4], B[:, 1:4]), "b": l1(np.concatenate(a[1:]), np.concatenate(b[1:]))}
     drift = {}
     for name in ("f64", "f32"):
         d0, d1 = res[name]["d0"], res[name]["d1"]
@@ -690,42 +696,6 @@ def orszag_tang_arm(args):
                        "cell_updates_per_s": res[name]["st"]["cell_updates"] / res[name]["s"]}
     print(json.dumps({"workload": "Orszag-Tang %d^3 (%d patches of %d^3)" % (lay.base_cells[0], npch, NCELL),
                       "t_end": args.t_end, "f32_vs_f64_relative_L1": errs, "per_form": drift}))
-
-
-def cshock_arm(args):
-    """Sec. 5.4's non-ideal C-shock experiments on the GPU (FP64 without
-    FMA, bit-identical to the oracle): from the Table 1 discontinuity on a
-    periodic box of 4 (300 cells, patches of 30 x 4 x 4; the shock at 3,
-    far enough from the wrap), local steps and CUDA graphs, to t = 0.2
-    (ambipolar) and 0.3 (Ohmic).  Reports the mean distance of B_y from the
-    steady C-shock profile (the ODE of the conservation laws, aligned at the
-    mid-value) over the jump, and the ratio of the largest to the smallest
-    per-patch step."""
-    import torch
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from cshock_ode import jump_input, most_common_steps, profile_error
-    from paper_1705_10774_gb300 import ics
-    from paper_1705_10774_gb300.dispatch import Dispatch
-    out = {}
-    for name, t_end in (("ad_iso", 0.2), ("ad_noniso", 0.2), ("ohm", 0.3)):
-        lay, f, gamma, kw, xc = jump_input(name)
-        g = Dispatch(lay.n, lay.lo, gamma=gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
-                     time_mode=1, graph=1, precision=0, sched_capacity=1 << 22, **kw)
-        g.set_state(*ics.to_patches(lay, f))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st = g.advance(t_end=t_end)
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        By = ics.from_patches(lay, *g.get_state())[2][0, 0]
-        steps = most_common_steps(g.schedule(), lay.npatch)
-        out[name] = {"t_end": t_end, "profile_error": profile_error(name, xc, By, 3.0),
-                     "step_ratio_between_patches": float(steps.max() / steps.min()),
-                     "patch_updates": st["patch_updates"], "sweeps": st["sweeps"], "seconds": el,
-                     "cell_updates_per_s": st["cell_updates"] / el, "coefficients": kw}
-        g.close()
-    print(json.dumps({"workload": "non-ideal C-shocks of Table 1, 300 cells over 4, 10 patches of 30x4x4",
-                      "cases": out}))
 
 
 def mixed_arm(args):
@@ -817,14 +787,15 @@ def amr_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-f32", action="store_true")
     ap.add_argument("--form", default="both", choices=["both", "f64", "f64_exact", "f32"],
                     help="f64 / f32: time only that form and print a short line (profiling runs)")
-    ap.add_argument("--patches", type=int, default=PATCHES,
-                    help="patches per axis for --form runs (profiling on a smaller box)")
+    ap.add_argument("--patches", type=int, default=0,
+                    help="patches per axis of 32^3 (default: 16 for the benchmark line, 8 for --form runs)")
+    ap.add_argument("--no-side", action="store_true", help="skip the 256^3 side forms")
     ap.add_argument("--variant", type=int, default=-1,
                     help="--form runs: use this compiled kernel variant instead of autotuning")
     ap.add_argument("--riemann", type=int, default=0, choices=[0, 1],
@@ -834,10 +805,10 @@ def main():
     ap.add_argument("--nonideal", action="store_true",
                     help="--form runs: with the non-ideal terms of the benchmark's non-ideal forms")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="turbulence",
-                    choices=["turbulence", "lts", "orszag-tang", "mixed", "amr", "cshock", "grace", "kitp"],
+                    choices=["turbulence", "lts", "orszag-tang", "mixed", "amr", "grace", "kitp"],
                     help="lts / orszag-tang: side measurements (one JSON line each), not the benchmark line")
     ap.add_argument("--t-end", type=float, default=0.01, help="end time of the lts / orszag-tang / mixed runs")
     ap.add_argument("--blocks", type=int, default=5, help="96^3 super-blocks per axis of the mixed run")
@@ -852,8 +823,6 @@ def main():
         return mixed_arm(args)
     if args.workload == "amr":
         return amr_arm(args)
-    if args.workload == "cshock":
-        return cshock_arm(args)
     if args.workload == "grace":
         return grace_arm(args)
     if args.workload == "kitp":

@@ -519,6 +519,72 @@ def config_orszag_tang(seed=10775, patches=16, n=32, pert=1e-3):
     return lay, Fields(rho=rho, v=v, p=p, bx=bx, by=by, bz=bz, gamma=5.0 / 3.0)
 
 
+def orszag_tang_patches(seed=10775, patches=16, n=32, pert=1e-3):
+    """The patch arrays of config_orszag_tang, cut directly into patches
+    without the global 3-D fields (which at 512^3 take tens of GB): every
+    field but the random v_z is independent of z, so faces, velocities and
+    the magnetic energy are built on the (y, x) plane and broadcast, and the
+    random v_z is drawn exactly as config_orszag_tang draws it.  The values
+    equal to_patches(*config_orszag_tang(...)) bit for bit (same elementwise
+    operations).  Returns (layout, (U, bx, by, bz))."""
+    rng = np.random.default_rng(seed)
+    lay = cartesian(patches, n)
+    X, Y, Z = lay.base_cells
+    x, y, z, dx = _grid(lay)
+    rho = 25.0 / (36.0 * np.pi)
+    p = 5.0 / (12.0 * np.pi)
+    gamma = 5.0 / 3.0
+    vz = pert * rng.standard_normal((Z, Y, X))
+    B0 = 1.0 / np.sqrt(4 * np.pi)
+    xe = np.arange(X) * dx
+    ye = np.arange(Y) * dx
+    YE, XE = np.meshgrid(ye, xe, indexing="ij")
+    Az = B0 * (np.cos(4 * np.pi * XE) / (4 * np.pi) + np.cos(2 * np.pi * YE) / (2 * np.pi))
+    bx2 = (np.roll(Az, -1, axis=0) - Az) / dx - 0.0
+    by2 = 0.0 - (np.roll(Az, -1, axis=1) - Az) / dx
+    yy, xx = np.meshgrid(y, x, indexing="ij")
+    vx2 = -np.sin(2 * np.pi * yy)
+    vy2 = np.sin(2 * np.pi * xx)
+    Bxc = 0.5 * (bx2 + np.roll(bx2, -1, axis=1))
+    Byc = 0.5 * (by2 + np.roll(by2, -1, axis=0))
+    Bzc = 0.5 * (np.zeros_like(bx2) + np.zeros_like(bx2))
+    me2 = Bxc ** 2 + Byc ** 2 + Bzc ** 2
+    P = patches
+    npch = P ** 3
+
+    def blocks(a):
+        """(Z, Y, X) -> (npatch, n, n, n), patches x fastest."""
+        return a.reshape(P, n, P, n, P, n).transpose(0, 2, 4, 1, 3, 5).reshape(npch, n, n, n)
+
+    def blocks2(a):
+        """(Y, X) plane -> (npatch, n, n, n) broadcast over z."""
+        b = a.reshape(P, n, P, n).transpose(0, 2, 1, 3)            # (py, px, ny, nx)
+        return np.broadcast_to(b[None, :, :, None], (P, P, P, n, n, n)).reshape(npch, n, n, n)
+
+    U = np.empty((npch, 5, n, n, n))
+    VZ = blocks(vz)
+    del vz
+    U[:, 0] = rho
+    U[:, 1] = blocks2(rho * vx2)
+    U[:, 2] = blocks2(rho * vy2)
+    U[:, 3] = rho * VZ
+    vx = blocks2(vx2)
+    vy = blocks2(vy2)
+    U[:, 4] = p / (gamma - 1.0) + 0.5 * rho * (vx ** 2 + vy ** 2 + VZ ** 2) + 0.5 * blocks2(me2)
+    del VZ, vx, vy
+    # faces of each patch (both boundary faces), periodic wrap at the box edge
+    cx = (np.arange(P)[:, None] * n + np.arange(n + 1)[None, :]) % X      # (px, n+1)
+    rw = (np.arange(P)[:, None] * n + np.arange(n)[None, :])              # (py, n)
+    fx = bx2[rw[:, None, :, None], cx[None, :, None, :]]                   # (py, px, n, n+1)
+    bx = np.broadcast_to(fx[None, :, :, None], (P, P, P, n, n, n + 1)).reshape(-1)
+    ry = (np.arange(P)[:, None] * n + np.arange(n + 1)[None, :]) % Y       # (py, n+1)
+    cl = (np.arange(P)[:, None] * n + np.arange(n)[None, :])               # (px, n)
+    fy = by2[ry[:, None, :, None], cl[None, :, None, :]]                   # (py, px, n+1, n)
+    by = np.broadcast_to(fy[None, :, :, None], (P, P, P, n, n + 1, n)).reshape(-1)
+    bz = np.zeros(npch * (n + 1) * n * n)
+    return lay, (U.reshape(-1), np.ascontiguousarray(bx), np.ascontiguousarray(by), bz)
+
+
 def config_uniform(layout, W0, gamma, seed=0, eps=0.0):
     """Uniform state plus an optional seeded cell-wise density perturbation."""
     rng = np.random.default_rng(seed)

@@ -14,8 +14,9 @@ sys.path.insert(0, ROOT)
 
 
 def test_reference_arm_prints_one_contract_line():
+    # a 4^3-patch box keeps the CPU run small; the line's keys do not depend on it
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+                          "--warmup", "3", "--patches", "4"], capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -32,11 +33,18 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_algorithmic_bytes_and_flops_per_cell_update():
     import bench
-    # read and write 8 stored fields, plus the radius-2 guard shell of a 32^3
-    # patch from one neighbour slice: ((36^3 - 32^3) / 32^3) * 8 values
-    shell = (36 ** 3 - 32 ** 3) / 32 ** 3
+    # read and write 8 stored fields, plus the g = 3 guard shell of a 32^3
+    # patch from one neighbour slice: ((38^3 - 32^3) / 32^3) * 8 values,
+    # 171.2 B (FP64) and 85.6 B (FP32) per cell-update; the stencil's own
+    # radius-2 shell beside it
+    shell = (38 ** 3 - 32 ** 3) / 32 ** 3
     assert bench.alg_bytes_per_cell(32, 8) == pytest.approx(8 * (16 + shell * 8))
-    assert bench.alg_bytes_per_cell(32, 4) == pytest.approx(4 * (16 + shell * 8))
+    assert bench.alg_bytes_per_cell(32, 8) == pytest.approx(171.2, abs=0.05)
+    assert bench.alg_bytes_per_cell(32, 4) == pytest.approx(85.6, abs=0.05)
+    assert bench.alg_bytes_per_cell(16, 8) == pytest.approx(230.4, abs=0.05)
+    assert bench.alg_bytes_per_cell(24, 4, sbar=2) == pytest.approx(125.0, abs=0.05)
+    shell2 = (36 ** 3 - 32 ** 3) / 32 ** 3
+    assert bench.alg_bytes_radius2(32, 4) == pytest.approx(4 * (16 + shell2 * 8))
     assert bench.ALG_FLOPS_PER_CELL == 1424
     assert bench.ALG_FLOPS_PER_CELL_HLLD == 1424 + 3 * (170 - 37)
 

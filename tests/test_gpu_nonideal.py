@@ -179,3 +179,36 @@ def test_nonideal_with_hlld_faces():
         else:
             for a, b in zip(g.get_state(), o.get_state()):
                 assert float(np.max(np.abs(a - b)) / np.max(np.abs(b))) <= 1e-11
+
+
+@pytest.mark.parametrize("name,t_end,bound,ratio", [("ad_iso", 0.2, 0.01, 2.0), ("ad_noniso", 0.2, 0.015, 2.0),
+                                                     ("ohm", 0.3, 0.03, 1.0)])
+def test_cshock_jump_settles_to_steady_profile_on_gpu(name, t_end, bound, ratio):
+    """Sec. 5.4's three C-shock experiments on the GPU (FP64 without FMA,
+    local steps, CUDA graphs), from the Table 1 discontinuity on a periodic
+    box of 4 (300 cells, patches of 30 x 4 x 4): B_y settles to the steady
+    C-shock profile of the conservation laws (mean distance within 0.3 of
+    the shock, over the jump, below `bound`), and the patch steps differ by
+    a factor of 2 in the ambipolar runs and not at all in the Ohmic one, as
+    the paper reports.  The figures are printed (run with -s)."""
+    import json
+    import time
+    from cshock_ode import jump_input, most_common_steps, profile_error
+    lay, f, gamma, kw, xc = jump_input(name)
+    g = Dispatch(lay.n, lay.lo, gamma=gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
+                 time_mode=1, graph=1, precision=0, sched_capacity=1 << 22, **kw)
+    g.set_state(*ics.to_patches(lay, f))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = g.advance(t_end=t_end)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    By = ics.from_patches(lay, *g.get_state())[2][0, 0]
+    steps = most_common_steps(g.schedule(), lay.npatch)
+    err = profile_error(name, xc, By, 3.0)
+    r = float(steps.max() / steps.min())
+    print("CSHOCK %s" % json.dumps({"case": name, "t_end": t_end, "profile_error": err, "step_ratio": r,
+                                    "patch_updates": st["patch_updates"], "seconds": el}))
+    g.close()
+    assert err < bound, err
+    assert r == ratio, r
