@@ -143,7 +143,20 @@ typedef struct {
  *                and the next older slice (the next newer where none is
  *                older; the newest three past the newest), which the closing
  *                paragraph of Sec. 3 B allows; any other value:
- *                DSP_ERR_INVALID_ARG */
+ *                DSP_ERR_INVALID_ARG
+ *   owned        NULL: every patch is this context's own.  Else one byte per
+ *                patch: 1 = owned (updated here), 0 = virtual, a copy of a
+ *                patch that another process owns (Sec. 3 C, the MPI process
+ *                view): never updated here, its new states arrive through
+ *                dsp_unpack.  With virtual patches the layout is one
+ *                process's share: it need not tile the box, but every guard
+ *                cell (nguard layers) of an owned patch must lie in a patch of
+ *                the layout (else DSP_ERR_INVALID_ARG); it needs local steps,
+ *                g = 0, the sweep dispatcher and one level (else
+ *                DSP_ERR_UNSUPPORTED); a sweep with no owned patch ready
+ *                returns normally (it waits for other processes), and
+ *                dsp_diagnostics counts owned patches only.  The array is
+ *                read during dsp_create only */
 typedef struct {
   double gamma, cfl, t0, dt_max, grace;
   double box_lo[3], box_len[3];
@@ -158,6 +171,7 @@ typedef struct {
   int32_t riemann;
   double eta, gamma_ad, rho_i, c_ohm, c_ad;
   int32_t time_order;
+  const uint8_t *owned;
 } dsp_params;
 
 /* Counters of one dsp_advance call.  kernel_ms and kernel_launches are the
@@ -318,6 +332,32 @@ DSP_API int dsp_diagnostics_noalloc(const void *U, const void *bx, const void *b
  * a run resumed from it is bit-identical to the uninterrupted run. */
 DSP_API int dsp_save(dsp_ctx *ctx, void *buf, size_t cap, size_t *used);
 DSP_API int dsp_load(dsp_ctx *ctx, const void *buf, size_t size);
+
+/* Packages between processes (Sec. 3 C, the MPI process view): after a
+ * process updates a patch that other processes hold as a virtual copy, it
+ * sends them the patch's whole interior and its time parameters, and each
+ * receiver stores them as the copy's new slice.  The paper ships the whole
+ * interior rather than guard layers only, which keeps packing simple; so do
+ * these calls.  A package of patch P is its newest slice: the values of U,
+ * bx, by, bz of P (dsp_set_state layout of one patch), contiguous, in the
+ * context's precision (float64, or float32 for precision 1), and three
+ * doubles of meta: the slice's time, P's last step, the slice's signal
+ * speed.  A list's packages are concatenated in list order.
+ *
+ * dsp_package_len: the number of values (not bytes) of the packages of the
+ * listed patches (distinct indices of this context).
+ * dsp_pack: write the packages of the listed patches into buf and meta
+ * (3 * count doubles); on_device: 1 if buf and meta are device memory, else
+ * host memory staged through a library-owned device buffer.
+ * dsp_unpack: store each listed package as the newest slice of its patch,
+ * which must be virtual (DSP_ERR_INVALID_ARG otherwise): written into the
+ * slot after the newest, which then becomes the newest, with the meta's
+ * time, last step and signal speed.  Not on a poisoned context.
+ * All three copy: the caller keeps its arrays; both are synchronous. */
+DSP_API int dsp_package_len(dsp_ctx *ctx, const int32_t *ids, int32_t count, int64_t *values);
+DSP_API int dsp_pack(dsp_ctx *ctx, const int32_t *ids, int32_t count, void *buf, double *meta, int32_t on_device);
+DSP_API int dsp_unpack(dsp_ctx *ctx, const int32_t *ids, int32_t count, const void *buf, const double *meta,
+                       int32_t on_device);
 
 /* Message of the last error on this context ("" if none).  Valid until the
  * next call on the context.  No counterpart in the paper. */

@@ -66,6 +66,7 @@ typedef struct {
   double dt_last;
   int nnb;
   int *nb;
+  int virt; /* 1: a copy of a patch another process owns (Sec. 3 C), never updated here */
 } opatch;
 
 typedef struct {
@@ -89,6 +90,7 @@ typedef struct {
   double *s_t, *s_dt;
   int64_t n_updates, n_cells, n_sweeps, n_fallback;
   int64_t n_floor; /* cells of new slices whose pressure recovery took the floor */
+  int nvirt;        /* virtual patches (Sec. 3 C); 0 in a whole-domain context */
   int status;
   char err[256];
 } orc_ctx;
@@ -1407,7 +1409,7 @@ static int slot_free(orc_ctx *c, int ip) {
 static int ready(orc_ctx *c, int ip, double t_end) {
   opatch *P = &c->p[ip];
   double t = P->ts[P->latest];
-  if (!(t < t_end)) return 0;
+  if (P->virt || !(t < t_end)) return 0;
   for (int q = 0; q < P->nnb; q++) {
     opatch *Q = &c->p[P->nb[q]];
     if (!(t <= Q->ts[Q->latest] + c->grace * Q->dt_last)) return 0;
@@ -1574,6 +1576,10 @@ int orc_advance(orc_ctx *c, double t_end, int64_t max_sweeps) {
     return ORC_EINVAL;
   }
   if (c->time_mode == 1 && c->disp_mode == 0) {
+    if (c->nvirt) {
+      snprintf(c->err, sizeof c->err, "a context with virtual patches advances by sweeps");
+      return ORC_EINVAL;
+    }
     rc = queue_run(c, t_end);
   } else {
     for (int64_t s = 0; max_sweeps <= 0 || s < max_sweeps; s++) {
@@ -1581,8 +1587,9 @@ int orc_advance(orc_ctx *c, double t_end, int64_t max_sweeps) {
       rc = sweep(c, t_end, &nr);
       if (rc) break;
       if (nr == 0) {
-        for (int i = 0; i < c->np; i++)
-          if (c->p[i].ts[c->p[i].latest] < t_end) { rc = ORC_EDEADLOCK; break; }
+        if (c->nvirt == 0)
+          for (int i = 0; i < c->np; i++)
+            if (c->p[i].ts[c->p[i].latest] < t_end) { rc = ORC_EDEADLOCK; break; }
         break;
       }
     }
@@ -1633,6 +1640,7 @@ void orc_diagnostics(orc_ctx *c, double *out) {
   double mdiv = 0.0, mb = 0.0;
   for (int ip = 0; ip < c->np; ip++) {
     opatch *P = &c->p[ip];
+    if (P->virt) continue; /* another process owns it and counts it */
     double dxl = ldexp(c->dx, -P->level);
     double dV = dxl * dxl * dxl;
     int s = P->latest, nx = P->n[0], ny = P->n[1], nz = P->n[2];
@@ -1661,4 +1669,65 @@ void orc_diagnostics(orc_ctx *c, double *out) {
   for (int q = 0; q < 8; q++) out[q] = acc[q].s + acc[q].c;
   out[8] = mdiv;
   out[9] = mb;
+}
+
+/* ------------------------------------------------------------------ */
+/* Several processes (Sec. 3 C, the MPI process view)                   */
+/* ------------------------------------------------------------------ */
+/* A process holds the patches it owns and 'virtual' copies of the patches
+ * other processes own next to them.  owned[i] = 1 for an owned patch, 0 for
+ * a virtual one.  A virtual patch is never updated here; each new state of
+ * it arrives as a package (its interior and its time parameters) that the
+ * owner sends after updating it, and is stored like a new time slice.
+ * Every sweep runs here only over the owned patches.  Local time steps with
+ * g = 0 only: a global step is a minimum over all processes, and with g > 0
+ * a slice's lifetime depends on neighbours held elsewhere. */
+int orc_set_owned(orc_ctx *c, const int8_t *owned) {
+  int nv = 0;
+  for (int i = 0; i < c->np; i++) {
+    c->p[i].virt = owned[i] ? 0 : 1;
+    nv += c->p[i].virt;
+  }
+  if (nv && (c->time_mode != 1 || c->grace > 0.0 || c->nlev > 1)) {
+    for (int i = 0; i < c->np; i++) c->p[i].virt = 0;
+    snprintf(c->err, sizeof c->err, "virtual patches need local steps, g = 0 and one level");
+    return ORC_EINVAL;
+  }
+  c->nvirt = nv;
+  return ORC_OK;
+}
+
+/* The package of patch ip: its newest slice (U, bx, by, bz in the
+ * dsp_set_state layout of one patch) and meta = (time of that slice, the
+ * patch's last step, the slice's signal speed). */
+int orc_get_newest(orc_ctx *c, int ip, double *U, double *bx, double *by, double *bz, double *meta) {
+  if (ip < 0 || ip >= c->np) return ORC_EINVAL;
+  opatch *P = &c->p[ip];
+  int s = P->latest;
+  memcpy(U, P->U[s], sizeof(double) * 5 * ncell(P));
+  memcpy(bx, P->bx[s], sizeof(double) * nfx(P));
+  memcpy(by, P->by[s], sizeof(double) * nfy(P));
+  memcpy(bz, P->bz[s], sizeof(double) * nfz(P));
+  meta[0] = P->ts[s];
+  meta[1] = P->dt_last;
+  meta[2] = P->smax[s];
+  return ORC_OK;
+}
+
+/* Store a received package as the newest slice of virtual patch ip (in the
+ * slot after its newest, as an update would). */
+int orc_push_slice(orc_ctx *c, int ip, const double *U, const double *bx, const double *by, const double *bz,
+                   const double *meta) {
+  if (ip < 0 || ip >= c->np || !c->p[ip].virt) return ORC_EINVAL;
+  opatch *P = &c->p[ip];
+  int s = (P->latest + 1) % c->nslot;
+  memcpy(P->U[s], U, sizeof(double) * 5 * ncell(P));
+  memcpy(P->bx[s], bx, sizeof(double) * nfx(P));
+  memcpy(P->by[s], by, sizeof(double) * nfy(P));
+  memcpy(P->bz[s], bz, sizeof(double) * nfz(P));
+  P->ts[s] = meta[0];
+  P->dt_last = meta[1];
+  P->smax[s] = meta[2];
+  P->latest = s;
+  return ORC_OK;
 }

@@ -91,6 +91,9 @@ def lib():
             L.orc_emf.argtypes = [P, P, P, P, ctypes.c_int, D, D, D, D]
             L.orc_pow2_floor.restype = D
             L.orc_pow2_floor.argtypes = [D]
+            L.orc_set_owned.argtypes = [P, P]
+            L.orc_get_newest.argtypes = [P, ctypes.c_int, P, P, P, P, P]
+            L.orc_push_slice.argtypes = [P, ctypes.c_int, P, P, P, P, P]
             _lib = L
     return _lib
 
@@ -217,6 +220,30 @@ class Oracle:
         sm = np.zeros(1)
         self._check(lib().orc_update_patch(self._h, ip, dt, _ptr(U), _ptr(bx), _ptr(by), _ptr(bz), _ptr(sm)))
         return U, bx, by, bz, float(sm[0])
+
+    def set_owned(self, owned):
+        """Sec. 3 C: owned[i] = 1 for a patch this process updates, 0 for a
+        virtual copy of a patch another process owns."""
+        o = np.ascontiguousarray(owned, dtype=np.int8)
+        assert o.size == self.np
+        self._check(lib().orc_set_owned(self._h, _ptr(o)))
+
+    def newest(self, ip):
+        """The package of patch ip: (U, bx, by, bz) of its newest slice and
+        (time, last step, signal speed)."""
+        U = np.empty(5 * self.ncell[ip])
+        bx = np.empty(self.nfx[ip])
+        by = np.empty(self.nfy[ip])
+        bz = np.empty(self.nfz[ip])
+        meta = np.empty(3)
+        self._check(lib().orc_get_newest(self._h, ip, _ptr(U), _ptr(bx), _ptr(by), _ptr(bz), _ptr(meta)))
+        return (U, bx, by, bz), meta
+
+    def push(self, ip, arrays, meta):
+        """Store a received package as the newest slice of virtual patch ip."""
+        U, bx, by, bz = (_f64(a) for a in arrays)
+        meta = _f64(meta)
+        self._check(lib().orc_push_slice(self._h, ip, _ptr(U), _ptr(bx), _ptr(by), _ptr(bz), _ptr(meta)))
 
     def fill_padded(self, ip, nguard=3):
         """The padded box of patch ip at its current time (guard depth

@@ -46,7 +46,11 @@ struct dsp_ctx {
   // device allocations
   void *slab;
   double *t_slot, *smax_slot, *dt_last, *dtR;
-  int *latest, *nbl_off_d, *nbl_d, *R, *ctl, *omap_d[2], *gmap0_d, *work_off_d, *rflag;
+  int *latest, *nbl_off_d, *nbl_d, *R, *ctl, *omap_d[2], *gmap0_d, *work_off_d, *rflag, *owned_d;
+  std::vector<int> owned;      // host copy (1 owned, 0 virtual)
+  int *pk_ids;                 // [np] patch list of a pack/unpack call
+  long long *pk_off;           // [np+1] its package offsets
+  double *pk_meta;             // [3 np] its meta values
   double *rdt;
   long long *gofs_d;
   void *gbuf;
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(EVAL_NT) plan_ready_kernel(DevCtx c, double t_
   int flag = 0;
   double dtP = 0.0;
   const double t = c.t_slot[(long long)P * c.ns + c.latest[P]];
-  if (t < t_end) {
+  if (t < t_end && (!c.owned || c.owned[P])) {
     c.ctl[CTL_NOTDONE] = 1;
     double tr;
     if (is_ready<false>(c, P, t_end, &tr)) {
@@ -262,8 +266,10 @@ __global__ void __launch_bounds__(PLAN_NT) plan_compact_kernel(DevCtx c, int glo
     } else {
       c.ctl[CTL_NREADY] = nr;
       if (nr == 0) {
+        // in a context with virtual patches an empty sweep waits for the
+        // packages of other processes; the caller detects a global deadlock
         if (!notdone) c.ctl[CTL_DONE] = 1;
-        else set_status(c, DSP_ERR_DEADLOCK, -1);
+        else if (!c.partial) set_status(c, DSP_ERR_DEADLOCK, -1);
       }
     }
   }
@@ -329,6 +335,45 @@ __global__ void xfer_kernel(DevCtx c, int first, int count, TU *U, TU *bx, TU *b
   }
 }
 
+// Packages of several processes (Sec. 3 C): the newest slice of each listed
+// patch -- its whole interior, U, bx, by, bz as laid out in a slice -- and
+// its time parameters.  dir 0 (pack): newest slice -> buf + off[k], meta[k] =
+// (time, last step, signal speed).  dir 1 (unpack): buf + off[k] -> the slot
+// after the newest, which then becomes the newest with meta's time, step and
+// signal speed.  One block per listed patch (the patches are distinct).
+template <typename T>
+__global__ void package_kernel(DevCtx c, const int *ids, const long long *off, int count, T *buf, double *meta,
+                               int dir) {
+  const int k = blockIdx.x;
+  if (k >= count) return;
+  const int P = ids[k];
+  const PatchGeo &g = c.geo[P];
+  const long long nc = (long long)g.n[0] * g.n[1] * g.n[2];
+  const long long len = 5 * nc + (long long)(g.n[0] + 1) * g.n[1] * g.n[2] + (long long)g.n[0] * (g.n[1] + 1) * g.n[2] +
+                        (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
+  const int L = c.latest[P];
+  const int s = dir == 0 ? L : (L + 1) % c.ns;
+  T *slot = (T *)c.slab + (long long)s * c.slot_stride + g.off;
+  T *pkg = buf + off[k];
+  for (long long l = threadIdx.x; l < len; l += blockDim.x) {
+    if (dir == 0) pkg[l] = slot[l];
+    else slot[l] = pkg[l];
+  }
+  if (threadIdx.x == 0) {
+    const long long ts = (long long)P * c.ns;
+    if (dir == 0) {
+      meta[3 * k] = c.t_slot[ts + L];
+      meta[3 * k + 1] = c.dt_last[P];
+      meta[3 * k + 2] = c.smax_slot[ts + L];
+    } else {
+      c.t_slot[ts + s] = meta[3 * k];
+      c.dt_last[P] = meta[3 * k + 1];
+      c.smax_slot[ts + s] = meta[3 * k + 2];
+      c.latest[P] = s;
+    }
+  }
+}
+
 __global__ void reset_times_kernel(DevCtx c, int first, int count, double t0) {
   for (int P = first + blockIdx.x * blockDim.x + threadIdx.x; P < first + count; P += gridDim.x * blockDim.x) {
     for (int s = 0; s < c.ns; s++) c.t_slot[(long long)P * c.ns + s] = s == 0 ? t0 : __longlong_as_double(0x7ff8000000000000ll);
@@ -378,6 +423,10 @@ __global__ void queue_init_kernel(DevCtx c, double t_end) {
 template <typename T>
 __global__ void __launch_bounds__(DIAG_NT) diag_kernel(DevCtx c, double *out) {
   const int P = blockIdx.x;
+  if (c.owned && !c.owned[P]) {  // a virtual patch: its owner counts it
+    if (threadIdx.x < DIAG_PER) out[(long long)P * DIAG_PER + threadIdx.x] = 0.0;
+    return;
+  }
   const PatchGeo &g = c.geo[P];
   const T *base = (const T *)c.slab + (long long)c.latest[P] * c.slot_stride + g.off;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -531,7 +580,7 @@ void free_all(dsp_ctx *c) {
                   c->work_off_d, c->geo_d, c->coff_d,
                   c->nbl_off_d, c->nbl_d, c->R,       c->ctl,     c->smax_new, c->cnt,    c->sched,
                   c->staging, c->q_patch, c->q_reads, c->p_state, c->tiles_done, c->q_dt, c->q_seq,
-                  c->q_free,  c->q_ctl};
+                  c->q_free,  c->q_ctl, c->owned_d, c->pk_ids, c->pk_off, c->pk_meta};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
@@ -642,6 +691,15 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
     for (int d = 0; d < 3; d++) bsz[0][d] = bsz[0][d] % 2 == 0 ? bsz[0][d] / 2 : 1;
   }
   if (nlev == 2 && prm->dispatcher == 0) return DSP_ERR_UNSUPPORTED;  // the ready queue runs one level
+  // several processes (Sec. 3 C): with virtual patches the layout is one
+  // process's share -- its own patches and copies of their neighbours --,
+  // advanced by local steps with g = 0 by sweeps, on one level
+  int nvirt = 0;
+  if (prm->owned)
+    for (int i = 0; i < npatch; i++) nvirt += prm->owned[i] ? 0 : 1;
+  const bool partial = nvirt > 0;
+  if (partial && (nlev == 2 || prm->time_mode != 1 || prm->grace > 0.0 || prm->dispatcher != 1))
+    return DSP_ERR_UNSUPPORTED;
   int mapd[2][3];
   long long nmap[2] = {1, 1};
   std::vector<int> omap[2], gmap0;
@@ -667,8 +725,32 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
           m = i;
         }
   }
-  for (long long k = 0; k < nmap[0]; k++)
-    if (omap[0][(size_t)k] < 0) return DSP_ERR_INVALID_ARG;  // level 0 is not a tiling
+  if (!partial) {
+    for (long long k = 0; k < nmap[0]; k++)
+      if (omap[0][(size_t)k] < 0) return DSP_ERR_INVALID_ARG;  // level 0 is not a tiling
+  } else {
+    // a share need not tile the box, but every guard cell of an owned patch
+    // must lie in a patch of the share
+    const int g = prm->nguard;
+    for (int i = 0; i < npatch; i++) {
+      if (!prm->owned[i]) continue;
+      const dsp_patch_desc &p = patches[i];
+      long long b0[3], b1[3];
+      for (int k = 0; k < 3; k++) {
+        const long long a = p.lo[k] - g, b = p.lo[k] + p.n[k] + g;
+        b0[k] = a >= 0 ? a / bsz[0][k] : -((-a + bsz[0][k] - 1) / bsz[0][k]);
+        b1[k] = (b - 1) >= 0 ? (b - 1) / bsz[0][k] : -((-(b - 1) + bsz[0][k] - 1) / bsz[0][k]);
+      }
+      for (long long bz = b0[2]; bz <= b1[2]; bz++)
+        for (long long by = b0[1]; by <= b1[1]; by++)
+          for (long long bx = b0[0]; bx <= b1[0]; bx++) {
+            const long long wx = ((bx % mapd[0][0]) + mapd[0][0]) % mapd[0][0];
+            const long long wy = ((by % mapd[0][1]) + mapd[0][1]) % mapd[0][1];
+            const long long wz = ((bz % mapd[0][2]) + mapd[0][2]) % mapd[0][2];
+            if (omap[0][(size_t)((wz * mapd[0][1] + wy) * mapd[0][0] + wx)] < 0) return DSP_ERR_INVALID_ARG;
+          }
+    }
+  }
   // the gather map of level 0: blocks covered by level 1 come from there
   gmap0 = omap[0];
   for (int i = 0; i < npatch; i++) {
@@ -868,7 +950,11 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
             alloc((void **)&c->rflag, sizeof(int) * npatch) && alloc((void **)&c->rdt, sizeof(double) * npatch) &&
             alloc((void **)&c->smax_new, sizeof(unsigned long long) * npatch) &&
             alloc((void **)&c->cnt, sizeof(long long) * CNT_COUNT) &&
-            alloc((void **)&c->sched, sizeof(dsp_sched_entry) * std::max<long long>(1, cap));
+            alloc((void **)&c->sched, sizeof(dsp_sched_entry) * std::max<long long>(1, cap)) &&
+            alloc((void **)&c->pk_ids, sizeof(int) * npatch) &&
+            alloc((void **)&c->pk_off, sizeof(long long) * (npatch + 1)) &&
+            alloc((void **)&c->pk_meta, sizeof(double) * 3 * npatch) &&
+            (!prm->owned || alloc((void **)&c->owned_d, sizeof(int) * npatch));
   if (ok && prm->dispatcher == 0) {
     const size_t C = 2 * (size_t)npatch;
     ok = alloc((void **)&c->q_patch, sizeof(int) * C) && alloc((void **)&c->q_dt, sizeof(double) * C) &&
@@ -919,6 +1005,12 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.p_state = c->p_state;
   d.tiles_done = c->tiles_done;
   d.wait_budget = prm->wait_budget > 0 ? prm->wait_budget : 4000000000ll;  // ~2 s of SM clock
+  c->owned.assign((size_t)npatch, 1);
+  if (prm->owned)
+    for (int i = 0; i < npatch; i++) c->owned[(size_t)i] = prm->owned[i] ? 1 : 0;
+  d.owned = prm->owned ? c->owned_d : nullptr;
+  d.partial = partial ? 1 : 0;
+  c->prm.owned = nullptr;  // the caller's array is not kept
   cudaError_t e = cudaMemcpyAsync(c->omap_d[0], omap[0].data(), sizeof(int) * omap[0].size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess && nlev == 2)
     e = cudaMemcpyAsync(c->omap_d[1], omap[1].data(), sizeof(int) * omap[1].size(), cudaMemcpyHostToDevice, c->stream);
@@ -926,6 +1018,8 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
     e = cudaMemcpyAsync(c->gmap0_d, gmap0.data(), sizeof(int) * gmap0.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->gofs_d, gofs.data(), sizeof(long long) * gofs.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && prm->owned)
+    e = cudaMemcpyAsync(c->owned_d, c->owned.data(), sizeof(int) * npatch, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess && gtotal > 0) e = cudaMemsetAsync(c->gbuf, 0, c->esize * (size_t)gtotal, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->geo_d, geo.data(), sizeof(PatchGeo) * geo.size(), cudaMemcpyHostToDevice, c->stream);
@@ -1362,6 +1456,85 @@ extern "C" int dsp_autotune(dsp_ctx *c, int32_t reps, int32_t *chosen, double *m
   if (chosen) *chosen = best->id;
   if (n) *n = count;
   return DSP_OK;
+}
+
+namespace {
+// Values of one patch's slice (and package).
+long long patch_len(const PatchGeo &g) {
+  const long long nc = (long long)g.n[0] * g.n[1] * g.n[2];
+  return 5 * nc + (long long)(g.n[0] + 1) * g.n[1] * g.n[2] + (long long)g.n[0] * (g.n[1] + 1) * g.n[2] +
+         (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
+}
+
+// Validate a patch list and build its package offsets; virtual_only: every
+// listed patch must be virtual.
+int package_plan(dsp_ctx *c, const int32_t *ids, int32_t count, bool virtual_only, std::vector<long long> &off) {
+  if (!ids || count < 0 || count > c->d.np) return fail(c, DSP_ERR_INVALID_ARG, "bad patch list");
+  std::vector<char> seen((size_t)c->d.np, 0);
+  off.assign((size_t)count + 1, 0);
+  for (int k = 0; k < count; k++) {
+    const int P = ids[k];
+    if (P < 0 || P >= c->d.np || seen[(size_t)P]) return fail(c, DSP_ERR_INVALID_ARG, "patch list entry %d: %d", k, P);
+    if (virtual_only && c->owned[(size_t)P]) return fail(c, DSP_ERR_INVALID_ARG, "patch %d is owned, not virtual", P);
+    seen[(size_t)P] = 1;
+    off[(size_t)k + 1] = off[(size_t)k] + patch_len(c->geo[(size_t)P]);
+  }
+  return DSP_OK;
+}
+
+int run_package(dsp_ctx *c, const int32_t *ids, int32_t count, void *buf, double *meta, int on_device, int dir) {
+  std::vector<long long> off;
+  int rc = package_plan(c, ids, count, dir == 1, off);
+  if (rc) return rc;
+  if (count == 0) return DSP_OK;
+  const size_t bytes = c->esize * (size_t)off[(size_t)count];
+  void *dbuf = buf;
+  double *dmeta = meta;
+  if (!on_device) {
+    rc = ensure_staging(c, bytes);
+    if (rc) return rc;
+    dbuf = c->staging;
+    dmeta = c->pk_meta;
+  }
+  CK(cudaMemcpyAsync(c->pk_ids, ids, sizeof(int) * count, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->pk_off, off.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, c->stream));
+  if (!on_device && dir == 1) {
+    CK(cudaMemcpyAsync(dbuf, buf, bytes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(dmeta, meta, sizeof(double) * 3 * count, cudaMemcpyHostToDevice, c->stream));
+  }
+  if (c->precision == 1)
+    package_kernel<float><<<count, 256, 0, c->stream>>>(c->d, c->pk_ids, c->pk_off, count, (float *)dbuf, dmeta, dir);
+  else
+    package_kernel<double><<<count, 256, 0, c->stream>>>(c->d, c->pk_ids, c->pk_off, count, (double *)dbuf, dmeta, dir);
+  CK(cudaGetLastError());
+  if (!on_device && dir == 0) {
+    CK(cudaMemcpyAsync(buf, dbuf, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(meta, dmeta, sizeof(double) * 3 * count, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return DSP_OK;
+}
+}  // namespace
+
+extern "C" int dsp_package_len(dsp_ctx *c, const int32_t *ids, int32_t count, int64_t *values) {
+  if (!c || !values) return DSP_ERR_INVALID_ARG;
+  std::vector<long long> off;
+  const int rc = package_plan(c, ids, count, false, off);
+  if (rc) return rc;
+  *values = off[(size_t)count];
+  return DSP_OK;
+}
+
+extern "C" int dsp_pack(dsp_ctx *c, const int32_t *ids, int32_t count, void *buf, double *meta, int32_t on_device) {
+  if (!c || !buf || !meta) return DSP_ERR_INVALID_ARG;
+  return run_package(c, ids, count, buf, meta, on_device, 0);
+}
+
+extern "C" int dsp_unpack(dsp_ctx *c, const int32_t *ids, int32_t count, const void *buf, const double *meta,
+                          int32_t on_device) {
+  if (!c || !buf || !meta) return DSP_ERR_INVALID_ARG;
+  if (c->poisoned) return fail(c, DSP_ERR_INVALID_ARG, "context is poisoned by an earlier error");
+  return run_package(c, ids, count, const_cast<void *>(buf), const_cast<double *>(meta), on_device, 1);
 }
 
 extern "C" const char *dsp_last_error(dsp_ctx *c) { return c ? c->err.c_str() : "null context"; }

@@ -83,6 +83,11 @@ struct DevCtx {
   double *smax_slot;       // [np][ns]
   int *latest;             // [np]
   double *dt_last;         // [np]
+  // several processes (Sec. 3 C): owned[P] = 1 for a patch this context
+  // updates, 0 for a virtual copy of a patch another process owns (NULL:
+  // every patch is owned); partial = 1 when some patch is virtual
+  const int *owned;
+  int partial;
   const int *nbl_off;      // [np+1] CSR of distinct neighbours (self excluded)
   const int *nbl;
   int *R;                  // [np] ready list of the current sweep

@@ -30,7 +30,7 @@ ERRORS = {v: k for k, v in globals().items() if k.startswith("DSP_ERR_")}
 
 EXPORTS = ["dsp_create", "dsp_set_state", "dsp_advance", "dsp_get_state", "dsp_get_times",
            "dsp_get_schedule", "dsp_diagnostics", "dsp_save", "dsp_load", "dsp_last_error",
-           "dsp_destroy", "dsp_diagnostics_noalloc", "dsp_autotune"]
+           "dsp_destroy", "dsp_diagnostics_noalloc", "dsp_autotune", "dsp_package_len", "dsp_pack", "dsp_unpack"]
 
 DSP_NOALLOC_MAX_PATCHES = 16384
 
@@ -50,7 +50,8 @@ class dsp_params(ctypes.Structure):
                 ("sched_capacity", ctypes.c_int64), ("timing", ctypes.c_int32), ("wait_budget", ctypes.c_int64),
                 ("graph", ctypes.c_int32), ("variant", ctypes.c_int32), ("riemann", ctypes.c_int32),
                 ("eta", ctypes.c_double), ("gamma_ad", ctypes.c_double), ("rho_i", ctypes.c_double),
-                ("c_ohm", ctypes.c_double), ("c_ad", ctypes.c_double), ("time_order", ctypes.c_int32)]
+                ("c_ohm", ctypes.c_double), ("c_ad", ctypes.c_double), ("time_order", ctypes.c_int32),
+                ("owned", ctypes.c_void_p)]
 
 
 class dsp_stats(ctypes.Structure):
@@ -110,6 +111,9 @@ def load(build_if_missing: bool = True):
         L.dsp_diagnostics_noalloc.argtypes = [VP, VP, VP, VP, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.POINTER(ctypes.c_int32), ctypes.c_double, VP,
                                               ctypes.POINTER(dsp_diag)]
+        L.dsp_package_len.argtypes = [VP, VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+        L.dsp_pack.argtypes = [VP, VP, ctypes.c_int32, VP, VP, ctypes.c_int32]
+        L.dsp_unpack.argtypes = [VP, VP, ctypes.c_int32, VP, VP, ctypes.c_int32]
         for name in EXPORTS:
             if name not in ("dsp_last_error", "dsp_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -138,7 +142,8 @@ class Dispatch:
     def __init__(self, n, lo, *, gamma, cfl, base_cells, box_len=(1.0, 1.0, 1.0), t0=0.0, dt_max=0.0,
                  nguard=3, nslices=3, precision=0, time_mode=0, dispatcher=1, tile_z=0,
                  sched_capacity=0, timing=0, wait_budget=0, graph=0, variant=-1, stream=None, level=None,
-                 riemann=0, eta=0.0, gamma_ad=0.0, rho_i=1.0, c_ohm=0.1, c_ad=0.1, grace=0.0, time_order=1):
+                 riemann=0, eta=0.0, gamma_ad=0.0, rho_i=1.0, c_ohm=0.1, c_ad=0.1, grace=0.0, time_order=1,
+                 owned=None):
         L = load()
         n = np.asarray(n, dtype=np.int64).reshape(-1, 3)
         lo = np.asarray(lo, dtype=np.int64).reshape(-1, 3)
@@ -171,9 +176,15 @@ class Dispatch:
         p.eta, p.gamma_ad, p.rho_i, p.c_ohm, p.c_ad = eta, gamma_ad, rho_i, c_ohm, c_ad
         # grace of Eq. 1 and the order of the time inter- and extrapolation
         p.time_order = time_order
+        # several processes (Sec. 3 C): 1 = owned, 0 = virtual copy
+        own = None if owned is None else np.ascontiguousarray(owned, dtype=np.uint8).reshape(-1)
+        if own is not None:
+            assert own.size == self.np
+            p.owned = own.ctypes.data_as(ctypes.c_void_p)
         self.params = p
         h = VP()
         rc = L.dsp_create(descs, self.np, ctypes.byref(p), VP(stream or 0), ctypes.byref(h))
+        p.owned = None                            # read during dsp_create only
         if rc != 0:
             raise DispatchError(rc, "dsp_create rejected the layout or parameters")
         self._h = h
@@ -274,6 +285,46 @@ class Dispatch:
 
     def load_state(self, blob: bytes):
         self._check(load().dsp_load(self._h, blob, len(blob)))
+
+    # ---- packages between processes (Sec. 3 C)
+    def package_len(self, ids):
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        n = ctypes.c_int64()
+        self._check(load().dsp_package_len(self._h, ids.ctypes.data_as(VP), ids.size, ctypes.byref(n)))
+        return n.value
+
+    def pack(self, ids, device=True):
+        """The packages of the listed patches: (values, meta (k, 3)), as torch
+        CUDA tensors (device=True) or numpy arrays."""
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        n = self.package_len(ids)
+        if device:
+            import torch
+            dt = torch.float32 if self.precision == 1 else torch.float64
+            buf = torch.empty(max(n, 1), dtype=dt, device="cuda")
+            meta = torch.empty((max(ids.size, 1), 3), dtype=torch.float64, device="cuda")
+            self._check(load().dsp_pack(self._h, ids.ctypes.data_as(VP), ids.size, VP(buf.data_ptr()),
+                                        VP(meta.data_ptr()), 1))
+            return buf[:n], meta[:ids.size]
+        buf = np.empty(max(n, 1), np.float32 if self.precision == 1 else np.float64)
+        meta = np.empty((max(ids.size, 1), 3))
+        self._check(load().dsp_pack(self._h, ids.ctypes.data_as(VP), ids.size, buf.ctypes.data_as(VP),
+                                    meta.ctypes.data_as(VP), 0))
+        return buf[:n], meta[:ids.size]
+
+    def unpack(self, ids, buf, meta):
+        """Store received packages as the newest slices of the listed virtual
+        patches (torch CUDA tensors or numpy arrays, both of one kind)."""
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        if ids.size == 0:
+            return
+        if not hasattr(buf, "data_ptr"):
+            buf = np.ascontiguousarray(buf)
+            meta = np.ascontiguousarray(meta, dtype=np.float64)
+        b, bdev, _ = _addr(buf)
+        m, mdev, _ = _addr(meta)
+        assert bdev == mdev
+        self._check(load().dsp_unpack(self._h, ids.ctypes.data_as(VP), ids.size, b, m, int(bdev)))
 
 
 def _check_noalloc_arrays(arrays, npatch, n):
