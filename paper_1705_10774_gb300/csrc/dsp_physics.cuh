@@ -69,8 +69,113 @@ __device__ __forceinline__ T tmin_nonneg(T a, T b) {
   using B = FBits<T>;
   return B::of(a) <= B::of(b) ? a : b;
 }
+// Evaluation order of the update's arithmetic.  kFast = false: the FP64
+// oracle's order, operation for operation (the FMA-free FP64 build).  kFast =
+// true (the FP64 build with fused multiply-adds and the FP32 build, which are
+// held to a tolerance, not to bit equality): FP64 comparisons, minima and
+// maxima as integer operations on the bit patterns (the FP64 pipe is the
+// FP64 kernel's bottleneck; the integer units are idle), and one division
+// per edge EMF instead of three.  Each translation unit of an update-kernel
+// variant defines DSP_FAST_ORDER from its precision.
+#ifndef DSP_FAST_ORDER
+#define DSP_FAST_ORDER 0
+#endif
+constexpr bool kFast = DSP_FAST_ORDER != 0;
+
+// Ordered integer key of an FP64 value: keys compare as the values do, for
+// every non-NaN input (-0 orders just below +0).
+__device__ __forceinline__ long long okey(double a) {
+  const long long i = __double_as_longlong(a);
+  return i ^ ((i >> 63) & 0x7fffffffffffffffll);
+}
+// min / max of two values (FP64 through ordered keys under kFast)
+template <typename T>
+__device__ __forceinline__ T fmin_k(T a, T b) {
+  if constexpr (kFast && sizeof(T) == 8) return okey(a) <= okey(b) ? a : b;
+  else return tmin(a, b);
+}
+template <typename T>
+__device__ __forceinline__ T fmax_k(T a, T b) {
+  if constexpr (kFast && sizeof(T) == 8) return okey(a) >= okey(b) ? a : b;
+  else return tmax(a, b);
+}
+// max(0, a, b): a negative value's bit pattern is a negative integer, a
+// positive value's orders as the value does
+template <typename T>
+__device__ __forceinline__ T pmax0(T a, T b) {
+  if constexpr (kFast && sizeof(T) == 8) {
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    return __longlong_as_double(max(max(ia, 0ll), ib));
+  } else {
+    return tmax(T(0), tmax(a, b));
+  }
+}
+// max(0, -a, -b)
+template <typename T>
+__device__ __forceinline__ T nmax0(T a, T b) {
+  if constexpr (kFast && sizeof(T) == 8) {
+    const long long s = (long long)0x8000000000000000ull;
+    const long long ia = __double_as_longlong(a) ^ s, ib = __double_as_longlong(b) ^ s;
+    return __longlong_as_double(max(max(ia, 0ll), ib));
+  } else {
+    return tmax(T(0), tmax(-a, -b));
+  }
+}
+// a >= 0 and a <= 0 (non-NaN a)
+template <typename T>
+__device__ __forceinline__ bool ge0(T a) {
+  if constexpr (kFast && sizeof(T) == 8) {
+    const long long i = __double_as_longlong(a);
+    return i >= 0 || i == (long long)0x8000000000000000ull;
+  } else {
+    return a >= T(0);
+  }
+}
+template <typename T>
+__device__ __forceinline__ bool le0(T a) {
+  if constexpr (kFast && sizeof(T) == 8) return __double_as_longlong(a) <= 0;
+  else return a <= T(0);
+}
+
 __device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ float tsqrt(float a) { return sqrtf(a); }
+
+// 1/x and sqrt(x) under kFast in FP64: the hardware approximations
+// (rcp.approx / rsqrt.approx, relative error about 1e-6) refined by two
+// Newton-Raphson steps, r <- r + r (1 - x r) and s <- s + (y/2)(x - s^2)
+// with y ~ 1/sqrt(x), which square the error twice (below 3e-16 relative,
+// measured against IEEE division and sqrt) in about 3.8 and 6.7 FP64-pipe
+// slots instead of the IEEE forms' 4.6 and 7.6.  Normal positive x (a
+// density, a sum of speeds squared); sqrt(0) = 0.  Elsewhere, and in FP32
+// (whose build divides and takes roots approximately already), the plain
+// operators.
+template <typename T>
+__device__ __forceinline__ T rcp_k(T x) {
+  if constexpr (kFast && sizeof(T) == 8) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"((double)x));
+    double e = fma(-(double)x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-(double)x, r, 1.0);
+    return fma(r, e, r);
+  } else {
+    return T(1) / x;
+  }
+}
+template <typename T>
+__device__ __forceinline__ T sqrt_k(T x) {
+  if constexpr (kFast && sizeof(T) == 8) {
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"((double)x));
+    double s = (double)x * y;
+    const double h = 0.5 * y;
+    s = fma(h, fma(-s, s, (double)x), s);
+    s = fma(h, fma(-s, s, (double)x), s);
+    return x == T(0) ? T(0) : s;
+  } else {
+    return tsqrt(x);
+  }
+}
 
 // Primitive state (rho, v, p, B) from conserved (rho, m, E) and the six faces.
 // With `floored`, *floored tells whether the pressure floor was taken.
@@ -78,7 +183,7 @@ template <typename T>
 __device__ __forceinline__ void prim(T rho, T mx, T my, T mz, T E, T bxl, T bxr, T byl, T byr, T bzl, T bzr,
                                      T gamma, T W[8], int *floored = nullptr) {
   const T h = T(0.5);
-  T irho = T(1) / rho;
+  T irho = rcp_k(rho);
   T Bx = h * (bxl + bxr);
   T By = h * (byl + byr);
   T Bz = h * (bzl + bzr);
@@ -89,8 +194,15 @@ __device__ __forceinline__ void prim(T rho, T mx, T my, T mz, T E, T bxl, T bxr,
   T me = h * (Bx * Bx + By * By + Bz * Bz);
   T p = (gamma - T(1)) * (E - ke - me);
   const T pf = T(PFLOOR) * rho;
-  if (floored) *floored = p < pf;
-  p = tmax(p, pf);
+  if constexpr (kFast && sizeof(T) == 8) {
+    // pf > 0: p's bit pattern orders below pf's exactly when p < pf
+    const bool fl = __double_as_longlong(p) < __double_as_longlong(pf);
+    if (floored) *floored = fl;
+    p = fl ? pf : p;
+  } else {
+    if (floored) *floored = p < pf;
+    p = tmax(p, pf);
+  }
   W[RHO] = rho; W[VX] = vx; W[VY] = vy; W[VZ] = vz; W[PR] = p;
   W[BX] = Bx; W[BY] = By; W[BZ] = Bz;
 }
@@ -105,7 +217,7 @@ __device__ __forceinline__ T cfast(T gamma, T irho, T p, T bn, T bt1, T bt2) {
   T s = a2 + bb;
   T disc = s * s - T(4) * a2 * ca2;
   if (tneg(disc)) disc = T(0);
-  return tsqrt(T(0.5) * (s + tsqrt(disc)));
+  return sqrt_k(T(0.5) * (s + sqrt_k(disc)));
 }
 
 // The non-ideal step limits of DISPATCH I, Sec. 4.3, as a signal speed s of
@@ -128,7 +240,7 @@ __device__ __forceinline__ T nonideal_speed(const T W[8], double cfl, double eta
 // Sum over axes of |v_d| + c_f,d: the signal speed that sets the Courant step.
 template <typename T>
 __device__ __forceinline__ T signal_sum(const T W[8], T gamma) {
-  T ir = T(1) / W[RHO];
+  T ir = rcp_k(W[RHO]);
   T cx = cfast(gamma, ir, W[PR], W[BX], W[BY], W[BZ]);
   T cy = cfast(gamma, ir, W[PR], W[BY], W[BZ], W[BX]);
   T cz = cfast(gamma, ir, W[PR], W[BZ], W[BX], W[BY]);
@@ -154,7 +266,7 @@ __device__ __forceinline__ void predict(const T W[8], const T dX[8], const T dY[
                                         T Ws[8]) {
   T rho = W[RHO], vx = W[VX], vy = W[VY], vz = W[VZ], p = W[PR];
   T Bx = W[BX], By = W[BY], Bz = W[BZ];
-  T irho = T(1) / rho;
+  T irho = rcp_k(rho);
   T divv = dX[VX] + dY[VY] + dZ[VZ];
   T r_rho = -(vx * dX[RHO] + vy * dY[RHO] + vz * dZ[RHO]) - rho * divv;
   T gpx = dX[PR] + (Bx * dX[BX] + By * dX[BY] + Bz * dX[BZ]);
@@ -201,7 +313,7 @@ __device__ __forceinline__ void hll(const T WL[8], const T WR[8], T gamma, T igm
     T E = p * igm1 + h * rho * v2 + h * B2;
     T PT = p + h * B2;
     T vB = vn * bn + vt1 * bt1 + vt2 * bt2;
-    T cf = cfast(gamma, T(1) / rho, p, bn, bt1, bt2);
+    T cf = cfast(gamma, rcp_k(rho), p, bn, bt1, bt2);
     T *Us = side ? UR : UL;
     T *Fs = side ? FR : FL;
     Us[0] = rho; Us[1] = rho * vn; Us[2] = rho * vt1; Us[3] = rho * vt2; Us[4] = E;
@@ -212,14 +324,15 @@ __device__ __forceinline__ void hll(const T WL[8], const T WR[8], T gamma, T igm
     Fs[4] = (E + PT) * vn - bn * vB;
     if (side) { cR = cf; vnR = vn; } else { cL = cf; vnL = vn; }
   }
-  SL = tmin(vnL - cL, vnR - cR);
-  SR = tmax(vnL + cL, vnR + cR);
+  SL = fmin_k(vnL - cL, vnR - cR);
+  SR = fmax_k(vnL + cL, vnR + cR);
   T Fr[5];
-  const T inv = T(1) / (SR - SL);
+  const T inv = rcp_k(SR - SL);
+  const bool left = ge0(SL), right = le0(SR);
 #pragma unroll
   for (int q = 0; q < 5; q++) {
-    if (SL >= T(0)) Fr[q] = FL[q];
-    else if (SR <= T(0)) Fr[q] = FR[q];
+    if (left) Fr[q] = FL[q];
+    else if (right) Fr[q] = FR[q];
     else Fr[q] = (SR * FL[q] - SL * FR[q] + SL * SR * (UR[q] - UL[q])) * inv;
   }
   F[0] = Fr[0];
@@ -357,10 +470,10 @@ __device__ __forceinline__ void hll_speeds(const T WL[8], const T WR[8], T gamma
   constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
   const T h = T(0.5);
   T bn = h * (WL[BX + D] + WR[BX + D]);
-  T cL = cfast(gamma, T(1) / WL[RHO], WL[PR], bn, WL[BX + t1], WL[BX + t2]);
-  T cR = cfast(gamma, T(1) / WR[RHO], WR[PR], bn, WR[BX + t1], WR[BX + t2]);
-  SL = tmin(WL[VX + D] - cL, WR[VX + D] - cR);
-  SR = tmax(WL[VX + D] + cL, WR[VX + D] + cR);
+  T cL = cfast(gamma, rcp_k(WL[RHO]), WL[PR], bn, WL[BX + t1], WL[BX + t2]);
+  T cR = cfast(gamma, rcp_k(WR[RHO]), WR[PR], bn, WR[BX + t1], WR[BX + t2]);
+  SL = fmin_k(WL[VX + D] - cL, WR[VX + D] - cR);
+  SR = fmax_k(WL[VX + D] + cL, WR[VX + D] + cR);
 }
 
 // Upwind HLL edge EMF from the four corner values around an edge (LL: low
@@ -375,8 +488,16 @@ __device__ __forceinline__ T emf(T Ell, T Erl, T Elr, T Err, T Ba_ll, T Ba_rl, T
   T BaL = h * (Ba_ll + Ba_rl);
   T BaR = h * (Ba_lr + Ba_rr);
   T num = apa * apb * Ell + ama * apb * Erl + apa * amb * Elr + ama * amb * Err;
-  T den = (apa + ama) * (apb + amb);
-  return num / den + apa * ama / (apa + ama) * (BbR - BbL) - apb * amb / (apb + amb) * (BaR - BaL);
+  if constexpr (kFast) {
+    // one reciprocal of the product of the two weight sums serves all three
+    // quotients
+    const T sa = apa + ama, sb = apb + amb;
+    const T r = rcp_k(sa * sb);
+    return num * r + (apa * ama * sb * r) * (BbR - BbL) - (apb * amb * sa * r) * (BaR - BaL);
+  } else {
+    T den = (apa + ama) * (apb + amb);
+    return num / den + apa * ama / (apa + ama) * (BbR - BbL) - apb * amb / (apb + amb) * (BaR - BaL);
+  }
 }
 
 }  // namespace dsp

@@ -745,10 +745,10 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const T rr_bz = (Sws[BZ * H1N + h0] - half * SdY[BZ * H1N + h0]) - half * SdZ[BZ * H1N + h0];
         const T Elr = lr_vz * lr_by - lr_vy * lr_bz;
         const T Err = rr_vz * rr_by - rr_vy * rr_bz;
-        const T apa = tmax(T(0), tmax(SYp[H1N + h0], SYc[H1N + h0]));
-        const T ama = tmax(T(0), tmax(-SYp[h0], -SYc[h0]));
-        const T apb = tmax(T(0), tmax(SZ[H1N + hm], SZ[H1N + h0]));
-        const T amb = tmax(T(0), tmax(-SZ[hm], -SZ[h0]));
+        const T apa = pmax0(SYp[H1N + h0], SYc[H1N + h0]);
+        const T ama = nmax0(SYp[h0], SYc[h0]);
+        const T apb = pmax0(SZ[H1N + hm], SZ[H1N + h0]);
+        const T amb = nmax0(SZ[hm], SZ[h0]);
         T ex = emf(Ell, Erl, Elr, Err, Ba_ll, Ba_rl, lr_by, rr_by, Bb_ll, Bb_rl, lr_bz, rr_bz, apa, ama, apb, amb);
         if constexpr (NI != 0) {
           const T en = eni_x(i, j, p);
@@ -774,10 +774,10 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const T rr_bx = (Sws[BX * H1N + h0] - half * SdZ[BX * H1N + h0]) - half * SdX[BX * H1N + h0];
         const T Erl = rl_vx * rl_bz - rl_vz * rl_bx;
         const T Err = rr_vx * rr_bz - rr_vz * rr_bx;
-        const T apa = tmax(T(0), tmax(SZ[H1N + hm], SZ[H1N + h0]));
-        const T ama = tmax(T(0), tmax(-SZ[hm], -SZ[h0]));
-        const T apb = tmax(T(0), tmax(SXp[H1N + h0], SXc[H1N + h0]));
-        const T amb = tmax(T(0), tmax(-SXp[h0], -SXc[h0]));
+        const T apa = pmax0(SZ[H1N + hm], SZ[H1N + h0]);
+        const T ama = nmax0(SZ[hm], SZ[h0]);
+        const T apb = pmax0(SXp[H1N + h0], SXc[H1N + h0]);
+        const T amb = nmax0(SXp[h0], SXc[h0]);
         T ey = emf(Ell, Erl, Elr, Err, Ba_ll, rl_bz, Ba_lr, rr_bz, Bb_ll, rl_bx, Bb_lr, rr_bx, apa, ama, apb, amb);
         if constexpr (NI != 0) {
           const T en = eni_y(i, j, p);
@@ -943,10 +943,10 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const T Erl = rl_vy * rl_bx - rl_vx * rl_by;
         const T Elr = lr_vy * lr_bx - lr_vx * lr_by;
         const T Err = rr_vy * rr_bx - rr_vx * rr_by;
-        const T apa = tmax(T(0), tmax(SXc[H1N + hrl], SXc[H1N + hrr]));
-        const T ama = tmax(T(0), tmax(-SXc[hrl], -SXc[hrr]));
-        const T apb = tmax(T(0), tmax(SYc[H1N + hlr], SYc[H1N + hrr]));
-        const T amb = tmax(T(0), tmax(-SYc[hlr], -SYc[hrr]));
+        const T apa = pmax0(SXc[H1N + hrl], SXc[H1N + hrr]);
+        const T ama = nmax0(SXc[hrl], SXc[hrr]);
+        const T apb = pmax0(SYc[H1N + hlr], SYc[H1N + hrr]);
+        const T amb = nmax0(SYc[hlr], SYc[hrr]);
         T ez = emf(Ell, Erl, Elr, Err, ll_bx, rl_bx, lr_bx, rr_bx, ll_by, rl_by, lr_by, rr_by, apa, ama, apb, amb);
         if constexpr (NI != 0) {
           const T en = eni_z(i, j, p);

@@ -3,6 +3,9 @@
 // defining V_ID, V_T, V_TX, V_TY, V_NT, V_MB, V_PREC, V_RS and V_NI (and the
 // floating-point flags of the precision: no FMA for FP64 parity, fast
 // division and square root for FP32).
+// FP64 without FMA keeps the oracle's evaluation order; the other builds
+// take the faster one (dsp_physics.cuh, kFast)
+#define DSP_FAST_ORDER (V_PREC != 0)
 #include "dsp_update.cuh"
 
 #define DSP_STR2(x) #x

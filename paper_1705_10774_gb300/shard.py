@@ -169,7 +169,8 @@ class ShardRunner:
             raise RuntimeError("rank %d: package from %d for patches it does not hold" % (self.plan.rank, peer))
         loc = self.plan.to_local(gids)
         self.engine.unpack(loc, vals, meta)
-        self._t[loc] = np.asarray(meta, np.float64).reshape(-1, 3)[:, 0]
+        m = meta.cpu().numpy() if hasattr(meta, "cpu") else np.asarray(meta)
+        self._t[loc] = np.asarray(m, np.float64).reshape(-1, 3)[:, 0]
 
     def not_done(self, t_end):
         t = np.asarray(self.engine.times(), np.float64)
