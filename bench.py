@@ -719,6 +719,9 @@ def mixed_arm(args):
     g = Dispatch(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
                  precision=1, time_mode=1, graph=1, timing=1, stream=stream.cuda_stream)
     g.set_state(*state)
+    if not args.no_tune:
+        g.autotune(reps=2)                    # a variant and z run per patch size
+    g.set_state(*state)
     g.advance(t_end=args.t_end / 4)           # warm-up
     g.set_state(*state)
     torch.cuda.synchronize()
@@ -733,7 +736,8 @@ def mixed_arm(args):
     print(json.dumps({"workload": "mixed 16/24/32 patches, %d^3, %d patches" % (X, lay.npatch),
                       "patch_sizes": dict(zip(map(int, sizes), map(int, counts))), "t_end": args.t_end,
                       "ms": ms, "cell_updates": st["cell_updates"], "sweeps": st["sweeps"],
-                      "cell_updates_per_s": st["cell_updates"] / (ms * 1e-3)}))
+                      "cell_updates_per_s": st["cell_updates"] / (ms * 1e-3), "tuning": g.tuning(),
+                      "tuning_candidates": getattr(g, "tuning_log", [])}))
     g.close()
 
 
@@ -757,7 +761,7 @@ def amr_arm(args):
                  box_len=lay.box_len, precision=1, time_mode=1, graph=1, timing=1, stream=stream.cuda_stream,
                  sched_capacity=1 << 22)
     g.set_state(*state)
-    tuned = g.autotune(reps=2)
+    tuned = g.autotune(reps=2) if not args.no_tune else (-1, {})
     g.set_state(*state)
     g.advance(t_end=args.t_end / 4)           # warm-up
     g.set_state(*state)
@@ -779,6 +783,7 @@ def amr_arm(args):
            "cell_updates_per_level": [int(cells[lev == l].sum()) for l in (0, 1)],
            "dt_per_level": [sorted(set(np.unique(dts[lev == l]).tolist()))[:4] for l in (0, 1)],
            "cell_updates_per_s": st["cell_updates"] / (ms * 1e-3), "variant": tuned[0],
+           "tuning": g.tuning(), "tuning_candidates": getattr(g, "tuning_log", []),
            "kernel_ms": st["kernel_ms"]}
     print(json.dumps(out))
     g.close()
@@ -812,6 +817,7 @@ def main():
                     help="lts / orszag-tang: side measurements (one JSON line each), not the benchmark line")
     ap.add_argument("--t-end", type=float, default=0.01, help="end time of the lts / orszag-tang / mixed runs")
     ap.add_argument("--blocks", type=int, default=5, help="96^3 super-blocks per axis of the mixed run")
+    ap.add_argument("--no-tune", action="store_true", help="mixed / amr runs: keep the default variant")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -21,8 +21,8 @@
  *   - the new state overwrites the oldest slice (Sec. 3 A).
  *
  * Every call returns 0 on success or one of the negative DSP_ERR_* codes.
- * After DSP_ERR_UNPHYSICAL, DSP_ERR_TIMEOUT, DSP_ERR_DEADLOCK, DSP_ERR_BRACKET
- * or DSP_ERR_CUDA the context is poisoned: only dsp_get_state, dsp_get_times,
+ * After DSP_ERR_UNPHYSICAL, DSP_ERR_TIMEOUT, DSP_ERR_DEADLOCK, DSP_ERR_BRACKET,
+ * DSP_ERR_BOUNDS or DSP_ERR_CUDA the context is poisoned: only dsp_get_state, dsp_get_times,
  * dsp_get_schedule, dsp_diagnostics, dsp_last_error and dsp_destroy remain
  * valid.  Calls on one context are not thread-safe; distinct contexts are
  * independent.  All device work is issued on the stream given to dsp_create
@@ -54,6 +54,7 @@ extern "C" {
 #define DSP_ERR_SCHEDULE_OVERFLOW (-7) /* the schedule log was larger than its capacity */
 #define DSP_ERR_UNSUPPORTED (-8)      /* a valid request this build does not implement */
 #define DSP_ERR_BRACKET (-9)          /* a neighbour's slices do not bracket a guard time */
+#define DSP_ERR_BOUNDS (-10)          /* bounds-checked build only: a global address outside every buffer */
 
 typedef struct dsp_ctx dsp_ctx;
 
@@ -277,18 +278,30 @@ DSP_API int dsp_get_schedule(dsp_ctx *ctx, dsp_sched_entry *buf, int64_t cap, in
  * host.  Valid on a poisoned context. */
 DSP_API int dsp_diagnostics(dsp_ctx *ctx, dsp_diag *out);
 
-/* Autotuner: time every compiled variant of the update kernel that fits this
- * context (tile shape, threads per block, blocks per SM) on the next sweep's
- * real ready list, `reps` launches each, and keep the fastest.  The paper has
- * no autotuner; its Sec. 5.3 notes that the best patch size depends on the
- * problem and the hardware, and on a GPU so does the tiling of a patch.  Nothing is
- * published and the state is unchanged (the update writes only the patches'
- * next slot); all variants compute bit-identical results.  Call after
- * dsp_set_state, before dsp_advance.  Writes the chosen variant id, and for
- * up to cap candidates their ids and average milliseconds per launch; *n
- * receives the number of candidates timed.  Any output pointer may be NULL. */
+/* Autotuner: for each patch-size class of the context (each distinct patch
+ * size, up to four, with the sweep dispatcher; else one class), time every
+ * compiled variant of the update kernel that fits (tile shape, threads per
+ * block, blocks per SM) with each z run of a work item (the patches' whole
+ * height and half of it, or dsp_params.tile_z when set) on the next sweep's
+ * real ready list of that class, `reps` launches each, and keep the fastest
+ * per class; every sweep then launches each class's own variant.  The paper
+ * has no autotuner; its Sec. 5.3 notes that the best patch size depends on
+ * the problem and the hardware, and on a GPU so does the tiling of a patch.
+ * Nothing is published and the state is unchanged (the update writes only
+ * the patches' next slot); all variants and z runs compute bit-identical
+ * results.  Call after dsp_set_state, before dsp_advance.  Writes the
+ * variant chosen for class 0, and for up to cap candidates their ids
+ * (class * 1000000 + z run * 1000 + variant id) and average milliseconds per
+ * launch; *n receives the number of candidates timed; dsp_get_tuning gives
+ * the choice of every class.  Any output pointer may be NULL. */
 DSP_API int dsp_autotune(dsp_ctx *ctx, int32_t reps, int32_t *chosen, double *ms, int32_t *ids, int32_t cap,
                          int32_t *n);
+
+/* The tuning in use: *ncls size classes; for each of the first cap classes
+ * its patch size (sizes[3k..3k+2], x y z), update-kernel variant and z run.
+ * Any output array may be NULL. */
+DSP_API int dsp_get_tuning(dsp_ctx *ctx, int32_t cap, int32_t *ncls, int32_t *sizes, int32_t *variant,
+                           int32_t *tile_z);
 
 /* Maximum number of patches dsp_diagnostics_noalloc accepts. */
 #define DSP_NOALLOC_MAX_PATCHES 16384

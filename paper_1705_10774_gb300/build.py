@@ -15,6 +15,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libdispatch_gpu.so")
+# the bounds-checked build: every global load and store of the update kernel
+# is checked against the slice and guard buffers (DSP_ERR_BOUNDS, no trap)
+OUT_DIR_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(OUT_DIR_CHECKED, "libdispatch_gpu_checked.so")
 ROOT = os.path.dirname(PKG)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -29,16 +33,21 @@ SOURCES = [
 PREC_FLAGS = {0: ["-fmad=false"], 1: ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"], 2: []}
 
 
-def variants():
-    """Rows of csrc/dsp_variants.h: (id, type, tx, ty, nt, mb, precision, riemann, nonideal)."""
+def variants(checked=False):
+    """Rows of csrc/dsp_variants.h: (id, type, tx, ty, nt, mb, precision,
+    riemann, nonideal) of the full list, or of the bounds-checked build's."""
     txt = open(os.path.join(CSRC, "dsp_variants.h")).read()
+    a = txt.index("#define DSP_VARIANT_LIST_ALL(X)")
+    b = txt.index("#define DSP_VARIANT_LIST_CHECKED(X)")
+    c = txt.index("#ifdef DSP_BOUNDS_CHECK")
+    txt = txt[b:c] if checked else txt[a:b]
     rows = re.findall(r"X\((\d+),\s*(\w+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", txt)
     return [(int(a), b, int(c), int(d), int(e), int(f), int(g), int(r), int(n)) for a, b, c, d, e, f, g, r, n in rows]
 
 
-def units():
+def units(checked=False):
     out = [(src, src.replace(".cu", ".o"), flags) for src, flags in SOURCES]
-    for vid, t, tx, ty, nt, mb, prec, rs, ni in variants():
+    for vid, t, tx, ty, nt, mb, prec, rs, ni in variants(checked):
         defs = ["-DV_ID=%d" % vid, "-DV_T=%s" % t, "-DV_TX=%d" % tx, "-DV_TY=%d" % ty, "-DV_NT=%d" % nt,
                 "-DV_MB=%d" % mb, "-DV_PREC=%d" % prec, "-DV_RS=%d" % rs, "-DV_NI=%d" % ni]
         out.append(("dsp_variant.cu", "dsp_variant_%d.o" % vid, defs + PREC_FLAGS[prec]))
@@ -59,22 +68,27 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(checked=False) -> bool:
+    lib = LIB_CHECKED if checked else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), checked=False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    out_dir = OUT_DIR_CHECKED if checked else OUT_DIR
+    if checked:
+        extra = tuple(extra) + ("-DDSP_BOUNDS_CHECK",)
+    if not force and up_to_date(checked):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     procs = []
     objs = []
-    for src, oname, flags in units():
-        obj = os.path.join(OUT_DIR, oname)
+    for src, oname, flags in units(checked):
+        obj = os.path.join(out_dir, oname)
         objs.append(obj)
         cmd = [nvcc, *COMMON, *ARCH, *flags, *extra, "-I", os.path.join(ROOT, "include"), "-c",
                os.path.join(CSRC, src), "-o", obj]
@@ -90,11 +104,11 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             failed.append(" ".join(cmd))
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     subprocess.check_call([nvcc, "-shared", *ARCH, "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

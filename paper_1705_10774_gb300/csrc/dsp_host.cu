@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -65,14 +66,25 @@ struct dsp_ctx {
   void *staging;
   size_t staging_bytes;
   int *h_ctl;  // pinned
-  int grid_update;
+  int grid_update;                         // grid of the ready-queue kernel
+  // size classes: each class's update-kernel variant, z run and grid
+  std::vector<int> cls;                    // [np] class of each patch
+  int ncls;
+  int cls_n[MAXCLS][3];                    // patch size of each class
+  const KernelVariant *var_cls[MAXCLS];
+  int tz_cls[MAXCLS];
+  int grid_cls[MAXCLS];
+  // launch groups: consecutive classes with the same variant share one
+  // launch over their stretches of the work list
+  int ngrp, grp_lo[MAXCLS], grp_hi[MAXCLS], grid_grp[MAXCLS];
+  int *Rk;
   cudaEvent_t ev[2 * 32];
   int nev;
   cudaGraphExec_t graph_exec;  // a captured batch of sweeps
   double graph_t_end;
   int graph_timing;
   int own_stream;  // the context created its stream (graph capture needs one)
-  const KernelVariant *var;  // the update-kernel variant in use
+  const KernelVariant *var;  // the update-kernel variant of class 0 (the ready queue's)
   int n_xlevel;              // patches with a cross-level guard buffer
   std::vector<dsp_patch_desc> patches;
 };
@@ -90,7 +102,7 @@ int fail(dsp_ctx *c, int code, const char *fmt, ...) {
     c->err = buf;
     if (code == DSP_ERR_CUDA) (void)cudaGetLastError();  // do not leak the error into later calls
     if (code == DSP_ERR_CUDA || code == DSP_ERR_UNPHYSICAL || code == DSP_ERR_TIMEOUT || code == DSP_ERR_DEADLOCK ||
-        code == DSP_ERR_BRACKET)
+        code == DSP_ERR_BRACKET || code == DSP_ERR_BOUNDS)
       c->poisoned = 1;
   }
   return code;
@@ -168,9 +180,38 @@ __global__ void __launch_bounds__(EVAL_NT) plan_ready_kernel(DevCtx c, double t_
   c.rdt[P] = dtP;
 }
 
-// Part 3 (one block): counters of the published sweep; the ready list in
-// patch order (ballot/popc scan), the global step (smallest ready step) in
-// global-step mode, the work offsets, and done / deadlock.
+// Block-wide exclusive scan of one flag per thread (ballot/popc per warp,
+// then warp 0 over the warp sums): *pos = this thread's position among the
+// flagged threads, returns their total.  Every thread of the block calls it.
+__device__ __forceinline__ int block_scan_flag(int flag, int *s_wsum, int &s_total, int *pos) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, flag);
+  if (lane == 0) s_wsum[wid] = __popc(bal);
+  __syncthreads();
+  if (wid == 0) {
+    const int v = s_wsum[lane];
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    s_wsum[lane] = incl - v;
+    if (lane == 31) s_total = incl;
+  }
+  __syncthreads();
+  *pos = s_wsum[wid] + __popc(bal & ((1u << lane) - 1u));
+  const int total = s_total;
+  __syncthreads();
+  return total;
+}
+
+// Part 3 (one block): counters of the published sweep; the ready list R in
+// patch order (publication and the schedule log follow it), the global step
+// (smallest ready step) in global-step mode, the work list Rk -- the ready
+// list's entries grouped by size class, each class's kernel taking its own
+// stretch [ctl[CTL_CLS + k], ctl[CTL_CLS + k + 1]) -- with its work offsets,
+// and done / deadlock.
 __global__ void __launch_bounds__(PLAN_NT) plan_compact_kernel(DevCtx c, int global_mode, int publish_only) {
   __shared__ int s_wsum[PLAN_NT / 32];
   __shared__ int s_base, s_total;
@@ -184,6 +225,7 @@ __global__ void __launch_bounds__(PLAN_NT) plan_compact_kernel(DevCtx c, int glo
       c.cnt[CNT_SWEEPS] += 1;
     }
     c.ctl[CTL_NREADY] = 0;
+    for (int k = 0; k <= MAXCLS; k++) c.ctl[CTL_CLS + k] = 0;
     s_base = 0;
     s_dtmin = 0x7ff0000000000000ull;  // +inf
   }
@@ -192,34 +234,22 @@ __global__ void __launch_bounds__(PLAN_NT) plan_compact_kernel(DevCtx c, int glo
   __syncthreads();
   if (tid == 0) c.ctl[CTL_NOTDONE] = 0;
   if (publish_only || c.ctl[CTL_STATUS] != 0) return;
+  // the ready list in patch order; rflag[P] becomes P's index in it plus one
   for (int chunk = 0; chunk < c.np; chunk += PLAN_NT) {
     const int P = chunk + tid;
     const int flag = P < c.np ? c.rflag[P] : 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, flag);
-    if (lane == 0) s_wsum[wid] = __popc(bal);
-    __syncthreads();
-    if (wid == 0) {
-      int v = s_wsum[lane];
-      int incl = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-      }
-      s_wsum[lane] = incl - v;
-      if (lane == 31) s_total = incl;
-    }
-    __syncthreads();
+    int pos;
+    const int total = block_scan_flag(flag, s_wsum, s_total, &pos);
     if (flag) {
       const double dtP = c.rdt[P];
-      const int idx = s_base + s_wsum[wid] + __popc(bal & ((1u << lane) - 1u));
+      const int idx = s_base + pos;
       c.R[idx] = P;
       c.dtR[idx] = dtP;
+      c.rflag[P] = idx + 1;
       c.smax_new[P] = 0ull;
       if (global_mode) atomicMin(&s_dtmin, (unsigned long long)__double_as_longlong(dtP));
     }
-    __syncthreads();
-    if (tid == 0) s_base += s_total;
+    if (tid == 0) s_base += total;
     __syncthreads();
   }
   const int nr = s_base;
@@ -227,13 +257,31 @@ __global__ void __launch_bounds__(PLAN_NT) plan_compact_kernel(DevCtx c, int glo
     const double dtg = __longlong_as_double((long long)s_dtmin);
     for (int r = tid; r < nr; r += PLAN_NT) c.dtR[r] = dtg;
   }
-  // work offsets: ready patch r owns update work items [work_off[r], work_off[r+1])
+  // the work list, grouped by size class
+  __shared__ int s_kb;
+  if (tid == 0) s_kb = 0;
+  __syncthreads();
+  for (int k = 0; k < c.ncls; k++) {
+    if (tid == 0) c.ctl[CTL_CLS + k] = s_kb;
+    for (int chunk = 0; chunk < c.np; chunk += PLAN_NT) {
+      const int P = chunk + tid;
+      const int ri = P < c.np ? c.rflag[P] : 0;
+      const int flag = ri > 0 && c.geo[P].cls == k;
+      int pos;
+      const int total = block_scan_flag(flag, s_wsum, s_total, &pos);
+      if (flag) c.Rk[s_kb + pos] = ri - 1;
+      if (tid == 0) s_kb += total;
+      __syncthreads();
+    }
+  }
+  if (tid == 0) c.ctl[CTL_CLS + c.ncls] = s_kb;
+  // work offsets: work-list entry i owns update work items [work_off[i], work_off[i+1])
   __shared__ int s_woff;
   if (tid == 0) s_woff = 0;
   __syncthreads();
   for (int chunk = 0; chunk < nr; chunk += PLAN_NT) {
     const int r = chunk + tid;
-    const int v = r < nr ? c.geo[c.R[r]].tiles : 0;
+    const int v = r < nr ? c.geo[c.R[c.Rk[r]]].tiles : 0;
     int incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -263,6 +311,7 @@ __global__ void __launch_bounds__(PLAN_NT) plan_compact_kernel(DevCtx c, int glo
   if (tid == 0) {
     if (c.ctl[CTL_STATUS] != 0) {
       c.ctl[CTL_NREADY] = 0;
+      for (int k = 0; k <= MAXCLS; k++) c.ctl[CTL_CLS + k] = 0;
     } else {
       c.ctl[CTL_NREADY] = nr;
       if (nr == 0) {
@@ -438,7 +487,36 @@ __global__ void __launch_bounds__(DIAG_NT) diag_kernel(DevCtx c, double *out) {
 
 int launch_queue(dsp_ctx *c, double t_end) { return c->var->launch_queue(c->d, c->grid_update, t_end, c->stream); }
 
-int launch_update(dsp_ctx *c) { return c->var->launch_update(c->d, c->grid_update, c->stream); }
+// The update kernels of a sweep: one launch per launch group (consecutive
+// size classes with the same variant), over its stretch of the work list.
+int launch_update(dsp_ctx *c) {
+  for (int g = 0; g < c->ngrp; g++) {
+    const int rc = c->var_cls[c->grp_lo[g]]->launch_update(c->d, c->grid_grp[g], c->stream, c->grp_lo[g], c->grp_hi[g]);
+    if (rc) return rc;
+  }
+  return DSP_OK;
+}
+
+// Only class k's update kernel (the autotuner's timing runs).
+int launch_update_class(dsp_ctx *c, int k) {
+  return c->var_cls[k]->launch_update(c->d, c->grid_cls[k], c->stream, k, k + 1);
+}
+
+// Launch groups and grids from the classes' variants.
+void make_groups(dsp_ctx *c) {
+  c->ngrp = 0;
+  for (int k = 0; k < c->ncls; k++) {
+    if (c->ngrp > 0 && c->var_cls[c->grp_lo[c->ngrp - 1]] == c->var_cls[k]) {
+      c->grp_hi[c->ngrp - 1] = k + 1;
+    } else {
+      c->grp_lo[c->ngrp] = k;
+      c->grp_hi[c->ngrp] = k + 1;
+      c->ngrp++;
+    }
+  }
+  for (int k = 0; k < c->ncls; k++) c->grid_cls[k] = c->var_cls[k]->grid(c->d, k, k + 1);
+  for (int g = 0; g < c->ngrp; g++) c->grid_grp[g] = c->var_cls[c->grp_lo[g]]->grid(c->d, c->grp_lo[g], c->grp_hi[g]);
+}
 
 // One dispatcher step: publish the previous sweep, then (unless
 // publish_only) find the next ready list and its steps.
@@ -465,41 +543,50 @@ const KernelVariant *(*const kVariants[])() = {DSP_VARIANT_LIST(DSP_VARIANT_ENTR
 #undef DSP_VARIANT_ENTRY
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
-// Per-patch tiles and offsets for the variant's tile shape; false if some
-// tile's owner table would not fit the kernel's table.
-bool make_geometry(const std::vector<dsp_patch_desc> &patches, int TX, int TY, int tz, const int bszl[2][3],
-                   std::vector<PatchGeo> &geo, long long &off, long long &total_tiles, int &uniform_tiles) {
+// Per-patch tiles and offsets, each patch tiled by its class's tile shape
+// tx[k] x ty[k] and z run tz[k]; false if some tile's owner table would not
+// fit the kernel's table.
+bool make_geometry(const std::vector<dsp_patch_desc> &patches, const std::vector<int> &cls, const int *tx,
+                   const int *ty, const int *tz, const int bszl[2][3], std::vector<PatchGeo> &geo, long long &off,
+                   long long &total_tiles, int &uniform_tiles, long long *cls_tiles) {
   const int npatch = (int)patches.size();
   geo.assign((size_t)npatch, PatchGeo());
   off = 0;
   total_tiles = 0;
+  for (int k = 0; k < MAXCLS; k++) cls_tiles[k] = 0;
   int tiles0 = -1;
   bool same_tiles = true;
   auto fdiv = [](long long a, long long b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
   for (int i = 0; i < npatch; i++) {
     PatchGeo &g = geo[(size_t)i];
+    const int k = cls[(size_t)i];
+    const int TX = tx[k], TY = ty[k];
     for (int d = 0; d < 3; d++) {
       g.n[d] = patches[(size_t)i].n[d];
       g.lo[d] = (int)patches[(size_t)i].lo[d];
     }
     g.level = patches[(size_t)i].level;
+    g.cls = k;
+    g.tz = std::min(tz[k], g.n[2]);
     const int *bsz = bszl[g.level];
     g.nt[0] = (g.n[0] + TX - 1) / TX;
     g.nt[1] = (g.n[1] + TY - 1) / TY;
-    g.nt[2] = (g.n[2] + tz - 1) / tz;
+    g.nt[2] = (g.n[2] + g.tz - 1) / g.tz;
     g.tiles = g.nt[0] * g.nt[1] * g.nt[2];
     g.off = off;
     const long long nc = (long long)g.n[0] * g.n[1] * g.n[2];
     off += 5 * nc + (long long)(g.n[0] + 1) * g.n[1] * g.n[2] + (long long)g.n[0] * (g.n[1] + 1) * g.n[2] +
            (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
     total_tiles += g.tiles;
+    cls_tiles[k] += g.tiles;
     if (tiles0 < 0) tiles0 = g.tiles;
     if (g.tiles != tiles0) same_tiles = false;
     for (int kz = 0; kz < g.nt[2]; kz++)
       for (int ky = 0; ky < g.nt[1]; ky++)
         for (int kx = 0; kx < g.nt[0]; kx++) {
-          const int org[3] = {kx * TX, ky * TY, kz * tz};
-          const int ext[3] = {std::min(TX, g.n[0] - org[0]), std::min(TY, g.n[1] - org[1]), std::min(tz, g.n[2] - org[2])};
+          const int org[3] = {kx * TX, ky * TY, kz * g.tz};
+          const int ext[3] = {std::min(TX, g.n[0] - org[0]), std::min(TY, g.n[1] - org[1]),
+                              std::min(g.tz, g.n[2] - org[2])};
           long long ne = 1;
           for (int d = 0; d < 3; d++)
             ne *= fdiv(g.lo[d] + org[d] + ext[d] + 2, bsz[d]) - fdiv(g.lo[d] + org[d] - 2, bsz[d]) + 1;
@@ -507,6 +594,31 @@ bool make_geometry(const std::vector<dsp_patch_desc> &patches, int TX, int TY, i
         }
   }
   uniform_tiles = same_tiles ? tiles0 : 0;
+  return true;
+}
+
+// Install the context's per-class variants and z runs: geometry, device
+// copy, grids.  False if some class's tiles do not fit.
+bool install_tuning(dsp_ctx *c) {
+  int tx[MAXCLS], ty[MAXCLS];
+  for (int k = 0; k < MAXCLS; k++) {
+    const KernelVariant *v = c->var_cls[k < c->ncls ? k : 0];
+    tx[k] = v->tx;
+    ty[k] = v->ty;
+  }
+  std::vector<PatchGeo> geo;
+  long long off = 0, tt = 0;
+  int ut = 0;
+  if (!make_geometry(c->patches, c->cls, tx, ty, c->tz_cls, c->d.bsz, geo, off, tt, ut, c->d.cls_tiles)) return false;
+  c->geo = geo;
+  c->d.total_tiles = tt;
+  c->d.uniform_tiles = ut;
+  c->var = c->var_cls[0];
+  if (cudaMemcpyAsync(c->geo_d, geo.data(), sizeof(PatchGeo) * geo.size(), cudaMemcpyHostToDevice, c->stream) !=
+      cudaSuccess)
+    return false;
+  make_groups(c);
+  c->grid_update = c->var->grid(c->d, 0, 1);
   return true;
 }
 
@@ -580,7 +692,7 @@ void free_all(dsp_ctx *c) {
                   c->work_off_d, c->geo_d, c->coff_d,
                   c->nbl_off_d, c->nbl_d, c->R,       c->ctl,     c->smax_new, c->cnt,    c->sched,
                   c->staging, c->q_patch, c->q_reads, c->p_state, c->tiles_done, c->q_dt, c->q_seq,
-                  c->q_free,  c->q_ctl, c->owned_d, c->pk_ids, c->pk_off, c->pk_meta};
+                  c->q_free,  c->q_ctl, c->owned_d, c->pk_ids, c->pk_off, c->pk_meta, c->Rk};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
@@ -770,14 +882,45 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
     if (prm->variant >= 0 ? v->id == prm->variant : !var) var = v;
   }
   if (!var) return DSP_ERR_INVALID_ARG;
-  int tz = prm->tile_z;
-  if (tz <= 0)
-    for (int i = 0; i < npatch; i++) tz = std::max(tz, patches[i].n[2]);
+  // size classes: one per distinct patch size (sweep dispatcher, at most
+  // MAXCLS sizes), else one for all; each starts with the default variant
+  // and a z run of its patches' whole height (or tile_z)
+  std::vector<int> cls((size_t)npatch, 0);
+  int ncls = 1, cls_n[MAXCLS][3] = {};
+  {
+    std::vector<std::array<int, 3>> sizes;
+    for (int i = 0; i < npatch; i++) {
+      const std::array<int, 3> s3 = {patches[i].n[0], patches[i].n[1], patches[i].n[2]};
+      if (std::find(sizes.begin(), sizes.end(), s3) == sizes.end()) sizes.push_back(s3);
+    }
+    std::sort(sizes.begin(), sizes.end());
+    if (prm->dispatcher == 1 && sizes.size() <= (size_t)MAXCLS) {
+      ncls = (int)sizes.size();
+      for (int i = 0; i < npatch; i++) {
+        const std::array<int, 3> s3 = {patches[i].n[0], patches[i].n[1], patches[i].n[2]};
+        cls[(size_t)i] = (int)(std::find(sizes.begin(), sizes.end(), s3) - sizes.begin());
+      }
+      for (int k = 0; k < ncls; k++)
+        for (int d = 0; d < 3; d++) cls_n[k][d] = sizes[(size_t)k][(size_t)d];
+    } else {
+      for (int d = 0; d < 3; d++) cls_n[0][d] = sizes.back()[(size_t)d];
+    }
+  }
+  int tzc[MAXCLS], txc[MAXCLS], tyc[MAXCLS];
+  for (int k = 0; k < MAXCLS; k++) {
+    txc[k] = var->tx;
+    tyc[k] = var->ty;
+    tzc[k] = 0;
+  }
+  for (int i = 0; i < npatch; i++) tzc[cls[(size_t)i]] = std::max(tzc[cls[(size_t)i]], patches[i].n[2]);
+  if (prm->tile_z > 0)
+    for (int k = 0; k < MAXCLS; k++) tzc[k] = prm->tile_z;
   std::vector<dsp_patch_desc> pvec(patches, patches + npatch);
   std::vector<PatchGeo> geo;
-  long long off = 0, total_tiles = 0;
+  long long off = 0, total_tiles = 0, cls_tiles[MAXCLS];
   int uniform_tiles = 0;
-  if (!make_geometry(pvec, var->tx, var->ty, tz, bsz, geo, off, total_tiles, uniform_tiles)) return DSP_ERR_UNSUPPORTED;
+  if (!make_geometry(pvec, cls, txc, tyc, tzc, bsz, geo, off, total_tiles, uniform_tiles, cls_tiles))
+    return DSP_ERR_UNSUPPORTED;
   const bool same_tiles = uniform_tiles > 0;
   if (prm->dispatcher == 0 && !same_tiles) return DSP_ERR_UNSUPPORTED;  // the ready queue needs equal tile counts
   dsp_ctx *c = new dsp_ctx();
@@ -802,10 +945,18 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   c->var = var;
   c->patches = pvec;
   c->n_xlevel = 0;
+  c->cls = cls;
+  c->ncls = ncls;
+  for (int k = 0; k < MAXCLS; k++) {
+    c->var_cls[k] = var;
+    c->tz_cls[k] = tzc[k];
+    for (int dd = 0; dd < 3; dd++) c->cls_n[k][dd] = cls_n[k][dd];
+  }
   DevCtx &d = c->d;
   d.np = npatch;
   d.ns = prm->nslices;
-  d.tz = tz;
+  d.ncls = ncls;
+  for (int k = 0; k < MAXCLS; k++) d.cls_tiles[k] = cls_tiles[k];
   d.uniform_tiles = uniform_tiles;
   d.total_tiles = total_tiles;
   d.slot_stride = off;
@@ -946,7 +1097,8 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
             alloc((void **)&c->work_off_d, sizeof(int) * (npatch + 1)) &&
             alloc((void **)&c->nbl_off_d, sizeof(int) * (npatch + 1)) &&
             alloc((void **)&c->nbl_d, sizeof(int) * std::max<size_t>(1, c->nbl.size())) &&
-            alloc((void **)&c->R, sizeof(int) * npatch) && alloc((void **)&c->ctl, sizeof(int) * CTL_COUNT) &&
+            alloc((void **)&c->R, sizeof(int) * npatch) && alloc((void **)&c->Rk, sizeof(int) * npatch) &&
+            alloc((void **)&c->ctl, sizeof(int) * CTL_COUNT) &&
             alloc((void **)&c->rflag, sizeof(int) * npatch) && alloc((void **)&c->rdt, sizeof(double) * npatch) &&
             alloc((void **)&c->smax_new, sizeof(unsigned long long) * npatch) &&
             alloc((void **)&c->cnt, sizeof(long long) * CNT_COUNT) &&
@@ -983,11 +1135,13 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.gmap[1] = d.omap[1];
   d.gofs = c->gofs_d;
   d.gbuf = c->gbuf;
+  d.gbuf_len = gtotal;
   d.coff = c->coff_d;
   d.work_off = c->work_off_d;
   d.nbl_off = c->nbl_off_d;
   d.nbl = c->nbl_d;
   d.R = c->R;
+  d.Rk = c->Rk;
   d.rflag = c->rflag;
   d.rdt = c->rdt;
   d.dtR = c->dtR;
@@ -1045,7 +1199,8 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
     delete c;
     return DSP_ERR_CUDA;
   }
-  c->grid_update = var->grid(d);
+  c->grid_update = var->grid(d, 0, 1);
+  make_groups(c);
   *out = c;
   return DSP_OK;
 }
@@ -1119,6 +1274,7 @@ int advance_queue(dsp_ctx *c, double t_end, const long long *c0, dsp_stats *out)
                        : st == DSP_ERR_TIMEOUT   ? "a ready-queue wait ran out of its budget"
                        : st == DSP_ERR_DEADLOCK  ? "no patch is ready but some are behind t_end"
                        : st == DSP_ERR_BRACKET   ? "neighbour slices do not bracket a guard-zone time"
+                       : st == DSP_ERR_BOUNDS    ? "a global address outside every buffer (bounds-checked build)"
                                                  : "device error";
     return fail(c, st, "%s (patch %d, cell %d)", what, c->h_ctl[CTL_ERRP], c->h_ctl[CTL_ERRC]);
   }
@@ -1237,6 +1393,7 @@ extern "C" int dsp_advance(dsp_ctx *c, double t_end, int64_t max_sweeps, dsp_sta
     const char *what = st == DSP_ERR_UNPHYSICAL ? "rho <= 0 or p <= 0 in a new state"
                        : st == DSP_ERR_DEADLOCK  ? "no patch is ready but some are behind t_end"
                        : st == DSP_ERR_BRACKET   ? "neighbour slices do not bracket a guard-zone time"
+                       : st == DSP_ERR_BOUNDS    ? "a global address outside every buffer (bounds-checked build)"
                                                  : "device error";
     return fail(c, st, "%s (patch %d, cell %d)", what, c->h_ctl[CTL_ERRP], c->h_ctl[CTL_ERRC]);
   }
@@ -1379,82 +1536,106 @@ extern "C" int dsp_autotune(dsp_ctx *c, int32_t reps, int32_t *chosen, double *m
                             int32_t *n) {
   if (!c || reps < 1) return DSP_ERR_INVALID_ARG;
   if (c->poisoned) return fail(c, DSP_ERR_INVALID_ARG, "context is poisoned by an earlier error");
-  const KernelVariant *best = nullptr;
-  double best_ms = 0.0;
-  int count = 0;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const std::vector<PatchGeo> geo_orig = c->geo;
-  const KernelVariant *var_orig = c->var;
-  const long long tt_orig = c->d.total_tiles;
-  const int ut_orig = c->d.uniform_tiles;
-  auto install = [&](const KernelVariant *v, const std::vector<PatchGeo> &geo, long long tt, int ut) -> int {
-    c->var = v;
-    c->geo = geo;
-    c->d.total_tiles = tt;
-    c->d.uniform_tiles = ut;
-    CK(cudaMemcpyAsync(c->geo_d, geo.data(), sizeof(PatchGeo) * geo.size(), cudaMemcpyHostToDevice, c->stream));
-    c->grid_update = v->grid(c->d);
-    return DSP_OK;
-  };
-  int rc = DSP_OK;
+  const KernelVariant *orig_var[MAXCLS];
+  int orig_tz[MAXCLS];
+  for (int k = 0; k < MAXCLS; k++) {
+    orig_var[k] = c->var_cls[k];
+    orig_tz[k] = c->tz_cls[k];
+  }
+  int rc = DSP_OK, count = 0;
   const int nonideal = c->var->nonideal;
-  for (int k = 0; k < kNumVariants && rc == DSP_OK; k++) {
-    const KernelVariant *v = kVariants[k]();
-    if (v->precision != c->precision || v->riemann != c->prm.riemann || v->nonideal != nonideal) continue;
-    std::vector<PatchGeo> geo;
-    long long off = 0, tt = 0;
-    int ut = 0;
-    if (!make_geometry(c->patches, v->tx, v->ty, c->d.tz, c->d.bsz, geo, off, tt, ut)) continue;
-    if (c->prm.dispatcher == 0 && ut == 0) continue;
-    rc = install(v, geo, tt, ut);
-    if (rc) break;
-    // plan the next sweep (nothing is published: the ready list is dropped
-    // afterwards, and the update kernel only writes the patches' next slot)
-    CK(cudaMemsetAsync(c->ctl + CTL_NREADY, 0, sizeof(int), c->stream));
-    if (launch_plan(c, INFINITY, c->prm.time_mode == 0, 0)) {
-      rc = fail(c, DSP_ERR_CUDA, "dispatcher kernel launch failed");
-      break;
+  // one class at a time: every fitting (variant, z run) pair, the others
+  // classes keeping their current choice
+  for (int k = 0; k < c->ncls && rc == DSP_OK; k++) {
+    const KernelVariant *best = nullptr;
+    int best_tz = 0;
+    double best_ms = 0.0;
+    const int nz = c->cls_n[k][2];
+    // z runs: the patches' whole height and half of it, or the caller's
+    const int tzs[2] = {c->prm.tile_z > 0 ? c->prm.tile_z : nz, c->prm.tile_z > 0 ? 0 : nz / 2};
+    for (int vi = 0; vi < kNumVariants && rc == DSP_OK; vi++) {
+      const KernelVariant *v = kVariants[vi]();
+      if (v->precision != c->precision || v->riemann != c->prm.riemann || v->nonideal != nonideal) continue;
+      for (int ti = 0; ti < 2 && rc == DSP_OK; ti++) {
+        const int tz = tzs[ti];
+        if (tz < 4 || (ti == 1 && tz == tzs[0])) continue;
+        c->var_cls[k] = v;
+        c->tz_cls[k] = tz;
+        if (!install_tuning(c)) continue;  // tiles do not fit this variant's tables
+        if (c->prm.dispatcher == 0 && c->d.uniform_tiles == 0) continue;
+        // plan the next sweep (nothing is published: the ready list is
+        // dropped afterwards, and the update kernel only writes the patches'
+        // next slot)
+        CK(cudaMemsetAsync(c->ctl + CTL_NREADY, 0, sizeof(int), c->stream));
+        if (launch_plan(c, INFINITY, c->prm.time_mode == 0, 0)) {
+          rc = fail(c, DSP_ERR_CUDA, "dispatcher kernel launch failed");
+          break;
+        }
+        rc = launch_xlevel(c);
+        if (rc) break;
+        rc = launch_update_class(c, k);
+        if (rc) break;
+        CK(cudaEventRecord(e0, c->stream));
+        for (int r = 0; r < reps && rc == DSP_OK; r++) rc = launch_update_class(c, k);
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        const double per = t / reps;
+        if (count < cap) {
+          if (ms) ms[count] = per;
+          if (ids) ids[count] = k * 1000000 + tz * 1000 + v->id;
+        }
+        count++;
+        if (!best || per < best_ms) {
+          best = v;
+          best_tz = tz;
+          best_ms = per;
+        }
+      }
     }
-    rc = launch_xlevel(c);
-    if (rc) break;
-    rc = launch_update(c);
-    if (rc) break;
-    CK(cudaEventRecord(e0, c->stream));
-    for (int r = 0; r < reps && rc == DSP_OK; r++) rc = launch_update(c);
-    CK(cudaEventRecord(e1, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    float t = 0.f;
-    CK(cudaEventElapsedTime(&t, e0, e1));
-    const double per = t / reps;
-    if (count < cap) {
-      if (ms) ms[count] = per;
-      if (ids) ids[count] = v->id;
-    }
-    count++;
-    if (!best || per < best_ms) {
-      best = v;
-      best_ms = per;
+    if (rc == DSP_OK && !best) rc = fail(c, DSP_ERR_UNSUPPORTED, "no kernel variant fits size class %d", k);
+    if (rc == DSP_OK) {
+      c->var_cls[k] = best;
+      c->tz_cls[k] = best_tz;
     }
   }
   CK(cudaMemsetAsync(c->ctl + CTL_NREADY, 0, sizeof(int), c->stream));
+  for (int k = 0; k <= MAXCLS; k++) CK(cudaMemsetAsync(c->ctl + CTL_CLS + k, 0, sizeof(int), c->stream));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (rc == DSP_OK && !best) rc = fail(c, DSP_ERR_UNSUPPORTED, "no kernel variant fits this layout");
   if (rc != DSP_OK) {
-    install(var_orig, geo_orig, tt_orig, ut_orig);
+    for (int k = 0; k < MAXCLS; k++) {
+      c->var_cls[k] = orig_var[k];
+      c->tz_cls[k] = orig_tz[k];
+    }
+    install_tuning(c);
     return rc;
   }
-  std::vector<PatchGeo> geo;
-  long long off = 0, tt = 0;
-  int ut = 0;
-  make_geometry(c->patches, best->tx, best->ty, c->d.tz, c->d.bsz, geo, off, tt, ut);
-  rc = install(best, geo, tt, ut);
-  if (rc) return rc;
+  if (!install_tuning(c)) return fail(c, DSP_ERR_CUDA, "installing the tuned variants failed");
   CK(cudaStreamSynchronize(c->stream));
-  if (chosen) *chosen = best->id;
+  if (c->graph_exec) {  // a captured batch holds the old launches
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  if (chosen) *chosen = c->var_cls[0]->id;
   if (n) *n = count;
+  return DSP_OK;
+}
+
+extern "C" int dsp_get_tuning(dsp_ctx *c, int32_t cap, int32_t *ncls, int32_t *sizes, int32_t *variant,
+                              int32_t *tile_z) {
+  if (!c || !ncls) return DSP_ERR_INVALID_ARG;
+  *ncls = c->ncls;
+  for (int k = 0; k < c->ncls && k < cap; k++) {
+    if (sizes)
+      for (int d = 0; d < 3; d++) sizes[3 * k + d] = c->cls_n[k][d];
+    if (variant) variant[k] = c->var_cls[k]->id;
+    if (tile_z) tile_z[k] = c->tz_cls[k];
+  }
   return DSP_OK;
 }
 

@@ -15,8 +15,14 @@ enum Ctl : int {
   CTL_ERRP = 3,     // patch of the first error
   CTL_ERRC = 4,     // cell (linear, patch-local) of the first error
   CTL_NOTDONE = 5,  // set by the readiness pass when some patch is behind t_end
-  CTL_COUNT = 8
+  CTL_CLS = 8,      // [MAXCLS + 1]: first ready-list entry of each size class, then the end
+  CTL_COUNT = 16
 };
+
+// Patch-size classes: each distinct patch size (up to MAXCLS of them) has its
+// own update-kernel variant and z run, chosen by dsp_autotune; more sizes
+// share one class.
+constexpr int MAXCLS = 4;
 
 // 64-bit counters in device memory.
 enum Cnt : int {
@@ -39,6 +45,8 @@ struct PatchGeo {
   int tiles;      // nt[0] * nt[1] * nt[2]
   int lo[3];      // first interior cell in the level's index space
   int level;      // refinement level (0, or 1 at half the cell size)
+  int tz;         // z run of the patch's work items (cells)
+  int cls;        // size class
   long long off;  // offset of the patch inside a slice
 };
 
@@ -48,9 +56,10 @@ constexpr int TABMAX = 128;
 // Everything a kernel needs, passed by value.
 struct DevCtx {
   int np, ns;
-  int tz;                  // z run of a work item (cells)
+  int ncls;                // size classes (1..MAXCLS)
   int uniform_tiles;       // tiles per patch when all patches have the same size, else 0
   long long total_tiles;   // tiles of all patches
+  long long cls_tiles[MAXCLS];  // tiles of each class's patches
   long long slot_stride;   // elements of one slice of all patches
   const PatchGeo *geo;     // [np]
   // per level l: the periodic box of L[l] cells per axis cut into blocks of
@@ -67,6 +76,7 @@ struct DevCtx {
   // a padded box of n + 4 cells per axis starting at lo - 2, laid out like a
   // patch slice, refilled before every update of the patch
   void *gbuf;
+  long long gbuf_len;      // elements of gbuf
   const long long *gofs;   // [np] element offset into gbuf, or -1
   const long long *coff;   // [4][np+1] offsets of each patch in the caller's U, bx, by, bz arrays
   int *work_off;           // [np+1] first work item of each ready patch (prefix of tiles)
@@ -90,7 +100,8 @@ struct DevCtx {
   int partial;
   const int *nbl_off;      // [np+1] CSR of distinct neighbours (self excluded)
   const int *nbl;
-  int *R;                  // [np] ready list of the current sweep
+  int *R;                  // [np] ready list of the current sweep (patch order)
+  int *Rk;                 // [np] the work list: indices into R grouped by size class
   int *rflag;              // [np] readiness of each patch (dispatcher scratch)
   double *rdt;             // [np] its step
   double *dtR;             // [np] step of each ready patch
@@ -118,9 +129,9 @@ struct KernelVariant {
   int nonideal;       // 1: with the non-ideal Ohmic and ambipolar terms
   int tx, ty, nt;     // tile and threads per block
   const char *name;
-  int (*launch_update)(const DevCtx &c, int grid, void *stream);
+  int (*launch_update)(const DevCtx &c, int grid, void *stream, int cls, int cls_end);
   int (*launch_queue)(const DevCtx &c, int grid, double t_end, void *stream);
-  int (*grid)(const DevCtx &c);
+  int (*grid)(const DevCtx &c, int cls, int cls_end);
 };
 
 #define DSP_DECLARE_VARIANT(id, T, TX, TY, NT, MB, PREC, RS, NI) const KernelVariant *variant_##id();

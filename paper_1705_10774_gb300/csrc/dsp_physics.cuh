@@ -256,8 +256,23 @@ __device__ __forceinline__ T mc(T dl, T dr) {
   using B = FBits<T>;
   const typename B::I a = B::of(dl), b = B::of(dr);
   if ((a & B::MAG) == 0 || (b & B::MAG) == 0 || (a ^ b) < 0) return T(0);
-  const T s = tmin_nonneg(tmin_nonneg(T(2) * tabs(dl), T(2) * tabs(dr)), T(0.5) * tabs(dl + dr));
-  return a < 0 ? B::to(B::of(s) ^ ~B::MAG) : s;
+  if constexpr (kFast && sizeof(T) == 8) {
+    // the same value as 2 min(|dl|, |dr|, |dl + dr| / 4): the power-of-two
+    // scalings are exact, so they are done on the exponent field with
+    // integer operations (an FP64 multiply where an exponent is near the
+    // ends of its range), leaving one FP64 operation, dl + dr
+    const long long m = min(a & B::MAG, b & B::MAG);
+    const double q = tabs(dl + dr);
+    long long iq = __double_as_longlong(q);
+    const long long one = 1ll << 52;
+    iq = (iq >> 52) > 2 ? iq - 2 * one : __double_as_longlong(0.25 * q);
+    long long is = min(m, iq);
+    is = (is >> 52) < 2046 && (is >> 52) > 0 ? is + one : __double_as_longlong(2.0 * __longlong_as_double(is));
+    return __longlong_as_double(a < 0 ? is | (long long)0x8000000000000000ull : is);
+  } else {
+    const T s = tmin_nonneg(tmin_nonneg(T(2) * tabs(dl), T(2) * tabs(dr)), T(0.5) * tabs(dl + dr));
+    return a < 0 ? B::to(B::of(s) ^ ~B::MAG) : s;
+  }
 }
 
 // Hancock half-step predictor in primitive form with d/dx_d -> dW_d, h = dt/(2dx).

@@ -199,8 +199,8 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
   const T hdt = (T)(0.5 * dt / dxl);
   const T dtdx = (T)(dt / dxl);
   const int tix = tile % gp.nt[0], tiy = (tile / gp.nt[0]) % gp.nt[1], tiz = tile / (gp.nt[0] * gp.nt[1]);
-  const int x0 = tix * TX, y0 = tiy * TY, z0 = tiz * c.tz;
-  const int tx = min(TX, nx - x0), ty = min(TY, ny - y0), tz = min(c.tz, nz - z0);
+  const int x0 = tix * TX, y0 = tiy * TY, z0 = tiz * gp.tz;
+  const int tx = min(TX, nx - x0), ty = min(TY, ny - y0), tz = min(gp.tz, nz - z0);
   const int Lp = newest<CONC>(c, P);
   const double tP = slot_time<CONC>(c, (long long)P * c.ns + Lp);
   const T *const own = (const T *)c.slab + (long long)Lp * c.slot_stride + gp.off;
@@ -277,16 +277,40 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     int e;
   };
   auto blended = [&](const Loc &l) -> bool { return l.e >= 0 && S.blend[l.e] != 0; };
+  // Bounds-checked build: every global address of the update is tested
+  // against the slab of slices and the cross-level guard buffers; an address
+  // outside both records DSP_ERR_BOUNDS and the access is redirected to the
+  // slab's first element (a load) or dropped (a store), so the run ends with
+  // that status and nothing faults.
+#ifdef DSP_BOUNDS_CHECK
+  auto inside = [&](const T *q) -> bool {
+    const T *s0 = (const T *)c.slab, *g0 = (const T *)c.gbuf;
+    return (q >= s0 && q < s0 + c.slot_stride * c.ns) || (g0 && q >= g0 && q < g0 + c.gbuf_len);
+  };
+  auto src = [&](const T *q) -> const T * {
+    if (inside(q)) return q;
+    set_error(c, DSP_ERR_BOUNDS, P, -1);
+    return (const T *)c.slab;
+  };
+  auto put_global = [&](T *q, T v) {
+    const T *s0 = (const T *)c.slab;
+    if ((const T *)q >= s0 && (const T *)q < s0 + c.slot_stride * c.ns) *q = v;
+    else set_error(c, DSP_ERR_BOUNDS, P, -1);
+  };
+#else
+  auto src = [&](const T *q) -> const T * { return q; };
+  auto put_global = [&](T *q, T v) { *q = v; };
+#endif
   auto fetch = [&](const Loc &l) -> T {
-    T a = *l.p;
+    T a = *src(l.p);
     if (l.e >= 0) {
       const int bl = S.blend[l.e];
       if (bl) {
-        const T b = l.p[(long long)(((bl >> 2) & 63) - 16) * c.slot_stride];
+        const T b = *src(l.p + (long long)(((bl >> 2) & 63) - 16) * c.slot_stride);
         if ((bl & 3) == 2) {
           a = a + S.wgt[0][l.e] * (b - a);
         } else {
-          const T cc = l.p[(long long)(((bl >> 8) & 63) - 16) * c.slot_stride];
+          const T cc = *src(l.p + (long long)(((bl >> 8) & 63) - 16) * c.slot_stride);
           a = (S.wgt[0][l.e] * a + S.wgt[1][l.e] * b) + S.wgt[2][l.e] * cc;
         }
       }
@@ -365,7 +389,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
       if constexpr (M == GATHER_NOW) {
         *dst = fetch(l);
       } else if constexpr (M == GATHER_ISSUE) {
-        if (!blended(l)) cp_async_elem(dst, l.p);
+        if (!blended(l)) cp_async_elem(dst, src(l.p));
       } else {
         if (blended(l)) *dst = fetch(l);
       }
@@ -400,24 +424,24 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         if (i >= tx || j >= ty) continue;
         const long long id = ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i);
 #pragma unroll
-        for (int k = 0; k < 5; k++) cp_async_elem(OLD + L::OLDU + k * TX * TY + ci, own + k * nc + id);
+        for (int k = 0; k < 5; k++) cp_async_elem(OLD + L::OLDU + k * TX * TY + ci, src(own + k * nc + id));
       }
       for (int ci = tid; ci < (TX + 1) * TY; ci += NT) {
         const int i = ci % (TX + 1), j = ci / (TX + 1);
         if (i > tx || j >= ty) continue;
-        cp_async_elem(OLD + L::OLDX + ci, own + ofx + ((long long)(p - 1) * ny + (y0 + j)) * (nx + 1) + (x0 + i));
+        cp_async_elem(OLD + L::OLDX + ci, src(own + ofx + ((long long)(p - 1) * ny + (y0 + j)) * (nx + 1) + (x0 + i)));
       }
       for (int ci = tid; ci < TX * (TY + 1); ci += NT) {
         const int i = ci % TX, j = ci / TX;
         if (i >= tx || j > ty) continue;
-        cp_async_elem(OLD + L::OLDY + ci, own + ofy + ((long long)(p - 1) * (ny + 1) + (y0 + j)) * nx + (x0 + i));
+        cp_async_elem(OLD + L::OLDY + ci, src(own + ofy + ((long long)(p - 1) * (ny + 1) + (y0 + j)) * nx + (x0 + i)));
       }
     }
     if (it >= 1) {
       for (int ci = tid; ci < TX * TY; ci += NT) {
         const int i = ci % TX, j = ci / TX;
         if (i >= tx || j >= ty) continue;
-        cp_async_elem(OLD + L::OLDZ + ci, own + ofz + ((long long)p * ny + (y0 + j)) * nx + (x0 + i));
+        cp_async_elem(OLD + L::OLDZ + ci, src(own + ofz + ((long long)p * ny + (y0 + j)) * nx + (x0 + i)));
       }
     }
     cp_async_commit();
@@ -861,7 +885,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     const int ui = tid % TX, uj = tid / TX;
     const bool mine = tid < TX * TY && ui < tx && uj < ty;
     if (ASYNC) cp_async_wait<1>();  // this thread's old values (not plane p+2's copies)
-    auto old_u = [&](int k, long long ci) -> T { return !ASYNC ? own[k * nc + ci] : OLD[L::OLDU + k * TX * TY + tid]; };
+    auto old_u = [&](int k, long long ci) -> T { return !ASYNC ? *src(own + k * nc + ci) : OLD[L::OLDU + k * TX * TY + tid]; };
     if (upd && mine) {
       const int i = ui, j = uj, h = H1(i, j);
       const long long ci = ((long long)(p - 1) * ny + (y0 + j)) * nx + (x0 + i);
@@ -869,7 +893,7 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
       for (int k = 0; k < 5; k++) {
         const T fz = FZc[k * H1N + h] - FZp[k * H1N + h];
         unew[k] = old_u(k, ci) - dtdx * (DUp[k * H1N + h] + fz);
-        dst[k * nc + ci] = unew[k];
+        put_global(dst + k * nc + ci, unew[k]);
       }
     }
     if (upd) {
@@ -878,17 +902,17 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const int i = ci % (TX + 1), j = ci / (TX + 1), h = H1(i, j);
         if (i > tx || j >= ty) continue;
         const long long id = ((long long)k * ny + (y0 + j)) * (nx + 1) + (x0 + i);
-        const T b = (!ASYNC ? own[ofx + id] : OLD[L::OLDX + ci]) - dtdx * ((EZ[H1(i, j + 1)] - EZ[h]) - (EYc[h] - EYp[h]));
+        const T b = (!ASYNC ? *src(own + ofx + id) : OLD[L::OLDX + ci]) - dtdx * ((EZ[H1(i, j + 1)] - EZ[h]) - (EYc[h] - EYp[h]));
         NBX[h] = b;
-        dst[ofx + id] = b;
+        put_global(dst + ofx + id, b);
       }
       for (int ci = tid; ci < TX * (TY + 1); ci += NT) {
         const int i = ci % TX, j = ci / TX, h = H1(i, j);
         if (i >= tx || j > ty) continue;
         const long long id = ((long long)k * (ny + 1) + (y0 + j)) * nx + (x0 + i);
-        const T b = (!ASYNC ? own[ofy + id] : OLD[L::OLDY + ci]) - dtdx * ((EXc[h] - EXp[h]) - (EZ[H1(i + 1, j)] - EZ[h]));
+        const T b = (!ASYNC ? *src(own + ofy + id) : OLD[L::OLDY + ci]) - dtdx * ((EXc[h] - EXp[h]) - (EZ[H1(i + 1, j)] - EZ[h]));
         NBY[h] = b;
-        dst[ofy + id] = b;
+        put_global(dst + ofy + id, b);
       }
     }
     if (it >= 1) {
@@ -896,9 +920,9 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         const int i = ci % TX, j = ci / TX, h = H1(i, j);
         if (i >= tx || j >= ty) continue;
         const long long id = ((long long)p * ny + (y0 + j)) * nx + (x0 + i);
-        const T b = (!ASYNC ? own[ofz + id] : OLD[L::OLDZ + ci]) - dtdx * ((EYc[H1(i + 1, j)] - EYc[h]) - (EXc[H1(i, j + 1)] - EXc[h]));
+        const T b = (!ASYNC ? *src(own + ofz + id) : OLD[L::OLDZ + ci]) - dtdx * ((EYc[H1(i + 1, j)] - EYc[h]) - (EXc[H1(i, j + 1)] - EXc[h]));
         NBZc[h] = b;
-        dst[ofz + id] = b;
+        put_global(dst + ofz + id, b);
       }
     }
     __syncthreads();
@@ -1025,26 +1049,28 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
 #undef F5
 }
 
-// Sweep dispatcher: every (ready patch, tile) work item of the current ready
-// list, grid-strided over a persistent grid.
+// Sweep dispatcher: every (ready patch, tile) work item of size classes
+// [cls, cls_end) in the current work list (grouped by class), grid-strided
+// over a persistent grid.
 // VARIANT only tells apart instantiations compiled with different
 // floating-point contraction flags (FP64 with and without FMA); RS is the
 // Riemann solver of the face fluxes (0 HLL, 1 HLLD).
 template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS, int NI>
-__global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c) {
+__global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c, int cls, int cls_end) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ TileShared<T, NT> S;
-  const int nr = c.ctl[CTL_NREADY];
-  const int nwork = c.work_off[nr];
-  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+  const int rb = c.ctl[CTL_CLS + cls], re = c.ctl[CTL_CLS + cls_end];
+  const int wb = c.work_off[rb], we = c.work_off[re];
+  for (int w = wb + blockIdx.x; w < we; w += gridDim.x) {
     // ready patch r owns work items [work_off[r], work_off[r+1])
-    int lo = 0, hi = nr - 1;
+    int lo = rb, hi = re - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (c.work_off[mid] <= w) lo = mid;
       else hi = mid - 1;
     }
-    process_tile<T, TX, TY, NT, false, RS, NI>(c, c.R[lo], c.dtR[lo], w - c.work_off[lo], reinterpret_cast<T *>(smraw),
+    const int r = c.Rk[lo];
+    process_tile<T, TX, TY, NT, false, RS, NI>(c, c.R[r], c.dtR[r], w - c.work_off[lo], reinterpret_cast<T *>(smraw),
                                                S);
   }
 }
@@ -1100,9 +1126,9 @@ static __device__ void try_queue(const DevCtx &c, int Q, double t_end) {
 }
 
 // The last tile of P is done: publish P's new slice (time, signal speed,
-// schedule entry, newest index with release), then queue P and every
-// neighbour that became ready.
-static __device__ void publish_and_queue(const DevCtx &c, int P, double dt, double t_end) {
+// schedule entry, newest index with release).  One thread; the block then
+// tests P and its neighbours for readiness, one patch per thread.
+static __device__ void publish_patch(const DevCtx &c, int P, double dt, double t_end) {
   const int ns = c.ns;
   const int L = ld_acquire(c.latest + P), Ln = (L + 1) % ns;
   const double t = __ldcg(c.t_slot + (long long)P * ns + L);
@@ -1125,8 +1151,6 @@ static __device__ void publish_and_queue(const DevCtx &c, int P, double dt, doub
   if (!(tn < t_end)) atomicAdd(&c.q_ctl[2], 1ull);
   st_release(&c.p_state[P], 0);
   __threadfence();
-  try_queue(c, P, t_end);
-  for (int k = c.nbl_off[P]; k < c.nbl_off[P + 1]; k++) try_queue(c, c.nbl[k], t_end);
 }
 
 // Persistent ready-queue dispatcher (one block per resident slot): claim the
@@ -1136,7 +1160,7 @@ template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS, int
 __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ TileShared<T, NT> S;
-  __shared__ int s_P, s_tile, s_exit;
+  __shared__ int s_P, s_tile, s_exit, s_last;
   __shared__ double s_dt;
   const int tid = threadIdx.x;
   const unsigned long long C = 2ull * (unsigned long long)c.np;
@@ -1178,21 +1202,30 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
     if (tid == 0) {
       __threadfence();
       const int k = atomicAdd(&c.tiles_done[P], 1);
-      if (k == c.uniform_tiles - 1) {
+      s_last = k == c.uniform_tiles - 1;
+      if (s_last) {
         __threadfence();
         c.tiles_done[P] = 0;
-        publish_and_queue(c, P, dt, t_end);
+        publish_patch(c, P, dt, t_end);
       }
+    }
+    __syncthreads();
+    if (s_last) {
+      // P and each neighbour tested (and queued if it became ready) by its
+      // own thread: the tests are independent (the queue claim is a CAS), and
+      // one thread doing all of them in turn took longer than the update
+      const int nb0 = c.nbl_off[P], nnb = c.nbl_off[P + 1] - nb0;
+      for (int i = tid; i <= nnb; i += NT) try_queue(c, i == 0 ? P : c.nbl[nb0 + i - 1], t_end);
     }
     __syncthreads();
   }
 }
 template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS, int NI>
-int launch_update(const DevCtx &c, int grid, void *stream) {
+int launch_update(const DevCtx &c, int grid, void *stream, int cls, int cls_end) {
   // the shared-memory attribute was set by update_grid when the context was
   // created (a launch may be inside a stream capture)
   const size_t smem = sizeof(T) * (size_t)Lay<TX, TY, NI>::total;
-  update_kernel<T, TX, TY, NT, MINB, VARIANT, RS, NI><<<grid, NT, smem, (cudaStream_t)stream>>>(c);
+  update_kernel<T, TX, TY, NT, MINB, VARIANT, RS, NI><<<grid, NT, smem, (cudaStream_t)stream>>>(c, cls, cls_end);
   return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;
 }
 
@@ -1219,7 +1252,7 @@ int launch_queue(const DevCtx &c, int grid, double t_end, void *stream) {
 }
 
 template <typename T, int TX, int TY, int NT, int MINB, int VARIANT, int RS, int NI>
-int update_grid(const DevCtx &c) {
+int update_grid(const DevCtx &c, int cls, int cls_end) {
   const size_t smem = sizeof(T) * (size_t)Lay<TX, TY, NI>::total;
   cudaFuncSetAttribute(update_kernel<T, TX, TY, NT, MINB, VARIANT, RS, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, nsm = 0, per = 0;
@@ -1227,7 +1260,8 @@ int update_grid(const DevCtx &c) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, update_kernel<T, TX, TY, NT, MINB, VARIANT, RS, NI>, NT, smem);
   if (per < 1) per = 1;
-  const long long maxwork = c.total_tiles;  // every patch ready
+  long long maxwork = 0;  // every patch of the classes ready
+  for (int k = cls; k < cls_end; k++) maxwork += c.cls_tiles[k];
   long long g = (long long)nsm * per;
   return (int)(g < maxwork ? g : maxwork);
 }

@@ -15,11 +15,15 @@
 
 namespace dsp {
 namespace {
-int lu(const DevCtx &c, int grid, void *s) { return launch_update<V_T, V_TX, V_TY, V_NT, V_MB, V_ID, V_RS, V_NI>(c, grid, s); }
+int lu(const DevCtx &c, int grid, void *s, int cls, int cls_end) {
+  return launch_update<V_T, V_TX, V_TY, V_NT, V_MB, V_ID, V_RS, V_NI>(c, grid, s, cls, cls_end);
+}
 int lq(const DevCtx &c, int grid, double t, void *s) {
   return launch_queue<V_T, V_TX, V_TY, V_NT, V_MB, V_ID, V_RS, V_NI>(c, grid, t, s);
 }
-int gr(const DevCtx &c) { return update_grid<V_T, V_TX, V_TY, V_NT, V_MB, V_ID, V_RS, V_NI>(c); }
+int gr(const DevCtx &c, int cls, int cls_end) {
+  return update_grid<V_T, V_TX, V_TY, V_NT, V_MB, V_ID, V_RS, V_NI>(c, cls, cls_end);
+}
 const KernelVariant kv = {V_ID, V_PREC, V_RS, V_NI, V_TX, V_TY, V_NT,
                           DSP_STR(V_T) " " DSP_STR(V_TX) "x" DSP_STR(V_TY) " " DSP_STR(V_NT) "t", lu, lq, gr};
 }  // namespace

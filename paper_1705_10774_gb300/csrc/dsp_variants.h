@@ -8,10 +8,11 @@
 // hold a third plane of faces, so the FP64 rows use a smaller tile).  All
 // variants of one precision, solver and physics compute bit-identical
 // results; they differ only in how the work is spread over threads, so
-// dsp_autotune may pick any of them.
+// dsp_autotune may pick any of them.  The bounds-checked build
+// (DSP_BOUNDS_CHECK) compiles the three rows of DSP_VARIANT_LIST_CHECKED only.
 #pragma once
 
-#define DSP_VARIANT_LIST(X)            \
+#define DSP_VARIANT_LIST_ALL(X)        \
   X(0, double, 16, 8, 256, 1, 0, 0, 0)    \
   X(1, double, 16, 8, 384, 1, 0, 0, 0)    \
   X(2, double, 16, 8, 256, 1, 2, 0, 0)    \
@@ -32,4 +33,16 @@
   X(17, double, 16, 4, 256, 1, 0, 0, 1) \
   X(18, double, 16, 4, 256, 1, 0, 1, 1) \
   X(19, double, 16, 4, 256, 1, 2, 1, 1) \
-  X(20, float, 16, 8, 256, 1, 1, 1, 1)
+  X(20, float, 16, 8, 256, 1, 1, 1, 1)   \
+  X(21, float, 24, 8, 256, 1, 1, 0, 0)
+
+#define DSP_VARIANT_LIST_CHECKED(X)    \
+  X(0, double, 16, 8, 256, 1, 0, 0, 0)    \
+  X(2, double, 16, 8, 256, 1, 2, 0, 0)    \
+  X(5, float, 16, 8, 256, 2, 1, 0, 0)
+
+#ifdef DSP_BOUNDS_CHECK
+#define DSP_VARIANT_LIST(X) DSP_VARIANT_LIST_CHECKED(X)
+#else
+#define DSP_VARIANT_LIST(X) DSP_VARIANT_LIST_ALL(X)
+#endif

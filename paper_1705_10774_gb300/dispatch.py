@@ -25,12 +25,14 @@ DSP_ERR_DEADLOCK = -6
 DSP_ERR_SCHEDULE_OVERFLOW = -7
 DSP_ERR_UNSUPPORTED = -8
 DSP_ERR_BRACKET = -9
+DSP_ERR_BOUNDS = -10
 
 ERRORS = {v: k for k, v in globals().items() if k.startswith("DSP_ERR_")}
 
 EXPORTS = ["dsp_create", "dsp_set_state", "dsp_advance", "dsp_get_state", "dsp_get_times",
            "dsp_get_schedule", "dsp_diagnostics", "dsp_save", "dsp_load", "dsp_last_error",
-           "dsp_destroy", "dsp_diagnostics_noalloc", "dsp_autotune", "dsp_package_len", "dsp_pack", "dsp_unpack"]
+           "dsp_destroy", "dsp_diagnostics_noalloc", "dsp_autotune", "dsp_package_len", "dsp_pack", "dsp_unpack",
+           "dsp_get_tuning"]
 
 DSP_NOALLOC_MAX_PATCHES = 16384
 
@@ -72,25 +74,27 @@ class dsp_diag(ctypes.Structure):
 
 
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 VP = ctypes.c_void_p
 
 
-def lib_path() -> str:
-    return _build.LIB
+def lib_path(checked: bool = False) -> str:
+    return _build.LIB_CHECKED if checked else _build.LIB
 
 
-def load(build_if_missing: bool = True):
-    """Load the CUDA library (building it in-tree with nvcc if needed)."""
-    global _lib
+def load(build_if_missing: bool = True, checked: bool = False):
+    """Load the CUDA library (building it in-tree with nvcc if needed); with
+    checked=True the bounds-checked build (every global address of the
+    update kernel tested, DSP_ERR_BOUNDS instead of a fault; three
+    variants)."""
     with _lock:
-        if _lib is not None:
-            return _lib
-        path = _build.LIB
-        if build_if_missing and not _build.up_to_date():
-            _build.build()
+        if checked in _libs:
+            return _libs[checked]
+        path = lib_path(checked)
+        if build_if_missing and not _build.up_to_date(checked):
+            _build.build(checked=checked)
         if not os.path.exists(path):
-            raise RuntimeError("libdispatch_gpu.so is not built (%s); run paper_1705_10774_gb300.build" % path)
+            raise RuntimeError("%s is not built; run paper_1705_10774_gb300.build" % path)
         L = ctypes.CDLL(path)
         L.dsp_create.argtypes = [ctypes.POINTER(dsp_patch_desc), ctypes.c_int32, ctypes.POINTER(dsp_params), VP,
                                  ctypes.POINTER(VP)]
@@ -111,13 +115,14 @@ def load(build_if_missing: bool = True):
         L.dsp_diagnostics_noalloc.argtypes = [VP, VP, VP, VP, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.POINTER(ctypes.c_int32), ctypes.c_double, VP,
                                               ctypes.POINTER(dsp_diag)]
+        L.dsp_get_tuning.argtypes = [VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), VP, VP, VP]
         L.dsp_package_len.argtypes = [VP, VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
         L.dsp_pack.argtypes = [VP, VP, ctypes.c_int32, VP, VP, ctypes.c_int32]
         L.dsp_unpack.argtypes = [VP, VP, ctypes.c_int32, VP, VP, ctypes.c_int32]
         for name in EXPORTS:
             if name not in ("dsp_last_error", "dsp_destroy"):
                 getattr(L, name).restype = ctypes.c_int
-        _lib = L
+        _libs[checked] = L
         return L
 
 
@@ -143,8 +148,9 @@ class Dispatch:
                  nguard=3, nslices=3, precision=0, time_mode=0, dispatcher=1, tile_z=0,
                  sched_capacity=0, timing=0, wait_budget=0, graph=0, variant=-1, stream=None, level=None,
                  riemann=0, eta=0.0, gamma_ad=0.0, rho_i=1.0, c_ohm=0.1, c_ad=0.1, grace=0.0, time_order=1,
-                 owned=None):
-        L = load()
+                 owned=None, checked=False):
+        L = load(checked=checked)
+        self._L = L
         n = np.asarray(n, dtype=np.int64).reshape(-1, 3)
         lo = np.asarray(lo, dtype=np.int64).reshape(-1, 3)
         self.np = n.shape[0]
@@ -197,12 +203,12 @@ class Dispatch:
 
     def _check(self, rc):
         if rc != 0 and rc != DSP_ERR_SCHEDULE_OVERFLOW:
-            raise DispatchError(rc, load().dsp_last_error(self._h).decode())
+            raise DispatchError(rc, self._L.dsp_last_error(self._h).decode())
         return rc
 
     def close(self):
         if getattr(self, "_h", None):
-            load().dsp_destroy(self._h)
+            self._L.dsp_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -216,7 +222,7 @@ class Dispatch:
         ptrs = [_addr(a) for a in (U, bx, by, bz)]
         dev, dt = ptrs[0][1], ptrs[0][2]
         assert all(p[1] == dev and p[2] == dt for p in ptrs)
-        self._check(load().dsp_set_state(self._h, first, count, *[p[0] for p in ptrs], dt, int(dev)))
+        self._check(self._L.dsp_set_state(self._h, first, count, *[p[0] for p in ptrs], dt, int(dev)))
 
     def get_state(self, out=None, dtype=np.float64, first=0, count=None):
         count = self.np - first if count is None else count
@@ -224,26 +230,26 @@ class Dispatch:
             sz = self.per_patch[first:first + count].sum(axis=0)
             out = [np.empty(int(s), dtype=dtype) for s in sz]
         ptrs = [_addr(a) for a in out]
-        self._check(load().dsp_get_state(self._h, first, count, *[p[0] for p in ptrs], ptrs[0][2], int(ptrs[0][1])))
+        self._check(self._L.dsp_get_state(self._h, first, count, *[p[0] for p in ptrs], ptrs[0][2], int(ptrs[0][1])))
         return out
 
     def advance(self, t_end=float("inf"), max_sweeps=0):
         st = dsp_stats()
-        self._check(load().dsp_advance(self._h, t_end, max_sweeps, ctypes.byref(st)))
+        self._check(self._L.dsp_advance(self._h, t_end, max_sweeps, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in dsp_stats._fields_}
 
     def times(self):
         t = np.empty(self.np)
         dt = np.empty(self.np)
-        self._check(load().dsp_get_times(self._h, t.ctypes.data_as(VP), dt.ctypes.data_as(VP)))
+        self._check(self._L.dsp_get_times(self._h, t.ctypes.data_as(VP), dt.ctypes.data_as(VP)))
         return t, dt
 
     def schedule(self):
         n = ctypes.c_int64()
-        load().dsp_get_schedule(self._h, None, 0, ctypes.byref(n))
+        self._L.dsp_get_schedule(self._h, None, 0, ctypes.byref(n))
         cap = n.value
         buf = (dsp_sched_entry * max(cap, 1))()
-        rc = self._check(load().dsp_get_schedule(self._h, buf, cap, ctypes.byref(n)))
+        rc = self._check(self._L.dsp_get_schedule(self._h, buf, cap, ctypes.byref(n)))
         k = min(cap, n.value)
         a = np.frombuffer(buf, dtype=np.dtype([("patch", np.int64), ("t", np.float64), ("dt", np.float64)]),
                           count=k).copy() if k else np.zeros(0, dtype=[("patch", np.int64), ("t", np.float64), ("dt", np.float64)])
@@ -253,44 +259,65 @@ class Dispatch:
 
     def diagnostics(self):
         d = dsp_diag()
-        self._check(load().dsp_diagnostics(self._h, ctypes.byref(d)))
+        self._check(self._L.dsp_diagnostics(self._h, ctypes.byref(d)))
         return dict(mass=d.mass, mom=np.array(d.mom[:]), energy=d.energy, bmean=np.array(d.bmean[:]),
                     max_divb=d.max_divb, max_b=d.max_b)
 
     def autotune(self, reps=3):
-        """dsp_autotune: returns (chosen variant id, {variant id: ms per launch})."""
+        """dsp_autotune: returns (variant chosen for size class 0,
+        {variant id: ms per launch} of class 0's whole-height candidates);
+        tuning() and self.tuning_log give every class's choice and
+        candidates."""
         chosen = ctypes.c_int32()
         n = ctypes.c_int32()
-        ms = np.zeros(32)
-        ids = np.zeros(32, np.int32)
-        self._check(load().dsp_autotune(self._h, reps, ctypes.byref(chosen), ms.ctypes.data_as(VP),
-                                        ids.ctypes.data_as(VP), 32, ctypes.byref(n)))
-        k = min(n.value, 32)
-        return chosen.value, {int(i): float(m) for i, m in zip(ids[:k], ms[:k])}
+        cap = 256
+        ms = np.zeros(cap)
+        ids = np.zeros(cap, np.int32)
+        self._check(self._L.dsp_autotune(self._h, reps, ctypes.byref(chosen), ms.ctypes.data_as(VP),
+                                        ids.ctypes.data_as(VP), cap, ctypes.byref(n)))
+        k = min(n.value, cap)
+        self.tuning_log = [dict(cls=int(i) // 1000000, tile_z=(int(i) // 1000) % 1000, variant=int(i) % 1000,
+                                ms=float(m)) for i, m in zip(ids[:k], ms[:k])]
+        first = {}
+        for e in self.tuning_log:
+            if e["cls"] == 0:
+                first.setdefault(e["variant"], e["ms"])
+        return chosen.value, first
+
+    def tuning(self):
+        """dsp_get_tuning: [{size, variant, tile_z}] per size class."""
+        nc = ctypes.c_int32()
+        sizes = np.zeros(12, np.int32)
+        var = np.zeros(4, np.int32)
+        tz = np.zeros(4, np.int32)
+        self._check(self._L.dsp_get_tuning(self._h, 4, ctypes.byref(nc), sizes.ctypes.data_as(VP),
+                                          var.ctypes.data_as(VP), tz.ctypes.data_as(VP)))
+        return [dict(size=sizes[3 * k:3 * k + 3].tolist(), variant=int(var[k]), tile_z=int(tz[k]))
+                for k in range(min(nc.value, 4))]
 
     def save(self) -> bytes:
         used = ctypes.c_size_t()
-        self._check(load().dsp_save(self._h, None, 0, ctypes.byref(used)))
+        self._check(self._L.dsp_save(self._h, None, 0, ctypes.byref(used)))
         buf = ctypes.create_string_buffer(used.value)
-        self._check(load().dsp_save(self._h, buf, used.value, ctypes.byref(used)))
+        self._check(self._L.dsp_save(self._h, buf, used.value, ctypes.byref(used)))
         return buf.raw
 
     def save_array(self) -> np.ndarray:
         """dsp_save into a numpy byte array (no second copy of a large state)."""
         used = ctypes.c_size_t()
-        self._check(load().dsp_save(self._h, None, 0, ctypes.byref(used)))
+        self._check(self._L.dsp_save(self._h, None, 0, ctypes.byref(used)))
         buf = np.empty(used.value, np.uint8)
-        self._check(load().dsp_save(self._h, buf.ctypes.data_as(ctypes.c_void_p), used.value, ctypes.byref(used)))
+        self._check(self._L.dsp_save(self._h, buf.ctypes.data_as(ctypes.c_void_p), used.value, ctypes.byref(used)))
         return buf
 
     def load_state(self, blob: bytes):
-        self._check(load().dsp_load(self._h, blob, len(blob)))
+        self._check(self._L.dsp_load(self._h, blob, len(blob)))
 
     # ---- packages between processes (Sec. 3 C)
     def package_len(self, ids):
         ids = np.ascontiguousarray(ids, dtype=np.int32)
         n = ctypes.c_int64()
-        self._check(load().dsp_package_len(self._h, ids.ctypes.data_as(VP), ids.size, ctypes.byref(n)))
+        self._check(self._L.dsp_package_len(self._h, ids.ctypes.data_as(VP), ids.size, ctypes.byref(n)))
         return n.value
 
     def pack(self, ids, device=True):
@@ -303,12 +330,12 @@ class Dispatch:
             dt = torch.float32 if self.precision == 1 else torch.float64
             buf = torch.empty(max(n, 1), dtype=dt, device="cuda")
             meta = torch.empty((max(ids.size, 1), 3), dtype=torch.float64, device="cuda")
-            self._check(load().dsp_pack(self._h, ids.ctypes.data_as(VP), ids.size, VP(buf.data_ptr()),
+            self._check(self._L.dsp_pack(self._h, ids.ctypes.data_as(VP), ids.size, VP(buf.data_ptr()),
                                         VP(meta.data_ptr()), 1))
             return buf[:n], meta[:ids.size]
         buf = np.empty(max(n, 1), np.float32 if self.precision == 1 else np.float64)
         meta = np.empty((max(ids.size, 1), 3))
-        self._check(load().dsp_pack(self._h, ids.ctypes.data_as(VP), ids.size, buf.ctypes.data_as(VP),
+        self._check(self._L.dsp_pack(self._h, ids.ctypes.data_as(VP), ids.size, buf.ctypes.data_as(VP),
                                     meta.ctypes.data_as(VP), 0))
         return buf[:n], meta[:ids.size]
 
@@ -324,7 +351,7 @@ class Dispatch:
         b, bdev, _ = _addr(buf)
         m, mdev, _ = _addr(meta)
         assert bdev == mdev
-        self._check(load().dsp_unpack(self._h, ids.ctypes.data_as(VP), ids.size, b, m, int(bdev)))
+        self._check(self._L.dsp_unpack(self._h, ids.ctypes.data_as(VP), ids.size, b, m, int(bdev)))
 
 
 def _check_noalloc_arrays(arrays, npatch, n):

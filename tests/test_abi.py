@@ -161,3 +161,13 @@ def test_noalloc_binding_refuses_arrays_it_cannot_vouch_for():
         D.diagnostics_noalloc(*cpu, npatch=npatch, n=n, dx=0.1)
     with pytest.raises(ValueError, match="every n"):
         D.diagnostics_noalloc(*cpu, npatch=npatch, n=(0, 3, 4), dx=0.1)
+
+
+def test_bounds_checked_library_exports_every_declared_symbol():
+    """The bounds-checked build (-DDSP_BOUNDS_CHECK, three variants) links and
+    exports the same calls."""
+    path = B.build(checked=True)
+    lib = ctypes.CDLL(path)
+    for name in declared():
+        assert hasattr(lib, name), name
+    assert [v[0] for v in B.variants(checked=True)] == [0, 2, 5]

@@ -432,3 +432,47 @@ def test_pressure_floor_count_matches_oracle(precision):
         st = g.advance(t_end=0.003)
         o.advance(t_end=0.003)
         assert st["floors"] == o.stats()["floors"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_per_size_class_tuning_changes_nothing(precision):
+    """Patches of 8^3, 16^3 and 32^3 (three size classes) and of 24^3 next to
+    32^3: the autotuner picks a variant and a z run per size class and every
+    sweep launches each class's kernel over its part of the work list; the
+    states equal an untuned context's bit for bit (and the oracle's in FP64),
+    schedules equal, also replayed from CUDA graphs."""
+    cases = [_mixed_case(seed=6)]
+    lay24 = ics.mixed_blocks(1, 96, sizes=(24, 16), probs=(1, 0), seed=2, remainder=32, rem_size=32)
+    X, Y, Z = lay24.base_cells
+    rng = np.random.default_rng(2)
+    v = ics.solenoidal_velocity((Z, Y, X), lay24.box_len, 1.0, 3.0, 1.0, rng)
+    cases.append((lay24, ics.Fields(rho=np.ones((Z, Y, X)), v=v, p=np.full((Z, Y, X), 0.6),
+                                    bx=np.full((Z, Y, X), 0.7), by=np.zeros((Z, Y, X)), bz=np.zeros((Z, Y, X)),
+                                    gamma=5.0 / 3.0)))
+    for lay, f in cases:
+        sizes = sorted({tuple(int(x) for x in n) for n in lay.n})
+        assert len(sizes) >= 2
+        state = ics.to_patches(lay, f)
+        outs = []
+        for tuned in (False, True):
+            g = Dispatch(lay.n, lay.lo, **kw_of(lay, f, time_mode=1), precision=precision, graph=1,
+                         sched_capacity=1 << 20)
+            g.set_state(*state)
+            if tuned:
+                g.autotune(reps=1)
+                tun = g.tuning()
+                assert [tuple(t["size"]) for t in tun] == sizes
+                assert {e["cls"] for e in g.tuning_log} == set(range(len(sizes)))
+            g.advance(t_end=0.002)
+            outs.append((g.get_state(), g.schedule()))
+            g.close()
+        for a, b in zip(outs[0][0], outs[1][0]):
+            assert np.array_equal(a, b)
+        key = lambda s: sorted(zip(*(x.tolist() for x in s)))
+        assert key(outs[0][1]) == key(outs[1][1])
+        if precision == 0:
+            o = Oracle(lay.n, lay.lo, **kw_of(lay, f, time_mode=1))
+            o.set_state(*state)
+            o.advance(t_end=0.002)
+            for a, b in zip(outs[1][0], o.get_state()):
+                assert np.array_equal(a, b)
