@@ -71,12 +71,15 @@ __device__ __forceinline__ T tmin_nonneg(T a, T b) {
 }
 // Evaluation order of the update's arithmetic.  kFast = false: the FP64
 // oracle's order, operation for operation (the FMA-free FP64 build).  kFast =
-// true (the FP64 build with fused multiply-adds and the FP32 build, which are
-// held to a tolerance, not to bit equality): FP64 comparisons, minima and
-// maxima as integer operations on the bit patterns (the FP64 pipe is the
-// FP64 kernel's bottleneck; the integer units are idle), and one division
-// per edge EMF instead of three.  Each translation unit of an update-kernel
-// variant defines DSP_FAST_ORDER from its precision.
+// true in the builds held to a tolerance rather than bit equality; every
+// kFast form below applies to FP64 only (the FP64 build with fused
+// multiply-adds), where the FP64 pipe is the kernel's bottleneck and the
+// integer units are idle: FP64 comparisons, minima, maxima and power-of-two
+// scalings as integer operations on the bit patterns, one division per edge
+// EMF instead of three, reciprocals and square roots by Newton steps from the
+// hardware approximations.  The FP32 build keeps the plain forms.  Each
+// translation unit of an update-kernel variant defines DSP_FAST_ORDER from
+// its precision.
 #ifndef DSP_FAST_ORDER
 #define DSP_FAST_ORDER 0
 #endif
@@ -182,8 +185,8 @@ __device__ __forceinline__ T sqrt_k(T x) {
 template <typename T>
 __device__ __forceinline__ void prim(T rho, T mx, T my, T mz, T E, T bxl, T bxr, T byl, T byr, T bzl, T bzr,
                                      T gamma, T W[8], int *floored = nullptr) {
-  const T h = T(0.5);
   T irho = rcp_k(rho);
+  const T h = T(0.5);
   T Bx = h * (bxl + bxr);
   T By = h * (byl + byr);
   T Bz = h * (bzl + bzr);
@@ -503,9 +506,10 @@ __device__ __forceinline__ T emf(T Ell, T Erl, T Elr, T Err, T Ba_ll, T Ba_rl, T
   T BaL = h * (Ba_ll + Ba_rl);
   T BaR = h * (Ba_lr + Ba_rr);
   T num = apa * apb * Ell + ama * apb * Erl + apa * amb * Elr + ama * amb * Err;
-  if constexpr (kFast) {
+  if constexpr (kFast && sizeof(T) == 8) {
     // one reciprocal of the product of the two weight sums serves all three
-    // quotients
+    // quotients (FP64: a division costs about five FP64-pipe slots; the FP32
+    // build divides approximately, at the cost of a multiply)
     const T sa = apa + ama, sb = apb + amb;
     const T r = rcp_k(sa * sb);
     return num * r + (apa * ama * sb * r) * (BbR - BbL) - (apb * amb * sa * r) * (BaR - BaL);
