@@ -62,7 +62,8 @@ NONIDEAL = dict(eta=1e-4, gamma_ad=75.0, rho_i=1.0)
 # of one launch divided by the cells it updated (captures of smaller cases
 # of the same kernel: traffic grows in proportion to the cells); a variant
 # without an entry reports null.
-TRAFFIC_PER_CELL = {}
+TRAFFIC_PER_CELL = {2: (549.619712e6 + 421.812224e6) / 7077888, 5: (236.742656e6 + 193.273600e6) / 7077888,
+                    10: (534.644224e6 + 421.614336e6) / 7077888, 15: (527.814400e6 + 424.025088e6) / 7077888}
 
 
 def guard_fraction(n, g):
