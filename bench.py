@@ -718,7 +718,8 @@ def mixed_arm(args):
     del f, v
     stream = torch.cuda.current_stream()
     g = Dispatch(lay.n, lay.lo, gamma=5.0 / 3.0, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len,
-                 precision=1, time_mode=1, graph=1, timing=1, stream=stream.cuda_stream)
+                 precision=1, time_mode=1, graph=1, timing=1, stream=stream.cuda_stream,
+                 dispatcher=args.dispatcher)
     g.set_state(*state)
     if not args.no_tune:
         g.autotune(reps=2)                    # a variant and z run per patch size
@@ -735,6 +736,7 @@ def mixed_arm(args):
     ms = e0.elapsed_time(e1)
     sizes, counts = np.unique(lay.n[:, 0], return_counts=True)
     print(json.dumps({"workload": "mixed 16/24/32 patches, %d^3, %d patches" % (X, lay.npatch),
+                      "dispatcher": "ready queue" if args.dispatcher == 0 else "sweeps from CUDA graphs",
                       "patch_sizes": dict(zip(map(int, sizes), map(int, counts))), "t_end": args.t_end,
                       "ms": ms, "cell_updates": st["cell_updates"], "sweeps": st["sweeps"],
                       "cell_updates_per_s": st["cell_updates"] / (ms * 1e-3), "tuning": g.tuning(),
@@ -819,6 +821,8 @@ def main():
     ap.add_argument("--t-end", type=float, default=0.01, help="end time of the lts / orszag-tang / mixed runs")
     ap.add_argument("--blocks", type=int, default=5, help="96^3 super-blocks per axis of the mixed run")
     ap.add_argument("--no-tune", action="store_true", help="mixed / amr runs: keep the default variant")
+    ap.add_argument("--dispatcher", type=int, default=1, choices=[0, 1],
+                    help="mixed run: 1 sweeps replayed from CUDA graphs, 0 the persistent ready queue")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -60,9 +60,9 @@ struct dsp_ctx {
   unsigned long long *smax_new;
   long long *cnt;
   dsp_sched_entry *sched;
-  int *q_patch, *q_reads, *p_state, *tiles_done;
+  int *q_patch, *p_state, *tiles_done;
   double *q_dt;
-  unsigned long long *q_seq, *q_free, *q_ctl;
+  unsigned long long *q_seq, *q_free, *q_ctl, *q_claim;
   void *staging;
   size_t staging_bytes;
   int *h_ctl;  // pinned
@@ -439,7 +439,7 @@ __global__ void queue_init_kernel(DevCtx c, double t_end) {
   for (int s = threadIdx.x; s < C; s += blockDim.x) {
     c.q_free[s] = (unsigned long long)s;
     c.q_seq[s] = ~0ull;
-    c.q_reads[s] = 0;
+    c.q_claim[s] = ~0ull;
   }
   for (int P = threadIdx.x; P < c.np; P += blockDim.x) {
     c.p_state[P] = 0;
@@ -449,6 +449,7 @@ __global__ void queue_init_kernel(DevCtx c, double t_end) {
   for (int r = threadIdx.x; r < nr; r += blockDim.x) {
     c.q_patch[r] = c.R[r];
     c.q_dt[r] = c.dtR[r];
+    c.q_claim[r] = (unsigned long long)r << 24;
     c.q_seq[r] = (unsigned long long)r;
     c.p_state[c.R[r]] = 1;
   }
@@ -691,7 +692,7 @@ void free_all(dsp_ctx *c) {
                   c->omap_d[1], c->gmap0_d, c->gofs_d, c->gbuf, c->rflag, c->rdt,
                   c->work_off_d, c->geo_d, c->coff_d,
                   c->nbl_off_d, c->nbl_d, c->R,       c->ctl,     c->smax_new, c->cnt,    c->sched,
-                  c->staging, c->q_patch, c->q_reads, c->p_state, c->tiles_done, c->q_dt, c->q_seq,
+                  c->staging, c->q_patch, c->q_claim, c->p_state, c->tiles_done, c->q_dt, c->q_seq,
                   c->q_free,  c->q_ctl, c->owned_d, c->pk_ids, c->pk_off, c->pk_meta, c->Rk};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -921,8 +922,6 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   int uniform_tiles = 0;
   if (!make_geometry(pvec, cls, txc, tyc, tzc, bsz, geo, off, total_tiles, uniform_tiles, cls_tiles))
     return DSP_ERR_UNSUPPORTED;
-  const bool same_tiles = uniform_tiles > 0;
-  if (prm->dispatcher == 0 && !same_tiles) return DSP_ERR_UNSUPPORTED;  // the ready queue needs equal tile counts
   dsp_ctx *c = new dsp_ctx();
   memset(&c->d, 0, sizeof c->d);
   c->prm = *prm;
@@ -1111,7 +1110,8 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
     const size_t C = 2 * (size_t)npatch;
     ok = alloc((void **)&c->q_patch, sizeof(int) * C) && alloc((void **)&c->q_dt, sizeof(double) * C) &&
          alloc((void **)&c->q_seq, sizeof(unsigned long long) * C) &&
-         alloc((void **)&c->q_free, sizeof(unsigned long long) * C) && alloc((void **)&c->q_reads, sizeof(int) * C) &&
+         alloc((void **)&c->q_free, sizeof(unsigned long long) * C) &&
+         alloc((void **)&c->q_claim, sizeof(unsigned long long) * C) &&
          alloc((void **)&c->q_ctl, sizeof(unsigned long long) * 4) && alloc((void **)&c->p_state, sizeof(int) * npatch) &&
          alloc((void **)&c->tiles_done, sizeof(int) * npatch);
   }
@@ -1154,7 +1154,7 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.q_dt = c->q_dt;
   d.q_seq = c->q_seq;
   d.q_free = c->q_free;
-  d.q_reads = c->q_reads;
+  d.q_claim = c->q_claim;
   d.q_ctl = c->q_ctl;
   d.p_state = c->p_state;
   d.tiles_done = c->tiles_done;
@@ -1565,7 +1565,6 @@ extern "C" int dsp_autotune(dsp_ctx *c, int32_t reps, int32_t *chosen, double *m
         c->var_cls[k] = v;
         c->tz_cls[k] = tz;
         if (!install_tuning(c)) continue;  // tiles do not fit this variant's tables
-        if (c->prm.dispatcher == 0 && c->d.uniform_tiles == 0) continue;
         // plan the next sweep (nothing is published: the ready list is
         // dropped afterwards, and the update kernel only writes the patches'
         // next slot)

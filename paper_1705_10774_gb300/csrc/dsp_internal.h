@@ -115,8 +115,8 @@ struct DevCtx {
   double *q_dt;                    // [2np] its step
   unsigned long long *q_seq;       // [2np] sequence number published in the slot
   unsigned long long *q_free;      // [2np] sequence number the slot may take next
-  int *q_reads;                    // [2np] tiles of the slot's entry claimed so far
-  unsigned long long *q_ctl;       // [4]: 0 next work item, 1 next entry, 2 patches done
+  unsigned long long *q_claim;     // [2np] the slot's entry << 24 | its tiles claimed so far
+  unsigned long long *q_ctl;       // [4]: 0 entry whose tiles are being claimed, 1 next entry, 2 patches done
   int *p_state;                    // [np] 0 idle, 1 queued or being updated
   int *tiles_done;                 // [np]
   long long wait_budget;           // clock64 cycles a wait may spin before DSP_ERR_TIMEOUT

@@ -1078,8 +1078,13 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c, int cls, int
 // ---------------------------------------------------------------- ready queue
 // The ring holds 2*np slots; entry e lives in slot e % (2*np).  A producer
 // may fill slot s with entry e once q_free[s] == e; a consumer may read it
-// once q_seq[s] == e.  Every wait is bounded by c.wait_budget clock cycles,
-// after which the waiter records DSP_ERR_TIMEOUT and the kernel winds down.
+// once q_seq[s] == e.  Entries carry their patch's own tile count: blocks
+// claim the tiles of the head entry (q_ctl[0]) one at a time with a
+// compare-and-swap on q_claim[s] = e << 24 | tiles claimed, whose entry part
+// keeps a late block from claiming in a slot that has moved on; the block
+// taking an entry's last tile advances the head and frees the slot.  Every
+// wait is bounded by c.wait_budget clock cycles, after which the waiter
+// records DSP_ERR_TIMEOUT and the kernel winds down.
 
 static __device__ __forceinline__ void queue_push(const DevCtx &c, int Q, double dt) {
   const unsigned long long C = 2ull * (unsigned long long)c.np;
@@ -1095,6 +1100,7 @@ static __device__ __forceinline__ void queue_push(const DevCtx &c, int Q, double
   }
   c.q_patch[slot] = Q;
   c.q_dt[slot] = dt;
+  c.q_claim[slot] = e << 24;
   st_release(&c.q_seq[slot], e);
 }
 
@@ -1167,11 +1173,8 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
   for (;;) {
     if (tid == 0) {
       s_exit = 0;
-      const unsigned long long w = atomicAdd(&c.q_ctl[0], 1ull);
-      const unsigned long long e = w / (unsigned long long)c.uniform_tiles;
-      const int slot = (int)(e % C);
       const long long t0 = clock64();
-      while (ld_acquire(&c.q_seq[slot]) != e) {
+      for (;;) {
         if (ld_acquire(&c.q_ctl[2]) >= (unsigned long long)c.np || ld_acquire(&c.ctl[CTL_STATUS]) != 0) {
           s_exit = 1;
           break;
@@ -1181,17 +1184,34 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
           s_exit = 1;
           break;
         }
-        __nanosleep(200);
-      }
-      if (!s_exit) {
-        s_P = __ldcg(c.q_patch + slot);
-        s_dt = __ldcg(c.q_dt + slot);
-        s_tile = (int)(w % (unsigned long long)c.uniform_tiles);
-        const int r = atomicAdd(&c.q_reads[slot], 1);
-        if (r == c.uniform_tiles - 1) {
-          c.q_reads[slot] = 0;
+        const unsigned long long e = ld_acquire(&c.q_ctl[0]);
+        const int slot = (int)(e % C);
+        const unsigned long long seq = ld_acquire(&c.q_seq[slot]);
+        if (seq != e) {
+          // not published yet (wait), or the slot has moved past e (the head
+          // read was stale: read it again)
+          if (seq == ~0ull || seq < e) __nanosleep(200);
+          continue;
+        }
+        const int P = __ldcg(c.q_patch + slot);
+        const double dt = __ldcg(c.q_dt + slot);
+        const unsigned long long v = ld_acquire(&c.q_claim[slot]);
+        if ((v >> 24) != e) continue;  // the slot was refilled meanwhile
+        const int T = c.geo[P].tiles;
+        const int got = (int)(v & 0xffffffull);
+        if (got >= T) {  // every tile claimed: help the head along
+          atomicCAS(&c.q_ctl[0], e, e + 1);
+          continue;
+        }
+        if (atomicCAS(&c.q_claim[slot], v, v + 1) != v) continue;
+        if (got == T - 1) {  // the entry's last tile: advance the head, free the slot
+          atomicCAS(&c.q_ctl[0], e, e + 1);
           st_release(&c.q_free[slot], e + C);
         }
+        s_P = P;
+        s_dt = dt;
+        s_tile = got;
+        break;
       }
     }
     __syncthreads();
@@ -1202,7 +1222,7 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
     if (tid == 0) {
       __threadfence();
       const int k = atomicAdd(&c.tiles_done[P], 1);
-      s_last = k == c.uniform_tiles - 1;
+      s_last = k == c.geo[P].tiles - 1;
       if (s_last) {
         __threadfence();
         c.tiles_done[P] = 0;

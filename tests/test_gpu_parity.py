@@ -307,6 +307,33 @@ def test_ready_queue_dispatcher_matches_sweeps_and_oracle(precision):
             assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ready_queue_with_mixed_patch_sizes(precision):
+    """Patches of 8^3, 16^3 and 32^3 in one ready queue: queue entries carry
+    their own tile counts (1 to 16 tiles), claimed tile by tile; the same
+    schedule as the sweeps (as a set) and the oracle, states bit for bit."""
+    lay, f = _mixed_case(seed=8)
+    assert len(np.unique(lay.n[:, 0])) == 3
+    state = ics.to_patches(lay, f)
+    kw = kw_of(lay, f, time_mode=1)
+    q = Dispatch(lay.n, lay.lo, **kw, precision=precision, dispatcher=0, sched_capacity=1 << 20)
+    w = Dispatch(lay.n, lay.lo, **kw, precision=precision, dispatcher=1, sched_capacity=1 << 20)
+    for g in (q, w):
+        g.set_state(*state)
+        g.advance(t_end=0.002)
+    key = lambda s: sorted(zip(*(x.tolist() for x in s)))
+    assert key(q.schedule()) == key(w.schedule())
+    for a, b in zip(q.get_state(), w.get_state()):
+        assert np.array_equal(a, b)
+    if precision == 0:
+        o = Oracle(lay.n, lay.lo, **kw_of(lay, f, time_mode=1))
+        o.set_state(*state)
+        o.advance(t_end=0.002)
+        assert key(q.schedule()) == key(o.schedule())
+        for a, b in zip(q.get_state(), o.get_state()):
+            assert np.array_equal(a, b)
+
+
 def test_ready_queue_wait_budget_ends_in_timeout_not_a_hang():
     """A wait budget of a few hundred cycles is too short for any update to
     finish: the blocks' waits run out, the kernel returns DSP_ERR_TIMEOUT,
