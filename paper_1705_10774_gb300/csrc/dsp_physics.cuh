@@ -174,7 +174,8 @@ __device__ __forceinline__ T sqrt_k(T x) {
     const double h = 0.5 * y;
     s = fma(h, fma(-s, s, (double)x), s);
     s = fma(h, fma(-s, s, (double)x), s);
-    return x == T(0) ? T(0) : s;
+    // x == +-0 tested on the bit pattern (an FP64 compare takes an FP64-pipe slot)
+    return (__double_as_longlong((double)x) << 1) == 0 ? T(0) : s;
   } else {
     return tsqrt(x);
   }

@@ -134,6 +134,14 @@ struct TileShared {
   int floors;  // new cells whose pressure recovery took the floor
 };
 
+// An axis known at run time (int) or at compile time (AxisC<V>): bodies
+// written once over `axis_value(d)` fold to constants in the second case.
+template <int V>
+struct AxisC {};
+__device__ __forceinline__ int axis_value(int d) { return d; }
+template <int V>
+__device__ __forceinline__ int axis_value(AxisC<V>) { return V; }
+
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 __device__ __forceinline__ int posmod(int a, int b) { const int r = a % b; return r < 0 ? r + b : r; }
 
@@ -152,6 +160,9 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
   // asynchronous copies of the next plane and of the old values (sweep
   // dispatcher, ideal MHD)
   constexpr bool ASYNC = !CONC && !NI;
+  // phases C and D as pools of work items over the whole block (FP64), or
+  // one loop per axis (FP32)
+  constexpr bool POOL = sizeof(T) == 8;
   constexpr int H2N = L::H2N, H1N = L::H1N, FPN = L::FPN;
   T *const Wr = sm + L::oW;
   T *const FB = sm + L::oFB;
@@ -181,6 +192,9 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
   int &s_fallback = S.fallback;
 
   const int tid = threadIdx.x;
+  // threads renumbered from the first warp after the TX*TY that update the
+  // tile's cells: pools of items that those warps need not take first
+  const int rot = (tid + NT - TX * TY) % NT;
   const PatchGeo &gp = c.geo[P];
   const int nx = gp.n[0], ny = gp.n[1], nz = gp.n[2];
   const int lox = gp.lo[0], loy = gp.lo[1], loz = gp.lo[2];
@@ -413,6 +427,59 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
     }
     if constexpr (M == GATHER_ISSUE) cp_async_commit();
   };
+  // The face updates of phase E as one pool of items: the x-faces of plane
+  // p-1 ([0, NBXF)), its y-faces, the z-faces at p-1/2.  eface gives an
+  // item's face (i, j) and kind (0 x, 1 y, 2 z; -1 outside a partial tile);
+  // the item's old value sits at OLD[OLDX + item].
+  constexpr int NBXF = (TX + 1) * TY, NBYF = TX * (TY + 1), NBF = NBXF + NBYF + TX * TY;
+  auto eface = [&](int e, int &i, int &j) -> int {
+    if (e < NBXF) {
+      i = e % (TX + 1);
+      j = e / (TX + 1);
+      return i <= tx && j < ty ? 0 : -1;
+    }
+    e -= NBXF;
+    if (e < NBYF) {
+      i = e % TX;
+      j = e / TX;
+      return i < tx && j <= ty ? 1 : -1;
+    }
+    e -= NBYF;
+    i = e % TX;
+    j = e / TX;
+    return i < tx && j < ty ? 2 : -1;
+  };
+  // Visit the face-update items this thread owns, x- and y-faces if xy,
+  // z-faces if zf: fn(item, kind, i, j), the kind an int in FP64's pool
+  // (dealt from the first warp after the cell-updating ones) and an AxisC<>
+  // constant in FP32's loops, one per kind from thread 0.
+  auto each_eface = [&](bool xy, bool zf, auto fn) {
+    if constexpr (POOL) {
+      for (int e = rot; e < NBF; e += NT) {
+        int i, j;
+        const int kd = eface(e, i, j);
+        if (kd < 0 || (kd < 2 ? !xy : !zf)) continue;
+        fn(e, kd, i, j);
+      }
+    } else {
+      if (xy) {
+        for (int e = tid; e < NBXF; e += NT) {
+          const int i = e % (TX + 1), j = e / (TX + 1);
+          if (i <= tx && j < ty) fn(e, AxisC<0>{}, i, j);
+        }
+        for (int e = tid; e < NBYF; e += NT) {
+          const int i = e % TX, j = e / TX;
+          if (i < tx && j <= ty) fn(NBXF + e, AxisC<1>{}, i, j);
+        }
+      }
+      if (zf) {
+        for (int e = tid; e < TX * TY; e += NT) {
+          const int i = e % TX, j = e / TX;
+          if (i < tx && j < ty) fn(NBXF + NBYF + e, AxisC<2>{}, i, j);
+        }
+      }
+    }
+  };
   // Start the copies of the old values phase E reads in iteration `it`
   // (plane p-1's U and x-/y-faces once it >= 2, the z-faces at p-1/2 once
   // it >= 1); each thread copies exactly the values it will update.
@@ -426,23 +493,15 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
 #pragma unroll
         for (int k = 0; k < 5; k++) cp_async_elem(OLD + L::OLDU + k * TX * TY + ci, src(own + k * nc + id));
       }
-      for (int ci = tid; ci < (TX + 1) * TY; ci += NT) {
-        const int i = ci % (TX + 1), j = ci / (TX + 1);
-        if (i > tx || j >= ty) continue;
-        cp_async_elem(OLD + L::OLDX + ci, src(own + ofx + ((long long)(p - 1) * ny + (y0 + j)) * (nx + 1) + (x0 + i)));
-      }
-      for (int ci = tid; ci < TX * (TY + 1); ci += NT) {
-        const int i = ci % TX, j = ci / TX;
-        if (i >= tx || j > ty) continue;
-        cp_async_elem(OLD + L::OLDY + ci, src(own + ofy + ((long long)(p - 1) * (ny + 1) + (y0 + j)) * nx + (x0 + i)));
-      }
     }
     if (it >= 1) {
-      for (int ci = tid; ci < TX * TY; ci += NT) {
-        const int i = ci % TX, j = ci / TX;
-        if (i >= tx || j >= ty) continue;
-        cp_async_elem(OLD + L::OLDZ + ci, src(own + ofz + ((long long)p * ny + (y0 + j)) * nx + (x0 + i)));
-      }
+      each_eface(it >= 2, true, [&](int e, auto kdd, int i, int j) {
+        const int kd = axis_value(kdd);
+        const T *g = kd == 0   ? own + ofx + ((long long)(p - 1) * ny + (y0 + j)) * (nx + 1) + (x0 + i)
+                     : kd == 1 ? own + ofy + ((long long)(p - 1) * (ny + 1) + (y0 + j)) * nx + (x0 + i)
+                               : own + ofz + ((long long)p * ny + (y0 + j)) * nx + (x0 + i);
+        cp_async_elem(OLD + L::OLDX + e, src(g));
+      });
     }
     cp_async_commit();
   };
@@ -640,190 +699,226 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
       else cp_async_commit();  // an empty group keeps the wait counts in step
     }
 
-    // ---- C: face fluxes
+    // ---- C: face fluxes: the x-, y- and z-faces whose fluxes are needed and
+    // those whose signal speeds alone are (the halo rows and columns around
+    // the tile).  A face's two states are loaded in the frame of its axis
+    // (normal component first, then the two tangential ones in cyclic
+    // order), the order in which the solvers of axis D read them, so one body
+    // serves every axis.  FP64 (POOL) deals all faces of the plane to the
+    // block as one pool, every axis running the same instructions in shared
+    // warps (an FP64 warp instruction costs its pipe slot whatever its
+    // active lanes, and the one block per SM has no other block's warps to
+    // fill its idle ones); FP32 runs one loop per axis with the axis a
+    // compile-time constant (fewer instructions: its two blocks per SM fill
+    // each other's idle warps).
     {
-      // x-faces (i-1/2, j) of plane p, i in [0,tx]: rows j in [0,ty) need
-      // fluxes and speeds, the halo rows j = -1 and j = ty speeds only
-      for (int ci = tid; ci < (TX + 1) * (TY + 2); ci += NT) {
-        int i, j;
-        const bool full = ci < (TX + 1) * TY;
-        if (full) {
-          i = ci % (TX + 1);
-          j = ci / (TX + 1);
-          if (j >= ty) continue;
-        } else {
-          const int k = ci - (TX + 1) * TY;
-          i = k % (TX + 1);
-          j = k / (TX + 1) == 0 ? -1 : ty;
-        }
-        if (i > tx) continue;
-        const int hl = H1(i - 1, j), hr = H1(i, j);
+      constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1), NZF = TX * TY;
+      constexpr int NXS = 2 * (TX + 1), NYS = 2 * (TY + 1), NZS = 2 * (TX + 2) + 2 * TY;
+      auto face_item = [&](auto dd, int i, int j, bool full) {
+        const int d = axis_value(dd);
+        // the face's cells: left hl, right hr (a z-face's left state is the
+        // upper z-face state of plane p-1, carried in ZP)
+        const int hr = H1(i, j), hl = hr - (d == 0 ? 1 : d == 1 ? TX + 2 : 0);
+        const T *const Sd = d == 0 ? SdX : d == 1 ? SdY : SdZ;
+        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
+        const int cmp[8] = {RHO, VX + d, VX + t1, VX + t2, PR, BX + d, BX + t1, BX + t2};
         T WL[8], WR[8], F[5], SL, SR;
 #pragma unroll
         for (int k = 0; k < 8; k++) {
-          WL[k] = Sws[k * H1N + hl] + half * SdX[k * H1N + hl];
-          WR[k] = Sws[k * H1N + hr] - half * SdX[k * H1N + hr];
+          const int o = cmp[k] * H1N;
+          WL[k] = d == 2 ? ZP[o + hr] : Sws[o + hl] + half * Sd[o + hl];
+          WR[k] = Sws[o + hr] - half * Sd[o + hr];
         }
         if (full) {
           face_flux<T, 0, RS>(WL, WR, gamma, igm1, F, SL, SR);
-#pragma unroll
-          for (int k = 0; k < 5; k++) FX[k * H1N + hr] = F[k];
+          T *const Fd = d == 0 ? FX : d == 1 ? FY : FZc;
+          Fd[hr] = F[0];
+          Fd[(1 + d) * H1N + hr] = F[1];
+          Fd[(1 + t1) * H1N + hr] = F[2];
+          Fd[(1 + t2) * H1N + hr] = F[3];
+          Fd[4 * H1N + hr] = F[4];
         } else {
           hll_speeds<T, 0>(WL, WR, gamma, SL, SR);
         }
-        SXc[hr] = SL;
-        SXc[H1N + hr] = SR;
-      }
-      // y-faces (i, j-1/2) of plane p, j in [0,ty]: columns i in [0,tx)
-      // need fluxes, the halo columns i = -1 and i = tx speeds only
-      for (int ci = tid; ci < (TX + 2) * (TY + 1); ci += NT) {
-        int i, j;
-        const bool full = ci < TX * (TY + 1);
-        if (full) {
-          i = ci % TX;
-          j = ci / TX;
-          if (i >= tx) continue;
-        } else {
-          const int k = ci - TX * (TY + 1);
+        T *const Sp = d == 0 ? SXc : d == 1 ? SYc : SZ;
+        Sp[hr] = SL;
+        Sp[H1N + hr] = SR;
+      };
+      // item k of axis d: its face (i, j), whether its flux is needed; false
+      // if the face lies outside a partial tile.  Per axis the faces with
+      // fluxes come first: x-faces (i-1/2, j), i in [0,tx], j in [0,ty),
+      // then the halo rows j = -1 and ty; y-faces (i, j-1/2), i in [0,tx),
+      // j in [0,ty], then the halo columns i = -1 and tx; z-faces (i, j,
+      // p-1/2) of the tile's cells, then the ring around them.
+      auto axis_item = [&](int d, int k, int &i, int &j, bool &full) -> bool {
+        if (d == 0) {
+          full = k < NXF;
+          if (full) {
+            i = k % (TX + 1);
+            j = k / (TX + 1);
+            return i <= tx && j < ty;
+          }
+          k -= NXF;
+          i = k % (TX + 1);
+          j = k / (TX + 1) == 0 ? -1 : ty;
+          return i <= tx;
+        }
+        if (d == 1) {
+          full = k < NYF;
+          if (full) {
+            i = k % TX;
+            j = k / TX;
+            return i < tx && j <= ty;
+          }
+          k -= NYF;
           i = k / (TY + 1) == 0 ? -1 : tx;
           j = k % (TY + 1);
+          return j <= ty;
         }
-        if (j > ty) continue;
-        const int hl = H1(i, j - 1), hr = H1(i, j);
-        T WL[8], WR[8], F[5], SL, SR;
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-          WL[k] = Sws[k * H1N + hl] + half * SdY[k * H1N + hl];
-          WR[k] = Sws[k * H1N + hr] - half * SdY[k * H1N + hr];
-        }
+        full = k < NZF;
         if (full) {
-          face_flux<T, 1, RS>(WL, WR, gamma, igm1, F, SL, SR);
-#pragma unroll
-          for (int k = 0; k < 5; k++) FY[k * H1N + hr] = F[k];
-        } else {
-          hll_speeds<T, 1>(WL, WR, gamma, SL, SR);
+          i = k % TX;
+          j = k / TX;
+          return i < tx && j < ty;
         }
-        SYc[hr] = SL;
-        SYc[H1N + hr] = SR;
-      }
-      // z-faces (i, j, p-1/2) on the H1 region: the tile's own faces need
-      // fluxes, the ring around them speeds only
-      if (it > 0) {
-        for (int ci = tid; ci < (TX + 2) * (TY + 2); ci += NT) {
+        k -= NZF;
+        if (k < 2 * (TX + 2)) {
+          i = k % (TX + 2) - 1;
+          j = k / (TX + 2) == 0 ? -1 : ty;
+          return i <= tx;
+        }
+        k -= 2 * (TX + 2);
+        i = k / TY == 0 ? -1 : tx;
+        j = k % TY;
+        return j < ty;
+      };
+      if constexpr (POOL) {
+        // the pool: every face with a flux (x, y, z), then every face with
+        // speeds only; one call site, the axis a run-time value
+        const int nfull = NXF + NYF + (it > 0 ? NZF : 0);
+        const int nitems = nfull + NXS + NYS + (it > 0 ? NZS : 0);
+        for (int ci = tid; ci < nitems; ci += NT) {
+          int d, k;
+          if (ci < nfull) {
+            d = ci < NXF ? 0 : ci < NXF + NYF ? 1 : 2;
+            k = ci - (d == 0 ? 0 : d == 1 ? NXF : NXF + NYF);
+          } else {
+            const int s = ci - nfull;
+            d = s < NXS ? 0 : s < NXS + NYS ? 1 : 2;
+            k = s - (d == 0 ? 0 : d == 1 ? NXS : NXS + NYS) + (d == 0 ? NXF : d == 1 ? NYF : NZF);
+          }
           int i, j;
-          const bool full = ci < TX * TY;
-          if (full) {
-            i = ci % TX;
-            j = ci / TX;
-            if (i >= tx || j >= ty) continue;
-          } else {
-            const int k = ci - TX * TY;
-            if (k < 2 * (TX + 2)) {
-              i = k % (TX + 2) - 1;
-              j = k / (TX + 2) == 0 ? -1 : ty;
-              if (i > tx) continue;
-            } else {
-              const int k2 = k - 2 * (TX + 2);
-              i = k2 / TY == 0 ? -1 : tx;
-              j = k2 % TY;
-              if (j >= ty) continue;
-            }
+          bool full;
+          if (axis_item(d, k, i, j, full)) face_item(d, i, j, full);
+        }
+      } else {
+        for (int ci = tid; ci < NXF + NXS; ci += NT) {
+          int i, j;
+          bool full;
+          if (axis_item(0, ci, i, j, full)) face_item(AxisC<0>{}, i, j, full);
+        }
+        for (int ci = tid; ci < NYF + NYS; ci += NT) {
+          int i, j;
+          bool full;
+          if (axis_item(1, ci, i, j, full)) face_item(AxisC<1>{}, i, j, full);
+        }
+        if (it > 0) {
+          for (int ci = tid; ci < NZF + NZS; ci += NT) {
+            int i, j;
+            bool full;
+            if (axis_item(2, ci, i, j, full)) face_item(AxisC<2>{}, i, j, full);
           }
-          const int h = H1(i, j);
-          T WL[8], WR[8], F[5], SL, SR;
-#pragma unroll
-          for (int k = 0; k < 8; k++) {
-            WL[k] = ZP[k * H1N + h];
-            WR[k] = Sws[k * H1N + h] - half * SdZ[k * H1N + h];
-          }
-          if (full) {
-            face_flux<T, 2, RS>(WL, WR, gamma, igm1, F, SL, SR);
-#pragma unroll
-            for (int k = 0; k < 5; k++) FZc[k * H1N + h] = F[k];
-          } else {
-            hll_speeds<T, 2>(WL, WR, gamma, SL, SR);
-          }
-          SZ[h] = SL;
-          SZ[H1N + h] = SR;
         }
       }
     }
     __syncthreads();
 
-    // ---- D: x- and y-edge EMFs at p-1/2, in-plane divergence of plane p
+    // ---- D: x- and y-edge EMFs at p-1/2, in-plane divergence of plane p.
+    // An edge along axis e has the two other axes a and b (x-edge: a = y,
+    // b = z; y-edge: a = z, b = x); its corner states at the plane below come
+    // carried in CX / CY, the two at plane p are extrapolated here, and one
+    // body serves both axes.  FP64 (POOL) deals the x- and y-edges and then,
+    // from the next warp boundary on, the cells' divergences to the block as
+    // one pool; FP32 runs one loop each with the axis a compile-time constant.
     if (it > 0) {
-      // x-edges (i, j-1/2, p-1/2): i in [0,tx), j in [0,ty]; a = y, b = z
-      for (int ci = tid; ci < TX * (TY + 1); ci += NT) {
-        const int i = ci % TX, j = ci / TX;
-        if (i >= tx || j > ty) continue;
-        const int hm = H1(i, j - 1), h0 = H1(i, j);
-        const T Ell = CX[0 * H1N + hm], Ba_ll = CX[1 * H1N + hm], Bb_ll = CX[2 * H1N + hm];
-        const T Erl = CX[3 * H1N + h0], Ba_rl = CX[4 * H1N + h0], Bb_rl = CX[5 * H1N + h0];
-        const T lr_vy = (Sws[VY * H1N + hm] + half * SdY[VY * H1N + hm]) - half * SdZ[VY * H1N + hm];
-        const T lr_vz = (Sws[VZ * H1N + hm] + half * SdY[VZ * H1N + hm]) - half * SdZ[VZ * H1N + hm];
-        const T lr_by = (Sws[BY * H1N + hm] + half * SdY[BY * H1N + hm]) - half * SdZ[BY * H1N + hm];
-        const T lr_bz = (Sws[BZ * H1N + hm] + half * SdY[BZ * H1N + hm]) - half * SdZ[BZ * H1N + hm];
-        const T rr_vy = (Sws[VY * H1N + h0] - half * SdY[VY * H1N + h0]) - half * SdZ[VY * H1N + h0];
-        const T rr_vz = (Sws[VZ * H1N + h0] - half * SdY[VZ * H1N + h0]) - half * SdZ[VZ * H1N + h0];
-        const T rr_by = (Sws[BY * H1N + h0] - half * SdY[BY * H1N + h0]) - half * SdZ[BY * H1N + h0];
-        const T rr_bz = (Sws[BZ * H1N + h0] - half * SdY[BZ * H1N + h0]) - half * SdZ[BZ * H1N + h0];
-        const T Elr = lr_vz * lr_by - lr_vy * lr_bz;
-        const T Err = rr_vz * rr_by - rr_vy * rr_bz;
-        const T apa = pmax0(SYp[H1N + h0], SYc[H1N + h0]);
-        const T ama = nmax0(SYp[h0], SYc[h0]);
-        const T apb = pmax0(SZ[H1N + hm], SZ[H1N + h0]);
-        const T amb = nmax0(SZ[hm], SZ[h0]);
-        T ex = emf(Ell, Erl, Elr, Err, Ba_ll, Ba_rl, lr_by, rr_by, Bb_ll, Bb_rl, lr_bz, rr_bz, apa, ama, apb, amb);
-        if constexpr (NI != 0) {
-          const T en = eni_x(i, j, p);
-          ENX[par * H1N + h0] = en;
-          ex = ex + en;
-        }
-        EXc[h0] = ex;
-      }
-      // y-edges (i-1/2, j, p-1/2): i in [0,tx], j in [0,ty); a = z, b = x
-      for (int ci = tid; ci < (TX + 1) * TY; ci += NT) {
-        const int i = ci % (TX + 1), j = ci / (TX + 1);
-        if (i > tx || j >= ty) continue;
-        const int hm = H1(i - 1, j), h0 = H1(i, j);
-        const T Ell = CY[0 * H1N + hm], Ba_ll = CY[1 * H1N + hm], Bb_ll = CY[2 * H1N + hm];
-        const T Elr = CY[3 * H1N + h0], Ba_lr = CY[4 * H1N + h0], Bb_lr = CY[5 * H1N + h0];
-        const T rl_vz = (Sws[VZ * H1N + hm] - half * SdZ[VZ * H1N + hm]) + half * SdX[VZ * H1N + hm];
-        const T rl_vx = (Sws[VX * H1N + hm] - half * SdZ[VX * H1N + hm]) + half * SdX[VX * H1N + hm];
-        const T rl_bz = (Sws[BZ * H1N + hm] - half * SdZ[BZ * H1N + hm]) + half * SdX[BZ * H1N + hm];
-        const T rl_bx = (Sws[BX * H1N + hm] - half * SdZ[BX * H1N + hm]) + half * SdX[BX * H1N + hm];
-        const T rr_vz = (Sws[VZ * H1N + h0] - half * SdZ[VZ * H1N + h0]) - half * SdX[VZ * H1N + h0];
-        const T rr_vx = (Sws[VX * H1N + h0] - half * SdZ[VX * H1N + h0]) - half * SdX[VX * H1N + h0];
-        const T rr_bz = (Sws[BZ * H1N + h0] - half * SdZ[BZ * H1N + h0]) - half * SdX[BZ * H1N + h0];
-        const T rr_bx = (Sws[BX * H1N + h0] - half * SdZ[BX * H1N + h0]) - half * SdX[BX * H1N + h0];
-        const T Erl = rl_vx * rl_bz - rl_vz * rl_bx;
-        const T Err = rr_vx * rr_bz - rr_vz * rr_bx;
-        const T apa = pmax0(SZ[H1N + hm], SZ[H1N + h0]);
-        const T ama = nmax0(SZ[hm], SZ[h0]);
-        const T apb = pmax0(SXp[H1N + h0], SXc[H1N + h0]);
-        const T amb = nmax0(SXp[h0], SXc[h0]);
-        T ey = emf(Ell, Erl, Elr, Err, Ba_ll, rl_bz, Ba_lr, rr_bz, Bb_ll, rl_bx, Bb_lr, rr_bx, apa, ama, apb, amb);
-        if constexpr (NI != 0) {
-          const T en = eni_y(i, j, p);
-          ENY[par * H1N + h0] = en;
-          ey = ey + en;
-        }
-        EYc[h0] = ey;
-      }
-      if (p < z0 + tz) {
-        // with non-ideal terms the energy part waits for the Poynting flux,
-        // which needs the edges above this plane: keep the ideal energy
-        // fluxes of the plane's x- and y-faces instead
-        constexpr int KD = NI ? 4 : 5;
-        for (int ci = tid; ci < TX * TY; ci += NT) {
-          const int i = ci % TX, j = ci / TX;
-          if (i >= tx || j >= ty) continue;
-          const int h = H1(i, j), hx = H1(i + 1, j), hy = H1(i, j + 1);
+      constexpr int NXE = TX * (TY + 1), NYE = (TX + 1) * TY, NE = NXE + NYE;
+      // with non-ideal terms the energy part waits for the Poynting flux,
+      // which needs the edges above this plane: keep the ideal energy
+      // fluxes of the plane's x- and y-faces instead
+      constexpr int KD = NI ? 4 : 5;
+      const bool div = p < z0 + tz;
+      auto div_item = [&](int k) {
+        const int i = k % TX, j = k / TX;
+        if (i >= tx || j >= ty) return;
+        const int h = H1(i, j), hx = H1(i + 1, j), hy = H1(i, j + 1);
 #pragma unroll
-          for (int k = 0; k < KD; k++)
-            DUc[k * H1N + h] = (FX[k * H1N + hx] - FX[k * H1N + h]) + (FY[k * H1N + hy] - FY[k * H1N + h]);
-        }
+        for (int q = 0; q < KD; q++)
+          DUc[q * H1N + h] = (FX[q * H1N + hx] - FX[q * H1N + h]) + (FY[q * H1N + hy] - FY[q * H1N + h]);
+      };
+      // edge k of axis d (x-edges (i, j-1/2, p-1/2): i in [0,tx), j in
+      // [0,ty]; y-edges (i-1/2, j, p-1/2): i in [0,tx], j in [0,ty))
+      auto edge_item = [&](auto dd, int k) {
+        const int d = axis_value(dd);
+        const int i = d == 0 ? k % TX : k % (TX + 1), j = d == 0 ? k / TX : k / (TX + 1);
+        if (d == 0 ? (i >= tx || j > ty) : (i > tx || j >= ty)) return;
+        // h0: the cell on the edge's high side along its in-plane normal (y
+        // for an x-edge, x for a y-edge), hm the one below it
+        const int h0 = H1(i, j), hm = h0 - (d == 0 ? TX + 2 : 1);
+        const T *const C6 = d == 0 ? CX : CY;
+        const T *const SdA = d == 0 ? SdY : SdZ;
+        const T *const SdB = d == 0 ? SdZ : SdX;
+        const int va = d == 0 ? VY : VZ, vb = d == 0 ? VZ : VX, ba = d == 0 ? BY : BZ, bb = d == 0 ? BZ : BX;
+        // the corner at hm: (+a,-b) of an x-edge's low-y cell, (-a,+b) of a
+        // y-edge's low-x cell; the corner at h0: (-a,-b)
+        const T sA = d == 0 ? half : -half, sB = -sA;
+        auto corner = [&](int c, int h, T s1, T s2) -> T {
+          return (Sws[c * H1N + h] + s1 * SdA[c * H1N + h]) + s2 * SdB[c * H1N + h];
+        };
+        const T vam = corner(va, hm, sA, sB), vbm = corner(vb, hm, sA, sB);
+        const T bam = corner(ba, hm, sA, sB), bbm = corner(bb, hm, sA, sB);
+        const T va0 = corner(va, h0, -half, -half), vb0 = corner(vb, h0, -half, -half);
+        const T ba0 = corner(ba, h0, -half, -half), bb0 = corner(bb, h0, -half, -half);
+        const T Em = vbm * bam - vam * bbm;
+        const T E0 = vb0 * ba0 - va0 * bb0;
+        // the two corners carried from the plane below: (-a,-b) at hm and the
+        // other one at h0
+        const T Ell = C6[hm], Ba_ll = C6[H1N + hm], Bb_ll = C6[2 * H1N + hm];
+        const T Ec = C6[3 * H1N + h0], Bac = C6[4 * H1N + h0], Bbc = C6[5 * H1N + h0];
+        const T Erl = d == 0 ? Ec : Em, Elr = d == 0 ? Em : Ec;
+        const T Ba_rl = d == 0 ? Bac : bam, Ba_lr = d == 0 ? bam : Bac;
+        const T Bb_rl = d == 0 ? Bbc : bbm, Bb_lr = d == 0 ? bbm : Bbc;
+        // weights: the faces normal to the in-plane normal (y-faces for an
+        // x-edge, x-faces for a y-edge) of planes p-1 and p at h0, and the
+        // z-faces at p-1/2 of hm and h0
+        const T *const Pp = d == 0 ? SYp : SXp;
+        const T *const Pc = d == 0 ? SYc : SXc;
+        const T ap2 = pmax0(Pp[H1N + h0], Pc[H1N + h0]), am2 = nmax0(Pp[h0], Pc[h0]);
+        const T apz = pmax0(SZ[H1N + hm], SZ[H1N + h0]), amz = nmax0(SZ[hm], SZ[h0]);
+        const T apa = d == 0 ? ap2 : apz, ama = d == 0 ? am2 : amz;
+        const T apb = d == 0 ? apz : ap2, amb = d == 0 ? amz : am2;
+        T e = emf(Ell, Erl, Elr, E0, Ba_ll, Ba_rl, Ba_lr, ba0, Bb_ll, Bb_rl, Bb_lr, bb0, apa, ama, apb, amb);
         if constexpr (NI != 0) {
+          const T en = d == 0 ? eni_x(i, j, p) : eni_y(i, j, p);
+          (d == 0 ? ENX : ENY)[par * H1N + h0] = en;
+          e = e + en;
+        }
+        (d == 0 ? EXc : EYc)[h0] = e;
+      };
+      if constexpr (POOL) {
+        constexpr int DU0 = (NE + 31) / 32 * 32;
+        const int nitems = div ? DU0 + TX * TY : NE;
+        for (int ci = tid; ci < nitems; ci += NT) {
+          if (ci < NE) edge_item(ci < NXE ? 0 : 1, ci < NXE ? ci : ci - NXE);
+          else if (ci >= DU0) div_item(ci - DU0);
+        }
+      } else {
+        for (int ci = tid; ci < NXE; ci += NT) edge_item(AxisC<0>{}, ci);
+        for (int ci = tid; ci < NYE; ci += NT) edge_item(AxisC<1>{}, ci);
+        if (div)
+          for (int ci = tid; ci < TX * TY; ci += NT) div_item(ci);
+      }
+      if constexpr (NI != 0) {
+        if (div) {
           for (int ci = tid; ci < (TX + 1) * (TY + 1); ci += NT) {
             const int i = ci % (TX + 1), j = ci / (TX + 1), h = H1(i, j);
             if (i <= tx && j < ty) FXE[par * H1N + h] = FX[4 * H1N + h];
@@ -896,34 +991,27 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         put_global(dst + k * nc + ci, unew[k]);
       }
     }
-    if (upd) {
-      const int k = p - 1;
-      for (int ci = tid; ci < (TX + 1) * TY; ci += NT) {
-        const int i = ci % (TX + 1), j = ci / (TX + 1), h = H1(i, j);
-        if (i > tx || j >= ty) continue;
-        const long long id = ((long long)k * ny + (y0 + j)) * (nx + 1) + (x0 + i);
-        const T b = (!ASYNC ? *src(own + ofx + id) : OLD[L::OLDX + ci]) - dtdx * ((EZ[H1(i, j + 1)] - EZ[h]) - (EYc[h] - EYp[h]));
-        NBX[h] = b;
-        put_global(dst + ofx + id, b);
-      }
-      for (int ci = tid; ci < TX * (TY + 1); ci += NT) {
-        const int i = ci % TX, j = ci / TX, h = H1(i, j);
-        if (i >= tx || j > ty) continue;
-        const long long id = ((long long)k * (ny + 1) + (y0 + j)) * nx + (x0 + i);
-        const T b = (!ASYNC ? *src(own + ofy + id) : OLD[L::OLDY + ci]) - dtdx * ((EXc[h] - EXp[h]) - (EZ[H1(i + 1, j)] - EZ[h]));
-        NBY[h] = b;
-        put_global(dst + ofy + id, b);
-      }
-    }
     if (it >= 1) {
-      for (int ci = tid; ci < TX * TY; ci += NT) {
-        const int i = ci % TX, j = ci / TX, h = H1(i, j);
-        if (i >= tx || j >= ty) continue;
-        const long long id = ((long long)p * ny + (y0 + j)) * nx + (x0 + i);
-        const T b = (!ASYNC ? *src(own + ofz + id) : OLD[L::OLDZ + ci]) - dtdx * ((EYc[H1(i + 1, j)] - EYc[h]) - (EXc[H1(i, j + 1)] - EXc[h]));
-        NBZc[h] = b;
-        put_global(dst + ofz + id, b);
-      }
+      each_eface(upd, true, [&](int e, auto kdd, int i, int j) {
+        const int kd = axis_value(kdd);
+        const int h = H1(i, j);
+        if (kd == 0) {
+          const long long id = ((long long)(p - 1) * ny + (y0 + j)) * (nx + 1) + (x0 + i);
+          const T b = (!ASYNC ? *src(own + ofx + id) : OLD[L::OLDX + e]) - dtdx * ((EZ[H1(i, j + 1)] - EZ[h]) - (EYc[h] - EYp[h]));
+          NBX[h] = b;
+          put_global(dst + ofx + id, b);
+        } else if (kd == 1) {
+          const long long id = ((long long)(p - 1) * (ny + 1) + (y0 + j)) * nx + (x0 + i);
+          const T b = (!ASYNC ? *src(own + ofy + id) : OLD[L::OLDX + e]) - dtdx * ((EXc[h] - EXp[h]) - (EZ[H1(i + 1, j)] - EZ[h]));
+          NBY[h] = b;
+          put_global(dst + ofy + id, b);
+        } else {
+          const long long id = ((long long)p * ny + (y0 + j)) * nx + (x0 + i);
+          const T b = (!ASYNC ? *src(own + ofz + id) : OLD[L::OLDX + e]) - dtdx * ((EYc[H1(i + 1, j)] - EYc[h]) - (EXc[H1(i, j + 1)] - EXc[h]));
+          NBZc[h] = b;
+          put_global(dst + ofz + id, b);
+        }
+      });
     }
     __syncthreads();
 
@@ -941,11 +1029,19 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
         smax_t = tmax(smax_t, tmax(signal_sum(Wn, gamma), nonideal_speed(Wn, c.cfl, c.eta, c.gad, c.rhoi, c.cohm, c.cad, dxl)));
       else smax_t = tmax(smax_t, signal_sum(Wn, gamma));
     }
-    if (p >= z0 && p < z0 + tz) {
+    {
+      // the z-edge EMFs of plane p and the values of plane p carried to the
+      // next plane (its upper z-face state and its +z corner values for the
+      // x- and y-edges above it).  FP64 deals them as one pool of items,
+      // the carried values from the next warp boundary on, from the first
+      // warp after the cell-updating ones (which have the new cells' signal
+      // speeds to compute); FP32 runs one loop each from thread 0.
+      constexpr int NZE = (TX + 1) * (TY + 1), CA0 = (NZE + 31) / 32 * 32, NCA = (TX + 2) * (TY + 2);
+      const bool zedges = p >= z0 && p < z0 + tz;
       // z-edges (i-1/2, j-1/2, p): i in [0,tx], j in [0,ty]; a = x, b = y
-      for (int ci = tid; ci < (TX + 1) * (TY + 1); ci += NT) {
-        const int i = ci % (TX + 1), j = ci / (TX + 1);
-        if (i > tx || j > ty) continue;
+      auto zedge_item = [&](int k) {
+        const int i = k % (TX + 1), j = k / (TX + 1);
+        if (i > tx || j > ty) return;
         const int hll_ = H1(i - 1, j - 1), hrl = H1(i, j - 1), hlr = H1(i - 1, j), hrr = H1(i, j);
         const T ll_vx = (Sws[VX * H1N + hll_] + half * SdX[VX * H1N + hll_]) + half * SdY[VX * H1N + hll_];
         const T ll_vy = (Sws[VY * H1N + hll_] + half * SdX[VY * H1N + hll_]) + half * SdY[VY * H1N + hll_];
@@ -978,14 +1074,10 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
           ez = ez + en;
         }
         EZ[hrr] = ez;
-      }
-    }
-    {
-      // values of plane p carried to the next plane: its upper z-face
-      // state and its +z corner values for the x- and y-edges above it
-      for (int ci = tid; ci < (TX + 2) * (TY + 2); ci += NT) {
-        const int i = ci % (TX + 2) - 1, j = ci / (TX + 2) - 1, h = H1(i, j);
-        if (i > tx || j > ty) continue;
+      };
+      auto carry_item = [&](int c) {
+        const int i = c % (TX + 2) - 1, j = c / (TX + 2) - 1, h = H1(i, j);
+        if (i > tx || j > ty) return;
 #pragma unroll
         for (int k = 0; k < 8; k++) ZP[k * H1N + h] = Sws[k * H1N + h] + half * SdZ[k * H1N + h];
         {  // x-edges: a = y, b = z; corners (+y,+z) and (-y,+z)
@@ -1020,6 +1112,19 @@ __device__ __forceinline__ void process_tile(const DevCtx &c, const int P, const
           CY[4 * H1N + h] = mx_bz;
           CY[5 * H1N + h] = mx_bx;
         }
+      };
+      if constexpr (POOL) {
+        for (int ci = rot; ci < CA0 + NCA; ci += NT) {
+          if (ci < CA0) {
+            if (zedges && ci < NZE) zedge_item(ci);
+          } else {
+            carry_item(ci - CA0);
+          }
+        }
+      } else {
+        if (zedges)
+          for (int ci = tid; ci < NZE; ci += NT) zedge_item(ci);
+        for (int ci = tid; ci < NCA; ci += NT) carry_item(ci);
       }
     }
     __syncthreads();
