@@ -62,8 +62,7 @@ NONIDEAL = dict(eta=1e-4, gamma_ad=75.0, rho_i=1.0)
 # of one launch divided by the cells it updated (captures of smaller cases
 # of the same kernel: traffic grows in proportion to the cells); a variant
 # without an entry reports null.
-TRAFFIC_PER_CELL = {2: (549.619712e6 + 421.812224e6) / 7077888, 5: (236.742656e6 + 193.273600e6) / 7077888,
-                    10: (534.644224e6 + 421.614336e6) / 7077888, 15: (527.814400e6 + 424.025088e6) / 7077888}
+TRAFFIC_PER_CELL = {4: (551.527168e6 + 427.680256e6) / 7077888, 5: (237.393920e6 + 193.476096e6) / 7077888}
 
 
 def guard_fraction(n, g):

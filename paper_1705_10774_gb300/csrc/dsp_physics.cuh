@@ -262,17 +262,34 @@ __device__ __forceinline__ T mc(T dl, T dr) {
   if ((a & B::MAG) == 0 || (b & B::MAG) == 0 || (a ^ b) < 0) return T(0);
   if constexpr (kFast && sizeof(T) == 8) {
     // the same value as 2 min(|dl|, |dr|, |dl + dr| / 4): the power-of-two
-    // scalings are exact, so they are done on the exponent field with
-    // integer operations (an FP64 multiply where an exponent is near the
-    // ends of its range), leaving one FP64 operation, dl + dr
+    // scalings are exact, so they are done on the bit patterns with integer
+    // operations, leaving one FP64 operation, dl + dr.  Both arms of each
+    // select are integer: near the ends of the exponent range, x/4 of a
+    // result below the normal range is the significand shifted right and
+    // rounded to nearest even (as the multiply would round it), 2x of a
+    // subnormal x is its pattern shifted left, 2x of the largest binade is
+    // infinity, and an infinity or NaN stays as it is.
     const long long m = min(a & B::MAG, b & B::MAG);
-    const double q = tabs(dl + dr);
-    long long iq = __double_as_longlong(q);
+    const long long iq0 = __double_as_longlong(dl + dr) & B::MAG;
     const long long one = 1ll << 52;
-    iq = (iq >> 52) > 2 ? iq - 2 * one : __double_as_longlong(0.25 * q);
-    long long is = min(m, iq);
-    is = (is >> 52) < 2046 && (is >> 52) > 0 ? is + one : __double_as_longlong(2.0 * __longlong_as_double(is));
-    return __longlong_as_double(a < 0 ? is | (long long)0x8000000000000000ull : is);
+    const int eq = (int)(iq0 >> 52);
+    long long iq;
+    if (eq == 2047) {
+      iq = iq0;  // the sum overflowed: infinity / 4 is infinity
+    } else if (eq > 2) {
+      iq = iq0 - 2 * one;
+    } else {
+      // |dl + dr| / 4 below the normal range: significand (with its leading
+      // bit for a normal input) times 2^(eq - 3), eq - 3 in [-3, -1]
+      const long long sig = eq > 0 ? one | (iq0 & (one - 1)) : iq0;
+      const int sh = eq > 0 ? 3 - eq : 2;
+      const long long r = sig >> sh, rem = sig & ((1ll << sh) - 1), hf = 1ll << (sh - 1);
+      iq = r + ((rem > hf || (rem == hf && (r & 1))) ? 1 : 0);
+    }
+    const long long is = min(m, iq);
+    const int es = (int)(is >> 52);
+    const long long i2 = es == 0 ? is << 1 : es < 2046 ? is + one : es == 2046 ? 0x7ff0000000000000ll : is;
+    return __longlong_as_double(a < 0 ? i2 | (long long)0x8000000000000000ull : i2);
   } else {
     const T s = tmin_nonneg(tmin_nonneg(T(2) * tabs(dl), T(2) * tabs(dr)), T(0.5) * tabs(dl + dr));
     return a < 0 ? B::to(B::of(s) ^ ~B::MAG) : s;

@@ -196,3 +196,4 @@ def test_hlld_variant_selection():
     with pytest.raises(DispatchError) as e:
         Dispatch(lay.n, lay.lo, **kw_of(lay, f.gamma), riemann=2)
     assert e.value.code == DSP_ERR_INVALID_ARG
+

@@ -212,3 +212,27 @@ def test_cshock_jump_settles_to_steady_profile_on_gpu(name, t_end, bound, ratio)
     g.close()
     assert err < bound, err
     assert r == ratio, r
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_nonideal_variants_identical(precision):
+    """The non-ideal variants of one precision (threads per block) give
+    bit-identical states with both terms on, the autotuner's choice
+    included."""
+    ids = [v[0] for v in B.variants() if v[6] == precision and v[7] == 0 and v[8] == 1]
+    assert len(ids) >= 2
+    lay, st, gamma = turbulent()
+    base = dict(gamma=gamma, cfl=0.4, base_cells=lay.base_cells, box_len=lay.box_len, time_mode=1)
+    outs = []
+    for vid in ids + [None]:
+        g = Dispatch(lay.n, lay.lo, **base, **BOTH, precision=precision, variant=-1 if vid is None else vid)
+        g.set_state(*st)
+        if vid is None:
+            chosen, table = g.autotune(reps=1)
+            assert chosen in ids and set(table) <= set(ids)
+        g.advance(t_end=0.004)
+        outs.append(g.get_state())
+        g.close()
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert np.array_equal(a, b)
