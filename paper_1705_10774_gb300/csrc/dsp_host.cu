@@ -60,9 +60,10 @@ struct dsp_ctx {
   unsigned long long *smax_new;
   long long *cnt;
   dsp_sched_entry *sched;
-  int *q_patch, *p_state, *tiles_done;
+  int *q_patch, *q_tile, *p_state, *tiles_done;
   double *q_dt;
-  unsigned long long *q_seq, *q_free, *q_ctl, *q_claim;
+  unsigned long long *q_seq, *q_free, *q_ctl;
+  long long q_alloc;  // slots of the ready queue's ring as allocated
   void *staging;
   size_t staging_bytes;
   int *h_ctl;  // pinned
@@ -431,27 +432,34 @@ __global__ void reset_times_kernel(DevCtx c, int first, int count, double t0) {
   }
 }
 
-// Seeds the persistent ready queue from the ready list the plan kernel just
-// built, and resets the queue's control words (one block).
-__global__ void queue_init_kernel(DevCtx c, double t_end) {
-  const int C = 2 * c.np;
-  const int nr = c.ctl[CTL_NREADY];
-  for (int s = threadIdx.x; s < C; s += blockDim.x) {
+// Empties the ready queue's ring: slot s first takes ticket s.
+__global__ void queue_ring_kernel(DevCtx c) {
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < c.q_cap; s += (long long)gridDim.x * blockDim.x) {
     c.q_free[s] = (unsigned long long)s;
     c.q_seq[s] = ~0ull;
-    c.q_claim[s] = ~0ull;
   }
+}
+
+// Seeds the persistent ready queue from the ready list the plan kernel just
+// built (the tiles of work-list entry r take tickets [work_off[r],
+// work_off[r+1])), and resets the queue's control words (one block).
+__global__ void queue_init_kernel(DevCtx c, double t_end) {
+  const int nr = c.ctl[CTL_NREADY];
   for (int P = threadIdx.x; P < c.np; P += blockDim.x) {
     c.p_state[P] = 0;
     c.tiles_done[P] = 0;
   }
   __syncthreads();
   for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-    c.q_patch[r] = c.R[r];
-    c.q_dt[r] = c.dtR[r];
-    c.q_claim[r] = (unsigned long long)r << 24;
-    c.q_seq[r] = (unsigned long long)r;
-    c.p_state[c.R[r]] = 1;
+    const int q = c.Rk[r], P = c.R[q];
+    const int base = c.work_off[r], T = c.geo[P].tiles;
+    for (int k = 0; k < T; k++) {
+      c.q_patch[base + k] = P;
+      c.q_tile[base + k] = k;
+      c.q_dt[base + k] = c.dtR[q];
+      c.q_seq[base + k] = (unsigned long long)(base + k);
+    }
+    c.p_state[P] = 1;
   }
   __shared__ int done;
   if (threadIdx.x == 0) done = 0;
@@ -461,7 +469,7 @@ __global__ void queue_init_kernel(DevCtx c, double t_end) {
   __syncthreads();
   if (threadIdx.x == 0) {
     c.q_ctl[0] = 0;
-    c.q_ctl[1] = (unsigned long long)nr;
+    c.q_ctl[1] = (unsigned long long)c.work_off[nr];
     c.q_ctl[2] = (unsigned long long)done;
     c.ctl[CTL_NREADY] = 0;
     if (nr == 0 && done < c.np) set_status(c, DSP_ERR_DEADLOCK, -1);
@@ -549,14 +557,12 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 // fit the kernel's table.
 bool make_geometry(const std::vector<dsp_patch_desc> &patches, const std::vector<int> &cls, const int *tx,
                    const int *ty, const int *tz, const int bszl[2][3], std::vector<PatchGeo> &geo, long long &off,
-                   long long &total_tiles, int &uniform_tiles, long long *cls_tiles) {
+                   long long &total_tiles, long long *cls_tiles) {
   const int npatch = (int)patches.size();
   geo.assign((size_t)npatch, PatchGeo());
   off = 0;
   total_tiles = 0;
   for (int k = 0; k < MAXCLS; k++) cls_tiles[k] = 0;
-  int tiles0 = -1;
-  bool same_tiles = true;
   auto fdiv = [](long long a, long long b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
   for (int i = 0; i < npatch; i++) {
     PatchGeo &g = geo[(size_t)i];
@@ -580,8 +586,6 @@ bool make_geometry(const std::vector<dsp_patch_desc> &patches, const std::vector
            (long long)g.n[0] * g.n[1] * (g.n[2] + 1);
     total_tiles += g.tiles;
     cls_tiles[k] += g.tiles;
-    if (tiles0 < 0) tiles0 = g.tiles;
-    if (g.tiles != tiles0) same_tiles = false;
     for (int kz = 0; kz < g.nt[2]; kz++)
       for (int ky = 0; ky < g.nt[1]; ky++)
         for (int kx = 0; kx < g.nt[0]; kx++) {
@@ -594,7 +598,6 @@ bool make_geometry(const std::vector<dsp_patch_desc> &patches, const std::vector
           if (ne > TABMAX) return false;
         }
   }
-  uniform_tiles = same_tiles ? tiles0 : 0;
   return true;
 }
 
@@ -609,11 +612,9 @@ bool install_tuning(dsp_ctx *c) {
   }
   std::vector<PatchGeo> geo;
   long long off = 0, tt = 0;
-  int ut = 0;
-  if (!make_geometry(c->patches, c->cls, tx, ty, c->tz_cls, c->d.bsz, geo, off, tt, ut, c->d.cls_tiles)) return false;
+  if (!make_geometry(c->patches, c->cls, tx, ty, c->tz_cls, c->d.bsz, geo, off, tt, c->d.cls_tiles)) return false;
   c->geo = geo;
   c->d.total_tiles = tt;
-  c->d.uniform_tiles = ut;
   c->var = c->var_cls[0];
   if (cudaMemcpyAsync(c->geo_d, geo.data(), sizeof(PatchGeo) * geo.size(), cudaMemcpyHostToDevice, c->stream) !=
       cudaSuccess)
@@ -692,7 +693,7 @@ void free_all(dsp_ctx *c) {
                   c->omap_d[1], c->gmap0_d, c->gofs_d, c->gbuf, c->rflag, c->rdt,
                   c->work_off_d, c->geo_d, c->coff_d,
                   c->nbl_off_d, c->nbl_d, c->R,       c->ctl,     c->smax_new, c->cnt,    c->sched,
-                  c->staging, c->q_patch, c->q_claim, c->p_state, c->tiles_done, c->q_dt, c->q_seq,
+                  c->staging, c->q_patch, c->q_tile, c->p_state, c->tiles_done, c->q_dt, c->q_seq,
                   c->q_free,  c->q_ctl, c->owned_d, c->pk_ids, c->pk_off, c->pk_meta, c->Rk};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -919,8 +920,7 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   std::vector<dsp_patch_desc> pvec(patches, patches + npatch);
   std::vector<PatchGeo> geo;
   long long off = 0, total_tiles = 0, cls_tiles[MAXCLS];
-  int uniform_tiles = 0;
-  if (!make_geometry(pvec, cls, txc, tyc, tzc, bsz, geo, off, total_tiles, uniform_tiles, cls_tiles))
+  if (!make_geometry(pvec, cls, txc, tyc, tzc, bsz, geo, off, total_tiles, cls_tiles))
     return DSP_ERR_UNSUPPORTED;
   dsp_ctx *c = new dsp_ctx();
   memset(&c->d, 0, sizeof c->d);
@@ -956,7 +956,6 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.ns = prm->nslices;
   d.ncls = ncls;
   for (int k = 0; k < MAXCLS; k++) d.cls_tiles[k] = cls_tiles[k];
-  d.uniform_tiles = uniform_tiles;
   d.total_tiles = total_tiles;
   d.slot_stride = off;
   d.nlev = nlev;
@@ -1107,12 +1106,8 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
             alloc((void **)&c->pk_meta, sizeof(double) * 3 * npatch) &&
             (!prm->owned || alloc((void **)&c->owned_d, sizeof(int) * npatch));
   if (ok && prm->dispatcher == 0) {
-    const size_t C = 2 * (size_t)npatch;
-    ok = alloc((void **)&c->q_patch, sizeof(int) * C) && alloc((void **)&c->q_dt, sizeof(double) * C) &&
-         alloc((void **)&c->q_seq, sizeof(unsigned long long) * C) &&
-         alloc((void **)&c->q_free, sizeof(unsigned long long) * C) &&
-         alloc((void **)&c->q_claim, sizeof(unsigned long long) * C) &&
-         alloc((void **)&c->q_ctl, sizeof(unsigned long long) * 4) && alloc((void **)&c->p_state, sizeof(int) * npatch) &&
+    // the ring itself is sized by the tiling in force at each advance
+    ok = alloc((void **)&c->q_ctl, sizeof(unsigned long long) * 4) && alloc((void **)&c->p_state, sizeof(int) * npatch) &&
          alloc((void **)&c->tiles_done, sizeof(int) * npatch);
   }
   if (ok && cudaMallocHost((void **)&c->h_ctl, sizeof(int) * CTL_COUNT) != cudaSuccess) ok = false;
@@ -1154,7 +1149,8 @@ extern "C" int dsp_create(const dsp_patch_desc *patches, int32_t npatch, const d
   d.q_dt = c->q_dt;
   d.q_seq = c->q_seq;
   d.q_free = c->q_free;
-  d.q_claim = c->q_claim;
+  d.q_tile = c->q_tile;
+  d.q_cap = 0;
   d.q_ctl = c->q_ctl;
   d.p_state = c->p_state;
   d.tiles_done = c->tiles_done;
@@ -1238,7 +1234,33 @@ int advance_queue(dsp_ctx *c, double t_end, const long long *c0, dsp_stats *out)
     for (int i = 0; i < 2; i++) CK(cudaEventCreate(&c->ev[i]));
     c->nev = 2;
   }
+  // the ring: every queued patch's tiles (each patch is queued at most once
+  // at a time) twice over, plus a ticket per block claimed ahead of a push
+  const long long cap = 2 * c->d.total_tiles + 4096;
+  if (cap > c->q_alloc) {
+    CK(cudaStreamSynchronize(c->stream));
+    void *old[] = {c->q_patch, c->q_tile, c->q_dt, c->q_seq, c->q_free};
+    for (void *p : old)
+      if (p) cudaFree(p);
+    c->q_patch = c->q_tile = nullptr;
+    c->q_dt = nullptr;
+    c->q_seq = c->q_free = nullptr;
+    c->q_alloc = 0;
+    auto alloc = [](void **q, size_t bytes) { return cudaMalloc(q, bytes) == cudaSuccess; };
+    if (!(alloc((void **)&c->q_patch, sizeof(int) * cap) && alloc((void **)&c->q_tile, sizeof(int) * cap) &&
+          alloc((void **)&c->q_dt, sizeof(double) * cap) && alloc((void **)&c->q_seq, sizeof(unsigned long long) * cap) &&
+          alloc((void **)&c->q_free, sizeof(unsigned long long) * cap)))
+      return fail(c, DSP_ERR_OOM, "cannot allocate the ready queue's ring of %lld tiles", cap);
+    c->q_alloc = cap;
+    c->d.q_patch = c->q_patch;
+    c->d.q_tile = c->q_tile;
+    c->d.q_dt = c->q_dt;
+    c->d.q_seq = c->q_seq;
+    c->d.q_free = c->q_free;
+  }
+  c->d.q_cap = cap;
   if (launch_plan(c, t_end, 0, 0)) return fail(c, DSP_ERR_CUDA, "dispatcher kernel launch failed");
+  queue_ring_kernel<<<(int)std::min<long long>((cap + 255) / 256, 1024), 256, 0, c->stream>>>(c->d);
   queue_init_kernel<<<1, 1024, 0, c->stream>>>(c->d, t_end);
   CK(cudaGetLastError());
   if (timing) CK(cudaEventRecord(c->ev[0], c->stream));

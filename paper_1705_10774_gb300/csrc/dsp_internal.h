@@ -57,7 +57,6 @@ constexpr int TABMAX = 128;
 struct DevCtx {
   int np, ns;
   int ncls;                // size classes (1..MAXCLS)
-  int uniform_tiles;       // tiles per patch when all patches have the same size, else 0
   long long total_tiles;   // tiles of all patches
   long long cls_tiles[MAXCLS];  // tiles of each class's patches
   long long slot_stride;   // elements of one slice of all patches
@@ -110,13 +109,15 @@ struct DevCtx {
   long long *cnt;          // [CNT_COUNT]
   dsp_sched_entry *sched;  // [sched_cap]
   long long sched_cap;
-  // persistent ready queue (dispatcher 0): a ring of 2*np entries
-  int *q_patch;                    // [2np] patch of each ring slot
-  double *q_dt;                    // [2np] its step
-  unsigned long long *q_seq;       // [2np] sequence number published in the slot
-  unsigned long long *q_free;      // [2np] sequence number the slot may take next
-  unsigned long long *q_claim;     // [2np] the slot's entry << 24 | its tiles claimed so far
-  unsigned long long *q_ctl;       // [4]: 0 entry whose tiles are being claimed, 1 next entry, 2 patches done
+  // persistent ready queue (dispatcher 0): a ring of q_cap tile tickets,
+  // each one work item (a tile of a queued patch)
+  long long q_cap;                 // ring slots: twice the tiles of all patches, plus the blocks' tickets
+  int *q_patch;                    // [q_cap] patch of each ring slot
+  int *q_tile;                     // [q_cap] the tile of that patch
+  double *q_dt;                    // [q_cap] its step
+  unsigned long long *q_seq;       // [q_cap] ticket published in the slot
+  unsigned long long *q_free;      // [q_cap] ticket the slot may take next
+  unsigned long long *q_ctl;       // [4]: 0 next ticket to claim, 1 next ticket to push, 2 patches done
   int *p_state;                    // [np] 0 idle, 1 queued or being updated
   int *tiles_done;                 // [np]
   long long wait_budget;           // clock64 cycles a wait may spin before DSP_ERR_TIMEOUT

@@ -1181,32 +1181,35 @@ __global__ void __launch_bounds__(NT, MINB) update_kernel(DevCtx c, int cls, int
 }
 
 // ---------------------------------------------------------------- ready queue
-// The ring holds 2*np slots; entry e lives in slot e % (2*np).  A producer
-// may fill slot s with entry e once q_free[s] == e; a consumer may read it
-// once q_seq[s] == e.  Entries carry their patch's own tile count: blocks
-// claim the tiles of the head entry (q_ctl[0]) one at a time with a
-// compare-and-swap on q_claim[s] = e << 24 | tiles claimed, whose entry part
-// keeps a late block from claiming in a slot that has moved on; the block
-// taking an entry's last tile advances the head and frees the slot.  Every
-// wait is bounded by c.wait_budget clock cycles, after which the waiter
-// records DSP_ERR_TIMEOUT and the kernel winds down.
+// The queue is a ring of c.q_cap tile tickets: pushing patch Q takes the
+// next T_Q tickets (one atomic add on q_ctl[1]) and publishes one slot per
+// tile; a block claims the next ticket (one atomic add on q_ctl[0]) and
+// waits until its slot carries that ticket.  Ticket t lives in slot
+// t % q_cap; a producer may fill the slot once q_free == t, a consumer read
+// it once q_seq == t.  Patches of different sizes simply take different
+// numbers of tickets.  Every wait is bounded by c.wait_budget clock cycles,
+// after which the waiter records DSP_ERR_TIMEOUT and the kernel winds down.
 
 static __device__ __forceinline__ void queue_push(const DevCtx &c, int Q, double dt) {
-  const unsigned long long C = 2ull * (unsigned long long)c.np;
-  const unsigned long long e = atomicAdd(&c.q_ctl[1], 1ull);
-  const int slot = (int)(e % C);
-  const long long t0 = clock64();
-  while (ld_acquire(&c.q_free[slot]) != e) {
-    if (clock64() - t0 > c.wait_budget || ld_acquire(&c.ctl[CTL_STATUS]) != 0) {
-      set_error(c, DSP_ERR_TIMEOUT, Q, -1);
-      return;
+  const unsigned long long C = (unsigned long long)c.q_cap;
+  const int T = c.geo[Q].tiles;
+  const unsigned long long t0 = atomicAdd(&c.q_ctl[1], (unsigned long long)T);
+  for (int k = 0; k < T; k++) {
+    const unsigned long long t = t0 + k;
+    const long long slot = (long long)(t % C);
+    const long long c0 = clock64();
+    while (ld_acquire(&c.q_free[slot]) != t) {
+      if (clock64() - c0 > c.wait_budget || ld_acquire(&c.ctl[CTL_STATUS]) != 0) {
+        set_error(c, DSP_ERR_TIMEOUT, Q, -1);
+        return;
+      }
+      __nanosleep(100);
     }
-    __nanosleep(100);
+    c.q_patch[slot] = Q;
+    c.q_tile[slot] = k;
+    c.q_dt[slot] = dt;
+    st_release(&c.q_seq[slot], t);
   }
-  c.q_patch[slot] = Q;
-  c.q_dt[slot] = dt;
-  c.q_claim[slot] = e << 24;
-  st_release(&c.q_seq[slot], e);
 }
 
 // Queue Q if it is idle and ready; the claim (p_state 0 -> 1) makes sure only
@@ -1274,12 +1277,14 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
   __shared__ int s_P, s_tile, s_exit, s_last;
   __shared__ double s_dt;
   const int tid = threadIdx.x;
-  const unsigned long long C = 2ull * (unsigned long long)c.np;
+  const unsigned long long C = (unsigned long long)c.q_cap;
   for (;;) {
     if (tid == 0) {
       s_exit = 0;
+      const unsigned long long t = atomicAdd(&c.q_ctl[0], 1ull);
+      const long long slot = (long long)(t % C);
       const long long t0 = clock64();
-      for (;;) {
+      while (ld_acquire(&c.q_seq[slot]) != t) {
         if (ld_acquire(&c.q_ctl[2]) >= (unsigned long long)c.np || ld_acquire(&c.ctl[CTL_STATUS]) != 0) {
           s_exit = 1;
           break;
@@ -1289,34 +1294,13 @@ __global__ void __launch_bounds__(NT, MINB) queue_kernel(DevCtx c, double t_end)
           s_exit = 1;
           break;
         }
-        const unsigned long long e = ld_acquire(&c.q_ctl[0]);
-        const int slot = (int)(e % C);
-        const unsigned long long seq = ld_acquire(&c.q_seq[slot]);
-        if (seq != e) {
-          // not published yet (wait), or the slot has moved past e (the head
-          // read was stale: read it again)
-          if (seq == ~0ull || seq < e) __nanosleep(200);
-          continue;
-        }
-        const int P = __ldcg(c.q_patch + slot);
-        const double dt = __ldcg(c.q_dt + slot);
-        const unsigned long long v = ld_acquire(&c.q_claim[slot]);
-        if ((v >> 24) != e) continue;  // the slot was refilled meanwhile
-        const int T = c.geo[P].tiles;
-        const int got = (int)(v & 0xffffffull);
-        if (got >= T) {  // every tile claimed: help the head along
-          atomicCAS(&c.q_ctl[0], e, e + 1);
-          continue;
-        }
-        if (atomicCAS(&c.q_claim[slot], v, v + 1) != v) continue;
-        if (got == T - 1) {  // the entry's last tile: advance the head, free the slot
-          atomicCAS(&c.q_ctl[0], e, e + 1);
-          st_release(&c.q_free[slot], e + C);
-        }
-        s_P = P;
-        s_dt = dt;
-        s_tile = got;
-        break;
+        __nanosleep(200);
+      }
+      if (!s_exit) {
+        s_P = __ldcg(c.q_patch + slot);
+        s_tile = __ldcg(c.q_tile + slot);
+        s_dt = __ldcg(c.q_dt + slot);
+        st_release(&c.q_free[slot], t + C);
       }
     }
     __syncthreads();
