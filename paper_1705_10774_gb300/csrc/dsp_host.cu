@@ -541,7 +541,7 @@ int launch_plan(dsp_ctx *c, double t_end, int global_mode, int publish_only) {
 // only), after the plan kernel and before the update kernel of a sweep.
 int launch_xlevel(dsp_ctx *c) {
   if (c->d.nlev < 2) return DSP_OK;
-  const int grid = std::max(1, std::min(c->n_xlevel, 4096));
+  const int grid = std::max(1, std::min(c->n_xlevel * XL_PARTS, 8192));
   if (c->precision == 1) xlevel_kernel<float><<<grid, 256, 0, c->stream>>>(c->d);
   else xlevel_kernel<double><<<grid, 256, 0, c->stream>>>(c->d);
   return cudaGetLastError() == cudaSuccess ? DSP_OK : DSP_ERR_CUDA;

@@ -172,12 +172,51 @@ __device__ __forceinline__ bool xl_cross(const DevCtx &c, int lev, const int g[3
   return c.gmap[lev][xl_block(c, lev, w)] < 0;
 }
 
-// Fill patch P's cross-level guard buffer for its current time (all threads
-// of the block).  The buffer is laid out like a slice of a patch of m = n+4
+// Position x (box coordinates, each in [0, b_d)) of shell item s of a box
+// of b0 x b1 x b2 points around an inner box [2, b_d - 2) per axis: the 2-deep
+// shell, enumerated as the four outer z-planes, then the four outer y-rows
+// of the inner z-range, then the four outer x-points of the inner y- and
+// z-range.  The shell has b0 b1 b2 - (b0-4)(b1-4)(b2-4) items.
+__device__ __forceinline__ void xl_shell(long long s, const int b[3], int x[3]) {
+  const long long pz = (long long)b[0] * b[1];
+  if (s < 4 * pz) {
+    const int k = (int)(s / pz);
+    const long long r = s - k * pz;
+    x[2] = k < 2 ? k : b[2] - 4 + k;
+    x[1] = (int)(r / b[0]);
+    x[0] = (int)(r % b[0]);
+    return;
+  }
+  s -= 4 * pz;
+  const long long py = 4ll * b[0];
+  if (s < py * (b[2] - 4)) {
+    x[2] = 2 + (int)(s / py);
+    const long long r = s % py;
+    const int k = (int)(r / b[0]);
+    x[1] = k < 2 ? k : b[1] - 4 + k;
+    x[0] = (int)(r % b[0]);
+    return;
+  }
+  s -= py * (b[2] - 4);
+  const long long px = 4ll * (b[1] - 4);
+  x[2] = 2 + (int)(s / px);
+  const long long r = s % px;
+  x[1] = 2 + (int)(r / 4);
+  const int k = (int)(r % 4);
+  x[0] = k < 2 ? k : b[0] - 4 + k;
+}
+__device__ __forceinline__ long long xl_shell_count(const int b[3]) {
+  return (long long)b[0] * b[1] * b[2] - (long long)(b[0] - 4) * (b[1] - 4) * (b[2] - 4);
+}
+
+// Fill patch P's cross-level guard buffer for its current time (block part
+// `part` of `parts`: its items are part*blockDim.x + threadIdx.x, step
+// parts*blockDim.x).  The buffer is laid out like a slice of a patch of m = n+4
 // cells per axis whose first cell is P's cell lo-2: cells x in [-2, n+2),
 // faces along an axis at x in [-2, n+2] (relative to lo).
 template <typename T>
-__device__ void fill_cross_level(const DevCtx &c, int P) {
+__device__ void fill_cross_level(const DevCtx &c, int P, int part, int parts) {
+  const long long i0 = (long long)part * blockDim.x + threadIdx.x, istep = (long long)parts * blockDim.x;
   const PatchGeo &gp = c.geo[P];
   const int lev = gp.level;
   const int n[3] = {gp.n[0], gp.n[1], gp.n[2]};
@@ -207,9 +246,13 @@ __device__ void fill_cross_level(const DevCtx &c, int P) {
   };
   if (lev == 0) {
     // restriction: guard cells and faces whose cell is covered by level 1
-    for (long long id = threadIdx.x; id < mc3; id += blockDim.x) {
-      const int x[3] = {(int)(id % m[0]) - 2, (int)((id / m[0]) % m[1]) - 2, (int)(id / ((long long)m[0] * m[1])) - 2};
-      if (interior(x)) continue;
+    // (the guard cells are the 2-deep shell of the (n+4)^3 box)
+    const long long ncs = xl_shell_count(m);
+    for (long long si = i0; si < ncs; si += istep) {
+      int b[3];
+      xl_shell(si, m, b);
+      const int x[3] = {b[0] - 2, b[1] - 2, b[2] - 2};
+      const long long id = ((long long)b[2] * m[1] + b[1]) * m[0] + b[0];
       const int g[3] = {gp.lo[0] + x[0], gp.lo[1] + x[1], gp.lo[2] + x[2]};
       if (!xl_cross(c, 0, g)) continue;
       T u[5];
@@ -221,11 +264,14 @@ __device__ void fill_cross_level(const DevCtx &c, int P) {
       for (int q = 0; q < 5; q++) buf[q * mc3 + id] = u[q];
     }
     for (int ax = 0; ax < 3; ax++) {
-      const int f0 = m[0] + (ax == 0), f1 = m[1] + (ax == 1), f2 = m[2] + (ax == 2);
-      const long long nf = (long long)f0 * f1 * f2;
-      for (long long id = threadIdx.x; id < nf; id += blockDim.x) {
-        const int x[3] = {(int)(id % f0) - 2, (int)((id / f0) % f1) - 2, (int)(id / ((long long)f0 * f1)) - 2};
-        if (own_face(ax, x)) continue;
+      // the faces along ax not P's own: the 2-deep shell of the face box
+      const int fb[3] = {m[0] + (ax == 0), m[1] + (ax == 1), m[2] + (ax == 2)};
+      const long long nfs = xl_shell_count(fb);
+      for (long long si = i0; si < nfs; si += istep) {
+        int b[3];
+        xl_shell(si, fb, b);
+        const int x[3] = {b[0] - 2, b[1] - 2, b[2] - 2};
+        const long long id = ((long long)b[2] * fb[1] + b[1]) * fb[0] + b[0];
         const int g[3] = {gp.lo[0] + x[0], gp.lo[1] + x[1], gp.lo[2] + x[2]};
         if (!xl_cross(c, 0, g)) continue;
         T v;
@@ -247,7 +293,7 @@ __device__ void fill_cross_level(const DevCtx &c, int P) {
     cn[d] = xl_floordiv(gp.lo[d] + n[d] + 2, 2) - c0[d] + 1;
   }
   const long long npar = (long long)cn[0] * cn[1] * cn[2];
-  for (long long id = threadIdx.x; id < npar; id += blockDim.x) {
+  for (long long id = i0; id < npar; id += istep) {
     const int C[3] = {c0[0] + (int)(id % cn[0]), c0[1] + (int)((id / cn[0]) % cn[1]),
                       c0[2] + (int)(id / ((long long)cn[0] * cn[1]))};
     const int f0[3] = {2 * C[0], 2 * C[1], 2 * C[2]};
@@ -321,14 +367,15 @@ __device__ void fill_cross_level(const DevCtx &c, int P) {
   }
 }
 
-// One block per ready patch that has a cross-level guard buffer.
+// XL_PARTS blocks per ready patch that has a cross-level guard buffer.
+constexpr int XL_PARTS = 8;
 template <typename T>
 __global__ void __launch_bounds__(256) xlevel_kernel(DevCtx c) {
   const int nr = c.ctl[CTL_NREADY];
-  for (int r = blockIdx.x; r < nr; r += gridDim.x) {
-    const int P = c.R[r];
+  for (long long w = blockIdx.x; w < (long long)nr * XL_PARTS; w += gridDim.x) {
+    const int P = c.R[w / XL_PARTS];
     if (c.gofs[P] < 0) continue;
-    fill_cross_level<T>(c, P);
+    fill_cross_level<T>(c, P, (int)(w % XL_PARTS), XL_PARTS);
   }
 }
 
