@@ -43,11 +43,16 @@ struct FBits<float> {
   static __device__ __forceinline__ float to(I i) { return __int_as_float(i); }
   static constexpr I MAG = 0x7fffffff, INF = 0x7f800000;
 };
-// |a| (as fabs: the sign bit cleared, for every input)
+// |a| (as fabs: the sign bit cleared, for every input); in FP32 the native
+// form, which the FP32 pipe folds into the operation that uses it
 template <typename T>
 __device__ __forceinline__ T tabs(T a) {
-  using B = FBits<T>;
-  return B::to(B::of(a) & B::MAG);
+  if constexpr (sizeof(T) == 4) {
+    return fabsf(a);
+  } else {
+    using B = FBits<T>;
+    return B::to(B::of(a) & B::MAG);
+  }
 }
 // a > 0 (for every input, NaN included)
 template <typename T>
@@ -290,6 +295,11 @@ __device__ __forceinline__ T mc(T dl, T dr) {
     const int es = (int)(is >> 52);
     const long long i2 = es == 0 ? is << 1 : es < 2046 ? is + one : es == 2046 ? 0x7ff0000000000000ll : is;
     return __longlong_as_double(a < 0 ? i2 | (long long)0x8000000000000000ull : i2);
+  } else if constexpr (sizeof(T) == 4) {
+    // FP32: the FP32 pipe's own minimum (the same value as the bit-pattern
+    // minimum of non-negative values) and absolute-value modifiers
+    const T s = fminf(fminf(T(2) * fabsf(dl), T(2) * fabsf(dr)), T(0.5) * fabsf(dl + dr));
+    return a < 0 ? B::to(B::of(s) ^ ~B::MAG) : s;
   } else {
     const T s = tmin_nonneg(tmin_nonneg(T(2) * tabs(dl), T(2) * tabs(dr)), T(0.5) * tabs(dl + dr));
     return a < 0 ? B::to(B::of(s) ^ ~B::MAG) : s;
