@@ -62,7 +62,7 @@ NONIDEAL = dict(eta=1e-4, gamma_ad=75.0, rho_i=1.0)
 # of one launch divided by the cells it updated (captures of smaller cases
 # of the same kernel: traffic grows in proportion to the cells); a variant
 # without an entry reports null.
-TRAFFIC_PER_CELL = {4: (555.389952e6 + 432.454656e6) / 7077888, 5: (237.393920e6 + 193.476096e6) / 7077888,
+TRAFFIC_PER_CELL = {4: (555.389952e6 + 432.454656e6) / 7077888, 5: (237.726720e6 + 193.273088e6) / 7077888,
                     10: (542.026496e6 + 422.849280e6) / 7077888, 15: (527.585792e6 + 424.571136e6) / 7077888}
 
 
